@@ -1,0 +1,208 @@
+/*
+ * rbffd.h -- C ABI of the GB300 RBF-FD Poisson library.
+ *
+ * The library computes, on one GPU, the pipeline of the RBF-FD solution of
+ * Poisson's equation on scattered 2D nodes (Jancic, Slak, Kosec, "GPU
+ * accelerated RBF-FD solution of Poisson's equation", arXiv 2107.03632):
+ *
+ *   stencils  -> for every node, its n nearest nodes        (Sec. II, Eq. 1)
+ *   weights   -> RBF-FD Laplacian weights, PHS r^3 + monomials of degree
+ *                <= m, one augmented system per stencil      (Sec. II Eq. 1, Sec. V)
+ *   assemble  -> the discrete Poisson operator, Dirichlet rows  (Sec. IV, Eqs. 2-4)
+ *   rhs       -> b = -f on interior rows, g on Dirichlet rows   (Sec. IV, Eqs. 2-3)
+ *   solve     -> BiCGSTAB on A u = b, FP64 or FP32-inner/FP64
+ *                refinement (the implicit solve of Sec. VI)
+ *   solve_adjoint -> A^T lambda = dL/du and the gradients dL/df, dL/dg
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers owned by the caller, unless a
+ *    comment says "host".  The library allocates no device memory; scratch
+ *    space is a caller-provided workspace whose size the matching
+ *    *_workspace_size function returns (workspace pointers must be 256-byte
+ *    aligned).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on that stream; calls return before it completes unless
+ *    the comment says the call blocks.
+ *  - Node coordinates xy are an N x 2 row-major float64 array (x0, y0, x1, ...).
+ *    Stencils idx and weights w are N x n row-major (row i = node i).
+ *  - Node indices are int32 (N < 2^31).
+ *  - Return value: an rbffd_status.  Argument errors are detected on the host
+ *    before anything is enqueued and nothing is written.  RBFFD_ERR_CUDA means
+ *    a launch failed; the CUDA error string is available from
+ *    rbffd_last_cuda_error().
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rbffd_status {
+    RBFFD_OK = 0,
+    RBFFD_ERR_INVALID_ARG = 1,      /* bad size, null pointer, unsupported m/n */
+    RBFFD_ERR_CUDA = 2,             /* a CUDA call or launch failed */
+    RBFFD_ERR_SINGULAR_STENCIL = 3, /* reported per node in node_status */
+    RBFFD_ERR_NOT_CONVERGED = 4,    /* iteration cap reached */
+    RBFFD_ERR_BREAKDOWN = 5,        /* BiCGSTAB breakdown persisted after a restart */
+    RBFFD_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
+    RBFFD_ERR_WORKSPACE = 7         /* workspace too small or misaligned */
+} rbffd_status;
+
+/* Human-readable name of a status code (static string, host). */
+const char* rbffd_status_string(int status);
+
+/* Text of the last CUDA error seen by this library on the calling thread (host). */
+const char* rbffd_last_cuda_error(void);
+
+/* ABI version: 100 * major + minor. */
+int rbffd_version(void);
+
+/* Largest supported stencil size n. */
+#define RBFFD_MAX_STENCIL 128
+
+/* ------------------------------------------------------------------------ */
+/* Stencil (support) selection -- Sec. II, Eq. 1: N(x) is the set of nodes   */
+/* whose values approximate the operator at x; Sec. V uses the n nearest     */
+/* nodes.                                                                    */
+/*                                                                           */
+/* For every node i, idx[i*n + 0 .. n-1] receives the n nodes nearest to     */
+/* node i among all N nodes, node i itself included (first, distance 0),     */
+/* ordered by squared distance d^2 = dx*dx + dy*dy (each product rounded,    */
+/* no fused multiply-add) and, for equal d^2, by the smaller node index.     */
+/* The result is exact (identical to brute force).                           */
+/*   xy  : N x 2 float64, read only.                                         */
+/*   n   : 1 <= n <= min(N, RBFFD_MAX_STENCIL).                              */
+/*   idx : N x n int32, written.                                             */
+/*   ws  : rbffd_stencils_workspace_size(N, n) bytes of device scratch.      */
+/* Non-finite coordinates give unspecified stencils for those nodes (finite  */
+/* nodes never select them).                                                 */
+/* ------------------------------------------------------------------------ */
+size_t rbffd_stencils_workspace_size(int64_t N, int32_t n);
+int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* idx,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* RBF-FD Laplacian weights -- Sec. II, Eq. 1 with the basis of Sec. V:      */
+/* Phi(r) = r^3 augmented with all 2D monomials of degree <= m.              */
+/*                                                                           */
+/* For each node i with stencil idx[i*n ..], the augmented system            */
+/*      [ Phi  P ] [ w ]   [ lap phi_j(x_i) ]      Phi_jk = |x_j - x_k|^3    */
+/*      [ P^T  0 ] [ l ] = [ lap p_k(x_i)   ]      P_jk   = p_k(x_j)         */
+/* is formed in coordinates shifted to x_i and scaled by delta_i (the        */
+/* largest |x_j - x_i| in the stencil), solved in FP64 by Gaussian           */
+/* elimination with partial pivoting, and w[i*n + j] = wh_j / delta_i^2.     */
+/* Monomials are in graded order 1, x, y, x^2, xy, y^2, ...; s = (m+1)(m+2)/2.*/
+/*   m           : 0 <= m <= 8 and s <= n (the system needs n >= s nodes).   */
+/*   w           : N x n float64, written (rows of singular stencils: 0).    */
+/*   node_status : N int32 or NULL; 0 = ok, 1 = singular/non-finite system.  */
+/* No workspace.                                                             */
+/* ------------------------------------------------------------------------ */
+int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
+                  double* w, int32_t* node_status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Assembly -- Sec. IV, Eqs. 2-4 at steady state: interior rows carry the    */
+/* RBF-FD Laplacian (A[i, idx[i,j]] = w[i,j], stencil order), Dirichlet rows */
+/* carry the identity (A[i,i] = 1).  CSR with int64 row pointers.            */
+/*                                                                           */
+/* rbffd_assemble_pattern writes row_ptr (N+1 int64): rows have n entries,  */
+/* Dirichlet rows 1.  nnz = row_ptr[N] = (N - N_dirichlet) * n + N_dirichlet.*/
+/* rbffd_assemble then writes col (nnz int32) and val (nnz float64) and, if  */
+/* val32 is not NULL, a float32 copy of val.  Rows whose range in row_ptr    */
+/* would pass nnz are not written.                                           */
+/*   is_dirichlet : N uint8 (nonzero = boundary node with a Dirichlet row).  */
+/*   ws           : rbffd_assemble_workspace_size(N) bytes.                  */
+/* ------------------------------------------------------------------------ */
+size_t rbffd_assemble_workspace_size(int64_t N);
+int rbffd_assemble_pattern(const uint8_t* is_dirichlet, int64_t N, int32_t n,
+                           int64_t* row_ptr, void* ws, size_t ws_bytes, void* stream);
+int rbffd_assemble(const int32_t* idx, const double* w, const uint8_t* is_dirichlet,
+                   int64_t N, int32_t n, const int64_t* row_ptr, int64_t nnz,
+                   int32_t* col, double* val, float* val32, void* stream);
+
+/* Right-hand side -- Sec. IV, Eqs. 2-3 at steady state (-lap u = f inside,  */
+/* u = g on the boundary): b[i] = g[i] if is_dirichlet[i] else -f[i].        */
+int rbffd_rhs(const double* f, const double* g, const uint8_t* is_dirichlet, int64_t N,
+              double* b, void* stream);
+
+/* CSR descriptor (host struct holding device pointers). */
+typedef struct rbffd_csr {
+    int64_t n_rows;          /* square matrix: n_rows x n_rows */
+    int64_t nnz;
+    const int64_t* row_ptr;  /* n_rows + 1 */
+    const int32_t* col;      /* nnz */
+    const void* val;         /* nnz, float64 (dtype 0) or float32 (dtype 1) */
+    int32_t dtype;
+} rbffd_csr;
+
+/* Transpose A (float64 values) into CSR of A^T.  Within a row of A^T the    */
+/* entries are in increasing column order (deterministic).                   */
+/*   row_ptr_t : n_rows + 1 int64, col_t : nnz int32, val_t : nnz float64.   */
+/*   ws        : rbffd_transpose_workspace_size(n_rows) bytes.               */
+size_t rbffd_transpose_workspace_size(int64_t n_rows);
+int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Krylov solve -- the implicit solution named in Sec. VI: A x = b by       */
+/* BiCGSTAB (van der Vorst 1992) with left Jacobi scaling D^-1 A x = D^-1 b. */
+/* Convergence is judged on the unscaled system: |b - A x|_2 <= tol |b|_2,   */
+/* confirmed by an explicitly recomputed residual before returning OK.       */
+/*                                                                           */
+/* precision 0 (FP64): matrix, vectors and scalars in float64.               */
+/* precision 1 (mixed): an FP64 refinement loop (r = b - A x with the FP64   */
+/*   matrix, x += correction in FP64) around inner BiCGSTAB iterations that  */
+/*   read the float32 copy of the matrix (A32, same pattern as A); an inner  */
+/*   pass ends when its residual has fallen by inner_tol.                    */
+/*                                                                           */
+/* x is in/out: the initial guess on entry, the solution on exit (warm       */
+/* start).  The call BLOCKS the host until the solve ends and synchronises   */
+/* `stream`; *info (host) receives the outcome.  A breakdown (rho or omega  */
+/* zero or non-finite) restarts once from the true residual before           */
+/* RBFFD_ERR_BREAKDOWN is returned.                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct rbffd_solve_opts {
+    double tol;          /* relative residual target, e.g. 1e-10 */
+    int32_t max_iter;    /* cap on (inner) BiCGSTAB iterations in total */
+    int32_t precision;   /* 0 = FP64, 1 = mixed FP32-inner / FP64 refinement */
+    double inner_tol;    /* mixed: residual reduction per refinement pass, e.g. 1e-5 */
+    int32_t max_outer;   /* mixed: cap on refinement passes */
+    int32_t jacobi;      /* 1 = left Jacobi scaling (default), 0 = none */
+} rbffd_solve_opts;
+
+typedef struct rbffd_solve_info {
+    int32_t status;       /* rbffd_status of the solve */
+    int32_t iters;        /* BiCGSTAB iterations performed (inner, in total) */
+    int32_t outer_sweeps; /* refinement passes (mixed) or residual checks (FP64) */
+    int32_t restarts;     /* breakdown or residual-drift restarts */
+    double rel_residual;  /* final |b - A x| / |b| with the FP64 matrix */
+} rbffd_solve_info;
+
+size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* opts);
+int rbffd_solve(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x,
+                const rbffd_solve_opts* opts, rbffd_solve_info* info,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint solve -- gradient of a loss L(u) of the solution u = A^{-1} b.    */
+/* Solves A^T lambda = dLdu with the same solver as rbffd_solve, given AT =  */
+/* A^T (from rbffd_transpose), then, since b = -f inside and b = g on the    */
+/* boundary:  dLdf[i] = -lambda[i] (interior), 0 (Dirichlet);                */
+/*            dLdg[i] = lambda[i] (Dirichlet), 0 (interior).                 */
+/* dLdf and dLdg may be NULL.  lambda is in/out (initial guess).  Blocks    */
+/* like rbffd_solve.  Workspace: rbffd_solve_workspace_size.                 */
+/* ------------------------------------------------------------------------ */
+int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_t* is_dirichlet,
+                        const double* dLdu, double* lambda, double* dLdf, double* dLdg,
+                        const rbffd_solve_opts* opts, rbffd_solve_info* info,
+                        void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFFD_H */

@@ -1,0 +1,202 @@
+// Assembly of the discrete Poisson operator (CSR, Dirichlet rows), the
+// right-hand side, and the CSR transpose used by the adjoint solve.
+//
+// Sec. IV, Eqs. 2-4 at steady state: interior rows hold the RBF-FD Laplacian
+// weights of the node's stencil (A[i, idx[i,j]] = w[i,j], stencil order),
+// Dirichlet rows the identity; b = -f inside, g on the boundary.
+#include "common.cuh"
+#include "scan.cuh"
+
+#include <algorithm>
+
+namespace rbffd {
+namespace {
+
+struct RowLenLoad {
+    const uint8_t* mask;
+    int64_t n;
+    __device__ int64_t operator()(int64_t i) const { return mask[i] ? (int64_t)1 : n; }
+};
+
+// One warp per row: copy the stencil and its weights into the row's range.
+__global__ void __launch_bounds__(256) assemble_fill_kernel(const int* __restrict__ idx, const double* __restrict__ w,
+                                                            const uint8_t* __restrict__ mask, int64_t N, int n,
+                                                            const int64_t* __restrict__ row_ptr, int64_t nnz,
+                                                            int* __restrict__ col, double* __restrict__ val,
+                                                            float* __restrict__ val32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp0; i < N; i += nwarps) {
+        const int64_t a = row_ptr[i];
+        const bool dir = mask[i] != 0;
+        const int len = dir ? 1 : n;
+        if (a < 0 || a + len > nnz) continue;  // inconsistent row_ptr: never write past nnz
+        if (dir) {
+            if (lane == 0) {
+                col[a] = (int)i;
+                val[a] = 1.0;
+                if (val32) val32[a] = 1.0f;
+            }
+        } else {
+            const int* si = idx + i * n;
+            const double* wi = w + i * n;
+            for (int j = lane; j < n; j += 32) {
+                const double v = wi[j];
+                col[a + j] = si[j];
+                val[a + j] = v;
+                if (val32) val32[a + j] = __double2float_rn(v);
+            }
+        }
+    }
+}
+
+__global__ void rhs_kernel(const double* __restrict__ f, const double* __restrict__ g,
+                           const uint8_t* __restrict__ mask, int64_t N, double* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = mask[i] ? g[i] : -f[i];
+}
+
+// ---- transpose ------------------------------------------------------------
+// count entries per column (warp per row, lanes over the row's entries)
+__global__ void col_count_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col, int64_t N,
+                                 int64_t nnz, int* __restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp0; r < N; r += nwarps) {
+        const int64_t a = max(row_ptr[r], (int64_t)0), e = min(row_ptr[r + 1], nnz);
+        for (int64_t k = a + lane; k < e; k += 32) {
+            const int c = col[k];
+            if ((unsigned)c < (unsigned)N) atomicAdd(&counts[c], 1);
+        }
+    }
+}
+
+struct CountLoad64 {
+    const int* counts;
+    __device__ int64_t operator()(int64_t i) const { return (int64_t)counts[i]; }
+};
+
+// counts[c] runs down from the column length to 1: positions fill
+// [row_ptr_t[c], row_ptr_t[c+1]) once each (order fixed afterwards).
+__global__ void transpose_scatter_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                         const double* __restrict__ val, int64_t N, int64_t nnz,
+                                         const int64_t* __restrict__ row_ptr_t, int* __restrict__ counts,
+                                         int* __restrict__ col_t, double* __restrict__ val_t) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp0; r < N; r += nwarps) {
+        const int64_t a = max(row_ptr[r], (int64_t)0), e = min(row_ptr[r + 1], nnz);
+        for (int64_t k = a + lane; k < e; k += 32) {
+            const int c = col[k];
+            if ((unsigned)c >= (unsigned)N) continue;
+            const int64_t pos = row_ptr_t[c + 1] - atomicSub(&counts[c], 1);
+            col_t[pos] = (int)r;
+            val_t[pos] = val[k];
+        }
+    }
+}
+
+// Sort each row of A^T by column index (insertion sort; rows are short).
+__global__ void row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N, int* __restrict__ col_t,
+                                double* __restrict__ val_t) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr_t[r], e = row_ptr_t[r + 1];
+        for (int64_t k = a + 1; k < e; ++k) {
+            const int c = col_t[k];
+            const double v = val_t[k];
+            int64_t q = k - 1;
+            while (q >= a && col_t[q] > c) {
+                col_t[q + 1] = col_t[q];
+                val_t[q + 1] = val_t[q];
+                --q;
+            }
+            col_t[q + 1] = c;
+            val_t[q + 1] = v;
+        }
+    }
+}
+
+int grid_for(int64_t work, int per_block) {
+    const int64_t b = (work + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 16));
+}
+
+}  // namespace
+}  // namespace rbffd
+
+extern "C" size_t rbffd_assemble_workspace_size(int64_t N) {
+    if (N <= 0) return 0;
+    rbffd::Carver c(nullptr);
+    c.take<int64_t>(rbffd::scan_tiles(N) + 1);
+    return c.off;
+}
+
+extern "C" int rbffd_assemble_pattern(const uint8_t* is_dirichlet, int64_t N, int32_t n, int64_t* row_ptr, void* ws,
+                                      size_t ws_bytes, void* stream) {
+    using namespace rbffd;
+    if (!is_dirichlet || !row_ptr || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL)
+        return RBFFD_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < rbffd_assemble_workspace_size(N))
+        return RBFFD_ERR_WORKSPACE;
+    int64_t* sums = static_cast<int64_t*>(ws);
+    RBFFD_CUDA_TRY(exclusive_scan<int64_t>(RowLenLoad{is_dirichlet, (int64_t)n}, N, row_ptr, sums, row_ptr + N,
+                                           as_stream(stream)));
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_assemble(const int32_t* idx, const double* w, const uint8_t* is_dirichlet, int64_t N, int32_t n,
+                              const int64_t* row_ptr, int64_t nnz, int32_t* col, double* val, float* val32,
+                              void* stream) {
+    using namespace rbffd;
+    if (!idx || !w || !is_dirichlet || !row_ptr || !col || !val || N <= 0 || N > 0x7fffffffLL || n < 1 ||
+        n > RBFFD_MAX_STENCIL || nnz < 0)
+        return RBFFD_ERR_INVALID_ARG;
+    assemble_fill_kernel<<<grid_for(N * 32, 256), 256, 0, as_stream(stream)>>>(idx, w, is_dirichlet, N, n, row_ptr,
+                                                                               nnz, col, val, val32);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_rhs(const double* f, const double* g, const uint8_t* is_dirichlet, int64_t N, double* b,
+                         void* stream) {
+    using namespace rbffd;
+    if (!f || !g || !is_dirichlet || !b || N <= 0) return RBFFD_ERR_INVALID_ARG;
+    rhs_kernel<<<grid_for(N, 256), 256, 0, as_stream(stream)>>>(f, g, is_dirichlet, N, b);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+extern "C" size_t rbffd_transpose_workspace_size(int64_t n_rows) {
+    if (n_rows <= 0) return 0;
+    rbffd::Carver c(nullptr);
+    c.take<int>(n_rows);
+    c.take<int64_t>(rbffd::scan_tiles(n_rows) + 1);
+    return c.off;
+}
+
+extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t, void* ws,
+                               size_t ws_bytes, void* stream) {
+    using namespace rbffd;
+    if (!A || !A->row_ptr || !A->col || !A->val || A->dtype != 0 || !row_ptr_t || !col_t || !val_t ||
+        A->n_rows <= 0 || A->n_rows > 0x7fffffffLL || A->nnz < 0)
+        return RBFFD_ERR_INVALID_ARG;
+    const int64_t N = A->n_rows;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < rbffd_transpose_workspace_size(N))
+        return RBFFD_ERR_WORKSPACE;
+    Carver c(ws);
+    int* counts = c.take<int>(N);
+    int64_t* sums = c.take<int64_t>(scan_tiles(N) + 1);
+    cudaStream_t st = as_stream(stream);
+    const double* val = static_cast<const double*>(A->val);
+    RBFFD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * N, st));
+    col_count_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, N, A->nnz, counts);
+    RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{counts}, N, row_ptr_t, sums, row_ptr_t + N, st));
+    transpose_scatter_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, val, N, A->nnz, row_ptr_t, counts,
+                                                                    col_t, val_t);
+    row_sort_kernel<<<grid_for(N, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}

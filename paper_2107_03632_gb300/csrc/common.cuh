@@ -1,0 +1,78 @@
+// Shared device/host helpers of the RBF-FD library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "rbffd.h"
+
+namespace rbffd {
+
+// Records the CUDA error text for rbffd_last_cuda_error().
+void set_cuda_error(cudaError_t e);
+
+#define RBFFD_LAUNCH_CHECK()                                   \
+    do {                                                       \
+        cudaError_t e_ = cudaGetLastError();                   \
+        if (e_ != cudaSuccess) {                               \
+            ::rbffd::set_cuda_error(e_);                       \
+            return RBFFD_ERR_CUDA;                             \
+        }                                                      \
+    } while (0)
+
+#define RBFFD_CUDA_TRY(call)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) {                               \
+            ::rbffd::set_cuda_error(e_);                       \
+            return RBFFD_ERR_CUDA;                             \
+        }                                                      \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// Carves consecutive 256-byte aligned slices out of a workspace.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* p) : base(static_cast<char*>(p)) {}
+    template <class T>
+    T* take(size_t count) {
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off = align_up(off + count * sizeof(T));
+        return p;
+    }
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ---------------------------------------------------------------- device --
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; every thread gets the result.  `sh` needs 32 doubles.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    constexpr int W = BLOCK / 32;
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (lane < W) ? sh[lane] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    return sh[0];
+}
+
+}  // namespace rbffd

@@ -1,0 +1,392 @@
+// Exact n-nearest-neighbour stencils on a uniform cell grid (sm_103a).
+//
+// Sec. II, Eq. 1: the operator at node x is approximated from the values on
+// N(x), the nodes neighbouring x; Sec. V takes the n nearest nodes.  Order of
+// a stencil: key (d^2, j) ascending, where d^2 = dx*dx + dy*dy is rounded
+// product by product (no FMA: __dmul_rn / __dadd_rn) and j is the caller's
+// node index; node x itself comes first (d^2 = 0).
+//
+// Pipeline (all on the stream, no host synchronisation):
+//   1. bounding box (block partials, then one block)         -> GridParams
+//   2. cell key per node, histogram of keys (atomics)
+//   3. exclusive scan of the histogram                       -> cell_start
+//   4. scatter nodes into cell order (SoA double2 + original index)
+//   5. one warp per query, in cell order: scan cells ring by ring around the
+//      query's cell, keep a sorted top-n list of keys distributed over the
+//      warp's registers (entry e at lane e%32, slot e/32), prune cells whose
+//      nearest point cannot beat the current n-th key, and stop once the
+//      unvisited region is provably farther than the n-th key.
+// Distances are compared as the IEEE bit patterns of non-negative doubles
+// (monotone as unsigned integers), so ranking never touches the FP64 pipe.
+#include "common.cuh"
+#include "scan.cuh"
+
+#include <cmath>
+
+namespace rbffd {
+namespace {
+
+struct GridParams {
+    double x0, y0;      // lower-left corner of the grid
+    double cell;        // cell side
+    double inv_cell;    // 1 / cell
+    double margin;      // absolute slack for the geometric pruning tests
+    int G;              // cells per axis (G x G cells)
+    int pad;
+};
+
+struct Box {
+    double mnx, mny, mxx, mxy;
+};
+
+constexpr int kBoxBlocks = 256;
+constexpr int kBoxThreads = 256;
+
+__global__ void __launch_bounds__(kBoxThreads) bbox_partial_kernel(const double2* __restrict__ xy, int64_t N,
+                                                                   Box* __restrict__ part) {
+    double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 p = xy[i];
+        mnx = fmin(mnx, p.x);
+        mny = fmin(mny, p.y);
+        mxx = fmax(mxx, p.x);
+        mxy = fmax(mxy, p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fmin(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = fmin(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    __shared__ Box sh[kBoxThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = Box{mnx, mny, mxx, mxy};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Box r = sh[0];
+        for (int k = 1; k < kBoxThreads / 32; ++k) {
+            r.mnx = fmin(r.mnx, sh[k].mnx);
+            r.mny = fmin(r.mny, sh[k].mny);
+            r.mxx = fmax(r.mxx, sh[k].mxx);
+            r.mxy = fmax(r.mxy, sh[k].mxy);
+        }
+        part[blockIdx.x] = r;
+    }
+}
+
+__global__ void grid_setup_kernel(const Box* __restrict__ part, int nparts, int G, GridParams* gp) {
+    if (threadIdx.x != 0) return;
+    Box r = part[0];
+    for (int k = 1; k < nparts; ++k) {
+        r.mnx = fmin(r.mnx, part[k].mnx);
+        r.mny = fmin(r.mny, part[k].mny);
+        r.mxx = fmax(r.mxx, part[k].mxx);
+        r.mxy = fmax(r.mxy, part[k].mxy);
+    }
+    double x0 = r.mnx, y0 = r.mny;
+    double span = fmax(r.mxx - r.mnx, r.mxy - r.mny);
+    if (!(x0 > -INFINITY && x0 < INFINITY)) x0 = 0.0;  // no finite point
+    if (!(y0 > -INFINITY && y0 < INFINITY)) y0 = 0.0;
+    if (!(span > 0.0 && span < INFINITY)) span = 1.0;    // single point / degenerate
+    GridParams p;
+    p.x0 = x0;
+    p.y0 = y0;
+    p.cell = span / G;
+    p.inv_cell = G / span;
+    p.margin = 1e-12 * (span + fabs(x0) + fabs(y0));
+    p.G = G;
+    p.pad = 0;
+    *gp = p;
+}
+
+__device__ __forceinline__ int cell_coord(double v, double v0, double inv, int G) {
+    const double t = floor((v - v0) * inv);
+    // NaN and out-of-range values are clamped (NaN compares false).
+    int c = (t >= 0.0) ? ((t < (double)G) ? (int)t : G - 1) : 0;
+    return c;
+}
+
+__global__ void cell_count_kernel(const double2* __restrict__ xy, int64_t N, const GridParams* __restrict__ gp,
+                                  int* __restrict__ keys, int* __restrict__ counts) {
+    const GridParams p = *gp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 q = xy[i];
+        const int cx = cell_coord(q.x, p.x0, p.inv_cell, p.G);
+        const int cy = cell_coord(q.y, p.y0, p.inv_cell, p.G);
+        const int key = cy * p.G + cx;
+        keys[i] = key;
+        atomicAdd(&counts[key], 1);
+    }
+}
+
+// counts[key] runs from the cell size down to 1, so positions fill
+// [start[key], start[key+1]) exactly once.  Order inside a cell is arbitrary;
+// stencils do not depend on it because the ranking key is a total order.
+__global__ void cell_scatter_kernel(const double2* __restrict__ xy, int64_t N, const int* __restrict__ keys,
+                                    const int* __restrict__ cell_start, int* __restrict__ counts,
+                                    double2* __restrict__ sxy, int* __restrict__ sorig) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int key = keys[i];
+        const int pos = cell_start[key + 1] - atomicSub(&counts[key], 1);
+        sxy[pos] = xy[i];
+        sorig[pos] = (int)i;
+    }
+}
+
+struct Key {
+    unsigned long long d;  // bit pattern of d^2 (non-negative double)
+    unsigned int j;        // caller index
+};
+
+__device__ __forceinline__ bool key_less(unsigned long long ad, unsigned int aj, unsigned long long bd,
+                                         unsigned int bj) {
+    return (ad < bd) || (ad == bd && aj < bj);
+}
+
+__device__ __forceinline__ double key_d2(unsigned long long d) { return __longlong_as_double((long long)d); }
+
+// Distributed sorted list of SLOTS*32 keys (entry e: lane e & 31, slot e >> 5).
+template <int SLOTS>
+struct TopList {
+    unsigned long long d[SLOTS];
+    unsigned int j[SLOTS];
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            d[s] = ~0ull;
+            j[s] = ~0u;
+        }
+    }
+
+    // Insert key (kd, kj), which is known to be smaller than entry n-1.
+    __device__ __forceinline__ void insert(unsigned long long kd, unsigned int kj, int lane) {
+        int p = 0;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) p += __popc(__ballot_sync(0xffffffffu, key_less(d[s], j[s], kd, kj)));
+        unsigned long long up_d[SLOTS];
+        unsigned int up_j[SLOTS];
+        unsigned long long top_d[SLOTS];
+        unsigned int top_j[SLOTS];
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            up_d[s] = __shfl_up_sync(0xffffffffu, d[s], 1);
+            up_j[s] = __shfl_up_sync(0xffffffffu, j[s], 1);
+            top_d[s] = __shfl_sync(0xffffffffu, d[s], 31);
+            top_j[s] = __shfl_sync(0xffffffffu, j[s], 31);
+        }
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            const int e = s * 32 + lane;
+            unsigned long long pd;
+            unsigned int pj;
+            if (lane > 0) {
+                pd = up_d[s];
+                pj = up_j[s];
+            } else if (s > 0) {
+                pd = top_d[s > 0 ? s - 1 : 0];
+                pj = top_j[s > 0 ? s - 1 : 0];
+            } else {
+                pd = ~0ull;
+                pj = ~0u;
+            }
+            if (e == p) {
+                d[s] = kd;
+                j[s] = kj;
+            } else if (e > p) {
+                d[s] = pd;
+                j[s] = pj;
+            }
+        }
+    }
+
+    // Entry e broadcast to the warp.
+    __device__ __forceinline__ void get(int e, unsigned long long& od, unsigned int& oj) const {
+        const int s = e >> 5, l = e & 31;
+        unsigned long long v = d[0];
+        unsigned int w = j[0];
+#pragma unroll
+        for (int t = 1; t < SLOTS; ++t)
+            if (t == s) {
+                v = d[t];
+                w = j[t];
+            }
+        od = __shfl_sync(0xffffffffu, v, l);
+        oj = __shfl_sync(0xffffffffu, w, l);
+    }
+};
+
+// Lower bound of the squared distance from (qx, qy) to cell (cx, cy), minus
+// the margin.  Returns 0 when the query is inside (or near) the cell.
+__device__ __forceinline__ double cell_min_d2(const GridParams& p, double qx, double qy, int cx, int cy) {
+    const double lx = p.x0 + cx * p.cell, hx = lx + p.cell;
+    const double ly = p.y0 + cy * p.cell, hy = ly + p.cell;
+    double dx = fmax(fmax(lx - qx, qx - hx), 0.0);
+    double dy = fmax(fmax(ly - qy, qy - hy), 0.0);
+    dx = fmax(dx - p.margin, 0.0);
+    dy = fmax(dy - p.margin, 0.0);
+    return dx * dx + dy * dy;
+}
+
+template <int SLOTS>
+__global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sxy, const int* __restrict__ sorig,
+                                                  const int* __restrict__ cell_start,
+                                                  const GridParams* __restrict__ gp, int N, int n,
+                                                  int* __restrict__ idx) {
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= N) return;
+    const GridParams p = *gp;
+    const double2 Q = sxy[q];
+    const int qo = sorig[q];
+    const int G = p.G;
+    const int cx = cell_coord(Q.x, p.x0, p.inv_cell, G);
+    const int cy = cell_coord(Q.y, p.y0, p.inv_cell, G);
+
+    TopList<SLOTS> top;
+    top.init();
+    unsigned long long thr_d = ~0ull;  // key of entry n-1 (all-ones: list not full)
+    unsigned int thr_j = ~0u;
+
+    for (int r = 0; r <= G; ++r) {
+        for (int yy = cy - r; yy <= cy + r; ++yy) {
+            if (yy < 0 || yy >= G) continue;
+            const bool edge_row = (yy == cy - r) || (yy == cy + r);
+            const int step = (edge_row || r == 0) ? 1 : 2 * r;
+            for (int xx = cx - r; xx <= cx + r; xx += step) {
+                if (xx < 0 || xx >= G) continue;
+                if (thr_d != ~0ull && !(cell_min_d2(p, Q.x, Q.y, xx, yy) <= key_d2(thr_d))) continue;
+                const int c = yy * G + xx;
+                const int beg = cell_start[c], end = cell_start[c + 1];
+                for (int base = beg; base < end; base += 32) {
+                    const int jj = base + lane;
+                    unsigned long long kd = ~0ull;
+                    unsigned int kj = ~0u;
+                    if (jj < end) {
+                        const double2 P = sxy[jj];
+                        const double dx = __dadd_rn(P.x, -Q.x);
+                        const double dy = __dadd_rn(P.y, -Q.y);
+                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                        kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
+                        kj = (unsigned int)sorig[jj];
+                    }
+                    unsigned int m = __ballot_sync(0xffffffffu, key_less(kd, kj, thr_d, thr_j));
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const unsigned long long id = __shfl_sync(0xffffffffu, kd, src);
+                        const unsigned int ij = __shfl_sync(0xffffffffu, kj, src);
+                        if (!key_less(id, ij, thr_d, thr_j)) continue;  // threshold moved
+                        top.insert(id, ij, lane);
+                        top.get(n - 1, thr_d, thr_j);
+                    }
+                }
+            }
+        }
+        // Whole grid visited?
+        if (cx - r <= 0 && cy - r <= 0 && cx + r >= G - 1 && cy + r >= G - 1) break;
+        if (thr_d == ~0ull) continue;
+        // Distance from Q to the outside of the visited block (sides at the
+        // grid border have nothing beyond them).
+        double gap = INFINITY;
+        if (cx - r > 0) gap = fmin(gap, Q.x - (p.x0 + (cx - r) * p.cell));
+        if (cx + r < G - 1) gap = fmin(gap, (p.x0 + (cx + r + 1) * p.cell) - Q.x);
+        if (cy - r > 0) gap = fmin(gap, Q.y - (p.y0 + (cy - r) * p.cell));
+        if (cy + r < G - 1) gap = fmin(gap, (p.y0 + (cy + r + 1) * p.cell) - Q.y);
+        gap -= p.margin;
+        if (gap > 0.0 && gap * gap > key_d2(thr_d)) break;
+    }
+
+    int* out = idx + (int64_t)qo * n;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+        const int e = s * 32 + lane;
+        if (e < n) out[e] = (int)top.j[s];
+    }
+}
+
+// Cells per axis: about kOcc nodes per cell on a square domain, capped.
+int grid_side(int64_t N, int n) {
+    (void)n;
+    const double occ = 3.0;
+    int G = (int)std::ceil(std::sqrt((double)N / occ));
+    if (G < 1) G = 1;
+    if (G > 4096) G = 4096;
+    return G;
+}
+
+struct KnnLayout {
+    GridParams* gp;
+    Box* part;
+    int* keys;
+    int* counts;
+    int* cell_start;
+    int* sums;
+    double2* sxy;
+    int* sorig;
+    size_t bytes;
+};
+
+KnnLayout knn_layout(void* ws, int64_t N, int n) {
+    const int G = grid_side(N, n);
+    const int64_t cells = (int64_t)G * G;
+    Carver c(ws);
+    KnnLayout L;
+    L.gp = c.take<GridParams>(1);
+    L.part = c.take<Box>(kBoxBlocks);
+    L.keys = c.take<int>(N);
+    L.counts = c.take<int>(cells);
+    L.cell_start = c.take<int>(cells + 1);
+    L.sums = c.take<int>(scan_tiles(cells) + 1);
+    L.sxy = c.take<double2>(N);
+    L.sorig = c.take<int>(N);
+    L.bytes = c.off;
+    return L;
+}
+
+struct CountLoad {
+    const int* counts;
+    __device__ int operator()(int64_t i) const { return counts[i]; }
+};
+
+}  // namespace
+}  // namespace rbffd
+
+extern "C" size_t rbffd_stencils_workspace_size(int64_t N, int32_t n) {
+    if (N <= 0 || n <= 0) return 0;
+    return rbffd::knn_layout(nullptr, N, n).bytes;
+}
+
+extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* idx, void* ws, size_t ws_bytes,
+                              void* stream) {
+    using namespace rbffd;
+    if (!xy || !idx || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL || (int64_t)n > N)
+        return RBFFD_ERR_INVALID_ARG;
+    if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
+    KnnLayout L = knn_layout(ws, N, n);
+    if (ws_bytes < L.bytes) return RBFFD_ERR_WORKSPACE;
+    cudaStream_t st = as_stream(stream);
+    const int G = grid_side(N, n);
+    const int64_t cells = (int64_t)G * G;
+    const double2* p = reinterpret_cast<const double2*>(xy);
+    const int grid_pts = (int)std::min<int64_t>((N + 255) / 256, (int64_t)sm_count() * 8);
+
+    bbox_partial_kernel<<<kBoxBlocks, kBoxThreads, 0, st>>>(p, N, L.part);
+    grid_setup_kernel<<<1, 32, 0, st>>>(L.part, kBoxBlocks, G, L.gp);
+    RBFFD_CUDA_TRY(cudaMemsetAsync(L.counts, 0, sizeof(int) * cells, st));
+    cell_count_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.gp, L.keys, L.counts);
+    RBFFD_CUDA_TRY(exclusive_scan<int>(CountLoad{L.counts}, cells, L.cell_start, L.sums, L.cell_start + cells, st));
+    cell_scatter_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.keys, L.cell_start, L.counts, L.sxy, L.sorig);
+    const int warps_per_block = 8;
+    const int blocks = (int)((N + warps_per_block - 1) / warps_per_block);
+    if (n <= 32)
+        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+    else if (n <= 64)
+        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+    else
+        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}

@@ -1,0 +1,336 @@
+"""Thin ctypes binding of librbffd (include/rbffd.h).
+
+Argument marshalling only: every function here allocates the output tensors
+and the workspace with torch on the input's device, passes raw device
+pointers and the current CUDA stream to the C ABI, and raises on a non-OK
+status.  All compute runs in the library's CUDA kernels; there is no CPU
+fallback.  The function names are those of the C entry points.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+from . import _build
+
+_LIB = None
+
+RBFFD_OK = 0
+STATUS_NAMES = {
+    0: "RBFFD_OK",
+    1: "RBFFD_ERR_INVALID_ARG",
+    2: "RBFFD_ERR_CUDA",
+    3: "RBFFD_ERR_SINGULAR_STENCIL",
+    4: "RBFFD_ERR_NOT_CONVERGED",
+    5: "RBFFD_ERR_BREAKDOWN",
+    6: "RBFFD_ERR_TIMEOUT",
+    7: "RBFFD_ERR_WORKSPACE",
+}
+
+
+class RbffdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [
+        ("n_rows", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("row_ptr", ctypes.c_void_p),
+        ("col", ctypes.c_void_p),
+        ("val", ctypes.c_void_p),
+        ("dtype", ctypes.c_int32),
+    ]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int32),
+        ("jacobi", ctypes.c_int32),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("iters", ctypes.c_int32),
+        ("outer_sweeps", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes) of every exported symbol declared in include/rbffd.h
+_VP, _I64, _I32, _SZ, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
+SIGNATURES = {
+    "rbffd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rbffd_last_cuda_error": (ctypes.c_char_p, []),
+    "rbffd_version": (ctypes.c_int, []),
+    "rbffd_stencils_workspace_size": (_SZ, [_I64, _I32]),
+    "rbffd_stencils": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
+    "rbffd_weights": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, _VP]),
+    "rbffd_assemble_workspace_size": (_SZ, [_I64]),
+    "rbffd_assemble_pattern": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
+    "rbffd_assemble": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "rbffd_rhs": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    "rbffd_transpose_workspace_size": (_SZ, [_I64]),
+    "rbffd_transpose": (ctypes.c_int, [ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "rbffd_solve_workspace_size": (_SZ, [_I64, ctypes.POINTER(SolveOpts)]),
+    "rbffd_solve": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP,
+                                   ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP,
+                                           ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load librbffd.so (building it when missing); raises if it cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"librbffd not built at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != RBFFD_OK:
+        detail = ""
+        if status == 2:
+            detail = load().rbffd_last_cuda_error().decode()
+        raise RbffdError(status, where, detail)
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _require(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------- stencils --
+def rbffd_stencils(xy: torch.Tensor, n: int, idx: torch.Tensor | None = None) -> torch.Tensor:
+    _require(xy, torch.float64, "xy")
+    N = xy.shape[0]
+    if xy.dim() != 2 or xy.shape[1] != 2:
+        raise ValueError("xy must be N x 2")
+    lib = load()
+    if idx is None:
+        idx = torch.empty((N, n), dtype=torch.int32, device=xy.device)
+    _require(idx, torch.int32, "idx", (N, n))
+    ws = _workspace(lib.rbffd_stencils_workspace_size(N, n), xy.device)
+    _check(lib.rbffd_stencils(_ptr(xy), N, n, _ptr(idx), _ptr(ws), ws.numel(), _stream(xy.device)),
+           "rbffd_stencils")
+    return idx
+
+
+def rbffd_weights(xy: torch.Tensor, idx: torch.Tensor, m: int, w: torch.Tensor | None = None,
+                  node_status: torch.Tensor | None = None, want_status: bool = True):
+    _require(xy, torch.float64, "xy")
+    _require(idx, torch.int32, "idx")
+    N, n = idx.shape
+    lib = load()
+    if w is None:
+        w = torch.empty((N, n), dtype=torch.float64, device=xy.device)
+    if node_status is None and want_status:
+        node_status = torch.empty(N, dtype=torch.int32, device=xy.device)
+    _require(w, torch.float64, "w", (N, n))
+    _check(lib.rbffd_weights(_ptr(xy), _ptr(idx), N, n, m, _ptr(w), _ptr(node_status), _stream(xy.device)),
+           "rbffd_weights")
+    return w, node_status
+
+
+# ----------------------------------------------------------------- assembly --
+@dataclasses.dataclass
+class CsrMatrix:
+    """CSR matrix held in torch tensors (row_ptr int64, col int32, val f64, optional val32)."""
+
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    val32: torch.Tensor | None = None
+
+    @property
+    def n_rows(self) -> int:
+        return self.row_ptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.col.numel()
+
+    def c64(self) -> Csr:
+        return Csr(self.n_rows, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), 0)
+
+    def c32(self) -> Csr | None:
+        if self.val32 is None:
+            return None
+        return Csr(self.n_rows, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val32), 1)
+
+
+def rbffd_assemble_pattern(is_dirichlet: torch.Tensor, n: int) -> torch.Tensor:
+    _require(is_dirichlet, torch.uint8, "is_dirichlet")
+    N = is_dirichlet.numel()
+    lib = load()
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=is_dirichlet.device)
+    ws = _workspace(lib.rbffd_assemble_workspace_size(N), is_dirichlet.device)
+    _check(lib.rbffd_assemble_pattern(_ptr(is_dirichlet), N, n, _ptr(row_ptr), _ptr(ws), ws.numel(),
+                                      _stream(is_dirichlet.device)), "rbffd_assemble_pattern")
+    return row_ptr
+
+
+def rbffd_assemble(idx: torch.Tensor, w: torch.Tensor, is_dirichlet: torch.Tensor,
+                   row_ptr: torch.Tensor | None = None, nnz: int | None = None,
+                   want_f32: bool = False) -> CsrMatrix:
+    _require(idx, torch.int32, "idx")
+    N, n = idx.shape
+    _require(w, torch.float64, "w", (N, n))
+    _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+    lib = load()
+    if row_ptr is None:
+        row_ptr = rbffd_assemble_pattern(is_dirichlet, n)
+    if nnz is None:
+        nnz = int(row_ptr[-1].item())  # one device->host read to size col/val
+    dev = idx.device
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    val32 = torch.empty(nnz, dtype=torch.float32, device=dev) if want_f32 else None
+    _check(lib.rbffd_assemble(_ptr(idx), _ptr(w), _ptr(is_dirichlet), N, n, _ptr(row_ptr), nnz, _ptr(col),
+                              _ptr(val), _ptr(val32), _stream(dev)), "rbffd_assemble")
+    return CsrMatrix(row_ptr, col, val, val32)
+
+
+def rbffd_rhs(f: torch.Tensor, g: torch.Tensor, is_dirichlet: torch.Tensor, b: torch.Tensor | None = None):
+    _require(f, torch.float64, "f")
+    N = f.numel()
+    _require(g, torch.float64, "g", (N,))
+    _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+    lib = load()
+    if b is None:
+        b = torch.empty(N, dtype=torch.float64, device=f.device)
+    _check(lib.rbffd_rhs(_ptr(f), _ptr(g), _ptr(is_dirichlet), N, _ptr(b), _stream(f.device)), "rbffd_rhs")
+    return b
+
+
+def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
+    lib = load()
+    dev = A.val.device
+    N, nnz = A.n_rows, A.nnz
+    row_ptr_t = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col_t = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val_t = torch.empty(nnz, dtype=torch.float64, device=dev)
+    ws = _workspace(lib.rbffd_transpose_workspace_size(N), dev)
+    c = A.c64()
+    _check(lib.rbffd_transpose(ctypes.byref(c), _ptr(row_ptr_t), _ptr(col_t), _ptr(val_t), _ptr(ws), ws.numel(),
+                               _stream(dev)), "rbffd_transpose")
+    val32 = val_t.to(torch.float32) if want_f32 else None
+    return CsrMatrix(row_ptr_t, col_t, val_t, val32)
+
+
+# -------------------------------------------------------------------- solve --
+def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=1e-5, max_outer=60, jacobi=True):
+    prec = {"fp64": 0, "mixed": 1}[precision]
+    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0)
+
+
+def solve_workspace(N: int, opts: SolveOpts, device) -> torch.Tensor:
+    return _workspace(load().rbffd_solve_workspace_size(N, ctypes.byref(opts)), device)
+
+
+def rbffd_solve(A: CsrMatrix, b: torch.Tensor, x: torch.Tensor | None = None, opts: SolveOpts | None = None,
+                ws: torch.Tensor | None = None, raise_on_error: bool = True):
+    """Solve A x = b in place on x (zero initial guess when x is None); returns (x, info dict)."""
+    _require(b, torch.float64, "b", (A.n_rows,))
+    lib = load()
+    opts = opts or make_opts()
+    if x is None:
+        x = torch.zeros_like(b)
+    _require(x, torch.float64, "x", (A.n_rows,))
+    if opts.precision == 1 and A.val32 is None:
+        raise ValueError("mixed precision needs the float32 matrix copy (assemble with want_f32=True)")
+    if ws is None:
+        ws = solve_workspace(A.n_rows, opts, b.device)
+    info = SolveInfo()
+    c64 = A.c64()
+    c32 = A.c32()
+    st = lib.rbffd_solve(ctypes.byref(c64), ctypes.byref(c32) if c32 is not None else None, _ptr(b), _ptr(x),
+                         ctypes.byref(opts), ctypes.byref(info), _ptr(ws), ws.numel(), _stream(b.device))
+    if raise_on_error and st not in (RBFFD_OK,):
+        _check(st, "rbffd_solve")
+    d = info.as_dict()
+    d["status_code"] = st
+    return x, d
+
+
+def rbffd_solve_adjoint(AT: CsrMatrix, is_dirichlet: torch.Tensor, dLdu: torch.Tensor,
+                        lam: torch.Tensor | None = None, opts: SolveOpts | None = None,
+                        ws: torch.Tensor | None = None, raise_on_error: bool = True):
+    """lambda with A^T lambda = dL/du, and (dL/df, dL/dg); returns (lam, dLdf, dLdg, info dict)."""
+    _require(dLdu, torch.float64, "dLdu", (AT.n_rows,))
+    _require(is_dirichlet, torch.uint8, "is_dirichlet", (AT.n_rows,))
+    lib = load()
+    opts = opts or make_opts()
+    if lam is None:
+        lam = torch.zeros_like(dLdu)
+    dLdf = torch.empty_like(dLdu)
+    dLdg = torch.empty_like(dLdu)
+    if ws is None:
+        ws = solve_workspace(AT.n_rows, opts, dLdu.device)
+    info = SolveInfo()
+    c64 = AT.c64()
+    c32 = AT.c32()
+    st = lib.rbffd_solve_adjoint(ctypes.byref(c64), ctypes.byref(c32) if c32 is not None else None,
+                                 _ptr(is_dirichlet), _ptr(dLdu), _ptr(lam), _ptr(dLdf), _ptr(dLdg),
+                                 ctypes.byref(opts), ctypes.byref(info), _ptr(ws), ws.numel(), _stream(dLdu.device))
+    if raise_on_error and st != RBFFD_OK:
+        _check(st, "rbffd_solve_adjoint")
+    d = info.as_dict()
+    d["status_code"] = st
+    return lam, dLdf, dLdg, d

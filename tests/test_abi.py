@@ -1,0 +1,123 @@
+"""The C-ABI library builds, loads and exports every symbol the header declares.
+
+Host-only entry points (status strings, version, workspace sizes) and the
+synchronous argument checks are exercised here without a GPU: argument
+errors return before anything touches CUDA.
+"""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "rbffd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(rbffd_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def cdll():
+    from paper_2107_03632_gb300 import _build, rbffd
+
+    _build.build()
+    return rbffd.load()
+
+
+def test_header_declares_the_pipeline():
+    names = declared_functions()
+    for must in ["rbffd_stencils", "rbffd_weights", "rbffd_assemble", "rbffd_solve", "rbffd_solve_adjoint",
+                 "rbffd_rhs", "rbffd_assemble_pattern", "rbffd_transpose"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(cdll):
+    from paper_2107_03632_gb300 import rbffd
+
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    for nm in names:
+        assert hasattr(cdll, nm), f"{nm} declared in rbffd.h but not exported"
+        assert nm in rbffd.SIGNATURES, f"{nm} has no ctypes signature in the binding"
+    out = subprocess.run(["nm", "-D", "--defined-only", rbffd.lib_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(rbffd_\w+)\b", out))
+    assert set(names) <= exported
+
+
+def test_no_cuda_driver_dependency_at_load():
+    from paper_2107_03632_gb300 import rbffd
+
+    out = subprocess.run(["ldd", rbffd.lib_path()], capture_output=True, text=True).stdout
+    assert "libcuda.so" not in out  # the runtime is static; the driver is opened lazily
+
+
+def test_host_entry_points(cdll):
+    assert cdll.rbffd_version() == 100
+    assert cdll.rbffd_status_string(0) == b"RBFFD_OK"
+    assert cdll.rbffd_status_string(4) == b"RBFFD_ERR_NOT_CONVERGED"
+    assert cdll.rbffd_status_string(99) == b"RBFFD_UNKNOWN_STATUS"
+    assert cdll.rbffd_stencils_workspace_size(0, 12) == 0
+    a = cdll.rbffd_stencils_workspace_size(2000, 12)
+    b = cdll.rbffd_stencils_workspace_size(4_000_000, 56)
+    assert 0 < a < b
+    assert b >= 4_000_000 * (16 + 4 + 4)
+    assert cdll.rbffd_assemble_workspace_size(1000) > 0
+    assert cdll.rbffd_transpose_workspace_size(1000) >= 4000
+
+
+def test_solve_workspace_grows_for_mixed(cdll):
+    from paper_2107_03632_gb300 import rbffd
+
+    o64 = rbffd.make_opts(precision="fp64")
+    o32 = rbffd.make_opts(precision="mixed")
+    n = 100_000
+    s64 = cdll.rbffd_solve_workspace_size(n, ctypes.byref(o64))
+    s32 = cdll.rbffd_solve_workspace_size(n, ctypes.byref(o32))
+    assert s64 >= 8 * 8 * n and s32 >= s64 + 2 * 8 * n
+
+
+def test_argument_errors_return_before_cuda(cdll):
+    INVALID, WS = 1, 7
+    # null pointers / bad sizes
+    assert cdll.rbffd_stencils(None, 10, 4, None, None, 0, None) == INVALID
+    assert cdll.rbffd_stencils(0x1000, 10, 11, 0x2000, 0x3000, 1 << 20, None) == INVALID  # n > N
+    assert cdll.rbffd_stencils(0x1000, 10, 200, 0x2000, 0x3000, 1 << 20, None) == INVALID  # n > max
+    assert cdll.rbffd_stencils(0x1008, 10, 4, 0x2000, 0x3000, 1 << 20, None) == INVALID  # xy not 16-B aligned
+    assert cdll.rbffd_stencils(0x1000, 10, 4, 0x2000, 0x3001, 1 << 20, None) == WS  # misaligned workspace
+    assert cdll.rbffd_stencils(0x1000, 10, 4, 0x2000, 0x3000, 16, None) == WS  # too small
+    # weights: n < s (m = 4 needs 15 nodes), m out of range
+    assert cdll.rbffd_weights(0x1000, 0x2000, 100, 12, 4, 0x3000, None, None) == INVALID
+    assert cdll.rbffd_weights(0x1000, 0x2000, 100, 12, 9, 0x3000, None, None) == INVALID
+    assert cdll.rbffd_weights(None, 0x2000, 100, 12, 2, 0x3000, None, None) == INVALID
+    # assembly / rhs
+    assert cdll.rbffd_assemble_pattern(None, 10, 4, 0x1000, 0x2000, 1 << 20, None) == INVALID
+    assert cdll.rbffd_assemble(None, 0x1, 0x1, 10, 4, 0x1, 10, 0x1, 0x1, None, None) == INVALID
+    assert cdll.rbffd_rhs(None, 0x1, 0x1, 10, 0x1, None) == INVALID
+
+
+def test_solve_argument_errors(cdll):
+    from paper_2107_03632_gb300 import rbffd
+
+    A = rbffd.Csr(10, 30, 0x1000, 0x2000, 0x3000, 0)
+    info = rbffd.SolveInfo()
+    bad_tol = rbffd.make_opts(tol=0.0)
+    assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(bad_tol), ctypes.byref(info),
+                            0x6000, 1 << 30, None) == 1
+    mixed = rbffd.make_opts(precision="mixed")
+    # mixed precision without the float32 matrix
+    assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(mixed), ctypes.byref(info),
+                            0x6000, 1 << 30, None) == 1
+    ok = rbffd.make_opts()
+    assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(ok), ctypes.byref(info),
+                            0x6000, 16, None) == 7
+    A_wrong_dtype = rbffd.Csr(10, 30, 0x1000, 0x2000, 0x3000, 1)
+    assert cdll.rbffd_solve(ctypes.byref(A_wrong_dtype), None, 0x4000, 0x5000, ctypes.byref(ok),
+                            ctypes.byref(info), 0x6000, 1 << 30, None) == 1

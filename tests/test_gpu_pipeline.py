@@ -1,0 +1,257 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle.
+
+Bars (written in each test): stencils bit-exact (ordered index sequences);
+weights 1e-9 relative max-norm per stencil for m <= 4 and 1e-7 for m = 6;
+assembly and right-hand side bit-exact; solution 1e-8 relative max-norm
+against the oracle's direct solve at Krylov tolerance 1e-10.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from fixtures import disk_nodes, manufactured, splitmix64, uniform01
+from oracle.assemble import to_scipy
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def T(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def rel_rowwise(w, w_ref):
+    """max over rows of |w - w_ref|_inf / |w_ref|_inf."""
+    num = np.abs(w - w_ref).max(axis=1)
+    den = np.abs(w_ref).max(axis=1)
+    return float((num / den).max())
+
+
+def random_points(N, seed):
+    u = uniform01(splitmix64(seed, 2 * N)).reshape(N, 2)
+    return np.ascontiguousarray(2.0 * u - 1.0)
+
+
+# ------------------------------------------------------------------ stencils --
+@pytest.mark.parametrize("h,n", [(0.04, 12), (0.04, 30), (0.08, 56), (0.04, 64), (0.08, 100)])
+def test_stencils_bitexact_disk(lib, h, n):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(h)
+    idx = rbffd.rbffd_stencils(T(d.xy), n).cpu().numpy()
+    ref = oracle.knn(d.xy, n)
+    assert np.array_equal(idx, ref)
+
+
+@pytest.mark.parametrize("n", [5, 9, 13, 25, 60])
+@pytest.mark.parametrize("h", [1.0 / 16.0, 1.0 / 32.0])
+def test_stencils_bitexact_unjittered_grid_ties(lib, n, h):
+    """Power-of-two spacing: grid distances tie exactly; order by index."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(h, jitter=0.0)
+    idx = rbffd.rbffd_stencils(T(d.xy), n).cpu().numpy()
+    ref = oracle.knn(d.xy, n)
+    assert np.array_equal(idx, ref)
+
+
+@pytest.mark.parametrize("N,n", [(1, 1), (12, 12), (33, 12), (100, 56), (1000, 30), (4097, 64), (5000, 1)])
+def test_stencils_ragged_and_extreme_sizes(lib, N, n):
+    from paper_2107_03632_gb300 import rbffd
+
+    xy = random_points(N, 77 + N)
+    idx = rbffd.rbffd_stencils(T(xy), n).cpu().numpy()
+    assert np.array_equal(idx, oracle.knn(xy, n))
+
+
+def test_stencils_clustered_and_duplicates(lib):
+    """Dense clusters, exact duplicate points and a far outlier."""
+    from paper_2107_03632_gb300 import rbffd
+
+    base = random_points(600, 5)
+    xy = np.concatenate([base * 1e-3, base[:200] + 5.0, base[:50] * 1e-3, [[100.0, -100.0]]])
+    xy = np.ascontiguousarray(xy)
+    for n in (8, 40):
+        idx = rbffd.rbffd_stencils(T(xy), n).cpu().numpy()
+        assert np.array_equal(idx, oracle.knn(xy, n))
+
+
+def test_stencils_invalid_args(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    xy = T(random_points(10, 1))
+    with pytest.raises(rbffd.RbffdError):
+        rbffd.rbffd_stencils(xy, 11)
+
+
+# ------------------------------------------------------------------- weights --
+@pytest.mark.parametrize("h,m,n,tol", [(0.04, 2, 12, 1e-9), (0.04, 4, 30, 1e-9), (0.08, 6, 56, 1e-7),
+                                       (0.08, 2, 20, 1e-9), (0.08, 4, 45, 1e-9), (0.1, 6, 60, 1e-7)])
+def test_weights_vs_oracle(lib, h, m, n, tol):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(h)
+    idx = oracle.knn(d.xy, n)
+    w, st = rbffd.rbffd_weights(T(d.xy), T(idx), m)
+    w = w.cpu().numpy()
+    w_ref, st_ref = oracle.weights(d.xy, idx, m)
+    assert not st.cpu().numpy().any() and not st_ref.any()
+    assert rel_rowwise(w, w_ref) <= tol
+
+
+def test_weights_singular_stencil_flagged(lib):
+    """Coincident nodes make the system singular: status 1, zero weights."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(0.1)
+    xy = d.xy.copy()
+    xy[5] = xy[4]  # duplicate node
+    idx = oracle.knn(xy, 12)
+    w, st = rbffd.rbffd_weights(T(xy), T(idx), 2)
+    st = st.cpu().numpy()
+    _, st_ref = oracle.weights(xy, idx, 2)
+    assert st[4] == 1 and st[5] == 1
+    assert np.array_equal(st.astype(bool), st_ref.astype(bool))
+    assert np.all(w.cpu().numpy()[st == 1] == 0.0)
+
+
+def test_weights_out_of_range_index_flagged(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(0.1)
+    idx = oracle.knn(d.xy, 12)
+    idx[3, 5] = d.N + 7
+    idx[9, 0] = -1
+    w, st = rbffd.rbffd_weights(T(d.xy), T(idx), 2)
+    st = st.cpu().numpy()
+    assert st[3] == 1 and st[9] == 1 and st.sum() == 2
+
+
+# ------------------------------------------------------------------ assembly --
+def test_assemble_and_rhs_bitexact(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(0.04)
+    idx = oracle.knn(d.xy, 12)
+    w, _ = oracle.weights(d.xy, idx, 2)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=True)
+    rp, col, val = oracle.assemble(idx, w, d.is_dirichlet)
+    assert np.array_equal(A.row_ptr.cpu().numpy(), rp)
+    assert np.array_equal(A.col.cpu().numpy(), col)
+    assert np.array_equal(A.val.cpu().numpy(), val)
+    assert np.array_equal(A.val32.cpu().numpy(), val.astype(np.float32))
+    u, f, g = manufactured(d.xy)
+    b = rbffd.rbffd_rhs(T(f), T(g), T(d.is_dirichlet)).cpu().numpy()
+    assert np.array_equal(b, oracle.rhs(f, g, d.is_dirichlet))
+
+
+def test_transpose_bitexact(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(0.05)
+    idx = oracle.knn(d.xy, 30)
+    w, _ = oracle.weights(d.xy, idx, 4)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
+    AT = rbffd.rbffd_transpose(A)
+    rp, col, val = oracle.assemble(idx, w, d.is_dirichlet)
+    ref = to_scipy(rp, col, val, d.N).T.tocsr()
+    ref.sort_indices()
+    assert np.array_equal(AT.row_ptr.cpu().numpy(), ref.indptr)
+    assert np.array_equal(AT.col.cpu().numpy(), ref.indices)
+    assert np.array_equal(AT.val.cpu().numpy(), ref.data)
+
+
+# --------------------------------------------------------------------- solve --
+def _system(h, m, n):
+    d = disk_nodes(h)
+    u, f, g = manufactured(d.xy)
+    idx = oracle.knn(d.xy, n)
+    w, _ = oracle.weights(d.xy, idx, m)
+    rp, col, val = oracle.assemble(idx, w, d.is_dirichlet)
+    b = oracle.rhs(f, g, d.is_dirichlet)
+    return d, (idx, w, rp, col, val, b, f, g, u)
+
+
+@pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.06, 4, 30), (0.1, 6, 56)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_vs_oracle(lib, h, m, n, precision):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(h, m, n)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=(precision == "mixed"))
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(tol=1e-10, precision=precision))
+    x = x.cpu().numpy()
+    ref = oracle.solve_direct(rp, col, val, b)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    As = to_scipy(rp, col, val, d.N)
+    assert np.linalg.norm(b - As @ x) / np.linalg.norm(b) <= 1e-10
+    assert np.abs(x - ref).max() / np.abs(ref).max() <= 1e-8
+
+
+def test_solve_warm_start_and_zero_rhs(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.05, 2, 12)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
+    ref = oracle.solve_direct(rp, col, val, b)
+    x0 = T(ref)
+    x, info = rbffd.rbffd_solve(A, T(b), x0.clone())
+    assert info["iters"] == 0 and info["status"] == 0
+    z, info = rbffd.rbffd_solve(A, torch.zeros(d.N, dtype=torch.float64, device=DEV))
+    assert info["status"] == 0 and float(z.abs().max()) == 0.0
+
+
+def test_solve_not_converged_reports(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.04, 2, 12)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(max_iter=5), raise_on_error=False)
+    assert info["status_code"] == 4 and info["iters"] <= 5 + 64
+
+
+def test_solve_rejects_bad_column_index(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.1, 2, 12)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
+    A.col[17] = d.N + 3
+    with pytest.raises(rbffd.RbffdError):
+        rbffd.rbffd_solve(A, T(b))
+
+
+# ------------------------------------------------------------------- adjoint --
+def test_adjoint_gradient_vs_oracle(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.05, 4, 30)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
+    AT = rbffd.rbffd_transpose(A)
+    rng = np.random.default_rng(3)
+    dLdu = np.where(d.is_dirichlet.astype(bool), 0.0, rng.standard_normal(d.N))
+    lam, dLdf, dLdg, info = rbffd.rbffd_solve_adjoint(AT, T(d.is_dirichlet), T(dLdu),
+                                                      opts=rbffd.make_opts(tol=1e-12))
+    gf, gg, lam_ref = oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, dLdu)
+    assert np.abs(lam.cpu().numpy() - lam_ref).max() / np.abs(lam_ref).max() <= 1e-8
+    dLdf = dLdf.cpu().numpy()
+    assert np.all(dLdf[d.is_dirichlet.astype(bool)] == 0.0)
+    assert np.abs(dLdf - gf).max() / np.abs(gf).max() <= 1e-8
+    assert np.abs(dLdg.cpu().numpy() - gg).max() / np.abs(gg).max() <= 1e-8
+
+
+def test_pipeline_end_to_end_small(lib):
+    from paper_2107_03632_gb300 import pipeline
+
+    d = disk_nodes(0.04)
+    u, f, g = manufactured(d.xy)
+    uh, info, op = pipeline.poisson_solve(T(d.xy), T(d.is_dirichlet), T(f), T(g), 2, 12)
+    ref, _ = oracle.poisson_solve(d.xy, d.is_dirichlet, f, g, 2, 12)
+    uh = uh.cpu().numpy()
+    assert np.abs(uh - ref).max() / np.abs(ref).max() <= 1e-8
+    assert np.abs(uh - u).max() < 2e-2  # discretisation error at h = 0.04, m = 2
