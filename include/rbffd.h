@@ -156,7 +156,8 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
 /* precision 0 (FP64): matrix, vectors and scalars in float64.               */
 /* precision 1 (mixed): an FP64 refinement loop (r = b - A x with the FP64   */
 /*   matrix, x += correction in FP64) around inner BiCGSTAB iterations that  */
-/*   read the float32 copy of the matrix (A32, same pattern as A); an inner  */
+/*   read the float32 copy of the matrix (A32: same row_ptr and col arrays  */
+/*   as A, float32 values); an inner                                         */
 /*   pass ends when its residual has fallen by inner_tol.                    */
 /*                                                                           */
 /* x is in/out: the initial guess on entry, the solution on exit (warm       */

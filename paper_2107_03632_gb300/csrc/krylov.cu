@@ -439,7 +439,9 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     if (!csr_ok(A, 0) || !b || !x || !o || !info) return RBFFD_ERR_INVALID_ARG;
     const bool mixed = o->precision == 1;
     if (o->precision != 0 && o->precision != 1) return RBFFD_ERR_INVALID_ARG;
-    if (mixed && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz)) return RBFFD_ERR_INVALID_ARG;
+    if (mixed && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz ||
+                  A32->row_ptr != A->row_ptr || A32->col != A->col))
+        return RBFFD_ERR_INVALID_ARG;  // the float32 copy shares A's (validated) pattern
     if (!(o->tol > 0.0) || o->max_iter < 0) return RBFFD_ERR_INVALID_ARG;
     if (mixed && (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1)) return RBFFD_ERR_INVALID_ARG;
     const int64_t N = A->n_rows;
