@@ -102,12 +102,18 @@ __device__ __forceinline__ double ld_val(const VT* p) {
     return (double)__ldcs(p);
 }
 
-// Sum of row `row` times x, TPR lanes cooperating (result valid in all of them).
+// Sum of row `row` times x, TPR lanes cooperating (result valid in all of
+// them).  All 32 lanes of the warp must call it together (shuffles); a lane
+// group with valid == false contributes an empty row.
 template <class VT, int TPR>
 __device__ __forceinline__ double row_dot(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                           const VT* __restrict__ val, const double* __restrict__ x, int64_t row,
-                                          int sub) {
-    const int64_t a = row_ptr[row], e = row_ptr[row + 1];
+                                          int sub, bool valid) {
+    int64_t a = 0, e = 0;
+    if (valid) {
+        a = row_ptr[row];
+        e = row_ptr[row + 1];
+    }
     double sum = 0.0;
 #pragma unroll 4
     for (int64_t k = a + sub; k < e; k += TPR) sum = fma(ld_val(val + k), x[__ldcs(col + k)], sum);
@@ -158,10 +164,13 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(const int64_t* __res
     const int sub = threadIdx.x & (TPR - 1);
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPR;
     const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / TPR;
+    const int64_t gw = g0 - (threadIdx.x & 31) / TPR;  // first group of this warp: loop bound is warp-uniform
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t i = g0; i < N; i += ng) {
-        const double ax = row_dot<VT, TPR>(row_ptr, col, val, x, i, sub);
-        if (sub == 0) {
+    for (int64_t base = gw; base < N; base += ng) {
+        const int64_t i = base + (g0 - gw);
+        const bool valid = i < N;
+        const double ax = row_dot<VT, TPR>(row_ptr, col, val, x, i, sub, valid);
+        if (valid && sub == 0) {
             const double bi = b[i];
             const double rt = bi - ax;
             const double ri = scale_out ? rt * dinv[i] : rt;
@@ -222,10 +231,13 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(const int64_t* __restric
     const int sub = threadIdx.x & (TPR - 1);
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPR;
     const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / TPR;
+    const int64_t gw = g0 - (threadIdx.x & 31) / TPR;  // warp-uniform loop bound
     double acc[2] = {0.0, 0.0};
-    for (int64_t i = g0; i < N; i += ng) {
-        const double ax = row_dot<VT, TPR>(row_ptr, col, val, xin, i, sub);
-        if (sub == 0) {
+    for (int64_t base = gw; base < N; base += ng) {
+        const int64_t i = base + (g0 - gw);
+        const bool valid = i < N;
+        const double ax = row_dot<VT, TPR>(row_ptr, col, val, xin, i, sub, valid);
+        if (valid && sub == 0) {
             const double yi = ax * dinv[i];
             y[i] = yi;
             if (MODE == 0) {
