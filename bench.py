@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark: solved nodes/s of the RBF-FD Poisson pipeline on GB300.
+
+Workload (default): the unit-disk problem with N ~ 4.0e6 scattered nodes,
+m = 6 (s = 28 monomials), n = 56 nearest neighbours, manufactured solution
+u = sin(pi x) sin(pi y), solved to a relative residual of 1e-10.
+
+One step = the whole hot path on inputs already resident in HBM:
+stencils -> weights -> assembly (pattern, f64 + f32 values) -> rhs ->
+BiCGSTAB solve.  The headline `value` uses the mixed FP32-inner / FP64
+refinement solve; the same steps with the plain FP64 solve are timed beside
+it ("fp64").  `e2e` repeats the step through the public API from pinned
+host buffers, host<->device copies inside the timed region.
+
+Multi-GPU: the problem is solved independently on every rank (replicas:
+the path has no cross-GPU exchange here), value = nodes of all ranks /
+max-over-ranks time, scaling "weak".
+
+`--impl reference` times the CPU oracle (the plain FP64 numpy/scipy
+implementation the tests check against) on a bounded sample of the same
+workload: the same disk recipe, m and n, at a spacing sized for seconds of
+single-core work per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (h, m, n) -- grid spacing fixed so N is reproducible
+    "disk_4M_m6_n56": (8.862e-4, 6, 56),
+    "disk_1M_m4_n30": (1.7725e-3, 4, 30),
+    "disk_h0.04_m2_n12": (0.04, 2, 12),
+}
+METRIC = "solved nodes/s (weights+solve) at m=6, 4M nodes; mixed vs FP64; % roofline"
+SEED = 2107
+CPU_SAMPLE_H = 0.012  # oracle sample: same recipe, ~22k nodes, ~10-30 s of one core
+
+
+# ------------------------------------------------------------------ helpers --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp64_peak_tflops(torch, dev):
+    """cuBLAS DGEMM throughput on this GPU (the FP64 denominator), best of 5."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize(dev)
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+# ------------------------------------------------------------ CPU oracle ------
+def oracle_sample_step(h: float, m: int, n: int):
+    """One pass of the oracle pipeline on the sample disk; returns (nodes, seconds)."""
+    import oracle
+    from fixtures import disk_nodes, manufactured
+
+    d = disk_nodes(h, SEED)
+    u, f, g = manufactured(d.xy)
+    t0 = time.perf_counter()
+    oracle.poisson_solve(d.xy, d.is_dirichlet, f, g, m, n)
+    return d.N, time.perf_counter() - t0
+
+
+def cpu_baseline_subprocess(h: float, m: int, n: int, steps: int = 1):
+    """Run the oracle in a single-threaded child process (BLAS pinned to one
+    thread, the paper's single-core convention)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = [bench.oracle_sample_step(%r, %d, %d) for _ in range(%d)]; print(json.dumps(r))"
+            % (ROOT, h, m, n, steps))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    h, m, n = WORKLOADS[args.workload]
+    res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=args.warmup + args.steps)
+    timed = res[args.warmup:]
+    nodes = timed[0][0]
+    secs = sum(t for _, t in timed)
+    value = nodes * len(timed) / secs
+    sample = (f"oracle pipeline (brute-force kNN, per-stencil LU, CSR assembly, SuperLU solve) on the same "
+              f"disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m={m}, n={n}) per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "sample_nodes": nodes, "m": m, "n": n},
+        "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm -----
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from fixtures import disk_nodes, manufactured
+    from paper_2107_03632_gb300 import rbffd
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rbffd.load()
+    lib = rbffd.load()
+
+    h, m, n = WORKLOADS[args.workload]
+    d = disk_nodes(h, SEED)
+    u_ex, f, g = manufactured(d.xy)
+    N = d.N
+    s = (m + 1) * (m + 2) // 2
+    M = n + s
+
+    # host (pinned) and device buffers
+    h_xy = torch.from_numpy(d.xy).pin_memory()
+    h_mask = torch.from_numpy(d.is_dirichlet).pin_memory()
+    h_f = torch.from_numpy(f).pin_memory()
+    h_g = torch.from_numpy(g).pin_memory()
+    h_u = torch.empty(N, dtype=torch.float64).pin_memory()
+    xy, mask = h_xy.to(dev), h_mask.to(dev)
+    fT, gT = h_f.to(dev), h_g.to(dev)
+    idx = torch.empty((N, n), dtype=torch.int32, device=dev)
+    w = torch.empty((N, n), dtype=torch.float64, device=dev)
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    b = torch.empty(N, dtype=torch.float64, device=dev)
+    x = torch.empty(N, dtype=torch.float64, device=dev)
+    ws_knn = rbffd.stencils_workspace(N, n, dev)
+    ws_asm = rbffd.assemble_workspace(N, dev)
+    row_ptr = rbffd.rbffd_assemble_pattern(mask, n, ws=ws_asm)
+    nnz = int(row_ptr[-1].item())
+    A = rbffd.CsrMatrix(row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
+                        torch.empty(nnz, dtype=torch.float64, device=dev),
+                        torch.empty(nnz, dtype=torch.float32, device=dev))
+    opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol),
+            "fp64": rbffd.make_opts(tol=1e-10, precision="fp64")}
+    ws_solve = rbffd.solve_workspace(N, opts["mixed"], dev)
+
+    def step(precision, ev=None):
+        if ev:
+            ev[0].record()
+        rbffd.rbffd_stencils(xy, n, idx, ws_knn)
+        if ev:
+            ev[1].record()
+        rbffd.rbffd_weights(xy, idx, m, w, st)
+        if ev:
+            ev[2].record()
+        rbffd.rbffd_assemble_pattern(mask, n, row_ptr, ws_asm)
+        rbffd.rbffd_assemble(idx, w, mask, out=A)
+        rbffd.rbffd_rhs(fT, gT, mask, b)
+        if ev:
+            ev[3].record()
+        x.zero_()
+        _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve)
+        if ev:
+            ev[4].record()
+        return info
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_loop(precision, k, profile=False):
+        stage = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(k)]
+        infos = []
+        barrier()
+        rbffd.rbffd_profile_read(reset=True)
+        if profile:
+            rbffd.rbffd_profile_enable(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        wall0 = time.perf_counter()
+        t0.record()
+        for i in range(k):
+            infos.append(step(precision, stage[i]))
+        t1.record()
+        barrier()
+        wall = time.perf_counter() - wall0
+        prof = rbffd.rbffd_profile_read(reset=True)
+        rbffd.rbffd_profile_enable(False)
+        ms = t0.elapsed_time(t1)
+        st_ms = np.array([[stage[i][j].elapsed_time(stage[i][j + 1]) for j in range(4)] for i in range(k)]).mean(0)
+        return ms, wall, st_ms, infos, prof
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up, then the timed mixed-precision steps ----
+    for _ in range(args.warmup):
+        step("mixed")
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, wall, st_ms, infos, prof = timed_loop("mixed", args.steps, profile=True)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms)
+    ms_step = ms / args.steps
+    value = ws * N * args.steps / (ms * 1e-3)
+
+    # ---- the same steps with the plain FP64 solve ----
+    step("fp64")
+    ms64, wall64, st64, infos64, prof64 = timed_loop("fp64", args.steps, profile=True)
+    ms64 = max_over_ranks(ms64)
+
+    # ---- end to end through the API from pinned host buffers ----
+    h2d = (h_xy.numel() * 8 + h_mask.numel() + h_f.numel() * 8 + h_g.numel() * 8)
+    d2h = N * 8
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.e2e_steps):
+        xy.copy_(h_xy, non_blocking=True)
+        mask.copy_(h_mask, non_blocking=True)
+        fT.copy_(h_f, non_blocking=True)
+        gT.copy_(h_g, non_blocking=True)
+        step("mixed")
+        h_u.copy_(x, non_blocking=True)
+    e1.record()
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+    e2e_value = ws * N * args.e2e_steps / (ms_e2e * 1e-3)
+
+    # ---- correctness of the timed solves (host check, outside timing) ----
+    err_exact = float(np.abs(h_u.numpy() - u_ex).max())
+
+    # ---- roofline: SpMV of the inner solve (dominant kernel) ----
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    sp_ms = prof["spmv32_ms"] / max(prof["spmv32_launches"], 1)
+    sp_bytes = prof["spmv32_bytes"] / max(prof["spmv32_launches"], 1)
+    sp_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9 if prof["spmv32_launches"] else 0.0
+    sp64_ms = prof64["spmv64_ms"] / max(prof64["spmv64_launches"], 1)
+    sp64_bytes = prof64["spmv64_bytes"] / max(prof64["spmv64_launches"], 1)
+    sp64_gbs = sp64_bytes / (sp64_ms * 1e-3) / 1e9 if prof64["spmv64_launches"] else 0.0
+
+    fp64_peak = fp64_peak_tflops(torch, dev)
+    w_flops = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M + 15.0 * n * (n - 1) / 2.0)
+    w_tflops = w_flops / (st_ms[1] * 1e-3) / 1e12
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=1)
+        nodes, secs = res[0]
+        cpu = {"value": nodes / secs, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle pipeline (brute-force kNN, per-stencil LU, CSR assembly, SuperLU) on the same "
+                         f"disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m={m}, n={n}), one core, {secs:.1f} s"}
+
+    iters = [i["iters"] for i in infos]
+    line = {
+        "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "nnz": nnz, "h": h, "m": m, "n": n, "seed": SEED,
+                   "tol": 1e-10, "precision": "mixed (f32 inner BiCGSTAB, f64 refinement)",
+                   "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
+        "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "solve": st_ms[3]},
+        "solve": {"iters": iters, "outer_sweeps": [i["outer_sweeps"] for i in infos],
+                  "rel_residual": [i["rel_residual"] for i in infos], "max_err_vs_exact": err_exact},
+        "fp64": {"value": ws * N * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                 "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2], "solve": st64[3]},
+                 "iters": [i["iters"] for i in infos64], "rel_residual": [i["rel_residual"] for i in infos64],
+                 "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm},
+        "roofline": {"kernel": "spmv_kernel<float> (inner BiCGSTAB SpMV)", "bound": "hbm", "achieved": sp_gbs,
+                     "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
+                     "launches": prof["spmv32_launches"]},
+        "weights_roofline": {"bound": "fp64", "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": w_tflops / fp64_peak, "peak_kind": "measured cuBLAS DGEMM 4096^3",
+                             "flops_per_node": w_flops / N},
+        "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps},
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS))
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

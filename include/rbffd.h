@@ -202,6 +202,30 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
                         const rbffd_solve_opts* opts, rbffd_solve_info* info,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement hooks (no counterpart in the paper; used to report roofline   */
+/* fractions).  The library counts every kernel it launches.  With profiling */
+/* enabled it also brackets each SpMV launch of the Krylov iteration with    */
+/* CUDA events on the solve's stream and sums their device time together     */
+/* with the launch's algorithmic bytes:                                      */
+/*   nnz * (value bytes + 4) + 8 (N + 1) [row_ptr] + 8 N [gathered vector,   */
+/*   read once] + 8 N [result] + 8 N [Jacobi scale] + 8 N [dot partner].     */
+/* Profiling is process-wide, off by default, and meant for one thread and   */
+/* one device.  rbffd_profile_read waits for bracketed launches to finish.   */
+/* ------------------------------------------------------------------------ */
+typedef struct rbffd_profile {
+    int64_t launches;         /* kernels launched since the last reset */
+    int64_t spmv64_launches;  /* timed SpMV launches, float64 values */
+    double spmv64_ms;
+    int64_t spmv64_bytes;
+    int64_t spmv32_launches;  /* timed SpMV launches, float32 values */
+    double spmv32_ms;
+    int64_t spmv32_bytes;
+} rbffd_profile;
+
+int rbffd_profile_enable(int on);
+int rbffd_profile_read(rbffd_profile* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,9 @@ are w = wh / delta^2.  Monomials are in graded order
 at xh = 0 only x^2 and y^2 have a nonzero Laplacian (2).
 
 The solve is LAPACK's LU with partial pivoting (numpy.linalg.solve), applied
-per stencil.
+per stencil.  A stencil holding two coincident nodes has two identical rows
+(and columns) in Phi and P, so its system is singular by definition; such
+stencils, and systems whose solve fails or is not finite, get status 1.
 """
 
 from __future__ import annotations
@@ -103,6 +105,11 @@ def weights(xy: np.ndarray, idx: np.ndarray, m: int, nodes=None, chunk: int = 20
         sel = nodes[s0 : s0 + chunk]
         xs, delta = scaled_stencil(xy, idx, sel)
         A, rhs = local_system(xs, m)
+        # coincident nodes: an exactly zero distance off the diagonal
+        dxx = xs[:, :, None, 0] - xs[:, None, :, 0]
+        dyy = xs[:, :, None, 1] - xs[:, None, :, 1]
+        off = ~np.eye(n, dtype=bool)[None]
+        dup = ((dxx == 0.0) & (dyy == 0.0) & off).any(axis=(1, 2))
         try:
             sol = np.linalg.solve(A, rhs[..., None])[..., 0]
             bad = ~np.isfinite(sol).all(axis=1)
@@ -115,6 +122,7 @@ def weights(xy: np.ndarray, idx: np.ndarray, m: int, nodes=None, chunk: int = 20
                     bad[r] = not np.isfinite(sol[r]).all()
                 except np.linalg.LinAlgError:
                     bad[r] = True
+        bad = bad | dup
         out[s0 : s0 + sel.size] = sol[:, :n] / (delta * delta)[:, None]
         status[s0 : s0 + sel.size] = bad.astype(np.int32)
         out[s0 : s0 + sel.size][bad] = 0.0

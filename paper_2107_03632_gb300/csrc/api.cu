@@ -1,8 +1,10 @@
 // Status strings, error bookkeeping and device queries of the C ABI.
 #include "common.cuh"
 
+#include <atomic>
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 namespace rbffd {
 
@@ -28,9 +30,107 @@ int sm_count() {
     return cached[dev];
 }
 
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_profiling{0};
+
+struct ProfPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;
+    int64_t bytes = 0;
+    bool pending = false;
+};
+
+static std::mutex g_prof_mu;
+static std::vector<ProfPair> g_pairs;
+static long long g_prof_launches[kProfKinds];
+static double g_prof_ms[kProfKinds];
+static long long g_prof_bytes[kProfKinds];
+
+void note_launches(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+bool profiling() { return g_profiling.load(std::memory_order_relaxed) != 0; }
+
+int prof_begin(cudaStream_t st) {
+    if (!profiling()) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int slot = -1;
+    for (size_t k = 0; k < g_pairs.size(); ++k)
+        if (!g_pairs[k].pending) {
+            slot = (int)k;
+            break;
+        }
+    if (slot < 0) {
+        ProfPair p;
+        if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return -1;
+        g_pairs.push_back(p);
+        slot = (int)g_pairs.size() - 1;
+    }
+    if (cudaEventRecord(g_pairs[slot].a, st) != cudaSuccess) return -1;
+    g_pairs[slot].pending = true;
+    return slot;
+}
+
+void prof_end(int slot, cudaStream_t st, int kind, int64_t bytes) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfPair& p = g_pairs[slot];
+    p.kind = kind;
+    p.bytes = bytes;
+    if (cudaEventRecord(p.b, st) != cudaSuccess) p.pending = false;
+}
+
+void prof_collect() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (ProfPair& p : g_pairs) {
+        if (!p.pending) continue;
+        if (cudaEventQuery(p.b) != cudaSuccess) continue;  // not finished yet: keep for later
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_prof_launches[p.kind] += 1;
+            g_prof_ms[p.kind] += ms;
+            g_prof_bytes[p.kind] += p.bytes;
+        }
+        p.pending = false;
+    }
+}
+
 }  // namespace rbffd
 
 extern "C" {
+
+int rbffd_profile_enable(int on) {
+    rbffd::g_profiling.store(on ? 1 : 0);
+    return RBFFD_OK;
+}
+
+int rbffd_profile_read(rbffd_profile* out, int reset) {
+    using namespace rbffd;
+    if (!out) return RBFFD_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (ProfPair& p : g_pairs)
+            if (p.pending) cudaEventSynchronize(p.b);
+    }
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    out->launches = g_launches.load();
+    out->spmv64_launches = g_prof_launches[kProfSpmv64];
+    out->spmv64_ms = g_prof_ms[kProfSpmv64];
+    out->spmv64_bytes = g_prof_bytes[kProfSpmv64];
+    out->spmv32_launches = g_prof_launches[kProfSpmv32];
+    out->spmv32_ms = g_prof_ms[kProfSpmv32];
+    out->spmv32_bytes = g_prof_bytes[kProfSpmv32];
+    if (reset) {
+        g_launches.store(0);
+        for (int k = 0; k < kProfKinds; ++k) {
+            g_prof_launches[k] = 0;
+            g_prof_ms[k] = 0.0;
+            g_prof_bytes[k] = 0;
+        }
+    }
+    return RBFFD_OK;
+}
+
 
 const char* rbffd_status_string(int s) {
     switch (s) {

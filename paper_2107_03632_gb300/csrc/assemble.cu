@@ -156,6 +156,7 @@ extern "C" int rbffd_assemble(const int32_t* idx, const double* w, const uint8_t
         return RBFFD_ERR_INVALID_ARG;
     assemble_fill_kernel<<<grid_for(N * 32, 256), 256, 0, as_stream(stream)>>>(idx, w, is_dirichlet, N, n, row_ptr,
                                                                                nnz, col, val, val32);
+    note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }
@@ -165,6 +166,7 @@ extern "C" int rbffd_rhs(const double* f, const double* g, const uint8_t* is_dir
     using namespace rbffd;
     if (!f || !g || !is_dirichlet || !b || N <= 0) return RBFFD_ERR_INVALID_ARG;
     rhs_kernel<<<grid_for(N, 256), 256, 0, as_stream(stream)>>>(f, g, is_dirichlet, N, b);
+    note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }
@@ -197,6 +199,7 @@ extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* 
     transpose_scatter_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, val, N, A->nnz, row_ptr_t, counts,
                                                                     col_t, val_t);
     row_sort_kernel<<<grid_for(N, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t);
+    note_launches(3);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }

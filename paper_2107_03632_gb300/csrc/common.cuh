@@ -52,6 +52,18 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Launch accounting and optional kernel timing (rbffd_profile_*).
+void note_launches(int count);
+bool profiling();
+enum ProfKind { kProfSpmv64 = 0, kProfSpmv32 = 1, kProfKinds = 2 };
+// Brackets one launch with events when profiling is on: call prof_begin
+// before and prof_end after the launch (both on stream `st`).
+int prof_begin(cudaStream_t st);
+void prof_end(int slot, cudaStream_t st, int kind, int64_t bytes);
+// Adds the device time of completed bracketed launches (call after the
+// stream has been synchronised).
+void prof_collect();
+
 // ---------------------------------------------------------------- device --
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -387,6 +387,7 @@ extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* i
         knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
     else
         knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+    note_launches(5);  // bbox, setup, count, scatter, knn (+3 in the scan)
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }

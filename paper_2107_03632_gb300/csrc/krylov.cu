@@ -376,18 +376,30 @@ struct Ops {
         residual_kernel<VT, TPR><<<nblocks(), kThreads, 0, st>>>(A.row_ptr, A.col, static_cast<const VT*>(A.val),
                                                                  A.n_rows, b, x, w.dinv, r, scale, init, w.rh, w.p,
                                                                  w.v, tol, max_iter, w.st, w.part);
+        note_launches(1);
+    }
+    // Algorithmic bytes of one SpMV launch (see rbffd_profile in rbffd.h).
+    static int64_t spmv_bytes(const rbffd_csr& A) {
+        return A.nnz * (int64_t)(sizeof(VT) + 4) + 8 * (A.n_rows + 1) + 4 * 8 * A.n_rows;
     }
     static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
         const int64_t N = A.n_rows;
         const int nb = nblocks();
         const VT* val = static_cast<const VT*>(A.val);
+        const int kind = sizeof(VT) == 8 ? kProfSpmv64 : kProfSpmv32;
+        const int64_t bytes = spmv_bytes(A);
         update_p_kernel<<<nb, kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
+        int ev = prof_begin(st);
         spmv_kernel<VT, TPR, 0><<<nb, kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.p, w.dinv, w.v, w.rh, w.st,
                                                          w.part);
+        prof_end(ev, st, kind, bytes);
         update_s_kernel<<<nb, kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
+        ev = prof_begin(st);
         spmv_kernel<VT, TPR, 1><<<nb, kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.s, w.dinv, w.t, nullptr,
                                                          w.st, w.part);
+        prof_end(ev, st, kind, bytes);
         update_xr_kernel<<<nb, kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d, w.st, w.part);
+        note_launches(5);
     }
 };
 
@@ -417,6 +429,7 @@ void iteration_dispatch(int tpr, const rbffd_csr& A, double* x, const Work& w, c
 int read_state(const Work& w, KState* hs, cudaStream_t st) {
     RBFFD_CUDA_TRY(cudaMemcpyAsync(hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (profiling()) prof_collect();
     return RBFFD_OK;
 }
 
@@ -465,6 +478,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     RBFFD_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(KState), st));
     diag_kernel<<<std::min<int64_t>((N + kThreads - 1) / kThreads, sm_count() * 8), kThreads, 0, st>>>(
         A->row_ptr, A->col, static_cast<const double*>(A->val), N, A->nnz, o->jacobi ? 1 : 0, w.d, w.dinv, w.st);
+    note_launches(1);
     RBFFD_LAUNCH_CHECK();
     int rc = read_state(w, &hs, st);
     if (rc != RBFFD_OK) return rc;
@@ -497,6 +511,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
             flag = bicgstab_run<float>(*A32, w.r_outer, w.dx, o->inner_tol, budget, w, st, &hs);
             if (flag >= 0) {
                 axpy_kernel<<<nblocks(), kThreads, 0, st>>>(N, x, w.dx);
+                note_launches(1);
                 RBFFD_LAUNCH_CHECK();
             }
         }
@@ -554,6 +569,7 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
         const int64_t N = AT->n_rows;
         adjoint_grad_kernel<<<std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, st>>>(N, is_dirichlet,
                                                                                                lambda, dLdf, dLdg);
+        note_launches(1);
         RBFFD_LAUNCH_CHECK();
     }
     return RBFFD_OK;

@@ -114,6 +114,7 @@ inline cudaError_t exclusive_scan(Load load, int64_t n, T* out, T* sums, T* gran
     scan_tiles_kernel<T, Load><<<tiles, kScanThreads, 0, st>>>(load, n, out, sums);
     scan_sums_kernel<T><<<1, kScanThreads, 0, st>>>(sums, tiles, grand);
     scan_add_kernel<T><<<tiles, kScanThreads, 0, st>>>(out, n, sums);
+    note_launches(3);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
 
         // ---- Phi block (upper triangle pairs, mirrored) and the RHS ---------
         const int npairs = n * (n - 1) / 2;
+        int coincident = 0;  // two stencil nodes at the same point: singular system
         {
             // pair p -> (j, k), j < k, enumerated row by row of the upper triangle
             for (int pidx = lane; pidx < npairs; pidx += 32) {
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                 const double dx = __dadd_rn(cs(2 * j), -cs(2 * k));
                 const double dy = __dadd_rn(cs(2 * j + 1), -cs(2 * k + 1));
                 const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                coincident |= (dx == 0.0 && dy == 0.0) ? 1 : 0;
                 const double phi = __dmul_rn(__dmul_rn(r, r), r);
                 A[(size_t)j * LD + k] = phi;
                 A[(size_t)k * LD + j] = phi;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         __syncwarp();
 
         // ---- Gaussian elimination with partial pivoting ---------------------
-        int singular = __any_sync(0xffffffffu, bad_index) ? 1 : 0;
+        int singular = __any_sync(0xffffffffu, bad_index | coincident) ? 1 : 0;
         for (int k = 0; k < M && !singular; ++k) {
             // pivot: largest |a_ik|, i >= k, lowest i on ties
             unsigned long long best = 0;
@@ -304,6 +306,7 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
     weights_kernel<<<blocks, 32 * wpb, smem, as_stream(stream)>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n,
                                                                   m, g.s, g.M, g.LD, g.coords_in_zero_block,
                                                                   g.smem_doubles, w, node_status);
+    note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }

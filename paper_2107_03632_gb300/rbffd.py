@@ -76,6 +76,21 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64),
+        ("spmv64_launches", ctypes.c_int64),
+        ("spmv64_ms", ctypes.c_double),
+        ("spmv64_bytes", ctypes.c_int64),
+        ("spmv32_launches", ctypes.c_int64),
+        ("spmv32_ms", ctypes.c_double),
+        ("spmv32_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # (name, restype, argtypes) of every exported symbol declared in include/rbffd.h
 _VP, _I64, _I32, _SZ, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
 SIGNATURES = {
@@ -96,6 +111,8 @@ SIGNATURES = {
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
 }
 
 
@@ -157,7 +174,8 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 
 
 # ----------------------------------------------------------------- stencils --
-def rbffd_stencils(xy: torch.Tensor, n: int, idx: torch.Tensor | None = None) -> torch.Tensor:
+def rbffd_stencils(xy: torch.Tensor, n: int, idx: torch.Tensor | None = None,
+                   ws: torch.Tensor | None = None) -> torch.Tensor:
     _require(xy, torch.float64, "xy")
     N = xy.shape[0]
     if xy.dim() != 2 or xy.shape[1] != 2:
@@ -166,7 +184,8 @@ def rbffd_stencils(xy: torch.Tensor, n: int, idx: torch.Tensor | None = None) ->
     if idx is None:
         idx = torch.empty((N, n), dtype=torch.int32, device=xy.device)
     _require(idx, torch.int32, "idx", (N, n))
-    ws = _workspace(lib.rbffd_stencils_workspace_size(N, n), xy.device)
+    if ws is None:
+        ws = _workspace(lib.rbffd_stencils_workspace_size(N, n), xy.device)
     _check(lib.rbffd_stencils(_ptr(xy), N, n, _ptr(idx), _ptr(ws), ws.numel(), _stream(xy.device)),
            "rbffd_stencils")
     return idx
@@ -215,12 +234,16 @@ class CsrMatrix:
         return Csr(self.n_rows, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val32), 1)
 
 
-def rbffd_assemble_pattern(is_dirichlet: torch.Tensor, n: int) -> torch.Tensor:
+def rbffd_assemble_pattern(is_dirichlet: torch.Tensor, n: int, row_ptr: torch.Tensor | None = None,
+                           ws: torch.Tensor | None = None) -> torch.Tensor:
     _require(is_dirichlet, torch.uint8, "is_dirichlet")
     N = is_dirichlet.numel()
     lib = load()
-    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=is_dirichlet.device)
-    ws = _workspace(lib.rbffd_assemble_workspace_size(N), is_dirichlet.device)
+    if row_ptr is None:
+        row_ptr = torch.empty(N + 1, dtype=torch.int64, device=is_dirichlet.device)
+    _require(row_ptr, torch.int64, "row_ptr", (N + 1,))
+    if ws is None:
+        ws = _workspace(lib.rbffd_assemble_workspace_size(N), is_dirichlet.device)
     _check(lib.rbffd_assemble_pattern(_ptr(is_dirichlet), N, n, _ptr(row_ptr), _ptr(ws), ws.numel(),
                                       _stream(is_dirichlet.device)), "rbffd_assemble_pattern")
     return row_ptr
@@ -228,20 +251,31 @@ def rbffd_assemble_pattern(is_dirichlet: torch.Tensor, n: int) -> torch.Tensor:
 
 def rbffd_assemble(idx: torch.Tensor, w: torch.Tensor, is_dirichlet: torch.Tensor,
                    row_ptr: torch.Tensor | None = None, nnz: int | None = None,
-                   want_f32: bool = False) -> CsrMatrix:
+                   want_f32: bool = False, out: CsrMatrix | None = None) -> CsrMatrix:
+    """CSR of the Poisson operator.  With `out`, its row_ptr (already holding
+    the pattern) and col/val(/val32) buffers are filled in place, without a
+    device->host read."""
     _require(idx, torch.int32, "idx")
     N, n = idx.shape
     _require(w, torch.float64, "w", (N, n))
     _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
     lib = load()
-    if row_ptr is None:
-        row_ptr = rbffd_assemble_pattern(is_dirichlet, n)
-    if nnz is None:
-        nnz = int(row_ptr[-1].item())  # one device->host read to size col/val
     dev = idx.device
-    col = torch.empty(nnz, dtype=torch.int32, device=dev)
-    val = torch.empty(nnz, dtype=torch.float64, device=dev)
-    val32 = torch.empty(nnz, dtype=torch.float32, device=dev) if want_f32 else None
+    if out is not None:
+        row_ptr, col, val, val32 = out.row_ptr, out.col, out.val, out.val32
+        nnz = col.numel()
+        _require(row_ptr, torch.int64, "row_ptr", (N + 1,))
+        _require(val, torch.float64, "val", (nnz,))
+        if val32 is not None:
+            _require(val32, torch.float32, "val32", (nnz,))
+    else:
+        if row_ptr is None:
+            row_ptr = rbffd_assemble_pattern(is_dirichlet, n)
+        if nnz is None:
+            nnz = int(row_ptr[-1].item())  # one device->host read to size col/val
+        col = torch.empty(nnz, dtype=torch.int32, device=dev)
+        val = torch.empty(nnz, dtype=torch.float64, device=dev)
+        val32 = torch.empty(nnz, dtype=torch.float32, device=dev) if want_f32 else None
     _check(lib.rbffd_assemble(_ptr(idx), _ptr(w), _ptr(is_dirichlet), N, n, _ptr(row_ptr), nnz, _ptr(col),
                               _ptr(val), _ptr(val32), _stream(dev)), "rbffd_assemble")
     return CsrMatrix(row_ptr, col, val, val32)
@@ -278,6 +312,14 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
 def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=1e-5, max_outer=60, jacobi=True):
     prec = {"fp64": 0, "mixed": 1}[precision]
     return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0)
+
+
+def stencils_workspace(N: int, n: int, device) -> torch.Tensor:
+    return _workspace(load().rbffd_stencils_workspace_size(N, n), device)
+
+
+def assemble_workspace(N: int, device) -> torch.Tensor:
+    return _workspace(load().rbffd_assemble_workspace_size(N), device)
 
 
 def solve_workspace(N: int, opts: SolveOpts, device) -> torch.Tensor:
@@ -334,3 +376,14 @@ def rbffd_solve_adjoint(AT: CsrMatrix, is_dirichlet: torch.Tensor, dLdu: torch.T
     d = info.as_dict()
     d["status_code"] = st
     return lam, dLdf, dLdg, d
+
+
+# --------------------------------------------------------------- profiling --
+def rbffd_profile_enable(on: bool = True):
+    _check(load().rbffd_profile_enable(1 if on else 0), "rbffd_profile_enable")
+
+
+def rbffd_profile_read(reset: bool = False) -> dict:
+    p = Profile()
+    _check(load().rbffd_profile_read(ctypes.byref(p), 1 if reset else 0), "rbffd_profile_read")
+    return p.as_dict()

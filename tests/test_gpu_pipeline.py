@@ -116,8 +116,10 @@ def test_weights_singular_stencil_flagged(lib):
     w, st = rbffd.rbffd_weights(T(xy), T(idx), 2)
     st = st.cpu().numpy()
     _, st_ref = oracle.weights(xy, idx, 2)
+    holds_both = np.array([(4 in row) and (5 in row) for row in idx])
     assert st[4] == 1 and st[5] == 1
     assert np.array_equal(st.astype(bool), st_ref.astype(bool))
+    assert np.array_equal(st.astype(bool), holds_both)
     assert np.all(w.cpu().numpy()[st == 1] == 0.0)
 
 

@@ -367,3 +367,16 @@ def test_fixture_counts_and_determinism():
     assert np.all(r[: a.n_interior] < 1 - 0.02) and np.allclose(r[a.n_interior:], 1.0)
     u = uniform01(splitmix64(1, 1000))
     assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 0.05
+
+
+def test_weights_coincident_nodes_flagged_singular():
+    """Two nodes at one point give two identical rows: every stencil that
+    holds both is singular (status 1, zero weights); the others are not."""
+    d = disk_nodes(0.1)
+    xy = d.xy.copy()
+    xy[5] = xy[4]
+    idx = oracle.knn(xy, 12)
+    w, st = oracle.weights(xy, idx, 2)
+    holds_both = np.array([(4 in row) and (5 in row) for row in idx])
+    assert np.array_equal(st.astype(bool), holds_both)
+    assert np.all(w[holds_both] == 0.0)
