@@ -157,8 +157,11 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
 /* precision 1 (mixed): an FP64 refinement loop (r = b - A x with the FP64   */
 /*   matrix, x += correction in FP64) around inner BiCGSTAB iterations that  */
 /*   read the float32 copy of the matrix (A32: same row_ptr and col arrays  */
-/*   as A, float32 values); an inner                                         */
-/*   pass ends when its residual has fallen by inner_tol.                    */
+/*   as A, float32 values) in difference form sum_j a_ij (d_j - d_i) +       */
+/*   (sum_j a_ij) d_i, with double-float (2 x float32) Krylov vectors; an   */
+/*   inner pass ends when its residual has fallen by inner_tol.             */
+/* FP64 mode recomputes the residual from b - A x whenever the recurrence    */
+/* residual has dropped 1e3 below its running maximum (residual replacement).*/
 /*                                                                           */
 /* x is in/out: the initial guess on entry, the solution on exit (warm       */
 /* start).  The call BLOCKS the host until the solve ends and synchronises   */
@@ -173,6 +176,9 @@ typedef struct rbffd_solve_opts {
     double inner_tol;    /* mixed: residual reduction per refinement pass, e.g. 1e-5 */
     int32_t max_outer;   /* mixed: cap on refinement passes */
     int32_t jacobi;      /* 1 = left Jacobi scaling (default), 0 = none */
+    int32_t refine;      /* mixed: 0 = restart the inner Krylov space at each
+                            refinement, 1 = keep the search direction across
+                            refinements (reliable updates) */
 } rbffd_solve_opts;
 
 typedef struct rbffd_solve_info {

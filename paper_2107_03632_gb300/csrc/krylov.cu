@@ -1,74 +1,95 @@
-// BiCGSTAB for the assembled RBF-FD Poisson system, FP64 and mixed
-// FP32-inner / FP64-refinement, plus the adjoint solve (sm_103a).
+// BiCGSTAB for the assembled RBF-FD Poisson system: an FP64 solver and a
+// mixed solver with FP32 matrix values inside FP64 refinement; plus the
+// adjoint solve (sm_103a).
 //
 // Sec. VI names the implicit solution of the Poisson problem as the next
 // step beyond the paper's explicit loop; A u = b is solved here by BiCGSTAB
 // (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) with left Jacobi
-// scaling D^-1 A u = D^-1 b.  Convergence is always judged on the unscaled
-// residual |b - A u| <= tol |b|, re-computed explicitly at the end.
+// scaling D^-1 A u = D^-1 b.  Convergence is judged on the unscaled residual
+// |b - A u| <= tol |b|, and a solve returns OK only after that residual has
+// been recomputed explicitly from u.
 //
-// One iteration = five kernels on the caller's stream:
-//   update_p : p = r + beta (p - omega v)            (beta from device state)
-//   spmv_v   : v = D^-1 A p,  partial (rh, v)        -> alpha
-//   update_s : s = r - alpha v
-//   spmv_t   : t = D^-1 A s,  partials (t,s), (t,t)  -> omega
-//   update_xr: x += alpha p + omega s, r = s - omega t,
-//              partials |D r|^2, (rh, r)             -> rho, stop test
+// Hardware facts that shape the kernels: FP64 on this chip issues about
+// 0.55e12 DFMA/s while HBM streams about 0.83e12 doubles/s, so an FP64
+// kernel that does one FP64 operation per double it reads is as much
+// FP64-bound as HBM-bound; FP32 runs ~60x faster.  Hence
+//  * the FP64 SpMV gives each row TPR <= 4 lanes (few FP64 reduction adds
+//    per row), and every vector kernel fuses its dot products;
+//  * the mixed solver keeps its Krylov vectors as double-float pairs
+//    (df32.cuh, ~48-bit) and does all inner arithmetic on the FP32 pipe, so
+//    its inner iteration is bound by HBM bytes only (4-byte values).
+//
+// FP64 iteration (five kernels on the caller's stream):
+//   update_p  p = r + beta (p - omega v)
+//   spmv(v)   v = D^-1 A p, (rh, v)               -> alpha
+//   update_s  s = r - alpha v
+//   spmv(t)   t = D^-1 A s, (t, s), (t, t)        -> omega
+//   update_xr x += alpha p + omega s, r = s - omega t, |D r|^2, (rh, r) -> rho
 // Scalars live in a device state block; each reduction is finished by the
-// last block to arrive (fixed order over block partials, so results are
-// deterministic for a given grid), so no iteration needs the host.  The
-// host enqueues iterations in chunks and reads the 100-byte state between
-// chunks; kernels of a finished solve return at once.
+// last block to arrive (fixed summation order: deterministic for a given
+// grid).  The host enqueues iterations in chunks and reads the state between
+// chunks; kernels of a finished run return at once.  Residual replacement
+// (van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000): when the recurrence
+// residual has fallen 1e3 below its running maximum, r is recomputed from
+// b - A x (keeping p and rh), which bounds the drift between the recurrence
+// and the true residual.
 //
-// SpMV: CSR, TPR lanes per row (TPR chosen from the mean row length so each
-// lane streams several entries), matrix streams read with evict-first
-// hints, gathered vector through L1/L2.  Mixed precision reads the float32
-// copy of the values (8 bytes per entry instead of 12).
+// Mixed solver: an FP64 refinement loop computes r = b - A x with the FP64
+// matrix and adds the inner correction to x in FP64.  The inner BiCGSTAB
+// runs on the float32 values, written in difference form
+//     (A d)_i = sum_j a_ij (d_j - d_i) + sigma_i d_i,  sigma_i = sum_j a_ij,
+// which is A exactly in exact arithmetic and keeps the zero row sums of the
+// RBF-FD Laplacian exact after rounding a_ij to float (plain float rounding
+// of a_ij would perturb the smooth modes by ~n eps_32 / h^2).  An inner pass
+// ends when its residual has fallen by inner_tol relative to the outer
+// residual; refine 0 restarts the Krylov space at each refinement
+// (classical iterative refinement), refine 1 keeps the search direction
+// across refinements (reliable updates).
 #include "common.cuh"
+#include "df32.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 namespace rbffd {
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 2048;
-constexpr int kSlots = 6;
+constexpr int kSlots = 8;
 constexpr int kQ = 3;
 
-enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3 };
+enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kReplace = 4 };
+enum Slot : int { kSlotResid = 0, kSlotV = 1, kSlotT = 2, kSlotXR = 3, kSlotLoad = 4 };
+enum ResidMode : int { kInit = 0, kReplaceR = 1, kCheck = 2 };
 
 struct KState {
     double rho, rho_new, alpha, omega;
-    double bnorm2;  // |b|^2 of the system being iterated
-    double tol2;    // stop when |r|^2 <= tol2 (unscaled)
+    double bnorm2;  // |b|^2 of the system (unscaled)
+    double tol2;    // converged when |r|^2 <= tol2
     double rnorm2;  // last recurrence |r|^2 (unscaled)
-    double tnorm2;  // last explicit residual |b - A x|^2
-    int iter;
+    double tnorm2;  // last explicit |b - A x|^2
+    double rmax2;   // reference |r|^2 of the replacement / refinement trigger
+    double repl2;   // trigger when |r|^2 < repl2 * rmax2
+    int iter;       // iterations of the current run
     int max_iter;
     int flag;
     int bad;        // input validation failure
+    int track_max;  // 1: rmax2 follows the running maximum
+    int pad;
     unsigned int counter[kSlots];
 };
-
-struct Work {
-    KState* st;
-    double* part;  // [kSlots][kQ][kMaxBlocks]
-    double *r, *rh, *p, *v, *s, *t;
-    double *d, *dinv;
-    double *r_outer, *dx;
-};
-
-enum Slot { kSlotResid = 0, kSlotV = 1, kSlotT = 2, kSlotXR = 3, kSlotDiag = 4 };
 
 __device__ __forceinline__ double* part_at(double* part, int slot, int q) {
     return part + ((size_t)slot * kQ + q) * kMaxBlocks;
 }
 
 // Block-reduce NQ values, store block partials, and let the last block to
-// arrive sum all partials (returned in tot[]).  Returns true in that block.
+// arrive sum all partials in block order (returned in tot[]).  True there.
 template <int NQ>
 __device__ bool reduce_last(double (&v)[NQ], double* part, int slot, unsigned int* counter, double (&tot)[NQ]) {
     __shared__ double sh[32];
@@ -97,157 +118,182 @@ __device__ bool reduce_last(double (&v)[NQ], double* part, int slot, unsigned in
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
-template <class VT>
-__device__ __forceinline__ double ld_val(const VT* p) {
-    return (double)__ldcs(p);
-}
+// Iterate rows in groups of TPR lanes with a warp-uniform loop (every lane
+// of a warp runs the same number of trips, so full-mask shuffles are safe).
+#define RBFFD_ROW_LOOP(TPR, N, i, valid, BODY)                                        \
+    {                                                                                 \
+        const int64_t g0_ = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / (TPR); \
+        const int64_t ng_ = ((int64_t)gridDim.x * blockDim.x) / (TPR);                \
+        const int64_t off_ = (threadIdx.x & 31) / (TPR);                              \
+        for (int64_t base_ = g0_ - off_; base_ < (N); base_ += ng_) {                 \
+            const int64_t i = base_ + off_;                                           \
+            const bool valid = i < (N);                                               \
+            BODY                                                                      \
+        }                                                                             \
+    }
 
-// Sum of row `row` times x, TPR lanes cooperating (result valid in all of
-// them).  All 32 lanes of the warp must call it together (shuffles); a lane
-// group with valid == false contributes an empty row.
-template <class VT, int TPR>
-__device__ __forceinline__ double row_dot(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
-                                          const VT* __restrict__ val, const double* __restrict__ x, int64_t row,
-                                          int sub, bool valid) {
+#define RBFFD_ELEM_LOOP(N, i) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (N); i += (int64_t)gridDim.x * blockDim.x)
+
+// ============================================================== FP64 ========
+// sum_k a_k x[col_k] over one row, TPR lanes (result in every lane).
+template <int TPR>
+__device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                            const double* __restrict__ val, const double* __restrict__ x,
+                                            int64_t row, int sub, bool valid) {
     int64_t a = 0, e = 0;
     if (valid) {
-        a = row_ptr[row];
-        e = row_ptr[row + 1];
+        a = __ldg(row_ptr + row);
+        e = __ldg(row_ptr + row + 1);
     }
     double sum = 0.0;
 #pragma unroll 4
-    for (int64_t k = a + sub; k < e; k += TPR) sum = fma(ld_val(val + k), x[__ldcs(col + k)], sum);
+    for (int64_t k = a + sub; k < e; k += TPR) sum = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), sum);
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
     return sum;
 }
 
-// ---- setup: diagonal, Jacobi scaling, validation ---------------------------
-__global__ void __launch_bounds__(kThreads) diag_kernel(const int64_t* __restrict__ row_ptr,
-                                                        const int* __restrict__ col, const double* __restrict__ val,
-                                                        int64_t N, int64_t nnz, int jacobi, double* __restrict__ d,
-                                                        double* __restrict__ dinv, KState* st) {
+// ---- setup: diagonal, row sums, Jacobi scaling, validation -----------------
+__global__ void __launch_bounds__(kThreads) setup_kernel(const int64_t* __restrict__ row_ptr,
+                                                         const int* __restrict__ col,
+                                                         const double* __restrict__ val, int64_t N, int64_t nnz,
+                                                         int jacobi, double* __restrict__ d,
+                                                         double* __restrict__ dinv, float* __restrict__ d32,
+                                                         float* __restrict__ dinv32, float* __restrict__ sigma32,
+                                                         KState* st) {
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    RBFFD_ELEM_LOOP(N, i) {
         const int64_t a = row_ptr[i], e = row_ptr[i + 1];
-        double di = 0.0;
+        double di = 0.0, rs = 0.0;
         if (a < 0 || e < a || e > nnz) {
             bad = 1;
         } else {
             for (int64_t k = a; k < e; ++k) {
                 const int c = col[k];
+                const double v = val[k];
                 if ((unsigned)c >= (unsigned)N) bad = 1;
-                if (c == (int)i) di = val[k];
+                if (c == (int)i) di = v;
+                rs += v;
             }
         }
         if (i == N - 1 && e != nnz) bad = 1;
         if (i == 0 && a != 0) bad = 1;
         const bool use = jacobi && di != 0.0 && isfinite(di);
-        d[i] = use ? di : 1.0;
-        dinv[i] = use ? 1.0 / di : 1.0;
+        const double dv = use ? di : 1.0;
+        const double iv = use ? 1.0 / di : 1.0;
+        d[i] = dv;
+        dinv[i] = iv;
+        if (d32) {
+            d32[i] = __double2float_rn(dv);
+            dinv32[i] = __double2float_rn(iv);
+            sigma32[i] = __double2float_rn(rs);
+        }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
 }
 
-// r = D^-1 (b - A x) (or unscaled when scale_out == 0); partials |b - A x|^2,
-// |b|^2, |r|^2.  With init: rh = r, p = v = 0 and the iteration scalars are
-// reset (rho_new = (rh, r)).
-template <class VT, int TPR>
-__global__ void __launch_bounds__(kThreads) residual_kernel(const int64_t* __restrict__ row_ptr,
-                                                            const int* __restrict__ col, const VT* __restrict__ val,
-                                                            int64_t N, const double* __restrict__ b,
-                                                            const double* __restrict__ x,
-                                                            const double* __restrict__ dinv, double* __restrict__ r,
-                                                            int scale_out, int init, double* __restrict__ rh,
-                                                            double* __restrict__ p, double* __restrict__ v,
-                                                            double tol, int max_iter, KState* st, double* part) {
+// kInit:     r = D^-1 (b - A x), rh = r, p = v = 0, scalars reset.
+// kReplaceR: r = D^-1 (b - A x), keep rh, p, v; rho_new = (rh, r).
+// kCheck:    r = b - A x (unscaled), |r|^2 and |b|^2 only.
+template <int TPR, int MODE>
+__global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __restrict__ row_ptr,
+                                                           const int* __restrict__ col,
+                                                           const double* __restrict__ val, int64_t N,
+                                                           const double* __restrict__ b,
+                                                           const double* __restrict__ x,
+                                                           const double* __restrict__ dinv,
+                                                           double* __restrict__ r, double* __restrict__ rh,
+                                                           double* __restrict__ p, double* __restrict__ v,
+                                                           double tol, int max_iter, double repl, KState* st,
+                                                           double* part) {
     const int sub = threadIdx.x & (TPR - 1);
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPR;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / TPR;
-    const int64_t gw = g0 - (threadIdx.x & 31) / TPR;  // first group of this warp: loop bound is warp-uniform
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t base = gw; base < N; base += ng) {
-        const int64_t i = base + (g0 - gw);
-        const bool valid = i < N;
-        const double ax = row_dot<VT, TPR>(row_ptr, col, val, x, i, sub, valid);
+    RBFFD_ROW_LOOP(TPR, N, i, valid, {
+        const double ax = row_dot64<TPR>(row_ptr, col, val, x, i, sub, valid);
         if (valid && sub == 0) {
             const double bi = b[i];
             const double rt = bi - ax;
-            const double ri = scale_out ? rt * dinv[i] : rt;
-            r[i] = ri;
-            if (init) {
-                rh[i] = ri;
-                p[i] = 0.0;
-                v[i] = 0.0;
-            }
             acc[0] = fma(rt, rt, acc[0]);
             acc[1] = fma(bi, bi, acc[1]);
-            acc[2] = fma(ri, ri, acc[2]);
+            if (MODE == kCheck) {
+                r[i] = rt;
+            } else {
+                const double ri = rt * dinv[i];
+                r[i] = ri;
+                if (MODE == kInit) {
+                    rh[i] = ri;
+                    p[i] = 0.0;
+                    v[i] = 0.0;
+                    acc[2] = fma(ri, ri, acc[2]);
+                } else {
+                    acc[2] = fma(rh[i], ri, acc[2]);
+                }
+            }
         }
-    }
+    })
     double tot[3];
     if (reduce_last<3>(acc, part, kSlotResid, &st->counter[kSlotResid], tot) && threadIdx.x == 0) {
         st->tnorm2 = tot[0];
-        if (init) {
+        if (MODE == kCheck) {
+            st->bnorm2 = tot[1];
+            return;
+        }
+        if (MODE == kInit) {
             st->bnorm2 = tot[1];
             st->tol2 = tol * tol * tot[1];
-            st->rnorm2 = tot[0];
             st->rho = 1.0;
             st->alpha = 1.0;
             st->omega = 1.0;
-            st->rho_new = tot[2];
             st->iter = 0;
             st->max_iter = max_iter;
-            int flag = kRunning;
-            if (!(tot[0] <= st->tol2)) {
-                if (!finite(tot[0]) || !finite(tot[2])) flag = kBreakdown;
-                else if (max_iter <= 0) flag = kMaxIter;
-            } else {
-                flag = kConverged;
-            }
-            st->flag = flag;
+            st->repl2 = repl * repl;
+            st->track_max = 1;
         }
+        st->rnorm2 = tot[0];
+        st->rmax2 = tot[0];
+        st->rho_new = tot[2];
+        int flag = kRunning;
+        if (tot[0] <= st->tol2) flag = kConverged;
+        else if (!finite(tot[0]) || !finite(tot[2])) flag = kBreakdown;
+        else if (st->iter >= st->max_iter) flag = kMaxIter;
+        st->flag = flag;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) update_p_kernel(int64_t N, const double* __restrict__ r,
-                                                            const double* __restrict__ v, double* __restrict__ p,
-                                                            const KState* st) {
+__global__ void __launch_bounds__(kThreads) update_p64_kernel(int64_t N, const double* __restrict__ r,
+                                                              const double* __restrict__ v, double* __restrict__ p,
+                                                              const KState* st) {
     if (st->flag != kRunning) return;
     const double beta = (st->rho_new / st->rho) * (st->alpha / st->omega);
     const double omega = st->omega;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+    RBFFD_ELEM_LOOP(N, i) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
 }
 
-// y = D^-1 A xin; partial (rh, y) [NQ = 1] or (y, s), (y, y) [NQ = 2].
-template <class VT, int TPR, int MODE>
-__global__ void __launch_bounds__(kThreads) spmv_kernel(const int64_t* __restrict__ row_ptr,
-                                                        const int* __restrict__ col, const VT* __restrict__ val,
-                                                        int64_t N, const double* __restrict__ xin,
-                                                        const double* __restrict__ dinv, double* __restrict__ y,
-                                                        const double* __restrict__ other, KState* st, double* part) {
+// y = D^-1 A xin; MODE 0: (rh, y) -> alpha.  MODE 1: (y, xin), (y, y) -> omega.
+template <int TPR, int MODE>
+__global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restrict__ row_ptr,
+                                                          const int* __restrict__ col,
+                                                          const double* __restrict__ val, int64_t N,
+                                                          const double* __restrict__ xin,
+                                                          const double* __restrict__ dinv, double* __restrict__ y,
+                                                          const double* __restrict__ rh, KState* st, double* part) {
     if (st->flag != kRunning) return;
     const int sub = threadIdx.x & (TPR - 1);
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPR;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / TPR;
-    const int64_t gw = g0 - (threadIdx.x & 31) / TPR;  // warp-uniform loop bound
     double acc[2] = {0.0, 0.0};
-    for (int64_t base = gw; base < N; base += ng) {
-        const int64_t i = base + (g0 - gw);
-        const bool valid = i < N;
-        const double ax = row_dot<VT, TPR>(row_ptr, col, val, xin, i, sub, valid);
+    RBFFD_ROW_LOOP(TPR, N, i, valid, {
+        const double ax = row_dot64<TPR>(row_ptr, col, val, xin, i, sub, valid);
         if (valid && sub == 0) {
             const double yi = ax * dinv[i];
             y[i] = yi;
             if (MODE == 0) {
-                acc[0] = fma(other[i], yi, acc[0]);  // (rh, v)
+                acc[0] = fma(rh[i], yi, acc[0]);
             } else {
-                acc[0] = fma(yi, xin[i], acc[0]);  // (t, s)
-                acc[1] = fma(yi, yi, acc[1]);      // (t, t)
+                acc[0] = fma(yi, xin[i], acc[0]);
+                acc[1] = fma(yi, yi, acc[1]);
             }
         }
-    }
+    })
     if (MODE == 0) {
         double a1[1] = {acc[0]}, tot[1];
         if (reduce_last<1>(a1, part, kSlotV, &st->counter[kSlotV], tot) && threadIdx.x == 0) {
@@ -269,26 +315,40 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(const int64_t* __restric
     }
 }
 
-__global__ void __launch_bounds__(kThreads) update_s_kernel(int64_t N, const double* __restrict__ r,
-                                                            const double* __restrict__ v, double* __restrict__ s,
-                                                            const KState* st) {
+__global__ void __launch_bounds__(kThreads) update_s64_kernel(int64_t N, const double* __restrict__ r,
+                                                              const double* __restrict__ v, double* __restrict__ s,
+                                                              const KState* st) {
     if (st->flag != kRunning) return;
     const double alpha = st->alpha;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        s[i] = fma(-alpha, v[i], r[i]);
+    RBFFD_ELEM_LOOP(N, i) s[i] = fma(-alpha, v[i], r[i]);
 }
 
-__global__ void __launch_bounds__(kThreads) update_xr_kernel(int64_t N, double* __restrict__ x,
-                                                             const double* __restrict__ p,
-                                                             const double* __restrict__ s,
-                                                             const double* __restrict__ t, double* __restrict__ r,
-                                                             const double* __restrict__ rh,
-                                                             const double* __restrict__ d, KState* st,
-                                                             double* part) {
+// Stop test shared by both engines' update_xr.
+__device__ __forceinline__ void finish_iteration(KState* st, double rn2, double rho_new) {
+    st->rnorm2 = rn2;
+    st->rho_new = rho_new;
+    const int it = st->iter + 1;
+    st->iter = it;
+    if (st->track_max && rn2 > st->rmax2) st->rmax2 = rn2;
+    int flag = kRunning;
+    if (rn2 <= st->tol2) flag = kConverged;
+    else if (!finite(rn2) || !finite(rho_new) || rho_new == 0.0 || st->omega == 0.0) flag = kBreakdown;
+    else if (rn2 < st->repl2 * st->rmax2) flag = kReplace;
+    else if (it >= st->max_iter) flag = kMaxIter;
+    st->flag = flag;
+}
+
+__global__ void __launch_bounds__(kThreads) update_xr64_kernel(int64_t N, double* __restrict__ x,
+                                                               const double* __restrict__ p,
+                                                               const double* __restrict__ s,
+                                                               const double* __restrict__ t, double* __restrict__ r,
+                                                               const double* __restrict__ rh,
+                                                               const double* __restrict__ d, KState* st,
+                                                               double* part) {
     if (st->flag != kRunning) return;
     const double alpha = st->alpha, omega = st->omega;
     double acc[2] = {0.0, 0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    RBFFD_ELEM_LOOP(N, i) {
         const double si = s[i];
         x[i] = fma(omega, si, fma(alpha, p[i], x[i]));
         const double ri = fma(-omega, t[i], si);
@@ -298,28 +358,190 @@ __global__ void __launch_bounds__(kThreads) update_xr_kernel(int64_t N, double* 
         acc[1] = fma(rh[i], ri, acc[1]);
     }
     double tot[2];
-    if (reduce_last<2>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0) {
-        const double rn2 = tot[0], rho_new = tot[1];
-        st->rnorm2 = rn2;
-        st->rho_new = rho_new;
-        const int it = st->iter + 1;
-        st->iter = it;
-        int flag = kRunning;
-        if (rn2 <= st->tol2) flag = kConverged;
-        else if (!finite(rn2) || !finite(rho_new) || rho_new == 0.0 || st->omega == 0.0) flag = kBreakdown;
-        else if (it >= st->max_iter) flag = kMaxIter;
-        st->flag = flag;
+    if (reduce_last<2>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
+        finish_iteration(st, tot[0], tot[1]);
+}
+
+// ============================================================ double-float ==
+// sum_j a_ij (d_j - d_i) over one row with float a_ij; TPR lanes, df32
+// accumulation (result in every lane).
+template <int TPR>
+__device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                           const float* __restrict__ val, const float2* __restrict__ x,
+                                           int64_t row, int sub, bool valid, df xi) {
+    int64_t a = 0, e = 0;
+    if (valid) {
+        a = __ldg(row_ptr + row);
+        e = __ldg(row_ptr + row + 1);
+    }
+    DfAcc acc;
+#pragma unroll 4
+    for (int64_t k = a + sub; k < e; k += TPR) {
+        const float w = __ldg(val + k);
+        const df xj = df_ldg(x + __ldg(col + k));
+        const df dh = two_sum(xj.hi, -xi.hi);  // exact difference of the leading parts
+        const float dl = __fadd_rn(dh.lo, __fsub_rn(xj.lo, xi.lo));
+        df pr = two_prod(w, dh.hi);
+        pr.lo = __fmaf_rn(w, dl, pr.lo);
+        acc.add(pr);
+    }
+    df sum = acc.value();
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) sum = df_add(sum, df_shfl_xor(sum, o, TPR));
+    return sum;
+}
+
+// Outer residual into the inner system: r = D^-1 r64 (df32), correction 0.
+// Restart (MODE 0): rh = r, p = v = 0, scalars reset.  Reliable (MODE 1):
+// keep rh, p, v; rho_new = (rh, r).  The trigger reference is |r64|^2.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const double* __restrict__ r64,
+                                                           const float* __restrict__ dinv32, float2* __restrict__ r,
+                                                           float2* __restrict__ rh, float2* __restrict__ p,
+                                                           float2* __restrict__ v, float2* __restrict__ xd,
+                                                           double inner_tol, int max_iter, int track_max,
+                                                           KState* st, double* part) {
+    DfAcc a0;
+    RBFFD_ELEM_LOOP(N, i) {
+        const df ri = df_mul_f(df_from_double(r64[i]), dinv32[i]);
+        df_store(r + i, ri);
+        xd[i] = make_float2(0.f, 0.f);
+        if (MODE == 0) {
+            df_store(rh + i, ri);
+            p[i] = make_float2(0.f, 0.f);
+            v[i] = make_float2(0.f, 0.f);
+            a0.add(df_mul(ri, ri));
+        } else {
+            a0.add(df_mul(df_load(rh + i), ri));
+        }
+    }
+    double acc[1] = {df_to_double(a0.value())}, tot[1];
+    if (reduce_last<1>(acc, part, kSlotLoad, &st->counter[kSlotLoad], tot) && threadIdx.x == 0) {
+        if (MODE == 0) {
+            st->rho = 1.0;
+            st->alpha = 1.0;
+            st->omega = 1.0;
+        }
+        st->rho_new = tot[0];
+        st->iter = 0;
+        st->max_iter = max_iter;
+        st->tol2 = 0.0;           // inner passes end on the relative trigger
+        st->rnorm2 = st->tnorm2;  // |r64|^2 from the preceding check
+        st->rmax2 = st->tnorm2;
+        st->repl2 = inner_tol * inner_tol;
+        st->track_max = track_max;
+        st->flag = (!finite(tot[0]) || tot[0] == 0.0) ? kBreakdown : (max_iter <= 0 ? kMaxIter : kRunning);
     }
 }
 
-__global__ void axpy_kernel(int64_t N, double* __restrict__ x, const double* __restrict__ dx) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += dx[i];
+__global__ void __launch_bounds__(kThreads) update_p_df_kernel(int64_t N, const float2* __restrict__ r,
+                                                               const float2* __restrict__ v,
+                                                               float2* __restrict__ p, const KState* st) {
+    if (st->flag != kRunning) return;
+    const df beta = df_from_double((st->rho_new / st->rho) * (st->alpha / st->omega));
+    const df nomega = df_from_double(-st->omega);
+    RBFFD_ELEM_LOOP(N, i) {
+        const df t = df_fma(nomega, df_load(v + i), df_load(p + i));
+        df_store(p + i, df_fma(beta, t, df_load(r + i)));
+    }
+}
+
+// y = D^-1 A32 xin (difference form); MODE 0: (rh, y) -> alpha; MODE 1:
+// (y, xin), (y, y) -> omega.
+template <int TPR, int MODE>
+__global__ void __launch_bounds__(kThreads) spmv_df_kernel(const int64_t* __restrict__ row_ptr,
+                                                           const int* __restrict__ col,
+                                                           const float* __restrict__ val, int64_t N,
+                                                           const float2* __restrict__ xin,
+                                                           const float* __restrict__ sigma,
+                                                           const float* __restrict__ dinv,
+                                                           float2* __restrict__ y, const float2* __restrict__ rh,
+                                                           KState* st, double* part) {
+    if (st->flag != kRunning) return;
+    const int sub = threadIdx.x & (TPR - 1);
+    DfAcc a0, a1;
+    RBFFD_ROW_LOOP(TPR, N, i, valid, {
+        const df xi = valid ? df_ldg(xin + i) : df_make(0.f, 0.f);
+        df ax = row_apply_df<TPR>(row_ptr, col, val, xin, i, sub, valid, xi);
+        if (valid && sub == 0) {
+            ax = df_add(ax, df_mul_f(xi, sigma[i]));
+            const df yi = df_mul_f(ax, dinv[i]);
+            df_store(y + i, yi);
+            if (MODE == 0) {
+                a0.add(df_mul(df_load(rh + i), yi));
+            } else {
+                a0.add(df_mul(yi, xi));
+                a1.add(df_mul(yi, yi));
+            }
+        }
+    })
+    if (MODE == 0) {
+        double acc[1] = {df_to_double(a0.value())}, tot[1];
+        if (reduce_last<1>(acc, part, kSlotV, &st->counter[kSlotV], tot) && threadIdx.x == 0) {
+            const double rv = tot[0];
+            if (rv == 0.0 || !finite(rv)) {
+                st->flag = kBreakdown;
+            } else {
+                st->alpha = st->rho_new / rv;
+                st->rho = st->rho_new;
+            }
+        }
+    } else {
+        double acc[2] = {df_to_double(a0.value()), df_to_double(a1.value())}, tot[2];
+        if (reduce_last<2>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0) {
+            const double ts = tot[0], tt = tot[1];
+            if (!finite(ts) || !finite(tt)) st->flag = kBreakdown;
+            else st->omega = (tt > 0.0) ? ts / tt : 0.0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) update_s_df_kernel(int64_t N, const float2* __restrict__ r,
+                                                               const float2* __restrict__ v,
+                                                               float2* __restrict__ s, const KState* st) {
+    if (st->flag != kRunning) return;
+    const df nalpha = df_from_double(-st->alpha);
+    RBFFD_ELEM_LOOP(N, i) df_store(s + i, df_fma(nalpha, df_load(v + i), df_load(r + i)));
+}
+
+__global__ void __launch_bounds__(kThreads) update_xr_df_kernel(int64_t N, float2* __restrict__ x,
+                                                                const float2* __restrict__ p,
+                                                                const float2* __restrict__ s,
+                                                                const float2* __restrict__ t,
+                                                                float2* __restrict__ r,
+                                                                const float2* __restrict__ rh,
+                                                                const float* __restrict__ d, KState* st,
+                                                                double* part) {
+    if (st->flag != kRunning) return;
+    const df alpha = df_from_double(st->alpha), omega = df_from_double(st->omega);
+    const df nomega = df_from_double(-st->omega);
+    DfAcc a0, a1;
+    RBFFD_ELEM_LOOP(N, i) {
+        const df si = df_load(s + i);
+        df_store(x + i, df_fma(omega, si, df_fma(alpha, df_load(p + i), df_load(x + i))));
+        const df ri = df_fma(nomega, df_load(t + i), si);
+        df_store(r + i, ri);
+        const df ru = df_mul_f(ri, d[i]);
+        a0.add(df_mul(ru, ru));
+        a1.add(df_mul(df_load(rh + i), ri));
+    }
+    double acc[2] = {df_to_double(a0.value()), df_to_double(a1.value())}, tot[2];
+    if (reduce_last<2>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
+        finish_iteration(st, tot[0], tot[1]);
+}
+
+// x64 += correction (df32), correction = 0.
+__global__ void refine_kernel(int64_t N, double* __restrict__ x, float2* __restrict__ xd) {
+    RBFFD_ELEM_LOOP(N, i) {
+        const float2 c = xd[i];
+        x[i] += (double)c.x + (double)c.y;
+        xd[i] = make_float2(0.f, 0.f);
+    }
 }
 
 __global__ void adjoint_grad_kernel(int64_t N, const uint8_t* __restrict__ mask, const double* __restrict__ lam,
                                     double* __restrict__ dLdf, double* __restrict__ dLdg) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    RBFFD_ELEM_LOOP(N, i) {
         const bool dir = mask[i] != 0;
         const double l = lam[i];
         if (dLdf) dLdf[i] = dir ? 0.0 : -l;
@@ -328,101 +550,189 @@ __global__ void adjoint_grad_kernel(int64_t N, const uint8_t* __restrict__ mask,
 }
 
 // ---------------------------------------------------------------- host -----
-Work carve(void* ws, int64_t N, bool mixed) {
-    Carver c(ws);
-    Work w;
-    w.st = c.take<KState>(1);
-    w.part = c.take<double>((size_t)kSlots * kQ * kMaxBlocks);
-    w.r = c.take<double>(N);
-    w.rh = c.take<double>(N);
-    w.p = c.take<double>(N);
-    w.v = c.take<double>(N);
-    w.s = c.take<double>(N);
-    w.t = c.take<double>(N);
-    w.d = c.take<double>(N);
-    w.dinv = c.take<double>(N);
-    w.r_outer = mixed ? c.take<double>(N) : nullptr;
-    w.dx = mixed ? c.take<double>(N) : nullptr;
-    return w;
-}
+struct Work {
+    KState* st;
+    double* part;
+    double *d, *dinv;
+    // FP64 engine
+    double *r, *rh, *p, *v, *s, *t;
+    // mixed engine
+    double* r64;
+    float *d32, *dinv32, *sigma32;
+    float2 *xd, *rd, *rhd, *pd, *vd, *sd, *td;
+};
 
-size_t work_bytes(int64_t N, bool mixed) {
-    Carver c(nullptr);
-    c.take<KState>(1);
-    c.take<double>((size_t)kSlots * kQ * kMaxBlocks);
-    for (int k = 0; k < 8; ++k) c.take<double>(N);
-    if (mixed) {
-        c.take<double>(N);
-        c.take<double>(N);
+// Carves the workspace (ws may be null to size it); returns the bytes used.
+size_t layout(void* ws, int64_t N, bool mixed, Work* w) {
+    Carver c(ws);
+    Work t{};
+    t.st = c.take<KState>(1);
+    t.part = c.take<double>((size_t)kSlots * kQ * kMaxBlocks);
+    t.d = c.take<double>(N);
+    t.dinv = c.take<double>(N);
+    if (!mixed) {
+        t.r = c.take<double>(N);
+        t.rh = c.take<double>(N);
+        t.p = c.take<double>(N);
+        t.v = c.take<double>(N);
+        t.s = c.take<double>(N);
+        t.t = c.take<double>(N);
+    } else {
+        t.r64 = c.take<double>(N);
+        t.d32 = c.take<float>(N);
+        t.dinv32 = c.take<float>(N);
+        t.sigma32 = c.take<float>(N);
+        t.xd = c.take<float2>(N);
+        t.rd = c.take<float2>(N);
+        t.rhd = c.take<float2>(N);
+        t.pd = c.take<float2>(N);
+        t.vd = c.take<float2>(N);
+        t.sd = c.take<float2>(N);
+        t.td = c.take<float2>(N);
     }
+    if (w) *w = t;
     return c.off;
 }
 
-int tpr_for(int64_t N, int64_t nnz) {
-    const double L = (double)nnz / (double)std::max<int64_t>(N, 1);
-    if (L <= 8) return 2;
-    if (L <= 24) return 4;
-    if (L <= 48) return 8;
-    if (L <= 96) return 16;
-    return 32;
+int env_int(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    return std::atoi(v);
 }
 
-int nblocks() { return std::min(kMaxBlocks, sm_count() * 8); }
+// Lanes per row: the FP64 SpMV keeps few lanes per row (each reduction step
+// costs FP64 adds); the df32 SpMV spends FP32 only and takes 8 lanes (one
+// 32-byte sector of float values per step).  RBFFD_TPR64 / RBFFD_TPR32
+// override for tuning sweeps.
+int tpr64_for(int64_t N, int64_t nnz) {
+    const int o = env_int("RBFFD_TPR64", 0);
+    if (o == 1 || o == 2 || o == 4 || o == 8) return o;
+    const double L = (double)nnz / (double)std::max<int64_t>(N, 1);
+    if (L >= 24) return 4;
+    if (L >= 8) return 2;
+    return 1;
+}
 
-template <class VT, int TPR>
-struct Ops {
-    static void residual(const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r, int scale,
-                         int init, double tol, int max_iter, cudaStream_t st) {
-        residual_kernel<VT, TPR><<<nblocks(), kThreads, 0, st>>>(A.row_ptr, A.col, static_cast<const VT*>(A.val),
-                                                                 A.n_rows, b, x, w.dinv, r, scale, init, w.rh, w.p,
-                                                                 w.v, tol, max_iter, w.st, w.part);
+int tpr32_for(int64_t N, int64_t nnz) {
+    const int o = env_int("RBFFD_TPR32", 0);
+    if (o == 2 || o == 4 || o == 8 || o == 16) return o;
+    const double L = (double)nnz / (double)std::max<int64_t>(N, 1);
+    if (L >= 24) return 8;
+    if (L >= 12) return 4;
+    return 2;
+}
+
+// Grid of a persistent-style launch: every block resident at once (blocks
+// per SM from the occupancy calculator, cached per kernel), capped at the
+// partial-sum capacity.  Reductions finish in the last block of the grid, so
+// each launch may use its own grid size.
+template <class K>
+int grid_of(K kernel) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    const void* key = reinterpret_cast<const void*>(kernel);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 4;
+    const int g = std::min(kMaxBlocks, per_sm * sm_count());
+    cache[key] = g;
+    return g;
+}
+
+int nblocks() { return std::min(kMaxBlocks, sm_count() * 4); }
+
+int64_t spmv_bytes(const rbffd_csr& A, int val_bytes) {
+    return A.nnz * (int64_t)(val_bytes + 4) + 8 * (A.n_rows + 1) + 4 * 8 * A.n_rows;
+}
+
+template <int TPR>
+struct Ops64 {
+    static void resid(int mode, const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r,
+                      double tol, int max_iter, double repl, cudaStream_t st) {
+        const double* val = static_cast<const double*>(A.val);
+        if (mode == kInit)
+            resid64_kernel<TPR, kInit><<<grid_of(resid64_kernel<TPR, kInit>), kThreads, 0, st>>>(
+                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
+        else if (mode == kReplaceR)
+            resid64_kernel<TPR, kReplaceR><<<grid_of(resid64_kernel<TPR, kReplaceR>), kThreads, 0, st>>>(
+                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
+        else
+            resid64_kernel<TPR, kCheck><<<grid_of(resid64_kernel<TPR, kCheck>), kThreads, 0, st>>>(
+                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
         note_launches(1);
-    }
-    // Algorithmic bytes of one SpMV launch (see rbffd_profile in rbffd.h).
-    static int64_t spmv_bytes(const rbffd_csr& A) {
-        return A.nnz * (int64_t)(sizeof(VT) + 4) + 8 * (A.n_rows + 1) + 4 * 8 * A.n_rows;
     }
     static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
         const int64_t N = A.n_rows;
-        const int nb = nblocks();
-        const VT* val = static_cast<const VT*>(A.val);
-        const int kind = sizeof(VT) == 8 ? kProfSpmv64 : kProfSpmv32;
-        const int64_t bytes = spmv_bytes(A);
-        update_p_kernel<<<nb, kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
+        const double* val = static_cast<const double*>(A.val);
+        const int64_t bytes = spmv_bytes(A, 8);
+        update_p64_kernel<<<grid_of(update_p64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
         int ev = prof_begin(st);
-        spmv_kernel<VT, TPR, 0><<<nb, kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.p, w.dinv, w.v, w.rh, w.st,
-                                                         w.part);
-        prof_end(ev, st, kind, bytes);
-        update_s_kernel<<<nb, kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
+        spmv64_kernel<TPR, 0><<<grid_of(spmv64_kernel<TPR, 0>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.p,
+                                                                                   w.dinv, w.v, w.rh, w.st, w.part);
+        prof_end(ev, st, kProfSpmv64, bytes);
+        update_s64_kernel<<<grid_of(update_s64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
         ev = prof_begin(st);
-        spmv_kernel<VT, TPR, 1><<<nb, kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.s, w.dinv, w.t, nullptr,
-                                                         w.st, w.part);
-        prof_end(ev, st, kind, bytes);
-        update_xr_kernel<<<nb, kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d, w.st, w.part);
+        spmv64_kernel<TPR, 1><<<grid_of(spmv64_kernel<TPR, 1>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.s,
+                                                                                   w.dinv, w.t, nullptr, w.st, w.part);
+        prof_end(ev, st, kProfSpmv64, bytes);
+        update_xr64_kernel<<<grid_of(update_xr64_kernel), kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d,
+                                                                             w.st, w.part);
         note_launches(5);
     }
 };
 
-template <class VT>
-void residual_dispatch(int tpr, const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r,
-                       int scale, int init, double tol, int max_iter, cudaStream_t st) {
+template <int TPR>
+struct OpsDf {
+    static void iteration(const rbffd_csr& A32, const Work& w, cudaStream_t st) {
+        const int64_t N = A32.n_rows;
+        const float* val = static_cast<const float*>(A32.val);
+        // algorithmic bytes: as the FP64 SpMV with 4-byte values, 8-byte
+        // df32 vectors, and 4-byte sigma and Jacobi scale instead of 8
+        const int64_t bytes = spmv_bytes(A32, 4);
+        update_p_df_kernel<<<grid_of(update_p_df_kernel), kThreads, 0, st>>>(N, w.rd, w.vd, w.pd, w.st);
+        int ev = prof_begin(st);
+        spmv_df_kernel<TPR, 0><<<grid_of(spmv_df_kernel<TPR, 0>), kThreads, 0, st>>>(
+            A32.row_ptr, A32.col, val, N, w.pd, w.sigma32, w.dinv32, w.vd, w.rhd, w.st, w.part);
+        prof_end(ev, st, kProfSpmv32, bytes);
+        update_s_df_kernel<<<grid_of(update_s_df_kernel), kThreads, 0, st>>>(N, w.rd, w.vd, w.sd, w.st);
+        ev = prof_begin(st);
+        spmv_df_kernel<TPR, 1><<<grid_of(spmv_df_kernel<TPR, 1>), kThreads, 0, st>>>(
+            A32.row_ptr, A32.col, val, N, w.sd, w.sigma32, w.dinv32, w.td, nullptr, w.st, w.part);
+        prof_end(ev, st, kProfSpmv32, bytes);
+        update_xr_df_kernel<<<grid_of(update_xr_df_kernel), kThreads, 0, st>>>(N, w.xd, w.pd, w.sd, w.td, w.rd,
+                                                                               w.rhd, w.d32, w.st, w.part);
+        note_launches(5);
+    }
+};
+
+void resid64(int tpr, int mode, const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r,
+             double tol, int max_iter, double repl, cudaStream_t st) {
     switch (tpr) {
-        case 2: Ops<VT, 2>::residual(A, b, x, w, r, scale, init, tol, max_iter, st); break;
-        case 4: Ops<VT, 4>::residual(A, b, x, w, r, scale, init, tol, max_iter, st); break;
-        case 8: Ops<VT, 8>::residual(A, b, x, w, r, scale, init, tol, max_iter, st); break;
-        case 16: Ops<VT, 16>::residual(A, b, x, w, r, scale, init, tol, max_iter, st); break;
-        default: Ops<VT, 32>::residual(A, b, x, w, r, scale, init, tol, max_iter, st); break;
+        case 1: Ops64<1>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
+        case 2: Ops64<2>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
+        case 8: Ops64<8>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
+        default: Ops64<4>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
     }
 }
 
-template <class VT>
-void iteration_dispatch(int tpr, const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
+void iter64(int tpr, const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
     switch (tpr) {
-        case 2: Ops<VT, 2>::iteration(A, x, w, st); break;
-        case 4: Ops<VT, 4>::iteration(A, x, w, st); break;
-        case 8: Ops<VT, 8>::iteration(A, x, w, st); break;
-        case 16: Ops<VT, 16>::iteration(A, x, w, st); break;
-        default: Ops<VT, 32>::iteration(A, x, w, st); break;
+        case 1: Ops64<1>::iteration(A, x, w, st); break;
+        case 2: Ops64<2>::iteration(A, x, w, st); break;
+        case 8: Ops64<8>::iteration(A, x, w, st); break;
+        default: Ops64<4>::iteration(A, x, w, st); break;
+    }
+}
+
+void iter_df(int tpr, const rbffd_csr& A32, const Work& w, cudaStream_t st) {
+    switch (tpr) {
+        case 2: OpsDf<2>::iteration(A32, w, st); break;
+        case 4: OpsDf<4>::iteration(A32, w, st); break;
+        case 16: OpsDf<16>::iteration(A32, w, st); break;
+        default: OpsDf<8>::iteration(A32, w, st); break;
     }
 }
 
@@ -433,30 +743,164 @@ int read_state(const Work& w, KState* hs, cudaStream_t st) {
     return RBFFD_OK;
 }
 
-// One BiCGSTAB run on A (values VT) for A x = b from the given x, to
-// |b - A x| <= tol |b| by the recurrence residual.  Returns the final flag.
-template <class VT>
-int bicgstab_run(const rbffd_csr& A, const double* b, double* x, double tol, int max_iter, const Work& w,
-                 cudaStream_t st, KState* hs) {
-    const int tpr = tpr_for(A.n_rows, A.nnz);
-    residual_dispatch<VT>(tpr, A, b, x, w, w.r, 1, 1, tol, max_iter, st);
-    RBFFD_LAUNCH_CHECK();
-    int chunk = 4;
-    int rc = read_state(w, hs, st);
-    if (rc != RBFFD_OK) return -rc;
+bool csr_ok(const rbffd_csr* A, int dtype) {
+    return A && A->row_ptr && A->col && A->val && A->dtype == dtype && A->n_rows > 0 &&
+           A->n_rows <= 0x7fffffffLL && A->nnz >= 0;
+}
+
+double rel_of(const KState& s) {
+    if (s.bnorm2 > 0.0) return std::sqrt(s.tnorm2 / s.bnorm2);
+    return std::sqrt(s.tnorm2);
+}
+
+constexpr double kReplaceFactor = 1e-3;  // FP64 residual replacement after a 1e3 drop
+
+// Runs chunks of iterations until the state leaves kRunning; returns the
+// flag, or minus a status on a CUDA error.
+template <class IterFn>
+int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn iter) {
     while (hs->flag == kRunning) {
-        for (int c = 0; c < chunk; ++c) iteration_dispatch<VT>(tpr, A, x, w, st);
+        for (int c = 0; c < chunk; ++c) iter();
         RBFFD_LAUNCH_CHECK();
-        rc = read_state(w, hs, st);
+        const int rc = read_state(w, hs, st);
         if (rc != RBFFD_OK) return -rc;
         chunk = std::min(chunk * 2, 64);
     }
     return hs->flag;
 }
 
-bool csr_ok(const rbffd_csr* A, int dtype) {
-    return A && A->row_ptr && A->col && A->val && A->dtype == dtype && A->n_rows > 0 &&
-           A->n_rows <= 0x7fffffffLL && A->nnz >= 0;
+int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve_opts& o, const Work& w,
+               cudaStream_t st, rbffd_solve_info* info) {
+    const int tpr = tpr64_for(A.n_rows, A.nnz);
+    KState hs;
+    int rc;
+    int total = 0, replacements = 0, breakdowns = 0, chunk = 4;
+    resid64(tpr, kInit, A, b, x, w, w.r, o.tol, o.max_iter, kReplaceFactor, st);
+    RBFFD_LAUNCH_CHECK();
+    if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+    int status = RBFFD_ERR_NOT_CONVERGED;
+    while (true) {
+        if (hs.flag == kRunning) {
+            const int f = run_chunks(w, &hs, st, chunk, [&] { iter64(tpr, A, x, w, st); });
+            if (f < 0) return -f;
+        }
+        if (hs.flag == kConverged || hs.flag == kReplace) {
+            // recompute r from b - A x (keeps p, rh); confirms convergence
+            resid64(tpr, kReplaceR, A, b, x, w, w.r, o.tol, o.max_iter, kReplaceFactor, st);
+            RBFFD_LAUNCH_CHECK();
+            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+            ++replacements;
+            if (hs.flag == kConverged) {
+                status = RBFFD_OK;
+                break;
+            }
+            continue;
+        }
+        if (hs.flag == kBreakdown) {
+            total += hs.iter;
+            if (++breakdowns >= 2) {
+                status = RBFFD_ERR_BREAKDOWN;
+                hs.iter = 0;
+                break;
+            }
+            resid64(tpr, kInit, A, b, x, w, w.r, o.tol, std::max(o.max_iter - total, 0), kReplaceFactor, st);
+            RBFFD_LAUNCH_CHECK();
+            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+            continue;
+        }
+        status = RBFFD_ERR_NOT_CONVERGED;  // kMaxIter
+        break;
+    }
+    total += hs.iter;
+    // explicit residual of the returned x
+    resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, kReplaceFactor, st);
+    RBFFD_LAUNCH_CHECK();
+    if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+    const bool zero = hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0;
+    const double rel = zero ? 0.0 : rel_of(hs);
+    if (zero) status = RBFFD_OK;
+    if (status == RBFFD_OK && !(rel <= o.tol)) status = RBFFD_ERR_NOT_CONVERGED;
+    info->status = status;
+    info->iters = total;
+    info->outer_sweeps = replacements;
+    info->restarts = breakdowns;
+    info->rel_residual = rel;
+    return status;
+}
+
+int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, double* x, const rbffd_solve_opts& o,
+                const Work& w, cudaStream_t st, rbffd_solve_info* info) {
+    const int64_t N = A.n_rows;
+    const int tpr64 = tpr64_for(N, A.nnz);
+    const int tpr32 = tpr32_for(N, A.nnz);
+    const int nb = nblocks();
+    const bool reliable = o.refine == 1;
+    KState hs;
+    int rc;
+    int total = 0, outer = 0, breakdowns = 0, chunk = 4;
+    int status = RBFFD_ERR_NOT_CONVERGED;
+    bool restart = true;
+    double rel = INFINITY;
+    while (true) {
+        resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
+        RBFFD_LAUNCH_CHECK();
+        if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
+            rel = 0.0;
+            status = RBFFD_OK;
+            break;
+        }
+        rel = rel_of(hs);
+        if (rel <= o.tol) {
+            status = RBFFD_OK;
+            break;
+        }
+        if (!std::isfinite(rel)) {
+            status = RBFFD_ERR_BREAKDOWN;
+            break;
+        }
+        if (total >= o.max_iter || outer >= o.max_outer) break;
+        ++outer;
+        // relative target of this pass: inner_tol, but no deeper than the
+        // outer tolerance needs
+        const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);
+        if (restart || !reliable)
+            load_df_kernel<0><<<grid_of(load_df_kernel<0>), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd, w.xd, inner,
+                                                       o.max_iter - total, reliable ? 1 : 0, w.st, w.part);
+        else
+            load_df_kernel<1><<<grid_of(load_df_kernel<1>), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd, w.xd, inner,
+                                                       o.max_iter - total, 1, w.st, w.part);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        restart = false;
+        const int f = run_chunks(w, &hs, st, chunk, [&] { iter_df(tpr32, A32, w, st); });
+        if (f < 0) return -f;
+        total += hs.iter;
+        refine_kernel<<<nb, kThreads, 0, st>>>(N, x, w.xd);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        if (hs.flag == kBreakdown) {
+            if (++breakdowns >= 3) {
+                status = RBFFD_ERR_BREAKDOWN;
+                break;
+            }
+            restart = true;
+        } else if (hs.flag == kMaxIter) {
+            resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
+            RBFFD_LAUNCH_CHECK();
+            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+            rel = rel_of(hs);
+            status = rel <= o.tol ? RBFFD_OK : RBFFD_ERR_NOT_CONVERGED;
+            break;
+        }
+    }
+    info->status = status;
+    info->iters = total;
+    info->outer_sweeps = outer;
+    info->restarts = breakdowns;
+    info->rel_residual = rel;
+    return status;
 }
 
 int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x, const rbffd_solve_opts* o,
@@ -467,78 +911,26 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     if (mixed && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz ||
                   A32->row_ptr != A->row_ptr || A32->col != A->col))
         return RBFFD_ERR_INVALID_ARG;  // the float32 copy shares A's (validated) pattern
-    if (!(o->tol > 0.0) || o->max_iter < 0) return RBFFD_ERR_INVALID_ARG;
+    if (!(o->tol > 0.0) || o->max_iter < 0 || (o->refine != 0 && o->refine != 1)) return RBFFD_ERR_INVALID_ARG;
     if (mixed && (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1)) return RBFFD_ERR_INVALID_ARG;
     const int64_t N = A->n_rows;
-    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < work_bytes(N, mixed)) return RBFFD_ERR_WORKSPACE;
-    Work w = carve(ws, N, mixed);
+    Work w{};
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, N, mixed, nullptr))
+        return RBFFD_ERR_WORKSPACE;
+    layout(ws, N, mixed, &w);
     std::memset(info, 0, sizeof(*info));
 
     KState hs;
     RBFFD_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(KState), st));
-    diag_kernel<<<std::min<int64_t>((N + kThreads - 1) / kThreads, sm_count() * 8), kThreads, 0, st>>>(
-        A->row_ptr, A->col, static_cast<const double*>(A->val), N, A->nnz, o->jacobi ? 1 : 0, w.d, w.dinv, w.st);
+    setup_kernel<<<(int)std::min<int64_t>((N + kThreads - 1) / kThreads, sm_count() * 8), kThreads, 0, st>>>(
+        A->row_ptr, A->col, static_cast<const double*>(A->val), N, A->nnz, o->jacobi ? 1 : 0, w.d, w.dinv, w.d32,
+        w.dinv32, w.sigma32, w.st);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
     int rc = read_state(w, &hs, st);
     if (rc != RBFFD_OK) return rc;
     if (hs.bad) return RBFFD_ERR_INVALID_ARG;
-
-    const int tpr = tpr_for(N, A->nnz);
-    int total_iters = 0, restarts = 0, breakdowns = 0, outer = 0;
-    const int max_outer = mixed ? o->max_outer : std::max(4, o->max_outer);
-    int status = RBFFD_ERR_NOT_CONVERGED;
-    double last_rel = INFINITY;
-    while (true) {
-        // explicit FP64 residual of the current x
-        residual_dispatch<double>(tpr, *A, b, x, w, mixed ? w.r_outer : w.r, 0, 1, o->tol, 1, st);
-        RBFFD_LAUNCH_CHECK();
-        rc = read_state(w, &hs, st);
-        if (rc != RBFFD_OK) return rc;
-        const double rel = hs.bnorm2 > 0.0 ? std::sqrt(hs.tnorm2 / hs.bnorm2) : std::sqrt(hs.tnorm2);
-        last_rel = rel;
-        if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) { status = RBFFD_OK; last_rel = 0.0; break; }
-        if (rel <= o->tol) { status = RBFFD_OK; break; }
-        if (!std::isfinite(rel)) { status = RBFFD_ERR_BREAKDOWN; break; }
-        if (total_iters >= o->max_iter || outer >= max_outer) { status = RBFFD_ERR_NOT_CONVERGED; break; }
-        ++outer;
-        int flag;
-        const int budget = o->max_iter - total_iters;
-        if (!mixed) {
-            flag = bicgstab_run<double>(*A, b, x, o->tol, budget, w, st, &hs);
-        } else {
-            RBFFD_CUDA_TRY(cudaMemsetAsync(w.dx, 0, sizeof(double) * N, st));
-            flag = bicgstab_run<float>(*A32, w.r_outer, w.dx, o->inner_tol, budget, w, st, &hs);
-            if (flag >= 0) {
-                axpy_kernel<<<nblocks(), kThreads, 0, st>>>(N, x, w.dx);
-                note_launches(1);
-                RBFFD_LAUNCH_CHECK();
-            }
-        }
-        if (flag < 0) return -flag;
-        total_iters += hs.iter;
-        if (flag == kBreakdown) {
-            if (++breakdowns >= 2) {
-                // measure where we are before reporting
-                residual_dispatch<double>(tpr, *A, b, x, w, w.r, 0, 1, o->tol, 1, st);
-                rc = read_state(w, &hs, st);
-                if (rc != RBFFD_OK) return rc;
-                last_rel = hs.bnorm2 > 0.0 ? std::sqrt(hs.tnorm2 / hs.bnorm2) : std::sqrt(hs.tnorm2);
-                status = last_rel <= o->tol ? RBFFD_OK : RBFFD_ERR_BREAKDOWN;
-                break;
-            }
-            ++restarts;
-        } else {
-            breakdowns = 0;
-            if (!mixed && flag == kConverged && outer > 1) ++restarts;
-        }
-    }
-    info->status = status;
-    info->iters = total_iters;
-    info->outer_sweeps = outer;
-    info->restarts = restarts;
-    info->rel_residual = last_rel;
-    return status;
+    return mixed ? solve_mixed(*A, *A32, b, x, *o, w, st, info) : solve_fp64(*A, b, x, *o, w, st, info);
 }
 
 }  // namespace
@@ -547,7 +939,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
 extern "C" size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* opts) {
     if (N <= 0) return 0;
     const bool mixed = opts && opts->precision == 1;
-    return rbffd::work_bytes(N, mixed);
+    return rbffd::layout(nullptr, N, mixed, nullptr);
 }
 
 extern "C" int rbffd_solve(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x,
@@ -567,8 +959,8 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
     if (rc != RBFFD_OK) return rc;
     if (dLdf || dLdg) {
         const int64_t N = AT->n_rows;
-        adjoint_grad_kernel<<<std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, st>>>(N, is_dirichlet,
-                                                                                               lambda, dLdf, dLdg);
+        adjoint_grad_kernel<<<(int)std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, st>>>(
+            N, is_dirichlet, lambda, dLdf, dLdg);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
     }

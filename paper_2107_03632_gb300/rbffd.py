@@ -60,6 +60,7 @@ class SolveOpts(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
         ("jacobi", ctypes.c_int32),
+        ("refine", ctypes.c_int32),
     ]
 
 
@@ -309,9 +310,11 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
 
 
 # -------------------------------------------------------------------- solve --
-def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=1e-5, max_outer=60, jacobi=True):
+def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=1e-5, max_outer=60, jacobi=True,
+              refine="restart"):
     prec = {"fp64": 0, "mixed": 1}[precision]
-    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0)
+    ref = {"restart": 0, "reliable": 1}[refine]
+    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0, ref)
 
 
 def stencils_workspace(N: int, n: int, device) -> torch.Tensor:

@@ -180,14 +180,14 @@ def _system(h, m, n):
     return d, (idx, w, rp, col, val, b, f, g, u)
 
 
-@pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.06, 4, 30), (0.1, 6, 56)])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_solve_vs_oracle(lib, h, m, n, precision):
+@pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.06, 4, 30), (0.1, 6, 56), (0.03, 4, 30)])
+@pytest.mark.parametrize("precision,refine", [("fp64", "restart"), ("mixed", "restart"), ("mixed", "reliable")])
+def test_solve_vs_oracle(lib, h, m, n, precision, refine):
     from paper_2107_03632_gb300 import rbffd
 
     d, (idx, w, rp, col, val, b, f, g, u) = _system(h, m, n)
     A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=(precision == "mixed"))
-    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(tol=1e-10, precision=precision))
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(tol=1e-10, precision=precision, refine=refine))
     x = x.cpu().numpy()
     ref = oracle.solve_direct(rp, col, val, b)
     assert info["status"] == 0 and info["rel_residual"] <= 1e-10
@@ -209,13 +209,44 @@ def test_solve_warm_start_and_zero_rhs(lib):
     assert info["status"] == 0 and float(z.abs().max()) == 0.0
 
 
-def test_solve_not_converged_reports(lib):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_not_converged_reports(lib, precision):
     from paper_2107_03632_gb300 import rbffd
 
     d, (idx, w, rp, col, val, b, f, g, u) = _system(0.04, 2, 12)
-    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
-    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(max_iter=5), raise_on_error=False)
-    assert info["status_code"] == 4 and info["iters"] <= 5 + 64
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=True)
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(max_iter=5, precision=precision),
+                                raise_on_error=False)
+    assert info["status_code"] == 4 and info["iters"] <= 5
+    assert info["rel_residual"] > 1e-10
+
+
+def test_solve_deterministic(lib):
+    """Fixed grids and block-ordered reductions: identical bits run to run."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.04, 4, 30)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=True)
+    for prec in ("fp64", "mixed"):
+        x1, i1 = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(precision=prec))
+        x2, i2 = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(precision=prec))
+        assert torch.equal(x1, x2) and i1["iters"] == i2["iters"]
+
+
+def test_profile_counts_launches_and_spmv_time(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, (idx, w, rp, col, val, b, f, g, u) = _system(0.05, 2, 12)
+    A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=True)
+    rbffd.rbffd_profile_read(reset=True)
+    rbffd.rbffd_profile_enable(True)
+    _, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(precision="fp64"))
+    prof = rbffd.rbffd_profile_read(reset=True)
+    rbffd.rbffd_profile_enable(False)
+    assert prof["spmv64_launches"] >= 2 * info["iters"] > 0
+    assert prof["spmv64_ms"] > 0 and prof["launches"] >= 5 * info["iters"]
+    N, nnz = d.N, len(col)
+    assert prof["spmv64_bytes"] == prof["spmv64_launches"] * (nnz * 12 + 8 * (N + 1) + 32 * N)
 
 
 def test_solve_rejects_bad_column_index(lib):
