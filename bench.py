@@ -244,7 +244,7 @@ def run_gpu(args):
                         torch.empty(nnz, dtype=torch.float64, device=dev),
                         torch.empty(nnz, dtype=torch.float32, device=dev))
     opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol),
-            "fp64": rbffd.make_opts(tol=1e-10, precision="fp64")}
+            "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.inner_tol64)}
     ws_solve = rbffd.solve_workspace(N, opts["mixed"], dev)
 
     def step(precision, ev=None):
@@ -314,9 +314,11 @@ def run_gpu(args):
     value = ws * N * args.steps / (ms * 1e-3)
 
     # ---- the same steps with the plain FP64 solve ----
-    step("fp64")
-    ms64, wall64, st64, infos64, prof64 = timed_loop("fp64", args.steps, profile=True)
-    ms64 = max_over_ranks(ms64)
+    k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
+    if k64 > 0:
+        step("fp64")
+        ms64, wall64, st64, infos64, prof64 = timed_loop("fp64", k64, profile=True)
+        ms64 = max_over_ranks(ms64)
 
     # ---- end to end through the API from pinned host buffers ----
     h2d = (h_xy.numel() * 8 + h_mask.numel() + h_f.numel() * 8 + h_g.numel() * 8)
@@ -325,7 +327,7 @@ def run_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.e2e_steps):
+    for _ in range(max(args.e2e_steps, 1)):
         xy.copy_(h_xy, non_blocking=True)
         mask.copy_(h_mask, non_blocking=True)
         fT.copy_(h_f, non_blocking=True)
@@ -335,7 +337,7 @@ def run_gpu(args):
     e1.record()
     barrier()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-    e2e_value = ws * N * args.e2e_steps / (ms_e2e * 1e-3)
+    e2e_value = ws * N * max(args.e2e_steps, 1) / (ms_e2e * 1e-3)
 
     # ---- correctness of the timed solves (host check, outside timing) ----
     err_exact = float(np.abs(h_u.numpy() - u_ex).max())
@@ -346,9 +348,19 @@ def run_gpu(args):
     sp_ms = prof["spmv32_ms"] / max(prof["spmv32_launches"], 1)
     sp_bytes = prof["spmv32_bytes"] / max(prof["spmv32_launches"], 1)
     sp_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9 if prof["spmv32_launches"] else 0.0
-    sp64_ms = prof64["spmv64_ms"] / max(prof64["spmv64_launches"], 1)
-    sp64_bytes = prof64["spmv64_bytes"] / max(prof64["spmv64_launches"], 1)
-    sp64_gbs = sp64_bytes / (sp64_ms * 1e-3) / 1e9 if prof64["spmv64_launches"] else 0.0
+    fp64_line = None
+    if k64 > 0:
+        sp64_ms = prof64["spmv64_ms"] / max(prof64["spmv64_launches"], 1)
+        sp64_bytes = prof64["spmv64_bytes"] / max(prof64["spmv64_launches"], 1)
+        sp64_gbs = sp64_bytes / (sp64_ms * 1e-3) / 1e9 if prof64["spmv64_launches"] else 0.0
+        fp64_line = {"value": ws * N * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                     "inner_tol": args.inner_tol64,
+                     "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2],
+                                   "solve": st64[3]},
+                     "iters": [i["iters"] for i in infos64], "passes": [i["outer_sweeps"] for i in infos64],
+                     "rel_residual": [i["rel_residual"] for i in infos64],
+                     "spmv_kernel": "spmv64_kernel", "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm,
+                     "spmv_ms_per_launch": sp64_ms}
 
     fp64_peak = fp64_peak_tflops(torch, dev)
     w_flops = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M + 15.0 * n * (n - 1) / 2.0)
@@ -372,13 +384,11 @@ def run_gpu(args):
                    "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
         "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "solve": st_ms[3]},
-        "solve": {"iters": iters, "outer_sweeps": [i["outer_sweeps"] for i in infos],
+        "solve": {"iters": iters, "refinements": [i["outer_sweeps"] for i in infos],
                   "rel_residual": [i["rel_residual"] for i in infos], "max_err_vs_exact": err_exact},
-        "fp64": {"value": ws * N * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
-                 "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2], "solve": st64[3]},
-                 "iters": [i["iters"] for i in infos64], "rel_residual": [i["rel_residual"] for i in infos64],
-                 "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm},
-        "roofline": {"kernel": "spmv_kernel<float> (inner BiCGSTAB SpMV)", "bound": "hbm", "achieved": sp_gbs,
+        "fp64": fp64_line,
+        "roofline": {"kernel": "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)", "bound": "hbm",
+                     "achieved": sp_gbs,
                      "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm, "traffic": None,
                      "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
                      "launches": prof["spmv32_launches"]},
@@ -386,7 +396,7 @@ def run_gpu(args):
                              "frac": w_tflops / fp64_peak, "peak_kind": "measured cuBLAS DGEMM 4096^3",
                              "flops_per_node": w_flops / N},
         "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": args.e2e_steps},
+                "steps": max(args.e2e_steps, 1)},
         "gpu_launches": prof["launches"],
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -407,8 +417,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS))
-    ap.add_argument("--inner-tol", type=float, default=1e-5)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
+    ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -152,6 +152,9 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
 /* BiCGSTAB (van der Vorst 1992) with left Jacobi scaling D^-1 A x = D^-1 b. */
 /* Convergence is judged on the unscaled system: |b - A x|_2 <= tol |b|_2,   */
 /* confirmed by an explicitly recomputed residual before returning OK.       */
+/* BiCGSTAB runs in restarted passes: each pass starts from the explicit    */
+/* residual (shadow residual = residual) and ends when its residual has     */
+/* fallen by inner_tol; at most max_outer passes.                            */
 /*                                                                           */
 /* precision 0 (FP64): matrix, vectors and scalars in float64.               */
 /* precision 1 (mixed): an FP64 refinement loop (r = b - A x with the FP64   */
@@ -160,8 +163,6 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
 /*   as A, float32 values) in difference form sum_j a_ij (d_j - d_i) +       */
 /*   (sum_j a_ij) d_i, with double-float (2 x float32) Krylov vectors; an   */
 /*   inner pass ends when its residual has fallen by inner_tol.             */
-/* FP64 mode recomputes the residual from b - A x whenever the recurrence    */
-/* residual has dropped 1e3 below its running maximum (residual replacement).*/
 /*                                                                           */
 /* x is in/out: the initial guess on entry, the solution on exit (warm       */
 /* start).  The call BLOCKS the host until the solve ends and synchronises   */
@@ -173,12 +174,9 @@ typedef struct rbffd_solve_opts {
     double tol;          /* relative residual target, e.g. 1e-10 */
     int32_t max_iter;    /* cap on (inner) BiCGSTAB iterations in total */
     int32_t precision;   /* 0 = FP64, 1 = mixed FP32-inner / FP64 refinement */
-    double inner_tol;    /* mixed: residual reduction per refinement pass, e.g. 1e-5 */
-    int32_t max_outer;   /* mixed: cap on refinement passes */
+    double inner_tol;    /* residual reduction per restarted pass, 0 < inner_tol < 1 */
+    int32_t max_outer;   /* cap on passes (refinement steps in mixed mode) */
     int32_t jacobi;      /* 1 = left Jacobi scaling (default), 0 = none */
-    int32_t refine;      /* mixed: 0 = restart the inner Krylov space at each
-                            refinement, 1 = keep the search direction across
-                            refinements (reliable updates) */
 } rbffd_solve_opts;
 
 typedef struct rbffd_solve_info {

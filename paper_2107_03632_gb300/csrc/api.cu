@@ -79,6 +79,23 @@ void prof_end(int slot, cudaStream_t st, int kind, int64_t bytes) {
     if (cudaEventRecord(p.b, st) != cudaSuccess) p.pending = false;
 }
 
+void prof_commit(const int* slots, int count, int keep) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int k = 0; k < count; ++k) {
+        const int sl = slots[k];
+        if (sl < 0 || sl >= (int)g_pairs.size()) continue;
+        ProfPair& p = g_pairs[sl];
+        if (!p.pending) continue;
+        float ms = 0.f;
+        if (k < keep && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_prof_launches[p.kind] += 1;
+            g_prof_ms[p.kind] += ms;
+            g_prof_bytes[p.kind] += p.bytes;
+        }
+        p.pending = false;
+    }
+}
+
 void prof_collect() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (ProfPair& p : g_pairs) {

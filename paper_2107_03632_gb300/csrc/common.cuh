@@ -63,6 +63,9 @@ void prof_end(int slot, cudaStream_t st, int kind, int64_t bytes);
 // Adds the device time of completed bracketed launches (call after the
 // stream has been synchronised).
 void prof_collect();
+// After a synchronisation: accounts the first `keep` of `count` bracketed
+// launches and drops the rest (launches that returned without work).
+void prof_commit(const int* slots, int count, int keep);
 
 // ---------------------------------------------------------------- device --
 __device__ __forceinline__ double warp_sum(double v) {

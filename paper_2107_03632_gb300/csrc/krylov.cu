@@ -28,23 +28,23 @@
 // Scalars live in a device state block; each reduction is finished by the
 // last block to arrive (fixed summation order: deterministic for a given
 // grid).  The host enqueues iterations in chunks and reads the state between
-// chunks; kernels of a finished run return at once.  Residual replacement
-// (van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000): when the recurrence
-// residual has fallen 1e3 below its running maximum, r is recomputed from
-// b - A x (keeping p and rh), which bounds the drift between the recurrence
-// and the true residual.
+// chunks; kernels of a finished pass return at once.
 //
-// Mixed solver: an FP64 refinement loop computes r = b - A x with the FP64
-// matrix and adds the inner correction to x in FP64.  The inner BiCGSTAB
-// runs on the float32 values, written in difference form
+// Both solvers run in restarted passes.  A pass starts from the explicit
+// residual r = b - A x (computed in FP64) with a fresh shadow residual
+// rh = r and ends when its recurrence residual has fallen by inner_tol (or
+// on a breakdown); the next pass restarts from the new explicit residual.
+// Long unrestarted BiCGSTAB runs on these nonsymmetric RBF-FD matrices were
+// measured to stall or diverge at 4e6 nodes, while restarted passes converge.
+//
+// Mixed solver: the passes are the inner solves of FP64 iterative
+// refinement -- r = b - A x with the FP64 matrix, the inner BiCGSTAB solves
+// A d = r on the float32 values, x += d in FP64.  The inner operator is
+// written in difference form
 //     (A d)_i = sum_j a_ij (d_j - d_i) + sigma_i d_i,  sigma_i = sum_j a_ij,
 // which is A exactly in exact arithmetic and keeps the zero row sums of the
 // RBF-FD Laplacian exact after rounding a_ij to float (plain float rounding
-// of a_ij would perturb the smooth modes by ~n eps_32 / h^2).  An inner pass
-// ends when its residual has fallen by inner_tol relative to the outer
-// residual; refine 0 restarts the Krylov space at each refinement
-// (classical iterative refinement), refine 1 keeps the search direction
-// across refinements (reliable updates).
+// of a_ij would perturb the smooth modes by ~n eps_32 / h^2).
 #include "common.cuh"
 #include "df32.cuh"
 
@@ -54,6 +54,7 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 namespace rbffd {
 namespace {
@@ -65,7 +66,7 @@ constexpr int kQ = 3;
 
 enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kReplace = 4 };
 enum Slot : int { kSlotResid = 0, kSlotV = 1, kSlotT = 2, kSlotXR = 3, kSlotLoad = 4 };
-enum ResidMode : int { kInit = 0, kReplaceR = 1, kCheck = 2 };
+enum ResidMode : int { kInit = 0, kCheck = 2 };
 
 struct KState {
     double rho, rho_new, alpha, omega;
@@ -73,13 +74,13 @@ struct KState {
     double tol2;    // converged when |r|^2 <= tol2
     double rnorm2;  // last recurrence |r|^2 (unscaled)
     double tnorm2;  // last explicit |b - A x|^2
-    double rmax2;   // reference |r|^2 of the replacement / refinement trigger
-    double repl2;   // trigger when |r|^2 < repl2 * rmax2
+    double rmax2;   // |r|^2 at the start of the pass
+    double repl2;   // the pass ends when |r|^2 < repl2 * rmax2
     int iter;       // iterations of the current run
     int max_iter;
     int flag;
     int bad;        // input validation failure
-    int track_max;  // 1: rmax2 follows the running maximum
+    int pad0;
     int pad;
     unsigned int counter[kSlots];
 };
@@ -193,9 +194,9 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(const int64_t* __restri
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
 }
 
-// kInit:     r = D^-1 (b - A x), rh = r, p = v = 0, scalars reset.
-// kReplaceR: r = D^-1 (b - A x), keep rh, p, v; rho_new = (rh, r).
-// kCheck:    r = b - A x (unscaled), |r|^2 and |b|^2 only.
+// kInit:  r = D^-1 (b - A x), rh = r, p = v = 0, scalars reset: a new pass
+//         that ends when |r|^2 < repl^2 |b - A x|^2.
+// kCheck: r = b - A x (unscaled), |r|^2 and |b|^2 only.
 template <int TPR, int MODE>
 __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __restrict__ row_ptr,
                                                            const int* __restrict__ col,
@@ -221,14 +222,10 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
             } else {
                 const double ri = rt * dinv[i];
                 r[i] = ri;
-                if (MODE == kInit) {
-                    rh[i] = ri;
-                    p[i] = 0.0;
-                    v[i] = 0.0;
-                    acc[2] = fma(ri, ri, acc[2]);
-                } else {
-                    acc[2] = fma(rh[i], ri, acc[2]);
-                }
+                rh[i] = ri;
+                p[i] = 0.0;
+                v[i] = 0.0;
+                acc[2] = fma(ri, ri, acc[2]);
             }
         }
     })
@@ -239,17 +236,14 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
             st->bnorm2 = tot[1];
             return;
         }
-        if (MODE == kInit) {
-            st->bnorm2 = tot[1];
-            st->tol2 = tol * tol * tot[1];
-            st->rho = 1.0;
-            st->alpha = 1.0;
-            st->omega = 1.0;
-            st->iter = 0;
-            st->max_iter = max_iter;
-            st->repl2 = repl * repl;
-            st->track_max = 1;
-        }
+        st->bnorm2 = tot[1];
+        st->tol2 = tol * tol * tot[1];
+        st->rho = 1.0;
+        st->alpha = 1.0;
+        st->omega = 1.0;
+        st->iter = 0;
+        st->max_iter = max_iter;
+        st->repl2 = repl * repl;
         st->rnorm2 = tot[0];
         st->rmax2 = tot[0];
         st->rho_new = tot[2];
@@ -329,7 +323,6 @@ __device__ __forceinline__ void finish_iteration(KState* st, double rn2, double 
     st->rho_new = rho_new;
     const int it = st->iter + 1;
     st->iter = it;
-    if (st->track_max && rn2 > st->rmax2) st->rmax2 = rn2;
     int flag = kRunning;
     if (rn2 <= st->tol2) flag = kConverged;
     else if (!finite(rn2) || !finite(rho_new) || rho_new == 0.0 || st->omega == 0.0) flag = kBreakdown;
@@ -379,9 +372,12 @@ __device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, 
     for (int64_t k = a + sub; k < e; k += TPR) {
         const float w = __ldg(val + k);
         const df xj = df_ldg(x + __ldg(col + k));
-        const df dh = two_sum(xj.hi, -xi.hi);  // exact difference of the leading parts
-        const float dl = __fadd_rn(dh.lo, __fsub_rn(xj.lo, xi.lo));
-        df pr = two_prod(w, dh.hi);
+        // d_j - d_i as an unnormalised pair: the rounding of the leading
+        // difference is at most eps_32 of that difference (exact when the
+        // two values are within a factor 2), so no cancellation is lost
+        const float dh = __fsub_rn(xj.hi, xi.hi);
+        const float dl = __fsub_rn(xj.lo, xi.lo);
+        df pr = two_prod(w, dh);
         pr.lo = __fmaf_rn(w, dl, pr.lo);
         acc.add(pr);
     }
@@ -391,37 +387,29 @@ __device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, 
     return sum;
 }
 
-// Outer residual into the inner system: r = D^-1 r64 (df32), correction 0.
-// Restart (MODE 0): rh = r, p = v = 0, scalars reset.  Reliable (MODE 1):
-// keep rh, p, v; rho_new = (rh, r).  The trigger reference is |r64|^2.
-template <int MODE>
+// Outer residual into the inner system: r = D^-1 r64 (df32), rh = r,
+// p = v = 0, correction 0, scalars reset.  The pass ends when the inner
+// residual has fallen below inner_tol |r64|.
 __global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const double* __restrict__ r64,
                                                            const float* __restrict__ dinv32, float2* __restrict__ r,
                                                            float2* __restrict__ rh, float2* __restrict__ p,
                                                            float2* __restrict__ v, float2* __restrict__ xd,
-                                                           double inner_tol, int max_iter, int track_max,
-                                                           KState* st, double* part) {
+                                                           double inner_tol, int max_iter, KState* st, double* part) {
     DfAcc a0;
     RBFFD_ELEM_LOOP(N, i) {
         const df ri = df_mul_f(df_from_double(r64[i]), dinv32[i]);
         df_store(r + i, ri);
+        df_store(rh + i, ri);
         xd[i] = make_float2(0.f, 0.f);
-        if (MODE == 0) {
-            df_store(rh + i, ri);
-            p[i] = make_float2(0.f, 0.f);
-            v[i] = make_float2(0.f, 0.f);
-            a0.add(df_mul(ri, ri));
-        } else {
-            a0.add(df_mul(df_load(rh + i), ri));
-        }
+        p[i] = make_float2(0.f, 0.f);
+        v[i] = make_float2(0.f, 0.f);
+        a0.add(df_mul(ri, ri));
     }
     double acc[1] = {df_to_double(a0.value())}, tot[1];
     if (reduce_last<1>(acc, part, kSlotLoad, &st->counter[kSlotLoad], tot) && threadIdx.x == 0) {
-        if (MODE == 0) {
-            st->rho = 1.0;
-            st->alpha = 1.0;
-            st->omega = 1.0;
-        }
+        st->rho = 1.0;
+        st->alpha = 1.0;
+        st->omega = 1.0;
         st->rho_new = tot[0];
         st->iter = 0;
         st->max_iter = max_iter;
@@ -429,7 +417,6 @@ __global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const doub
         st->rnorm2 = st->tnorm2;  // |r64|^2 from the preceding check
         st->rmax2 = st->tnorm2;
         st->repl2 = inner_tol * inner_tol;
-        st->track_max = track_max;
         st->flag = (!finite(tot[0]) || tot[0] == 0.0) ? kBreakdown : (max_iter <= 0 ? kMaxIter : kRunning);
     }
 }
@@ -600,15 +587,15 @@ int env_int(const char* name, int dflt) {
     return std::atoi(v);
 }
 
-// Lanes per row: the FP64 SpMV keeps few lanes per row (each reduction step
-// costs FP64 adds); the df32 SpMV spends FP32 only and takes 8 lanes (one
-// 32-byte sector of float values per step).  RBFFD_TPR64 / RBFFD_TPR32
-// override for tuning sweeps.
+// Lanes per row, from sweeps on GB300: the FP64 SpMV keeps few lanes per row
+// (each reduction step costs FP64 adds): 4 for ~56 entries, 2 for ~30; the
+// df32 SpMV does best with 4.  RBFFD_TPR64 / RBFFD_TPR32 override for
+// tuning sweeps.
 int tpr64_for(int64_t N, int64_t nnz) {
     const int o = env_int("RBFFD_TPR64", 0);
     if (o == 1 || o == 2 || o == 4 || o == 8) return o;
     const double L = (double)nnz / (double)std::max<int64_t>(N, 1);
-    if (L >= 24) return 4;
+    if (L >= 40) return 4;
     if (L >= 8) return 2;
     return 1;
 }
@@ -617,7 +604,6 @@ int tpr32_for(int64_t N, int64_t nnz) {
     const int o = env_int("RBFFD_TPR32", 0);
     if (o == 2 || o == 4 || o == 8 || o == 16) return o;
     const double L = (double)nnz / (double)std::max<int64_t>(N, 1);
-    if (L >= 24) return 8;
     if (L >= 12) return 4;
     return 2;
 }
@@ -656,28 +642,27 @@ struct Ops64 {
         if (mode == kInit)
             resid64_kernel<TPR, kInit><<<grid_of(resid64_kernel<TPR, kInit>), kThreads, 0, st>>>(
                 A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
-        else if (mode == kReplaceR)
-            resid64_kernel<TPR, kReplaceR><<<grid_of(resid64_kernel<TPR, kReplaceR>), kThreads, 0, st>>>(
-                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
         else
             resid64_kernel<TPR, kCheck><<<grid_of(resid64_kernel<TPR, kCheck>), kThreads, 0, st>>>(
                 A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
         note_launches(1);
     }
-    static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
+    static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st, std::vector<int>& ev) {
         const int64_t N = A.n_rows;
         const double* val = static_cast<const double*>(A.val);
         const int64_t bytes = spmv_bytes(A, 8);
         update_p64_kernel<<<grid_of(update_p64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
-        int ev = prof_begin(st);
+        int e = prof_begin(st);
         spmv64_kernel<TPR, 0><<<grid_of(spmv64_kernel<TPR, 0>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.p,
                                                                                    w.dinv, w.v, w.rh, w.st, w.part);
-        prof_end(ev, st, kProfSpmv64, bytes);
+        prof_end(e, st, kProfSpmv64, bytes);
+        ev.push_back(e);
         update_s64_kernel<<<grid_of(update_s64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
-        ev = prof_begin(st);
+        e = prof_begin(st);
         spmv64_kernel<TPR, 1><<<grid_of(spmv64_kernel<TPR, 1>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.s,
                                                                                    w.dinv, w.t, nullptr, w.st, w.part);
-        prof_end(ev, st, kProfSpmv64, bytes);
+        prof_end(e, st, kProfSpmv64, bytes);
+        ev.push_back(e);
         update_xr64_kernel<<<grid_of(update_xr64_kernel), kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d,
                                                                              w.st, w.part);
         note_launches(5);
@@ -686,22 +671,24 @@ struct Ops64 {
 
 template <int TPR>
 struct OpsDf {
-    static void iteration(const rbffd_csr& A32, const Work& w, cudaStream_t st) {
+    static void iteration(const rbffd_csr& A32, const Work& w, cudaStream_t st, std::vector<int>& ev) {
         const int64_t N = A32.n_rows;
         const float* val = static_cast<const float*>(A32.val);
-        // algorithmic bytes: as the FP64 SpMV with 4-byte values, 8-byte
-        // df32 vectors, and 4-byte sigma and Jacobi scale instead of 8
+        // algorithmic bytes: nnz (4 + 4) + row_ptr + 8-byte df32 vectors
+        // (gathered once, result, dot partner) + 4-byte sigma and scale
         const int64_t bytes = spmv_bytes(A32, 4);
         update_p_df_kernel<<<grid_of(update_p_df_kernel), kThreads, 0, st>>>(N, w.rd, w.vd, w.pd, w.st);
-        int ev = prof_begin(st);
+        int e = prof_begin(st);
         spmv_df_kernel<TPR, 0><<<grid_of(spmv_df_kernel<TPR, 0>), kThreads, 0, st>>>(
             A32.row_ptr, A32.col, val, N, w.pd, w.sigma32, w.dinv32, w.vd, w.rhd, w.st, w.part);
-        prof_end(ev, st, kProfSpmv32, bytes);
+        prof_end(e, st, kProfSpmv32, bytes);
+        ev.push_back(e);
         update_s_df_kernel<<<grid_of(update_s_df_kernel), kThreads, 0, st>>>(N, w.rd, w.vd, w.sd, w.st);
-        ev = prof_begin(st);
+        e = prof_begin(st);
         spmv_df_kernel<TPR, 1><<<grid_of(spmv_df_kernel<TPR, 1>), kThreads, 0, st>>>(
             A32.row_ptr, A32.col, val, N, w.sd, w.sigma32, w.dinv32, w.td, nullptr, w.st, w.part);
-        prof_end(ev, st, kProfSpmv32, bytes);
+        prof_end(e, st, kProfSpmv32, bytes);
+        ev.push_back(e);
         update_xr_df_kernel<<<grid_of(update_xr_df_kernel), kThreads, 0, st>>>(N, w.xd, w.pd, w.sd, w.td, w.rd,
                                                                                w.rhd, w.d32, w.st, w.part);
         note_launches(5);
@@ -718,28 +705,27 @@ void resid64(int tpr, int mode, const rbffd_csr& A, const double* b, const doubl
     }
 }
 
-void iter64(int tpr, const rbffd_csr& A, double* x, const Work& w, cudaStream_t st) {
+void iter64(int tpr, const rbffd_csr& A, double* x, const Work& w, cudaStream_t st, std::vector<int>& ev) {
     switch (tpr) {
-        case 1: Ops64<1>::iteration(A, x, w, st); break;
-        case 2: Ops64<2>::iteration(A, x, w, st); break;
-        case 8: Ops64<8>::iteration(A, x, w, st); break;
-        default: Ops64<4>::iteration(A, x, w, st); break;
+        case 1: Ops64<1>::iteration(A, x, w, st, ev); break;
+        case 2: Ops64<2>::iteration(A, x, w, st, ev); break;
+        case 8: Ops64<8>::iteration(A, x, w, st, ev); break;
+        default: Ops64<4>::iteration(A, x, w, st, ev); break;
     }
 }
 
-void iter_df(int tpr, const rbffd_csr& A32, const Work& w, cudaStream_t st) {
+void iter_df(int tpr, const rbffd_csr& A32, const Work& w, cudaStream_t st, std::vector<int>& ev) {
     switch (tpr) {
-        case 2: OpsDf<2>::iteration(A32, w, st); break;
-        case 4: OpsDf<4>::iteration(A32, w, st); break;
-        case 16: OpsDf<16>::iteration(A32, w, st); break;
-        default: OpsDf<8>::iteration(A32, w, st); break;
+        case 2: OpsDf<2>::iteration(A32, w, st, ev); break;
+        case 8: OpsDf<8>::iteration(A32, w, st, ev); break;
+        case 16: OpsDf<16>::iteration(A32, w, st, ev); break;
+        default: OpsDf<4>::iteration(A32, w, st, ev); break;
     }
 }
 
 int read_state(const Work& w, KState* hs, cudaStream_t st) {
     RBFFD_CUDA_TRY(cudaMemcpyAsync(hs, w.st, sizeof(KState), cudaMemcpyDeviceToHost, st));
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-    if (profiling()) prof_collect();
     return RBFFD_OK;
 }
 
@@ -753,17 +739,21 @@ double rel_of(const KState& s) {
     return std::sqrt(s.tnorm2);
 }
 
-constexpr double kReplaceFactor = 1e-3;  // FP64 residual replacement after a 1e3 drop
-
 // Runs chunks of iterations until the state leaves kRunning; returns the
-// flag, or minus a status on a CUDA error.
+// flag, or minus a status on a CUDA error.  With profiling on, only the SpMV
+// launches of iterations that ran are accounted (launches after the pass
+// ended return at once and are dropped).
 template <class IterFn>
 int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn iter) {
+    std::vector<int> ev;
     while (hs->flag == kRunning) {
-        for (int c = 0; c < chunk; ++c) iter();
+        const int before = hs->iter;
+        ev.clear();
+        for (int c = 0; c < chunk; ++c) iter(ev);
         RBFFD_LAUNCH_CHECK();
         const int rc = read_state(w, hs, st);
         if (rc != RBFFD_OK) return -rc;
+        if (profiling()) prof_commit(ev.data(), (int)ev.size(), 2 * (hs->iter - before));
         chunk = std::min(chunk * 2, 64);
     }
     return hs->flag;
@@ -774,55 +764,51 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     const int tpr = tpr64_for(A.n_rows, A.nnz);
     KState hs;
     int rc;
-    int total = 0, replacements = 0, breakdowns = 0, chunk = 4;
-    resid64(tpr, kInit, A, b, x, w, w.r, o.tol, o.max_iter, kReplaceFactor, st);
-    RBFFD_LAUNCH_CHECK();
-    if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+    int total = 0, passes = 0, breakdowns = 0, chunk = 4;
     int status = RBFFD_ERR_NOT_CONVERGED;
+    double rel = INFINITY;
     while (true) {
-        if (hs.flag == kRunning) {
-            const int f = run_chunks(w, &hs, st, chunk, [&] { iter64(tpr, A, x, w, st); });
-            if (f < 0) return -f;
+        // explicit residual; starts a fresh pass (rh = r, p = v = 0)
+        resid64(tpr, kInit, A, b, x, w, w.r, o.tol, std::max(o.max_iter - total, 0), o.inner_tol, st);
+        RBFFD_LAUNCH_CHECK();
+        if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
+            rel = 0.0;
+            status = RBFFD_OK;
+            break;
         }
-        if (hs.flag == kConverged || hs.flag == kReplace) {
-            // recompute r from b - A x (keeps p, rh); confirms convergence
-            resid64(tpr, kReplaceR, A, b, x, w, w.r, o.tol, o.max_iter, kReplaceFactor, st);
-            RBFFD_LAUNCH_CHECK();
-            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-            ++replacements;
-            if (hs.flag == kConverged) {
-                status = RBFFD_OK;
-                break;
-            }
-            continue;
+        rel = rel_of(hs);
+        if (rel <= o.tol) {
+            status = RBFFD_OK;
+            break;
         }
+        if (!std::isfinite(rel)) {
+            status = RBFFD_ERR_BREAKDOWN;
+            break;
+        }
+        if (total >= o.max_iter || passes >= o.max_outer) break;
+        ++passes;
+        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); });
+        if (f < 0) return -f;
+        total += hs.iter;
         if (hs.flag == kBreakdown) {
-            total += hs.iter;
-            if (++breakdowns >= 2) {
+            if (++breakdowns >= 3) {
                 status = RBFFD_ERR_BREAKDOWN;
-                hs.iter = 0;
                 break;
             }
-            resid64(tpr, kInit, A, b, x, w, w.r, o.tol, std::max(o.max_iter - total, 0), kReplaceFactor, st);
-            RBFFD_LAUNCH_CHECK();
-            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-            continue;
+        } else {
+            breakdowns = 0;
         }
-        status = RBFFD_ERR_NOT_CONVERGED;  // kMaxIter
-        break;
     }
-    total += hs.iter;
-    // explicit residual of the returned x
-    resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, kReplaceFactor, st);
-    RBFFD_LAUNCH_CHECK();
-    if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-    const bool zero = hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0;
-    const double rel = zero ? 0.0 : rel_of(hs);
-    if (zero) status = RBFFD_OK;
-    if (status == RBFFD_OK && !(rel <= o.tol)) status = RBFFD_ERR_NOT_CONVERGED;
+    if (status != RBFFD_OK && std::isfinite(rel) && total > 0) {
+        resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, 0.0, st);
+        RBFFD_LAUNCH_CHECK();
+        if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        rel = rel_of(hs);
+    }
     info->status = status;
     info->iters = total;
-    info->outer_sweeps = replacements;
+    info->outer_sweeps = passes;
     info->restarts = breakdowns;
     info->rel_residual = rel;
     return status;
@@ -833,13 +819,10 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     const int64_t N = A.n_rows;
     const int tpr64 = tpr64_for(N, A.nnz);
     const int tpr32 = tpr32_for(N, A.nnz);
-    const int nb = nblocks();
-    const bool reliable = o.refine == 1;
     KState hs;
     int rc;
     int total = 0, outer = 0, breakdowns = 0, chunk = 4;
     int status = RBFFD_ERR_NOT_CONVERGED;
-    bool restart = true;
     double rel = INFINITY;
     while (true) {
         resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
@@ -864,20 +847,15 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         // relative target of this pass: inner_tol, but no deeper than the
         // outer tolerance needs
         const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);
-        if (restart || !reliable)
-            load_df_kernel<0><<<grid_of(load_df_kernel<0>), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd, w.xd, inner,
-                                                       o.max_iter - total, reliable ? 1 : 0, w.st, w.part);
-        else
-            load_df_kernel<1><<<grid_of(load_df_kernel<1>), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd, w.xd, inner,
-                                                       o.max_iter - total, 1, w.st, w.part);
+        load_df_kernel<<<grid_of(load_df_kernel), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd,
+                                                                     w.xd, inner, o.max_iter - total, w.st, w.part);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-        restart = false;
-        const int f = run_chunks(w, &hs, st, chunk, [&] { iter_df(tpr32, A32, w, st); });
+        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter_df(tpr32, A32, w, st, ev); });
         if (f < 0) return -f;
         total += hs.iter;
-        refine_kernel<<<nb, kThreads, 0, st>>>(N, x, w.xd);
+        refine_kernel<<<grid_of(refine_kernel), kThreads, 0, st>>>(N, x, w.xd);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if (hs.flag == kBreakdown) {
@@ -885,15 +863,15 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
                 status = RBFFD_ERR_BREAKDOWN;
                 break;
             }
-            restart = true;
-        } else if (hs.flag == kMaxIter) {
-            resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
-            RBFFD_LAUNCH_CHECK();
-            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-            rel = rel_of(hs);
-            status = rel <= o.tol ? RBFFD_OK : RBFFD_ERR_NOT_CONVERGED;
-            break;
+        } else {
+            breakdowns = 0;
         }
+    }
+    if (status != RBFFD_OK && std::isfinite(rel) && total > 0) {
+        resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
+        RBFFD_LAUNCH_CHECK();
+        if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        rel = rel_of(hs);
     }
     info->status = status;
     info->iters = total;
@@ -911,8 +889,8 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     if (mixed && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz ||
                   A32->row_ptr != A->row_ptr || A32->col != A->col))
         return RBFFD_ERR_INVALID_ARG;  // the float32 copy shares A's (validated) pattern
-    if (!(o->tol > 0.0) || o->max_iter < 0 || (o->refine != 0 && o->refine != 1)) return RBFFD_ERR_INVALID_ARG;
-    if (mixed && (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1)) return RBFFD_ERR_INVALID_ARG;
+    if (!(o->tol > 0.0) || o->max_iter < 0) return RBFFD_ERR_INVALID_ARG;
+    if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1) return RBFFD_ERR_INVALID_ARG;
     const int64_t N = A->n_rows;
     Work w{};
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, N, mixed, nullptr))

@@ -60,7 +60,6 @@ class SolveOpts(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
         ("jacobi", ctypes.c_int32),
-        ("refine", ctypes.c_int32),
     ]
 
 
@@ -310,11 +309,13 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
 
 
 # -------------------------------------------------------------------- solve --
-def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=1e-5, max_outer=60, jacobi=True,
-              refine="restart"):
+def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_outer=200, jacobi=True):
+    """Solver options.  inner_tol: residual reduction per restarted pass
+    (default 1e-3 for FP64, 1e-5 for mixed)."""
     prec = {"fp64": 0, "mixed": 1}[precision]
-    ref = {"restart": 0, "reliable": 1}[refine]
-    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0, ref)
+    if inner_tol is None:
+        inner_tol = 1e-5 if prec == 1 else 1e-3
+    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0)
 
 
 def stencils_workspace(N: int, n: int, device) -> torch.Tensor:

@@ -181,13 +181,14 @@ def _system(h, m, n):
 
 
 @pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.06, 4, 30), (0.1, 6, 56), (0.03, 4, 30)])
-@pytest.mark.parametrize("precision,refine", [("fp64", "restart"), ("mixed", "restart"), ("mixed", "reliable")])
-def test_solve_vs_oracle(lib, h, m, n, precision, refine):
+@pytest.mark.parametrize("precision,inner_tol", [("fp64", 1e-3), ("fp64", 1e-8), ("mixed", 1e-5), ("mixed", 1e-3)])
+def test_solve_vs_oracle(lib, h, m, n, precision, inner_tol):
     from paper_2107_03632_gb300 import rbffd
 
     d, (idx, w, rp, col, val, b, f, g, u) = _system(h, m, n)
     A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet), want_f32=(precision == "mixed"))
-    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(tol=1e-10, precision=precision, refine=refine))
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(tol=1e-10, precision=precision,
+                                                              inner_tol=inner_tol))
     x = x.cpu().numpy()
     ref = oracle.solve_direct(rp, col, val, b)
     assert info["status"] == 0 and info["rel_residual"] <= 1e-10
