@@ -64,7 +64,9 @@ constexpr int kMaxBlocks = 2048;
 constexpr int kSlots = 8;
 constexpr int kQ = 3;
 
-enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kReplace = 4 };
+enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kReplace = 4, kDiverged = 5 };
+// A pass whose residual has grown 1e3 above its start is ended early.
+constexpr double kGrowth2 = 1e6;
 enum Slot : int { kSlotResid = 0, kSlotV = 1, kSlotT = 2, kSlotXR = 3, kSlotLoad = 4 };
 enum ResidMode : int { kInit = 0, kCheck = 2 };
 
@@ -118,6 +120,29 @@ __device__ bool reduce_last(double (&v)[NQ], double* part, int slot, unsigned in
 }
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// omega = (t, s) / (t, t), enlarged when t and s are far from parallel
+// (|cos| < 0.7): the stabilisation of Sleijpen & van der Vorst (Numer.
+// Algorithms 10, 1995), which keeps the BiCG part of BiCGSTAB from
+// stagnating or breaking down when omega would be tiny (complex spectra).
+__device__ __forceinline__ void set_omega(KState* st, double ts, double tt, double ss) {
+    if (!finite(ts) || !finite(tt) || !finite(ss)) {
+        st->flag = kBreakdown;
+        return;
+    }
+    if (!(tt > 0.0)) {
+        st->omega = 0.0;
+        return;
+    }
+    double om = ts / tt;
+    const double den = sqrt(tt) * sqrt(ss);
+    if (den > 0.0) {
+        const double c = fabs(ts) / den;
+        if (c < 0.7) om *= 0.7 / fmax(c, 1e-300);
+    }
+    st->omega = om;
+}
+
 
 // Iterate rows in groups of TPR lanes with a warp-uniform loop (every lane
 // of a warp runs the same number of trips, so full-mask shuffles are safe).
@@ -274,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
                                                           const double* __restrict__ rh, KState* st, double* part) {
     if (st->flag != kRunning) return;
     const int sub = threadIdx.x & (TPR - 1);
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
         const double ax = row_dot64<TPR>(row_ptr, col, val, xin, i, sub, valid);
         if (valid && sub == 0) {
@@ -283,8 +308,10 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
             if (MODE == 0) {
                 acc[0] = fma(rh[i], yi, acc[0]);
             } else {
-                acc[0] = fma(yi, xin[i], acc[0]);
+                const double si = xin[i];
+                acc[0] = fma(yi, si, acc[0]);
                 acc[1] = fma(yi, yi, acc[1]);
+                acc[2] = fma(si, si, acc[2]);
             }
         }
     })
@@ -300,12 +327,9 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
             }
         }
     } else {
-        double tot[2];
-        if (reduce_last<2>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0) {
-            const double ts = tot[0], tt = tot[1];
-            if (!finite(ts) || !finite(tt)) st->flag = kBreakdown;
-            else st->omega = (tt > 0.0) ? ts / tt : 0.0;
-        }
+        double tot[3];
+        if (reduce_last<3>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0)
+            set_omega(st, tot[0], tot[1], tot[2]);
     }
 }
 
@@ -327,6 +351,7 @@ __device__ __forceinline__ void finish_iteration(KState* st, double rn2, double 
     if (rn2 <= st->tol2) flag = kConverged;
     else if (!finite(rn2) || !finite(rho_new) || rho_new == 0.0 || st->omega == 0.0) flag = kBreakdown;
     else if (rn2 < st->repl2 * st->rmax2) flag = kReplace;
+    else if (rn2 > kGrowth2 * st->rmax2) flag = kDiverged;
     else if (it >= st->max_iter) flag = kMaxIter;
     st->flag = flag;
 }
@@ -446,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) spmv_df_kernel(const int64_t* __rest
                                                            KState* st, double* part) {
     if (st->flag != kRunning) return;
     const int sub = threadIdx.x & (TPR - 1);
-    DfAcc a0, a1;
+    DfAcc a0, a1, a2;
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
         const df xi = valid ? df_ldg(xin + i) : df_make(0.f, 0.f);
         df ax = row_apply_df<TPR>(row_ptr, col, val, xin, i, sub, valid, xi);
@@ -459,6 +484,7 @@ __global__ void __launch_bounds__(kThreads) spmv_df_kernel(const int64_t* __rest
             } else {
                 a0.add(df_mul(yi, xi));
                 a1.add(df_mul(yi, yi));
+                a2.add(df_mul(xi, xi));
             }
         }
     })
@@ -474,12 +500,9 @@ __global__ void __launch_bounds__(kThreads) spmv_df_kernel(const int64_t* __rest
             }
         }
     } else {
-        double acc[2] = {df_to_double(a0.value()), df_to_double(a1.value())}, tot[2];
-        if (reduce_last<2>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0) {
-            const double ts = tot[0], tt = tot[1];
-            if (!finite(ts) || !finite(tt)) st->flag = kBreakdown;
-            else st->omega = (tt > 0.0) ? ts / tt : 0.0;
-        }
+        double acc[3] = {df_to_double(a0.value()), df_to_double(a1.value()), df_to_double(a2.value())}, tot[3];
+        if (reduce_last<3>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0)
+            set_omega(st, tot[0], tot[1], tot[2]);
     }
 }
 
@@ -541,6 +564,7 @@ struct Work {
     KState* st;
     double* part;
     double *d, *dinv;
+    double* x_save;  // iterate at the start of the current pass
     // FP64 engine
     double *r, *rh, *p, *v, *s, *t;
     // mixed engine
@@ -557,6 +581,7 @@ size_t layout(void* ws, int64_t N, bool mixed, Work* w) {
     t.part = c.take<double>((size_t)kSlots * kQ * kMaxBlocks);
     t.d = c.take<double>(N);
     t.dinv = c.take<double>(N);
+    t.x_save = c.take<double>(N);
     if (!mixed) {
         t.r = c.take<double>(N);
         t.rh = c.take<double>(N);
@@ -759,19 +784,40 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn it
     return hs->flag;
 }
 
+// Pass bookkeeping shared by both solvers.  A pass that leaves the explicit
+// residual larger than at its start is undone (the iterate is restored from
+// the copy taken before the pass) and the next pass gets half the iteration
+// budget of the rejected one: the early part of a BiCGSTAB pass is the part
+// that reduces the residual.
+struct PassGuard {
+    double prev = INFINITY;  // explicit |r|^2 at the start of the pass just run
+    int cap = 0x7fffffff;    // iteration budget of the next pass
+    int rejected = 0;
+};
+
 int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve_opts& o, const Work& w,
                cudaStream_t st, rbffd_solve_info* info) {
-    const int tpr = tpr64_for(A.n_rows, A.nnz);
+    const int64_t N = A.n_rows;
+    const int tpr = tpr64_for(N, A.nnz);
     KState hs;
     int rc;
     int total = 0, passes = 0, breakdowns = 0, chunk = 4;
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
+    PassGuard g;
     while (true) {
         // explicit residual; starts a fresh pass (rh = r, p = v = 0)
-        resid64(tpr, kInit, A, b, x, w, w.r, o.tol, std::max(o.max_iter - total, 0), o.inner_tol, st);
+        const int budget = std::min(std::max(o.max_iter - total, 0), g.cap);
+        resid64(tpr, kInit, A, b, x, w, w.r, o.tol, budget, o.inner_tol, st);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        if (passes > 0 && !(hs.tnorm2 <= g.prev)) {
+            // the pass made things worse: undo it and retry with a shorter pass
+            RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            ++g.rejected;
+            g.prev = INFINITY;
+            continue;
+        }
         if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
             rel = 0.0;
             status = RBFFD_OK;
@@ -788,16 +834,17 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         }
         if (total >= o.max_iter || passes >= o.max_outer) break;
         ++passes;
+        g.prev = hs.tnorm2;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); });
         if (f < 0) return -f;
         total += hs.iter;
+        g.cap = (hs.flag == kDiverged || hs.flag == kBreakdown) ? std::max(hs.iter / 2, 8) : 0x7fffffff;
         if (hs.flag == kBreakdown) {
-            if (++breakdowns >= 3) {
+            if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
                 break;
             }
-        } else {
-            breakdowns = 0;
         }
     }
     if (status != RBFFD_OK && std::isfinite(rel) && total > 0) {
@@ -809,7 +856,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     info->status = status;
     info->iters = total;
     info->outer_sweeps = passes;
-    info->restarts = breakdowns;
+    info->restarts = g.rejected;
     info->rel_residual = rel;
     return status;
 }
@@ -824,10 +871,18 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     int total = 0, outer = 0, breakdowns = 0, chunk = 4;
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
+    PassGuard g;
     while (true) {
         resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        if (outer > 0 && !(hs.tnorm2 <= g.prev)) {
+            // the correction made things worse: undo it, shorter next pass
+            RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            ++g.rejected;
+            g.prev = INFINITY;
+            continue;
+        }
         if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
             rel = 0.0;
             status = RBFFD_OK;
@@ -844,27 +899,29 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         }
         if (total >= o.max_iter || outer >= o.max_outer) break;
         ++outer;
+        g.prev = hs.tnorm2;
         // relative target of this pass: inner_tol, but no deeper than the
         // outer tolerance needs
         const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);
+        const int budget = std::min(o.max_iter - total, g.cap);
         load_df_kernel<<<grid_of(load_df_kernel), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd,
-                                                                     w.xd, inner, o.max_iter - total, w.st, w.part);
+                                                                     w.xd, inner, budget, w.st, w.part);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
         const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter_df(tpr32, A32, w, st, ev); });
         if (f < 0) return -f;
         total += hs.iter;
+        g.cap = (hs.flag == kDiverged || hs.flag == kBreakdown) ? std::max(hs.iter / 2, 8) : 0x7fffffff;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         refine_kernel<<<grid_of(refine_kernel), kThreads, 0, st>>>(N, x, w.xd);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if (hs.flag == kBreakdown) {
-            if (++breakdowns >= 3) {
+            if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
                 break;
             }
-        } else {
-            breakdowns = 0;
         }
     }
     if (status != RBFFD_OK && std::isfinite(rel) && total > 0) {
@@ -876,7 +933,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     info->status = status;
     info->iters = total;
     info->outer_sweeps = outer;
-    info->restarts = breakdowns;
+    info->restarts = g.rejected;
     info->rel_residual = rel;
     return status;
 }

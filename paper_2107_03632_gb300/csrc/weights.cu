@@ -27,6 +27,8 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 namespace rbffd {
 namespace {
@@ -271,14 +273,369 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Null-space (block) elimination of the same saddle-point system.
+//
+// With P of full column rank, pick s pivot rows r1 of P by Gauss-Jordan
+// elimination with row pivoting (the other q = n - s rows are r2) and let
+// X = P[r2] P[r1]^-1 (q x s).  The columns of Z = [-X^T ; I] (rows r1, r2)
+// span {z : P^T z = 0}, every solution of P^T w = g is w0 + Z y with
+// w0[r1] = P[r1]^-T g, w0[r2] = 0, and the first block row reduces to
+//     (Z^T Phi Z) y = Z^T (f - Phi w0).
+// r^3 is conditionally positive definite of order 2 and the columns of Z
+// annihilate every polynomial of degree <= m (>= 1), so Z^T Phi Z is
+// symmetric positive definite: Cholesky, no pivoting.  The weights are
+// the same as from the full (n+s) x (n+s) solve in exact arithmetic; the
+// FP64 work is ~n s^2 (elimination) + 2 s^2 q + s q^2 (reduced matrix) +
+// q^3/3 flops instead of (2/3)(n+s)^3, about half at m = 6, n = 56.
+//
+// Shared memory per warp (doubles unless noted), nodes in permuted order
+// [r1, r2] once the pivots are known:
+//   Phi  n x LDF     r^3 kernel matrix; T = Phi12 - Phi11 X^T overwrites
+//                    Phi12, S = Z^T Phi Z (lower triangle) overwrites Phi22
+//   P    (n+1) x LDS monomials, row n holds g; after elimination rows r2
+//                    hold X and row n holds w0[r1]
+//   crd  2n          scaled coordinates (caller order)
+//   fv, uv, wv  n    rhs 9|xh|, f - Phi w0, permuted weights
+//   tv   n           reduced rhs / solution (q used)
+//   perm, act  n int permutation and the active-row list
+struct NsGeom {
+    int n, m, s, q, LDF, LDS;
+    int doubles, ints, bytes;
+};
+
+NsGeom ns_geom(int n, int m) {
+    NsGeom g;
+    g.n = n;
+    g.m = m;
+    g.s = (m + 1) * (m + 2) / 2;
+    g.q = n - g.s;
+    g.LDF = n | 1;
+    g.LDS = g.s | 1;
+    g.doubles = n * g.LDF + (n + 1) * g.LDS + 2 * n + 4 * n;
+    g.ints = 2 * n;
+    g.bytes = (int)align_up((size_t)g.doubles * 8 + (size_t)g.ints * 4, 16);
+    return g;
+}
+
+__global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
+                                                         int N, int n, int m, int s, int LDF, int LDS,
+                                                         int bytes_per_warp, double* __restrict__ w,
+                                                         int* __restrict__ node_status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int q = n - s;
+    double* Phi = reinterpret_cast<double*>(smem_raw + (size_t)wib * bytes_per_warp);
+    double* P = Phi + (size_t)n * LDF;
+    double* crd = P + (size_t)(n + 1) * LDS;
+    double* fv = crd + 2 * n;
+    double* uv = fv + n;
+    double* wv = uv + n;
+    double* tv = wv + n;
+    int* perm = reinterpret_cast<int*>(tv + n);
+    int* act = perm + n;
+    const int total_warps = gridDim.x * wpb;
+
+    for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
+        const int* sten = idx + (int64_t)node * n;
+        const double2 c = xy[node];
+
+        // ---- shift, scale ----------------------------------------------------
+        unsigned long long dmax = 0;
+        int bad = 0;
+        for (int j = lane; j < n; j += 32) {
+            const int sj = sten[j];
+            const bool ok = (unsigned)sj < (unsigned)N;  // never read outside xy
+            bad |= ok ? 0 : 1;
+            const double2 p = ok ? xy[sj] : c;
+            const double dx = __dadd_rn(p.x, -c.x);
+            const double dy = __dadd_rn(p.y, -c.y);
+            const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            const unsigned long long b = abs_bits(d2);
+            dmax = (b > dmax) ? b : dmax;
+            crd[2 * j] = dx;
+            crd[2 * j + 1] = dy;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, dmax, o);
+            dmax = (t > dmax) ? t : dmax;
+        }
+        const double delta = __dsqrt_rn(__longlong_as_double((long long)dmax));
+        const double delta2 = __dmul_rn(delta, delta);
+        __syncwarp();
+
+        // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
+        for (int j = lane; j < n; j += 32) {
+            const double xh = __ddiv_rn(crd[2 * j], delta);
+            const double yh = __ddiv_rn(crd[2 * j + 1], delta);
+            crd[2 * j] = xh;
+            crd[2 * j + 1] = yh;
+            double xp[9], yp[9];
+            xp[0] = 1.0;
+            yp[0] = 1.0;
+#pragma unroll
+            for (int t = 1; t < 9; ++t) {
+                xp[t] = (t <= m) ? __dmul_rn(xp[t - 1], xh) : 0.0;
+                yp[t] = (t <= m) ? __dmul_rn(yp[t - 1], yh) : 0.0;
+            }
+            int col = 0;
+            for (int d = 0; d <= m; ++d)
+                for (int i = 0; i <= d; ++i, ++col) P[(size_t)j * LDS + col] = (d == 0) ? 1.0 : __dmul_rn(xp[d - i], yp[i]);
+            act[j] = j;
+        }
+        for (int col = lane; col < s; col += 32) {
+            // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5)
+            P[(size_t)n * LDS + col] = (col == 3 || col == 5) ? 2.0 : 0.0;
+        }
+        __syncwarp();
+
+        // ---- Gauss-Jordan with row pivoting on P ------------------------------
+        int na = n;  // active (not yet pivot) rows act[0..na)
+        int singular = __any_sync(0xffffffffu, bad) ? 1 : 0;
+        for (int k = 0; k < s && !singular; ++k) {
+            unsigned long long best = 0;
+            int bi = 0x7fffffff, bpos = -1;
+            for (int t = lane; t < na; t += 32) {
+                const int r = act[t];
+                const unsigned long long b = abs_bits(P[(size_t)r * LDS + k]);
+                if (b > best || (b == best && r < bi)) {
+                    best = b;
+                    bi = r;
+                    bpos = t;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                    bpos = op;
+                }
+            }
+            if (best == 0 || best >= 0x7ff0000000000000ull) {  // rank deficient or non-finite
+                singular = 1;
+                break;
+            }
+            const int pr = bi;
+            const double inv = __ddiv_rn(1.0, P[(size_t)pr * LDS + k]);
+            __syncwarp();
+            if (lane == 0) {
+                perm[k] = pr;
+                act[bpos] = act[na - 1];  // swap-remove the pivot row
+            }
+            --na;
+            __syncwarp();
+            // scale column k on the active rows and the g row; pivot row -> e_k
+            for (int t = lane; t <= na; t += 32) {
+                const int r = (t < na) ? act[t] : n;
+                P[(size_t)r * LDS + k] = __dmul_rn(P[(size_t)r * LDS + k], inv);
+            }
+            __syncwarp();
+            // column j -= P[pr][j] * column k, on active rows and the g row;
+            // flattened (row t, column jj) with incremental indices
+            const int cols = s - 1, rows = na + 1, total = rows * cols;
+            if (cols > 0) {
+                int t = lane / cols, jj = lane - (lane / cols) * cols;
+                const int st = 32 / cols, sj = 32 - (32 / cols) * cols;
+                const double* prow = P + (size_t)pr * LDS;
+                for (int e = lane; e < total; e += 32) {
+                    const int j = jj + ((jj >= k) ? 1 : 0);
+                    const int r = (t < na) ? act[t] : n;
+                    double* rr = P + (size_t)r * LDS;
+                    rr[j] = fma(-prow[j], rr[k], rr[j]);
+                    t += st;
+                    jj += sj;
+                    if (jj >= cols) {
+                        jj -= cols;
+                        ++t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (!singular) {
+            for (int t = lane; t < q; t += 32) perm[s + t] = act[t];
+        }
+        __syncwarp();
+
+        // ---- Phi in permuted order, and f = 9 |xh| ---------------------------
+        int coincident = 0;
+        if (!singular) {
+            const int npairs = n * (n - 1) / 2;
+            for (int pidx = lane; pidx < npairs; pidx += 32) {
+                int a = (int)((2.0f * n - 1.0f - sqrtf((2.0f * n - 1.0f) * (2.0f * n - 1.0f) - 8.0f * pidx)) * 0.5f);
+                if (a < 0) a = 0;
+                while (a > 0 && a * (2 * n - a - 1) / 2 > pidx) --a;
+                while ((a + 1) * (2 * n - a - 2) / 2 <= pidx) ++a;
+                const int b = pidx - a * (2 * n - a - 1) / 2 + a + 1;
+                const int ja = perm[a], jb = perm[b];
+                const double dx = __dadd_rn(crd[2 * ja], -crd[2 * jb]);
+                const double dy = __dadd_rn(crd[2 * ja + 1], -crd[2 * jb + 1]);
+                coincident |= (dx == 0.0 && dy == 0.0) ? 1 : 0;
+                const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                const double phi = __dmul_rn(__dmul_rn(r, r), r);
+                Phi[(size_t)a * LDF + b] = phi;
+                Phi[(size_t)b * LDF + a] = phi;
+            }
+            for (int a = lane; a < n; a += 32) {
+                Phi[(size_t)a * LDF + a] = 0.0;
+                const int ja = perm[a];
+                const double xh = crd[2 * ja], yh = crd[2 * ja + 1];
+                fv[a] = __dmul_rn(9.0, __dsqrt_rn(__dadd_rn(__dmul_rn(xh, xh), __dmul_rn(yh, yh))));
+            }
+        }
+        singular |= __any_sync(0xffffffffu, coincident) ? 1 : 0;
+        __syncwarp();
+
+        if (!singular) {
+            // X[j][k] = P[perm[s + j]][k], w0[k] = P[n][k]
+            const double* w0 = P + (size_t)n * LDS;
+            // ---- T = Phi12 - Phi11 X^T  (s x q, in place) --------------------
+            for (int e = lane; e < s * q; e += 32) {
+                const int a = e / q, j = e - (e / q) * q;
+                const double* xr = P + (size_t)perm[s + j] * LDS;
+                const double* pr = Phi + (size_t)a * LDF;
+                double acc = pr[s + j];
+                for (int k = 0; k < s; ++k) acc = fma(-pr[k], xr[k], acc);
+                Phi[(size_t)a * LDF + s + j] = acc;
+            }
+            // ---- u = f - Phi[:, 0..s) w0 ----------------------------------------
+            for (int a = lane; a < n; a += 32) {
+                const double* pr = Phi + (size_t)a * LDF;
+                double acc = fv[a];
+                for (int k = 0; k < s; ++k) acc = fma(-pr[k], w0[k], acc);
+                uv[a] = acc;
+            }
+            __syncwarp();
+            // ---- S = Phi22 - Phi21 X^T - X T (lower triangle, in place) -----
+            const int nlow = q * (q + 1) / 2;
+            for (int e = lane; e < nlow; e += 32) {
+                int j = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                while (j * (j + 1) / 2 > e) --j;
+                while ((j + 1) * (j + 2) / 2 <= e) ++j;
+                const int l = e - j * (j + 1) / 2;
+                const double* xj = P + (size_t)perm[s + j] * LDS;
+                const double* xl = P + (size_t)perm[s + l] * LDS;
+                const double* prj = Phi + (size_t)(s + j) * LDF;
+                double acc = prj[s + l];
+                for (int k = 0; k < s; ++k) {
+                    acc = fma(-prj[k], xl[k], acc);
+                    acc = fma(-xj[k], Phi[(size_t)k * LDF + s + l], acc);
+                }
+                Phi[(size_t)(s + j) * LDF + s + l] = acc;
+            }
+            // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
+            for (int j = lane; j < q; j += 32) {
+                const double* xj = P + (size_t)perm[s + j] * LDS;
+                double acc = uv[s + j];
+                for (int k = 0; k < s; ++k) acc = fma(-xj[k], uv[k], acc);
+                tv[j] = acc;
+            }
+            __syncwarp();
+            // ---- Cholesky S = L L^T (lower, in place) ----------------------------
+            for (int cI = 0; cI < q && !singular; ++cI) {
+                double* sc = Phi + (size_t)(s + cI) * LDF + s;
+                const double dcc = sc[cI];
+                if (!(dcc > 0.0) || !isfinite(dcc)) {
+                    singular = 1;
+                    break;
+                }
+                const double lcc = __dsqrt_rn(dcc);
+                const double inv = __ddiv_rn(1.0, lcc);
+                __syncwarp();
+                for (int i = cI + 1 + lane; i < q; i += 32) {
+                    double* si = Phi + (size_t)(s + i) * LDF + s;
+                    si[cI] = __dmul_rn(si[cI], inv);
+                }
+                if (lane == 0) sc[cI] = lcc;
+                __syncwarp();
+                // trailing lower triangle: S[i][j] -= L[i][c] L[j][c], c < j <= i
+                const int rem = q - cI - 1, ntr = rem * (rem + 1) / 2;
+                for (int e = lane; e < ntr; e += 32) {
+                    int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                    while (i * (i + 1) / 2 > e) --i;
+                    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                    const int j = e - i * (i + 1) / 2;
+                    double* si = Phi + (size_t)(s + cI + 1 + i) * LDF + s;
+                    const double* sj = Phi + (size_t)(s + cI + 1 + j) * LDF + s;
+                    si[cI + 1 + j] = fma(-si[cI], sj[cI], si[cI + 1 + j]);
+                }
+                __syncwarp();
+            }
+        }
+        if (!singular) {
+            // ---- forward (L y = t) and back (L^T z = y) substitution -------------
+            for (int cI = 0; cI < q; ++cI) {
+                const double* sc = Phi + (size_t)(s + cI) * LDF + s;
+                const double yc = __ddiv_rn(tv[cI], sc[cI]);
+                __syncwarp();
+                for (int i = cI + 1 + lane; i < q; i += 32)
+                    tv[i] = fma(-Phi[(size_t)(s + i) * LDF + s + cI], yc, tv[i]);
+                if (lane == 0) tv[cI] = yc;
+                __syncwarp();
+            }
+            for (int cI = q - 1; cI >= 0; --cI) {
+                const double* sc = Phi + (size_t)(s + cI) * LDF + s;
+                const double zc = __ddiv_rn(tv[cI], sc[cI]);
+                __syncwarp();
+                for (int i = lane; i < cI; i += 32) tv[i] = fma(-sc[i], zc, tv[i]);
+                if (lane == 0) tv[cI] = zc;
+                __syncwarp();
+            }
+            // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
+            const double* w0 = P + (size_t)n * LDS;
+            for (int k = lane; k < s; k += 32) {
+                double acc = w0[k];
+                for (int j = 0; j < q; ++j) acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
+                wv[k] = acc;
+            }
+            for (int j = lane; j < q; j += 32) wv[s + j] = tv[j];
+            __syncwarp();
+        }
+
+        // ---- scale back to the caller's order --------------------------------
+        double* wout = w + (int64_t)node * n;
+        int nonfinite = 0;
+        for (int a = lane; a < n; a += 32) {
+            const double v = singular ? 0.0 : __ddiv_rn(wv[a], delta2);
+            nonfinite |= isfinite(v) ? 0 : 1;
+            wv[a] = v;
+        }
+        const int fail = (singular || __any_sync(0xffffffffu, nonfinite)) ? 1 : 0;
+        __syncwarp();
+        for (int a = lane; a < n; a += 32) wout[singular ? a : perm[a]] = fail ? 0.0 : wv[a];
+        if (node_status && lane == 0) node_status[node] = fail;
+        __syncwarp();
+    }
+}
+
+// Warps per block maximising resident warps per SM for a per-warp shared
+// memory footprint (228 KB per SM, 1 KB reserved per block, <= 32 blocks).
+int warps_per_block_for(size_t per_warp, size_t* smem_bytes) {
+    int best_w = 1, best_res = 0;
+    for (int wpb = 1; wpb <= 4; ++wpb) {
+        const size_t blk = per_warp * wpb;
+        if (blk > 227 * 1024) break;
+        int blocks = (int)(233472 / (blk + 1024));
+        blocks = std::min(blocks, 32);
+        const int res = std::min(blocks * wpb, 64);
+        if (res >= best_res) {
+            best_res = res;
+            best_w = wpb;
+        }
+    }
+    *smem_bytes = per_warp * best_w;
+    return best_w;
+}
+
 int weights_warps_per_block(const WeightsGeom& g, size_t* smem_bytes) {
-    // one warp per block when a warp needs a lot of shared memory (m = 6),
-    // four otherwise; the per-SM residency is then set by shared memory.
-    const size_t per_warp = (size_t)g.smem_doubles * sizeof(double);
-    int wpb = 4;
-    while (wpb > 1 && per_warp * wpb > 227 * 1024) --wpb;
-    *smem_bytes = per_warp * wpb;
-    return wpb;
+    return warps_per_block_for((size_t)g.smem_doubles * sizeof(double), smem_bytes);
 }
 
 }  // namespace
@@ -292,20 +649,44 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
     if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
     const int s = (m + 1) * (m + 2) / 2;
     if (n < s) return RBFFD_ERR_INVALID_ARG;
-    WeightsGeom g = weights_geom(n, m);
-    size_t smem = 0;
-    const int wpb = weights_warps_per_block(g, &smem);
-    if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;  // system too large for one SM
-    RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    int per_sm = 0;
-    RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_kernel, 32 * wpb, smem));
-    if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
-    const int64_t need = (N + wpb - 1) / wpb;
-    const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
-    weights_kernel<<<blocks, 32 * wpb, smem, as_stream(stream)>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n,
-                                                                  m, g.s, g.M, g.LD, g.coords_in_zero_block,
-                                                                  g.smem_doubles, w, node_status);
+    cudaStream_t st = as_stream(stream);
+    // RBFFD_WEIGHTS=lu selects the full-system Gaussian elimination kernel
+    // (kept for comparison); the default is the null-space elimination.
+    const char* sel = std::getenv("RBFFD_WEIGHTS");
+    // The null-space form needs r^3 to be positive definite on the null
+    // space of P^T, which holds once P contains the linear monomials (m >= 1).
+    const bool use_lu = (sel && std::strcmp(sel, "lu") == 0) || m < 1;
+    if (use_lu) {
+        WeightsGeom g = weights_geom(n, m);
+        size_t smem = 0;
+        const int wpb = weights_warps_per_block(g, &smem);
+        if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;  // system too large for one SM
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0;
+        RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_kernel, 32 * wpb, smem));
+        if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
+        const int64_t need = (N + wpb - 1) / wpb;
+        const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
+        weights_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m, g.s,
+                                                       g.M, g.LD, g.coords_in_zero_block, g.smem_doubles, w,
+                                                       node_status);
+    } else {
+        NsGeom g = ns_geom(n, m);
+        size_t smem = 0;
+        const int wpb = warps_per_block_for((size_t)g.bytes, &smem);
+        if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;
+        RBFFD_CUDA_TRY(
+            cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0;
+        RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_ns_kernel, 32 * wpb, smem));
+        if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
+        const int64_t need = (N + wpb - 1) / wpb;
+        const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
+        weights_ns_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m,
+                                                          g.s, g.LDF, g.LDS, g.bytes, w, node_status);
+    }
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

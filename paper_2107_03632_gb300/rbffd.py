@@ -309,7 +309,7 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
 
 
 # -------------------------------------------------------------------- solve --
-def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_outer=200, jacobi=True):
+def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_outer=1000, jacobi=True):
     """Solver options.  inner_tol: residual reduction per restarted pass
     (default 1e-3 for FP64, 1e-5 for mixed)."""
     prec = {"fp64": 0, "mixed": 1}[precision]

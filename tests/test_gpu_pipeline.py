@@ -91,9 +91,22 @@ def test_stencils_invalid_args(lib):
 
 
 # ------------------------------------------------------------------- weights --
+@pytest.fixture(params=["nullspace", "lu"])
+def weights_kernel(request, monkeypatch):
+    """Both weight kernels: the default null-space elimination and the full
+    Gaussian elimination kept for comparison (RBFFD_WEIGHTS=lu)."""
+    if request.param == "lu":
+        monkeypatch.setenv("RBFFD_WEIGHTS", "lu")
+    else:
+        monkeypatch.delenv("RBFFD_WEIGHTS", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("h,m,n,tol", [(0.04, 2, 12, 1e-9), (0.04, 4, 30, 1e-9), (0.08, 6, 56, 1e-7),
-                                       (0.08, 2, 20, 1e-9), (0.08, 4, 45, 1e-9), (0.1, 6, 60, 1e-7)])
-def test_weights_vs_oracle(lib, h, m, n, tol):
+                                       (0.08, 2, 20, 1e-9), (0.08, 4, 45, 1e-9), (0.1, 6, 60, 1e-7),
+                                       (0.1, 2, 6, 1e-9), (0.1, 4, 15, 1e-9), (0.06, 6, 100, 1e-7),
+                                       (0.1, 8, 90, 1e-7), (0.05, 1, 8, 1e-9), (0.05, 0, 5, 1e-9)])
+def test_weights_vs_oracle(lib, weights_kernel, h, m, n, tol):
     from paper_2107_03632_gb300 import rbffd
 
     d = disk_nodes(h)
@@ -105,7 +118,7 @@ def test_weights_vs_oracle(lib, h, m, n, tol):
     assert rel_rowwise(w, w_ref) <= tol
 
 
-def test_weights_singular_stencil_flagged(lib):
+def test_weights_singular_stencil_flagged(lib, weights_kernel):
     """Coincident nodes make the system singular: status 1, zero weights."""
     from paper_2107_03632_gb300 import rbffd
 
@@ -123,7 +136,7 @@ def test_weights_singular_stencil_flagged(lib):
     assert np.all(w.cpu().numpy()[st == 1] == 0.0)
 
 
-def test_weights_out_of_range_index_flagged(lib):
+def test_weights_out_of_range_index_flagged(lib, weights_kernel):
     from paper_2107_03632_gb300 import rbffd
 
     d = disk_nodes(0.1)
@@ -289,3 +302,15 @@ def test_pipeline_end_to_end_small(lib):
     uh = uh.cpu().numpy()
     assert np.abs(uh - ref).max() / np.abs(ref).max() <= 1e-8
     assert np.abs(uh - u).max() < 2e-2  # discretisation error at h = 0.04, m = 2
+
+
+def test_weights_collinear_stencil_flagged(lib, weights_kernel):
+    """Nodes on one line cannot determine quadratics: P is rank deficient."""
+    from paper_2107_03632_gb300 import rbffd
+
+    t = np.linspace(-1.0, 1.0, 40)
+    xy = np.ascontiguousarray(np.stack([t, 0.5 * t], axis=1))
+    idx = oracle.knn(xy, 12)
+    w, st = rbffd.rbffd_weights(T(xy), T(idx), 2)
+    _, st_ref = oracle.weights(xy, idx, 2)
+    assert st.cpu().numpy().all() and st_ref.all()
