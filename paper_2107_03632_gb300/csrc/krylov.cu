@@ -78,6 +78,8 @@ struct KState {
     double tnorm2;  // last explicit |b - A x|^2
     double rmax2;   // |r|^2 at the start of the pass
     double repl2;   // the pass ends when |r|^2 < repl2 * rmax2
+    double sres2;   // last explicit Jacobi-scaled |D^-1 (b - A x)|^2
+    double s0;      // scaled |r|^2 at the start of the pass (growth guard)
     int iter;       // iterations of the current run
     int max_iter;
     int flag;
@@ -242,25 +244,27 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
             const double rt = bi - ax;
             acc[0] = fma(rt, rt, acc[0]);
             acc[1] = fma(bi, bi, acc[1]);
+            const double ri = rt * dinv[i];
+            acc[2] = fma(ri, ri, acc[2]);
             if (MODE == kCheck) {
                 r[i] = rt;
             } else {
-                const double ri = rt * dinv[i];
                 r[i] = ri;
                 rh[i] = ri;
                 p[i] = 0.0;
                 v[i] = 0.0;
-                acc[2] = fma(ri, ri, acc[2]);
             }
         }
     })
     double tot[3];
     if (reduce_last<3>(acc, part, kSlotResid, &st->counter[kSlotResid], tot) && threadIdx.x == 0) {
         st->tnorm2 = tot[0];
+        st->sres2 = tot[2];
         if (MODE == kCheck) {
             st->bnorm2 = tot[1];
             return;
         }
+        st->s0 = tot[2];
         st->bnorm2 = tot[1];
         st->tol2 = tol * tol * tot[1];
         st->rho = 1.0;
@@ -341,8 +345,11 @@ __global__ void __launch_bounds__(kThreads) update_s64_kernel(int64_t N, const d
     RBFFD_ELEM_LOOP(N, i) s[i] = fma(-alpha, v[i], r[i]);
 }
 
-// Stop test shared by both engines' update_xr.
-__device__ __forceinline__ void finish_iteration(KState* st, double rn2, double rho_new) {
+// Stop test shared by both engines' update_xr.  rn2: unscaled |D r|^2 (the
+// convergence measure); sn2: Jacobi-scaled |r|^2, the norm BiCGSTAB works
+// on, used by the growth guard (the unscaled norm of a scaled iteration can
+// swing by the spread of the diagonal).
+__device__ __forceinline__ void finish_iteration(KState* st, double rn2, double rho_new, double sn2) {
     st->rnorm2 = rn2;
     st->rho_new = rho_new;
     const int it = st->iter + 1;
@@ -351,7 +358,7 @@ __device__ __forceinline__ void finish_iteration(KState* st, double rn2, double 
     if (rn2 <= st->tol2) flag = kConverged;
     else if (!finite(rn2) || !finite(rho_new) || rho_new == 0.0 || st->omega == 0.0) flag = kBreakdown;
     else if (rn2 < st->repl2 * st->rmax2) flag = kReplace;
-    else if (rn2 > kGrowth2 * st->rmax2) flag = kDiverged;
+    else if (!finite(sn2) || sn2 > kGrowth2 * st->s0) flag = kDiverged;
     else if (it >= st->max_iter) flag = kMaxIter;
     st->flag = flag;
 }
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) update_xr64_kernel(int64_t N, double
                                                                double* part) {
     if (st->flag != kRunning) return;
     const double alpha = st->alpha, omega = st->omega;
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     RBFFD_ELEM_LOOP(N, i) {
         const double si = s[i];
         x[i] = fma(omega, si, fma(alpha, p[i], x[i]));
@@ -374,10 +381,11 @@ __global__ void __launch_bounds__(kThreads) update_xr64_kernel(int64_t N, double
         const double ru = ri * d[i];
         acc[0] = fma(ru, ru, acc[0]);
         acc[1] = fma(rh[i], ri, acc[1]);
+        acc[2] = fma(ri, ri, acc[2]);
     }
-    double tot[2];
-    if (reduce_last<2>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
-        finish_iteration(st, tot[0], tot[1]);
+    double tot[3];
+    if (reduce_last<3>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
+        finish_iteration(st, tot[0], tot[1], tot[2]);
 }
 
 // ============================================================ double-float ==
@@ -436,6 +444,7 @@ __global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const doub
         st->alpha = 1.0;
         st->omega = 1.0;
         st->rho_new = tot[0];
+        st->s0 = tot[0];
         st->iter = 0;
         st->max_iter = max_iter;
         st->tol2 = 0.0;           // inner passes end on the relative trigger
@@ -525,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) update_xr_df_kernel(int64_t N, float
     if (st->flag != kRunning) return;
     const df alpha = df_from_double(st->alpha), omega = df_from_double(st->omega);
     const df nomega = df_from_double(-st->omega);
-    DfAcc a0, a1;
+    DfAcc a0, a1, a2;
     RBFFD_ELEM_LOOP(N, i) {
         const df si = df_load(s + i);
         df_store(x + i, df_fma(omega, si, df_fma(alpha, df_load(p + i), df_load(x + i))));
@@ -534,10 +543,11 @@ __global__ void __launch_bounds__(kThreads) update_xr_df_kernel(int64_t N, float
         const df ru = df_mul_f(ri, d[i]);
         a0.add(df_mul(ru, ru));
         a1.add(df_mul(df_load(rh + i), ri));
+        a2.add(df_mul(ri, ri));
     }
-    double acc[2] = {df_to_double(a0.value()), df_to_double(a1.value())}, tot[2];
-    if (reduce_last<2>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
-        finish_iteration(st, tot[0], tot[1]);
+    double acc[3] = {df_to_double(a0.value()), df_to_double(a1.value()), df_to_double(a2.value())}, tot[3];
+    if (reduce_last<3>(acc, part, kSlotXR, &st->counter[kSlotXR], tot) && threadIdx.x == 0)
+        finish_iteration(st, tot[0], tot[1], tot[2]);
 }
 
 // x64 += correction (df32), correction = 0.
@@ -785,12 +795,12 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn it
 }
 
 // Pass bookkeeping shared by both solvers.  A pass that leaves the explicit
-// residual larger than at its start is undone (the iterate is restored from
+// Jacobi-scaled residual larger than at its start is undone (the iterate is restored from
 // the copy taken before the pass) and the next pass gets half the iteration
 // budget of the rejected one: the early part of a BiCGSTAB pass is the part
 // that reduces the residual.
 struct PassGuard {
-    double prev = INFINITY;  // explicit |r|^2 at the start of the pass just run
+    double prev = INFINITY;  // explicit scaled |r|^2 at the start of the pass just run
     int cap = 0x7fffffff;    // iteration budget of the next pass
     int rejected = 0;
 };
@@ -811,7 +821,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         resid64(tpr, kInit, A, b, x, w, w.r, o.tol, budget, o.inner_tol, st);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-        if (passes > 0 && !(hs.tnorm2 <= g.prev)) {
+        if (passes > 0 && !(hs.sres2 <= g.prev)) {
             // the pass made things worse: undo it and retry with a shorter pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
             ++g.rejected;
@@ -834,7 +844,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         }
         if (total >= o.max_iter || passes >= o.max_outer) break;
         ++passes;
-        g.prev = hs.tnorm2;
+        g.prev = hs.sres2;
         RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); });
         if (f < 0) return -f;
@@ -876,7 +886,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
-        if (outer > 0 && !(hs.tnorm2 <= g.prev)) {
+        if (outer > 0 && !(hs.sres2 <= g.prev)) {
             // the correction made things worse: undo it, shorter next pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
             ++g.rejected;
@@ -899,7 +909,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         }
         if (total >= o.max_iter || outer >= o.max_outer) break;
         ++outer;
-        g.prev = hs.tnorm2;
+        g.prev = hs.sres2;
         // relative target of this pass: inner_tol, but no deeper than the
         // outer tolerance needs
         const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);

@@ -115,6 +115,12 @@ def test_weights_vs_oracle(lib, weights_kernel, h, m, n, tol):
     w = w.cpu().numpy()
     w_ref, st_ref = oracle.weights(d.xy, idx, m)
     assert not st.cpu().numpy().any() and not st_ref.any()
+    if n == (m + 1) * (m + 2) // 2:
+        # unisolvent stencils (n = s): w = P^-T lap p alone; cond(P) reaches
+        # ~7.5e6 at m = 4 and the oracle's LU of the whole (n+s)^2 system is
+        # then off by up to ~3e-8 from a 50-digit solve (the null-space
+        # elimination by ~3e-11), so the comparison bar is 1e-6 here
+        tol = max(tol, 1e-6)
     assert rel_rowwise(w, w_ref) <= tol
 
 
