@@ -418,7 +418,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     bpos = op;
                 }
             }
-            if (best == 0 || best >= 0x7ff0000000000000ull) {  // rank deficient or non-finite
+            // rank deficient (pivot below 1e-12: P's entries are monomials of
+            // points in the unit disk, so |P| <= 1) or non-finite
+            if (__longlong_as_double((long long)best) < 1e-12 || best >= 0x7ff0000000000000ull) {
                 singular = 1;
                 break;
             }
