@@ -262,7 +262,9 @@ def run_gpu(args):
         if ev:
             ev[3].record()
         x.zero_()
-        _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve)
+        _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve, raise_on_error=False)
+        if info["status_code"] not in (0, 4):
+            raise rbffd.RbffdError(info["status_code"], "rbffd_solve")
         if ev:
             ev[4].record()
         return info
@@ -358,6 +360,7 @@ def run_gpu(args):
                      "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2],
                                    "solve": st64[3]},
                      "iters": [i["iters"] for i in infos64], "passes": [i["outer_sweeps"] for i in infos64],
+                     "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos64],
                      "rel_residual": [i["rel_residual"] for i in infos64],
                      "spmv_kernel": "spmv64_kernel", "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm,
                      "spmv_ms_per_launch": sp64_ms}
@@ -385,6 +388,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
         "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "solve": st_ms[3]},
         "solve": {"iters": iters, "refinements": [i["outer_sweeps"] for i in infos],
+                  "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos],
                   "rel_residual": [i["rel_residual"] for i in infos], "max_err_vs_exact": err_exact},
         "fp64": fp64_line,
         "roofline": {"kernel": "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)", "bound": "hbm",

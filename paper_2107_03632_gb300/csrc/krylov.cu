@@ -172,6 +172,52 @@ __device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr,
     return sum;
 }
 
+// b_i - sum_k a_k x[col_k] for one row with compensated arithmetic: each
+// product split exactly by FMA (p + e = a x) and the running sum kept as an
+// unevaluated pair (TwoSum, Knuth), so the residual is accurate to about
+// eps |r_i| instead of eps sum |a x| (the latter reaches 1e-10 of |b| on the
+// finest m = 6 workload).  Used for the explicit residuals that decide
+// convergence and restart every pass; ~10 FP64 operations per entry.
+__device__ __forceinline__ void two_sum64(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    const double bb = __dadd_rn(s, -a);
+    e = __dadd_rn(__dadd_rn(a, -__dadd_rn(s, -bb)), __dadd_rn(b, -bb));
+}
+
+template <int TPR>
+__device__ __forceinline__ double row_residual64(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                 const double* __restrict__ val, const double* __restrict__ x,
+                                                 int64_t row, int sub, bool valid, double bi) {
+    int64_t a = 0, e = 0;
+    if (valid) {
+        a = __ldg(row_ptr + row);
+        e = __ldg(row_ptr + row + 1);
+    }
+    double sh = 0.0, sl = 0.0;
+#pragma unroll 2
+    for (int64_t k = a + sub; k < e; k += TPR) {
+        const double av = __ldg(val + k), xv = __ldg(x + __ldg(col + k));
+        const double p = __dmul_rn(av, xv);
+        const double pe = fma(av, xv, -p);
+        double t, te;
+        two_sum64(sh, p, t, te);
+        sh = t;
+        sl = __dadd_rn(sl, __dadd_rn(te, pe));
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) {
+        const double oh = __shfl_xor_sync(0xffffffffu, sh, o, TPR);
+        const double ol = __shfl_xor_sync(0xffffffffu, sl, o, TPR);
+        double t, te;
+        two_sum64(sh, oh, t, te);
+        sh = t;
+        sl = __dadd_rn(sl, __dadd_rn(ol, te));
+    }
+    double rh, rl;
+    two_sum64(bi, -sh, rh, rl);
+    return __dadd_rn(rh, __dadd_rn(rl, -sl));
+}
+
 // ---- setup: diagonal, row sums, Jacobi scaling, validation -----------------
 __global__ void __launch_bounds__(kThreads) setup_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int* __restrict__ col,
@@ -228,10 +274,9 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
     const int sub = threadIdx.x & (TPR - 1);
     double acc[3] = {0.0, 0.0, 0.0};
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
-        const double ax = row_dot64<TPR>(row_ptr, col, val, x, i, sub, valid);
+        const double bi = valid ? b[i] : 0.0;
+        const double rt = row_residual64<TPR>(row_ptr, col, val, x, i, sub, valid, bi);
         if (valid && sub == 0) {
-            const double bi = b[i];
-            const double rt = bi - ax;
             acc[0] = fma(rt, rt, acc[0]);
             acc[1] = fma(bi, bi, acc[1]);
             const double ri = rt * dinv[i];
@@ -800,7 +845,22 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn it
 struct PassGuard {
     double prev = INFINITY;  // explicit scaled |r|^2 at the start of the pass just run
     int cap = 0x7fffffff;    // iteration budget of the next pass
-    int rejected = 0;
+    int last_iters = 0;      // iterations of the pass just run
+    int rejected = 0;        // passes undone in a row
+    int rejected_total = 0;
+    // Called when the explicit residual after a pass is not below the one
+    // before it.  Returns false once retrying is pointless: the pass was a
+    // single iteration already (the iterate sits at the rounding floor of
+    // the explicit residual) or passes were undone 12 times in a row.
+    bool reject() {
+        ++rejected;
+        ++rejected_total;
+        prev = INFINITY;
+        if (last_iters <= 1 || rejected > 12) return false;
+        cap = std::max(last_iters / 2, 1);
+        return true;
+    }
+    void accept() { rejected = 0; }
 };
 
 int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve_opts& o, const Work& w,
@@ -822,11 +882,19 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         if (passes > 0 && !(hs.sres2 <= g.prev)) {
             // the pass made things worse: undo it and retry with a shorter pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            if (trace_on()) fprintf(stderr, "[rbffd] pass rejected (explicit residual grew), retry shorter\n");
-            ++g.rejected;
-            g.prev = INFINITY;
+            const bool retry = g.reject();
+            if (trace_on()) fprintf(stderr, "[rbffd fp64] pass undone, %s\n", retry ? "retry shorter" : "stop");
+            if (!retry) {
+                resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, 0.0, st);
+                RBFFD_LAUNCH_CHECK();
+                if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+                rel = rel_of(hs);
+                status = rel <= o.tol ? RBFFD_OK : RBFFD_ERR_NOT_CONVERGED;
+                break;
+            }
             continue;
         }
+        g.accept();
         if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
             rel = 0.0;
             status = RBFFD_OK;
@@ -852,7 +920,8 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         if (trace_on())
             fprintf(stderr, "[rbffd fp64] pass %d: %d its, flag %d, recurrence |r|/|r0| %.3e, rel at start %.3e\n",
                     passes, hs.iter, hs.flag, std::sqrt(hs.rnorm2 / start2), rel);
-        g.cap = (hs.flag == kDiverged || hs.flag == kBreakdown) ? std::max(hs.iter / 2, 8) : 0x7fffffff;
+        g.last_iters = hs.iter;
+        if (g.rejected == 0) g.cap = 0x7fffffff;
         if (hs.flag == kBreakdown) {
             if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
@@ -869,7 +938,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     info->status = status;
     info->iters = total;
     info->outer_sweeps = passes;
-    info->restarts = g.rejected;
+    info->restarts = g.rejected_total;
     info->rel_residual = rel;
     return status;
 }
@@ -892,11 +961,19 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         if (outer > 0 && !(hs.sres2 <= g.prev)) {
             // the correction made things worse: undo it, shorter next pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            if (trace_on()) fprintf(stderr, "[rbffd] pass rejected (explicit residual grew), retry shorter\n");
-            ++g.rejected;
-            g.prev = INFINITY;
+            const bool retry = g.reject();
+            if (trace_on()) fprintf(stderr, "[rbffd mixed] pass undone, %s\n", retry ? "retry shorter" : "stop");
+            if (!retry) {
+                resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
+                RBFFD_LAUNCH_CHECK();
+                if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+                rel = rel_of(hs);
+                status = rel <= o.tol ? RBFFD_OK : RBFFD_ERR_NOT_CONVERGED;
+                break;
+            }
             continue;
         }
+        g.accept();
         if (hs.bnorm2 == 0.0 && hs.tnorm2 == 0.0) {
             rel = 0.0;
             status = RBFFD_OK;
@@ -930,7 +1007,8 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         if (trace_on())
             fprintf(stderr, "[rbffd mixed] pass %d: %d its, flag %d, inner |r|/|r0| %.3e, rel at start %.3e\n", outer,
                     hs.iter, hs.flag, std::sqrt(hs.rnorm2 / start2), rel);
-        g.cap = (hs.flag == kDiverged || hs.flag == kBreakdown) ? std::max(hs.iter / 2, 8) : 0x7fffffff;
+        g.last_iters = hs.iter;
+        if (g.rejected == 0) g.cap = 0x7fffffff;
         RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         refine_kernel<<<grid_of(refine_kernel), kThreads, 0, st>>>(N, x, w.xd);
         note_launches(1);
@@ -951,7 +1029,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     info->status = status;
     info->iters = total;
     info->outer_sweeps = outer;
-    info->restarts = g.rejected;
+    info->restarts = g.rejected_total;
     info->rel_residual = rel;
     return status;
 }
