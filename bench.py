@@ -325,21 +325,25 @@ def run_gpu(args):
     # ---- end to end through the API from pinned host buffers ----
     h2d = (h_xy.numel() * 8 + h_mask.numel() + h_f.numel() * 8 + h_g.numel() * 8)
     d2h = N * 8
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(max(args.e2e_steps, 1)):
-        xy.copy_(h_xy, non_blocking=True)
-        mask.copy_(h_mask, non_blocking=True)
-        fT.copy_(h_f, non_blocking=True)
-        gT.copy_(h_g, non_blocking=True)
-        step("mixed")
-        h_u.copy_(x, non_blocking=True)
-    e1.record()
-    barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-    e2e_value = ws * N * max(args.e2e_steps, 1) / (ms_e2e * 1e-3)
+    e2e_value = None
+    if args.e2e_steps > 0:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.e2e_steps):
+            xy.copy_(h_xy, non_blocking=True)
+            mask.copy_(h_mask, non_blocking=True)
+            fT.copy_(h_f, non_blocking=True)
+            gT.copy_(h_g, non_blocking=True)
+            step("mixed")
+            h_u.copy_(x, non_blocking=True)
+        e1.record()
+        barrier()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        e2e_value = ws * N * args.e2e_steps / (ms_e2e * 1e-3)
+    else:
+        h_u.copy_(x)
 
     # ---- correctness of the timed solves (host check, outside timing) ----
     err_exact = float(np.abs(h_u.numpy() - u_ex).max())
@@ -365,7 +369,7 @@ def run_gpu(args):
                      "spmv_kernel": "spmv64_kernel", "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm,
                      "spmv_ms_per_launch": sp64_ms}
 
-    fp64_peak = fp64_peak_tflops(torch, dev)
+    fp64_peak = fp64_peak_tflops(torch, dev) if not args.no_peak_probe else float("nan")
     w_flops = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M + 15.0 * n * (n - 1) / 2.0)
     w_tflops = w_flops / (st_ms[1] * 1e-3) / 1e12
 
@@ -399,8 +403,8 @@ def run_gpu(args):
         "weights_roofline": {"bound": "fp64", "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                              "frac": w_tflops / fp64_peak, "peak_kind": "measured cuBLAS DGEMM 4096^3",
                              "flops_per_node": w_flops / N},
-        "e2e": {"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": max(args.e2e_steps, 1)},
+        "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "steps": args.e2e_steps} if e2e_value is not None else None),
         "gpu_launches": prof["launches"],
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -426,6 +430,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peak-probe", action="store_true", help="skip the cuBLAS DGEMM FP64 peak probe")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -838,10 +838,11 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn it
 }
 
 // Pass bookkeeping shared by both solvers.  A pass that leaves the explicit
-// Jacobi-scaled residual larger than at its start is undone (the iterate is restored from
-// the copy taken before the pass) and the next pass gets half the iteration
-// budget of the rejected one: the early part of a BiCGSTAB pass is the part
-// that reduces the residual.
+// Jacobi-scaled residual larger than at its start is undone (the iterate is
+// restored from the copy taken before the pass) and later passes get half
+// the iteration budget of the undone one (growing again by a quarter per
+// kept pass): the early part of a BiCGSTAB pass is the part that reduces
+// the residual.
 struct PassGuard {
     double prev = INFINITY;  // explicit scaled |r|^2 at the start of the pass just run
     int cap = 0x7fffffff;    // iteration budget of the next pass
@@ -860,7 +861,13 @@ struct PassGuard {
         cap = std::max(last_iters / 2, 1);
         return true;
     }
-    void accept() { rejected = 0; }
+    // A pass was kept: the budget found by halving stays in force (long
+    // passes on these matrices tend to diverge again from the same kind of
+    // residual) and grows by a quarter per kept pass.
+    void accept() {
+        rejected = 0;
+        if (cap < 0x7fffffff / 2) cap += std::max(cap / 4, 1);
+    }
 };
 
 int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve_opts& o, const Work& w,
@@ -921,7 +928,6 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
             fprintf(stderr, "[rbffd fp64] pass %d: %d its, flag %d, recurrence |r|/|r0| %.3e, rel at start %.3e\n",
                     passes, hs.iter, hs.flag, std::sqrt(hs.rnorm2 / start2), rel);
         g.last_iters = hs.iter;
-        if (g.rejected == 0) g.cap = 0x7fffffff;
         if (hs.flag == kBreakdown) {
             if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
@@ -1008,7 +1014,6 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
             fprintf(stderr, "[rbffd mixed] pass %d: %d its, flag %d, inner |r|/|r0| %.3e, rel at start %.3e\n", outer,
                     hs.iter, hs.flag, std::sqrt(hs.rnorm2 / start2), rel);
         g.last_iters = hs.iter;
-        if (g.rejected == 0) g.cap = 0x7fffffff;
         RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         refine_kernel<<<grid_of(refine_kernel), kThreads, 0, st>>>(N, x, w.xd);
         note_launches(1);
