@@ -27,9 +27,12 @@ are w = wh / delta^2.  Monomials are in graded order
 at xh = 0 only x^2 and y^2 have a nonzero Laplacian (2).
 
 The solve is LAPACK's LU with partial pivoting (numpy.linalg.solve), applied
-per stencil.  A stencil holding two coincident nodes has two identical rows
-(and columns) in Phi and P, so its system is singular by definition; such
-stencils, and systems whose solve fails or is not finite, get status 1.
+per stencil.  The system is singular when two stencil nodes coincide (two
+identical rows and columns) or when P lacks full column rank (the nodes do
+not determine the polynomials, e.g. all on one line); rank is read from the
+singular values of P (smallest below 1e-12 of the largest: P's entries are
+monomials of points in the unit disk).  Such stencils, and systems whose
+solve fails or is not finite, get status 1.
 """
 
 from __future__ import annotations
@@ -110,6 +113,8 @@ def weights(xy: np.ndarray, idx: np.ndarray, m: int, nodes=None, chunk: int = 20
         dyy = xs[:, :, None, 1] - xs[:, None, :, 1]
         off = ~np.eye(n, dtype=bool)[None]
         dup = ((dxx == 0.0) & (dyy == 0.0) & off).any(axis=(1, 2))
+        sv = np.linalg.svd(A[:, :n, n:], compute_uv=False)
+        dup |= ~(sv[:, -1] > 1e-12 * sv[:, 0])
         try:
             sol = np.linalg.solve(A, rhs[..., None])[..., 0]
             bad = ~np.isfinite(sol).all(axis=1)

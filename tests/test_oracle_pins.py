@@ -380,3 +380,15 @@ def test_weights_coincident_nodes_flagged_singular():
     holds_both = np.array([(4 in row) and (5 in row) for row in idx])
     assert np.array_equal(st.astype(bool), holds_both)
     assert np.all(w[holds_both] == 0.0)
+
+
+def test_weights_rank_deficient_stencil_flagged():
+    """All nodes on one line: P (monomials to degree 2) has rank 3 < 6, so every
+    system is singular; a jittered disk has no such stencil."""
+    t = np.linspace(-1.0, 1.0, 40)
+    xy = np.ascontiguousarray(np.stack([t, 0.5 * t], axis=1))
+    w, st = oracle.weights(xy, oracle.knn(xy, 12), 2)
+    assert st.all() and np.all(w == 0.0)
+    d = disk_nodes(0.08)
+    _, st = oracle.weights(d.xy, oracle.knn(d.xy, 56), 6)
+    assert not st.any()
