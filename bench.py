@@ -113,6 +113,25 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of the inner-solve SpMV from one ncu capture (see
+# profiles/spmv_df_kernel_disk_1M_m4_n30.md): dram read + write per launch
+# divided by the kernel's algorithmic bytes at that size.  The ratio scales
+# the capture to a full-size launch (traffic grows with the matrix) and is
+# valid only while the kernel's source is the one captured.
+SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorithmic": (271.693312e6 + 8.42624e6)
+                   / 279652728.0}
+
+
+def spmv_df_source_hash():
+    import hashlib
+
+    src = open(os.path.join(ROOT, "paper_2107_03632_gb300", "csrc", "krylov.cu")).read()
+    a = src.index("// ============================================================ double-float ==")
+    b = src.index("__global__ void __launch_bounds__(kThreads) update_s_df_kernel")
+    seg = src[a:b] + open(os.path.join(ROOT, "paper_2107_03632_gb300", "csrc", "df32.cuh")).read()
+    return hashlib.sha256(seg.encode()).hexdigest()[:16]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -120,6 +139,19 @@ def measured_peaks():
             d = json.load(f)
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def weights_flops(n: int, m: int) -> float:
+    """FP64 flops per node of the null-space weight solve (division and square
+    root counted as one flop each): scaling 2n, monomials ~n s, Gauss-Jordan
+    on P (2s - 1)(n s - s(s-1)/2), kernel matrix 4 n(n-1) + 5n, T = 2 s^2 q,
+    u = 2 n s, S (lower) 2 s q (q+1), t = 2 q s, Cholesky q^3/3 + q^2/2 + 2q,
+    substitutions 2 q^2 + 2q, w = 2 s q, output n."""
+    s = (m + 1) * (m + 2) // 2
+    q = n - s
+    return (2 * n + n * s + (2 * s - 1) * (n * s - s * (s - 1) / 2) + 4 * n * (n - 1) + 5 * n + 2 * s * s * q
+            + 2 * n * s + 2 * s * q * (q + 1) + 2 * q * s + q ** 3 / 3 + q * q / 2 + 2 * q + 2 * q * q + 2 * q
+            + 2 * s * q + n)
 
 
 def fp64_peak_tflops(torch, dev):
@@ -370,8 +402,9 @@ def run_gpu(args):
                      "spmv_ms_per_launch": sp64_ms}
 
     fp64_peak = fp64_peak_tflops(torch, dev) if not args.no_peak_probe else float("nan")
-    w_flops = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M + 15.0 * n * (n - 1) / 2.0)
+    w_flops = N * weights_flops(n, m)
     w_tflops = w_flops / (st_ms[1] * 1e-3) / 1e12
+    lu_equiv = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M) / (st_ms[1] * 1e-3) / 1e12
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -397,12 +430,16 @@ def run_gpu(args):
         "fp64": fp64_line,
         "roofline": {"kernel": "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)", "bound": "hbm",
                      "achieved": sp_gbs,
-                     "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm, "traffic": None,
+                     "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm,
+                     "traffic": (SPMV_DF_TRAFFIC["traffic_over_algorithmic"] * sp_bytes
+                                 if spmv_df_source_hash() == SPMV_DF_TRAFFIC["source_sha256_16"] else None),
                      "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
                      "launches": prof["spmv32_launches"]},
-        "weights_roofline": {"bound": "fp64", "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+        "weights_roofline": {"kernel": "weights_ns_kernel (null-space elimination)", "bound": "fp64",
+                             "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                              "frac": w_tflops / fp64_peak, "peak_kind": "measured cuBLAS DGEMM 4096^3",
-                             "flops_per_node": w_flops / N},
+                             "flops_per_node": w_flops / N,
+                             "lu_equivalent_tflops": lu_equiv},
         "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "steps": args.e2e_steps} if e2e_value is not None else None),
         "gpu_launches": prof["launches"],

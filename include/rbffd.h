@@ -207,6 +207,45 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
                         void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched solve -- many independent node sets (instances) of uneven size   */
+/* and degree, each with several right-hand sides, through the whole        */
+/* pipeline of this header at once (the paper's method applied per          */
+/* instance; batching has no counterpart in the paper).                     */
+/*                                                                           */
+/* Instances are stored back to back: instance i owns nodes                 */
+/* [node_offset_i, node_offset_i + n_nodes_i) of xy (N_total x 2) and        */
+/* is_dirichlet, and the same rows of the node-major right-hand-side and    */
+/* solution arrays f, g, u (N_total x n_rhs, entry [node * n_rhs + k]).     */
+/* Per instance: stencils, weights (degree m_i, stencil size n_i), the      */
+/* block of the block-diagonal CSR, and n_rhs right-hand sides b = -f | g.  */
+/* The solve is the mixed one of rbffd_solve (float32 inner BiCGSTAB in     */
+/* double-float vectors, FP64 refinement), run for all (instance, rhs)      */
+/* pairs together: each pair has its own BiCGSTAB scalars and stops on its  */
+/* own relative residual; the inner iterations are replayed as one CUDA     */
+/* graph per chunk of iterations.  Blocks the host like rbffd_solve.        */
+/*   desc    : host array of n_inst descriptors (offsets contiguous, in      */
+/*             order: node_offset_0 = 0, node_offset_{i+1} = node_offset_i + */
+/*             n_nodes_i).                                                  */
+/*   n_rhs   : 1 <= n_rhs <= 64.                                             */
+/*   u       : N_total x n_rhs float64, in: initial guess, out: solution.    */
+/*   info    : host array of n_inst; per instance the worst right-hand side */
+/*             (largest final relative residual, most iterations).          */
+/* Returns RBFFD_OK when every pair converged, else the worst status.       */
+/* ------------------------------------------------------------------------ */
+typedef struct rbffd_batch_desc {
+    int64_t node_offset;
+    int64_t n_nodes;
+    int32_t m;
+    int32_t n;
+} rbffd_batch_desc;
+
+size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs);
+int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst, const double* xy,
+                        const uint8_t* is_dirichlet, const double* f, const double* g, int32_t n_rhs,
+                        double* u, const rbffd_solve_opts* opts, rbffd_solve_info* info, void* ws,
+                        size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Measurement hooks (no counterpart in the paper; used to report roofline   */
 /* fractions).  The library counts every kernel it launches.  With profiling */
 /* enabled it also brackets each SpMV launch of the Krylov iteration with    */

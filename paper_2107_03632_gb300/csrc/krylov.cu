@@ -706,7 +706,6 @@ int grid_of(K kernel) {
     return g;
 }
 
-int nblocks() { return std::min(kMaxBlocks, sm_count() * 4); }
 
 int64_t spmv_bytes(const rbffd_csr& A, int val_bytes) {
     return A.nnz * (int64_t)(val_bytes + 4) + 8 * (A.n_rows + 1) + 4 * 8 * A.n_rows;

@@ -91,6 +91,15 @@ class Profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [
+        ("node_offset", ctypes.c_int64),
+        ("n_nodes", ctypes.c_int64),
+        ("m", ctypes.c_int32),
+        ("n", ctypes.c_int32),
+    ]
+
+
 # (name, restype, argtypes) of every exported symbol declared in include/rbffd.h
 _VP, _I64, _I32, _SZ, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
 SIGNATURES = {
@@ -110,6 +119,9 @@ SIGNATURES = {
     "rbffd_solve": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP,
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP,
+                                           ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32]),
+    "rbffd_solve_batched": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _VP, _VP, _VP, _VP, _I32, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
@@ -391,3 +403,41 @@ def rbffd_profile_read(reset: bool = False) -> dict:
     p = Profile()
     _check(load().rbffd_profile_read(ctypes.byref(p), 1 if reset else 0), "rbffd_profile_read")
     return p.as_dict()
+
+
+# ----------------------------------------------------------------- batched --
+def batch_descs(sizes):
+    """Descriptor array for instances [(n_nodes, m, n), ...] stored back to back."""
+    arr = (BatchDesc * len(sizes))()
+    off = 0
+    for i, (N, m, n) in enumerate(sizes):
+        arr[i] = BatchDesc(off, int(N), int(m), int(n))
+        off += int(N)
+    return arr, off
+
+
+def rbffd_solve_batched(sizes, xy: torch.Tensor, is_dirichlet: torch.Tensor, f: torch.Tensor, g: torch.Tensor,
+                        u: torch.Tensor | None = None, opts: SolveOpts | None = None, raise_on_error: bool = True):
+    """Solve every instance for every right-hand side.  f, g, u: N_total x n_rhs
+    (node-major).  Returns (u, list of per-instance info dicts, status)."""
+    descs, N = batch_descs(sizes)
+    _require(xy, torch.float64, "xy", (N, 2))
+    _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+    R = f.shape[1]
+    _require(f, torch.float64, "f", (N, R))
+    _require(g, torch.float64, "g", (N, R))
+    lib = load()
+    opts = opts or make_opts(precision="mixed")
+    if u is None:
+        u = torch.zeros_like(f)
+    _require(u, torch.float64, "u", (N, R))
+    nbytes = lib.rbffd_batched_workspace_size(descs, len(sizes), R)
+    if nbytes == 0:
+        raise RbffdError(1, "rbffd_batched_workspace_size")
+    ws = _workspace(nbytes, xy.device)
+    infos = (SolveInfo * len(sizes))()
+    st = lib.rbffd_solve_batched(descs, len(sizes), _ptr(xy), _ptr(is_dirichlet), _ptr(f), _ptr(g), R, _ptr(u),
+                                 ctypes.byref(opts), infos, _ptr(ws), ws.numel(), _stream(xy.device))
+    if raise_on_error and st != RBFFD_OK:
+        _check(st, "rbffd_solve_batched")
+    return u, [infos[i].as_dict() for i in range(len(sizes))], st

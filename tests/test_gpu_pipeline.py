@@ -319,4 +319,5 @@ def test_weights_collinear_stencil_flagged(lib, weights_kernel):
     idx = oracle.knn(xy, 12)
     w, st = rbffd.rbffd_weights(T(xy), T(idx), 2)
     _, st_ref = oracle.weights(xy, idx, 2)
-    assert st.cpu().numpy().all() and st_ref.all()
+    st = st.cpu().numpy()
+    assert st_ref.all() and st.all()
