@@ -55,6 +55,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, v: float, device=None) -> float:
+    """Largest value of v over all ranks (the slowest rank's time); v itself on one rank."""
+    if dist is None:
+        return float(v)
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(dist, ws: int, units_per_rank: int, steps: int, ms_local: float, device=None):
+    """Whole-job throughput of independent replicas: the units all ranks processed / the slowest rank's time.
+
+    Returns (value in units/s, max-over-ranks ms)."""
+    ms = max_over_ranks(dist, ms_local, device)
+    return ws * units_per_rank * steps / (ms * 1e-3), ms
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -329,13 +348,6 @@ def run_gpu(args):
         st_ms = np.array([[stage[i][j].elapsed_time(stage[i][j + 1]) for j in range(4)] for i in range(k)]).mean(0)
         return ms, wall, st_ms, infos, prof
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- warm-up, then the timed mixed-precision steps ----
     for _ in range(args.warmup):
         step("mixed")
@@ -343,16 +355,15 @@ def run_gpu(args):
     clocks.start()
     ms, wall, st_ms, infos, prof = timed_loop("mixed", args.steps, profile=True)
     clk = clocks.stop()
-    ms = max_over_ranks(ms)
+    value, ms = replica_value(dist, ws, N, args.steps, ms, dev)
     ms_step = ms / args.steps
-    value = ws * N * args.steps / (ms * 1e-3)
 
     # ---- the same steps with the plain FP64 solve ----
     k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
     if k64 > 0:
         step("fp64")
         ms64, wall64, st64, infos64, prof64 = timed_loop("fp64", k64, profile=True)
-        ms64 = max_over_ranks(ms64)
+        ms64 = max_over_ranks(dist, ms64, dev)
 
     # ---- end to end through the API from pinned host buffers ----
     h2d = (h_xy.numel() * 8 + h_mask.numel() + h_f.numel() * 8 + h_g.numel() * 8)
@@ -372,8 +383,7 @@ def run_gpu(args):
             h_u.copy_(x, non_blocking=True)
         e1.record()
         barrier()
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-        e2e_value = ws * N * args.e2e_steps / (ms_e2e * 1e-3)
+        e2e_value, _ = replica_value(dist, ws, N, args.e2e_steps, e0.elapsed_time(e1), dev)
     else:
         h_u.copy_(x)
 
