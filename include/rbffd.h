@@ -86,6 +86,28 @@ int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* idx,
                    void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* rbffd_stencils without any device allocation and without a workspace.    */
+/* (The paper has no counterpart: this serves callers that cannot allocate  */
+/* device memory on their path -- code inside a CUDA stream capture, a      */
+/* memory arena that owns all device memory, a loop that must not allocate  */
+/* -- and cannot hand over scratch space either.)                           */
+/* Same arguments, results and errors as rbffd_stencils, for N up to        */
+/* RBFFD_STENCILS_NOALLOC_MAX_NODES; larger N returns RBFFD_ERR_INVALID_ARG  */
+/* before anything is enqueued.  The scratch is one fixed device array of   */
+/* RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES inside the library, held by every   */
+/* GPU that loads the library until the process exits.  The first call on  */
+/* a device looks up that array's device address (cudaGetSymbolAddress,     */
+/* with the device current): make that first call before any stream        */
+/* capture.  All calls share the array: calls whose work overlaps on the    */
+/* GPU (other streams, other threads) race and give wrong stencils; calls   */
+/* ordered on one stream are safe.  It calls no cudaMalloc, cudaFree or     */
+/* other allocating routine.                                                 */
+/* ------------------------------------------------------------------------ */
+#define RBFFD_STENCILS_NOALLOC_MAX_NODES (1LL << 20)
+#define RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES (28u << 20)
+int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* RBF-FD Laplacian weights -- Sec. II, Eq. 1 with the basis of Sec. V:      */
 /* Phi(r) = r^3 augmented with all 2D monomials of degree <= m.              */
 /*                                                                           */

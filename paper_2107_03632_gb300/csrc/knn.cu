@@ -22,6 +22,7 @@
 #include "scan.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace rbffd {
 namespace {
@@ -390,4 +391,49 @@ extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* i
     note_launches(5);  // bbox, setup, count, scatter, knn (+3 in the scan)
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stencils without any device allocation, for callers that cannot call
+// cudaMalloc (or any allocating routine) on the path -- for example code
+// running inside a CUDA stream capture, a custom memory arena that owns all
+// device memory, or a real-time loop that must not allocate -- and cannot
+// provide a workspace either.  The scratch of rbffd_stencils lives in one
+// file-scope device array sized for RBFFD_STENCILS_NOALLOC_MAX_NODES nodes;
+// every GPU that loads this library keeps that array until the process
+// exits.  In host code the array's name is only a host-side stand-in, so
+// its device address is looked up with cudaGetSymbolAddress, once per
+// device, with that device current, on the first call there.
+static __device__ __align__(256) unsigned char g_stencils_noalloc_scratch[RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+}  // namespace
+
+extern "C" int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx, void* stream) {
+    using namespace rbffd;
+    if (N > RBFFD_STENCILS_NOALLOC_MAX_NODES || N <= 0) return RBFFD_ERR_INVALID_ARG;
+    const size_t need = rbffd_stencils_workspace_size(N, n);
+    if (need == 0 || need > (size_t)RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES) return RBFFD_ERR_INVALID_ARG;
+    int dev = 0;
+    RBFFD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return RBFFD_ERR_INVALID_ARG;
+    void* ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_stencils_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+                return RBFFD_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        ptr = g_noalloc_ptr[dev];
+    }
+    // rbffd_stencils clears the cell histogram before use; everything else in
+    // the scratch is overwritten, so leftovers of earlier calls do no harm
+    return rbffd_stencils(xy, N, n, idx, ptr, (size_t)RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES, stream);
 }

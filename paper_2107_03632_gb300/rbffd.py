@@ -108,6 +108,7 @@ SIGNATURES = {
     "rbffd_version": (ctypes.c_int, []),
     "rbffd_stencils_workspace_size": (_SZ, [_I64, _I32]),
     "rbffd_stencils": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
+    "rbffd_stencils_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP]),
     "rbffd_weights": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, _VP]),
     "rbffd_assemble_workspace_size": (_SZ, [_I64]),
     "rbffd_assemble_pattern": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
