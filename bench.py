@@ -33,6 +33,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -43,6 +45,13 @@ WORKLOADS = {
     "disk_h0.04_m2_n12": (0.04, 2, 12),
 }
 METRIC = "solved nodes/s (weights+solve) at m=6, 4M nodes; mixed vs FP64; % roofline"
+# The batched workload (a separate measurement, not the headline line): 256
+# disks with N log-uniform in [1e4, 2e5] and m uniform in {2, 4, 6} (n = 2s),
+# 64 random Fourier right-hand sides each, g = 0, mixed solve to 1e-10.
+BATCH_WORKLOAD = "disk_batch256_rhs64"
+BATCH_METRIC = "solved node-rhs/s, 256 disks (N log-uniform 1e4..2e5, m in {2,4,6}) x 64 rhs, mixed, tol 1e-10"
+BATCH_RHS = 64
+BATCH_SAMPLE_RHS = 8  # oracle sample: right-hand sides of the smallest instance per step
 SEED = 2107
 CPU_SAMPLE_H = 0.012  # oracle sample: same recipe, ~22k nodes, ~10-30 s of one core
 
@@ -206,16 +215,48 @@ def oracle_sample_step(h: float, m: int, n: int):
     return d.N, time.perf_counter() - t0
 
 
-def cpu_baseline_subprocess(h: float, m: int, n: int, steps: int = 1):
+def oracle_batch_sample_step(seed: int, h: float, m: int, n: int, n_rhs: int):
+    """The oracle on one instance of the batched workload with all its right-hand
+    sides (stencils and weights once, one sparse solve per rhs); returns
+    (node-rhs pairs, seconds)."""
+    import oracle
+    from fixtures import disk_nodes, fourier_sources
+
+    d = disk_nodes(h, seed)
+    F = fourier_sources(d.xy, n_rhs, seed)
+    zero = np.zeros(d.N)
+    t0 = time.perf_counter()
+    idx = oracle.knn(d.xy, n)
+    w, _ = oracle.weights(d.xy, idx, m)
+    rp, col, val = oracle.assemble(idx, w, d.is_dirichlet)
+    for k in range(n_rhs):
+        oracle.solve_direct(rp, col, val, oracle.rhs(F[k], zero, d.is_dirichlet))
+    return d.N * n_rhs, time.perf_counter() - t0
+
+
+def batch_sample_spec():
+    """The smallest instance of the batched workload (the CPU sample)."""
+    from fixtures import disk_nodes
+
+    specs = batch_specs()
+    return min(specs, key=lambda sp: disk_nodes(sp[1], sp[0]).N)
+
+
+def cpu_baseline_subprocess(h: float, m: int, n: int, steps: int = 1, batch: bool = False):
     """Run the oracle in a single-threaded child process (BLAS pinned to one
     thread, the paper's single-core convention)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
     env.pop("CUDA_VISIBLE_DEVICES", None)
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = [bench.oracle_sample_step(%r, %d, %d) for _ in range(%d)]; print(json.dumps(r))"
-            % (ROOT, h, m, n, steps))
+    if batch:
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; sp = bench.batch_sample_spec(); "
+                "r = [bench.oracle_batch_sample_step(*sp, %d) for _ in range(%d)]; print(json.dumps(r))"
+                % (ROOT, BATCH_SAMPLE_RHS, steps))
+    else:
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "r = [bench.oracle_sample_step(%r, %d, %d) for _ in range(%d)]; print(json.dumps(r))"
+                % (ROOT, h, m, n, steps))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -226,6 +267,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == BATCH_WORKLOAD:
+        return run_reference_batched(args)
     h, m, n = WORKLOADS[args.workload]
     res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=args.warmup + args.steps)
     timed = res[args.warmup:]
@@ -243,6 +286,157 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batched(args):
+    sp = batch_sample_spec()
+    res = cpu_baseline_subprocess(0.0, 0, 0, steps=args.warmup + args.steps, batch=True)
+    timed = res[args.warmup:]
+    pairs = timed[0][0]
+    secs = sum(t for _, t in timed)
+    value = pairs * len(timed) / secs
+    sample = (f"oracle (brute-force kNN, per-stencil LU, CSR assembly, one SuperLU solve per rhs) on the "
+              f"smallest instance of the batched recipe ({pairs // BATCH_SAMPLE_RHS} nodes, m={sp[2]}, n={sp[3]}) "
+              f"x its first {BATCH_SAMPLE_RHS} rhs per step")
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "node-rhs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_nodes": pairs // BATCH_SAMPLE_RHS, "m": sp[2], "n": sp[3],
+                   "sample_rhs": BATCH_SAMPLE_RHS},
+        "cpu_baseline": {"value": value, "unit": "node-rhs/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "node-rhs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------- batched workload ----
+def batch_specs(count: int = 256):
+    """(seed_i, h_i, m_i, n_i) of the batched workload's instances."""
+    from fixtures import batched_instances
+
+    return [(s, h, m, (m + 1) * (m + 2)) for s, h, m in batched_instances(SEED, count)]
+
+
+def batch_sources_gpu(torch, xy, n_rhs: int, seed: int):
+    """The fixture's Fourier sources (same draws), evaluated on the device: N x n_rhs."""
+    from fixtures import fourier_params
+
+    kx, ky, a = (torch.from_numpy(v).to(xy.device) for v in fourier_params(n_rhs, seed))
+    arg = xy[:, 0, None, None] * kx[None] + xy[:, 1, None, None] * ky[None]  # N x R x waves
+    return (torch.sin(arg) * a[None]).sum(dim=2).contiguous()
+
+
+def run_gpu_batched(args):
+    import numpy as np
+    import torch
+
+    from fixtures import disk_nodes
+    from paper_2107_03632_gb300 import rbffd
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rbffd.load()
+    specs = batch_specs()
+    R = BATCH_RHS
+    nodes = [disk_nodes(h, s) for s, h, m, n in specs]
+    sizes = [(d.N, m, n) for d, (s, h, m, n) in zip(nodes, specs)]
+    N = sum(d.N for d in nodes)
+    h_xy = torch.from_numpy(np.concatenate([d.xy for d in nodes])).pin_memory()
+    h_mask = torch.from_numpy(np.concatenate([d.is_dirichlet for d in nodes])).pin_memory()
+    xy, mask = h_xy.to(dev), h_mask.to(dev)
+    F = torch.empty((N, R), dtype=torch.float64, device=dev)
+    off = 0
+    for d, (s, h, m, n) in zip(nodes, specs):
+        F[off:off + d.N] = batch_sources_gpu(torch, xy[off:off + d.N], R, s)
+        off += d.N
+    G = torch.zeros_like(F)
+    U = torch.zeros_like(F)
+    h_F = torch.empty((N, R), dtype=torch.float64).pin_memory()
+    h_F.copy_(F)
+    h_U = torch.empty((N, R), dtype=torch.float64).pin_memory()
+    wsb = rbffd.batched_workspace(sizes, R, dev)
+    opts = rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol)
+
+    def step():
+        U.zero_()
+        _, infos, st = rbffd.rbffd_solve_batched(sizes, xy, mask, F, G, U, opts, raise_on_error=False, ws=wsb)
+        if st != 0:
+            raise rbffd.RbffdError(st, "rbffd_solve_batched")
+        return infos
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    rbffd.rbffd_profile_read(reset=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        infos = step()
+    t1.record()
+    barrier()
+    clk = clocks.stop()
+    prof = rbffd.rbffd_profile_read(reset=True)
+    value, ms = replica_value(dist, ws, N * R, args.steps, t0.elapsed_time(t1), dev)
+
+    e2e_value = None
+    h2d = h_xy.numel() * 8 + h_mask.numel() + h_F.numel() * 8
+    d2h = N * R * 8
+    if args.e2e_steps > 0:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.e2e_steps):
+            xy.copy_(h_xy, non_blocking=True)
+            mask.copy_(h_mask, non_blocking=True)
+            F.copy_(h_F, non_blocking=True)
+            step()
+            h_U.copy_(U, non_blocking=True)
+        e1.record()
+        barrier()
+        e2e_value, _ = replica_value(dist, ws, N * R, args.e2e_steps, e0.elapsed_time(e1), dev)
+
+    status = [i["status"] for i in infos]
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": "node-rhs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "instances": len(sizes), "N_total": N, "rhs": R,
+                   "m_counts": {m: sum(1 for x in sizes if x[1] == m) for m in (2, 4, 6)},
+                   "tol": 1e-10, "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (vectors ~%.0f GB)" % (N * R * 8 * 8 / 1e9)},
+        "solve": {"iters_max": max(i["iters"] for i in infos), "iters_mean": float(np.mean([i["iters"] for i in infos])),
+                  "rounds_max": max(i["outer_sweeps"] for i in infos),
+                  "worst_rel_residual": max(i["rel_residual"] for i in infos),
+                  "failed_instances": sum(1 for x in status if x != 0)},
+        "e2e": ({"value": e2e_value, "unit": "node-rhs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "steps": args.e2e_steps} if e2e_value is not None else None),
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -471,7 +665,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD])
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
     ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
@@ -483,6 +677,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == BATCH_WORKLOAD:
+        return run_gpu_batched(args)
     return run_gpu(args)
 
 

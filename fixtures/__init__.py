@@ -11,6 +11,7 @@ from .disk import (  # noqa: F401
     disk_nodes,
     h_for_nodes,
     manufactured,
+    fourier_params,
     fourier_sources,
     batched_instances,
     DiskNodes,

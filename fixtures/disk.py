@@ -104,8 +104,8 @@ def manufactured(xy: np.ndarray):
     return u, 2.0 * math.pi * math.pi * u, u.copy()
 
 
-def fourier_sources(xy: np.ndarray, n_rhs: int, seed: int, n_waves: int = 8) -> np.ndarray:
-    """Random Fourier sources f = sum_k a_k sin(kx_k x + ky_k y), shape (n_rhs, N).
+def fourier_params(n_rhs: int, seed: int, n_waves: int = 8):
+    """Wave numbers and amplitudes of the random Fourier sources, each (n_rhs, n_waves).
 
     kx_k, ky_k are integers uniform in [1, 8] (top three bits of a draw, + 1) and
     a_k ~ N(0, 1) by Box-Muller (u1 in (0, 1], u2 in [0, 1)).  Four draws per
@@ -117,6 +117,13 @@ def fourier_sources(xy: np.ndarray, n_rhs: int, seed: int, n_waves: int = 8) -> 
     u1 = 1.0 - uniform01(z[..., 2])
     u2 = uniform01(z[..., 3])
     a = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    return kx, ky, a
+
+
+def fourier_sources(xy: np.ndarray, n_rhs: int, seed: int, n_waves: int = 8) -> np.ndarray:
+    """Random Fourier sources f = sum_k a_k sin(kx_k x + ky_k y), shape (n_rhs, N);
+    the draws are those of fourier_params."""
+    kx, ky, a = fourier_params(n_rhs, seed, n_waves)
     out = np.zeros((n_rhs, xy.shape[0]), dtype=np.float64)
     for r in range(n_rhs):
         for k in range(n_waves):

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kBT) b_check_kernel(const Unit* __restrict__ u
     }
 }
 
-// Inner pass start for active pairs: r = D^-1 r64 (df32), rh = r, p = v = 0,
+// Inner pass start for active pairs: r = D^-1 r64 (df32), rh pseudo-random, p = v = 0,
 // correction 0; scalars reset; the pass ends when |D r| < inner_tol |r64|.
 __global__ void __launch_bounds__(kBT) b_load_kernel(const Unit* __restrict__ units, int n_units,
                                                      const Inst* __restrict__ inst, int R,
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kBT) b_load_kernel(const Unit* __restrict__ un
                                                      float2* __restrict__ rh, float2* __restrict__ p,
                                                      float2* __restrict__ v, float2* __restrict__ xd, Pairs pr,
                                                      unsigned* inst_cnt, int* inst_running, Ctl* ctl, double* part,
-                                                     double inner_tol, int max_iter) {
+                                                     double inner_tol, int max_iter, unsigned long long seed) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k0 = lane, k1 = lane + 32;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -307,28 +307,34 @@ __global__ void __launch_bounds__(kBT) b_load_kernel(const Unit* __restrict__ un
         if (!any) continue;
         const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kPassEnd;
         const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kPassEnd;
-        DfAcc c0, c1;
+        // shadow residual: pseudo-random per (row, rhs) -- see load_df_kernel
+        DfAcc c0, c1, h0, h1;
         for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
             const float di = dinv32[row];
             if (on0) {
                 const int64_t e = row * R + k0;
                 const df ri = df_mul_f(df_from_double(r64[e]), di);
+                const df hi = df_make(shadow_value(seed, e), 0.f);
                 df_store(rr + e, ri);
-                df_store(rh + e, ri);
+                df_store(rh + e, hi);
                 p[e] = v[e] = xd[e] = make_float2(0.f, 0.f);
                 c0.add(df_mul(ri, ri));
+                h0.add(df_mul(hi, ri));
             }
             if (on1) {
                 const int64_t e = row * R + k1;
                 const df ri = df_mul_f(df_from_double(r64[e]), di);
+                const df hi = df_make(shadow_value(seed, e), 0.f);
                 df_store(rr + e, ri);
-                df_store(rh + e, ri);
+                df_store(rh + e, hi);
                 p[e] = v[e] = xd[e] = make_float2(0.f, 0.f);
                 c1.add(df_mul(ri, ri));
+                h1.add(df_mul(hi, ri));
             }
         }
-        double a0[1] = {df_to_double(c0.value())}, a1[1] = {df_to_double(c1.value())};
-        unit_store<1>(a0, a1, part, n_units, R, u);
+        double a0[2] = {df_to_double(c0.value()), df_to_double(h0.value())};
+        double a1[2] = {df_to_double(c1.value()), df_to_double(h1.value())};
+        unit_store<2>(a0, a1, part, n_units, R, u);
         if (last_unit(&inst_cnt[un.inst], in.n_units)) {
             int running = 0;
             for (int k = threadIdx.x; k < R; k += blockDim.x) {
@@ -339,13 +345,14 @@ __global__ void __launch_bounds__(kBT) b_load_kernel(const Unit* __restrict__ un
                     continue;
                 }
                 const double rr2 = inst_sum(part, n_units, R, 0, in, k);
+                const double hr = inst_sum(part, n_units, R, 1, in, k);
                 pr.rho[pi] = pr.alpha[pi] = pr.omega[pi] = 1.0;
-                pr.rho_new[pi] = rr2;
+                pr.rho_new[pi] = hr;
                 pr.s0[pi] = rr2;
                 pr.rn2[pi] = pr.tn2[pi];
                 pr.repl2[pi] = inner_tol * inner_tol;
                 pr.pass_iters[pi] = 0;
-                pr.flag[pi] = (rr2 > 0.0 && isfinite(rr2)) ? kRun : kFail;
+                pr.flag[pi] = (rr2 > 0.0 && isfinite(rr2) && hr != 0.0 && isfinite(hr)) ? kRun : kFail;
                 running += pr.flag[pi] == kRun;
             }
             // per-instance running count (threads < R each handled one pair)
@@ -818,7 +825,8 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
         if (hc.active == 0 || rounds >= o->max_outer) break;
         ++rounds;
         b_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, w.dinv32, w.r, w.rh, w.p, w.v, w.xd,
-                                          w.pr, w.inst_cnt, w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter);
+                                          w.pr, w.inst_cnt, w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter,
+                                          0x5EED2107ull + (unsigned long long)rounds);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         for (int guard = 0; guard < 1 << 20; ++guard) {

@@ -74,6 +74,20 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Entry i of a pseudo-random shadow residual for BiCGSTAB: uniform in
+// [-1, 1), exact in float32, from the SplitMix64 finaliser (Steele, Lea and
+// Flood, 2014) of seed + (i + 1) * golden.  A shadow residual drawn this way
+// instead of the starting residual keeps the bi-orthogonality coefficient
+// (r^, r) away from zero when the starting residual is concentrated in a few
+// modes, as it is in late refinement passes.
+__device__ __forceinline__ float shadow_value(unsigned long long seed, long long i) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)(z >> 40) * 0x1p-23f - 1.0f;
+}
+
 // Block-wide sum; every thread gets the result.  `sh` needs 32 doubles.
 template <int BLOCK>
 __device__ __forceinline__ double block_sum(double v, double* sh) {

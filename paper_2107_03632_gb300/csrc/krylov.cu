@@ -455,30 +455,38 @@ __device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, 
     return sum;
 }
 
-// Outer residual into the inner system: r = D^-1 r64 (df32), rh = r,
-// p = v = 0, correction 0, scalars reset.  The pass ends when the inner
-// residual has fallen below inner_tol |r64|.
+// Outer residual into the inner system: r = D^-1 r64 (df32), p = v = 0,
+// correction 0, scalars reset, and the shadow residual rh: a pseudo-random
+// vector (seed != 0) or r itself (seed == 0).  The outer residual of a late
+// refinement pass is the float32 rounding of the matrix acting on the last
+// correction; with rh = r, BiCGSTAB on it was seen to break down within ~50
+// iterations (residual growth 1e3), in exact FP64 arithmetic too, while a
+// random rh converged.  The pass ends when the inner residual has fallen
+// below inner_tol |r64|.
 __global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const double* __restrict__ r64,
                                                            const float* __restrict__ dinv32, float2* __restrict__ r,
                                                            float2* __restrict__ rh, float2* __restrict__ p,
                                                            float2* __restrict__ v, float2* __restrict__ xd,
-                                                           double inner_tol, int max_iter, KState* st, double* part) {
-    DfAcc a0;
+                                                           double inner_tol, int max_iter, unsigned long long seed,
+                                                           KState* st, double* part) {
+    DfAcc a0, a1;
     RBFFD_ELEM_LOOP(N, i) {
         const df ri = df_mul_f(df_from_double(r64[i]), dinv32[i]);
         df_store(r + i, ri);
-        df_store(rh + i, ri);
+        const df hi = seed ? df_make(shadow_value(seed, i), 0.f) : ri;
+        df_store(rh + i, hi);
         xd[i] = make_float2(0.f, 0.f);
         p[i] = make_float2(0.f, 0.f);
         v[i] = make_float2(0.f, 0.f);
         a0.add(df_mul(ri, ri));
+        a1.add(df_mul(hi, ri));
     }
-    double acc[1] = {df_to_double(a0.value())}, tot[1];
-    if (reduce_last<1>(acc, part, kSlotLoad, &st->counter[kSlotLoad], tot) && threadIdx.x == 0) {
+    double acc[2] = {df_to_double(a0.value()), df_to_double(a1.value())}, tot[2];
+    if (reduce_last<2>(acc, part, kSlotLoad, &st->counter[kSlotLoad], tot) && threadIdx.x == 0) {
         st->rho = 1.0;
         st->alpha = 1.0;
         st->omega = 1.0;
-        st->rho_new = tot[0];
+        st->rho_new = tot[1];
         st->s0 = tot[0];
         st->iter = 0;
         st->max_iter = max_iter;
@@ -486,7 +494,9 @@ __global__ void __launch_bounds__(kThreads) load_df_kernel(int64_t N, const doub
         st->rnorm2 = st->tnorm2;  // |r64|^2 from the preceding check
         st->rmax2 = st->tnorm2;
         st->repl2 = inner_tol * inner_tol;
-        st->flag = (!finite(tot[0]) || tot[0] == 0.0) ? kBreakdown : (max_iter <= 0 ? kMaxIter : kRunning);
+        st->flag = (!finite(tot[0]) || tot[0] == 0.0 || !finite(tot[1]) || tot[1] == 0.0)
+                       ? kBreakdown
+                       : (max_iter <= 0 ? kMaxIter : kRunning);
     }
 }
 
@@ -654,6 +664,11 @@ size_t layout(void* ws, int64_t N, bool mixed, Work* w) {
 int env_int(const char* name, int dflt);
 
 // RBFFD_TRACE=1 prints one line per pass to stderr (diagnostics only).
+bool shadow_random() {
+    static const int on = env_int("RBFFD_SHADOW", 0);
+    return on != 0;
+}
+
 bool trace_on() {
     static const int on = env_int("RBFFD_TRACE", 0);
     return on != 0;
@@ -1000,8 +1015,12 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         // outer tolerance needs
         const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);
         const int budget = std::min(o.max_iter - total, g.cap);
+        // shadow residual: r itself by default; RBFFD_SHADOW=1 draws a fresh
+        // pseudo-random one per pass (better on late passes of small
+        // systems, worse on the long first pass of 4M-node systems)
+        const unsigned long long seed = shadow_random() ? 0x5EED2107ull + (unsigned long long)outer : 0ull;
         load_df_kernel<<<grid_of(load_df_kernel), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd,
-                                                                     w.xd, inner, budget, w.st, w.part);
+                                                                     w.xd, inner, budget, seed, w.st, w.part);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;

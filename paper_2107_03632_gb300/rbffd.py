@@ -417,10 +417,20 @@ def batch_descs(sizes):
     return arr, off
 
 
+def batched_workspace(sizes, n_rhs: int, device) -> torch.Tensor:
+    descs, _ = batch_descs(sizes)
+    nbytes = load().rbffd_batched_workspace_size(descs, len(sizes), n_rhs)
+    if nbytes == 0:
+        raise RbffdError(1, "rbffd_batched_workspace_size")
+    return _workspace(nbytes, device)
+
+
 def rbffd_solve_batched(sizes, xy: torch.Tensor, is_dirichlet: torch.Tensor, f: torch.Tensor, g: torch.Tensor,
-                        u: torch.Tensor | None = None, opts: SolveOpts | None = None, raise_on_error: bool = True):
+                        u: torch.Tensor | None = None, opts: SolveOpts | None = None, raise_on_error: bool = True,
+                        ws: torch.Tensor | None = None):
     """Solve every instance for every right-hand side.  f, g, u: N_total x n_rhs
-    (node-major).  Returns (u, list of per-instance info dicts, status)."""
+    (node-major); u holds the initial guess on entry.  Returns (u, list of
+    per-instance info dicts, status)."""
     descs, N = batch_descs(sizes)
     _require(xy, torch.float64, "xy", (N, 2))
     _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
@@ -432,10 +442,8 @@ def rbffd_solve_batched(sizes, xy: torch.Tensor, is_dirichlet: torch.Tensor, f: 
     if u is None:
         u = torch.zeros_like(f)
     _require(u, torch.float64, "u", (N, R))
-    nbytes = lib.rbffd_batched_workspace_size(descs, len(sizes), R)
-    if nbytes == 0:
-        raise RbffdError(1, "rbffd_batched_workspace_size")
-    ws = _workspace(nbytes, xy.device)
+    if ws is None:
+        ws = batched_workspace(sizes, R, xy.device)
     infos = (SolveInfo * len(sizes))()
     st = lib.rbffd_solve_batched(descs, len(sizes), _ptr(xy), _ptr(is_dirichlet), _ptr(f), _ptr(g), R, _ptr(u),
                                  ctypes.byref(opts), infos, _ptr(ws), ws.numel(), _stream(xy.device))
