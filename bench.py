@@ -7,10 +7,14 @@ u = sin(pi x) sin(pi y), solved to a relative residual of 1e-10.
 
 One step = the whole hot path on inputs already resident in HBM:
 stencils -> weights -> assembly (pattern, f64 + f32 values) -> rhs ->
-BiCGSTAB solve.  The headline `value` uses the mixed FP32-inner / FP64
-refinement solve; the same steps with the plain FP64 solve are timed beside
-it ("fp64").  `e2e` repeats the step through the public API from pinned
-host buffers, host<->device copies inside the timed region.
+multigrid hierarchy (coarse node sets, rediscretised operators, transfer
+operators) -> BiCGSTAB solve right-preconditioned by a V-cycle.  The
+headline `value` uses the mixed solve (float32 V-cycle inside the FP64
+BiCGSTAB); the same steps with an FP64 V-cycle are timed beside it ("fp64").
+`--precond jacobi` runs the Jacobi-scaled solvers instead (mixed: float32
+inner BiCGSTAB in FP64 refinement).  `e2e` repeats the step through the
+public API from pinned host buffers, host<->device copies inside the timed
+region.
 
 Multi-GPU: the problem is solved independently on every rank (replicas:
 the path has no cross-GPU exchange here), value = nodes of all ranks /
@@ -180,6 +184,11 @@ def weights_flops(n: int, m: int) -> float:
     return (2 * n + n * s + (2 * s - 1) * (n * s - s * (s - 1) / 2) + 4 * n * (n - 1) + 5 * n + 2 * s * s * q
             + 2 * n * s + 2 * s * q * (q + 1) + 2 * q * s + q ** 3 / 3 + q * q / 2 + 2 * q + 2 * q * q + 2 * q
             + 2 * s * q + n)
+
+
+# FP64 (non-tensor and tensor alike on this chip) peak from unit counts and the
+# maximum clock: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz.
+FP64_PEAK_TFLOPS_UNITS = 152 * 2 * 2 * 2070e6 / 1e12
 
 
 def fp64_peak_tflops(torch, dev):
@@ -488,9 +497,24 @@ def run_gpu(args):
     A = rbffd.CsrMatrix(row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
                         torch.empty(nnz, dtype=torch.float64, device=dev),
                         torch.empty(nnz, dtype=torch.float32, device=dev))
-    opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol),
-            "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.inner_tol64)}
+    use_mg = args.precond == "mg"
+    mg = None
+    if use_mg:
+        # first build (allocates the hierarchy's workspace); every step rebuilds it
+        rbffd.rbffd_stencils(xy, n, idx, ws_knn)
+        rbffd.rbffd_weights(xy, idx, m, w, st)
+        rbffd.rbffd_assemble(idx, w, mask, out=A)
+        mg = rbffd.Multigrid(xy, mask, A, nu=args.mg_nu, omega=args.mg_omega)
+        opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.mg_pass_tol, mg=mg),
+                "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.mg_pass_tol, mg=mg)}
+    else:
+        opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol),
+                "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.inner_tol64)}
     ws_solve = rbffd.solve_workspace(N, opts["mixed"], dev)
+    if use_mg:
+        ws_solve64 = ws_solve
+    else:
+        ws_solve64 = rbffd.solve_workspace(N, opts["fp64"], dev)
 
     def step(precision, ev=None):
         if ev:
@@ -506,12 +530,17 @@ def run_gpu(args):
         rbffd.rbffd_rhs(fT, gT, mask, b)
         if ev:
             ev[3].record()
+        if mg is not None:
+            mg.setup(xy, mask, A, nu=args.mg_nu, omega=args.mg_omega)
+        if ev:
+            ev[4].record()
         x.zero_()
-        _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve, raise_on_error=False)
+        _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve if precision == "mixed" else ws_solve64,
+                                    raise_on_error=False)
         if info["status_code"] not in (0, 4):
             raise rbffd.RbffdError(info["status_code"], "rbffd_solve")
         if ev:
-            ev[4].record()
+            ev[5].record()
         return info
 
     def barrier():
@@ -521,7 +550,7 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
 
     def timed_loop(precision, k, profile=False):
-        stage = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(k)]
+        stage = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(k)]
         infos = []
         barrier()
         rbffd.rbffd_profile_read(reset=True)
@@ -539,7 +568,7 @@ def run_gpu(args):
         prof = rbffd.rbffd_profile_read(reset=True)
         rbffd.rbffd_profile_enable(False)
         ms = t0.elapsed_time(t1)
-        st_ms = np.array([[stage[i][j].elapsed_time(stage[i][j + 1]) for j in range(4)] for i in range(k)]).mean(0)
+        st_ms = np.array([[stage[i][j].elapsed_time(stage[i][j + 1]) for j in range(5)] for i in range(k)]).mean(0)
         return ms, wall, st_ms, infos, prof
 
     # ---- warm-up, then the timed mixed-precision steps ----
@@ -584,26 +613,40 @@ def run_gpu(args):
     # ---- correctness of the timed solves (host check, outside timing) ----
     err_exact = float(np.abs(h_u.numpy() - u_ex).max())
 
-    # ---- roofline: SpMV of the inner solve (dominant kernel) ----
+    # ---- roofline of the dominant kernel: the finest-level V-cycle sweep
+    # (multigrid) or the inner SpMV (Jacobi) ----
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    sp_ms = prof["spmv32_ms"] / max(prof["spmv32_launches"], 1)
-    sp_bytes = prof["spmv32_bytes"] / max(prof["spmv32_launches"], 1)
-    sp_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9 if prof["spmv32_launches"] else 0.0
+
+    def per_launch(pr, kind):
+        nl = pr[kind + "_launches"]
+        if not nl:
+            return 0.0, 0.0, 0.0, 0
+        ms_ = pr[kind + "_ms"] / nl
+        by = pr[kind + "_bytes"] / nl
+        return ms_, by, by / (ms_ * 1e-3) / 1e9, nl
+
+    dom = "mg" if use_mg else "spmv32"
+    sp_ms, sp_bytes, sp_gbs, sp_n = per_launch(prof, dom)
+    dom_name = ("mg_jacobi_kernel<float> (finest-level damped Jacobi sweep of the float32 V-cycle)" if use_mg
+                else "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)")
+    outer_ms, outer_bytes, outer_gbs, outer_n = per_launch(prof, "spmv64")
     fp64_line = None
     if k64 > 0:
-        sp64_ms = prof64["spmv64_ms"] / max(prof64["spmv64_launches"], 1)
-        sp64_bytes = prof64["spmv64_bytes"] / max(prof64["spmv64_launches"], 1)
-        sp64_gbs = sp64_bytes / (sp64_ms * 1e-3) / 1e9 if prof64["spmv64_launches"] else 0.0
+        sp64_ms, sp64_bytes, sp64_gbs, _ = per_launch(prof64, "mg" if use_mg else "spmv64")
+        o64_ms, o64_bytes, o64_gbs, _ = per_launch(prof64, "spmv64")
         fp64_line = {"value": ws * N * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
-                     "inner_tol": args.inner_tol64,
+                     "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol64,
                      "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2],
-                                   "solve": st64[3]},
+                                   "mg_setup": st64[3], "solve": st64[4]},
                      "iters": [i["iters"] for i in infos64], "passes": [i["outer_sweeps"] for i in infos64],
                      "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos64],
                      "rel_residual": [i["rel_residual"] for i in infos64],
-                     "spmv_kernel": "spmv64_kernel", "spmv_gbs": sp64_gbs, "spmv_frac_hbm": sp64_gbs / hbm,
-                     "spmv_ms_per_launch": sp64_ms}
+                     "dominant_kernel": ("mg_jacobi_kernel<double> (finest-level sweep, FP64 V-cycle)" if use_mg
+                                         else "spmv64_kernel"),
+                     "dominant_gbs": sp64_gbs, "dominant_frac_hbm": sp64_gbs / hbm,
+                     "dominant_ms_per_launch": sp64_ms,
+                     "spmv64_gbs": o64_gbs, "spmv64_frac_hbm": o64_gbs / hbm, "spmv64_ms_per_launch": o64_ms}
 
     fp64_peak = fp64_peak_tflops(torch, dev) if not args.no_peak_probe else float("nan")
     w_flops = N * weights_flops(n, m)
@@ -618,32 +661,45 @@ def run_gpu(args):
                "sample": f"oracle pipeline (brute-force kNN, per-stencil LU, CSR assembly, SuperLU) on the same "
                          f"disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m={m}, n={n}), one core, {secs:.1f} s"}
 
+    roof_solve = {"kernel": dom_name, "bound": "hbm", "achieved": sp_gbs,
+                  "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm,
+                  "traffic": (None if use_mg else
+                              (SPMV_DF_TRAFFIC["traffic_over_algorithmic"] * sp_bytes
+                               if spmv_df_source_hash() == SPMV_DF_TRAFFIC["source_sha256_16"] else None)),
+                  "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
+                  "launches": sp_n, "ms_per_step": sp_ms * sp_n / max(args.steps, 1)}
+    roof_weights = {"kernel": "weights_ns_kernel (null-space elimination, FP64)", "bound": "alu",
+                    "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
+                    "frac": w_tflops / FP64_PEAK_TFLOPS_UNITS,
+                    "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)",
+                    "traffic": None, "flops_per_node": w_flops / N, "ms_per_launch": st_ms[1],
+                    "launches": 1, "cublas_dgemm_tflops": fp64_peak, "lu_equivalent_tflops": lu_equiv}
+    weights_dominate = st_ms[1] > roof_solve["ms_per_step"]
     iters = [i["iters"] for i in infos]
     line = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "nnz": nnz, "h": h, "m": m, "n": n, "seed": SEED,
-                   "tol": 1e-10, "precision": "mixed (f32 inner BiCGSTAB, f64 refinement)",
-                   "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
+                   "tol": 1e-10,
+                   "precision": ("mixed (FP64 BiCGSTAB right-preconditioned by a float32 multigrid V-cycle)"
+                                 if use_mg else "mixed (f32 inner BiCGSTAB, f64 refinement)"),
+                   "precond": (f"multigrid V({args.mg_nu},{args.mg_nu}) omega {args.mg_omega}, levels "
+                               f"{mg.levels()}" if use_mg else "jacobi"),
+                   "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
-        "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "solve": st_ms[3]},
+        "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "mg_setup": st_ms[3],
+                      "solve": st_ms[4]},
         "solve": {"iters": iters, "refinements": [i["outer_sweeps"] for i in infos],
                   "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos],
                   "rel_residual": [i["rel_residual"] for i in infos], "max_err_vs_exact": err_exact},
         "fp64": fp64_line,
-        "roofline": {"kernel": "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)", "bound": "hbm",
-                     "achieved": sp_gbs,
-                     "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm,
-                     "traffic": (SPMV_DF_TRAFFIC["traffic_over_algorithmic"] * sp_bytes
-                                 if spmv_df_source_hash() == SPMV_DF_TRAFFIC["source_sha256_16"] else None),
-                     "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
-                     "launches": prof["spmv32_launches"]},
-        "weights_roofline": {"kernel": "weights_ns_kernel (null-space elimination)", "bound": "fp64",
-                             "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                             "frac": w_tflops / fp64_peak, "peak_kind": "measured cuBLAS DGEMM 4096^3",
-                             "flops_per_node": w_flops / N,
-                             "lu_equivalent_tflops": lu_equiv},
+        # the dominant kernel of the step (largest device time) and the solver's own
+        "roofline": roof_weights if weights_dominate else roof_solve,
+        "solve_roofline": roof_solve if weights_dominate else roof_weights,
+        "outer_spmv": {"kernel": "spmv64_kernel (outer BiCGSTAB SpMV, float64 values)", "achieved_gbs": outer_gbs,
+                       "frac": outer_gbs / hbm, "ms_per_launch": outer_ms, "launches": outer_n},
         "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "steps": args.e2e_steps} if e2e_value is not None else None),
         "gpu_launches": prof["launches"],
@@ -668,6 +724,12 @@ def main():
     ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD])
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
     ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
+    ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
+                    help="mg: BiCGSTAB right-preconditioned by the multigrid V-cycle; jacobi: the plain solvers")
+    ap.add_argument("--mg-nu", type=int, default=2, help="Jacobi sweeps before and after the coarse correction")
+    ap.add_argument("--mg-omega", type=float, default=0.5, help="Jacobi damping of the V-cycle")
+    ap.add_argument("--mg-pass-tol", type=float, default=1e-10,
+                    help="multigrid: residual drop per restarted BiCGSTAB pass (1e-10: a single pass)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

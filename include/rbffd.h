@@ -170,6 +170,50 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
                     void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Multigrid preconditioner (an addition of this library: the paper has no  */
+/* implicit solver, Sec. VI names one as the next step).  A geometric       */
+/* V-cycle on the node sets themselves, built from the pieces of this      */
+/* header:                                                                   */
+/*  * coarsening: one node per cell of a uniform grid of side ~2x the mean   */
+/*    spacing (a Dirichlet node where the cell has one, else the node        */
+/*    nearest the cell centre; ties to the lower index), so each level has   */
+/*    at most half the nodes of the one above; down to <= 512 nodes;         */
+/*  * coarse operators: rediscretised -- stencils, RBF-FD Laplacian weights  */
+/*    (r^3 + monomials of degree 2, n = 12) and Dirichlet rows on the coarse */
+/*    nodes, as in Sec. II Eq. 1 / Sec. IV;                                  */
+/*  * prolongation P: PHS r^3 + degree-2 interpolation from the 12 nearest   */
+/*    coarse nodes (zero rows at Dirichlet nodes); restriction R = (N_c/N_f) */
+/*    P^T with zero rows at coarse Dirichlet nodes;                          */
+/*  * smoothing: nu damped Jacobi sweeps (weight omega) before and after;    */
+/*    coarsest level: a dense inverse (Gauss-Jordan, partial pivoting).     */
+/* With opts->precond = 1, rbffd_solve runs BiCGSTAB right-preconditioned by */
+/* one V-cycle per application (FP64 V-cycle in precision 0; in precision 1 */
+/* the V-cycle runs in float32 values and vectors inside the FP64 BiCGSTAB, */
+/* which needs A32).  The adjoint solve does not take it.                   */
+/*   mg       : host object filled here; read by rbffd_solve.  It points     */
+/*              into ws, which must stay allocated and unchanged meanwhile.  */
+/*   A, A32   : the fine-level operator (as passed to rbffd_solve; A32 may   */
+/*              be NULL, then only the FP64 V-cycle is available).           */
+/*   nu       : 1..8 sweeps; omega: 0 < omega < 1 (e.g. nu 2, omega 0.5).   */
+/*   ws       : rbffd_mg_workspace_size(N, A->nnz) bytes (a bound).          */
+/* Synchronises `stream` (level sizes are read back).  Errors: invalid       */
+/* arguments, RBFFD_ERR_SINGULAR_STENCIL if a coarse stencil or the coarsest */
+/* matrix is singular.                                                       */
+/* ------------------------------------------------------------------------ */
+#define RBFFD_MG_MAX_LEVELS 24
+typedef struct rbffd_mg {
+    uint64_t opaque[2048];
+} rbffd_mg;
+
+size_t rbffd_mg_workspace_size(int64_t N, int64_t nnz);
+int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
+                   const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws, size_t ws_bytes,
+                   void* stream);
+/* Levels of a built hierarchy (finest first); n_nodes: RBFFD_MG_MAX_LEVELS  */
+/* entries, may be NULL.  Returns the level count, 0 if mg was not built.    */
+int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes);
+
+/* ------------------------------------------------------------------------ */
 /* Krylov solve -- the implicit solution named in Sec. VI: A x = b by       */
 /* BiCGSTAB (van der Vorst 1992) with left Jacobi scaling D^-1 A x = D^-1 b. */
 /* Convergence is judged on the unscaled system: |b - A x|_2 <= tol |b|_2,   */
@@ -199,6 +243,8 @@ typedef struct rbffd_solve_opts {
     double inner_tol;    /* residual reduction per restarted pass, 0 < inner_tol < 1 */
     int32_t max_outer;   /* cap on passes (refinement steps in mixed mode) */
     int32_t jacobi;      /* 1 = left Jacobi scaling (default), 0 = none */
+    int32_t precond;     /* 0 = none / Jacobi as above, 1 = multigrid (mg) */
+    const rbffd_mg* mg;  /* hierarchy from rbffd_mg_setup when precond = 1 */
 } rbffd_solve_opts;
 
 typedef struct rbffd_solve_info {
@@ -275,6 +321,10 @@ int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst, const doub
 /* with the launch's algorithmic bytes:                                      */
 /*   nnz * (value bytes + 4) + 8 (N + 1) [row_ptr] + 8 N [gathered vector,   */
 /*   read once] + 8 N [result] + 8 N [Jacobi scale] + 8 N [dot partner].     */
+/* With the multigrid preconditioner it also brackets the finest level's     */
+/* Jacobi sweeps of every V-cycle (mg_*): nnz * (value bytes + 4) +          */
+/* 8 (N + 1) + N * (2 x vector bytes [iterate gathered once, result] +      */
+/* right-hand-side bytes + value bytes [D^-1]).                              */
 /* Profiling is process-wide, off by default, and meant for one thread and   */
 /* one device.  rbffd_profile_read waits for bracketed launches to finish.   */
 /* ------------------------------------------------------------------------ */
@@ -286,6 +336,9 @@ typedef struct rbffd_profile {
     int64_t spmv32_launches;  /* timed SpMV launches, float32 values */
     double spmv32_ms;
     int64_t spmv32_bytes;
+    int64_t mg_launches;      /* timed finest-level V-cycle sweeps */
+    double mg_ms;
+    int64_t mg_bytes;
 } rbffd_profile;
 
 int rbffd_profile_enable(int on);

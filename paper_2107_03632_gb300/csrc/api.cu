@@ -137,6 +137,9 @@ int rbffd_profile_read(rbffd_profile* out, int reset) {
     out->spmv32_launches = g_prof_launches[kProfSpmv32];
     out->spmv32_ms = g_prof_ms[kProfSpmv32];
     out->spmv32_bytes = g_prof_bytes[kProfSpmv32];
+    out->mg_launches = g_prof_launches[kProfMg];
+    out->mg_ms = g_prof_ms[kProfMg];
+    out->mg_bytes = g_prof_bytes[kProfMg];
     if (reset) {
         g_launches.store(0);
         for (int k = 0; k < kProfKinds; ++k) {

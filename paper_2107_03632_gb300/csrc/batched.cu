@@ -724,6 +724,7 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     if (!xy || !is_dirichlet || !f || !g || !u || !o || !info || !make_plan(desc, n_inst, n_rhs, &pl))
         return RBFFD_ERR_INVALID_ARG;
     if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
+    if (o->precond != 0) return RBFFD_ERR_INVALID_ARG;  // no multigrid hierarchy for the batched form
     if (!(o->tol > 0.0) || o->max_iter < 0 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1)
         return RBFFD_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, pl, nullptr))

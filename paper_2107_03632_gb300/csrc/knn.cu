@@ -19,6 +19,7 @@
 // Distances are compared as the IEEE bit patterns of non-negative doubles
 // (monotone as unsigned integers), so ranking never touches the FP64 pipe.
 #include "common.cuh"
+#include "internal.cuh"
 #include "scan.cuh"
 
 #include <cmath>
@@ -230,17 +231,21 @@ __device__ __forceinline__ double cell_min_d2(const GridParams& p, double qx, do
     return dx * dx + dy * dy;
 }
 
+// Queries: the indexed points themselves in cell order (qxy = sxy, qorig =
+// sorig: stencils), or separate points in their own order (qorig = NULL:
+// output row q).
 template <int SLOTS>
 __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sxy, const int* __restrict__ sorig,
                                                   const int* __restrict__ cell_start,
-                                                  const GridParams* __restrict__ gp, int N, int n,
-                                                  int* __restrict__ idx) {
+                                                  const GridParams* __restrict__ gp, int Nq,
+                                                  const double2* __restrict__ qxy, const int* __restrict__ qorig,
+                                                  int n, int* __restrict__ idx) {
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (q >= N) return;
+    if (q >= Nq) return;
     const GridParams p = *gp;
-    const double2 Q = sxy[q];
-    const int qo = sorig[q];
+    const double2 Q = qxy[q];
+    const int qo = qorig ? qorig[q] : q;
     const int G = p.G;
     const int cx = cell_coord(Q.x, p.x0, p.inv_cell, G);
     const int cy = cell_coord(Q.y, p.y0, p.inv_cell, G);
@@ -366,9 +371,14 @@ extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* i
         return RBFFD_ERR_INVALID_ARG;
     if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
+    return knn_search(xy, N, nullptr, N, n, idx, ws, ws_bytes, as_stream(stream));
+}
+
+int rbffd::knn_search(const double* xy, int64_t N, const double* qxy, int64_t Nq, int32_t n, int32_t* idx, void* ws,
+                      size_t ws_bytes, cudaStream_t st) {
     KnnLayout L = knn_layout(ws, N, n);
     if (ws_bytes < L.bytes) return RBFFD_ERR_WORKSPACE;
-    cudaStream_t st = as_stream(stream);
+    if (Nq <= 0 || Nq > 0x7fffffffLL) return RBFFD_ERR_INVALID_ARG;
     const int G = grid_side(N, n);
     const int64_t cells = (int64_t)G * G;
     const double2* p = reinterpret_cast<const double2*>(xy);
@@ -381,13 +391,15 @@ extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* i
     RBFFD_CUDA_TRY(exclusive_scan<int>(CountLoad{L.counts}, cells, L.cell_start, L.sums, L.cell_start + cells, st));
     cell_scatter_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.keys, L.cell_start, L.counts, L.sxy, L.sorig);
     const int warps_per_block = 8;
-    const int blocks = (int)((N + warps_per_block - 1) / warps_per_block);
+    const int blocks = (int)((Nq + warps_per_block - 1) / warps_per_block);
+    const double2* q = qxy ? reinterpret_cast<const double2*>(qxy) : L.sxy;
+    const int* qo = qxy ? nullptr : L.sorig;
     if (n <= 32)
-        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
     else if (n <= 64)
-        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
     else
-        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)N, n, idx);
+        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
     note_launches(5);  // bbox, setup, count, scatter, knn (+3 in the scan)
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

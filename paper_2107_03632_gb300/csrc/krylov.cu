@@ -47,9 +47,11 @@
 // of a_ij would perturb the smooth modes by ~n eps_32 / h^2).
 #include "common.cuh"
 #include "df32.cuh"
+#include "internal.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -329,13 +331,16 @@ __global__ void __launch_bounds__(kThreads) update_p64_kernel(int64_t N, const d
 }
 
 // y = D^-1 A xin; MODE 0: (rh, y) -> alpha.  MODE 1: (y, xin), (y, y) -> omega.
+// With right preconditioning xin is M^-1 s and the omega dots take s itself
+// (dotv); dotv NULL: xin.
 template <int TPR, int MODE>
 __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restrict__ row_ptr,
                                                           const int* __restrict__ col,
                                                           const double* __restrict__ val, int64_t N,
                                                           const double* __restrict__ xin,
                                                           const double* __restrict__ dinv, double* __restrict__ y,
-                                                          const double* __restrict__ rh, KState* st, double* part) {
+                                                          const double* __restrict__ rh, KState* st, double* part,
+                                                          const double* __restrict__ dotv) {
     if (st->flag != kRunning) return;
     const int sub = threadIdx.x & (TPR - 1);
     double acc[3] = {0.0, 0.0, 0.0};
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
             if (MODE == 0) {
                 acc[0] = fma(rh[i], yi, acc[0]);
             } else {
-                const double si = xin[i];
+                const double si = dotv ? dotv[i] : xin[i];
                 acc[0] = fma(yi, si, acc[0]);
                 acc[1] = fma(yi, yi, acc[1]);
                 acc[2] = fma(si, si, acc[2]);
@@ -398,19 +403,21 @@ __device__ __forceinline__ void finish_iteration(KState* st, double rn2, double 
     st->flag = flag;
 }
 
+// x += alpha p + omega sx (sx = M^-1 s with right preconditioning, else s),
+// r = s - omega t.
 __global__ void __launch_bounds__(kThreads) update_xr64_kernel(int64_t N, double* __restrict__ x,
                                                                const double* __restrict__ p,
                                                                const double* __restrict__ s,
                                                                const double* __restrict__ t, double* __restrict__ r,
                                                                const double* __restrict__ rh,
                                                                const double* __restrict__ d, KState* st,
-                                                               double* part) {
+                                                               double* part, const double* __restrict__ sx) {
     if (st->flag != kRunning) return;
     const double alpha = st->alpha, omega = st->omega;
     double acc[3] = {0.0, 0.0, 0.0};
     RBFFD_ELEM_LOOP(N, i) {
         const double si = s[i];
-        x[i] = fma(omega, si, fma(alpha, p[i], x[i]));
+        x[i] = fma(omega, sx ? sx[i] : si, fma(alpha, p[i], x[i]));
         const double ri = fma(-omega, t[i], si);
         r[i] = ri;
         const double ru = ri * d[i];
@@ -622,6 +629,10 @@ struct Work {
     double* x_save;  // iterate at the start of the current pass
     // FP64 engine
     double *r, *rh, *p, *v, *s, *t;
+    // multigrid right preconditioning: ph = M^-1 p, sh = M^-1 s
+    double *ph, *sh;
+    const MgHierarchy* mg;  // host object, NULL without multigrid
+    bool mg32;              // float32 V-cycle
     // mixed engine
     double* r64;
     float *d32, *dinv32, *sigma32;
@@ -629,7 +640,9 @@ struct Work {
 };
 
 // Carves the workspace (ws may be null to size it); returns the bytes used.
-size_t layout(void* ws, int64_t N, bool mixed, Work* w) {
+// With multigrid (mg) the FP64 engine runs in both precisions (the float32
+// part is the V-cycle), so `mixed` then selects nothing here.
+size_t layout(void* ws, int64_t N, bool mixed, bool mg, Work* w) {
     Carver c(ws);
     Work t{};
     t.st = c.take<KState>(1);
@@ -637,13 +650,17 @@ size_t layout(void* ws, int64_t N, bool mixed, Work* w) {
     t.d = c.take<double>(N);
     t.dinv = c.take<double>(N);
     t.x_save = c.take<double>(N);
-    if (!mixed) {
+    if (!mixed || mg) {
         t.r = c.take<double>(N);
         t.rh = c.take<double>(N);
         t.p = c.take<double>(N);
         t.v = c.take<double>(N);
         t.s = c.take<double>(N);
         t.t = c.take<double>(N);
+        if (mg) {
+            t.ph = c.take<double>(N);
+            t.sh = c.take<double>(N);
+        }
     } else {
         t.r64 = c.take<double>(N);
         t.d32 = c.take<float>(N);
@@ -743,20 +760,26 @@ struct Ops64 {
         const int64_t N = A.n_rows;
         const double* val = static_cast<const double*>(A.val);
         const int64_t bytes = spmv_bytes(A, 8);
+        // right preconditioning: the SpMVs act on M^-1 p and M^-1 s
+        const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const char*>(w.st) + offsetof(KState, flag));
+        const double* pin = w.mg ? w.ph : w.p;
+        const double* sin_ = w.mg ? w.sh : w.s;
         update_p64_kernel<<<grid_of(update_p64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
+        if (w.mg) mg_apply(w.mg, w.mg32, w.p, w.ph, flag, st, &ev);
         int e = prof_begin(st);
-        spmv64_kernel<TPR, 0><<<grid_of(spmv64_kernel<TPR, 0>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.p,
-                                                                                   w.dinv, w.v, w.rh, w.st, w.part);
+        spmv64_kernel<TPR, 0><<<grid_of(spmv64_kernel<TPR, 0>), kThreads, 0, st>>>(
+            A.row_ptr, A.col, val, N, pin, w.dinv, w.v, w.rh, w.st, w.part, nullptr);
         prof_end(e, st, kProfSpmv64, bytes);
         ev.push_back(e);
         update_s64_kernel<<<grid_of(update_s64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
+        if (w.mg) mg_apply(w.mg, w.mg32, w.s, w.sh, flag, st, &ev);
         e = prof_begin(st);
-        spmv64_kernel<TPR, 1><<<grid_of(spmv64_kernel<TPR, 1>), kThreads, 0, st>>>(A.row_ptr, A.col, val, N, w.s,
-                                                                                   w.dinv, w.t, nullptr, w.st, w.part);
+        spmv64_kernel<TPR, 1><<<grid_of(spmv64_kernel<TPR, 1>), kThreads, 0, st>>>(
+            A.row_ptr, A.col, val, N, sin_, w.dinv, w.t, nullptr, w.st, w.part, w.mg ? w.s : nullptr);
         prof_end(e, st, kProfSpmv64, bytes);
         ev.push_back(e);
-        update_xr64_kernel<<<grid_of(update_xr64_kernel), kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d,
-                                                                             w.st, w.part);
+        update_xr64_kernel<<<grid_of(update_xr64_kernel), kThreads, 0, st>>>(N, x, pin, w.s, w.t, w.r, w.rh, w.d,
+                                                                             w.st, w.part, w.mg ? w.sh : nullptr);
         note_launches(5);
     }
 };
@@ -845,7 +868,9 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn it
         RBFFD_LAUNCH_CHECK();
         const int rc = read_state(w, hs, st);
         if (rc != RBFFD_OK) return -rc;
-        if (profiling()) prof_commit(ev.data(), (int)ev.size(), 2 * (hs->iter - before));
+        // every iteration brackets the same number of launches, in order
+        const int per_iter = chunk > 0 ? (int)ev.size() / chunk : 0;
+        if (profiling()) prof_commit(ev.data(), (int)ev.size(), per_iter * (hs->iter - before));
         chunk = std::min(chunk * 2, 64);
     }
     return hs->flag;
@@ -1062,28 +1087,40 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     if (!csr_ok(A, 0) || !b || !x || !o || !info) return RBFFD_ERR_INVALID_ARG;
     const bool mixed = o->precision == 1;
     if (o->precision != 0 && o->precision != 1) return RBFFD_ERR_INVALID_ARG;
-    if (mixed && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz ||
+    if (mixed && o->precond != 1 && (!csr_ok(A32, 1) || A32->n_rows != A->n_rows || A32->nnz != A->nnz ||
                   A32->row_ptr != A->row_ptr || A32->col != A->col))
         return RBFFD_ERR_INVALID_ARG;  // the float32 copy shares A's (validated) pattern
     if (!(o->tol > 0.0) || o->max_iter < 0) return RBFFD_ERR_INVALID_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1) return RBFFD_ERR_INVALID_ARG;
     const int64_t N = A->n_rows;
+    if (o->precond != 0 && o->precond != 1) return RBFFD_ERR_INVALID_ARG;
+    const MgHierarchy* mg = nullptr;
+    if (o->precond == 1) {
+        mg = mg_hierarchy(o->mg);
+        if (!mg || mg_fine_rows(mg) != N || (mixed && !mg_has_fp32(mg))) return RBFFD_ERR_INVALID_ARG;
+    }
     Work w{};
-    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, N, mixed, nullptr))
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, N, mixed, mg != nullptr, nullptr))
         return RBFFD_ERR_WORKSPACE;
-    layout(ws, N, mixed, &w);
+    layout(ws, N, mixed, mg != nullptr, &w);
+    w.mg = mg;
+    w.mg32 = mg && mixed;
     std::memset(info, 0, sizeof(*info));
 
     KState hs;
     RBFFD_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(KState), st));
+    // with the multigrid preconditioner the outer system is not rescaled
+    const int jacobi = (o->jacobi && !mg) ? 1 : 0;
     setup_kernel<<<(int)std::min<int64_t>((N + kThreads - 1) / kThreads, sm_count() * 8), kThreads, 0, st>>>(
-        A->row_ptr, A->col, static_cast<const double*>(A->val), N, A->nnz, o->jacobi ? 1 : 0, w.d, w.dinv, w.d32,
-        w.dinv32, w.sigma32, w.st);
+        A->row_ptr, A->col, static_cast<const double*>(A->val), N, A->nnz, jacobi, w.d, w.dinv, w.d32, w.dinv32,
+        w.sigma32, w.st);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
     int rc = read_state(w, &hs, st);
     if (rc != RBFFD_OK) return rc;
     if (hs.bad) return RBFFD_ERR_INVALID_ARG;
+    // multigrid: the FP64 BiCGSTAB, its V-cycle in float32 when mixed
+    if (mg) return solve_fp64(*A, b, x, *o, w, st, info);
     return mixed ? solve_mixed(*A, *A32, b, x, *o, w, st, info) : solve_fp64(*A, b, x, *o, w, st, info);
 }
 
@@ -1093,7 +1130,8 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
 extern "C" size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* opts) {
     if (N <= 0) return 0;
     const bool mixed = opts && opts->precision == 1;
-    return rbffd::layout(nullptr, N, mixed, nullptr);
+    const bool mg = opts && opts->precond == 1;
+    return rbffd::layout(nullptr, N, mixed, mg, nullptr);
 }
 
 extern "C" int rbffd_solve(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x,
@@ -1108,6 +1146,7 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
                                    void* stream) {
     using namespace rbffd;
     if (!is_dirichlet && (dLdf || dLdg)) return RBFFD_ERR_INVALID_ARG;
+    if (opts && opts->precond != 0) return RBFFD_ERR_INVALID_ARG;  // the hierarchy is built for A, not A^T
     cudaStream_t st = as_stream(stream);
     const int rc = solve_impl(AT, AT32, dLdu, lambda, opts, info, ws, ws_bytes, st);
     if (rc != RBFFD_OK) return rc;

@@ -1,0 +1,954 @@
+// Geometric multigrid preconditioner on RBF-FD node sets (sm_103a).
+//
+// The paper stops at an explicit time loop and names the implicit solve as
+// the next step (Sec. VI); Jacobi-scaled BiCGSTAB on the RBF-FD Laplacian
+// needs O(1/h) iterations (tens of thousands at 4M nodes).  This file builds
+// a V-cycle whose every level is an RBF-FD discretisation of the same
+// problem, made by this library's own stages:
+//
+//  * coarsening: the nodes of a level are binned on a uniform grid of side
+//    c ~ 2x their mean spacing; each occupied cell keeps one node, a
+//    Dirichlet node if the cell has one, else the node nearest the cell
+//    centre (ties: lower index; one 64-bit atomicMin per node on the packed
+//    key (interior?, d^2 to the centre, index), so the choice does not depend
+//    on thread order).  c grows until at most half the nodes survive.
+//    Survivors keep their relative order, so coarse indices inherit the
+//    fine ordering's locality.
+//  * coarse operator: stencils, Laplacian weights (PHS r^3 + monomials of
+//    degree 2, n = 12) and the Dirichlet-row assembly of the fine problem,
+//    rerun on the coarse nodes (rediscretisation; Sec. II Eq. 1, Sec. IV).
+//  * prolongation P (ELL, 12 per row): PHS r^3 + degree-2 interpolation from
+//    the 12 nearest coarse nodes; rows of Dirichlet nodes are zero (the
+//    correction vanishes on the boundary).  Restriction R = (N_c / N_f) P^T
+//    (a deterministic transpose), zero rows at coarse Dirichlet nodes.
+//  * smoothing: nu damped Jacobi sweeps x += omega D^-1 (b - A x) before
+//    and after the coarse correction; the coarsest level (<= 512 nodes) is
+//    solved with its dense inverse (Gauss-Jordan with partial pivoting).
+//
+// A V-cycle is a fixed linear map (fixed sweeps, exact coarsest solve), so
+// it can right-precondition BiCGSTAB.  It runs in FP64, or in float32 values
+// and vectors (the mixed-precision solve: the preconditioner needs no FP64
+// accuracy, the outer FP64 BiCGSTAB keeps the residual exact).
+#include "common.cuh"
+#include "internal.cuh"
+#include "scan.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace rbffd {
+
+constexpr int kMgCoarsest = 512;  // dense inverse at or below this size
+constexpr int kMgK = 12;          // coarse nodes per interpolation stencil
+constexpr int kMgInterpM = 2;     // interpolation degree
+constexpr int kMgCoarseN = 12;    // coarse operator: stencil size
+constexpr int kMgCoarseM = 2;     //                  and degree
+constexpr uint32_t kMgMagic = 0x4D475242u;
+
+struct MgLevel {
+    int64_t N;
+    // operator of this level (level 0: the caller's matrix)
+    const int64_t* row_ptr;
+    const int* col;
+    const double* val;
+    const float* val32;
+    int64_t nnz;
+    int tpr;
+    double* dinv;
+    float* dinv32;
+    // geometry of coarse levels (level 0: the caller's arrays)
+    const double* xy;
+    const uint8_t* mask;
+    // transfer to the next level: P (N x kMgK, ELL row-major), R (CSR)
+    int32_t* pidx;
+    double* pval;
+    float* pval32;
+    int64_t* rrow;
+    int32_t* rcol;
+    double* rval;
+    float* rval32;
+    int rtpr;
+    // vectors (x and t alternate as the current iterate)
+    double *x, *t, *r, *b;
+    float *x32, *t32, *r32, *b32;
+    // coarsest: dense inverse, row-major N x N
+    double* minv;
+    float* minv32;
+};
+
+struct MgHierarchy {
+    uint32_t magic;
+    int n_levels;
+    int nu;
+    int has32;
+    double omega;
+    MgLevel lv[RBFFD_MG_MAX_LEVELS];
+};
+static_assert(sizeof(MgHierarchy) <= sizeof(rbffd_mg), "rbffd_mg is too small for the hierarchy");
+
+namespace {
+
+constexpr int kT = 256;
+
+// Rows of a CSR matrix, TPR lanes per row; every lane of a warp runs the same
+// number of trips (warp-uniform loop), so full-mask shuffles are safe.
+#define MG_ROWS(TPR, N, i, valid, ...)                                                 \
+    {                                                                                  \
+        const int64_t g0_ = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / (TPR); \
+        const int64_t ng_ = ((int64_t)gridDim.x * blockDim.x) / (TPR);                \
+        const int64_t off_ = (threadIdx.x & 31) / (TPR);                              \
+        for (int64_t base_ = g0_ - off_; base_ < (N); base_ += ng_) {                 \
+            const int64_t i = base_ + off_;                                           \
+            const bool valid = i < (N);                                               \
+            __VA_ARGS__                                                               \
+        }                                                                             \
+    }
+
+#define MG_ELEMS(N, i) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (N); i += (int64_t)gridDim.x * blockDim.x)
+
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fmaT<double>(double a, double b, double c) {
+    return fma(a, b, c);
+}
+template <>
+__device__ __forceinline__ float fmaT<float>(float a, float b, float c) {
+    return fmaf(a, b, c);
+}
+
+template <typename T, int TPR>
+__device__ __forceinline__ T row_sum(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                     const T* __restrict__ val, const T* __restrict__ x, int64_t row, int sub,
+                                     bool valid) {
+    int64_t a = 0, e = 0;
+    if (valid) {
+        a = __ldg(row_ptr + row);
+        e = __ldg(row_ptr + row + 1);
+    }
+    T sum = T(0);
+#pragma unroll 4
+    for (int64_t k = a + sub; k < e; k += TPR) sum = fmaT<T>(__ldg(val + k), __ldg(x + __ldg(col + k)), sum);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
+    return sum;
+}
+
+__device__ __forceinline__ bool stopped(const int* flag) { return flag && *(volatile const int*)flag != 0; }
+
+// x = omega D^-1 b (the first sweep from x = 0)
+template <typename T, typename BT>
+__global__ void __launch_bounds__(kT) mg_first_kernel(int64_t N, const BT* __restrict__ b, const T* __restrict__ dinv,
+                                                      T omega, T* __restrict__ x, const int* flag) {
+    if (stopped(flag)) return;
+    MG_ELEMS(N, i) x[i] = omega * dinv[i] * (T)b[i];
+}
+
+// xo = xi + omega D^-1 (b - A xi)
+template <typename T, typename BT, typename OT, int TPR>
+__global__ void __launch_bounds__(kT) mg_jacobi_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                       const T* __restrict__ val, int64_t N, const T* __restrict__ xi,
+                                                       const BT* __restrict__ b, const T* __restrict__ dinv, T omega,
+                                                       OT* __restrict__ xo, const int* flag) {
+    if (stopped(flag)) return;
+    const int sub = threadIdx.x & (TPR - 1);
+    MG_ROWS(TPR, N, i, valid, {
+        const T ax = row_sum<T, TPR>(row_ptr, col, val, xi, i, sub, valid);
+        if (valid && sub == 0) xo[i] = (OT)fmaT<T>(omega * dinv[i], (T)b[i] - ax, xi[i]);
+    })
+}
+
+// r = b - A x
+template <typename T, typename BT, int TPR>
+__global__ void __launch_bounds__(kT) mg_resid_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                      const T* __restrict__ val, int64_t N, const T* __restrict__ x,
+                                                      const BT* __restrict__ b, T* __restrict__ r, const int* flag) {
+    if (stopped(flag)) return;
+    const int sub = threadIdx.x & (TPR - 1);
+    MG_ROWS(TPR, N, i, valid, {
+        const T ax = row_sum<T, TPR>(row_ptr, col, val, x, i, sub, valid);
+        if (valid && sub == 0) r[i] = (T)b[i] - ax;
+    })
+}
+
+// y = R r (restriction, CSR with n rows)
+template <typename T, int TPR>
+__global__ void __launch_bounds__(kT) mg_restrict_kernel(const int64_t* __restrict__ row_ptr,
+                                                         const int* __restrict__ col, const T* __restrict__ val,
+                                                         int64_t n, const T* __restrict__ r, T* __restrict__ y,
+                                                         const int* flag) {
+    if (stopped(flag)) return;
+    const int sub = threadIdx.x & (TPR - 1);
+    MG_ROWS(TPR, n, i, valid, {
+        const T v = row_sum<T, TPR>(row_ptr, col, val, r, i, sub, valid);
+        if (valid && sub == 0) y[i] = v;
+    })
+}
+
+// x += P e (ELL, kMgK entries per row)
+template <typename T>
+__global__ void __launch_bounds__(kT) mg_prolong_kernel(int64_t N, const int32_t* __restrict__ pidx,
+                                                        const T* __restrict__ pval, const T* __restrict__ e,
+                                                        T* __restrict__ x, const int* flag) {
+    if (stopped(flag)) return;
+    MG_ELEMS(N, i) {
+        const int32_t* ip = pidx + i * kMgK;
+        const T* vp = pval + i * kMgK;
+        T acc = x[i];
+#pragma unroll
+        for (int j = 0; j < kMgK; ++j) acc = fmaT<T>(__ldg(vp + j), __ldg(e + __ldg(ip + j)), acc);
+        x[i] = acc;
+    }
+}
+
+// x = Minv b, one warp per row
+template <typename T, typename BT, typename OT>
+__global__ void __launch_bounds__(kT) mg_dense_kernel(int n, const T* __restrict__ minv, const BT* __restrict__ b,
+                                                      OT* __restrict__ x, const int* flag) {
+    if (stopped(flag)) return;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        T acc = T(0);
+        for (int j = lane; j < n; j += 32) acc = fmaT<T>(minv[(int64_t)i * n + j], (T)b[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[i] = (OT)acc;
+    }
+}
+
+// ------------------------------------------------------------------ setup --
+struct MgBox {
+    double mnx, mny, mxx, mxy;
+};
+
+__global__ void __launch_bounds__(kT) mg_bbox_kernel(const double2* __restrict__ xy, int64_t N, MgBox* out) {
+    double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+    MG_ELEMS(N, i) {
+        const double2 p = xy[i];
+        mnx = fmin(mnx, p.x);
+        mny = fmin(mny, p.y);
+        mxx = fmax(mxx, p.x);
+        mxy = fmax(mxy, p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fmin(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = fmin(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    __shared__ MgBox sh[kT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = MgBox{mnx, mny, mxx, mxy};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        MgBox r = sh[0];
+        for (int k = 1; k < kT / 32; ++k) {
+            r.mnx = fmin(r.mnx, sh[k].mnx);
+            r.mny = fmin(r.mny, sh[k].mny);
+            r.mxx = fmax(r.mxx, sh[k].mxx);
+            r.mxy = fmax(r.mxy, sh[k].mxy);
+        }
+        out[blockIdx.x] = r;
+    }
+}
+
+struct CellGrid {
+    double x0, y0, inv_c;
+    int gx, gy;
+};
+
+__device__ __forceinline__ int64_t cell_of(const CellGrid& g, double x, double y) {
+    int cx = (int)floor((x - g.x0) * g.inv_c);
+    int cy = (int)floor((y - g.y0) * g.inv_c);
+    cx = cx < 0 ? 0 : (cx >= g.gx ? g.gx - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= g.gy ? g.gy - 1 : cy);
+    return (int64_t)cy * g.gx + cx;
+}
+
+// Packed ranking key: bit 63 = interior node (Dirichlet nodes win), bits
+// 62..31 = float32 bits of (d / c)^2 to the cell centre (non-negative, so
+// monotone as an integer; < 2^31), bits 30..0 = node index.
+__global__ void __launch_bounds__(kT) mg_mark_kernel(const double2* __restrict__ xy, const uint8_t* __restrict__ mask,
+                                                     int64_t N, CellGrid g, unsigned long long* __restrict__ best) {
+    MG_ELEMS(N, i) {
+        const double2 p = xy[i];
+        const int64_t c = cell_of(g, p.x, p.y);
+        const int cx = (int)(c % g.gx), cy = (int)(c / g.gx);
+        const double ux = (p.x - g.x0) * g.inv_c - (cx + 0.5);
+        const double uy = (p.y - g.y0) * g.inv_c - (cy + 0.5);
+        float d2 = (float)(ux * ux + uy * uy);
+        if (!(d2 >= 0.f) || d2 > 1e30f) d2 = 1e30f;
+        const unsigned long long key = ((unsigned long long)(mask[i] ? 0u : 1u) << 63) |
+                                       ((unsigned long long)__float_as_uint(d2) << 31) | (unsigned long long)i;
+        atomicMin(best + c, key);
+    }
+}
+
+__global__ void __launch_bounds__(kT) mg_select_kernel(const double2* __restrict__ xy, int64_t N, CellGrid g,
+                                                       const unsigned long long* __restrict__ best,
+                                                       int* __restrict__ sel) {
+    MG_ELEMS(N, i) {
+        const double2 p = xy[i];
+        const int64_t c = cell_of(g, p.x, p.y);
+        sel[i] = ((best[c] & 0x7fffffffull) == (unsigned long long)i) ? 1 : 0;
+    }
+}
+
+struct SelLoad {
+    const int* sel;
+    __device__ int operator()(int64_t i) const { return sel[i]; }
+};
+
+__global__ void __launch_bounds__(kT) mg_gather_kernel(const double2* __restrict__ xy, const uint8_t* __restrict__ mask,
+                                                       int64_t N, const int* __restrict__ sel,
+                                                       const int* __restrict__ pos, double2* __restrict__ cxy,
+                                                       uint8_t* __restrict__ cmask) {
+    MG_ELEMS(N, i) {
+        if (sel[i]) {
+            const int k = pos[i];
+            cxy[k] = xy[i];
+            cmask[k] = mask[i] ? 1 : 0;
+        }
+    }
+}
+
+// D^-1 from the diagonal of a CSR matrix (1 where the diagonal is zero or
+// missing); float copies of dinv and, if val32 != NULL, of the values.
+__global__ void __launch_bounds__(kT) mg_diag_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                     const double* __restrict__ val, int64_t N,
+                                                     double* __restrict__ dinv, float* __restrict__ dinv32,
+                                                     int* __restrict__ bad) {
+    int nb = 0;
+    MG_ELEMS(N, i) {
+        double d = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] == (int)i) d = val[k];
+        const bool ok = d != 0.0 && isfinite(d);
+        nb |= ok ? 0 : 1;
+        const double iv = ok ? 1.0 / d : 1.0;
+        dinv[i] = iv;
+        dinv32[i] = __double2float_rn(iv);
+    }
+    if (nb) atomicOr(bad, 1);
+}
+
+// Interpolation rows: zero at Dirichlet nodes; where the interpolation
+// system was singular (its nodes on one conic), the value of the nearest
+// coarse node; float copy; CSR row pointer of the ELL layout.
+__global__ void __launch_bounds__(kT) mg_pfix_kernel(int64_t N, const uint8_t* __restrict__ mask,
+                                                     const int* __restrict__ pstat, double* __restrict__ pval,
+                                                     float* __restrict__ pval32, int64_t* __restrict__ prow) {
+    MG_ELEMS(N, i) {
+        const bool dir = mask[i] != 0;
+        const bool sing = pstat[i] != 0;
+        for (int j = 0; j < kMgK; ++j) {
+            const int64_t e = i * kMgK + j;
+            const double v = dir ? 0.0 : (sing ? (j == 0 ? 1.0 : 0.0) : pval[e]);
+            pval[e] = v;
+            pval32[e] = __double2float_rn(v);
+        }
+        prow[i] = i * kMgK;
+        if (i == N - 1) prow[N] = N * kMgK;
+    }
+}
+
+// R = scale P^T with zero rows at coarse Dirichlet nodes; float copy.
+__global__ void __launch_bounds__(kT) mg_rscale_kernel(const int64_t* __restrict__ rrow, int64_t Nc,
+                                                       const uint8_t* __restrict__ cmask, double scale,
+                                                       double* __restrict__ rval, float* __restrict__ rval32) {
+    MG_ELEMS(Nc, c) {
+        const double f = cmask[c] ? 0.0 : scale;
+        for (int64_t k = rrow[c]; k < rrow[c + 1]; ++k) {
+            const double v = rval[k] * f;
+            rval[k] = v;
+            rval32[k] = __double2float_rn(v);
+        }
+    }
+}
+
+// A singular stencil at an interior node (Dirichlet rows ignore weights).
+__global__ void __launch_bounds__(kT) mg_count_kernel(const int* __restrict__ stat, const uint8_t* __restrict__ mask,
+                                                      int64_t N, int* __restrict__ bad) {
+    int nb = 0;
+    MG_ELEMS(N, i) nb |= (stat[i] && !mask[i]) ? 1 : 0;
+    if (nb) atomicOr(bad, 1);
+}
+
+// Dense [A | I] (n x 2n, row-major) from CSR.
+__global__ void __launch_bounds__(kT) mg_dense_build_kernel(const int64_t* __restrict__ row_ptr,
+                                                            const int* __restrict__ col,
+                                                            const double* __restrict__ val, int n,
+                                                            double* __restrict__ aug) {
+    const int64_t total = (int64_t)n * 2 * n;
+    MG_ELEMS(total, e) aug[e] = 0.0;
+    __syncthreads();  // (single block: the zero fill precedes the scatter)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) aug[(int64_t)i * 2 * n + col[k]] += val[k];
+        aug[(int64_t)i * 2 * n + n + i] = 1.0;
+    }
+}
+
+// Gauss-Jordan step k (one block): pivot = largest |a_ik|, i >= k (lowest i on
+// ties), swap rows k and pivot, scale row k, save the column multipliers.
+__global__ void __launch_bounds__(kT) mg_gj_pivot_kernel(double* __restrict__ aug, int n, int k,
+                                                         double* __restrict__ f, int* __restrict__ bad) {
+    __shared__ double sv[kT];
+    __shared__ int si[kT];
+    __shared__ double piv;
+    __shared__ int prow;
+    const int n2 = 2 * n;
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+        const double v = fabs(aug[(int64_t)i * n2 + k]);
+        if (v > best) {
+            best = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double ov = sv[threadIdx.x + o];
+            const int oi = si[threadIdx.x + o];
+            if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        prow = si[0];
+        if (!(sv[0] > 0.0) || prow >= n) {
+            *bad = 1;
+            prow = k;
+        }
+    }
+    __syncthreads();
+    const int p = prow;
+    if (p != k)
+        for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+            const double t = aug[(int64_t)k * n2 + j];
+            aug[(int64_t)k * n2 + j] = aug[(int64_t)p * n2 + j];
+            aug[(int64_t)p * n2 + j] = t;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double d = aug[(int64_t)k * n2 + k];
+        piv = (d != 0.0) ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n2; j += blockDim.x) aug[(int64_t)k * n2 + j] *= piv;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : aug[(int64_t)i * n2 + k];
+}
+
+// Gauss-Jordan elimination of column k from every other row.
+__global__ void __launch_bounds__(kT) mg_gj_elim_kernel(double* __restrict__ aug, int n, int k,
+                                                        const double* __restrict__ f) {
+    const int n2 = 2 * n;
+    const int64_t total = (int64_t)n * n2;
+    MG_ELEMS(total, e) {
+        const int i = (int)(e / n2), j = (int)(e - (int64_t)i * n2);
+        if (i != k) aug[e] = fma(-f[i], aug[(int64_t)k * n2 + j], aug[e]);
+    }
+}
+
+__global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restrict__ aug, int n,
+                                                           double* __restrict__ minv, float* __restrict__ minv32) {
+    const int64_t total = (int64_t)n * n;
+    MG_ELEMS(total, e) {
+        const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+        const double v = aug[(int64_t)i * 2 * n + n + j];
+        minv[e] = v;
+        minv32[e] = __double2float_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------- host --
+int tpr_for(int64_t rows, int64_t nnz) {
+    const double L = (double)nnz / (double)std::max<int64_t>(rows, 1);
+    if (L >= 40) return 4;
+    if (L >= 8) return 2;
+    return 1;
+}
+
+int blocks_for(int64_t threads) {
+    const int64_t b = (threads + kT - 1) / kT;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 16));
+}
+
+// Upper bounds of the level sizes: each coarsening keeps at most half.
+std::vector<int64_t> level_bounds(int64_t N) {
+    std::vector<int64_t> nb{N};
+    while (nb.back() > kMgCoarsest && (int)nb.size() < RBFFD_MG_MAX_LEVELS) nb.push_back(nb.back() / 2);
+    return nb;
+}
+
+struct MgScratch {
+    unsigned long long* cells;
+    int* sel;
+    int* pos;
+    int* sums;
+    MgBox* box;
+    int* flags;  // [0] singular / bad, [1] spare
+    int* pstat;
+    int32_t* sidx;   // coarse stencils
+    double* sw;      // coarse weights
+    int32_t* sstat;  // coarse weight status
+    void* knn_ws;
+    size_t knn_bytes;
+    void* asm_ws;
+    size_t asm_bytes;
+    void* tr_ws;
+    size_t tr_bytes;
+    double* aug;
+    double* gjf;
+    int64_t* prow;
+};
+
+constexpr int kBoxParts = 64;
+
+// Carves the workspace; with ws == NULL only sizes it.
+size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
+    const std::vector<int64_t> nb = level_bounds(N);
+    Carver c(ws);
+    MgScratch t{};
+    size_t knn_b = 0, asm_b = 0, tr_b = 0;
+    for (size_t l = 0; l < nb.size(); ++l) {
+        knn_b = std::max(knn_b, rbffd_stencils_workspace_size(std::max<int64_t>(nb[l], kMgCoarseN), kMgCoarseN));
+        asm_b = std::max(asm_b, rbffd_assemble_workspace_size(nb[l]));
+        tr_b = std::max(tr_b, rbffd_transpose_workspace_size(nb[l]));
+    }
+    t.cells = c.take<unsigned long long>((size_t)(2 * N + 16));
+    t.sel = c.take<int>(N);
+    t.pos = c.take<int>(N + 1);
+    t.sums = c.take<int>(scan_tiles(N) + 1);
+    t.box = c.take<MgBox>(kBoxParts);
+    t.flags = c.take<int>(64);
+    t.pstat = c.take<int>(N);
+    t.prow = c.take<int64_t>(N + 1);
+    const int64_t n1 = nb.size() > 1 ? nb[1] : 1;
+    t.sidx = c.take<int32_t>((size_t)n1 * kMgCoarseN);
+    t.sw = c.take<double>((size_t)n1 * kMgCoarseN);
+    t.sstat = c.take<int32_t>(n1);
+    t.knn_ws = c.take<char>(knn_b);
+    t.knn_bytes = knn_b;
+    t.asm_ws = c.take<char>(asm_b);
+    t.asm_bytes = asm_b;
+    t.tr_ws = c.take<char>(tr_b);
+    t.tr_bytes = tr_b;
+    t.aug = c.take<double>((size_t)kMgCoarsest * 2 * kMgCoarsest);
+    t.gjf = c.take<double>(kMgCoarsest);
+    MgHierarchy hh{};
+    for (size_t l = 0; l < nb.size(); ++l) {
+        const int64_t n = nb[l];
+        MgLevel& L = hh.lv[l];
+        if (l > 0) {
+            double* xy = c.take<double>((size_t)2 * n);
+            L.xy = xy;
+            uint8_t* mk = c.take<uint8_t>(n);
+            L.mask = mk;
+            int64_t* rp = c.take<int64_t>(n + 1);
+            L.row_ptr = rp;
+            int* cl = c.take<int>((size_t)n * kMgCoarseN);
+            L.col = cl;
+            double* v = c.take<double>((size_t)n * kMgCoarseN);
+            L.val = v;
+            float* v32 = c.take<float>((size_t)n * kMgCoarseN);
+            L.val32 = v32;
+        }
+        L.dinv = c.take<double>(n);
+        L.dinv32 = c.take<float>(n);
+        L.x = c.take<double>(n);
+        L.t = c.take<double>(n);
+        L.r = c.take<double>(n);
+        L.b = c.take<double>(n);
+        L.x32 = c.take<float>(n);
+        L.t32 = c.take<float>(n);
+        L.r32 = c.take<float>(n);
+        L.b32 = c.take<float>(n);
+        if (l + 1 < nb.size()) {
+            L.pidx = c.take<int32_t>((size_t)n * kMgK);
+            L.pval = c.take<double>((size_t)n * kMgK);
+            L.pval32 = c.take<float>((size_t)n * kMgK);
+            L.rrow = c.take<int64_t>(n + 1);
+            L.rcol = c.take<int32_t>((size_t)n * kMgK);
+            L.rval = c.take<double>((size_t)n * kMgK);
+            L.rval32 = c.take<float>((size_t)n * kMgK);
+        }
+    }
+    // the dense inverse goes with whichever level ends up coarsest
+    double* minv = c.take<double>((size_t)kMgCoarsest * kMgCoarsest);
+    float* minv32 = c.take<float>((size_t)kMgCoarsest * kMgCoarsest);
+    for (size_t l = 0; l < nb.size(); ++l) {
+        hh.lv[l].minv = minv;
+        hh.lv[l].minv32 = minv32;
+    }
+    if (h) *h = hh;
+    if (s) *s = t;
+    return c.off;
+}
+
+// Selects the coarse nodes of level l into level l + 1; returns their count
+// in *nc.
+int coarsen(const MgLevel& L, MgLevel& C, const MgScratch& s, cudaStream_t st, int64_t* nc) {
+    const int64_t N = L.N;
+    const double2* xy = reinterpret_cast<const double2*>(L.xy);
+    mg_bbox_kernel<<<kBoxParts, kT, 0, st>>>(xy, N, s.box);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    MgBox parts[kBoxParts];
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(parts, s.box, sizeof(parts), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    MgBox bx = parts[0];
+    for (int k = 1; k < kBoxParts; ++k) {
+        bx.mnx = std::min(bx.mnx, parts[k].mnx);
+        bx.mny = std::min(bx.mny, parts[k].mny);
+        bx.mxx = std::max(bx.mxx, parts[k].mxx);
+        bx.mxy = std::max(bx.mxy, parts[k].mxy);
+    }
+    const double W = bx.mxx - bx.mnx, H = bx.mxy - bx.mny;
+    if (!(std::isfinite(W) && std::isfinite(H)) || !(W > 0.0 || H > 0.0)) return RBFFD_ERR_INVALID_ARG;
+    double c = (W > 0.0 && H > 0.0) ? 2.0 * std::sqrt(W * H / (double)N) : 2.0 * std::max(W, H) / (double)N;
+    for (int attempt = 0; attempt < 200; ++attempt, c *= 1.25) {
+        CellGrid g;
+        g.x0 = bx.mnx;
+        g.y0 = bx.mny;
+        g.inv_c = 1.0 / c;
+        const double gx = std::floor(W / c) + 1.0, gy = std::floor(H / c) + 1.0;
+        if (gx * gy > (double)(2 * N + 16)) continue;
+        g.gx = (int)gx;
+        g.gy = (int)gy;
+        const int64_t cells = (int64_t)g.gx * g.gy;
+        RBFFD_CUDA_TRY(cudaMemsetAsync(s.cells, 0xff, sizeof(unsigned long long) * cells, st));
+        mg_mark_kernel<<<blocks_for(N), kT, 0, st>>>(xy, L.mask, N, g, s.cells);
+        mg_select_kernel<<<blocks_for(N), kT, 0, st>>>(xy, N, g, s.cells, s.sel);
+        note_launches(2);
+        RBFFD_LAUNCH_CHECK();
+        RBFFD_CUDA_TRY(exclusive_scan<int>(SelLoad{s.sel}, N, s.pos, s.sums, s.pos + N, st));
+        int cnt = 0;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnt, s.pos + N, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((int64_t)cnt > N / 2) continue;
+        if (cnt <= kMgK) return RBFFD_ERR_INVALID_ARG;  // degenerate node set
+        mg_gather_kernel<<<blocks_for(N), kT, 0, st>>>(xy, L.mask, N, s.sel, s.pos,
+                                                       reinterpret_cast<double2*>(const_cast<double*>(C.xy)),
+                                                       const_cast<uint8_t*>(C.mask));
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        *nc = cnt;
+        return RBFFD_OK;
+    }
+    return RBFFD_ERR_INVALID_ARG;
+}
+
+int dense_inverse(const MgLevel& L, const MgScratch& s, cudaStream_t st) {
+    const int n = (int)L.N;
+    mg_dense_build_kernel<<<1, kT, 0, st>>>(L.row_ptr, L.col, L.val, n, s.aug);
+    note_launches(1);
+    for (int k = 0; k < n; ++k) {
+        mg_gj_pivot_kernel<<<1, kT, 0, st>>>(s.aug, n, k, s.gjf, s.flags);
+        mg_gj_elim_kernel<<<blocks_for((int64_t)n * 2 * n), kT, 0, st>>>(s.aug, n, k, s.gjf);
+    }
+    note_launches(2 * n);
+    mg_dense_copy_kernel<<<blocks_for((int64_t)n * n), kT, 0, st>>>(s.aug, n, L.minv, L.minv32);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+// ---- V-cycle ----------------------------------------------------------------
+template <typename T>
+struct Sel;
+template <>
+struct Sel<double> {
+    static const double* val(const MgLevel& L) { return L.val; }
+    static const double* dinv(const MgLevel& L) { return L.dinv; }
+    static const double* pval(const MgLevel& L) { return L.pval; }
+    static const double* rval(const MgLevel& L) { return L.rval; }
+    static const double* minv(const MgLevel& L) { return L.minv; }
+    static double* x(const MgLevel& L) { return L.x; }
+    static double* t(const MgLevel& L) { return L.t; }
+    static double* r(const MgLevel& L) { return L.r; }
+    static double* b(const MgLevel& L) { return L.b; }
+};
+template <>
+struct Sel<float> {
+    static const float* val(const MgLevel& L) { return L.val32; }
+    static const float* dinv(const MgLevel& L) { return L.dinv32; }
+    static const float* pval(const MgLevel& L) { return L.pval32; }
+    static const float* rval(const MgLevel& L) { return L.rval32; }
+    static const float* minv(const MgLevel& L) { return L.minv32; }
+    static float* x(const MgLevel& L) { return L.x32; }
+    static float* t(const MgLevel& L) { return L.t32; }
+    static float* r(const MgLevel& L) { return L.r32; }
+    static float* b(const MgLevel& L) { return L.b32; }
+};
+
+template <typename T, typename BT, typename OT>
+void jacobi(const MgLevel& L, const T* xi, const BT* b, T omega, OT* xo, const int* flag, cudaStream_t st) {
+    const int g = blocks_for(L.N * L.tpr);
+    const T* val = Sel<T>::val(L);
+    const T* dinv = Sel<T>::dinv(L);
+    switch (L.tpr) {
+        case 4: mg_jacobi_kernel<T, BT, OT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
+        case 2: mg_jacobi_kernel<T, BT, OT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
+        default: mg_jacobi_kernel<T, BT, OT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
+    }
+}
+
+template <typename T, typename BT>
+void resid(const MgLevel& L, const T* x, const BT* b, T* r, const int* flag, cudaStream_t st) {
+    const int g = blocks_for(L.N * L.tpr);
+    const T* val = Sel<T>::val(L);
+    switch (L.tpr) {
+        case 4: mg_resid_kernel<T, BT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
+        case 2: mg_resid_kernel<T, BT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
+        default: mg_resid_kernel<T, BT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
+    }
+}
+
+template <typename T>
+void restrict_to(const MgLevel& L, int64_t nc, const T* r, T* bc, const int* flag, cudaStream_t st) {
+    const int g = blocks_for(nc * L.rtpr);
+    const T* val = Sel<T>::rval(L);
+    switch (L.rtpr) {
+        case 4: mg_restrict_kernel<T, 4><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
+        case 2: mg_restrict_kernel<T, 2><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
+        default: mg_restrict_kernel<T, 1><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
+    }
+}
+
+// One level of the cycle: b (BT) in, result in x (OT) for level 0, in the
+// level's own current-iterate buffer otherwise (returned).
+template <typename T>
+T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, double* out, const int* flag,
+               cudaStream_t st, int* launches, std::vector<int>* ev) {
+    const MgLevel& L = h.lv[l];
+    const T omega = (T)h.omega;
+    const bool last_level = (l == h.n_levels - 1);
+    const bool top = (l == 0);
+    T* cur = Sel<T>::x(L);
+    T* oth = Sel<T>::t(L);
+    auto launch_first = [&](T* x) {
+        const int g = blocks_for(L.N);
+        if (b_is_double)
+            mg_first_kernel<T, double><<<g, kT, 0, st>>>(L.N, static_cast<const double*>(bin), Sel<T>::dinv(L), omega, x, flag);
+        else
+            mg_first_kernel<T, T><<<g, kT, 0, st>>>(L.N, static_cast<const T*>(bin), Sel<T>::dinv(L), omega, x, flag);
+        ++*launches;
+    };
+    auto sweep = [&](T* xi, T* xo, double* xo64) {
+        // finest-level sweeps are timed when profiling (algorithmic bytes:
+        // matrix, row pointers, iterate once, rhs, D^-1, result)
+        const int e = (top && ev) ? prof_begin(st) : -1;
+        if (b_is_double) {
+            const double* b = static_cast<const double*>(bin);
+            if (xo64) jacobi<T, double, double>(L, xi, b, omega, xo64, flag, st);
+            else jacobi<T, double, T>(L, xi, b, omega, xo, flag, st);
+        } else {
+            const T* b = static_cast<const T*>(bin);
+            if (xo64) jacobi<T, T, double>(L, xi, b, omega, xo64, flag, st);
+            else jacobi<T, T, T>(L, xi, b, omega, xo, flag, st);
+        }
+        if (top && ev) {
+            const int64_t bytes = L.nnz * (int64_t)(sizeof(T) + 4) + 8 * (L.N + 1) +
+                                  L.N * (int64_t)(2 * sizeof(T) + (b_is_double ? 8 : sizeof(T)) + sizeof(T)) +
+                                  (xo64 ? L.N * (int64_t)(8 - sizeof(T)) : 0);
+            prof_end(e, st, kProfMg, bytes);
+            ev->push_back(e);
+        }
+        ++*launches;
+    };
+    if (last_level) {
+        const int g = blocks_for((int64_t)L.N * 32);
+        const T* mv = Sel<T>::minv(L);
+        if (top) {
+            mg_dense_kernel<T, double, double><<<g, kT, 0, st>>>((int)L.N, mv, static_cast<const double*>(bin), out, flag);
+        } else {
+            mg_dense_kernel<T, T, T><<<g, kT, 0, st>>>((int)L.N, mv, static_cast<const T*>(bin), cur, flag);
+        }
+        ++*launches;
+        return cur;
+    }
+    // pre-smoothing
+    launch_first(cur);
+    for (int k = 1; k < h.nu; ++k) {
+        sweep(cur, oth, nullptr);
+        std::swap(cur, oth);
+    }
+    // residual, restriction, coarse correction
+    if (b_is_double) resid<T, double>(L, cur, static_cast<const double*>(bin), Sel<T>::r(L), flag, st);
+    else resid<T, T>(L, cur, static_cast<const T*>(bin), Sel<T>::r(L), flag, st);
+    const MgLevel& C = h.lv[l + 1];
+    restrict_to<T>(L, C.N, Sel<T>::r(L), Sel<T>::b(C), flag, st);
+    *launches += 2;
+    T* e = cycle_level<T>(h, l + 1, Sel<T>::b(C), false, nullptr, flag, st, launches, ev);
+    mg_prolong_kernel<T><<<blocks_for(L.N), kT, 0, st>>>(L.N, L.pidx, Sel<T>::pval(L), e, cur, flag);
+    ++*launches;
+    // post-smoothing; the last sweep of level 0 writes the FP64 output
+    for (int k = 0; k < h.nu; ++k) {
+        const bool final_top = top && k == h.nu - 1;
+        sweep(cur, oth, final_top ? out : nullptr);
+        if (!final_top) std::swap(cur, oth);
+    }
+    return cur;
+}
+
+}  // namespace
+
+const MgHierarchy* mg_hierarchy(const rbffd_mg* h) {
+    if (!h) return nullptr;
+    const MgHierarchy* m = reinterpret_cast<const MgHierarchy*>(h);
+    if (m->magic != kMgMagic || m->n_levels < 1) return nullptr;
+    return m;
+}
+
+int64_t mg_fine_rows(const MgHierarchy* h) { return h ? h->lv[0].N : 0; }
+
+bool mg_has_fp32(const MgHierarchy* h) { return h && h->has32; }
+
+int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
+             std::vector<int>* ev) {
+    if (!h || !b || !x) return RBFFD_ERR_INVALID_ARG;
+    if (fp32 && !h->has32) return RBFFD_ERR_INVALID_ARG;
+    int launches = 0;
+    if (fp32) cycle_level<float>(*h, 0, b, true, x, flag, st, &launches, ev);
+    else cycle_level<double>(*h, 0, b, true, x, flag, st, &launches, ev);
+    note_launches(launches);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+// ---------------------------------------------------------------- C ABI -----
+extern "C" size_t rbffd_mg_workspace_size(int64_t N, int64_t nnz) {
+    (void)nnz;  // the fine matrix stays the caller's
+    if (N <= 0 || N > 0x7fffffffLL) return 0;
+    return rbffd::mg_layout(nullptr, N, nullptr, nullptr);
+}
+
+extern "C" int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes) {
+    const rbffd::MgHierarchy* h = rbffd::mg_hierarchy(mg);
+    if (!h) return 0;
+    if (n_nodes)
+        for (int l = 0; l < RBFFD_MG_MAX_LEVELS; ++l) n_nodes[l] = l < h->n_levels ? h->lv[l].N : 0;
+    return h->n_levels;
+}
+
+extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
+                              const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
+                              size_t ws_bytes, void* stream) {
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    std::memset(mg, 0, sizeof(*mg));
+    if (!xy || !is_dirichlet || !A || !A->row_ptr || !A->col || !A->val || A->dtype != 0 || N <= 0 ||
+        N > 0x7fffffffLL || A->n_rows != N || A->nnz <= 0)
+        return RBFFD_ERR_INVALID_ARG;
+    if (A32 && (!A32->val || A32->dtype != 1 || A32->n_rows != N || A32->nnz != A->nnz || A32->row_ptr != A->row_ptr ||
+                A32->col != A->col))
+        return RBFFD_ERR_INVALID_ARG;
+    if (nu < 1 || nu > 8 || !(omega > 0.0 && omega < 1.0)) return RBFFD_ERR_INVALID_ARG;
+    if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
+    const size_t need = mg_layout(nullptr, N, nullptr, nullptr);
+    if (ws_bytes < need) return RBFFD_ERR_WORKSPACE;
+    cudaStream_t st = as_stream(stream);
+
+    MgHierarchy h{};
+    MgScratch s{};
+    mg_layout(ws, N, &h, &s);
+    h.magic = 0;
+    h.nu = nu;
+    h.omega = omega;
+    h.has32 = A32 ? 1 : 0;
+    RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
+
+    MgLevel& L0 = h.lv[0];
+    L0.N = N;
+    L0.row_ptr = A->row_ptr;
+    L0.col = A->col;
+    L0.val = static_cast<const double*>(A->val);
+    L0.val32 = A32 ? static_cast<const float*>(A32->val) : nullptr;
+    L0.nnz = A->nnz;
+    L0.tpr = tpr_for(N, A->nnz);
+    L0.xy = xy;
+    L0.mask = is_dirichlet;
+    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, L0.dinv, L0.dinv32, s.flags + 1);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+
+    int levels = 1;
+    int rc = RBFFD_OK;
+    for (int l = 0;; ++l) {
+        MgLevel& L = h.lv[l];
+        if (L.N <= kMgCoarsest || l + 1 >= RBFFD_MG_MAX_LEVELS) {
+            if (L.N > kMgCoarsest) return RBFFD_ERR_INVALID_ARG;
+            if ((rc = dense_inverse(L, s, st)) != RBFFD_OK) return rc;
+            levels = l + 1;
+            break;
+        }
+        MgLevel& C = h.lv[l + 1];
+        int64_t nc = 0;
+        if ((rc = coarsen(L, C, s, st, &nc)) != RBFFD_OK) return rc;
+        C.N = nc;
+        // coarse operator: stencils, weights, Dirichlet-row assembly
+        if ((rc = rbffd_stencils(C.xy, nc, kMgCoarseN, s.sidx, s.knn_ws, s.knn_bytes, st)) != RBFFD_OK) return rc;
+        if ((rc = rbffd_weights(C.xy, s.sidx, nc, kMgCoarseN, kMgCoarseM, s.sw, s.sstat, st)) != RBFFD_OK) return rc;
+        mg_count_kernel<<<blocks_for(nc), kT, 0, st>>>(s.sstat, C.mask, nc, s.flags);
+        note_launches(1);
+        int64_t* crow = const_cast<int64_t*>(C.row_ptr);
+        if ((rc = rbffd_assemble_pattern(C.mask, nc, kMgCoarseN, crow, s.asm_ws, s.asm_bytes, st)) != RBFFD_OK)
+            return rc;
+        int64_t cnnz = 0;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnnz, crow + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((rc = rbffd_assemble(s.sidx, s.sw, C.mask, nc, kMgCoarseN, crow, cnnz, const_cast<int*>(C.col),
+                                 const_cast<double*>(C.val), const_cast<float*>(C.val32), st)) != RBFFD_OK)
+            return rc;
+        C.nnz = cnnz;
+        C.tpr = tpr_for(nc, cnnz);
+        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, C.dinv, C.dinv32, s.flags + 1);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        // prolongation: interpolation from the kMgK nearest coarse nodes
+        if ((rc = knn_search(C.xy, nc, L.xy, L.N, kMgK, L.pidx, s.knn_ws, s.knn_bytes, st)) != RBFFD_OK) return rc;
+        if ((rc = interp_weights(C.xy, nc, L.xy, L.N, L.pidx, kMgK, kMgInterpM, L.pval, s.pstat, st)) != RBFFD_OK)
+            return rc;
+        mg_pfix_kernel<<<blocks_for(L.N), kT, 0, st>>>(L.N, L.mask, s.pstat, L.pval, L.pval32, s.prow);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        // restriction: (N_c / N_f) P^T, P viewed as an N_f x N_f matrix
+        rbffd_csr P{};
+        P.n_rows = L.N;
+        P.nnz = L.N * kMgK;
+        P.row_ptr = s.prow;
+        P.col = L.pidx;
+        P.val = L.pval;
+        P.dtype = 0;
+        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
+        mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, C.mask, (double)nc / (double)L.N, L.rval,
+                                                        L.rval32);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        L.rtpr = tpr_for(nc, L.N * kMgK);
+    }
+    int flags[2] = {0, 0};
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags[0]) return RBFFD_ERR_SINGULAR_STENCIL;
+    h.n_levels = levels;
+    h.magic = kMgMagic;
+    std::memcpy(mg, &h, sizeof(h));
+    return RBFFD_OK;
+}

@@ -25,6 +25,7 @@
 //    P are built (when it is large enough), so a warp needs no extra shared
 //    memory and four m = 6 stencils (M = 84) fit on one SM.
 #include "common.cuh"
+#include "internal.cuh"
 
 #include <algorithm>
 #include <cstdlib>
@@ -58,10 +59,15 @@ WeightsGeom weights_geom(int n, int m) {
 
 // Warp-per-stencil kernel.  Dynamic shared memory: warps_per_block *
 // smem_doubles doubles.
+//   op 0 (Laplacian): centres cxy = xy, weights of lap at the centre.
+//   op 1 (interpolation): centres cxy are other points (N of them; the
+//        stencils index the Nd points xy); weights of the value at the
+//        centre, right-hand side [ |xh_j|^3 ; p_k(0) ], no rescaling.
 __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
                                                       int N, int n, int m, int s, int M, int LD, int coords_zb,
                                                       int smem_doubles, double* __restrict__ w,
-                                                      int* __restrict__ node_status) {
+                                                      int* __restrict__ node_status,
+                                                      const double2* __restrict__ cxy, int Nd, int op) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
 
     for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
         const int* sten = idx + (int64_t)node * n;
-        const double2 c = xy[node];
+        const double2 c = cxy[node];
 
         // ---- shift, scale --------------------------------------------------
         // Coordinates go to a linear scratch of 2n doubles.  In the zero
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         int bad_index = 0;
         for (int j = lane; j < n; j += 32) {
             const int sj = sten[j];
-            const bool ok = (unsigned)sj < (unsigned)N;  // never read outside xy
+            const bool ok = (unsigned)sj < (unsigned)Nd;  // never read outside xy
             bad_index |= ok ? 0 : 1;
             const double2 p = ok ? xy[sj] : c;
             const double dx = __dadd_rn(p.x, -c.x);
@@ -136,7 +142,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                 A[(size_t)j * LD + j] = 0.0;
                 const double xh = cs(2 * j), yh = cs(2 * j + 1);
                 const double rj = __dsqrt_rn(__dadd_rn(__dmul_rn(xh, xh), __dmul_rn(yh, yh)));
-                A[(size_t)j * LD + M] = __dmul_rn(9.0, rj);
+                A[(size_t)j * LD + M] = op ? __dmul_rn(__dmul_rn(rj, rj), rj) : __dmul_rn(9.0, rj);
                 // monomials x^a y^b, graded order; powers by repeated products
                 double xp[9], yp[9];
                 xp[0] = 1.0;
@@ -164,7 +170,9 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
             int col = 0;
             for (int d = 0; d <= m; ++d)
                 for (int i = 0; i <= d; ++i, ++col)
-                    if (lane == 0) A[(size_t)(n + col) * LD + M] = ((d == 2 && (i == 0 || i == 2)) ? 2.0 : 0.0);
+                    if (lane == 0)
+                        A[(size_t)(n + col) * LD + M] =
+                            op ? (d == 0 ? 1.0 : 0.0) : ((d == 2 && (i == 0 || i == 2)) ? 2.0 : 0.0);
         }
         __syncwarp();
 
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         int bad = singular;
         double* wout = w + (int64_t)node * n;
         for (int j = lane; j < n; j += 32) {
-            const double v = singular ? 0.0 : __ddiv_rn(A[(size_t)j * LD + M], delta2);
+            const double v = singular ? 0.0 : (op ? A[(size_t)j * LD + M] : __ddiv_rn(A[(size_t)j * LD + M], delta2));
             if (!isfinite(v)) bad = 1;
             A[(size_t)j * LD + M] = v;
         }
@@ -672,7 +680,7 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
         const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
         weights_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m, g.s,
                                                        g.M, g.LD, g.coords_in_zero_block, g.smem_doubles, w,
-                                                       node_status);
+                                                       node_status, reinterpret_cast<const double2*>(xy), (int)N, 0);
     } else {
         NsGeom g = ns_geom(n, m);
         size_t smem = 0;
@@ -689,6 +697,36 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
         weights_ns_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m,
                                                           g.s, g.LDF, g.LDS, g.bytes, w, node_status);
     }
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+// Interpolation weights (used by the multigrid transfer operators): for each
+// of the Nq points q, the weights w (Nq x n) with sum_j w_j u(x_{idx_j})
+// exact for polynomials of degree <= m, from the PHS r^3 + monomial system
+// centred at q (the kernel above with op 1).  node_status: 1 where the
+// system is singular (weights then 0).
+int rbffd::interp_weights(const double* xy, int64_t Nd, const double* qxy, int64_t Nq, const int32_t* idx,
+                          int32_t n, int32_t m, double* w, int32_t* node_status, cudaStream_t st) {
+    if (!xy || !qxy || !idx || !w || Nq <= 0 || Nq > 0x7fffffffLL || Nd <= 0 || Nd > 0x7fffffffLL || n < 1 ||
+        n > RBFFD_MAX_STENCIL || m < 0 || m > 8)
+        return RBFFD_ERR_INVALID_ARG;
+    const int s = (m + 1) * (m + 2) / 2;
+    if (n < s) return RBFFD_ERR_INVALID_ARG;
+    WeightsGeom g = weights_geom(n, m);
+    size_t smem = 0;
+    const int wpb = weights_warps_per_block(g, &smem);
+    if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;
+    RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_kernel, 32 * wpb, smem));
+    if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
+    const int64_t need = (Nq + wpb - 1) / wpb;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
+    weights_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)Nq, n, m, g.s,
+                                                   g.M, g.LD, g.coords_in_zero_block, g.smem_doubles, w, node_status,
+                                                   reinterpret_cast<const double2*>(qxy), (int)Nd, 1);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

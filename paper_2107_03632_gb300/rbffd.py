@@ -52,6 +52,15 @@ class Csr(ctypes.Structure):
     ]
 
 
+class MgHandle(ctypes.Structure):
+    """rbffd_mg: host object filled by rbffd_mg_setup (opaque)."""
+
+    _fields_ = [("opaque", ctypes.c_uint64 * 2048)]
+
+
+MG_MAX_LEVELS = 24
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_double),
@@ -60,6 +69,8 @@ class SolveOpts(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
         ("jacobi", ctypes.c_int32),
+        ("precond", ctypes.c_int32),
+        ("mg", ctypes.POINTER(MgHandle)),
     ]
 
 
@@ -85,6 +96,9 @@ class Profile(ctypes.Structure):
         ("spmv32_launches", ctypes.c_int64),
         ("spmv32_ms", ctypes.c_double),
         ("spmv32_bytes", ctypes.c_int64),
+        ("mg_launches", ctypes.c_int64),
+        ("mg_ms", ctypes.c_double),
+        ("mg_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -124,6 +138,10 @@ SIGNATURES = {
     "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32]),
     "rbffd_solve_batched": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _VP, _VP, _VP, _VP, _I32, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_mg_workspace_size": (_SZ, [_I64, _I64]),
+    "rbffd_mg_setup": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(Csr), ctypes.POINTER(Csr), _I32, _D,
+                                      ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
+    "rbffd_mg_levels": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(ctypes.c_int64)]),
     "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
 }
@@ -322,13 +340,68 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
 
 
 # -------------------------------------------------------------------- solve --
-def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_outer=1000, jacobi=True):
+def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_outer=1000, jacobi=True,
+              mg: "Multigrid | None" = None):
     """Solver options.  inner_tol: residual reduction per restarted pass
-    (default 1e-3 for FP64, 1e-5 for mixed)."""
+    (default 1e-3 for FP64, 1e-5 for mixed; 1e-10 with multigrid, i.e. one
+    pass).  mg: a Multigrid hierarchy -> BiCGSTAB right-preconditioned by its
+    V-cycle (float32 V-cycle when precision is "mixed")."""
     prec = {"fp64": 0, "mixed": 1}[precision]
     if inner_tol is None:
-        inner_tol = 1e-5 if prec == 1 else 1e-3
-    return SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0)
+        inner_tol = 1e-10 if mg is not None else (1e-5 if prec == 1 else 1e-3)
+    o = SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0, 0, None)
+    if mg is not None:
+        o.precond = 1
+        o.mg = ctypes.pointer(mg.handle)
+        o._mg_ref = mg  # keeps the hierarchy (and its device workspace) alive
+    return o
+
+
+class Multigrid:
+    """Geometric multigrid hierarchy for the operator A of a node set (rbffd_mg_setup).
+
+    Holds the host handle and the device workspace it points into."""
+
+    def __init__(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2,
+                 omega: float = 0.5, ws: torch.Tensor | None = None):
+        N = xy.shape[0]
+        _require(xy, torch.float64, "xy", (N, 2))
+        _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+        lib = load()
+        self.handle = MgHandle()
+        if ws is None:
+            ws = mg_workspace(N, A.nnz, xy.device)
+        self.ws = ws
+        self.A = A
+        c64 = A.c64()
+        c32 = A.c32()
+        _check(lib.rbffd_mg_setup(_ptr(xy), _ptr(is_dirichlet), N, ctypes.byref(c64),
+                                  ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
+                                  ctypes.byref(self.handle), _ptr(ws), ws.numel(), _stream(xy.device)),
+               "rbffd_mg_setup")
+
+    def setup(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2, omega: float = 0.5):
+        """Rebuilds the hierarchy in the same workspace (same node count)."""
+        lib = load()
+        c64 = A.c64()
+        c32 = A.c32()
+        self.A = A
+        _check(lib.rbffd_mg_setup(_ptr(xy), _ptr(is_dirichlet), xy.shape[0], ctypes.byref(c64),
+                                  ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
+                                  ctypes.byref(self.handle), _ptr(self.ws), self.ws.numel(), _stream(xy.device)),
+               "rbffd_mg_setup")
+
+    def levels(self) -> list:
+        arr = (ctypes.c_int64 * MG_MAX_LEVELS)()
+        n = load().rbffd_mg_levels(ctypes.byref(self.handle), arr)
+        return [int(arr[i]) for i in range(n)]
+
+
+def mg_workspace(N: int, nnz: int, device) -> torch.Tensor:
+    nbytes = load().rbffd_mg_workspace_size(N, nnz)
+    if nbytes == 0:
+        raise RbffdError(1, "rbffd_mg_workspace_size")
+    return _workspace(nbytes, device)
 
 
 def stencils_workspace(N: int, n: int, device) -> torch.Tensor:
@@ -352,7 +425,7 @@ def rbffd_solve(A: CsrMatrix, b: torch.Tensor, x: torch.Tensor | None = None, op
     if x is None:
         x = torch.zeros_like(b)
     _require(x, torch.float64, "x", (A.n_rows,))
-    if opts.precision == 1 and A.val32 is None:
+    if opts.precision == 1 and opts.precond == 0 and A.val32 is None:
         raise ValueError("mixed precision needs the float32 matrix copy (assemble with want_f32=True)")
     if ws is None:
         ws = solve_workspace(A.n_rows, opts, b.device)

@@ -121,3 +121,42 @@ def test_solve_argument_errors(cdll):
     A_wrong_dtype = rbffd.Csr(10, 30, 0x1000, 0x2000, 0x3000, 1)
     assert cdll.rbffd_solve(ctypes.byref(A_wrong_dtype), None, 0x4000, 0x5000, ctypes.byref(ok),
                             ctypes.byref(info), 0x6000, 1 << 30, None) == 1
+
+
+def test_multigrid_argument_errors(cdll):
+    """Multigrid entry points reject bad arguments before touching the device."""
+    from paper_2107_03632_gb300 import rbffd
+
+    INVALID, WS = 1, 7
+    A = rbffd.Csr(1000, 12000, 0x1000, 0x2000, 0x3000, 0)
+    A32_wrong_pattern = rbffd.Csr(1000, 12000, 0x1100, 0x2000, 0x4000, 1)
+    h = rbffd.MgHandle()
+    ws = cdll.rbffd_mg_workspace_size(1000, 12000)
+    assert ws > 0 and cdll.rbffd_mg_workspace_size(0, 0) == 0
+    args = dict(nu=2, omega=0.5)
+    setup = lambda xy, N, a, a32, nu, om, w, nb: cdll.rbffd_mg_setup(  # noqa: E731
+        xy, 0x5000, N, ctypes.byref(a) if a else None, ctypes.byref(a32) if a32 else None, nu, om,
+        ctypes.byref(h), w, nb, None)
+    assert setup(0x7000, 1000, A, None, 2, 0.5, 0x8000, ws - 1) == WS  # workspace too small
+    assert setup(0x7000, 1000, A, None, 2, 0.5, 0x8001, ws) == WS  # misaligned workspace
+    assert setup(0x7008, 1000, A, None, 2, 0.5, 0x8000, ws) == INVALID  # xy not 16-B aligned
+    assert setup(0x7000, 999, A, None, 2, 0.5, 0x8000, ws) == INVALID  # N != rows of A
+    assert setup(0x7000, 1000, None, None, 2, 0.5, 0x8000, ws) == INVALID
+    assert setup(0x7000, 1000, A, A32_wrong_pattern, 2, 0.5, 0x8000, ws) == INVALID
+    assert setup(0x7000, 1000, A, None, 0, 0.5, 0x8000, ws) == INVALID  # nu
+    assert setup(0x7000, 1000, A, None, 2, 1.0, 0x8000, ws) == INVALID  # omega
+    assert cdll.rbffd_mg_levels(ctypes.byref(h), None) == 0  # nothing built
+    # a solve asking for multigrid with a handle that was never built
+    opts = rbffd.make_opts()
+    opts.precond = 1
+    opts.mg = ctypes.pointer(h)
+    info = rbffd.SolveInfo()
+    assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(opts), ctypes.byref(info),
+                            0x6000, 1 << 30, None) == INVALID
+    opts.precond = 2
+    assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(opts), ctypes.byref(info),
+                            0x6000, 1 << 30, None) == INVALID
+    # the adjoint solve takes no hierarchy
+    opts.precond = 1
+    assert cdll.rbffd_solve_adjoint(ctypes.byref(A), None, 0x7000, 0x4000, 0x5000, None, None,
+                                    ctypes.byref(opts), ctypes.byref(info), 0x6000, 1 << 30, None) == INVALID
