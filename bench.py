@@ -47,6 +47,9 @@ WORKLOADS = {
     "disk_4M_m6_n56": (8.862e-4, 6, 56),
     "disk_1M_m4_n30": (1.7725e-3, 4, 30),
     "disk_h0.04_m2_n12": (0.04, 2, 12),
+    # profiling case: the 1M-node set at the highest degree (m = 6 weights and
+    # solve at a quarter of the headline size, for ncu captures)
+    "disk_1M_m6_n56": (1.7725e-3, 6, 56),
 }
 METRIC = "solved nodes/s (weights+solve) at m=6, 4M nodes; mixed vs FP64; % roofline"
 # The batched workload (a separate measurement, not the headline line): 256
@@ -54,6 +57,13 @@ METRIC = "solved nodes/s (weights+solve) at m=6, 4M nodes; mixed vs FP64; % roof
 # 64 random Fourier right-hand sides each, g = 0, mixed solve to 1e-10.
 BATCH_WORKLOAD = "disk_batch256_rhs64"
 BATCH_METRIC = "solved node-rhs/s, 256 disks (N log-uniform 1e4..2e5, m in {2,4,6}) x 64 rhs, mixed, tol 1e-10"
+# The paper's own GPU workload (Sec. IV Eq. 4, Sec. V): the explicit Euler
+# loop, dt = 1e-6; measured on the 1M-node disk (m = 4, n = 30) and swept over
+# N and n for the L2 data-size model of Table 1.
+EXPLICIT_WORKLOAD = "explicit_1M_m4_n30"
+EXPLICIT_METRIC = "explicit Euler node-steps/s (Eq. 4), 1M-node disk, m=4, n=30, dt=1e-6"
+EXPLICIT_SWEEP_N = (1e4, 3e4, 1e5, 3e5, 1e6, 3e6)
+EXPLICIT_SWEEP_n = (12, 15, 20, 30, 45, 60)
 BATCH_RHS = 64
 BATCH_SAMPLE_RHS = 8  # oracle sample: right-hand sides of the smallest instance per step
 SEED = 2107
@@ -278,6 +288,8 @@ def run_reference(args):
         return 0
     if args.workload == BATCH_WORKLOAD:
         return run_reference_batched(args)
+    if args.workload == EXPLICIT_WORKLOAD:
+        return run_reference_explicit(args)
     h, m, n = WORKLOADS[args.workload]
     res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=args.warmup + args.steps)
     timed = res[args.warmup:]
@@ -293,6 +305,52 @@ def run_reference(args):
         "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "sample_nodes": nodes, "m": m, "n": n},
         "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_explicit_sample(h: float, m: int, n: int, steps: int):
+    """The oracle's explicit step (Eq. 4) repeated on the sample disk; returns
+    (node-steps, seconds of the steps alone)."""
+    import oracle
+    from fixtures import disk_nodes, manufactured
+
+    d = disk_nodes(h, SEED)
+    u, f, g = manufactured(d.xy)
+    idx = oracle.knn(d.xy, n)
+    w, _ = oracle.weights(d.xy, idx, m)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = oracle.explicit_step(idx, w, d.is_dirichlet, f, u, 1e-6)
+    return d.N * steps, time.perf_counter() - t0
+
+
+def run_reference_explicit(args):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    k_steps = 100
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = [bench.oracle_explicit_sample(%r, 4, 30, %d) for _ in range(%d)]; print(json.dumps(r))"
+            % (ROOT, CPU_SAMPLE_H, k_steps, args.warmup + args.steps))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])[args.warmup:]
+    units = sum(u for u, _ in res)
+    secs = sum(t for _, t in res)
+    value = units / secs
+    sample = (f"oracle explicit step (numpy gather + einsum) on the same disk recipe at h={CPU_SAMPLE_H}, m=4, "
+              f"n=30, {k_steps} steps per sample, one core")
+    line = {
+        "impl": "reference", "metric": EXPLICIT_METRIC, "value": value, "unit": "node-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(res),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "m": 4, "n": 30, "dt": 1e-6},
+        "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -374,6 +432,14 @@ def run_gpu_batched(args):
     h_F = torch.empty((N, R), dtype=torch.float64).pin_memory()
     h_F.copy_(F)
     h_U = torch.empty((N, R), dtype=torch.float64).pin_memory()
+    # one-time tuning of the weight solve per (n, m), on the first instance of each
+    wcfg = {}
+    off = 0
+    for d, (s, h, m, n) in zip(nodes, specs):
+        if (n, m) not in wcfg:
+            xi = xy[off:off + d.N]
+            wcfg[(n, m)] = rbffd.rbffd_weights_autotune(xi, rbffd.rbffd_stencils(xi, n), m)
+        off += d.N
     wsb = rbffd.batched_workspace(sizes, R, dev)
     opts = rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol)
 
@@ -431,6 +497,7 @@ def run_gpu_batched(args):
         "config": {"workload": BATCH_WORKLOAD, "instances": len(sizes), "N_total": N, "rhs": R,
                    "m_counts": {m: sum(1 for x in sizes if x[1] == m) for m in (2, 4, 6)},
                    "tol": 1e-10, "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
+                   "weights_config": {f"n{k[0]}_m{k[1]}": v for k, v in wcfg.items()},
                    "l2": "inputs larger than L2 (vectors ~%.0f GB)" % (N * R * 8 * 8 / 1e9)},
         "solve": {"iters_max": max(i["iters"] for i in infos), "iters_mean": float(np.mean([i["iters"] for i in infos])),
                   "rounds_max": max(i["outer_sweeps"] for i in infos),
@@ -440,6 +507,117 @@ def run_gpu_batched(args):
                  "steps": args.e2e_steps} if e2e_value is not None else None),
         "gpu_launches": prof["launches"],
         "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------ explicit workload ----
+def explicit_bytes_per_step(N: int, Ni: int, n: int) -> int:
+    """Algorithmic bytes of one step: the packed interior rows (n weights +
+    n indices + the row id), f, u read and u written per interior row, u read
+    once per node for the gathers."""
+    return Ni * (n * 12 + 4 + 8 + 8 + 8) + N * 8
+
+
+def run_gpu_explicit(args):
+    import torch
+
+    from fixtures import disk_nodes, h_for_nodes, manufactured
+    from paper_2107_03632_gb300 import rbffd
+
+    ws_, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws_ > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rbffd.load()
+    dt = 1e-6
+
+    def prepare(h, m, n):
+        d = disk_nodes(h, SEED)
+        u, f, g = manufactured(d.xy)
+        xy, mask = torch.from_numpy(d.xy).to(dev), torch.from_numpy(d.is_dirichlet).to(dev)
+        idx = rbffd.rbffd_stencils(xy, n)
+        w, _ = rbffd.rbffd_weights(xy, idx, m)
+        loop = rbffd.ExplicitLoop(idx, w, mask)
+        return d, loop, torch.from_numpy(f).to(dev), torch.from_numpy(u).to(dev)
+
+    def time_steps(loop, fT, uT, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        loop.run(fT, uT, dt, steps)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    h, m, n = 1.7725e-3, 4, 30
+    d, loop, fT, uT = prepare(h, m, n)
+    steps = 1024 * max(args.steps, 1)
+    for _ in range(args.warmup):
+        loop.run(fT, uT, dt, 256)
+    clocks = ClockSampler(local)
+    clocks.start()
+    rbffd.rbffd_profile_read(reset=True)
+    ms = time_steps(loop, fT, uT, steps)
+    clk = clocks.stop()
+    prof = rbffd.rbffd_profile_read(reset=True)
+    value, ms = replica_value(dist, ws_, d.N, steps, ms, dev)
+    by = explicit_bytes_per_step(d.N, loop.n_interior, n)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    gbs = by / (ms / steps * 1e-3) / 1e9
+    # e2e: the same loop through the API from pinned host buffers
+    h_u = torch.from_numpy(manufactured(d.xy)[0]).pin_memory()
+    h_out = torch.empty_like(h_u).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    uT.copy_(h_u, non_blocking=True)
+    loop.run(fT, uT, dt, steps)
+    h_out.copy_(uT, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    e2e_value, _ = replica_value(dist, ws_, d.N, steps, e0.elapsed_time(e1), dev)
+
+    sweep = []
+    if not args.no_sweep:
+        for nn in EXPLICIT_SWEEP_n:
+            for Nt in EXPLICIT_SWEEP_N:
+                ds, lp, fs, us = prepare(h_for_nodes(Nt), 2, nn)
+                lp.run(fs, us, dt, 128)
+                k = 512
+                t = time_steps(lp, fs, us, k)
+                b = explicit_bytes_per_step(ds.N, lp.n_interior, nn)
+                sweep.append({"n": nn, "N": ds.N, "ns_per_node_step": t * 1e6 / (k * ds.N),
+                              "gbs": b / (t / k * 1e-3) / 1e9,
+                              "table1_bytes": 8 * ds.N * (4 + nn) + 4 * (lp.n_interior + ds.N * nn)})
+                del ds, lp, fs, us
+    line = {
+        "metric": EXPLICIT_METRIC, "value": value, "unit": "node-steps/s", "n_gpus": ws_, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": EXPLICIT_WORKLOAD, "N": d.N, "N_interior": loop.n_interior, "m": m, "n": n,
+                   "dt": dt, "parallelism": f"replicas x{ws_}",
+                   "l2": "inputs larger than L2 (%.0f MB per step)" % (by / 1e6)},
+        "roofline": {"kernel": "explicit_step_kernel (packed ELL, one thread per interior row)", "bound": "hbm",
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_launch": by, "ms_per_launch": ms / steps, "launches": steps},
+        "e2e": {"value": e2e_value, "unit": "node-steps/s", "h2d_bytes_per_step": d.N * 8 / steps,
+                "d2h_bytes_per_step": d.N * 8 / steps, "steps": steps},
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+        "sweep": sweep,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -497,6 +675,9 @@ def run_gpu(args):
     A = rbffd.CsrMatrix(row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
                         torch.empty(nnz, dtype=torch.float64, device=dev),
                         torch.empty(nnz, dtype=torch.float32, device=dev))
+    # one-time tuning of the weight solve's launch configuration for (n, m)
+    rbffd.rbffd_stencils(xy, n, idx, ws_knn)
+    wcfg = rbffd.rbffd_weights_autotune(xy, idx, m)
     use_mg = args.precond == "mg"
     mg = None
     if use_mg:
@@ -537,8 +718,8 @@ def run_gpu(args):
         x.zero_()
         _, info = rbffd.rbffd_solve(A, b, x, opts[precision], ws_solve if precision == "mixed" else ws_solve64,
                                     raise_on_error=False)
-        if info["status_code"] not in (0, 4):
-            raise rbffd.RbffdError(info["status_code"], "rbffd_solve")
+        if info["status_code"] != 0:  # a step that did not reach the tolerance measures nothing
+            raise rbffd.RbffdError(info["status_code"], "rbffd_solve", f"{info}")
         if ev:
             ev[5].record()
         return info
@@ -687,7 +868,7 @@ def run_gpu(args):
                    "precond": (f"multigrid V({args.mg_nu},{args.mg_nu}) omega {args.mg_omega}, levels "
                                f"{mg.levels()}" if use_mg else "jacobi"),
                    "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol,
-                   "parallelism": f"replicas x{ws}",
+                   "parallelism": f"replicas x{ws}", "weights_config": wcfg,
                    "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
         "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "mg_setup": st_ms[3],
                       "solve": st_ms[4]},
@@ -721,13 +902,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk_4M_m6_n56", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--workload", default="disk_4M_m6_n56",
+                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, EXPLICIT_WORKLOAD])
+    ap.add_argument("--no-sweep", action="store_true", help="explicit workload: skip the N x n sweep")
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
     ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
     ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
                     help="mg: BiCGSTAB right-preconditioned by the multigrid V-cycle; jacobi: the plain solvers")
     ap.add_argument("--mg-nu", type=int, default=2, help="Jacobi sweeps before and after the coarse correction")
-    ap.add_argument("--mg-omega", type=float, default=0.5, help="Jacobi damping of the V-cycle")
+    ap.add_argument("--mg-omega", type=float, default=0.6, help="Jacobi damping of the V-cycle")
     ap.add_argument("--mg-pass-tol", type=float, default=1e-10,
                     help="multigrid: residual drop per restarted BiCGSTAB pass (1e-10: a single pass)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
@@ -741,6 +924,8 @@ def main():
         return run_reference(args)
     if args.workload == BATCH_WORKLOAD:
         return run_gpu_batched(args)
+    if args.workload == EXPLICIT_WORKLOAD:
+        return run_gpu_explicit(args)
     return run_gpu(args)
 
 

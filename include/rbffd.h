@@ -115,8 +115,11 @@ int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx,
 /*      [ Phi  P ] [ w ]   [ lap phi_j(x_i) ]      Phi_jk = |x_j - x_k|^3    */
 /*      [ P^T  0 ] [ l ] = [ lap p_k(x_i)   ]      P_jk   = p_k(x_j)         */
 /* is formed in coordinates shifted to x_i and scaled by delta_i (the        */
-/* largest |x_j - x_i| in the stencil), solved in FP64 by Gaussian           */
-/* elimination with partial pivoting, and w[i*n + j] = wh_j / delta_i^2.     */
+/* largest |x_j - x_i| in the stencil), solved in FP64, and                  */
+/* w[i*n + j] = wh_j / delta_i^2.  Two solvers, one warp per stencil with    */
+/* the system in shared memory: null-space elimination (Gauss-Jordan with   */
+/* row pivoting on P, Cholesky of Z^T Phi Z; the default for m >= 1) and     */
+/* Gaussian elimination with partial pivoting of the whole system (m = 0).   */
 /* Monomials are in graded order 1, x, y, x^2, xy, y^2, ...; s = (m+1)(m+2)/2.*/
 /*   m           : 0 <= m <= 8 and s <= n (the system needs n >= s nodes).   */
 /*   w           : N x n float64, written (rows of singular stencils: 0).    */
@@ -125,6 +128,28 @@ int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx,
 /* ------------------------------------------------------------------------ */
 int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
                   double* w, int32_t* node_status, void* stream);
+
+/* Weight-solve launch configuration ("tile shape") per (n, m): the solver   */
+/* (0 null-space elimination, 1 full Gaussian elimination) and the stencils */
+/* (warps) per block, 1..4.  rbffd_weights_autotune times every candidate   */
+/* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */
+/* the given set (3 launches each after one warm-up, CUDA events), records  */
+/* the fastest for (current device, n, m) in a process-wide table that      */
+/* rbffd_weights and rbffd_solve_batched then use, and returns it in *best   */
+/* (may be NULL).  w and node_status serve as its scratch (their first rows */
+/* are overwritten).  Synchronises `stream`.  (Autotuning has no            */
+/* counterpart in the paper.)  rbffd_weights_get_config returns the          */
+/* configuration in force; rbffd_weights_set_config pins one (NULL: back to  */
+/* the default, which follows the shared-memory footprint).                  */
+typedef struct rbffd_weights_config {
+    int32_t kernel;          /* 0 = null-space elimination, 1 = Gaussian elimination */
+    int32_t warps_per_block; /* stencils per block, one warp each */
+    double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
+} rbffd_weights_config;
+int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
+                           double* w, int32_t* node_status, rbffd_weights_config* best, void* stream);
+int rbffd_weights_get_config(int32_t n, int32_t m, rbffd_weights_config* cfg);
+int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weights_config* cfg);
 
 /* ------------------------------------------------------------------------ */
 /* Assembly -- Sec. IV, Eqs. 2-4 at steady state: interior rows carry the    */
@@ -170,6 +195,27 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
                     void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Explicit time loop -- Sec. IV, Eq. 4, the paper's GPU workload: forward  */
+/* Euler for u_t = lap u + f,                                               */
+/*   u_2[i] = u_1[i] + dt (f[i] + sum_j w[i,j] u_1[idx[i,j]])   (interior), */
+/* Dirichlet nodes unchanged.                                                */
+/* rbffd_explicit_pack copies the interior rows of (idx, w) (N x n, as from  */
+/* rbffd_stencils / rbffd_weights) into the workspace as column-major ELL    */
+/* arrays with the interior list (Sec. V's data model), returns the         */
+/* interior count in *n_interior (host) and synchronises `stream`;          */
+/* RBFFD_ERR_INVALID_ARG if a stencil index of an interior row is outside   */
+/* [0, N).  rbffd_explicit_run then advances u (device, N float64, in/out)   */
+/* by `steps` steps of size dt on the stream (asynchronous; the steps run as */
+/* replays of a CUDA graph of 64 launches).  f: N float64 (device).          */
+/*   ws : rbffd_explicit_workspace_size(N, n) bytes, the same for both calls.*/
+/* ------------------------------------------------------------------------ */
+size_t rbffd_explicit_workspace_size(int64_t N, int32_t n);
+int rbffd_explicit_pack(const int32_t* idx, const double* w, const uint8_t* is_dirichlet, int64_t N,
+                        int32_t n, int64_t* n_interior, void* ws, size_t ws_bytes, void* stream);
+int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t n_interior, double dt,
+                       int64_t steps, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Multigrid preconditioner (an addition of this library: the paper has no  */
 /* implicit solver, Sec. VI names one as the next step).  A geometric       */
 /* V-cycle on the node sets themselves, built from the pieces of this      */
@@ -194,7 +240,7 @@ int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, doub
 /*              into ws, which must stay allocated and unchanged meanwhile.  */
 /*   A, A32   : the fine-level operator (as passed to rbffd_solve; A32 may   */
 /*              be NULL, then only the FP64 V-cycle is available).           */
-/*   nu       : 1..8 sweeps; omega: 0 < omega < 1 (e.g. nu 2, omega 0.5).   */
+/*   nu       : 1..8 sweeps; omega: 0 < omega < 1 (e.g. nu 2, omega 0.6).   */
 /*   ws       : rbffd_mg_workspace_size(N, A->nnz) bytes (a bound).          */
 /* Synchronises `stream` (level sizes are read back).  Errors: invalid       */
 /* arguments, RBFFD_ERR_SINGULAR_STENCIL if a coarse stencil or the coarsest */
@@ -340,6 +386,13 @@ typedef struct rbffd_profile {
     double mg_ms;
     int64_t mg_bytes;
 } rbffd_profile;
+
+/* Diagnostics (no counterpart in the paper): evaluates on the device, for   */
+/* each of the n float64 values x (device), the library's own FP64           */
+/* reciprocal and reciprocal square root -- Newton-Raphson refinement of a   */
+/* float32 seed, used inside the weight solves -- into rcp and rsqrt        */
+/* (device, n float64 each; either may be NULL).  Asynchronous on stream.    */
+int rbffd_diag_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream);
 
 int rbffd_profile_enable(int on);
 int rbffd_profile_read(rbffd_profile* out, int reset);

@@ -1,6 +1,7 @@
 // Status strings, error bookkeeping and device queries of the C ABI.
 #include "common.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -171,3 +172,29 @@ const char* rbffd_last_cuda_error(void) { return rbffd::g_last_error; }
 int rbffd_version(void) { return 100; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Diagnostics: the library's FP64 reciprocal and reciprocal square root
+// (Newton-Raphson on float seeds, used inside the weight solves), evaluated
+// elementwise so that tests can hold them against IEEE results.
+namespace rbffd {
+namespace {
+__global__ void diag_recip_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ rcp,
+                                  double* __restrict__ rsq) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (rcp) rcp[i] = rcp64(x[i]);
+        if (rsq) rsq[i] = rsqrt64(x[i]);
+    }
+}
+}  // namespace
+}  // namespace rbffd
+
+extern "C" int rbffd_diag_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {
+    using namespace rbffd;
+    if (!x || n <= 0 || (!rcp && !rsqrt)) return RBFFD_ERR_INVALID_ARG;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    diag_recip_kernel<<<blocks, 256, 0, as_stream(stream)>>>(x, n, rcp, rsqrt);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}

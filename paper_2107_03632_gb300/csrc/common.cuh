@@ -88,6 +88,34 @@ __device__ __forceinline__ float shadow_value(unsigned long long seed, long long
     return (float)(z >> 40) * 0x1p-23f - 1.0f;
 }
 
+// FP64 reciprocal and reciprocal square root by Newton-Raphson refinement of
+// a float32 seed (Newton's method on f(y) = 1/y - a and f(y) = 1/y^2 - a:
+// y <- y + y (1 - a y) and y <- y + y (1/2 - (a/2) y^2), each step doubling
+// the correct bits: ~22 -> ~44 -> full double precision, within about one
+// ulp of the correctly rounded result).  Two FMAs per step against the much
+// longer correctly rounded division and square root; the weight solves call
+// them on scalars that every lane of a warp computes.  Outside the float32
+// normal range the seeds are meaningless, so there the IEEE operations run.
+__device__ __forceinline__ double rcp64(double a) {
+    const double m = fabs(a);
+    if (!(m > 1e-30 && m < 1e30)) return __ddiv_rn(1.0, a);
+    double y = (double)__frcp_rn((float)a);
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt64(double a) {
+    if (!(a > 1e-30 && a < 1e30)) return __ddiv_rn(1.0, __dsqrt_rn(a));
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    double e = fma(-h * y, y, 0.5);
+    y = fma(y, e, y);
+    e = fma(-h * y, y, 0.5);
+    return fma(y, e, y);
+}
+
 // Block-wide sum; every thread gets the result.  `sh` needs 32 doubles.
 template <int BLOCK>
 __device__ __forceinline__ double block_sum(double v, double* sh) {

@@ -28,8 +28,13 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 namespace rbffd {
 namespace {
@@ -210,9 +215,12 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                 }
             }
             __syncwarp();
-            const double inv = __ddiv_rn(1.0, A[(size_t)k * LD + k]);
+            // the pivot's reciprocal replaces the pivot (only the back
+            // substitution reads it again, and multiplies by it)
+            const double inv = rcp64(A[(size_t)k * LD + k]);
             for (int i = k + 1 + lane; i < M; i += 32) A[(size_t)i * LD + k] = __dmul_rn(A[(size_t)i * LD + k], inv);
             __syncwarp();
+            if (lane == 0) A[(size_t)k * LD + k] = inv;
             // trailing update, flattened over rows i in (k, M), cols j in (k, M]
             const int R = M - k - 1, C = M - k;
             if (R > 0) {
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         // ---- back substitution on U x = b' (b' in column M) -----------------
         if (!singular) {
             for (int j = M - 1; j >= 0; --j) {
-                const double xj = __ddiv_rn(A[(size_t)j * LD + M], A[(size_t)j * LD + j]);
+                const double xj = __dmul_rn(A[(size_t)j * LD + M], A[(size_t)j * LD + j]);
                 __syncwarp();
                 for (int i = lane; i < j; i += 32) A[(size_t)i * LD + M] = fma(-A[(size_t)i * LD + j], xj, A[(size_t)i * LD + M]);
                 if (lane == 0) A[(size_t)j * LD + M] = xj;
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 break;
             }
             const int pr = bi;
-            const double inv = __ddiv_rn(1.0, P[(size_t)pr * LDS + k]);
+            const double inv = rcp64(P[(size_t)pr * LDS + k]);
             __syncwarp();
             if (lane == 0) {
                 perm[k] = pr;
@@ -488,8 +496,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 const double dx = __dadd_rn(crd[2 * ja], -crd[2 * jb]);
                 const double dy = __dadd_rn(crd[2 * ja + 1], -crd[2 * jb + 1]);
                 coincident |= (dx == 0.0 && dy == 0.0) ? 1 : 0;
-                const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-                const double phi = __dmul_rn(__dmul_rn(r, r), r);
+                // r^3 = r^2 * (r^2 / r), r^2 / r = r^2 * rsqrt(r^2)
+                const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                const double phi = (r2 > 0.0) ? __dmul_rn(r2, __dmul_rn(r2, rsqrt64(r2))) : 0.0;
                 Phi[(size_t)a * LDF + b] = phi;
                 Phi[(size_t)b * LDF + a] = phi;
             }
@@ -511,16 +520,28 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 const int a = e / q, j = e - (e / q) * q;
                 const double* xr = P + (size_t)perm[s + j] * LDS;
                 const double* pr = Phi + (size_t)a * LDF;
-                double acc = pr[s + j];
-                for (int k = 0; k < s; ++k) acc = fma(-pr[k], xr[k], acc);
-                Phi[(size_t)a * LDF + s + j] = acc;
+                // two independent FMA chains (few warps per SM: latency, not
+                // issue, limits a single chain)
+                double acc = pr[s + j], acc1 = 0.0;
+                int k = 0;
+                for (; k + 1 < s; k += 2) {
+                    acc = fma(-pr[k], xr[k], acc);
+                    acc1 = fma(-pr[k + 1], xr[k + 1], acc1);
+                }
+                if (k < s) acc = fma(-pr[k], xr[k], acc);
+                Phi[(size_t)a * LDF + s + j] = acc + acc1;
             }
             // ---- u = f - Phi[:, 0..s) w0 ----------------------------------------
             for (int a = lane; a < n; a += 32) {
                 const double* pr = Phi + (size_t)a * LDF;
-                double acc = fv[a];
-                for (int k = 0; k < s; ++k) acc = fma(-pr[k], w0[k], acc);
-                uv[a] = acc;
+                double acc = fv[a], acc1 = 0.0;
+                int k = 0;
+                for (; k + 1 < s; k += 2) {
+                    acc = fma(-pr[k], w0[k], acc);
+                    acc1 = fma(-pr[k + 1], w0[k + 1], acc1);
+                }
+                if (k < s) acc = fma(-pr[k], w0[k], acc);
+                uv[a] = acc + acc1;
             }
             __syncwarp();
             // ---- S = Phi22 - Phi21 X^T - X T (lower triangle, in place) -----
@@ -533,19 +554,24 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 const double* xj = P + (size_t)perm[s + j] * LDS;
                 const double* xl = P + (size_t)perm[s + l] * LDS;
                 const double* prj = Phi + (size_t)(s + j) * LDF;
-                double acc = prj[s + l];
+                double acc = prj[s + l], acc1 = 0.0;
                 for (int k = 0; k < s; ++k) {
                     acc = fma(-prj[k], xl[k], acc);
-                    acc = fma(-xj[k], Phi[(size_t)k * LDF + s + l], acc);
+                    acc1 = fma(-xj[k], Phi[(size_t)k * LDF + s + l], acc1);
                 }
-                Phi[(size_t)(s + j) * LDF + s + l] = acc;
+                Phi[(size_t)(s + j) * LDF + s + l] = acc + acc1;
             }
             // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
             for (int j = lane; j < q; j += 32) {
                 const double* xj = P + (size_t)perm[s + j] * LDS;
-                double acc = uv[s + j];
-                for (int k = 0; k < s; ++k) acc = fma(-xj[k], uv[k], acc);
-                tv[j] = acc;
+                double acc = uv[s + j], acc1 = 0.0;
+                int k = 0;
+                for (; k + 1 < s; k += 2) {
+                    acc = fma(-xj[k], uv[k], acc);
+                    acc1 = fma(-xj[k + 1], uv[k + 1], acc1);
+                }
+                if (k < s) acc = fma(-xj[k], uv[k], acc);
+                tv[j] = acc + acc1;
             }
             __syncwarp();
             // ---- Cholesky S = L L^T (lower, in place) ----------------------------
@@ -556,14 +582,19 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     singular = 1;
                     break;
                 }
-                const double lcc = __dsqrt_rn(dcc);
-                const double inv = __ddiv_rn(1.0, lcc);
+                // l = sqrt(d) and 1/l from one reciprocal square root; 1/l is
+                // kept (in fv, free by now) for the substitutions
+                const double inv = rsqrt64(dcc);
+                const double lcc = __dmul_rn(dcc, inv);
                 __syncwarp();
                 for (int i = cI + 1 + lane; i < q; i += 32) {
                     double* si = Phi + (size_t)(s + i) * LDF + s;
                     si[cI] = __dmul_rn(si[cI], inv);
                 }
-                if (lane == 0) sc[cI] = lcc;
+                if (lane == 0) {
+                    sc[cI] = lcc;
+                    fv[cI] = inv;
+                }
                 __syncwarp();
                 // trailing lower triangle: S[i][j] -= L[i][c] L[j][c], c < j <= i
                 const int rem = q - cI - 1, ntr = rem * (rem + 1) / 2;
@@ -582,8 +613,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         if (!singular) {
             // ---- forward (L y = t) and back (L^T z = y) substitution -------------
             for (int cI = 0; cI < q; ++cI) {
-                const double* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const double yc = __ddiv_rn(tv[cI], sc[cI]);
+                const double yc = __dmul_rn(tv[cI], fv[cI]);
                 __syncwarp();
                 for (int i = cI + 1 + lane; i < q; i += 32)
                     tv[i] = fma(-Phi[(size_t)(s + i) * LDF + s + cI], yc, tv[i]);
@@ -592,7 +622,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             }
             for (int cI = q - 1; cI >= 0; --cI) {
                 const double* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const double zc = __ddiv_rn(tv[cI], sc[cI]);
+                const double zc = __dmul_rn(tv[cI], fv[cI]);
                 __syncwarp();
                 for (int i = lane; i < cI; i += 32) tv[i] = fma(-sc[i], zc, tv[i]);
                 if (lane == 0) tv[cI] = zc;
@@ -601,9 +631,14 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
             const double* w0 = P + (size_t)n * LDS;
             for (int k = lane; k < s; k += 32) {
-                double acc = w0[k];
-                for (int j = 0; j < q; ++j) acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
-                wv[k] = acc;
+                double acc = w0[k], acc1 = 0.0;
+                int j = 0;
+                for (; j + 1 < q; j += 2) {
+                    acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
+                    acc1 = fma(-P[(size_t)perm[s + j + 1] * LDS + k], tv[j + 1], acc1);
+                }
+                if (j < q) acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
+                wv[k] = acc + acc1;
             }
             for (int j = lane; j < q; j += 32) wv[s + j] = tv[j];
             __syncwarp();
@@ -651,54 +686,191 @@ int weights_warps_per_block(const WeightsGeom& g, size_t* smem_bytes) {
 }  // namespace
 }  // namespace rbffd
 
-extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m, double* w,
-                             int32_t* node_status, void* stream) {
-    using namespace rbffd;
-    if (!xy || !idx || !w || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8)
-        return RBFFD_ERR_INVALID_ARG;
-    if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
-    const int s = (m + 1) * (m + 2) / 2;
-    if (n < s) return RBFFD_ERR_INVALID_ARG;
-    cudaStream_t st = as_stream(stream);
-    // RBFFD_WEIGHTS=lu selects the full-system Gaussian elimination kernel
-    // (kept for comparison); the default is the null-space elimination.
+namespace rbffd {
+namespace {
+
+// Launch configuration of the weight solve: kernel variant and warps (one
+// stencil each) per block.  The default per (n, m) follows the shared-memory
+// footprint; rbffd_weights_autotune replaces it with the fastest measured
+// candidate, kept in a process-wide table per (device, n, m).
+struct WCfg {
+    int kernel;  // 0 null-space elimination, 1 full Gaussian elimination
+    int wpb;
+};
+
+std::mutex g_wcfg_mu;
+std::map<std::tuple<int, int, int>, std::pair<WCfg, double>> g_wcfg;  // -> (config, ms per 1e6 stencils)
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+size_t smem_per_warp(int kernel, int n, int m) {
+    if (kernel == 1) return (size_t)weights_geom(n, m).smem_doubles * sizeof(double);
+    return (size_t)ns_geom(n, m).bytes;
+}
+
+WCfg default_cfg(int n, int m) {
+    WCfg c;
+    // the null-space form needs r^3 positive definite on the null space of
+    // P^T, which holds once P contains the linear monomials (m >= 1)
+    c.kernel = m < 1 ? 1 : 0;
+    size_t smem = 0;
+    c.wpb = warps_per_block_for(smem_per_warp(c.kernel, n, m), &smem);
+    return c;
+}
+
+WCfg chosen_cfg(int n, int m) {
+    // RBFFD_WEIGHTS=lu forces the full Gaussian elimination (comparisons)
     const char* sel = std::getenv("RBFFD_WEIGHTS");
-    // The null-space form needs r^3 to be positive definite on the null
-    // space of P^T, which holds once P contains the linear monomials (m >= 1).
-    const bool use_lu = (sel && std::strcmp(sel, "lu") == 0) || m < 1;
-    if (use_lu) {
-        WeightsGeom g = weights_geom(n, m);
+    if (sel && std::strcmp(sel, "lu") == 0) {
+        WCfg c = default_cfg(n, m);
         size_t smem = 0;
-        const int wpb = weights_warps_per_block(g, &smem);
-        if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;  // system too large for one SM
+        c.kernel = 1;
+        c.wpb = warps_per_block_for(smem_per_warp(1, n, m), &smem);
+        return c;
+    }
+    std::lock_guard<std::mutex> lk(g_wcfg_mu);
+    auto it = g_wcfg.find(std::make_tuple(current_device(), n, m));
+    if (it != g_wcfg.end()) return it->second.first;
+    return default_cfg(n, m);
+}
+
+int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t N, int n, int m, double* w,
+                   int32_t* node_status, cudaStream_t st) {
+    if (c.kernel == 0 && m < 1) return RBFFD_ERR_INVALID_ARG;
+    if (c.wpb < 1 || c.wpb > 4) return RBFFD_ERR_INVALID_ARG;  // __launch_bounds__(128)
+    const size_t smem = smem_per_warp(c.kernel, n, m) * c.wpb;
+    if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;  // system too large for one SM
+    const int wpb = c.wpb;
+    const int64_t need = (N + wpb - 1) / wpb;
+    int per_sm = 0;
+    if (c.kernel == 1) {
+        WeightsGeom g = weights_geom(n, m);
         RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        int per_sm = 0;
         RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_kernel, 32 * wpb, smem));
         if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
-        const int64_t need = (N + wpb - 1) / wpb;
         const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
         weights_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m, g.s,
                                                        g.M, g.LD, g.coords_in_zero_block, g.smem_doubles, w,
                                                        node_status, reinterpret_cast<const double2*>(xy), (int)N, 0);
     } else {
         NsGeom g = ns_geom(n, m);
-        size_t smem = 0;
-        const int wpb = warps_per_block_for((size_t)g.bytes, &smem);
-        if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;
         RBFFD_CUDA_TRY(
             cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        int per_sm = 0;
         RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_ns_kernel, 32 * wpb, smem));
         if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
-        const int64_t need = (N + wpb - 1) / wpb;
         const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
         weights_ns_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m,
                                                           g.s, g.LDF, g.LDS, g.bytes, w, node_status);
     }
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
+bool weights_args_ok(const double* xy, const int32_t* idx, const double* w, int64_t N, int32_t n, int32_t m) {
+    if (!xy || !idx || !w || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8)
+        return false;
+    if (((uintptr_t)xy & 15) != 0) return false;
+    return n >= (m + 1) * (m + 2) / 2;
+}
+
+}  // namespace
+}  // namespace rbffd
+
+extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m, double* w,
+                             int32_t* node_status, void* stream) {
+    using namespace rbffd;
+    if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
+    return launch_weights(chosen_cfg(n, m), xy, idx, N, n, m, w, node_status, as_stream(stream));
+}
+
+extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
+                                      double* w, int32_t* node_status, rbffd_weights_config* best, void* stream) {
+    using namespace rbffd;
+    if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    // sample: the first stencils, enough for several waves of resident warps
+    const int64_t S = std::min<int64_t>(N, (int64_t)sm_count() * 128);
+    std::vector<WCfg> cands;
+    for (int kernel = (m < 1 ? 1 : 0); kernel <= 1; ++kernel)
+        for (int wpb = 1; wpb <= 4; ++wpb)
+            if (smem_per_warp(kernel, n, m) * wpb <= 227 * 1024) cands.push_back(WCfg{kernel, wpb});
+    if (cands.empty()) return RBFFD_ERR_INVALID_ARG;
+    cudaEvent_t e0, e1;
+    RBFFD_CUDA_TRY(cudaEventCreate(&e0));
+    RBFFD_CUDA_TRY(cudaEventCreate(&e1));
+    WCfg win = cands[0];
+    double win_ms = INFINITY;
+    int rc = RBFFD_OK;
+    for (const WCfg& c : cands) {
+        if ((rc = launch_weights(c, xy, idx, S, n, m, w, node_status, st)) != RBFFD_OK) break;  // warm-up
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = RBFFD_ERR_CUDA; break; }
+        for (int r = 0; r < 3 && rc == RBFFD_OK; ++r) rc = launch_weights(c, xy, idx, S, n, m, w, node_status, st);
+        if (rc != RBFFD_OK) break;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = RBFFD_ERR_CUDA;
+            break;
+        }
+        const double per = ms / 3.0 * 1e6 / (double)S;  // ms per 1e6 stencils
+        if (per < win_ms) {
+            win_ms = per;
+            win = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RBFFD_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_wcfg_mu);
+        g_wcfg[std::make_tuple(current_device(), (int)n, (int)m)] = std::make_pair(win, win_ms);
+    }
+    if (best) {
+        best->kernel = win.kernel;
+        best->warps_per_block = win.wpb;
+        best->ms_per_mnode = win_ms;
+    }
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_weights_get_config(int32_t n, int32_t m, rbffd_weights_config* cfg) {
+    using namespace rbffd;
+    if (!cfg || n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8 || n < (m + 1) * (m + 2) / 2)
+        return RBFFD_ERR_INVALID_ARG;
+    const WCfg c = chosen_cfg(n, m);
+    double ms = 0.0;
+    {
+        std::lock_guard<std::mutex> lk(g_wcfg_mu);
+        auto it = g_wcfg.find(std::make_tuple(current_device(), (int)n, (int)m));
+        if (it != g_wcfg.end() && it->second.first.kernel == c.kernel && it->second.first.wpb == c.wpb)
+            ms = it->second.second;
+    }
+    cfg->kernel = c.kernel;
+    cfg->warps_per_block = c.wpb;
+    cfg->ms_per_mnode = ms;
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weights_config* cfg) {
+    using namespace rbffd;
+    if (n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8 || n < (m + 1) * (m + 2) / 2) return RBFFD_ERR_INVALID_ARG;
+    const auto key = std::make_tuple(current_device(), (int)n, (int)m);
+    std::lock_guard<std::mutex> lk(g_wcfg_mu);
+    if (!cfg) {
+        g_wcfg.erase(key);
+        return RBFFD_OK;
+    }
+    if (cfg->kernel < 0 || cfg->kernel > 1 || (cfg->kernel == 0 && m < 1) || cfg->warps_per_block < 1 ||
+        cfg->warps_per_block > 4 || smem_per_warp(cfg->kernel, n, m) * cfg->warps_per_block > 227 * 1024)
+        return RBFFD_ERR_INVALID_ARG;
+    g_wcfg[key] = std::make_pair(WCfg{cfg->kernel, cfg->warps_per_block}, 0.0);
     return RBFFD_OK;
 }
 

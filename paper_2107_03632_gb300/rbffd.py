@@ -52,6 +52,18 @@ class Csr(ctypes.Structure):
     ]
 
 
+class WeightsConfig(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_int32),
+        ("warps_per_block", ctypes.c_int32),
+        ("ms_per_mnode", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {"kernel": ("null-space", "gauss")[self.kernel], "warps_per_block": self.warps_per_block,
+                "ms_per_mnode": self.ms_per_mnode}
+
+
 class MgHandle(ctypes.Structure):
     """rbffd_mg: host object filled by rbffd_mg_setup (opaque)."""
 
@@ -124,6 +136,10 @@ SIGNATURES = {
     "rbffd_stencils": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
     "rbffd_stencils_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP]),
     "rbffd_weights": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, _VP]),
+    "rbffd_weights_autotune": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, ctypes.POINTER(WeightsConfig),
+                                              _VP]),
+    "rbffd_weights_get_config": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(WeightsConfig)]),
+    "rbffd_weights_set_config": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(WeightsConfig)]),
     "rbffd_assemble_workspace_size": (_SZ, [_I64]),
     "rbffd_assemble_pattern": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
     "rbffd_assemble": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _VP, _I64, _VP, _VP, _VP, _VP]),
@@ -138,10 +154,15 @@ SIGNATURES = {
     "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32]),
     "rbffd_solve_batched": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _VP, _VP, _VP, _VP, _I32, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_explicit_workspace_size": (_SZ, [_I64, _I32]),
+    "rbffd_explicit_pack": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(ctypes.c_int64), _VP, _SZ,
+                                           _VP]),
+    "rbffd_explicit_run": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I64, _D, _I64, _VP, _SZ, _VP]),
     "rbffd_mg_workspace_size": (_SZ, [_I64, _I64]),
     "rbffd_mg_setup": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(Csr), ctypes.POINTER(Csr), _I32, _D,
                                       ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
     "rbffd_mg_levels": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(ctypes.c_int64)]),
+    "rbffd_diag_recip": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP]),
     "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
 }
@@ -363,7 +384,7 @@ class Multigrid:
     Holds the host handle and the device workspace it points into."""
 
     def __init__(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2,
-                 omega: float = 0.5, ws: torch.Tensor | None = None):
+                 omega: float = 0.6, ws: torch.Tensor | None = None):
         N = xy.shape[0]
         _require(xy, torch.float64, "xy", (N, 2))
         _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
@@ -380,7 +401,7 @@ class Multigrid:
                                   ctypes.byref(self.handle), _ptr(ws), ws.numel(), _stream(xy.device)),
                "rbffd_mg_setup")
 
-    def setup(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2, omega: float = 0.5):
+    def setup(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2, omega: float = 0.6):
         """Rebuilds the hierarchy in the same workspace (same node count)."""
         lib = load()
         c64 = A.c64()
@@ -395,6 +416,61 @@ class Multigrid:
         arr = (ctypes.c_int64 * MG_MAX_LEVELS)()
         n = load().rbffd_mg_levels(ctypes.byref(self.handle), arr)
         return [int(arr[i]) for i in range(n)]
+
+
+class ExplicitLoop:
+    """The explicit time loop of Eq. 4 on packed interior rows (rbffd_explicit_*)."""
+
+    def __init__(self, idx: torch.Tensor, w: torch.Tensor, is_dirichlet: torch.Tensor, ws: torch.Tensor | None = None):
+        N, n = idx.shape
+        _require(idx, torch.int32, "idx", (N, n))
+        _require(w, torch.float64, "w", (N, n))
+        _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+        lib = load()
+        self.N, self.n = N, n
+        self.ws = ws if ws is not None else _workspace(lib.rbffd_explicit_workspace_size(N, n), idx.device)
+        ni = ctypes.c_int64(0)
+        _check(lib.rbffd_explicit_pack(_ptr(idx), _ptr(w), _ptr(is_dirichlet), N, n, ctypes.byref(ni), _ptr(self.ws),
+                                       self.ws.numel(), _stream(idx.device)), "rbffd_explicit_pack")
+        self.n_interior = int(ni.value)
+
+    def run(self, f: torch.Tensor, u: torch.Tensor, dt: float, steps: int) -> torch.Tensor:
+        """Advances u in place by `steps` forward-Euler steps; returns u."""
+        _require(f, torch.float64, "f", (self.N,))
+        _require(u, torch.float64, "u", (self.N,))
+        _check(load().rbffd_explicit_run(_ptr(f), _ptr(u), self.N, self.n, self.n_interior, float(dt), int(steps),
+                                         _ptr(self.ws), self.ws.numel(), _stream(u.device)), "rbffd_explicit_run")
+        return u
+
+
+def rbffd_weights_autotune(xy: torch.Tensor, idx: torch.Tensor, m: int) -> dict:
+    """Times the weight-solve configurations on (a sample of) these stencils and
+    keeps the fastest for (n, m); returns it."""
+    N, n = idx.shape
+    _require(xy, torch.float64, "xy", (N, 2))
+    _require(idx, torch.int32, "idx", (N, n))
+    w = torch.empty((N, n), dtype=torch.float64, device=xy.device)
+    st = torch.empty(N, dtype=torch.int32, device=xy.device)
+    best = WeightsConfig()
+    _check(load().rbffd_weights_autotune(_ptr(xy), _ptr(idx), N, n, int(m), _ptr(w), _ptr(st), ctypes.byref(best),
+                                         _stream(xy.device)), "rbffd_weights_autotune")
+    return best.as_dict()
+
+
+def weights_config(n: int, m: int) -> dict:
+    c = WeightsConfig()
+    _check(load().rbffd_weights_get_config(int(n), int(m), ctypes.byref(c)), "rbffd_weights_get_config")
+    return c.as_dict()
+
+
+def set_weights_config(n: int, m: int, kernel: str | None = None, warps_per_block: int = 0):
+    """Pins the weight-solve configuration for (n, m); kernel None: back to the default."""
+    lib = load()
+    if kernel is None:
+        _check(lib.rbffd_weights_set_config(int(n), int(m), None), "rbffd_weights_set_config")
+        return
+    c = WeightsConfig({"null-space": 0, "gauss": 1}[kernel], int(warps_per_block), 0.0)
+    _check(lib.rbffd_weights_set_config(int(n), int(m), ctypes.byref(c)), "rbffd_weights_set_config")
 
 
 def mg_workspace(N: int, nnz: int, device) -> torch.Tensor:

@@ -160,3 +160,24 @@ def test_multigrid_argument_errors(cdll):
     opts.precond = 1
     assert cdll.rbffd_solve_adjoint(ctypes.byref(A), None, 0x7000, 0x4000, 0x5000, None, None,
                                     ctypes.byref(opts), ctypes.byref(info), 0x6000, 1 << 30, None) == INVALID
+
+
+def test_weights_config_table(cdll):
+    """The weight-solve configuration table is host-side: pin, read back, reject, clear."""
+    from paper_2107_03632_gb300 import rbffd
+
+    c = rbffd.WeightsConfig()
+    assert cdll.rbffd_weights_get_config(56, 6, ctypes.byref(c)) == 0
+    assert c.kernel == 0 and 1 <= c.warps_per_block <= 4  # null-space by default for m >= 1
+    assert cdll.rbffd_weights_get_config(12, 0, ctypes.byref(c)) == 0 and c.kernel == 1  # m = 0: elimination
+    pin = rbffd.WeightsConfig(1, 2, 0.0)
+    assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(pin)) == 0
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0
+    assert (c.kernel, c.warps_per_block) == (1, 2)
+    assert cdll.rbffd_weights_set_config(30, 4, None) == 0
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0
+    for bad in (rbffd.WeightsConfig(2, 1, 0.0), rbffd.WeightsConfig(0, 5, 0.0), rbffd.WeightsConfig(0, 0, 0.0)):
+        assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(bad)) == 1
+    assert cdll.rbffd_weights_set_config(12, 0, ctypes.byref(rbffd.WeightsConfig(0, 1, 0.0))) == 1  # m = 0
+    assert cdll.rbffd_weights_set_config(10, 4, ctypes.byref(pin)) == 1  # n < s
+    assert cdll.rbffd_weights_autotune(None, 0x1000, 10, 6, 2, 0x2000, None, None, None) == 1

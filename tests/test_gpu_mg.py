@@ -121,3 +121,39 @@ def test_mg_rejects_mismatched_hierarchy(lib):
     _, info = rbffd.rbffd_solve(A1, torch.ones(d1.N, dtype=torch.float64, device=DEV),
                                 opts=rbffd.make_opts(precision="mixed", mg=mg), raise_on_error=False)
     assert info["status_code"] == 1
+
+
+def test_mg_full_size_sampled_residual(lib):
+    """1M nodes, m = 4, n = 30, the bench's launch configuration (multigrid,
+    float32 V-cycle): the oracle cannot solve the system at this size, but it
+    can recompute sampled rows of A from their own stencils and weights; on
+    those rows |b_i - (A u)_i| must stay within the solve's bound
+    1e-10 |b|_2 plus what the weights' parity bar (1e-9 of a stencil's
+    largest weight) allows."""
+    from paper_2107_03632_gb300 import rbffd
+
+    h, m, n = 1.7725e-3, 4, 30
+    d = disk_nodes(h)
+    u_ex, f, g = manufactured(d.xy)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    idx = rbffd.rbffd_stencils(xy, n)
+    w, st = rbffd.rbffd_weights(xy, idx, m)
+    A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
+    b = rbffd.rbffd_rhs(T(f), T(g), mask)
+    mg = rbffd.Multigrid(xy, mask, A)
+    x, info = rbffd.rbffd_solve(A, b, opts=rbffd.make_opts(tol=1e-10, precision="mixed", mg=mg))
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10 and info["iters"] <= 40
+    u = x.cpu().numpy()
+    bh = oracle.rhs(f, g, d.is_dirichlet)
+    rng = np.random.default_rng(11)
+    rows = rng.choice(np.flatnonzero(d.is_dirichlet == 0), 200, replace=False)
+    idx_o = oracle.knn_query(d.xy, n, rows)
+    full = np.zeros((d.N, n), dtype=np.int32)
+    full[rows] = idx_o
+    w_o, _ = oracle.weights(d.xy, full, m, nodes=rows)
+    uu = u[idx_o.astype(np.int64)]
+    r = bh[rows] - (w_o * uu).sum(axis=1)
+    bound = 1e-10 * np.linalg.norm(bh) + 1e-9 * np.abs(w_o).max(axis=1) * np.abs(uu).sum(axis=1)
+    assert (np.abs(r) <= bound).all()
+    # and the discrete solution approximates sin(pi x) sin(pi y) to the scheme's accuracy
+    assert np.abs(u - u_ex).max() <= 1e-6
