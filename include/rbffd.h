@@ -130,8 +130,10 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
                   double* w, int32_t* node_status, void* stream);
 
 /* Weight-solve launch configuration ("tile shape") per (n, m): the solver   */
-/* (0 null-space elimination, 1 full Gaussian elimination) and the stencils */
-/* (warps) per block, 1..4.  rbffd_weights_autotune times every candidate   */
+/* and its threads per stencil -- 0 null-space elimination, one warp per    */
+/* stencil, 1..4 stencils (warps) per block; 1 full Gaussian elimination,  */
+/* likewise; 2 null-space elimination with two warps per stencil, one       */
+/* stencil per block (warps_per_block = 2).  rbffd_weights_autotune times every candidate   */
 /* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */
 /* the given set (3 launches each after one warm-up, CUDA events), records  */
 /* the fastest for (current device, n, m) in a process-wide table that      */
@@ -142,8 +144,8 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* configuration in force; rbffd_weights_set_config pins one (NULL: back to  */
 /* the default, which follows the shared-memory footprint).                  */
 typedef struct rbffd_weights_config {
-    int32_t kernel;          /* 0 = null-space elimination, 1 = Gaussian elimination */
-    int32_t warps_per_block; /* stencils per block, one warp each */
+    int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 null-space (2 warps/stencil) */
+    int32_t warps_per_block; /* warps per block (kernels 0, 1: one stencil per warp; kernel 2: 2) */
     double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
 } rbffd_weights_config;
 int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,

@@ -334,14 +334,64 @@ NsGeom ns_geom(int n, int m) {
     return g;
 }
 
+// Synchronisation and reductions over the threads of one stencil: a warp
+// (NT = 32) or the whole block (NT = 64, one stencil per block).
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+    if (NT == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ int group_any(int p) {
+    if (NT == 32) return __any_sync(0xffffffffu, p);
+    return __syncthreads_or(p);
+}
+
+// Max over the group of a per-warp maximum (already reduced within each warp).
+template <int NT>
+__device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v, unsigned long long* sh) {
+    if (NT == 32) return v;
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    const unsigned long long r = sh[0] > sh[1] ? sh[0] : sh[1];
+    __syncthreads();
+    return r;
+}
+
+// Pivot (largest |value|, then lowest row) over the group, from per-warp results.
+template <int NT>
+__device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, int& bpos, unsigned long long* shb,
+                                             int* shi) {
+    if (NT == 32) return;
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        shb[w] = best;
+        shi[2 * w] = bi;
+        shi[2 * w + 1] = bpos;
+    }
+    __syncthreads();
+    const bool second = shb[1] > shb[0] || (shb[1] == shb[0] && shi[2] < shi[0]);
+    best = second ? shb[1] : shb[0];
+    bi = second ? shi[2] : shi[0];
+    bpos = second ? shi[3] : shi[1];
+    __syncthreads();
+}
+
+template <int NT>
 __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
                                                          int N, int n, int m, int s, int LDF, int LDS,
                                                          int bytes_per_warp, double* __restrict__ w,
                                                          int* __restrict__ node_status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
+    // NT threads per stencil: one warp (several stencils per block) or two
+    // warps (one stencil per block, block-wide synchronisation)
+    const int lane = threadIdx.x % NT;
+    const int wib = threadIdx.x / NT;
+    const int wpb = blockDim.x / NT;
+    __shared__ unsigned long long red_u64[2];
+    __shared__ int red_i[4];
     const int q = n - s;
     double* Phi = reinterpret_cast<double*>(smem_raw + (size_t)wib * bytes_per_warp);
     double* P = Phi + (size_t)n * LDF;
@@ -361,7 +411,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         // ---- shift, scale ----------------------------------------------------
         unsigned long long dmax = 0;
         int bad = 0;
-        for (int j = lane; j < n; j += 32) {
+        for (int j = lane; j < n; j += NT) {
             const int sj = sten[j];
             const bool ok = (unsigned)sj < (unsigned)N;  // never read outside xy
             bad |= ok ? 0 : 1;
@@ -379,12 +429,13 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             const unsigned long long t = __shfl_xor_sync(0xffffffffu, dmax, o);
             dmax = (t > dmax) ? t : dmax;
         }
+        dmax = group_max_u64<NT>(dmax, red_u64);
         const double delta = __dsqrt_rn(__longlong_as_double((long long)dmax));
         const double delta2 = __dmul_rn(delta, delta);
-        __syncwarp();
+        group_sync<NT>();
 
         // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
-        for (int j = lane; j < n; j += 32) {
+        for (int j = lane; j < n; j += NT) {
             const double xh = __ddiv_rn(crd[2 * j], delta);
             const double yh = __ddiv_rn(crd[2 * j + 1], delta);
             crd[2 * j] = xh;
@@ -402,19 +453,19 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 for (int i = 0; i <= d; ++i, ++col) P[(size_t)j * LDS + col] = (d == 0) ? 1.0 : __dmul_rn(xp[d - i], yp[i]);
             act[j] = j;
         }
-        for (int col = lane; col < s; col += 32) {
+        for (int col = lane; col < s; col += NT) {
             // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5)
             P[(size_t)n * LDS + col] = (col == 3 || col == 5) ? 2.0 : 0.0;
         }
-        __syncwarp();
+        group_sync<NT>();
 
         // ---- Gauss-Jordan with row pivoting on P ------------------------------
         int na = n;  // active (not yet pivot) rows act[0..na)
-        int singular = __any_sync(0xffffffffu, bad) ? 1 : 0;
+        int singular = group_any<NT>(bad) ? 1 : 0;
         for (int k = 0; k < s && !singular; ++k) {
             unsigned long long best = 0;
             int bi = 0x7fffffff, bpos = -1;
-            for (int t = lane; t < na; t += 32) {
+            for (int t = lane; t < na; t += NT) {
                 const int r = act[t];
                 const unsigned long long b = abs_bits(P[(size_t)r * LDS + k]);
                 if (b > best || (b == best && r < bi)) {
@@ -434,6 +485,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     bpos = op;
                 }
             }
+            group_argmax<NT>(best, bi, bpos, red_u64, red_i);
             // rank deficient (pivot below 1e-12: P's entries are monomials of
             // points in the unit disk, so |P| <= 1) or non-finite
             if (__longlong_as_double((long long)best) < 1e-12 || best >= 0x7ff0000000000000ull) {
@@ -442,27 +494,27 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             }
             const int pr = bi;
             const double inv = rcp64(P[(size_t)pr * LDS + k]);
-            __syncwarp();
+            group_sync<NT>();
             if (lane == 0) {
                 perm[k] = pr;
                 act[bpos] = act[na - 1];  // swap-remove the pivot row
             }
             --na;
-            __syncwarp();
+            group_sync<NT>();
             // scale column k on the active rows and the g row; pivot row -> e_k
-            for (int t = lane; t <= na; t += 32) {
+            for (int t = lane; t <= na; t += NT) {
                 const int r = (t < na) ? act[t] : n;
                 P[(size_t)r * LDS + k] = __dmul_rn(P[(size_t)r * LDS + k], inv);
             }
-            __syncwarp();
+            group_sync<NT>();
             // column j -= P[pr][j] * column k, on active rows and the g row;
             // flattened (row t, column jj) with incremental indices
             const int cols = s - 1, rows = na + 1, total = rows * cols;
             if (cols > 0) {
                 int t = lane / cols, jj = lane - (lane / cols) * cols;
-                const int st = 32 / cols, sj = 32 - (32 / cols) * cols;
+                const int st = NT / cols, sj = NT - (NT / cols) * cols;
                 const double* prow = P + (size_t)pr * LDS;
-                for (int e = lane; e < total; e += 32) {
+                for (int e = lane; e < total; e += NT) {
                     const int j = jj + ((jj >= k) ? 1 : 0);
                     const int r = (t < na) ? act[t] : n;
                     double* rr = P + (size_t)r * LDS;
@@ -475,18 +527,18 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     }
                 }
             }
-            __syncwarp();
+            group_sync<NT>();
         }
         if (!singular) {
-            for (int t = lane; t < q; t += 32) perm[s + t] = act[t];
+            for (int t = lane; t < q; t += NT) perm[s + t] = act[t];
         }
-        __syncwarp();
+        group_sync<NT>();
 
         // ---- Phi in permuted order, and f = 9 |xh| ---------------------------
         int coincident = 0;
         if (!singular) {
             const int npairs = n * (n - 1) / 2;
-            for (int pidx = lane; pidx < npairs; pidx += 32) {
+            for (int pidx = lane; pidx < npairs; pidx += NT) {
                 int a = (int)((2.0f * n - 1.0f - sqrtf((2.0f * n - 1.0f) * (2.0f * n - 1.0f) - 8.0f * pidx)) * 0.5f);
                 if (a < 0) a = 0;
                 while (a > 0 && a * (2 * n - a - 1) / 2 > pidx) --a;
@@ -502,21 +554,21 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 Phi[(size_t)a * LDF + b] = phi;
                 Phi[(size_t)b * LDF + a] = phi;
             }
-            for (int a = lane; a < n; a += 32) {
+            for (int a = lane; a < n; a += NT) {
                 Phi[(size_t)a * LDF + a] = 0.0;
                 const int ja = perm[a];
                 const double xh = crd[2 * ja], yh = crd[2 * ja + 1];
                 fv[a] = __dmul_rn(9.0, __dsqrt_rn(__dadd_rn(__dmul_rn(xh, xh), __dmul_rn(yh, yh))));
             }
         }
-        singular |= __any_sync(0xffffffffu, coincident) ? 1 : 0;
-        __syncwarp();
+        singular |= group_any<NT>(coincident) ? 1 : 0;
+        group_sync<NT>();
 
         if (!singular) {
             // X[j][k] = P[perm[s + j]][k], w0[k] = P[n][k]
             const double* w0 = P + (size_t)n * LDS;
             // ---- T = Phi12 - Phi11 X^T  (s x q, in place) --------------------
-            for (int e = lane; e < s * q; e += 32) {
+            for (int e = lane; e < s * q; e += NT) {
                 const int a = e / q, j = e - (e / q) * q;
                 const double* xr = P + (size_t)perm[s + j] * LDS;
                 const double* pr = Phi + (size_t)a * LDF;
@@ -532,7 +584,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 Phi[(size_t)a * LDF + s + j] = acc + acc1;
             }
             // ---- u = f - Phi[:, 0..s) w0 ----------------------------------------
-            for (int a = lane; a < n; a += 32) {
+            for (int a = lane; a < n; a += NT) {
                 const double* pr = Phi + (size_t)a * LDF;
                 double acc = fv[a], acc1 = 0.0;
                 int k = 0;
@@ -543,10 +595,10 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 if (k < s) acc = fma(-pr[k], w0[k], acc);
                 uv[a] = acc + acc1;
             }
-            __syncwarp();
+            group_sync<NT>();
             // ---- S = Phi22 - Phi21 X^T - X T (lower triangle, in place) -----
             const int nlow = q * (q + 1) / 2;
-            for (int e = lane; e < nlow; e += 32) {
+            for (int e = lane; e < nlow; e += NT) {
                 int j = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
                 while (j * (j + 1) / 2 > e) --j;
                 while ((j + 1) * (j + 2) / 2 <= e) ++j;
@@ -562,7 +614,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 Phi[(size_t)(s + j) * LDF + s + l] = acc + acc1;
             }
             // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
-            for (int j = lane; j < q; j += 32) {
+            for (int j = lane; j < q; j += NT) {
                 const double* xj = P + (size_t)perm[s + j] * LDS;
                 double acc = uv[s + j], acc1 = 0.0;
                 int k = 0;
@@ -573,7 +625,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 if (k < s) acc = fma(-xj[k], uv[k], acc);
                 tv[j] = acc + acc1;
             }
-            __syncwarp();
+            group_sync<NT>();
             // ---- Cholesky S = L L^T (lower, in place) ----------------------------
             for (int cI = 0; cI < q && !singular; ++cI) {
                 double* sc = Phi + (size_t)(s + cI) * LDF + s;
@@ -586,8 +638,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 // kept (in fv, free by now) for the substitutions
                 const double inv = rsqrt64(dcc);
                 const double lcc = __dmul_rn(dcc, inv);
-                __syncwarp();
-                for (int i = cI + 1 + lane; i < q; i += 32) {
+                group_sync<NT>();
+                for (int i = cI + 1 + lane; i < q; i += NT) {
                     double* si = Phi + (size_t)(s + i) * LDF + s;
                     si[cI] = __dmul_rn(si[cI], inv);
                 }
@@ -595,10 +647,10 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     sc[cI] = lcc;
                     fv[cI] = inv;
                 }
-                __syncwarp();
+                group_sync<NT>();
                 // trailing lower triangle: S[i][j] -= L[i][c] L[j][c], c < j <= i
                 const int rem = q - cI - 1, ntr = rem * (rem + 1) / 2;
-                for (int e = lane; e < ntr; e += 32) {
+                for (int e = lane; e < ntr; e += NT) {
                     int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
                     while (i * (i + 1) / 2 > e) --i;
                     while ((i + 1) * (i + 2) / 2 <= e) ++i;
@@ -607,30 +659,30 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     const double* sj = Phi + (size_t)(s + cI + 1 + j) * LDF + s;
                     si[cI + 1 + j] = fma(-si[cI], sj[cI], si[cI + 1 + j]);
                 }
-                __syncwarp();
+                group_sync<NT>();
             }
         }
         if (!singular) {
             // ---- forward (L y = t) and back (L^T z = y) substitution -------------
             for (int cI = 0; cI < q; ++cI) {
                 const double yc = __dmul_rn(tv[cI], fv[cI]);
-                __syncwarp();
-                for (int i = cI + 1 + lane; i < q; i += 32)
+                group_sync<NT>();
+                for (int i = cI + 1 + lane; i < q; i += NT)
                     tv[i] = fma(-Phi[(size_t)(s + i) * LDF + s + cI], yc, tv[i]);
                 if (lane == 0) tv[cI] = yc;
-                __syncwarp();
+                group_sync<NT>();
             }
             for (int cI = q - 1; cI >= 0; --cI) {
                 const double* sc = Phi + (size_t)(s + cI) * LDF + s;
                 const double zc = __dmul_rn(tv[cI], fv[cI]);
-                __syncwarp();
-                for (int i = lane; i < cI; i += 32) tv[i] = fma(-sc[i], zc, tv[i]);
+                group_sync<NT>();
+                for (int i = lane; i < cI; i += NT) tv[i] = fma(-sc[i], zc, tv[i]);
                 if (lane == 0) tv[cI] = zc;
-                __syncwarp();
+                group_sync<NT>();
             }
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
             const double* w0 = P + (size_t)n * LDS;
-            for (int k = lane; k < s; k += 32) {
+            for (int k = lane; k < s; k += NT) {
                 double acc = w0[k], acc1 = 0.0;
                 int j = 0;
                 for (; j + 1 < q; j += 2) {
@@ -640,23 +692,23 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 if (j < q) acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
                 wv[k] = acc + acc1;
             }
-            for (int j = lane; j < q; j += 32) wv[s + j] = tv[j];
-            __syncwarp();
+            for (int j = lane; j < q; j += NT) wv[s + j] = tv[j];
+            group_sync<NT>();
         }
 
         // ---- scale back to the caller's order --------------------------------
         double* wout = w + (int64_t)node * n;
         int nonfinite = 0;
-        for (int a = lane; a < n; a += 32) {
+        for (int a = lane; a < n; a += NT) {
             const double v = singular ? 0.0 : __ddiv_rn(wv[a], delta2);
             nonfinite |= isfinite(v) ? 0 : 1;
             wv[a] = v;
         }
-        const int fail = (singular || __any_sync(0xffffffffu, nonfinite)) ? 1 : 0;
-        __syncwarp();
-        for (int a = lane; a < n; a += 32) wout[singular ? a : perm[a]] = fail ? 0.0 : wv[a];
+        const int fail = (singular || group_any<NT>(nonfinite)) ? 1 : 0;
+        group_sync<NT>();
+        for (int a = lane; a < n; a += NT) wout[singular ? a : perm[a]] = fail ? 0.0 : wv[a];
         if (node_status && lane == 0) node_status[node] = fail;
-        __syncwarp();
+        group_sync<NT>();
     }
 }
 
@@ -694,8 +746,9 @@ namespace {
 // footprint; rbffd_weights_autotune replaces it with the fastest measured
 // candidate, kept in a process-wide table per (device, n, m).
 struct WCfg {
-    int kernel;  // 0 null-space elimination, 1 full Gaussian elimination
-    int wpb;
+    int kernel;  // 0 null-space elimination (one warp per stencil), 1 full Gaussian
+                 // elimination, 2 null-space elimination with two warps per stencil
+    int wpb;     // warps per block (kernel 2: always 2, one stencil)
 };
 
 std::mutex g_wcfg_mu;
@@ -707,9 +760,21 @@ int current_device() {
     return d;
 }
 
-size_t smem_per_warp(int kernel, int n, int m) {
+// Shared memory per stencil.
+size_t smem_per_stencil(int kernel, int n, int m) {
     if (kernel == 1) return (size_t)weights_geom(n, m).smem_doubles * sizeof(double);
     return (size_t)ns_geom(n, m).bytes;
+}
+
+// Stencils per block of a configuration, and its dynamic shared memory.
+int stencils_per_block(const WCfg& c) { return c.kernel == 2 ? 1 : c.wpb; }
+size_t block_smem(const WCfg& c, int n, int m) { return smem_per_stencil(c.kernel, n, m) * stencils_per_block(c); }
+
+bool cfg_valid(const WCfg& c, int n, int m) {
+    if (c.kernel < 0 || c.kernel > 2) return false;
+    if (c.kernel != 1 && m < 1) return false;  // null-space form needs the linear monomials
+    if (c.kernel == 2 ? c.wpb != 2 : (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
+    return block_smem(c, n, m) <= 227 * 1024;
 }
 
 WCfg default_cfg(int n, int m) {
@@ -718,7 +783,7 @@ WCfg default_cfg(int n, int m) {
     // P^T, which holds once P contains the linear monomials (m >= 1)
     c.kernel = m < 1 ? 1 : 0;
     size_t smem = 0;
-    c.wpb = warps_per_block_for(smem_per_warp(c.kernel, n, m), &smem);
+    c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
     return c;
 }
 
@@ -729,7 +794,7 @@ WCfg chosen_cfg(int n, int m) {
         WCfg c = default_cfg(n, m);
         size_t smem = 0;
         c.kernel = 1;
-        c.wpb = warps_per_block_for(smem_per_warp(1, n, m), &smem);
+        c.wpb = warps_per_block_for(smem_per_stencil(1, n, m), &smem);
         return c;
     }
     std::lock_guard<std::mutex> lk(g_wcfg_mu);
@@ -738,36 +803,48 @@ WCfg chosen_cfg(int n, int m) {
     return default_cfg(n, m);
 }
 
+template <int NT>
+int launch_ns(const WCfg& c, const double2* xy, const int32_t* idx, int64_t N, int n, int m, double* w,
+              int32_t* node_status, cudaStream_t st) {
+    NsGeom g = ns_geom(n, m);
+    const int spb = stencils_per_block(c);
+    const size_t smem = block_smem(c, n, m);
+    auto kern = weights_ns_kernel<NT>;
+    RBFFD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBFFD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int per_sm = 0;
+    RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT * spb, smem));
+    if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
+    const int64_t need = (N + spb - 1) / spb;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
+    kern<<<blocks, NT * spb, smem, st>>>(xy, idx, (int)N, n, m, g.s, g.LDF, g.LDS, g.bytes, w, node_status);
+    return RBFFD_OK;
+}
+
 int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t N, int n, int m, double* w,
                    int32_t* node_status, cudaStream_t st) {
-    if (c.kernel == 0 && m < 1) return RBFFD_ERR_INVALID_ARG;
-    if (c.wpb < 1 || c.wpb > 4) return RBFFD_ERR_INVALID_ARG;  // __launch_bounds__(128)
-    const size_t smem = smem_per_warp(c.kernel, n, m) * c.wpb;
-    if (smem > 227 * 1024) return RBFFD_ERR_INVALID_ARG;  // system too large for one SM
-    const int wpb = c.wpb;
-    const int64_t need = (N + wpb - 1) / wpb;
-    int per_sm = 0;
+    if (!cfg_valid(c, n, m)) return RBFFD_ERR_INVALID_ARG;
+    const double2* p = reinterpret_cast<const double2*>(xy);
+    int rc = RBFFD_OK;
     if (c.kernel == 1) {
         WeightsGeom g = weights_geom(n, m);
+        const int wpb = c.wpb;
+        const size_t smem = block_smem(c, n, m);
         RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0;
         RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_kernel, 32 * wpb, smem));
         if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
+        const int64_t need = (N + wpb - 1) / wpb;
         const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
-        weights_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m, g.s,
-                                                       g.M, g.LD, g.coords_in_zero_block, g.smem_doubles, w,
-                                                       node_status, reinterpret_cast<const double2*>(xy), (int)N, 0);
+        weights_kernel<<<blocks, 32 * wpb, smem, st>>>(p, idx, (int)N, n, m, g.s, g.M, g.LD, g.coords_in_zero_block,
+                                                       g.smem_doubles, w, node_status, p, (int)N, 0);
+    } else if (c.kernel == 0) {
+        rc = launch_ns<32>(c, p, idx, N, n, m, w, node_status, st);
     } else {
-        NsGeom g = ns_geom(n, m);
-        RBFFD_CUDA_TRY(
-            cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        RBFFD_CUDA_TRY(cudaFuncSetAttribute(weights_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, weights_ns_kernel, 32 * wpb, smem));
-        if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
-        const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
-        weights_ns_kernel<<<blocks, 32 * wpb, smem, st>>>(reinterpret_cast<const double2*>(xy), idx, (int)N, n, m,
-                                                          g.s, g.LDF, g.LDS, g.bytes, w, node_status);
+        rc = launch_ns<64>(c, p, idx, N, n, m, w, node_status, st);
     }
+    if (rc != RBFFD_OK) return rc;
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
@@ -798,9 +875,10 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
     // sample: the first stencils, enough for several waves of resident warps
     const int64_t S = std::min<int64_t>(N, (int64_t)sm_count() * 128);
     std::vector<WCfg> cands;
-    for (int kernel = (m < 1 ? 1 : 0); kernel <= 1; ++kernel)
+    for (int kernel = 0; kernel <= 1; ++kernel)
         for (int wpb = 1; wpb <= 4; ++wpb)
-            if (smem_per_warp(kernel, n, m) * wpb <= 227 * 1024) cands.push_back(WCfg{kernel, wpb});
+            if (cfg_valid(WCfg{kernel, wpb}, n, m)) cands.push_back(WCfg{kernel, wpb});
+    if (cfg_valid(WCfg{2, 2}, n, m)) cands.push_back(WCfg{2, 2});
     if (cands.empty()) return RBFFD_ERR_INVALID_ARG;
     cudaEvent_t e0, e1;
     RBFFD_CUDA_TRY(cudaEventCreate(&e0));
@@ -867,9 +945,7 @@ extern "C" int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weight
         g_wcfg.erase(key);
         return RBFFD_OK;
     }
-    if (cfg->kernel < 0 || cfg->kernel > 1 || (cfg->kernel == 0 && m < 1) || cfg->warps_per_block < 1 ||
-        cfg->warps_per_block > 4 || smem_per_warp(cfg->kernel, n, m) * cfg->warps_per_block > 227 * 1024)
-        return RBFFD_ERR_INVALID_ARG;
+    if (!cfg_valid(WCfg{cfg->kernel, cfg->warps_per_block}, n, m)) return RBFFD_ERR_INVALID_ARG;
     g_wcfg[key] = std::make_pair(WCfg{cfg->kernel, cfg->warps_per_block}, 0.0);
     return RBFFD_OK;
 }

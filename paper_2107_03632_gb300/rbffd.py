@@ -60,8 +60,8 @@ class WeightsConfig(ctypes.Structure):
     ]
 
     def as_dict(self):
-        return {"kernel": ("null-space", "gauss")[self.kernel], "warps_per_block": self.warps_per_block,
-                "ms_per_mnode": self.ms_per_mnode}
+        return {"kernel": ("null-space", "gauss", "null-space-2warp")[self.kernel],
+                "warps_per_block": self.warps_per_block, "ms_per_mnode": self.ms_per_mnode}
 
 
 class MgHandle(ctypes.Structure):
@@ -469,7 +469,7 @@ def set_weights_config(n: int, m: int, kernel: str | None = None, warps_per_bloc
     if kernel is None:
         _check(lib.rbffd_weights_set_config(int(n), int(m), None), "rbffd_weights_set_config")
         return
-    c = WeightsConfig({"null-space": 0, "gauss": 1}[kernel], int(warps_per_block), 0.0)
+    c = WeightsConfig({"null-space": 0, "gauss": 1, "null-space-2warp": 2}[kernel], int(warps_per_block), 0.0)
     _check(lib.rbffd_weights_set_config(int(n), int(m), ctypes.byref(c)), "rbffd_weights_set_config")
 
 
