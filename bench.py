@@ -440,8 +440,14 @@ def run_gpu_batched(args):
             xi = xy[off:off + d.N]
             wcfg[(n, m)] = rbffd.rbffd_weights_autotune(xi, rbffd.rbffd_stencils(xi, n), m)
         off += d.N
-    wsb = rbffd.batched_workspace(sizes, R, dev)
-    opts = rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol)
+    use_mg = args.precond == "mg"
+    if use_mg:
+        # per-instance multigrid; FP64 BiCGSTAB per (instance, rhs), one pass
+        opts = rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.mg_pass_tol)
+        opts.precond = 1
+    else:
+        opts = rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol)
+    wsb = rbffd.batched_workspace(sizes, R, dev, opts)
 
     def step():
         U.zero_()
@@ -496,7 +502,10 @@ def run_gpu_batched(args):
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "instances": len(sizes), "N_total": N, "rhs": R,
                    "m_counts": {m: sum(1 for x in sizes if x[1] == m) for m in (2, 4, 6)},
-                   "tol": 1e-10, "inner_tol": args.inner_tol, "parallelism": f"replicas x{ws}",
+                   "tol": 1e-10, "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol,
+                   "precond": ("per-instance multigrid V(2,2), float32 V-cycle over all rhs, FP64 BiCGSTAB per pair"
+                               if use_mg else "jacobi (float32 inner BiCGSTAB, FP64 refinement)"),
+                   "parallelism": f"replicas x{ws}",
                    "weights_config": {f"n{k[0]}_m{k[1]}": v for k, v in wcfg.items()},
                    "l2": "inputs larger than L2 (vectors ~%.0f GB)" % (N * R * 8 * 8 / 1e9)},
         "solve": {"iters_max": max(i["iters"] for i in infos), "iters_mean": float(np.mean([i["iters"] for i in infos])),

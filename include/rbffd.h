@@ -132,8 +132,8 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* Weight-solve launch configuration ("tile shape") per (n, m): the solver   */
 /* and its threads per stencil -- 0 null-space elimination, one warp per    */
 /* stencil, 1..4 stencils (warps) per block; 1 full Gaussian elimination,  */
-/* likewise; 2 null-space elimination with two warps per stencil, one       */
-/* stencil per block (warps_per_block = 2).  rbffd_weights_autotune times every candidate   */
+/* likewise; 2 / 3 null-space elimination with two / four warps per        */
+/* stencil, one stencil per block (warps_per_block = 2 / 4).  rbffd_weights_autotune times every candidate   */
 /* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */
 /* the given set (3 launches each after one warm-up, CUDA events), records  */
 /* the fastest for (current device, n, m) in a process-wide table that      */
@@ -144,8 +144,8 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* configuration in force; rbffd_weights_set_config pins one (NULL: back to  */
 /* the default, which follows the shared-memory footprint).                  */
 typedef struct rbffd_weights_config {
-    int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 null-space (2 warps/stencil) */
-    int32_t warps_per_block; /* warps per block (kernels 0, 1: one stencil per warp; kernel 2: 2) */
+    int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 / 3 null-space (2 / 4 warps) */
+    int32_t warps_per_block; /* warps per block (kernels 0, 1: one stencil per warp; kernels 2, 3: 2, 4) */
     double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
 } rbffd_weights_config;
 int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
@@ -225,7 +225,7 @@ int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t
 /*  * coarsening: one node per cell of a uniform grid of side ~2x the mean   */
 /*    spacing (a Dirichlet node where the cell has one, else the node        */
 /*    nearest the cell centre; ties to the lower index), so each level has   */
-/*    at most half the nodes of the one above; down to <= 512 nodes;         */
+/*    at most half the nodes of the one above; down to <= 128 nodes;         */
 /*  * coarse operators: rediscretised -- stencils, RBF-FD Laplacian weights  */
 /*    (r^3 + monomials of degree 2, n = 12) and Dirichlet rows on the coarse */
 /*    nodes, as in Sec. II Eq. 1 / Sec. IV;                                  */
@@ -334,11 +334,17 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
 /* solution arrays f, g, u (N_total x n_rhs, entry [node * n_rhs + k]).     */
 /* Per instance: stencils, weights (degree m_i, stencil size n_i), the      */
 /* block of the block-diagonal CSR, and n_rhs right-hand sides b = -f | g.  */
-/* The solve is the mixed one of rbffd_solve (float32 inner BiCGSTAB in     */
-/* double-float vectors, FP64 refinement), run for all (instance, rhs)      */
-/* pairs together: each pair has its own BiCGSTAB scalars and stops on its  */
-/* own relative residual; the inner iterations are replayed as one CUDA     */
-/* graph per chunk of iterations.  Blocks the host like rbffd_solve.        */
+/* With opts->precond = 0 the solve is the Jacobi mixed one of rbffd_solve */
+/* (float32 inner BiCGSTAB in double-float vectors, FP64 refinement), run   */
+/* for all (instance, rhs) pairs together; the inner iterations are         */
+/* replayed as one CUDA graph per chunk of iterations.  With                */
+/* opts->precond = 1 (opts->mg is not used) each instance gets its own      */
+/* multigrid hierarchy (as rbffd_mg_setup, V(2,2), omega 0.6) and every     */
+/* pair runs FP64 BiCGSTAB right-preconditioned by the instance's float32   */
+/* V-cycle, applied to all of its right-hand sides at once; one iteration  */
+/* for all instances is one CUDA graph.  Either way each pair has its own   */
+/* BiCGSTAB scalars and stops on its own relative residual (explicit FP64  */
+/* residual, tol).  Blocks the host like rbffd_solve.                       */
 /*   desc    : host array of n_inst descriptors (offsets contiguous, in      */
 /*             order: node_offset_0 = 0, node_offset_{i+1} = node_offset_i + */
 /*             n_nodes_i).                                                  */
@@ -355,7 +361,10 @@ typedef struct rbffd_batch_desc {
     int32_t n;
 } rbffd_batch_desc;
 
-size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs);
+/* Workspace of rbffd_solve_batched for these instances and the solver     */
+/* options it will get (opts NULL: precond 0).                               */
+size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs,
+                                    const rbffd_solve_opts* opts);
 int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst, const double* xy,
                         const uint8_t* is_dirichlet, const double* f, const double* g, int32_t n_rhs,
                         double* u, const rbffd_solve_opts* opts, rbffd_solve_info* info, void* ws,

@@ -27,18 +27,33 @@
 // block.
 #include "common.cuh"
 #include "df32.cuh"
+#include "internal.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "scan.cuh"
+
+#define RBFFD_CUDA_TRY_NEG(call)               \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) {               \
+            ::rbffd::set_cuda_error(e_);       \
+            return -(int)RBFFD_ERR_CUDA;       \
+        }                                      \
+    } while (0)
 
 namespace rbffd {
 namespace {
 
 constexpr int kBT = 256;          // threads per block (8 warps)
+constexpr int kSetupStreams = 8;  // instances' stencils and weights run on this many streams
 constexpr int kUnitRows = 256;    // rows per unit (32 per warp)
 constexpr int kMaxRhs = 64;
 constexpr int kPassCap = 1500;    // inner iterations per pass at most
@@ -91,6 +106,13 @@ struct BWork {
     double *d, *dinv;
     float *d32, *dinv32, *sig32;
     float2 *xd, *r, *rh, *p, *v, *s, *t;
+    // multigrid mode: FP64 Krylov vectors (r is r64), the preconditioned
+    // directions, the float V-cycle's level-0 work vectors, the coarse-level
+    // vectors and the per-instance hierarchies' workspaces
+    double *mrh, *mp, *mv, *ms, *mt, *mph, *msh;
+    float *f0, *f1, *f2;
+    float* coarse;
+    char* mgws;
 };
 
 __device__ __forceinline__ int find_inst(const Inst* inst, int n_inst, int64_t row) {
@@ -614,6 +636,263 @@ __global__ void __launch_bounds__(kBT) b_refine_kernel(const Unit* __restrict__ 
     }
 }
 
+// ------------------------------------------------------ multigrid mode -----
+// FP64 BiCGSTAB for every (instance, rhs) pair, right-preconditioned by the
+// instance's float32 V-cycle (applied to all of its right-hand sides at
+// once): the FP64 matrix, vectors and scalars decide convergence, the float
+// V-cycle only shapes the search directions.  Passes start from the
+// explicit residual of b_check (r = r64, rh = r, p = v = 0).
+
+__global__ void __launch_bounds__(kBT) m_load_kernel(const Unit* __restrict__ units, int n_units,
+                                                     const Inst* __restrict__ inst, int R,
+                                                     const double* __restrict__ r64, double* __restrict__ rh,
+                                                     double* __restrict__ p, double* __restrict__ v, Pairs pr,
+                                                     unsigned* inst_cnt, int* inst_running, Ctl* ctl, double* part,
+                                                     double inner_tol, int max_iter) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k0 = lane, k1 = lane + 32;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        const Inst in = inst[un.inst];
+        bool any = false;
+        for (int k = 0; k < R; ++k) any |= pr.flag[un.inst * R + k] == kPassEnd;
+        if (!any) continue;
+        const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kPassEnd;
+        const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kPassEnd;
+        double a0[1] = {0.0}, a1[1] = {0.0};
+        for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
+            if (on0) {
+                const int64_t e = row * R + k0;
+                const double ri = r64[e];
+                rh[e] = ri;
+                p[e] = 0.0;
+                v[e] = 0.0;
+                a0[0] = fma(ri, ri, a0[0]);
+            }
+            if (on1) {
+                const int64_t e = row * R + k1;
+                const double ri = r64[e];
+                rh[e] = ri;
+                p[e] = 0.0;
+                v[e] = 0.0;
+                a1[0] = fma(ri, ri, a1[0]);
+            }
+        }
+        unit_store<1>(a0, a1, part, n_units, R, u);
+        if (last_unit(&inst_cnt[un.inst], in.n_units)) {
+            int running = 0;
+            for (int k = threadIdx.x; k < R; k += blockDim.x) {
+                const int pi = un.inst * R + k;
+                if (pr.flag[pi] != kPassEnd) continue;
+                if (pr.iters[pi] >= max_iter) {
+                    pr.flag[pi] = kFail;
+                    continue;
+                }
+                const double rr2 = inst_sum(part, n_units, R, 0, in, k);
+                pr.rho[pi] = pr.alpha[pi] = pr.omega[pi] = 1.0;
+                pr.rho_new[pi] = rr2;
+                pr.s0[pi] = rr2;
+                pr.rn2[pi] = pr.tn2[pi];
+                pr.repl2[pi] = inner_tol * inner_tol;
+                pr.pass_iters[pi] = 0;
+                pr.flag[pi] = (rr2 > 0.0 && isfinite(rr2)) ? kRun : kFail;
+                running += pr.flag[pi] == kRun;
+            }
+            __shared__ int cnt;
+            if (threadIdx.x == 0) cnt = 0;
+            __syncthreads();
+            if (running) atomicAdd(&cnt, running);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                inst_running[un.inst] = cnt;
+                atomicAdd(&ctl->running, cnt);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBT) m_update_p_kernel(const Unit* __restrict__ units, int n_units, int R,
+                                                         const double* __restrict__ rr, const double* __restrict__ v,
+                                                         double* __restrict__ p, Pairs pr,
+                                                         const int* __restrict__ inst_running) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        if (!inst_live(inst_running, un.inst)) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            if (k >= R) continue;
+            const int pi = un.inst * R + k;
+            if (pr.flag[pi] != kRun) continue;
+            const double beta = (pr.rho_new[pi] / pr.rho[pi]) * (pr.alpha[pi] / pr.omega[pi]);
+            const double om = pr.omega[pi];
+            for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
+                const int64_t e = row * R + k;
+                p[e] = fma(beta, fma(-om, v[e], p[e]), rr[e]);
+            }
+        }
+    }
+}
+
+// y = A xin (FP64); MODE 0: (rh, y) -> alpha; MODE 1: (y, s), (y, y) -> omega.
+template <int MODE>
+__global__ void __launch_bounds__(kBT) m_spmm_kernel(const Unit* __restrict__ units, int n_units,
+                                                     const Inst* __restrict__ inst,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                     int R, const double* __restrict__ xin, double* __restrict__ y,
+                                                     const double* __restrict__ dotv, Pairs pr,
+                                                     int* __restrict__ inst_running, unsigned* inst_cnt, Ctl* ctl,
+                                                     double* part) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k0 = lane, k1 = lane + 32;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        if (!inst_live(inst_running, un.inst)) continue;
+        const Inst in = inst[un.inst];
+        const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kRun;
+        const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kRun;
+        double a0[2] = {0.0, 0.0}, a1[2] = {0.0, 0.0};
+        for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
+            const int64_t lo = row_ptr[row], hi = row_ptr[row + 1];
+            double s0 = 0.0, s1 = 0.0;
+            for (int64_t q = lo; q < hi; ++q) {
+                const double a = __ldg(val + q);
+                const int64_t c = (int64_t)__ldg(col + q) * R;
+                if (on0) s0 = fma(a, xin[c + k0], s0);
+                if (on1) s1 = fma(a, xin[c + k1], s1);
+            }
+            if (on0) {
+                const int64_t e = row * R + k0;
+                y[e] = s0;
+                if (MODE == 0) a0[0] = fma(dotv[e], s0, a0[0]);
+                else {
+                    a0[0] = fma(s0, dotv[e], a0[0]);
+                    a0[1] = fma(s0, s0, a0[1]);
+                }
+            }
+            if (on1) {
+                const int64_t e = row * R + k1;
+                y[e] = s1;
+                if (MODE == 0) a1[0] = fma(dotv[e], s1, a1[0]);
+                else {
+                    a1[0] = fma(s1, dotv[e], a1[0]);
+                    a1[1] = fma(s1, s1, a1[1]);
+                }
+            }
+        }
+        unit_store<2>(a0, a1, part, n_units, R, u);
+        if (last_unit(&inst_cnt[un.inst], in.n_units)) {
+            int ended = 0;
+            for (int k = threadIdx.x; k < R; k += blockDim.x) {
+                const int pi = un.inst * R + k;
+                if (pr.flag[pi] != kRun) continue;
+                const double q0 = inst_sum(part, n_units, R, 0, in, k);
+                bool brk = false;
+                if (MODE == 0) {
+                    if (q0 == 0.0 || !isfinite(q0)) {
+                        brk = true;
+                    } else {
+                        pr.alpha[pi] = pr.rho_new[pi] / q0;
+                        pr.rho[pi] = pr.rho_new[pi];
+                    }
+                } else {
+                    const double q1 = inst_sum(part, n_units, R, 1, in, k);
+                    if (!isfinite(q0) || !isfinite(q1)) brk = true;
+                    else pr.omega[pi] = (q1 > 0.0) ? q0 / q1 : 0.0;
+                }
+                if (brk) {
+                    pr.flag[pi] = kPassEnd;
+                    ++ended;
+                }
+            }
+            end_pairs(ended, inst_running + un.inst, ctl);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBT) m_update_s_kernel(const Unit* __restrict__ units, int n_units, int R,
+                                                         const double* __restrict__ rr, const double* __restrict__ v,
+                                                         double* __restrict__ s, Pairs pr,
+                                                         const int* __restrict__ inst_running) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        if (!inst_live(inst_running, un.inst)) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            if (k >= R) continue;
+            const int pi = un.inst * R + k;
+            if (pr.flag[pi] != kRun) continue;
+            const double al = pr.alpha[pi];
+            for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
+                const int64_t e = row * R + k;
+                s[e] = fma(-al, v[e], rr[e]);
+            }
+        }
+    }
+}
+
+// x += alpha ph + omega sh, r = s - omega t; pass end on convergence of the
+// recurrence (inner_tol of the pass start), breakdown, growth, caps.
+__global__ void __launch_bounds__(kBT) m_update_xr_kernel(const Unit* __restrict__ units, int n_units,
+                                                          const Inst* __restrict__ inst, int R, double* __restrict__ x,
+                                                          const double* __restrict__ ph, const double* __restrict__ sh,
+                                                          const double* __restrict__ s, const double* __restrict__ t,
+                                                          double* __restrict__ rr, const double* __restrict__ rh,
+                                                          Pairs pr, int* __restrict__ inst_running, unsigned* inst_cnt,
+                                                          Ctl* ctl, double* part, int max_iter) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        if (!inst_live(inst_running, un.inst)) continue;
+        const Inst in = inst[un.inst];
+        double a[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            if (k >= R) continue;
+            const int pi = un.inst * R + k;
+            if (pr.flag[pi] != kRun) continue;
+            const double al = pr.alpha[pi], om = pr.omega[pi];
+            for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
+                const int64_t e = row * R + k;
+                x[e] = fma(om, sh[e], fma(al, ph[e], x[e]));
+                const double ri = fma(-om, t[e], s[e]);
+                rr[e] = ri;
+                a[h][0] = fma(ri, ri, a[h][0]);
+                a[h][1] = fma(rh[e], ri, a[h][1]);
+            }
+        }
+        unit_store<2>(a[0], a[1], part, n_units, R, u);
+        if (last_unit(&inst_cnt[un.inst], in.n_units)) {
+            int ended = 0;
+            for (int k = threadIdx.x; k < R; k += blockDim.x) {
+                const int pi = un.inst * R + k;
+                if (pr.flag[pi] != kRun) continue;
+                const double rn2 = inst_sum(part, n_units, R, 0, in, k);
+                const double rho_new = inst_sum(part, n_units, R, 1, in, k);
+                pr.rn2[pi] = rn2;
+                pr.rho_new[pi] = rho_new;
+                pr.iters[pi] += 1;
+                pr.pass_iters[pi] += 1;
+                bool end = false;
+                if (!isfinite(rn2) || !isfinite(rho_new) || rho_new == 0.0 || pr.omega[pi] == 0.0) end = true;
+                else if (rn2 <= pr.tol2[pi] || rn2 < pr.repl2[pi] * pr.tn2[pi]) end = true;
+                else if (!(rn2 <= kGrowth2 * pr.s0[pi])) end = true;
+                else if (pr.pass_iters[pi] >= kPassCap || pr.iters[pi] >= max_iter) end = true;
+                if (end) {
+                    pr.flag[pi] = kPassEnd;
+                    ++ended;
+                }
+            }
+            end_pairs(ended, inst_running + un.inst, ctl);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host ---
 struct Plan {
     int n_inst = 0, R = 0, n_units = 0;
@@ -621,12 +900,18 @@ struct Plan {
     size_t knn_ws = 0;
     std::vector<Inst> inst;
     std::vector<Unit> units;
+    // multigrid mode: per instance its hierarchy's workspace and its
+    // coarse-level multi-rhs vectors (bounds), as offsets into two areas
+    bool mg = false;
+    std::vector<size_t> mg_off, mg_bytes, coarse_off;
+    size_t mg_total = 0, coarse_total = 0;
 };
 
-bool make_plan(const rbffd_batch_desc* desc, int32_t n_inst, int32_t R, Plan* pl) {
+bool make_plan(const rbffd_batch_desc* desc, int32_t n_inst, int32_t R, bool mg, Plan* pl) {
     if (!desc || n_inst < 1 || R < 1 || R > kMaxRhs) return false;
     pl->n_inst = n_inst;
     pl->R = R;
+    pl->mg = mg;
     int64_t off = 0, idx_off = 0;
     int uoff = 0;
     for (int i = 0; i < n_inst; ++i) {
@@ -653,6 +938,17 @@ bool make_plan(const rbffd_batch_desc* desc, int32_t n_inst, int32_t R, Plan* pl
         }
         uoff += in.n_units;
         pl->inst.push_back(in);
+        if (mg) {
+            const size_t b = align_up(rbffd_mg_workspace_size(d.n_nodes, 0));
+            if (b == 0) return false;
+            pl->mg_off.push_back(pl->mg_total);
+            pl->mg_bytes.push_back(b);
+            pl->mg_total += b;
+            // coarse levels hold at most half the nodes of the level above:
+            // 4 vectors x R x (N/2 + N/4 + ...) < 4 R N floats
+            pl->coarse_off.push_back(pl->coarse_total);
+            pl->coarse_total += align_up((size_t)4 * R * d.n_nodes * sizeof(float)) / sizeof(float);
+        }
         pl->knn_ws = std::max(pl->knn_ws, rbffd_stencils_workspace_size(d.n_nodes, d.n));
         off += d.n_nodes;
         idx_off += d.n_nodes * d.n;
@@ -690,7 +986,7 @@ size_t layout(void* ws, const Plan& pl, BWork* w) {
     t.val = c.take<double>(pl.nnz_cap);
     t.val32 = c.take<float>(pl.nnz_cap);
     t.scan_sums = c.take<int64_t>(scan_tiles(N) + 1);
-    t.knn_ws = c.take<char>(pl.knn_ws);
+    t.knn_ws = c.take<char>(align_up(pl.knn_ws) * kSetupStreams);
     t.b = c.take<double>(NR);
     t.r64 = c.take<double>(NR);
     t.d = c.take<double>(N);
@@ -698,20 +994,229 @@ size_t layout(void* ws, const Plan& pl, BWork* w) {
     t.d32 = c.take<float>(N);
     t.dinv32 = c.take<float>(N);
     t.sig32 = c.take<float>(N);
-    float2** vv[] = {&t.xd, &t.r, &t.rh, &t.p, &t.v, &t.s, &t.t};
-    for (float2** q : vv) *q = c.take<float2>(NR);
+    if (!pl.mg) {
+        float2** vv[] = {&t.xd, &t.r, &t.rh, &t.p, &t.v, &t.s, &t.t};
+        for (float2** q : vv) *q = c.take<float2>(NR);
+    } else {
+        double** mm[] = {&t.mrh, &t.mp, &t.mv, &t.ms, &t.mt, &t.mph, &t.msh};
+        for (double** q : mm) *q = c.take<double>(NR);
+        t.f0 = c.take<float>(NR);
+        t.f1 = c.take<float>(NR);
+        t.f2 = c.take<float>(NR);
+        t.coarse = c.take<float>(pl.coarse_total);
+        t.mgws = c.take<char>(pl.mg_total);
+    }
     if (w) *w = t;
     return c.off;
 }
 
 int grid_units(int n_units) { return std::max(1, std::min(n_units, sm_count() * 8)); }
 
+// RBFFD_TRACE=1: phase times of the batched solve on stderr (host clock
+// after a stream synchronisation; diagnostics only).
+struct PhaseClock {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t0;
+    explicit PhaseClock(cudaStream_t s) : st(s) {
+        const char* v = std::getenv("RBFFD_TRACE");
+        on = v && *v && std::atoi(v) != 0;
+        t0 = std::chrono::steady_clock::now();
+    }
+    void mark(const char* what) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "[rbffd batched] %s: %.1f ms\n", what,
+                std::chrono::duration<double, std::milli>(t - t0).count());
+        t0 = t;
+    }
+};
+
+int finish_info(const Plan& pl, const BWork& w, int rounds, const std::vector<int>& inst_bad, rbffd_solve_info* info,
+                cudaStream_t st);
+
+// Multigrid mode: one hierarchy per instance (its fine level is the
+// instance's block of the batched matrix), then rounds of (explicit FP64
+// residual per pair, BiCGSTAB passes); one iteration for all instances --
+// the outer kernels and every instance's two V-cycles -- is one CUDA graph,
+// replayed while any pair is in a pass.  Returns the rounds run, or minus
+// an error status.
+int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* mask, double* u,
+             const rbffd_solve_opts* o, cudaStream_t st) {
+    const int R = pl.R;
+    const int gu = grid_units(pl.n_units);
+    PhaseClock clk(st);
+    std::vector<rbffd_mg> hs(pl.n_inst);
+    std::vector<const MgHierarchy*> H(pl.n_inst);
+    {
+        // The hierarchy setups read level sizes back to the host, so each
+        // blocks its thread: kSetupStreams host threads, each on its own
+        // stream, build disjoint sets of instances; `st` then waits for them.
+        if (cudaStreamSynchronize(st) != cudaSuccess) return -(int)RBFFD_ERR_CUDA;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::vector<int> rcs(kSetupStreams, RBFFD_OK);
+        std::vector<std::thread> th;
+        for (int t = 0; t < kSetupStreams; ++t) {
+            th.emplace_back([&, t]() {
+                cudaSetDevice(dev);
+                cudaStream_t ts;
+                if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+                    rcs[t] = RBFFD_ERR_CUDA;
+                    return;
+                }
+                for (int i = t; i < pl.n_inst && rcs[t] == RBFFD_OK; i += kSetupStreams) {
+                    const Inst& in = pl.inst[i];
+                    rcs[t] = mg_setup_core(xy + 2 * in.node_off, mask + in.node_off, in.n_nodes,
+                                           w.row_ptr + in.node_off, w.col, w.val, w.val32,
+                                           in.n_nodes * (int64_t)in.n, (int)in.node_off, 2, 0.6, &hs[i],
+                                           w.mgws + pl.mg_off[i], pl.mg_bytes[i], ts);
+                }
+                if (cudaStreamSynchronize(ts) != cudaSuccess && rcs[t] == RBFFD_OK) rcs[t] = RBFFD_ERR_CUDA;
+                cudaStreamDestroy(ts);
+            });
+        }
+        for (auto& x : th) x.join();
+        for (int t = 0; t < kSetupStreams; ++t)
+            if (rcs[t] != RBFFD_OK) return -rcs[t];
+    }
+    for (int i = 0; i < pl.n_inst; ++i) {
+        H[i] = mg_hierarchy(&hs[i]);
+        if (!H[i] || mg_multi_coarse_floats(H[i], R) * sizeof(float) >
+                         (i + 1 < pl.n_inst ? pl.coarse_off[i + 1] - pl.coarse_off[i]
+                                            : pl.coarse_total - pl.coarse_off[i]) *
+                             sizeof(float))
+            return -RBFFD_ERR_WORKSPACE;
+    }
+    clk.mark("multigrid hierarchies");
+    int vlaunch = 0;
+    auto vcycles = [&](const double* in, double* out, cudaStream_t s) -> int {
+        for (int i = 0; i < pl.n_inst; ++i) {
+            const int rc = mg_apply_multi(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
+                                          w.coarse + pl.coarse_off[i], w.inst_running + i, s, &vlaunch);
+            if (rc != RBFFD_OK) return rc;
+        }
+        return RBFFD_OK;
+    };
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // the instances' V-cycles are independent: in the graph they run as
+    // kVStreams parallel branches (forked from and joined back to the outer
+    // kernels), so the many small coarse-level kernels overlap
+    constexpr int kVStreams = 32;
+    cudaStream_t vs[kVStreams];
+    cudaEvent_t fork_ev, join_ev[kVStreams];
+    for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&vs[k], cudaStreamNonBlocking));
+    RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming));
+    auto vcycles_par = [&](const double* in, double* out, cudaStream_t s) -> int {
+        if (cudaEventRecord(fork_ev, s) != cudaSuccess) return RBFFD_ERR_CUDA;
+        for (int k = 0; k < kVStreams; ++k)
+            if (cudaStreamWaitEvent(vs[k], fork_ev, 0) != cudaSuccess) return RBFFD_ERR_CUDA;
+        for (int i = 0; i < pl.n_inst; ++i) {
+            const int rc = mg_apply_multi(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
+                                          w.coarse + pl.coarse_off[i], w.inst_running + i, vs[i % kVStreams],
+                                          &vlaunch);
+            if (rc != RBFFD_OK) return rc;
+        }
+        for (int k = 0; k < kVStreams; ++k) {
+            if (cudaEventRecord(join_ev[k], vs[k]) != cudaSuccess) return RBFFD_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, join_ev[k], 0) != cudaSuccess) return RBFFD_ERR_CUDA;
+        }
+        return RBFFD_OK;
+    };
+    (void)vcycles;
+    auto destroy_par = [&]() {
+        for (int k = 0; k < kVStreams; ++k) {
+            cudaStreamDestroy(vs[k]);
+            cudaEventDestroy(join_ev[k]);
+        }
+        cudaEventDestroy(fork_ev);
+    };
+    {
+        cudaStream_t cap;
+        RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = RBFFD_OK;
+        if (e == cudaSuccess) {
+            m_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, w.r64, w.mv, w.mp, w.pr, w.inst_running);
+            rc = vcycles_par(w.mp, w.mph, cap);
+            m_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.mph,
+                                                  w.mv, w.mrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+            m_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, w.r64, w.mv, w.ms, w.pr, w.inst_running);
+            if (rc == RBFFD_OK) rc = vcycles_par(w.ms, w.msh, cap);
+            m_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.msh,
+                                                  w.mt, w.ms, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+            m_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, w.mph, w.msh, w.ms, w.mt, w.r64,
+                                                    w.mrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part,
+                                                    o->max_iter);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        if (e == cudaSuccess && rc == RBFFD_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaStreamDestroy(cap);
+        destroy_par();
+        if (e != cudaSuccess || rc != RBFFD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) set_cuda_error(e);
+            return -(rc != RBFFD_OK ? rc : (int)RBFFD_ERR_CUDA);
+        }
+    }
+    const int per_iter = 5 + vlaunch;
+    clk.mark("iteration graph capture");
+    int rounds = 0, err = RBFFD_OK;
+    Ctl hc;
+    for (;;) {
+        if (cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st) != cudaSuccess) { err = RBFFD_ERR_CUDA; break; }
+        b_check_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.b, u, w.dinv,
+                                           w.r64, w.pr, w.inst_cnt, w.ctl, w.part, o->tol);
+        note_launches(1);
+        if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            err = RBFFD_ERR_CUDA;
+            break;
+        }
+        if (hc.active == 0 || rounds >= o->max_outer) break;
+        ++rounds;
+        m_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, w.mrh, w.mp, w.mv, w.pr, w.inst_cnt,
+                                          w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter);
+        note_launches(1);
+        for (int guard = 0; guard < 1 << 20; ++guard) {
+            if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                err = RBFFD_ERR_CUDA;
+                break;
+            }
+            if (hc.running <= 0) break;
+            if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+                err = RBFFD_ERR_CUDA;
+                break;
+            }
+            note_launches(per_iter);
+        }
+        if (err != RBFFD_OK) break;
+    }
+    clk.mark("solve");
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (err == RBFFD_OK) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            err = RBFFD_ERR_CUDA;
+        }
+    }
+    return err != RBFFD_OK ? -err : rounds;
+}
+
 }  // namespace
 }  // namespace rbffd
 
-extern "C" size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs) {
+extern "C" size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs,
+                                               const rbffd_solve_opts* opts) {
     rbffd::Plan pl;
-    if (!rbffd::make_plan(desc, n_inst, n_rhs, &pl)) return 0;
+    if (opts && opts->precond != 0 && opts->precond != 1) return 0;
+    if (!rbffd::make_plan(desc, n_inst, n_rhs, opts && opts->precond == 1, &pl)) return 0;
     return rbffd::layout(nullptr, pl, nullptr);
 }
 
@@ -721,10 +1226,11 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
                                    size_t ws_bytes, void* stream) {
     using namespace rbffd;
     Plan pl;
-    if (!xy || !is_dirichlet || !f || !g || !u || !o || !info || !make_plan(desc, n_inst, n_rhs, &pl))
+    if (!o || (o->precond != 0 && o->precond != 1)) return RBFFD_ERR_INVALID_ARG;
+    const bool use_mg = o->precond == 1;
+    if (!xy || !is_dirichlet || !f || !g || !u || !info || !make_plan(desc, n_inst, n_rhs, use_mg, &pl))
         return RBFFD_ERR_INVALID_ARG;
     if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
-    if (o->precond != 0) return RBFFD_ERR_INVALID_ARG;  // no multigrid hierarchy for the batched form
     if (!(o->tol > 0.0) || o->max_iter < 0 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0) || o->max_outer < 1)
         return RBFFD_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, pl, nullptr))
@@ -742,13 +1248,41 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     RBFFD_CUDA_TRY(cudaMemsetAsync(w.pr.iters, 0, sizeof(int) * P, st));
 
     // ---- setup: stencils and weights per instance, then one CSR -----------
-    for (int i = 0; i < pl.n_inst; ++i) {
-        const Inst& in = pl.inst[i];
-        const double* xy_i = xy + 2 * in.node_off;
-        int rc = rbffd_stencils(xy_i, in.n_nodes, in.n, w.idx + in.idx_off, w.knn_ws, pl.knn_ws, stream);
-        if (rc != RBFFD_OK) return rc;
-        rc = rbffd_weights(xy_i, w.idx + in.idx_off, in.n_nodes, in.n, in.m, w.w + in.idx_off, w.nstat + in.node_off,
-                           stream);
+    PhaseClock clk(st);
+    {
+        // independent instances: spread over streams (each with its own
+        // stencil workspace), forked from and joined back to `st`
+        cudaStream_t ss[kSetupStreams];
+        cudaEvent_t fork_ev, join_ev[kSetupStreams];
+        RBFFD_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+        for (int k = 0; k < kSetupStreams; ++k) {
+            RBFFD_CUDA_TRY(cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking));
+            RBFFD_CUDA_TRY(cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming));
+        }
+        RBFFD_CUDA_TRY(cudaEventRecord(fork_ev, st));
+        int rc = RBFFD_OK;
+        for (int k = 0; k < kSetupStreams && rc == RBFFD_OK; ++k)
+            if (cudaStreamWaitEvent(ss[k], fork_ev, 0) != cudaSuccess) rc = RBFFD_ERR_CUDA;
+        const size_t kws = align_up(pl.knn_ws);
+        for (int i = 0; i < pl.n_inst && rc == RBFFD_OK; ++i) {
+            const Inst& in = pl.inst[i];
+            const int k = i % kSetupStreams;
+            const double* xy_i = xy + 2 * in.node_off;
+            rc = rbffd_stencils(xy_i, in.n_nodes, in.n, w.idx + in.idx_off, static_cast<char*>(w.knn_ws) + k * kws,
+                                pl.knn_ws, ss[k]);
+            if (rc == RBFFD_OK)
+                rc = rbffd_weights(xy_i, w.idx + in.idx_off, in.n_nodes, in.n, in.m, w.w + in.idx_off,
+                                   w.nstat + in.node_off, ss[k]);
+        }
+        for (int k = 0; k < kSetupStreams; ++k) {
+            if (cudaEventRecord(join_ev[k], ss[k]) != cudaSuccess || cudaStreamWaitEvent(st, join_ev[k], 0) != cudaSuccess)
+                rc = RBFFD_ERR_CUDA;
+        }
+        for (int k = 0; k < kSetupStreams; ++k) {
+            cudaStreamDestroy(ss[k]);
+            cudaEventDestroy(join_ev[k]);
+        }
+        cudaEventDestroy(fork_ev);
         if (rc != RBFFD_OK) return rc;
     }
     RBFFD_CUDA_TRY(exclusive_scan<int64_t>(BRowLen{w.inst, pl.n_inst, is_dirichlet}, N, w.row_ptr, w.scan_sums,
@@ -763,6 +1297,7 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     RBFFD_LAUNCH_CHECK();
 
     // per-node weight status: any singular stencil fails the instance
+    clk.mark("stencils, weights, matrix");
     std::vector<int32_t> hstat(N);
     RBFFD_CUDA_TRY(cudaMemcpyAsync(hstat.data(), w.nstat, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
@@ -774,8 +1309,13 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
                 break;
             }
 
-    // ---- solve: rounds of (FP64 residual, inner passes, refinement) --------
     const int gu = grid_units(pl.n_units);
+    if (use_mg) {
+        const int rc = solve_mg(pl, w, xy, is_dirichlet, u, o, st);
+        return finish_info(pl, w, rc, inst_bad, info, st);
+    }
+
+    // ---- solve: rounds of (FP64 residual, inner passes, refinement) --------
     const int chunk = 16;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -844,7 +1384,19 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
 
-    // ---- per-instance summary ------------------------------------------------
+    (void)hflag;
+    return finish_info(pl, w, rounds, inst_bad, info, st);
+}
+
+namespace rbffd {
+namespace {
+// Per-instance summary: the worst right-hand side of each instance.
+int finish_info(const Plan& pl, const BWork& w, int rounds, const std::vector<int>& inst_bad, rbffd_solve_info* info,
+                cudaStream_t st) {
+    const int R = pl.R, P = pl.n_inst * pl.R;
+    if (rounds < 0) return -rounds;  // an error code from the solve
+    int rc = RBFFD_OK;
+    std::vector<int> hflag(P);
     std::vector<double> tn(P), bn(P);
     std::vector<int> it(P);
     RBFFD_CUDA_TRY(cudaMemcpyAsync(hflag.data(), w.pr.flag, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
@@ -871,3 +1423,5 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     }
     return rc;
 }
+}  // namespace
+}  // namespace rbffd

@@ -22,7 +22,53 @@ int interp_weights(const double* xy, int64_t Nd, const double* qxy, int64_t Nq, 
                    int32_t m, double* w, int32_t* node_status, cudaStream_t st);
 
 // Multigrid hierarchy built by rbffd_mg_setup (lives in the caller's rbffd_mg).
-struct MgHierarchy;
+constexpr int kMgCoarsest = 128;  // dense inverse (one-block Gauss-Jordan) at or below this size
+constexpr int kMgK = 12;          // coarse nodes per interpolation stencil
+constexpr int kMgInterpM = 2;     // interpolation degree
+constexpr int kMgCoarseN = 12;    // coarse operator: stencil size
+constexpr int kMgCoarseM = 2;     //                  and degree
+constexpr uint32_t kMgMagic = 0x4D475242u;
+
+struct MgLevel {
+    int64_t N;
+    // operator of this level (level 0: the caller's matrix)
+    const int64_t* row_ptr;
+    const int* col;
+    const double* val;
+    const float* val32;
+    int64_t nnz;
+    int tpr;
+    double* dinv;
+    float* dinv32;
+    // geometry of coarse levels (level 0: the caller's arrays)
+    const double* xy;
+    const uint8_t* mask;
+    // transfer to the next level: P (N x kMgK, ELL row-major), R (CSR)
+    int32_t* pidx;
+    double* pval;
+    float* pval32;
+    int64_t* rrow;
+    int32_t* rcol;
+    double* rval;
+    float* rval32;
+    int rtpr;
+    // vectors (x and t alternate as the current iterate)
+    double *x, *t, *r, *b;
+    float *x32, *t32, *r32, *b32;
+    // coarsest: dense inverse, row-major N x N
+    double* minv;
+    float* minv32;
+};
+
+struct MgHierarchy {
+    uint32_t magic;
+    int n_levels;
+    int nu;
+    int has32;
+    int col_base;  // level-0 column indices are offset by this (rows local)
+    double omega;
+    MgLevel lv[RBFFD_MG_MAX_LEVELS];
+};
 const MgHierarchy* mg_hierarchy(const rbffd_mg* h);
 int64_t mg_fine_rows(const MgHierarchy* h);
 bool mg_has_fp32(const MgHierarchy* h);
@@ -32,5 +78,23 @@ bool mg_has_fp32(const MgHierarchy* h);
 // events (their slots appended to ev).
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev = nullptr);
+
+// rbffd_mg_setup for a fine operator given by arrays: row_ptr points at the
+// fine rows' first entry (values are offsets into col/val), and column
+// indices are offset by col_base (a block of a larger block-diagonal matrix).
+int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_t* row_ptr, const int* col,
+                  const double* val, const float* val32, int64_t nnz, int col_base, int nu, double omega,
+                  rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// Multi-right-hand-side float32 V-cycle on node-major vectors [row][R]
+// (R <= 64): x = M^-1 b for every column.  Level 0 works on rows
+// [row_off, row_off + N) of the caller's arrays b (FP64), x (FP64 output)
+// and the float work vectors x0, t0, r0 (all with the same row numbering,
+// which the level-0 column indices, offset by the hierarchy's col_base,
+// also use); the coarse levels use `coarse` (mg_multi_coarse_floats floats).
+// Every kernel returns at once while *live == 0 (live may be NULL).
+size_t mg_multi_coarse_floats(const MgHierarchy* h, int R);
+int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b, double* x, float* x0, float* t0,
+                   float* r0, float* coarse, const int* live, cudaStream_t st, int* launches);
 
 }  // namespace rbffd

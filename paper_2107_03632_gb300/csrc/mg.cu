@@ -22,8 +22,9 @@
 //    correction vanishes on the boundary).  Restriction R = (N_c / N_f) P^T
 //    (a deterministic transpose), zero rows at coarse Dirichlet nodes.
 //  * smoothing: nu damped Jacobi sweeps x += omega D^-1 (b - A x) before
-//    and after the coarse correction; the coarsest level (<= 512 nodes) is
-//    solved with its dense inverse (Gauss-Jordan with partial pivoting).
+//    and after the coarse correction; the coarsest level (<= 128 nodes) is
+//    solved with its dense inverse (Gauss-Jordan with partial pivoting, one
+//    block).
 //
 // A V-cycle is a fixed linear map (fixed sweeps, exact coarsest solve), so
 // it can right-precondition BiCGSTAB.  It runs in FP64, or in float32 values
@@ -40,52 +41,6 @@
 
 namespace rbffd {
 
-constexpr int kMgCoarsest = 512;  // dense inverse at or below this size
-constexpr int kMgK = 12;          // coarse nodes per interpolation stencil
-constexpr int kMgInterpM = 2;     // interpolation degree
-constexpr int kMgCoarseN = 12;    // coarse operator: stencil size
-constexpr int kMgCoarseM = 2;     //                  and degree
-constexpr uint32_t kMgMagic = 0x4D475242u;
-
-struct MgLevel {
-    int64_t N;
-    // operator of this level (level 0: the caller's matrix)
-    const int64_t* row_ptr;
-    const int* col;
-    const double* val;
-    const float* val32;
-    int64_t nnz;
-    int tpr;
-    double* dinv;
-    float* dinv32;
-    // geometry of coarse levels (level 0: the caller's arrays)
-    const double* xy;
-    const uint8_t* mask;
-    // transfer to the next level: P (N x kMgK, ELL row-major), R (CSR)
-    int32_t* pidx;
-    double* pval;
-    float* pval32;
-    int64_t* rrow;
-    int32_t* rcol;
-    double* rval;
-    float* rval32;
-    int rtpr;
-    // vectors (x and t alternate as the current iterate)
-    double *x, *t, *r, *b;
-    float *x32, *t32, *r32, *b32;
-    // coarsest: dense inverse, row-major N x N
-    double* minv;
-    float* minv32;
-};
-
-struct MgHierarchy {
-    uint32_t magic;
-    int n_levels;
-    int nu;
-    int has32;
-    double omega;
-    MgLevel lv[RBFFD_MG_MAX_LEVELS];
-};
 static_assert(sizeof(MgHierarchy) <= sizeof(rbffd_mg), "rbffd_mg is too small for the hierarchy");
 
 namespace {
@@ -320,14 +275,14 @@ __global__ void __launch_bounds__(kT) mg_gather_kernel(const double2* __restrict
 // D^-1 from the diagonal of a CSR matrix (1 where the diagonal is zero or
 // missing); float copies of dinv and, if val32 != NULL, of the values.
 __global__ void __launch_bounds__(kT) mg_diag_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
-                                                     const double* __restrict__ val, int64_t N,
+                                                     const double* __restrict__ val, int64_t N, int col_base,
                                                      double* __restrict__ dinv, float* __restrict__ dinv32,
                                                      int* __restrict__ bad) {
     int nb = 0;
     MG_ELEMS(N, i) {
         double d = 0.0;
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
-            if (col[k] == (int)i) d = val[k];
+            if (col[k] - col_base == (int)i) d = val[k];
         const bool ok = d != 0.0 && isfinite(d);
         nb |= ok ? 0 : 1;
         const double iv = ok ? 1.0 / d : 1.0;
@@ -382,83 +337,89 @@ __global__ void __launch_bounds__(kT) mg_count_kernel(const int* __restrict__ st
 // Dense [A | I] (n x 2n, row-major) from CSR.
 __global__ void __launch_bounds__(kT) mg_dense_build_kernel(const int64_t* __restrict__ row_ptr,
                                                             const int* __restrict__ col,
-                                                            const double* __restrict__ val, int n,
+                                                            const double* __restrict__ val, int n, int col_base,
                                                             double* __restrict__ aug) {
     const int64_t total = (int64_t)n * 2 * n;
     MG_ELEMS(total, e) aug[e] = 0.0;
     __syncthreads();  // (single block: the zero fill precedes the scatter)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) aug[(int64_t)i * 2 * n + col[k]] += val[k];
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int c = col[k] - col_base;
+            if ((unsigned)c < (unsigned)n) aug[(int64_t)i * 2 * n + c] += val[k];
+        }
         aug[(int64_t)i * 2 * n + n + i] = 1.0;
     }
 }
 
-// Gauss-Jordan step k (one block): pivot = largest |a_ik|, i >= k (lowest i on
-// ties), swap rows k and pivot, scale row k, save the column multipliers.
-__global__ void __launch_bounds__(kT) mg_gj_pivot_kernel(double* __restrict__ aug, int n, int k,
-                                                         double* __restrict__ f, int* __restrict__ bad) {
-    __shared__ double sv[kT];
-    __shared__ int si[kT];
-    __shared__ double piv;
+// Gauss-Jordan inversion of [A | I] (n x 2n, row-major, n <= kMgCoarsest) by
+// one block: for each column k, the pivot is the largest |a_ik|, i >= k
+// (lowest i on ties); rows k and pivot are swapped, row k is scaled, and
+// column k is eliminated from every other row with multipliers saved in
+// shared memory first (the pivot row itself is not written in that phase).
+// Sets *bad on a zero pivot.
+constexpr int kGJ = 256;
+__global__ void __launch_bounds__(kGJ) mg_gj_kernel(double* __restrict__ aug, int n, int* __restrict__ bad) {
+    __shared__ double sv[kGJ];
+    __shared__ int si[kGJ];
+    __shared__ double f[kMgCoarsest];
     __shared__ int prow;
+    __shared__ double piv;
     const int n2 = 2 * n;
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        const double v = fabs(aug[(int64_t)i * n2 + k]);
-        if (v > best) {
-            best = v;
-            bi = i;
+    const int tid = threadIdx.x;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += kGJ) {
+            const double v = fabs(aug[(int64_t)i * n2 + k]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
         }
-    }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            const double ov = sv[threadIdx.x + o];
-            const int oi = si[threadIdx.x + o];
-            if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-                sv[threadIdx.x] = ov;
-                si[threadIdx.x] = oi;
+        sv[tid] = best;
+        si[tid] = bi;
+        __syncthreads();
+        for (int o = kGJ / 2; o > 0; o >>= 1) {
+            if (tid < o) {
+                const double ov = sv[tid + o];
+                const int oi = si[tid + o];
+                if (ov > sv[tid] || (ov == sv[tid] && oi < si[tid])) {
+                    sv[tid] = ov;
+                    si[tid] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            prow = si[0];
+            if (!(sv[0] > 0.0) || prow >= n) {
+                *bad = 1;
+                prow = k;
             }
         }
         __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        prow = si[0];
-        if (!(sv[0] > 0.0) || prow >= n) {
-            *bad = 1;
-            prow = k;
+        const int p = prow;
+        if (p != k)
+            for (int j = tid; j < n2; j += kGJ) {
+                const double t = aug[(int64_t)k * n2 + j];
+                aug[(int64_t)k * n2 + j] = aug[(int64_t)p * n2 + j];
+                aug[(int64_t)p * n2 + j] = t;
+            }
+        __syncthreads();
+        if (tid == 0) {
+            const double d = aug[(int64_t)k * n2 + k];
+            piv = (d != 0.0) ? 1.0 / d : 0.0;
         }
-    }
-    __syncthreads();
-    const int p = prow;
-    if (p != k)
-        for (int j = threadIdx.x; j < n2; j += blockDim.x) {
-            const double t = aug[(int64_t)k * n2 + j];
-            aug[(int64_t)k * n2 + j] = aug[(int64_t)p * n2 + j];
-            aug[(int64_t)p * n2 + j] = t;
+        __syncthreads();
+        for (int j = tid; j < n2; j += kGJ) aug[(int64_t)k * n2 + j] *= piv;
+        for (int i = tid; i < n; i += kGJ) f[i] = (i == k) ? 0.0 : aug[(int64_t)i * n2 + k];
+        __syncthreads();
+        const int64_t total = (int64_t)n * n2;
+        for (int64_t e = tid; e < total; e += kGJ) {
+            const int i = (int)(e / n2), j = (int)(e - (int64_t)i * n2);
+            if (i != k) aug[e] = fma(-f[i], aug[(int64_t)k * n2 + j], aug[e]);
         }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double d = aug[(int64_t)k * n2 + k];
-        piv = (d != 0.0) ? 1.0 / d : 0.0;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n2; j += blockDim.x) aug[(int64_t)k * n2 + j] *= piv;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : aug[(int64_t)i * n2 + k];
-}
-
-// Gauss-Jordan elimination of column k from every other row.
-__global__ void __launch_bounds__(kT) mg_gj_elim_kernel(double* __restrict__ aug, int n, int k,
-                                                        const double* __restrict__ f) {
-    const int n2 = 2 * n;
-    const int64_t total = (int64_t)n * n2;
-    MG_ELEMS(total, e) {
-        const int i = (int)(e / n2), j = (int)(e - (int64_t)i * n2);
-        if (i != k) aug[e] = fma(-f[i], aug[(int64_t)k * n2 + j], aug[e]);
+        __syncthreads();
     }
 }
 
@@ -470,6 +431,129 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
         const double v = aug[(int64_t)i * 2 * n + n + j];
         minv[e] = v;
         minv32[e] = __double2float_rn(v);
+    }
+}
+
+// ------------------------------------------------------ multi-RHS V-cycle --
+// Node-major vectors [row][R], R <= 64: a warp owns a row, lane k and k + 32
+// own right-hand sides k and k + 32, so each matrix entry is read once for
+// all of them and every gathered row is a contiguous segment.  Level-0 rows
+// are rows row_off + i of the caller's arrays.
+
+__device__ __forceinline__ bool dead(const int* live) { return live && *(volatile const int*)live == 0; }
+
+template <typename BT>
+__global__ void __launch_bounds__(kT) mr_first_kernel(int64_t N, int64_t row_off, int R, const BT* __restrict__ b,
+                                                      const float* __restrict__ dinv, float omega,
+                                                      float* __restrict__ x, const int* live) {
+    if (dead(live)) return;
+    const int64_t total = N * R;
+    MG_ELEMS(total, e) {
+        const int64_t i = e / R;
+        const int64_t g = (row_off + i) * R + (e - i * R);
+        x[g] = omega * dinv[i] * (float)b[g];
+    }
+}
+
+// xo = xi + omega D^-1 (b - A xi), or (RESID) r = b - A xi
+template <typename BT, typename OT, bool RESID>
+__global__ void __launch_bounds__(kT) mr_row_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                    const float* __restrict__ val, int64_t N, int64_t row_off, int R,
+                                                    const float* __restrict__ xi, const BT* __restrict__ b,
+                                                    const float* __restrict__ dinv, float omega, OT* __restrict__ out,
+                                                    const int* live) {
+    if (dead(live)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool on0 = lane < R, on1 = lane + 32 < R;
+    for (int64_t i = w0; i < N; i += nw) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+            const float a = __ldg(val + q);
+            const int64_t c = (int64_t)__ldg(col + q) * R;
+            if (on0) s0 = fmaf(a, __ldg(xi + c + lane), s0);
+            if (on1) s1 = fmaf(a, __ldg(xi + c + lane + 32), s1);
+        }
+        const int64_t g = (row_off + i) * R;
+        const float di = omega * dinv[i];
+        if (on0) {
+            const float r = (float)b[g + lane] - s0;
+            out[g + lane] = RESID ? (OT)r : (OT)fmaf(di, r, xi[g + lane]);
+        }
+        if (on1) {
+            const float r = (float)b[g + lane + 32] - s1;
+            out[g + lane + 32] = RESID ? (OT)r : (OT)fmaf(di, r, xi[g + lane + 32]);
+        }
+    }
+}
+
+// y = R r (CSR, n rows; r and y with their own row numbering)
+__global__ void __launch_bounds__(kT) mr_restrict_kernel(const int64_t* __restrict__ rrow, const int* __restrict__ rcol,
+                                                         const float* __restrict__ rval, int64_t n, int R,
+                                                         const float* __restrict__ r, float* __restrict__ y,
+                                                         const int* live) {
+    if (dead(live)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool on0 = lane < R, on1 = lane + 32 < R;
+    for (int64_t i = w0; i < n; i += nw) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int64_t q = rrow[i]; q < rrow[i + 1]; ++q) {
+            const float a = __ldg(rval + q);
+            const int64_t c = (int64_t)__ldg(rcol + q) * R;
+            if (on0) s0 = fmaf(a, __ldg(r + c + lane), s0);
+            if (on1) s1 = fmaf(a, __ldg(r + c + lane + 32), s1);
+        }
+        if (on0) y[i * R + lane] = s0;
+        if (on1) y[i * R + lane + 32] = s1;
+    }
+}
+
+// x += P e (ELL, kMgK per row)
+__global__ void __launch_bounds__(kT) mr_prolong_kernel(int64_t N, int R, const int32_t* __restrict__ pidx,
+                                                        const float* __restrict__ pval, const float* __restrict__ e,
+                                                        float* __restrict__ x, const int* live) {
+    if (dead(live)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool on0 = lane < R, on1 = lane + 32 < R;
+    for (int64_t i = w0; i < N; i += nw) {
+        float s0 = on0 ? x[i * R + lane] : 0.f, s1 = on1 ? x[i * R + lane + 32] : 0.f;
+#pragma unroll
+        for (int j = 0; j < kMgK; ++j) {
+            const float a = __ldg(pval + i * kMgK + j);
+            const int64_t c = (int64_t)__ldg(pidx + i * kMgK + j) * R;
+            if (on0) s0 = fmaf(a, __ldg(e + c + lane), s0);
+            if (on1) s1 = fmaf(a, __ldg(e + c + lane + 32), s1);
+        }
+        if (on0) x[i * R + lane] = s0;
+        if (on1) x[i * R + lane + 32] = s1;
+    }
+}
+
+// x = Minv b (dense n x n), rows row_off + i of b and x
+template <typename BT, typename OT>
+__global__ void __launch_bounds__(kT) mr_dense_kernel(int n, int64_t row_off, int R, const float* __restrict__ minv,
+                                                      const BT* __restrict__ b, OT* __restrict__ x, const int* live) {
+    if (dead(live)) return;
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const bool on0 = lane < R, on1 = lane + 32 < R;
+    for (int i = w0; i < n; i += nw) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int j = 0; j < n; ++j) {
+            const float a = minv[(int64_t)i * n + j];
+            const int64_t c = (row_off + j) * R;
+            if (on0) s0 = fmaf(a, (float)b[c + lane], s0);
+            if (on1) s1 = fmaf(a, (float)b[c + lane + 32], s1);
+        }
+        const int64_t g = (row_off + i) * R;
+        if (on0) x[g + lane] = (OT)s0;
+        if (on1) x[g + lane + 32] = (OT)s1;
     }
 }
 
@@ -511,7 +595,6 @@ struct MgScratch {
     void* tr_ws;
     size_t tr_bytes;
     double* aug;
-    double* gjf;
     int64_t* prow;
 };
 
@@ -547,7 +630,6 @@ size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
     t.tr_ws = c.take<char>(tr_b);
     t.tr_bytes = tr_b;
     t.aug = c.take<double>((size_t)kMgCoarsest * 2 * kMgCoarsest);
-    t.gjf = c.take<double>(kMgCoarsest);
     MgHierarchy hh{};
     for (size_t l = 0; l < nb.size(); ++l) {
         const int64_t n = nb[l];
@@ -651,15 +733,11 @@ int coarsen(const MgLevel& L, MgLevel& C, const MgScratch& s, cudaStream_t st, i
     return RBFFD_ERR_INVALID_ARG;
 }
 
-int dense_inverse(const MgLevel& L, const MgScratch& s, cudaStream_t st) {
+int dense_inverse(const MgLevel& L, int col_base, const MgScratch& s, cudaStream_t st) {
     const int n = (int)L.N;
-    mg_dense_build_kernel<<<1, kT, 0, st>>>(L.row_ptr, L.col, L.val, n, s.aug);
-    note_launches(1);
-    for (int k = 0; k < n; ++k) {
-        mg_gj_pivot_kernel<<<1, kT, 0, st>>>(s.aug, n, k, s.gjf, s.flags);
-        mg_gj_elim_kernel<<<blocks_for((int64_t)n * 2 * n), kT, 0, st>>>(s.aug, n, k, s.gjf);
-    }
-    note_launches(2 * n);
+    mg_dense_build_kernel<<<1, kT, 0, st>>>(L.row_ptr, L.col, L.val, n, col_base, s.aug);
+    mg_gj_kernel<<<1, kGJ, 0, st>>>(s.aug, n, s.flags);
+    note_launches(2);
     mg_dense_copy_kernel<<<blocks_for((int64_t)n * n), kT, 0, st>>>(s.aug, n, L.minv, L.minv32);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
@@ -804,7 +882,117 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
     return cur;
 }
 
+// Multi-RHS cycle on level l (float32).  bin: level-0 right-hand side
+// (FP64, global rows) or the level's own b; returns the level's iterate
+// (coarse levels), writes `out` (FP64) at level 0.
+float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, int64_t row_off, double* out,
+                   float* x0, float* t0, float* r0, float* coarse, int R, const int* live, cudaStream_t st,
+                   int* launches) {
+    const MgLevel& L = h.lv[l];
+    const float omega = (float)h.omega;
+    const bool top = (l == 0);
+    // coarse-level buffers: [x | t | r | b] per level, levels 1.. in order
+    auto level_base = [&](int lev) {
+        size_t off = 0;
+        for (int k = 1; k < lev; ++k) off += (size_t)4 * h.lv[k].N * R;
+        return coarse + off;
+    };
+    float* cur;
+    float* oth;
+    float* rr;
+    if (top) {
+        cur = x0;
+        oth = t0;
+        rr = r0;
+    } else {
+        float* base = level_base(l);
+        const size_t n = (size_t)L.N * R;
+        cur = base;
+        oth = base + n;
+        rr = base + 2 * n;
+    }
+    const int64_t off = top ? row_off : 0;
+    const int gw = blocks_for(L.N * 32);
+    if (l == h.n_levels - 1) {
+        if (top)
+            mr_dense_kernel<double, double><<<gw, kT, 0, st>>>((int)L.N, off, R, L.minv32,
+                                                               static_cast<const double*>(bin), out, live);
+        else
+            mr_dense_kernel<float, float><<<gw, kT, 0, st>>>((int)L.N, 0, R, L.minv32, static_cast<const float*>(bin),
+                                                             cur, live);
+        ++*launches;
+        return cur;
+    }
+    auto first = [&](float* x) {
+        if (b_double)
+            mr_first_kernel<double><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const double*>(bin),
+                                                                       L.dinv32, omega, x, live);
+        else
+            mr_first_kernel<float><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const float*>(bin),
+                                                                      L.dinv32, omega, x, live);
+        ++*launches;
+    };
+    auto sweep = [&](float* xi, float* xo, double* xo64) {
+        if (b_double) {
+            const double* b = static_cast<const double*>(bin);
+            if (xo64)
+                mr_row_kernel<double, double, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
+                                                                        L.dinv32, omega, xo64, live);
+            else
+                mr_row_kernel<double, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
+                                                                       L.dinv32, omega, xo, live);
+        } else {
+            const float* b = static_cast<const float*>(bin);
+            mr_row_kernel<float, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
+                                                                  L.dinv32, omega, xo, live);
+        }
+        ++*launches;
+    };
+    first(cur);
+    for (int k = 1; k < h.nu; ++k) {
+        sweep(cur, oth, nullptr);
+        std::swap(cur, oth);
+    }
+    if (b_double)
+        mr_row_kernel<double, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
+                                                              static_cast<const double*>(bin), L.dinv32, omega, rr,
+                                                              live);
+    else
+        mr_row_kernel<float, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
+                                                             static_cast<const float*>(bin), L.dinv32, omega, rr, live);
+    const MgLevel& C = h.lv[l + 1];
+    float* cb = level_base(l + 1) + (size_t)3 * C.N * R;
+    mr_restrict_kernel<<<blocks_for(C.N * 32), kT, 0, st>>>(L.rrow, L.rcol, L.rval32, C.N, R, rr + off * R, cb, live);
+    *launches += 2;
+    float* e = multi_level(h, l + 1, cb, false, 0, nullptr, x0, t0, r0, coarse, R, live, st, launches);
+    mr_prolong_kernel<<<gw, kT, 0, st>>>(L.N, R, L.pidx, L.pval32, e, cur + off * R, live);
+    ++*launches;
+    for (int k = 0; k < h.nu; ++k) {
+        const bool final_top = top && k == h.nu - 1;
+        sweep(cur, oth, final_top ? out : nullptr);
+        if (!final_top) std::swap(cur, oth);
+    }
+    return cur;
+}
+
 }  // namespace
+
+size_t mg_multi_coarse_floats(const MgHierarchy* h, int R) {
+    if (!h) return 0;
+    size_t t = 0;
+    for (int l = 1; l < h->n_levels; ++l) t += (size_t)4 * h->lv[l].N * R;
+    return t;
+}
+
+int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b, double* x, float* x0, float* t0,
+                   float* r0, float* coarse, const int* live, cudaStream_t st, int* launches) {
+    if (!h || !b || !x || !x0 || !t0 || !r0 || R < 1 || R > 64 || !h->has32) return RBFFD_ERR_INVALID_ARG;
+    if (h->n_levels > 1 && !coarse) return RBFFD_ERR_INVALID_ARG;
+    int n = 0;
+    multi_level(*h, 0, b, true, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
+    if (launches) *launches += n;
+    return RBFFD_OK;
+}
 
 const MgHierarchy* mg_hierarchy(const rbffd_mg* h) {
     if (!h) return nullptr;
@@ -819,7 +1007,7 @@ bool mg_has_fp32(const MgHierarchy* h) { return h && h->has32; }
 
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev) {
-    if (!h || !b || !x) return RBFFD_ERR_INVALID_ARG;
+    if (!h || !b || !x || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;
     if (fp32 && !h->has32) return RBFFD_ERR_INVALID_ARG;
     int launches = 0;
     if (fp32) cycle_level<float>(*h, 0, b, true, x, flag, st, &launches, ev);
@@ -858,12 +1046,21 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
     if (A32 && (!A32->val || A32->dtype != 1 || A32->n_rows != N || A32->nnz != A->nnz || A32->row_ptr != A->row_ptr ||
                 A32->col != A->col))
         return RBFFD_ERR_INVALID_ARG;
+    return mg_setup_core(xy, is_dirichlet, N, A->row_ptr, A->col, static_cast<const double*>(A->val),
+                         A32 ? static_cast<const float*>(A32->val) : nullptr, A->nnz, 0, nu, omega, mg, ws, ws_bytes,
+                         as_stream(stream));
+}
+
+int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t N, const int64_t* row_ptr,
+                         const int* col, const double* val, const float* val32, int64_t nnz, int col_base, int nu,
+                         double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st) {
+    using namespace rbffd;
+    std::memset(mg, 0, sizeof(*mg));
     if (nu < 1 || nu > 8 || !(omega > 0.0 && omega < 1.0)) return RBFFD_ERR_INVALID_ARG;
     if (((uintptr_t)xy & 15) != 0) return RBFFD_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
     const size_t need = mg_layout(nullptr, N, nullptr, nullptr);
     if (ws_bytes < need) return RBFFD_ERR_WORKSPACE;
-    cudaStream_t st = as_stream(stream);
 
     MgHierarchy h{};
     MgScratch s{};
@@ -871,20 +1068,22 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
     h.magic = 0;
     h.nu = nu;
     h.omega = omega;
-    h.has32 = A32 ? 1 : 0;
+    h.has32 = val32 ? 1 : 0;
+    h.col_base = col_base;
     RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
 
     MgLevel& L0 = h.lv[0];
     L0.N = N;
-    L0.row_ptr = A->row_ptr;
-    L0.col = A->col;
-    L0.val = static_cast<const double*>(A->val);
-    L0.val32 = A32 ? static_cast<const float*>(A32->val) : nullptr;
-    L0.nnz = A->nnz;
-    L0.tpr = tpr_for(N, A->nnz);
+    L0.row_ptr = row_ptr;
+    L0.col = col;
+    L0.val = val;
+    L0.val32 = val32;
+    L0.nnz = nnz;
+    L0.tpr = tpr_for(N, nnz);
     L0.xy = xy;
     L0.mask = is_dirichlet;
-    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, L0.dinv, L0.dinv32, s.flags + 1);
+    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, col_base, L0.dinv, L0.dinv32,
+                                                 s.flags + 1);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
 
@@ -894,7 +1093,7 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
         MgLevel& L = h.lv[l];
         if (L.N <= kMgCoarsest || l + 1 >= RBFFD_MG_MAX_LEVELS) {
             if (L.N > kMgCoarsest) return RBFFD_ERR_INVALID_ARG;
-            if ((rc = dense_inverse(L, s, st)) != RBFFD_OK) return rc;
+            if ((rc = dense_inverse(L, l == 0 ? col_base : 0, s, st)) != RBFFD_OK) return rc;
             levels = l + 1;
             break;
         }
@@ -918,7 +1117,7 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
             return rc;
         C.nnz = cnnz;
         C.tpr = tpr_for(nc, cnnz);
-        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, C.dinv, C.dinv32, s.flags + 1);
+        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.dinv, C.dinv32, s.flags + 1);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         // prolongation: interpolation from the kMgK nearest coarse nodes

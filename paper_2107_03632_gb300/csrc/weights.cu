@@ -352,10 +352,13 @@ __device__ __forceinline__ int group_any(int p) {
 template <int NT>
 __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v, unsigned long long* sh) {
     if (NT == 32) return v;
+    constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) sh[w] = v;
     __syncthreads();
-    const unsigned long long r = sh[0] > sh[1] ? sh[0] : sh[1];
+    unsigned long long r = sh[0];
+#pragma unroll
+    for (int k = 1; k < W; ++k) r = sh[k] > r ? sh[k] : r;
     __syncthreads();
     return r;
 }
@@ -365,6 +368,7 @@ template <int NT>
 __device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, int& bpos, unsigned long long* shb,
                                              int* shi) {
     if (NT == 32) return;
+    constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         shb[w] = best;
@@ -372,10 +376,16 @@ __device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, 
         shi[2 * w + 1] = bpos;
     }
     __syncthreads();
-    const bool second = shb[1] > shb[0] || (shb[1] == shb[0] && shi[2] < shi[0]);
-    best = second ? shb[1] : shb[0];
-    bi = second ? shi[2] : shi[0];
-    bpos = second ? shi[3] : shi[1];
+    best = shb[0];
+    bi = shi[0];
+    bpos = shi[1];
+#pragma unroll
+    for (int k = 1; k < W; ++k)
+        if (shb[k] > best || (shb[k] == best && shi[2 * k] < bi)) {
+            best = shb[k];
+            bi = shi[2 * k];
+            bpos = shi[2 * k + 1];
+        }
     __syncthreads();
 }
 
@@ -390,8 +400,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     const int lane = threadIdx.x % NT;
     const int wib = threadIdx.x / NT;
     const int wpb = blockDim.x / NT;
-    __shared__ unsigned long long red_u64[2];
-    __shared__ int red_i[4];
+    __shared__ unsigned long long red_u64[4];
+    __shared__ int red_i[8];
     const int q = n - s;
     double* Phi = reinterpret_cast<double*>(smem_raw + (size_t)wib * bytes_per_warp);
     double* P = Phi + (size_t)n * LDF;
@@ -747,8 +757,9 @@ namespace {
 // candidate, kept in a process-wide table per (device, n, m).
 struct WCfg {
     int kernel;  // 0 null-space elimination (one warp per stencil), 1 full Gaussian
-                 // elimination, 2 null-space elimination with two warps per stencil
-    int wpb;     // warps per block (kernel 2: always 2, one stencil)
+                 // elimination, 2 / 3 null-space elimination with two / four warps
+                 // per stencil
+    int wpb;     // warps per block (kernels 2, 3: 2 or 4, one stencil)
 };
 
 std::mutex g_wcfg_mu;
@@ -767,13 +778,15 @@ size_t smem_per_stencil(int kernel, int n, int m) {
 }
 
 // Stencils per block of a configuration, and its dynamic shared memory.
-int stencils_per_block(const WCfg& c) { return c.kernel == 2 ? 1 : c.wpb; }
+int stencils_per_block(const WCfg& c) { return c.kernel >= 2 ? 1 : c.wpb; }
 size_t block_smem(const WCfg& c, int n, int m) { return smem_per_stencil(c.kernel, n, m) * stencils_per_block(c); }
 
 bool cfg_valid(const WCfg& c, int n, int m) {
-    if (c.kernel < 0 || c.kernel > 2) return false;
+    if (c.kernel < 0 || c.kernel > 3) return false;
     if (c.kernel != 1 && m < 1) return false;  // null-space form needs the linear monomials
-    if (c.kernel == 2 ? c.wpb != 2 : (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
+    if (c.kernel == 2 && c.wpb != 2) return false;
+    if (c.kernel == 3 && c.wpb != 4) return false;
+    if (c.kernel <= 1 && (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
     return block_smem(c, n, m) <= 227 * 1024;
 }
 
@@ -841,8 +854,10 @@ int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t 
                                                        g.smem_doubles, w, node_status, p, (int)N, 0);
     } else if (c.kernel == 0) {
         rc = launch_ns<32>(c, p, idx, N, n, m, w, node_status, st);
-    } else {
+    } else if (c.kernel == 2) {
         rc = launch_ns<64>(c, p, idx, N, n, m, w, node_status, st);
+    } else {
+        rc = launch_ns<128>(c, p, idx, N, n, m, w, node_status, st);
     }
     if (rc != RBFFD_OK) return rc;
     note_launches(1);
@@ -879,6 +894,7 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
         for (int wpb = 1; wpb <= 4; ++wpb)
             if (cfg_valid(WCfg{kernel, wpb}, n, m)) cands.push_back(WCfg{kernel, wpb});
     if (cfg_valid(WCfg{2, 2}, n, m)) cands.push_back(WCfg{2, 2});
+    if (cfg_valid(WCfg{3, 4}, n, m)) cands.push_back(WCfg{3, 4});
     if (cands.empty()) return RBFFD_ERR_INVALID_ARG;
     cudaEvent_t e0, e1;
     RBFFD_CUDA_TRY(cudaEventCreate(&e0));

@@ -60,7 +60,7 @@ class WeightsConfig(ctypes.Structure):
     ]
 
     def as_dict(self):
-        return {"kernel": ("null-space", "gauss", "null-space-2warp")[self.kernel],
+        return {"kernel": ("null-space", "gauss", "null-space-2warp", "null-space-4warp")[self.kernel],
                 "warps_per_block": self.warps_per_block, "ms_per_mnode": self.ms_per_mnode}
 
 
@@ -151,7 +151,7 @@ SIGNATURES = {
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
-    "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32]),
+    "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32, ctypes.POINTER(SolveOpts)]),
     "rbffd_solve_batched": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _VP, _VP, _VP, _VP, _I32, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_explicit_workspace_size": (_SZ, [_I64, _I32]),
@@ -469,7 +469,8 @@ def set_weights_config(n: int, m: int, kernel: str | None = None, warps_per_bloc
     if kernel is None:
         _check(lib.rbffd_weights_set_config(int(n), int(m), None), "rbffd_weights_set_config")
         return
-    c = WeightsConfig({"null-space": 0, "gauss": 1, "null-space-2warp": 2}[kernel], int(warps_per_block), 0.0)
+    c = WeightsConfig({"null-space": 0, "gauss": 1, "null-space-2warp": 2, "null-space-4warp": 3}[kernel],
+                      int(warps_per_block), 0.0)
     _check(lib.rbffd_weights_set_config(int(n), int(m), ctypes.byref(c)), "rbffd_weights_set_config")
 
 
@@ -566,9 +567,10 @@ def batch_descs(sizes):
     return arr, off
 
 
-def batched_workspace(sizes, n_rhs: int, device) -> torch.Tensor:
+def batched_workspace(sizes, n_rhs: int, device, opts: SolveOpts | None = None) -> torch.Tensor:
     descs, _ = batch_descs(sizes)
-    nbytes = load().rbffd_batched_workspace_size(descs, len(sizes), n_rhs)
+    nbytes = load().rbffd_batched_workspace_size(descs, len(sizes), n_rhs,
+                                                 ctypes.byref(opts) if opts is not None else None)
     if nbytes == 0:
         raise RbffdError(1, "rbffd_batched_workspace_size")
     return _workspace(nbytes, device)
@@ -592,7 +594,7 @@ def rbffd_solve_batched(sizes, xy: torch.Tensor, is_dirichlet: torch.Tensor, f: 
         u = torch.zeros_like(f)
     _require(u, torch.float64, "u", (N, R))
     if ws is None:
-        ws = batched_workspace(sizes, R, xy.device)
+        ws = batched_workspace(sizes, R, xy.device, opts)
     infos = (SolveInfo * len(sizes))()
     st = lib.rbffd_solve_batched(descs, len(sizes), _ptr(xy), _ptr(is_dirichlet), _ptr(f), _ptr(g), R, _ptr(u),
                                  ctypes.byref(opts), infos, _ptr(ws), ws.numel(), _stream(xy.device))

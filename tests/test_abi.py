@@ -177,7 +177,9 @@ def test_weights_config_table(cdll):
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
     assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0
     assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(rbffd.WeightsConfig(2, 2, 0.0))) == 0
-    for bad in (rbffd.WeightsConfig(3, 1, 0.0), rbffd.WeightsConfig(2, 1, 0.0), rbffd.WeightsConfig(0, 5, 0.0),
+    assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(rbffd.WeightsConfig(3, 4, 0.0))) == 0
+    for bad in (rbffd.WeightsConfig(4, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
+                rbffd.WeightsConfig(0, 5, 0.0),
                 rbffd.WeightsConfig(0, 0, 0.0)):
         assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(bad)) == 1
     assert cdll.rbffd_weights_set_config(12, 0, ctypes.byref(rbffd.WeightsConfig(0, 1, 0.0))) == 1  # m = 0

@@ -2,6 +2,8 @@
 the oracle's direct solve of that instance (1e-8 relative max-norm at
 relative residual 1e-10), instances of uneven size and degree."""
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -30,8 +32,9 @@ def _batch(specs, n_rhs, seed):
     return sizes, np.concatenate(nodes), np.concatenate(masks), np.concatenate(fs), np.concatenate(gs)
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("n_rhs", [1, 3, 64])
-def test_batched_vs_oracle(lib, n_rhs):
+def test_batched_vs_oracle(lib, n_rhs, precond):
     from paper_2107_03632_gb300 import rbffd
 
     specs = [(0.06, 2, 12), (0.1, 6, 56), (0.07, 4, 30), (0.09, 2, 12), (0.08, 4, 30)]
@@ -39,8 +42,9 @@ def test_batched_vs_oracle(lib, n_rhs):
         specs = specs[:3]
     sizes, xy, mask, F, G = _batch(specs, n_rhs, 31)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
-    u, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G),
-                                             opts=rbffd.make_opts(precision="mixed", tol=1e-10))
+    opts = rbffd.make_opts(precision="mixed", tol=1e-10)
+    opts.precond = precond  # 1: per-instance multigrid, FP64 BiCGSTAB per pair
+    u, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G), opts=opts)
     u = u.cpu().numpy()
     assert st == 0 and all(i["status"] == 0 for i in infos)
     off = 0
@@ -62,7 +66,41 @@ def test_batched_rejects_bad_descriptors(lib):
     from paper_2107_03632_gb300 import rbffd
 
     descs, N = rbffd.batch_descs([(100, 4, 12)])  # n < s = 15
-    assert lib.rbffd_batched_workspace_size(descs, 1, 4) == 0
+    assert lib.rbffd_batched_workspace_size(descs, 1, 4, None) == 0
     descs, N = rbffd.batch_descs([(100, 2, 12)])
-    assert lib.rbffd_batched_workspace_size(descs, 1, 65) == 0
-    assert lib.rbffd_batched_workspace_size(descs, 1, 64) > 0
+    assert lib.rbffd_batched_workspace_size(descs, 1, 65, None) == 0
+    assert lib.rbffd_batched_workspace_size(descs, 1, 64, None) > 0
+    mg = rbffd.make_opts(precision="mixed")
+    mg.precond = 1
+    assert lib.rbffd_batched_workspace_size(descs, 1, 64, ctypes.byref(mg)) > 0
+
+
+def test_batched_multigrid_multilevel_vs_oracle(lib):
+    """Instances large enough for 3-4 multigrid levels each (uneven sizes
+    and degrees), several right-hand sides, against the oracle's direct
+    solves."""
+    from paper_2107_03632_gb300 import rbffd
+
+    specs = [(0.02, 6, 56), (0.03, 2, 12), (0.025, 4, 30)]
+    R = 4
+    sizes, xy, mask, F, G = _batch(specs, R, 47)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    opts = rbffd.make_opts(precision="mixed", tol=1e-10)
+    opts.precond = 1
+    u, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G), opts=opts)
+    u = u.cpu().numpy()
+    assert st == 0 and all(i["status"] == 0 for i in infos)
+    assert all(i["iters"] <= 60 for i in infos), infos
+    off = 0
+    for (N, m, n), info in zip(sizes, infos):
+        sl = slice(off, off + N)
+        idx = oracle.knn(xy[sl], n)
+        w, _ = oracle.weights(xy[sl], idx, m)
+        rp, col, val = oracle.assemble(idx, w, mask[sl])
+        for k in range(R):
+            b = oracle.rhs(F[sl, k], G[sl, k], mask[sl])
+            ref = oracle.solve_direct(rp, col, val, b)
+            err = np.abs(u[sl, k] - ref).max() / np.abs(ref).max()
+            assert err <= 1e-8, (N, m, k, err)
+        assert info["rel_residual"] <= 1e-10
+        off += N
