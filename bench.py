@@ -468,6 +468,7 @@ def run_gpu_batched(args):
     clocks.start()
     barrier()
     rbffd.rbffd_profile_read(reset=True)
+    rbffd.rbffd_profile_enable(True)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(args.steps):
@@ -476,6 +477,7 @@ def run_gpu_batched(args):
     barrier()
     clk = clocks.stop()
     prof = rbffd.rbffd_profile_read(reset=True)
+    rbffd.rbffd_profile_enable(False)
     value, ms = replica_value(dist, ws, N * R, args.steps, t0.elapsed_time(t1), dev)
 
     e2e_value = None
@@ -517,6 +519,17 @@ def run_gpu_batched(args):
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    if prof["batch_iter_launches"]:
+        it_ms = prof["batch_iter_ms"] / prof["batch_iter_launches"]
+        it_by = prof["batch_iter_bytes"] / prof["batch_iter_launches"]
+        gbs = it_by / (it_ms * 1e-3) / 1e9
+        line["roofline"] = {"kernel": "one batched multigrid iteration (graph replay: outer FP64 kernels and every "
+                                      "instance's two float32 V-cycles)", "bound": "hbm", "achieved": gbs,
+                            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_kind": peak_kind,
+                            "bytes_per_launch": it_by, "ms_per_launch": it_ms,
+                            "launches": prof["batch_iter_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

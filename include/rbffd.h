@@ -381,7 +381,11 @@ int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst, const doub
 /* With the multigrid preconditioner it also brackets the finest level's     */
 /* Jacobi sweeps of every V-cycle (mg_*): nnz * (value bytes + 4) +          */
 /* 8 (N + 1) + N * (2 x vector bytes [iterate gathered once, result] +      */
-/* right-hand-side bytes + value bytes [D^-1]).                              */
+/* right-hand-side bytes + value bytes [D^-1]).  The batched multigrid     */
+/* solve brackets each iteration (one graph replay for all instances) with  */
+/* its algorithmic bytes for all pairs: 168 B per (node, rhs) for the outer */
+/* FP64 kernels + 2 x 12 nnz (FP64 matrix, once per rhs block) and, per     */
+/* V-cycle, 118 B per (node, rhs) + 4 passes x 8 nnz on the finest level.   */
 /* Profiling is process-wide, off by default, and meant for one thread and   */
 /* one device.  rbffd_profile_read waits for bracketed launches to finish.   */
 /* ------------------------------------------------------------------------ */
@@ -396,6 +400,9 @@ typedef struct rbffd_profile {
     int64_t mg_launches;      /* timed finest-level V-cycle sweeps */
     double mg_ms;
     int64_t mg_bytes;
+    int64_t batch_iter_launches;  /* timed iterations (graph replays) of the batched multigrid solve */
+    double batch_iter_ms;
+    int64_t batch_iter_bytes;
 } rbffd_profile;
 
 /* Diagnostics (no counterpart in the paper): evaluates on the device, for   */

@@ -141,6 +141,9 @@ int rbffd_profile_read(rbffd_profile* out, int reset) {
     out->mg_launches = g_prof_launches[kProfMg];
     out->mg_ms = g_prof_ms[kProfMg];
     out->mg_bytes = g_prof_bytes[kProfMg];
+    out->batch_iter_launches = g_prof_launches[kProfBatchIter];
+    out->batch_iter_ms = g_prof_ms[kProfBatchIter];
+    out->batch_iter_bytes = g_prof_bytes[kProfBatchIter];
     if (reset) {
         g_launches.store(0);
         for (int k = 0; k < kProfKinds; ++k) {

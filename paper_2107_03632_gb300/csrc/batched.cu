@@ -1163,6 +1163,13 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         }
     }
     const int per_iter = 5 + vlaunch;
+    // algorithmic bytes of one iteration with every pair running (see the
+    // profiling hooks in rbffd.h)
+    int64_t nnz = 0;
+    if (cudaMemcpyAsync(&nnz, w.row_ptr + pl.N, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return -(int)RBFFD_ERR_CUDA;
+    const int64_t iter_bytes = (int64_t)(168 + 2 * 118) * pl.N * R + 2 * 12 * nnz + 2 * 4 * 8 * nnz;
     clk.mark("iteration graph capture");
     int rounds = 0, err = RBFFD_OK;
     Ctl hc;
@@ -1188,10 +1195,13 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
                 break;
             }
             if (hc.running <= 0) break;
+            const int ev = prof_begin(st);
             if (cudaGraphLaunch(exec, st) != cudaSuccess) {
                 err = RBFFD_ERR_CUDA;
                 break;
             }
+            // bytes in proportion to the pairs still in a pass
+            prof_end(ev, st, kProfBatchIter, (int64_t)((double)iter_bytes * hc.running / (pl.n_inst * (double)R)));
             note_launches(per_iter);
         }
         if (err != RBFFD_OK) break;

@@ -55,7 +55,7 @@ int sm_count();
 // Launch accounting and optional kernel timing (rbffd_profile_*).
 void note_launches(int count);
 bool profiling();
-enum ProfKind { kProfSpmv64 = 0, kProfSpmv32 = 1, kProfMg = 2, kProfKinds = 3 };
+enum ProfKind { kProfSpmv64 = 0, kProfSpmv32 = 1, kProfMg = 2, kProfBatchIter = 3, kProfKinds = 4 };
 // Brackets one launch with events when profiling is on: call prof_begin
 // before and prof_end after the launch (both on stream `st`).
 int prof_begin(cudaStream_t st);

@@ -111,6 +111,9 @@ class Profile(ctypes.Structure):
         ("mg_launches", ctypes.c_int64),
         ("mg_ms", ctypes.c_double),
         ("mg_bytes", ctypes.c_int64),
+        ("batch_iter_launches", ctypes.c_int64),
+        ("batch_iter_ms", ctypes.c_double),
+        ("batch_iter_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):
