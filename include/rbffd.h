@@ -340,11 +340,13 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
 /* replayed as one CUDA graph per chunk of iterations.  With                */
 /* opts->precond = 1 (opts->mg is not used) each instance gets its own      */
 /* multigrid hierarchy (as rbffd_mg_setup, V(2,2), omega 0.6) and every     */
-/* pair runs FP64 BiCGSTAB right-preconditioned by the instance's float32   */
-/* V-cycle, applied to all of its right-hand sides at once; one iteration  */
-/* for all instances is one CUDA graph.  Either way each pair has its own   */
-/* BiCGSTAB scalars and stops on its own relative residual (explicit FP64  */
-/* residual, tol).  Blocks the host like rbffd_solve.                       */
+/* pair runs BiCGSTAB right-preconditioned by the instance's float32        */
+/* V-cycle, applied to all of its right-hand sides at once, with            */
+/* double-float (2 x float32) Krylov vectors and the matrix read as float32 */
+/* (leading, trailing) pairs, the solution kept in FP64; one iteration for  */
+/* all instances is one CUDA graph.  Either way each pair has its own       */
+/* BiCGSTAB scalars and stops on its own relative residual (explicit FP64   */
+/* residual with the FP64 matrix, tol).  Blocks the host like rbffd_solve.  */
 /*   desc    : host array of n_inst descriptors (offsets contiguous, in      */
 /*             order: node_offset_0 = 0, node_offset_{i+1} = node_offset_i + */
 /*             n_nodes_i).                                                  */

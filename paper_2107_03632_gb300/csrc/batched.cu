@@ -109,7 +109,9 @@ struct BWork {
     // multigrid mode: FP64 Krylov vectors (r is r64), the preconditioned
     // directions, the float V-cycle's level-0 work vectors, the coarse-level
     // vectors and the per-instance hierarchies' workspaces
-    double *mrh, *mp, *mv, *ms, *mt, *mph, *msh;
+    double *mrh, *mp, *mv, *ms, *mt, *mph, *msh;  // used as float2 (double-float) vectors
+    float2* mr;                                   // double-float residual
+    float* val_lo;                                // val - val32, as float (val32 holds the leading part)
     float *f0, *f1, *f2;
     float* coarse;
     char* mgws;
@@ -637,18 +639,32 @@ __global__ void __launch_bounds__(kBT) b_refine_kernel(const Unit* __restrict__ 
 }
 
 // ------------------------------------------------------ multigrid mode -----
-// FP64 BiCGSTAB for every (instance, rhs) pair, right-preconditioned by the
-// instance's float32 V-cycle (applied to all of its right-hand sides at
-// once): the FP64 matrix, vectors and scalars decide convergence, the float
-// V-cycle only shapes the search directions.  Passes start from the
-// explicit residual of b_check (r = r64, rh = r, p = v = 0).
+// Every (instance, rhs) pair runs BiCGSTAB right-preconditioned by its
+// instance's float32 V-cycle (applied to all of the instance's right-hand
+// sides at once); passes start from the explicit FP64 residual of b_check
+// (r = r64, rh = r, p = v = 0).
 
-__global__ void __launch_bounds__(kBT) m_load_kernel(const Unit* __restrict__ units, int n_units,
-                                                     const Inst* __restrict__ inst, int R,
-                                                     const double* __restrict__ r64, double* __restrict__ rh,
-                                                     double* __restrict__ p, double* __restrict__ v, Pairs pr,
-                                                     unsigned* inst_cnt, int* inst_running, Ctl* ctl, double* part,
-                                                     double inner_tol, int max_iter) {
+// ---- double-float outer solve (multigrid mode) ----------------------------
+// The outer BiCGSTAB of the multigrid mode keeps its vectors as double-float
+// pairs and reads the matrix as (val32, val_lo) float pairs, so the 64-rhs
+// SpMM runs on the FP32 pipe (one FP64 multiply-add per matrix entry and rhs
+// would make it FP64-bound on this chip) at ~1e-14 relative accuracy; the
+// solution x stays FP64 and the explicit FP64 residual of b_check decides
+// convergence.
+
+__global__ void __launch_bounds__(kBT) md_split_kernel(const double* __restrict__ val, const float* __restrict__ hi,
+                                                       int64_t nnz, float* __restrict__ lo) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        lo[k] = __double2float_rn(val[k] - (double)hi[k]);
+}
+
+__global__ void __launch_bounds__(kBT) md_load_kernel(const Unit* __restrict__ units, int n_units,
+                                                      const Inst* __restrict__ inst, int R,
+                                                      const double* __restrict__ r64, float2* __restrict__ rr,
+                                                      float2* __restrict__ rh, float2* __restrict__ p,
+                                                      float2* __restrict__ v, Pairs pr, unsigned* inst_cnt,
+                                                      int* inst_running, Ctl* ctl, double* part, double inner_tol,
+                                                      int max_iter) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k0 = lane, k1 = lane + 32;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -659,25 +675,26 @@ __global__ void __launch_bounds__(kBT) m_load_kernel(const Unit* __restrict__ un
         if (!any) continue;
         const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kPassEnd;
         const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kPassEnd;
-        double a0[1] = {0.0}, a1[1] = {0.0};
+        DfAcc c0, c1;
         for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
             if (on0) {
                 const int64_t e = row * R + k0;
-                const double ri = r64[e];
-                rh[e] = ri;
-                p[e] = 0.0;
-                v[e] = 0.0;
-                a0[0] = fma(ri, ri, a0[0]);
+                const df ri = df_from_double(r64[e]);
+                df_store(rr + e, ri);
+                df_store(rh + e, ri);
+                p[e] = v[e] = make_float2(0.f, 0.f);
+                c0.add(df_mul(ri, ri));
             }
             if (on1) {
                 const int64_t e = row * R + k1;
-                const double ri = r64[e];
-                rh[e] = ri;
-                p[e] = 0.0;
-                v[e] = 0.0;
-                a1[0] = fma(ri, ri, a1[0]);
+                const df ri = df_from_double(r64[e]);
+                df_store(rr + e, ri);
+                df_store(rh + e, ri);
+                p[e] = v[e] = make_float2(0.f, 0.f);
+                c1.add(df_mul(ri, ri));
             }
         }
+        double a0[1] = {df_to_double(c0.value())}, a1[1] = {df_to_double(c1.value())};
         unit_store<1>(a0, a1, part, n_units, R, u);
         if (last_unit(&inst_cnt[un.inst], in.n_units)) {
             int running = 0;
@@ -711,10 +728,10 @@ __global__ void __launch_bounds__(kBT) m_load_kernel(const Unit* __restrict__ un
     }
 }
 
-__global__ void __launch_bounds__(kBT) m_update_p_kernel(const Unit* __restrict__ units, int n_units, int R,
-                                                         const double* __restrict__ rr, const double* __restrict__ v,
-                                                         double* __restrict__ p, Pairs pr,
-                                                         const int* __restrict__ inst_running) {
+__global__ void __launch_bounds__(kBT) md_update_p_kernel(const Unit* __restrict__ units, int n_units, int R,
+                                                          const float2* __restrict__ rr, const float2* __restrict__ v,
+                                                          float2* __restrict__ p, Pairs pr,
+                                                          const int* __restrict__ inst_running) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
@@ -725,26 +742,29 @@ __global__ void __launch_bounds__(kBT) m_update_p_kernel(const Unit* __restrict_
             if (k >= R) continue;
             const int pi = un.inst * R + k;
             if (pr.flag[pi] != kRun) continue;
-            const double beta = (pr.rho_new[pi] / pr.rho[pi]) * (pr.alpha[pi] / pr.omega[pi]);
-            const double om = pr.omega[pi];
+            const df beta = df_from_double((pr.rho_new[pi] / pr.rho[pi]) * (pr.alpha[pi] / pr.omega[pi]));
+            const df nom = df_from_double(-pr.omega[pi]);
             for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
                 const int64_t e = row * R + k;
-                p[e] = fma(beta, fma(-om, v[e], p[e]), rr[e]);
+                const df t = df_fma(nom, df_load(v + e), df_load(p + e));
+                df_store(p + e, df_fma(beta, t, df_load(rr + e)));
             }
         }
     }
 }
 
-// y = A xin (FP64); MODE 0: (rh, y) -> alpha; MODE 1: (y, s), (y, y) -> omega.
+// y = A xin with A as (hi, lo) float pairs; MODE 0: (rh, y) -> alpha;
+// MODE 1: (y, s), (y, y) -> omega.
 template <int MODE>
-__global__ void __launch_bounds__(kBT) m_spmm_kernel(const Unit* __restrict__ units, int n_units,
-                                                     const Inst* __restrict__ inst,
-                                                     const int64_t* __restrict__ row_ptr,
-                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
-                                                     int R, const double* __restrict__ xin, double* __restrict__ y,
-                                                     const double* __restrict__ dotv, Pairs pr,
-                                                     int* __restrict__ inst_running, unsigned* inst_cnt, Ctl* ctl,
-                                                     double* part) {
+__global__ void __launch_bounds__(kBT) md_spmm_kernel(const Unit* __restrict__ units, int n_units,
+                                                      const Inst* __restrict__ inst,
+                                                      const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ vhi,
+                                                      const float* __restrict__ vlo, int R,
+                                                      const float2* __restrict__ xin, float2* __restrict__ y,
+                                                      const float2* __restrict__ dotv, Pairs pr,
+                                                      int* __restrict__ inst_running, unsigned* inst_cnt, Ctl* ctl,
+                                                      double* part) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k0 = lane, k1 = lane + 32;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -753,35 +773,49 @@ __global__ void __launch_bounds__(kBT) m_spmm_kernel(const Unit* __restrict__ un
         const Inst in = inst[un.inst];
         const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kRun;
         const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kRun;
-        double a0[2] = {0.0, 0.0}, a1[2] = {0.0, 0.0};
+        DfAcc c0a, c0b, c1a, c1b;
         for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
             const int64_t lo = row_ptr[row], hi = row_ptr[row + 1];
-            double s0 = 0.0, s1 = 0.0;
+            DfAcc s0, s1;
             for (int64_t q = lo; q < hi; ++q) {
-                const double a = __ldg(val + q);
+                const float ah = __ldg(vhi + q), al = __ldg(vlo + q);
                 const int64_t c = (int64_t)__ldg(col + q) * R;
-                if (on0) s0 = fma(a, xin[c + k0], s0);
-                if (on1) s1 = fma(a, xin[c + k1], s1);
+                if (on0) {
+                    const df xj = df_load(xin + c + k0);
+                    df pp = two_prod(ah, xj.hi);
+                    pp.lo = __fmaf_rn(ah, xj.lo, __fmaf_rn(al, xj.hi, pp.lo));
+                    s0.add(pp);
+                }
+                if (on1) {
+                    const df xj = df_load(xin + c + k1);
+                    df pp = two_prod(ah, xj.hi);
+                    pp.lo = __fmaf_rn(ah, xj.lo, __fmaf_rn(al, xj.hi, pp.lo));
+                    s1.add(pp);
+                }
             }
             if (on0) {
                 const int64_t e = row * R + k0;
-                y[e] = s0;
-                if (MODE == 0) a0[0] = fma(dotv[e], s0, a0[0]);
+                const df yv = s0.value();
+                df_store(y + e, yv);
+                if (MODE == 0) c0a.add(df_mul(df_load(dotv + e), yv));
                 else {
-                    a0[0] = fma(s0, dotv[e], a0[0]);
-                    a0[1] = fma(s0, s0, a0[1]);
+                    c0a.add(df_mul(yv, df_load(dotv + e)));
+                    c0b.add(df_mul(yv, yv));
                 }
             }
             if (on1) {
                 const int64_t e = row * R + k1;
-                y[e] = s1;
-                if (MODE == 0) a1[0] = fma(dotv[e], s1, a1[0]);
+                const df yv = s1.value();
+                df_store(y + e, yv);
+                if (MODE == 0) c1a.add(df_mul(df_load(dotv + e), yv));
                 else {
-                    a1[0] = fma(s1, dotv[e], a1[0]);
-                    a1[1] = fma(s1, s1, a1[1]);
+                    c1a.add(df_mul(yv, df_load(dotv + e)));
+                    c1b.add(df_mul(yv, yv));
                 }
             }
         }
+        double a0[2] = {df_to_double(c0a.value()), df_to_double(c0b.value())};
+        double a1[2] = {df_to_double(c1a.value()), df_to_double(c1b.value())};
         unit_store<2>(a0, a1, part, n_units, R, u);
         if (last_unit(&inst_cnt[un.inst], in.n_units)) {
             int ended = 0;
@@ -812,10 +846,10 @@ __global__ void __launch_bounds__(kBT) m_spmm_kernel(const Unit* __restrict__ un
     }
 }
 
-__global__ void __launch_bounds__(kBT) m_update_s_kernel(const Unit* __restrict__ units, int n_units, int R,
-                                                         const double* __restrict__ rr, const double* __restrict__ v,
-                                                         double* __restrict__ s, Pairs pr,
-                                                         const int* __restrict__ inst_running) {
+__global__ void __launch_bounds__(kBT) md_update_s_kernel(const Unit* __restrict__ units, int n_units, int R,
+                                                          const float2* __restrict__ rr, const float2* __restrict__ v,
+                                                          float2* __restrict__ s, Pairs pr,
+                                                          const int* __restrict__ inst_running) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
@@ -826,24 +860,24 @@ __global__ void __launch_bounds__(kBT) m_update_s_kernel(const Unit* __restrict_
             if (k >= R) continue;
             const int pi = un.inst * R + k;
             if (pr.flag[pi] != kRun) continue;
-            const double al = pr.alpha[pi];
+            const df na = df_from_double(-pr.alpha[pi]);
             for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
                 const int64_t e = row * R + k;
-                s[e] = fma(-al, v[e], rr[e]);
+                df_store(s + e, df_fma(na, df_load(v + e), df_load(rr + e)));
             }
         }
     }
 }
 
-// x += alpha ph + omega sh, r = s - omega t; pass end on convergence of the
-// recurrence (inner_tol of the pass start), breakdown, growth, caps.
-__global__ void __launch_bounds__(kBT) m_update_xr_kernel(const Unit* __restrict__ units, int n_units,
-                                                          const Inst* __restrict__ inst, int R, double* __restrict__ x,
-                                                          const double* __restrict__ ph, const double* __restrict__ sh,
-                                                          const double* __restrict__ s, const double* __restrict__ t,
-                                                          double* __restrict__ rr, const double* __restrict__ rh,
-                                                          Pairs pr, int* __restrict__ inst_running, unsigned* inst_cnt,
-                                                          Ctl* ctl, double* part, int max_iter) {
+// x (FP64) += alpha ph + omega sh, r = s - omega t (double-float).
+__global__ void __launch_bounds__(kBT) md_update_xr_kernel(const Unit* __restrict__ units, int n_units,
+                                                           const Inst* __restrict__ inst, int R,
+                                                           double* __restrict__ x, const float2* __restrict__ ph,
+                                                           const float2* __restrict__ sh, const float2* __restrict__ s,
+                                                           const float2* __restrict__ t, float2* __restrict__ rr,
+                                                           const float2* __restrict__ rh, Pairs pr,
+                                                           int* __restrict__ inst_running, unsigned* inst_cnt,
+                                                           Ctl* ctl, double* part, int max_iter) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
@@ -857,14 +891,19 @@ __global__ void __launch_bounds__(kBT) m_update_xr_kernel(const Unit* __restrict
             const int pi = un.inst * R + k;
             if (pr.flag[pi] != kRun) continue;
             const double al = pr.alpha[pi], om = pr.omega[pi];
+            const df nom = df_from_double(-om);
+            DfAcc c0, c1;
             for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
                 const int64_t e = row * R + k;
-                x[e] = fma(om, sh[e], fma(al, ph[e], x[e]));
-                const double ri = fma(-om, t[e], s[e]);
-                rr[e] = ri;
-                a[h][0] = fma(ri, ri, a[h][0]);
-                a[h][1] = fma(rh[e], ri, a[h][1]);
+                const float2 pv = ph[e], sv = sh[e];
+                x[e] = fma(om, (double)sv.x + (double)sv.y, fma(al, (double)pv.x + (double)pv.y, x[e]));
+                const df ri = df_fma(nom, df_load(t + e), df_load(s + e));
+                df_store(rr + e, ri);
+                c0.add(df_mul(ri, ri));
+                c1.add(df_mul(df_load(rh + e), ri));
             }
+            a[h][0] = df_to_double(c0.value());
+            a[h][1] = df_to_double(c1.value());
         }
         unit_store<2>(a[0], a[1], part, n_units, R, u);
         if (last_unit(&inst_cnt[un.inst], in.n_units)) {
@@ -1000,6 +1039,8 @@ size_t layout(void* ws, const Plan& pl, BWork* w) {
     } else {
         double** mm[] = {&t.mrh, &t.mp, &t.mv, &t.ms, &t.mt, &t.mph, &t.msh};
         for (double** q : mm) *q = c.take<double>(NR);
+        t.mr = c.take<float2>(NR);
+        t.val_lo = c.take<float>(pl.nnz_cap);
         t.f0 = c.take<float>(NR);
         t.f1 = c.take<float>(NR);
         t.f2 = c.take<float>(NR);
@@ -1091,14 +1132,15 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
     }
     clk.mark("multigrid hierarchies");
     int vlaunch = 0;
-    auto vcycles = [&](const double* in, double* out, cudaStream_t s) -> int {
-        for (int i = 0; i < pl.n_inst; ++i) {
-            const int rc = mg_apply_multi(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
-                                          w.coarse + pl.coarse_off[i], w.inst_running + i, s, &vlaunch);
-            if (rc != RBFFD_OK) return rc;
-        }
-        return RBFFD_OK;
-    };
+    // double-float views of the outer vectors
+    float2* vr = w.mr;
+    float2* vrh = reinterpret_cast<float2*>(w.mrh);
+    float2* vp = reinterpret_cast<float2*>(w.mp);
+    float2* vv = reinterpret_cast<float2*>(w.mv);
+    float2* vsv = reinterpret_cast<float2*>(w.ms);
+    float2* vt = reinterpret_cast<float2*>(w.mt);
+    float2* vph = reinterpret_cast<float2*>(w.mph);
+    float2* vsh = reinterpret_cast<float2*>(w.msh);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // the instances' V-cycles are independent: in the graph they run as
@@ -1110,14 +1152,14 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
     for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&vs[k], cudaStreamNonBlocking));
     RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
     for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming));
-    auto vcycles_par = [&](const double* in, double* out, cudaStream_t s) -> int {
+    auto vcycles_par = [&](const float2* in, float2* out, cudaStream_t s) -> int {
         if (cudaEventRecord(fork_ev, s) != cudaSuccess) return RBFFD_ERR_CUDA;
         for (int k = 0; k < kVStreams; ++k)
             if (cudaStreamWaitEvent(vs[k], fork_ev, 0) != cudaSuccess) return RBFFD_ERR_CUDA;
         for (int i = 0; i < pl.n_inst; ++i) {
-            const int rc = mg_apply_multi(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
-                                          w.coarse + pl.coarse_off[i], w.inst_running + i, vs[i % kVStreams],
-                                          &vlaunch);
+            const int rc = mg_apply_multi_df(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
+                                             w.coarse + pl.coarse_off[i], w.inst_running + i, vs[i % kVStreams],
+                                             &vlaunch);
             if (rc != RBFFD_OK) return rc;
         }
         for (int k = 0; k < kVStreams; ++k) {
@@ -1126,7 +1168,6 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         }
         return RBFFD_OK;
     };
-    (void)vcycles;
     auto destroy_par = [&]() {
         for (int k = 0; k < kVStreams; ++k) {
             cudaStreamDestroy(vs[k]);
@@ -1140,17 +1181,16 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int rc = RBFFD_OK;
         if (e == cudaSuccess) {
-            m_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, w.r64, w.mv, w.mp, w.pr, w.inst_running);
-            rc = vcycles_par(w.mp, w.mph, cap);
-            m_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.mph,
-                                                  w.mv, w.mrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
-            m_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, w.r64, w.mv, w.ms, w.pr, w.inst_running);
-            if (rc == RBFFD_OK) rc = vcycles_par(w.ms, w.msh, cap);
-            m_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.msh,
-                                                  w.mt, w.ms, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
-            m_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, w.mph, w.msh, w.ms, w.mt, w.r64,
-                                                    w.mrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part,
-                                                    o->max_iter);
+            md_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vp, w.pr, w.inst_running);
+            rc = vcycles_par(vp, vph, cap);
+            md_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
+                                                   R, vph, vv, vrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+            md_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vsv, w.pr, w.inst_running);
+            if (rc == RBFFD_OK) rc = vcycles_par(vsv, vsh, cap);
+            md_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
+                                                   R, vsh, vt, vsv, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+            md_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, vph, vsh, vsv, vt, vr, vrh,
+                                                     w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part, o->max_iter);
             e = cudaStreamEndCapture(cap, &graph);
         }
         if (e == cudaSuccess && rc == RBFFD_OK) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1170,6 +1210,10 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         cudaStreamSynchronize(st) != cudaSuccess)
         return -(int)RBFFD_ERR_CUDA;
     const int64_t iter_bytes = (int64_t)(168 + 2 * 118) * pl.N * R + 2 * 12 * nnz + 2 * 4 * 8 * nnz;
+    // the matrix's trailing float parts for the double-float SpMM
+    md_split_kernel<<<std::max(1, std::min((int)((nnz + kBT - 1) / kBT), sm_count() * 16)), kBT, 0, st>>>(
+        w.val, w.val32, nnz, w.val_lo);
+    note_launches(1);
     clk.mark("iteration graph capture");
     int rounds = 0, err = RBFFD_OK;
     Ctl hc;
@@ -1185,8 +1229,8 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         }
         if (hc.active == 0 || rounds >= o->max_outer) break;
         ++rounds;
-        m_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, w.mrh, w.mp, w.mv, w.pr, w.inst_cnt,
-                                          w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter);
+        md_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, vr, vrh, vp, vv, w.pr, w.inst_cnt,
+                                           w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter);
         note_launches(1);
         for (int guard = 0; guard < 1 << 20; ++guard) {
             if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

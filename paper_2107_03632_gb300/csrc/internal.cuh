@@ -96,5 +96,9 @@ int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_
 size_t mg_multi_coarse_floats(const MgHierarchy* h, int R);
 int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b, double* x, float* x0, float* t0,
                    float* r0, float* coarse, const int* live, cudaStream_t st, int* launches);
+// The same with double-float (float2: leading, trailing) right-hand sides
+// and results (the result's trailing part is zero).
+int mg_apply_multi_df(const MgHierarchy* h, int64_t row_off, int R, const float2* b, float2* x, float* x0, float* t0,
+                      float* r0, float* coarse, const int* live, cudaStream_t st, int* launches);
 
 }  // namespace rbffd

@@ -442,6 +442,27 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
 
 __device__ __forceinline__ bool dead(const int* live) { return live && *(volatile const int*)live == 0; }
 
+// Level-0 right-hand sides come as FP64 or as double-float pairs (the
+// leading float suffices for a preconditioner); the level-0 result goes out
+// as FP64 or as a pair with a zero low part.
+__device__ __forceinline__ float to_f(double v) { return (float)v; }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(float2 v) { return v.x; }
+template <typename OT>
+__device__ __forceinline__ OT from_f(float v);
+template <>
+__device__ __forceinline__ double from_f<double>(float v) {
+    return (double)v;
+}
+template <>
+__device__ __forceinline__ float from_f<float>(float v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 from_f<float2>(float v) {
+    return make_float2(v, 0.f);
+}
+
 template <typename BT>
 __global__ void __launch_bounds__(kT) mr_first_kernel(int64_t N, int64_t row_off, int R, const BT* __restrict__ b,
                                                       const float* __restrict__ dinv, float omega,
@@ -451,7 +472,7 @@ __global__ void __launch_bounds__(kT) mr_first_kernel(int64_t N, int64_t row_off
     MG_ELEMS(total, e) {
         const int64_t i = e / R;
         const int64_t g = (row_off + i) * R + (e - i * R);
-        x[g] = omega * dinv[i] * (float)b[g];
+        x[g] = omega * dinv[i] * to_f(b[g]);
     }
 }
 
@@ -478,12 +499,12 @@ __global__ void __launch_bounds__(kT) mr_row_kernel(const int64_t* __restrict__ 
         const int64_t g = (row_off + i) * R;
         const float di = omega * dinv[i];
         if (on0) {
-            const float r = (float)b[g + lane] - s0;
-            out[g + lane] = RESID ? (OT)r : (OT)fmaf(di, r, xi[g + lane]);
+            const float r = to_f(b[g + lane]) - s0;
+            out[g + lane] = from_f<OT>(RESID ? r : fmaf(di, r, xi[g + lane]));
         }
         if (on1) {
-            const float r = (float)b[g + lane + 32] - s1;
-            out[g + lane + 32] = RESID ? (OT)r : (OT)fmaf(di, r, xi[g + lane + 32]);
+            const float r = to_f(b[g + lane + 32]) - s1;
+            out[g + lane + 32] = from_f<OT>(RESID ? r : fmaf(di, r, xi[g + lane + 32]));
         }
     }
 }
@@ -548,12 +569,12 @@ __global__ void __launch_bounds__(kT) mr_dense_kernel(int n, int64_t row_off, in
         for (int j = 0; j < n; ++j) {
             const float a = minv[(int64_t)i * n + j];
             const int64_t c = (row_off + j) * R;
-            if (on0) s0 = fmaf(a, (float)b[c + lane], s0);
-            if (on1) s1 = fmaf(a, (float)b[c + lane + 32], s1);
+            if (on0) s0 = fmaf(a, to_f(b[c + lane]), s0);
+            if (on1) s1 = fmaf(a, to_f(b[c + lane + 32]), s1);
         }
         const int64_t g = (row_off + i) * R;
-        if (on0) x[g + lane] = (OT)s0;
-        if (on1) x[g + lane + 32] = (OT)s1;
+        if (on0) x[g + lane] = from_f<OT>(s0);
+        if (on1) x[g + lane + 32] = from_f<OT>(s1);
     }
 }
 
@@ -882,12 +903,13 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
     return cur;
 }
 
-// Multi-RHS cycle on level l (float32).  bin: level-0 right-hand side
-// (FP64, global rows) or the level's own b; returns the level's iterate
-// (coarse levels), writes `out` (FP64) at level 0.
-float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, int64_t row_off, double* out,
-                   float* x0, float* t0, float* r0, float* coarse, int R, const int* live, cudaStream_t st,
-                   int* launches) {
+// Multi-RHS cycle on level l (float32).  Level 0 reads B0 (FP64 or
+// double-float) right-hand sides on global rows and writes O0 output;
+// coarse levels use their own float vectors.  Returns the level's iterate
+// (coarse levels).
+template <typename B0, typename O0>
+float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off, O0* out, float* x0, float* t0,
+                   float* r0, float* coarse, int R, const int* live, cudaStream_t st, int* launches) {
     const MgLevel& L = h.lv[l];
     const float omega = (float)h.omega;
     const bool top = (l == 0);
@@ -915,8 +937,8 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, 
     const int gw = blocks_for(L.N * 32);
     if (l == h.n_levels - 1) {
         if (top)
-            mr_dense_kernel<double, double><<<gw, kT, 0, st>>>((int)L.N, off, R, L.minv32,
-                                                               static_cast<const double*>(bin), out, live);
+            mr_dense_kernel<B0, O0><<<gw, kT, 0, st>>>((int)L.N, off, R, L.minv32, static_cast<const B0*>(bin), out,
+                                                       live);
         else
             mr_dense_kernel<float, float><<<gw, kT, 0, st>>>((int)L.N, 0, R, L.minv32, static_cast<const float*>(bin),
                                                              cur, live);
@@ -924,23 +946,23 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, 
         return cur;
     }
     auto first = [&](float* x) {
-        if (b_double)
-            mr_first_kernel<double><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const double*>(bin),
-                                                                       L.dinv32, omega, x, live);
+        if (top)
+            mr_first_kernel<B0><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const B0*>(bin),
+                                                                   L.dinv32, omega, x, live);
         else
             mr_first_kernel<float><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const float*>(bin),
                                                                       L.dinv32, omega, x, live);
         ++*launches;
     };
-    auto sweep = [&](float* xi, float* xo, double* xo64) {
-        if (b_double) {
-            const double* b = static_cast<const double*>(bin);
-            if (xo64)
-                mr_row_kernel<double, double, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                        L.dinv32, omega, xo64, live);
+    auto sweep = [&](float* xi, float* xo, bool final_top) {
+        if (top) {
+            const B0* b = static_cast<const B0*>(bin);
+            if (final_top)
+                mr_row_kernel<B0, O0, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
+                                                                L.dinv32, omega, out, live);
             else
-                mr_row_kernel<double, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                       L.dinv32, omega, xo, live);
+                mr_row_kernel<B0, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
+                                                                   L.dinv32, omega, xo, live);
         } else {
             const float* b = static_cast<const float*>(bin);
             mr_row_kernel<float, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
@@ -950,13 +972,12 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, 
     };
     first(cur);
     for (int k = 1; k < h.nu; ++k) {
-        sweep(cur, oth, nullptr);
+        sweep(cur, oth, false);
         std::swap(cur, oth);
     }
-    if (b_double)
-        mr_row_kernel<double, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
-                                                              static_cast<const double*>(bin), L.dinv32, omega, rr,
-                                                              live);
+    if (top)
+        mr_row_kernel<B0, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
+                                                          static_cast<const B0*>(bin), L.dinv32, omega, rr, live);
     else
         mr_row_kernel<float, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
                                                              static_cast<const float*>(bin), L.dinv32, omega, rr, live);
@@ -964,12 +985,12 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, bool b_double, 
     float* cb = level_base(l + 1) + (size_t)3 * C.N * R;
     mr_restrict_kernel<<<blocks_for(C.N * 32), kT, 0, st>>>(L.rrow, L.rcol, L.rval32, C.N, R, rr + off * R, cb, live);
     *launches += 2;
-    float* e = multi_level(h, l + 1, cb, false, 0, nullptr, x0, t0, r0, coarse, R, live, st, launches);
+    float* e = multi_level<B0, O0>(h, l + 1, cb, 0, nullptr, x0, t0, r0, coarse, R, live, st, launches);
     mr_prolong_kernel<<<gw, kT, 0, st>>>(L.N, R, L.pidx, L.pval32, e, cur + off * R, live);
     ++*launches;
     for (int k = 0; k < h.nu; ++k) {
         const bool final_top = top && k == h.nu - 1;
-        sweep(cur, oth, final_top ? out : nullptr);
+        sweep(cur, oth, final_top);
         if (!final_top) std::swap(cur, oth);
     }
     return cur;
@@ -989,7 +1010,17 @@ int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b
     if (!h || !b || !x || !x0 || !t0 || !r0 || R < 1 || R > 64 || !h->has32) return RBFFD_ERR_INVALID_ARG;
     if (h->n_levels > 1 && !coarse) return RBFFD_ERR_INVALID_ARG;
     int n = 0;
-    multi_level(*h, 0, b, true, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
+    multi_level<double, double>(*h, 0, b, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
+    if (launches) *launches += n;
+    return RBFFD_OK;
+}
+
+int mg_apply_multi_df(const MgHierarchy* h, int64_t row_off, int R, const float2* b, float2* x, float* x0, float* t0,
+                      float* r0, float* coarse, const int* live, cudaStream_t st, int* launches) {
+    if (!h || !b || !x || !x0 || !t0 || !r0 || R < 1 || R > 64 || !h->has32) return RBFFD_ERR_INVALID_ARG;
+    if (h->n_levels > 1 && !coarse) return RBFFD_ERR_INVALID_ARG;
+    int n = 0;
+    multi_level<float2, float2>(*h, 0, b, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
     if (launches) *launches += n;
     return RBFFD_OK;
 }
