@@ -64,6 +64,12 @@ EXPLICIT_WORKLOAD = "explicit_1M_m4_n30"
 EXPLICIT_METRIC = "explicit Euler node-steps/s (Eq. 4), 1M-node disk, m=4, n=30, dt=1e-6"
 EXPLICIT_SWEEP_N = (1e4, 3e4, 1e5, 3e5, 1e6, 3e6)
 EXPLICIT_SWEEP_n = (12, 15, 20, 30, 45, 60)
+# The differentiable solve: forward solve and the adjoint gradient of
+# L = sum_interior (u - u*)^2 with respect to f and g, on the 1M-node disk
+# (m = 4, n = 30); u* solves the problem with a seeded Fourier source.
+ADJOINT_WORKLOAD = "adjoint_1M_m4_n30"
+ADJOINT_METRIC = ("differentiable solve nodes/s (forward + adjoint gradient dL/df, dL/dg), 1M-node disk, m=4, "
+                  "n=30, tol 1e-10")
 BATCH_RHS = 64
 BATCH_SAMPLE_RHS = 8  # oracle sample: right-hand sides of the smallest instance per step
 SEED = 2107
@@ -290,6 +296,8 @@ def run_reference(args):
         return run_reference_batched(args)
     if args.workload == EXPLICIT_WORKLOAD:
         return run_reference_explicit(args)
+    if args.workload == ADJOINT_WORKLOAD:
+        return run_reference_adjoint(args)
     h, m, n = WORKLOADS[args.workload]
     res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=args.warmup + args.steps)
     timed = res[args.warmup:]
@@ -326,27 +334,39 @@ def oracle_explicit_sample(h: float, m: int, n: int, steps: int):
     return d.N * steps, time.perf_counter() - t0
 
 
-def run_reference_explicit(args):
+def oracle_subprocess(call: str):
+    """Runs `call` (an expression over the module bench) in a fresh one-thread
+    interpreter with no GPU and returns its JSON result."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
     env.pop("CUDA_VISIBLE_DEVICES", None)
-    k_steps = 100
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "r = [bench.oracle_explicit_sample(%r, 4, 30, %d) for _ in range(%d)]; print(json.dumps(r))"
-            % (ROOT, CPU_SAMPLE_H, k_steps, args.warmup + args.steps))
+    code = "import sys, json; sys.path.insert(0, %r); import bench; print(json.dumps(%s))" % (ROOT, call)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    res = json.loads(out.stdout.strip().splitlines()[-1])[args.warmup:]
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+EXPLICIT_SAMPLE_STEPS = 100
+
+
+def cpu_explicit(warmup: int, steps: int):
+    """(value node-steps/s, seconds per sample, sample text) of the oracle's explicit step."""
+    res = oracle_subprocess("[bench.oracle_explicit_sample(%r, 4, 30, %d) for _ in range(%d)]"
+                            % (CPU_SAMPLE_H, EXPLICIT_SAMPLE_STEPS, warmup + steps))[warmup:]
     units = sum(u for u, _ in res)
     secs = sum(t for _, t in res)
-    value = units / secs
     sample = (f"oracle explicit step (numpy gather + einsum) on the same disk recipe at h={CPU_SAMPLE_H}, m=4, "
-              f"n=30, {k_steps} steps per sample, one core")
+              f"n=30, {EXPLICIT_SAMPLE_STEPS} steps per sample, one core")
+    return units / secs, secs / len(res), sample
+
+
+def run_reference_explicit(args):
+    value, secs, sample = cpu_explicit(args.warmup, args.steps)
     line = {
         "impl": "reference", "metric": EXPLICIT_METRIC, "value": value, "unit": "node-steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(res),
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "m": 4, "n": 30, "dt": 1e-6},
         "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
@@ -356,19 +376,24 @@ def run_reference_explicit(args):
     return 0
 
 
-def run_reference_batched(args):
+def cpu_batched(warmup: int, steps: int):
+    """(value node-rhs/s, seconds per step, pairs per step, sample text) of the oracle on the batched sample."""
     sp = batch_sample_spec()
-    res = cpu_baseline_subprocess(0.0, 0, 0, steps=args.warmup + args.steps, batch=True)
-    timed = res[args.warmup:]
+    timed = cpu_baseline_subprocess(0.0, 0, 0, steps=warmup + steps, batch=True)[warmup:]
     pairs = timed[0][0]
     secs = sum(t for _, t in timed)
-    value = pairs * len(timed) / secs
     sample = (f"oracle (brute-force kNN, per-stencil LU, CSR assembly, one SuperLU solve per rhs) on the "
               f"smallest instance of the batched recipe ({pairs // BATCH_SAMPLE_RHS} nodes, m={sp[2]}, n={sp[3]}) "
-              f"x its first {BATCH_SAMPLE_RHS} rhs per step")
+              f"x its first {BATCH_SAMPLE_RHS} rhs per step, one core")
+    return pairs * len(timed) / secs, secs / len(timed), pairs, sample
+
+
+def run_reference_batched(args):
+    sp = batch_sample_spec()
+    value, secs, pairs, sample = cpu_batched(args.warmup, args.steps)
     line = {
         "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "node-rhs/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample_nodes": pairs // BATCH_SAMPLE_RHS, "m": sp[2], "n": sp[3],
                    "sample_rhs": BATCH_SAMPLE_RHS},
@@ -519,6 +544,10 @@ def run_gpu_batched(args):
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cv, csecs, _, csample = cpu_batched(0, 1)
+        line["cpu_baseline"] = {"value": cv, "unit": "node-rhs/s", "cores": 1, "kind": "oracle",
+                                "sample": csample + f", {csecs:.1f} s"}
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     if prof["batch_iter_launches"]:
@@ -641,11 +670,215 @@ def run_gpu_explicit(args):
         "clocks": clk,
         "sweep": sweep,
     }
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        cv, csecs, csample = cpu_explicit(0, 1)
+        line["cpu_baseline"] = {"value": cv, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": csample + f", {csecs:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------- adjoint workload ----
+def run_gpu_adjoint(args):
+    import numpy as np
+    import torch
+
+    from fixtures import disk_nodes, fourier_sources, manufactured
+    from paper_2107_03632_gb300 import rbffd
+
+    ws_, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws_ > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rbffd.load()
+    h, m, n = 1.7725e-3, 4, 30
+    d = disk_nodes(h, SEED)
+    N = d.N
+    u_ex, f, g = manufactured(d.xy)
+    fstar = fourier_sources(d.xy, 1, SEED + 1)[0]
+    xy, mask = torch.from_numpy(d.xy).to(dev), torch.from_numpy(d.is_dirichlet).to(dev)
+    fT, gT, fsT = (torch.from_numpy(a).to(dev) for a in (f, g, fstar))
+    idx = rbffd.rbffd_stencils(xy, n)
+    wcfg = rbffd.rbffd_weights_autotune(xy, idx, m)
+    w, st = rbffd.rbffd_weights(xy, idx, m)
+    A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A)
+    mga = rbffd.Multigrid.adjoint_of(mg, AT)
+    opts = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mg)
+    opts_a = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mga)
+    ws_s = rbffd.solve_workspace(N, opts, dev)
+    # target u* (fixed, outside the timed steps)
+    ustar, _ = rbffd.rbffd_solve(A, rbffd.rbffd_rhs(fsT, gT, mask), opts=opts, ws=ws_s)
+    b = torch.empty(N, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    lam = torch.empty(N, dtype=torch.float64, device=dev)
+    dLdu = torch.empty(N, dtype=torch.float64, device=dev)
+    ws_knn = rbffd.stencils_workspace(N, n, dev)
+    ws_asm = rbffd.assemble_workspace(N, dev)
+
+    stage_names = ("stencils", "weights", "assemble_transpose_rhs", "mg_setup_forward", "mg_setup_adjoint",
+                   "forward_solve", "adjoint_solve")
+
+    def step(ev=None):
+        mark = (lambda k: ev[k].record()) if ev is not None else (lambda k: None)
+        mark(0)
+        rbffd.rbffd_stencils(xy, n, idx, ws_knn)
+        mark(1)
+        rbffd.rbffd_weights(xy, idx, m, w, st)
+        mark(2)
+        rbffd.rbffd_assemble_pattern(mask, n, A.row_ptr, ws_asm)
+        rbffd.rbffd_assemble(idx, w, mask, out=A)
+        AT2 = rbffd.rbffd_transpose(A, want_f32=True)
+        rbffd.rbffd_rhs(fT, gT, mask, b)
+        mark(3)
+        mg.setup(xy, mask, A)
+        mark(4)
+        mga.rebuild_from(mg, AT2)
+        mark(5)
+        u.zero_()
+        _, info = rbffd.rbffd_solve(A, b, u, opts, ws_s, raise_on_error=False)
+        mark(6)
+        rbffd.rbffd_misfit_grad(u, ustar, mask, dLdu)
+        lam.zero_()
+        _, dLdf, dLdg, info_a = rbffd.rbffd_solve_adjoint(AT2, mask, dLdu, lam, opts_a, ws_s, raise_on_error=False)
+        mark(7)
+        if info["status_code"] != 0 or info_a["status_code"] != 0:
+            raise rbffd.RbffdError(max(info["status_code"], info_a["status_code"]), "differentiable solve",
+                                   f"{info} {info_a}")
+        return info, info_a, dLdf, dLdg
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    rbffd.rbffd_profile_read(reset=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        info, info_a, dLdf, dLdg = step()
+    t1.record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    prof = rbffd.rbffd_profile_read(reset=True)
+    value, ms = replica_value(dist, ws_, N, args.steps, t0.elapsed_time(t1), dev)
+    # stage times: one more (untimed) step with events between the stages
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)]
+    step(evs)
+    torch.cuda.synchronize(dev)
+    stages = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(stage_names)}
+    # e2e: geometry, sources, boundary data and the target from pinned host
+    # memory, both gradients back, every step
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_xy, h_mask, h_f, h_g, h_us = pin(d.xy), pin(d.is_dirichlet), pin(f), pin(g), pin(ustar.cpu().numpy())
+    h_df = torch.empty(N, dtype=torch.float64).pin_memory()
+    h_dg = torch.empty(N, dtype=torch.float64).pin_memory()
+    h2d = N * (16 + 1 + 8 + 8 + 8)
+    d2h = 2 * N * 8
+    e2e_value = None
+    if args.e2e_steps > 0:
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.e2e_steps):
+            xy.copy_(h_xy, non_blocking=True)
+            mask.copy_(h_mask, non_blocking=True)
+            fT.copy_(h_f, non_blocking=True)
+            gT.copy_(h_g, non_blocking=True)
+            ustar.copy_(h_us, non_blocking=True)
+            _, _, dLdf, dLdg = step()
+            h_df.copy_(dLdf, non_blocking=True)
+            h_dg.copy_(dLdg, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        e2e_value, _ = replica_value(dist, ws_, N, args.e2e_steps, e0.elapsed_time(e1), dev)
+    w_tflops = weights_flops(n, m) * N / (stages["weights"] * 1e-3) / 1e12
+    cpu = None
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        cv, csecs, cnodes, csample = cpu_adjoint(0, 1)
+        cpu = {"value": cv, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": csample + f", {csecs:.1f} s"}
+    line = {
+        "metric": ADJOINT_METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws_, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": ADJOINT_WORKLOAD, "N": N, "m": m, "n": n, "tol": 1e-10,
+                   "precond": "multigrid (forward) and transposed multigrid (adjoint), float32 V-cycles",
+                   "weights_config": wcfg, "parallelism": f"replicas x{ws_}",
+                   "l2": "inputs larger than L2 (CSR + transpose ~%.1f GB)" % (2 * A.nnz * 16 / 1e9)},
+        "solve": {"forward_iters": info["iters"], "adjoint_iters": info_a["iters"],
+                  "forward_rel_residual": info["rel_residual"], "adjoint_rel_residual": info_a["rel_residual"],
+                  "grad_f_norm": float(dLdf.norm()), "grad_g_norm": float(dLdg.norm())},
+        "stages_ms": stages,
+        "roofline": {"kernel": "weights_ns_kernel (null-space elimination, FP64), m=4, n=30", "bound": "alu",
+                     "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
+                     "frac": w_tflops / FP64_PEAK_TFLOPS_UNITS,
+                     "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)", "traffic": None,
+                     "flops_per_node": weights_flops(n, m), "ms_per_launch": stages["weights"], "launches": 1},
+        "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "steps": args.e2e_steps} if e2e_value is not None else None),
+        "cpu_baseline": cpu,
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def oracle_adjoint_sample(h: float, m: int, n: int):
+    """The oracle's differentiable solve on the sample disk: forward direct
+    solve, misfit gradient, adjoint direct solve; returns (nodes, seconds)."""
+    import oracle
+    from fixtures import disk_nodes, fourier_sources, manufactured
+
+    d = disk_nodes(h, SEED)
+    u, f, g = manufactured(d.xy)
+    fstar = fourier_sources(d.xy, 1, SEED + 1)[0]
+    ustar, _ = oracle.poisson_solve(d.xy, d.is_dirichlet, fstar, g, m, n)
+    t0 = time.perf_counter()
+    uu, (idx, w, rp, col, val, b) = oracle.poisson_solve(d.xy, d.is_dirichlet, f, g, m, n)
+    dLdu = np.where(d.is_dirichlet == 1, 0.0, 2.0 * (uu - ustar))
+    oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, dLdu)
+    return d.N, time.perf_counter() - t0
+
+
+def cpu_adjoint(warmup: int, steps: int):
+    """(value nodes/s, seconds per step, sample nodes, sample text) of the oracle's differentiable solve."""
+    res = oracle_subprocess("[bench.oracle_adjoint_sample(%r, 4, 30) for _ in range(%d)]"
+                            % (CPU_SAMPLE_H, warmup + steps))[warmup:]
+    nodes = res[0][0]
+    secs = sum(t for _, t in res)
+    sample = (f"oracle differentiable solve (brute-force kNN, per-stencil LU, SuperLU forward and adjoint solves) "
+              f"on the same disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m=4, n=30), one core")
+    return nodes * len(res) / secs, secs / len(res), nodes, sample
+
+
+def run_reference_adjoint(args):
+    value, secs, nodes, sample = cpu_adjoint(args.warmup, args.steps)
+    line = {
+        "impl": "reference", "metric": ADJOINT_METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "sample_nodes": nodes, "m": 4, "n": 30},
+        "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -925,7 +1158,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="disk_4M_m6_n56",
-                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, EXPLICIT_WORKLOAD])
+                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, EXPLICIT_WORKLOAD, ADJOINT_WORKLOAD])
     ap.add_argument("--no-sweep", action="store_true", help="explicit workload: skip the N x n sweep")
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
     ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
@@ -948,6 +1181,8 @@ def main():
         return run_gpu_batched(args)
     if args.workload == EXPLICIT_WORKLOAD:
         return run_gpu_explicit(args)
+    if args.workload == ADJOINT_WORKLOAD:
+        return run_gpu_adjoint(args)
     return run_gpu(args)
 
 

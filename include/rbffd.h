@@ -237,7 +237,8 @@ int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t
 /* With opts->precond = 1, rbffd_solve runs BiCGSTAB right-preconditioned by */
 /* one V-cycle per application (FP64 V-cycle in precision 0; in precision 1 */
 /* the V-cycle runs in float32 values and vectors inside the FP64 BiCGSTAB, */
-/* which needs A32).  The adjoint solve does not take it.                   */
+/* which needs A32).  The adjoint solve takes the hierarchy of             */
+/* rbffd_mg_setup_adjoint (below).                                          */
 /*   mg       : host object filled here; read by rbffd_solve.  It points     */
 /*              into ws, which must stay allocated and unchanged meanwhile.  */
 /*   A, A32   : the fine-level operator (as passed to rbffd_solve; A32 may   */
@@ -257,9 +258,67 @@ size_t rbffd_mg_workspace_size(int64_t N, int64_t nnz);
 int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
                    const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws, size_t ws_bytes,
                    void* stream);
+/* rbffd_mg_setup_adjoint: the same hierarchy for the adjoint operator AT  */
+/* = A^T (as passed to rbffd_solve_adjoint): every level's operator is the  */
+/* transpose of the forward one (coarse levels rediscretised, then          */
+/* transposed), restriction P^T and prolongation R^T = (N_c / N_f) P with   */
+/* the coarse Dirichlet columns zeroed -- the exact transpose of the        */
+/* forward V-cycle, so the adjoint iteration sees the transposed            */
+/* preconditioned operator.  rbffd_solve takes only forward hierarchies,   */
+/* rbffd_solve_adjoint only adjoint ones (else RBFFD_ERR_INVALID_ARG).      */
+int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* AT,
+                           const rbffd_csr* AT32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
+                           size_t ws_bytes, void* stream);
+/* rbffd_mg_adjoint_of: the adjoint hierarchy of a built forward hierarchy */
+/* `fwd` for AT = A^T (the matrix rbffd_solve_adjoint gets): the coarse      */
+/* node sets, smoother weights and interpolation are fwd's (copied into ws, */
+/* so fwd may be rebuilt or freed afterwards), the operators transposed,    */
+/* the coarsest transposed operator inverted.  The result holds the same    */
+/* values as rbffd_mg_setup_adjoint on the same inputs; it costs the        */
+/* transposes instead of a second coarsening, kNN and weight solve.         */
+/*   AT, AT32 : as for rbffd_mg_setup_adjoint (AT32 needs fwd built with a  */
+/*              float32 copy).  ws: rbffd_mg_workspace_size(N, AT->nnz).     */
+/* Synchronises `stream`.  Errors: RBFFD_ERR_INVALID_ARG (fwd not a built    */
+/* forward hierarchy, sizes differ), RBFFD_ERR_WORKSPACE.                    */
+int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32, rbffd_mg* mg, void* ws,
+                        size_t ws_bytes, void* stream);
 /* Levels of a built hierarchy (finest first); n_nodes: RBFFD_MG_MAX_LEVELS  */
 /* entries, may be NULL.  Returns the level count, 0 if mg was not built.    */
 int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes);
+/* rbffd_mg_level: read-only view of one level of a built hierarchy, for     */
+/* inspection.  Every pointer is a device pointer into the hierarchy's       */
+/* workspace (level 0: the caller's xy, mask and matrix), valid until the    */
+/* workspace is rebuilt or freed.                                            */
+/*   A      : the level's operator (FP64; the adjoint hierarchy: the         */
+/*            transposed operator).                                          */
+/*   w      : smoother weights W = Omega D^-1 (omega / a_ii on interior      */
+/*            rows, 1 / a_ii on Dirichlet rows).                             */
+/*   p_idx, p_val : the prolongation from level + 1 into this level, ELL    */
+/*            n_nodes x p_k (coarse indices); forward hierarchy: P, the     */
+/*            interpolation; adjoint: R^T = (N_c / N_f) P without the coarse */
+/*            Dirichlet columns.  NULL (p_k 0) at the coarsest level.        */
+/*   minv   : coarsest level only: its dense inverse, row-major.            */
+/* Errors: RBFFD_ERR_INVALID_ARG (mg not built, level out of range).        */
+typedef struct rbffd_mg_level_info {
+    int64_t n_nodes;
+    const double* xy;
+    const uint8_t* is_dirichlet;
+    rbffd_csr A;
+    const double* w;
+    const int32_t* p_idx;
+    const double* p_val;
+    int32_t p_k;
+    const double* minv;
+} rbffd_mg_level_info;
+int rbffd_mg_level(const rbffd_mg* mg, int32_t level, rbffd_mg_level_info* out);
+/* rbffd_mg_apply: x = M b, one application of the preconditioner on        */
+/* `stream` (b, x: device, N float64 each, distinct).  Forward hierarchy:   */
+/* one V-cycle B from x = 0.  Adjoint hierarchy: the transpose of the       */
+/* forward preconditioner E_b + B (I - A E_b) (E_b selects the Dirichlet    */
+/* entries), i.e. B^T followed by the Dirichlet back substitution           */
+/* x_b = b_b - sum_i a_ib x_i.  fp32 != 0: float32 V-cycle (needs a         */
+/* hierarchy built with A32).  Errors: RBFFD_ERR_INVALID_ARG.               */
+int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Krylov solve -- the implicit solution named in Sec. VI: A x = b by       */
@@ -321,6 +380,12 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
                         const double* dLdu, double* lambda, double* dLdf, double* dLdg,
                         const rbffd_solve_opts* opts, rbffd_solve_info* info,
                         void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient of the misfit L(u) = sum over interior nodes of (u - u_target)^2 */
+/* (the loss of the differentiable solve): dLdu = 2 (u - u_target) on        */
+/* interior nodes, 0 on Dirichlet nodes.  Device arrays of N; asynchronous. */
+int rbffd_misfit_grad(const double* u, const double* u_target, const uint8_t* is_dirichlet, int64_t N,
+                      double* dLdu, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched solve -- many independent node sets (instances) of uneven size   */

@@ -180,6 +180,17 @@ __global__ void b_rhs_kernel(int64_t N, int R, const uint8_t* __restrict__ mask,
         b[e] = mask[e / R] ? g[e] : -f[e];
 }
 
+// Starting guess on the Dirichlet (identity) rows: u_b = b_b, so every
+// residual is zero there (with nonzero boundary data, a Dirichlet part of
+// the residual is coupled into the interior by a block of size ~1/h^2 of
+// the preconditioned operator).
+__global__ void b_dstart_kernel(int64_t N, int R, const uint8_t* __restrict__ mask, const double* __restrict__ b,
+                                double* __restrict__ u) {
+    const int64_t total = N * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        if (mask[e / R]) u[e] = b[e];
+}
+
 __global__ void b_diag_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const double* __restrict__ val, int64_t N, double* __restrict__ d,
                               double* __restrict__ dinv, float* __restrict__ d32, float* __restrict__ dinv32,
@@ -1345,9 +1356,10 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
     b_fill_kernel<<<gb, 256, 0, st>>>(w.inst, pl.n_inst, N, is_dirichlet, w.idx, w.w, w.row_ptr, pl.nnz_cap, w.col,
                                       w.val, w.val32);
     b_rhs_kernel<<<sm_count() * 8, 256, 0, st>>>(N, R, is_dirichlet, f, g, w.b);
+    b_dstart_kernel<<<sm_count() * 8, 256, 0, st>>>(N, R, is_dirichlet, w.b, u);
     b_diag_kernel<<<(int)std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, st>>>(
         w.row_ptr, w.col, w.val, N, w.d, w.dinv, w.d32, w.dinv32, w.sig32);
-    note_launches(3);
+    note_launches(4);
     RBFFD_LAUNCH_CHECK();
 
     // per-node weight status: any singular stencil fails the instance

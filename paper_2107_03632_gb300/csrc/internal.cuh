@@ -66,25 +66,41 @@ struct MgHierarchy {
     int nu;
     int has32;
     int col_base;  // level-0 column indices are offset by this (rows local)
+    int transposed;  // built for A^T (rbffd_mg_setup_adjoint)
     double omega;
     MgLevel lv[RBFFD_MG_MAX_LEVELS];
 };
 const MgHierarchy* mg_hierarchy(const rbffd_mg* h);
 int64_t mg_fine_rows(const MgHierarchy* h);
 bool mg_has_fp32(const MgHierarchy* h);
+bool mg_is_transposed(const MgHierarchy* h);
 // Enqueues x = M^-1 b, one V-cycle (FP64, or float32 values and vectors when
 // fp32), on st; every kernel returns at once while *flag != 0.  With
 // profiling on and ev given, the finest-level sweeps are bracketed with
 // events (their slots appended to ev).
+// Forward hierarchies: B, the V-cycle.  Adjoint hierarchies: B^T, then the
+// Dirichlet back substitution (mg_dirichlet_fix), i.e. the transpose of
+// M = E_b + B (I - A E_b) (E_b: the Dirichlet rows' selector), which equals
+// B on the residuals a forward solve started by mg_dirichlet_fix produces.
+// With A = [I 0; L_ib L_ii] (Dirichlet rows first) M A = diag(I, B_ii L_ii),
+// so the adjoint's preconditioned operator is block diagonal.
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev = nullptr);
+// y_b += W_b (r_b - (A y)_b) on the Dirichlet rows of level 0 (see
+// mg_bfix_kernel); one launch on st.
+int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int* flag, cudaStream_t st);
 
 // rbffd_mg_setup for a fine operator given by arrays: row_ptr points at the
 // fine rows' first entry (values are offsets into col/val), and column
 // indices are offset by col_base (a block of a larger block-diagonal matrix).
 int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_t* row_ptr, const int* col,
                   const double* val, const float* val32, int64_t nnz, int col_base, int nu, double omega,
-                  rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st);
+                  rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed = false);
+
+// The adjoint hierarchy of the forward hierarchy F for AT = A^T
+// (rbffd_mg_adjoint_of).
+int mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg, void* ws,
+                  size_t ws_bytes, cudaStream_t st);
 
 // Multi-right-hand-side float32 V-cycle on node-major vectors [row][R]
 // (R <= 64): x = M^-1 b for every column.  Level 0 works on rows

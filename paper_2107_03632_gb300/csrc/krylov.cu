@@ -50,6 +50,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdlib>
@@ -65,7 +66,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 2048;
 constexpr int kSlots = 8;
-constexpr int kQ = 3;
+constexpr int kQ = 4;
 
 enum Flag : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIter = 3, kReplace = 4, kDiverged = 5 };
 // A pass whose residual has grown 1e3 above its start is ended early.
@@ -259,8 +260,9 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(const int64_t* __restri
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
 }
 
-// kInit:  r = D^-1 (b - A x), rh = r, p = v = 0, scalars reset: a new pass
-//         that ends when |r|^2 < repl^2 |b - A x|^2.
+// kInit:  r = D^-1 (b - A x), rh = r (seed 0) or the pseudo-random shadow
+//         residual of seed, p = v = 0, scalars reset: a new pass that ends
+//         when |r|^2 < repl^2 |b - A x|^2.
 // kCheck: r = b - A x (unscaled), |r|^2 and |b|^2 only.
 template <int TPR, int MODE>
 __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __restrict__ row_ptr,
@@ -271,10 +273,10 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
                                                            const double* __restrict__ dinv,
                                                            double* __restrict__ r, double* __restrict__ rh,
                                                            double* __restrict__ p, double* __restrict__ v,
-                                                           double tol, int max_iter, double repl, KState* st,
-                                                           double* part) {
+                                                           double tol, int max_iter, double repl,
+                                                           unsigned long long seed, KState* st, double* part) {
     const int sub = threadIdx.x & (TPR - 1);
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
         const double bi = valid ? b[i] : 0.0;
         const double rt = row_residual64<TPR>(row_ptr, col, val, x, i, sub, valid, bi);
@@ -286,15 +288,17 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
             if (MODE == kCheck) {
                 r[i] = rt;
             } else {
+                const double hi = seed ? (double)shadow_value(seed, i) : ri;
                 r[i] = ri;
-                rh[i] = ri;
+                rh[i] = hi;
                 p[i] = 0.0;
                 v[i] = 0.0;
+                acc[3] = fma(hi, ri, acc[3]);
             }
         }
     })
-    double tot[3];
-    if (reduce_last<3>(acc, part, kSlotResid, &st->counter[kSlotResid], tot) && threadIdx.x == 0) {
+    double tot[4];
+    if (reduce_last<4>(acc, part, kSlotResid, &st->counter[kSlotResid], tot) && threadIdx.x == 0) {
         st->tnorm2 = tot[0];
         st->sres2 = tot[2];
         if (MODE == kCheck) {
@@ -312,10 +316,10 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
         st->repl2 = repl * repl;
         st->rnorm2 = tot[0];
         st->rmax2 = tot[0];
-        st->rho_new = tot[2];
+        st->rho_new = tot[3];
         int flag = kRunning;
         if (tot[0] <= st->tol2) flag = kConverged;
-        else if (!finite(tot[0]) || !finite(tot[2])) flag = kBreakdown;
+        else if (!finite(tot[0]) || !finite(tot[2]) || !finite(tot[3]) || tot[3] == 0.0) flag = kBreakdown;
         else if (st->iter >= st->max_iter) flag = kMaxIter;
         st->flag = flag;
     }
@@ -611,6 +615,11 @@ __global__ void refine_kernel(int64_t N, double* __restrict__ x, float2* __restr
     }
 }
 
+__global__ void misfit_grad_kernel(int64_t N, const double* __restrict__ u, const double* __restrict__ ut,
+                                   const uint8_t* __restrict__ mask, double* __restrict__ g) {
+    RBFFD_ELEM_LOOP(N, i) g[i] = mask[i] ? 0.0 : 2.0 * (u[i] - ut[i]);
+}
+
 __global__ void adjoint_grad_kernel(int64_t N, const uint8_t* __restrict__ mask, const double* __restrict__ lam,
                                     double* __restrict__ dLdf, double* __restrict__ dLdg) {
     RBFFD_ELEM_LOOP(N, i) {
@@ -746,14 +755,14 @@ int64_t spmv_bytes(const rbffd_csr& A, int val_bytes) {
 template <int TPR>
 struct Ops64 {
     static void resid(int mode, const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r,
-                      double tol, int max_iter, double repl, cudaStream_t st) {
+                      double tol, int max_iter, double repl, unsigned long long seed, cudaStream_t st) {
         const double* val = static_cast<const double*>(A.val);
         if (mode == kInit)
             resid64_kernel<TPR, kInit><<<grid_of(resid64_kernel<TPR, kInit>), kThreads, 0, st>>>(
-                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
+                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, seed, w.st, w.part);
         else
             resid64_kernel<TPR, kCheck><<<grid_of(resid64_kernel<TPR, kCheck>), kThreads, 0, st>>>(
-                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, w.st, w.part);
+                A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, seed, w.st, w.part);
         note_launches(1);
     }
     static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st, std::vector<int>& ev) {
@@ -811,12 +820,12 @@ struct OpsDf {
 };
 
 void resid64(int tpr, int mode, const rbffd_csr& A, const double* b, const double* x, const Work& w, double* r,
-             double tol, int max_iter, double repl, cudaStream_t st) {
+             double tol, int max_iter, double repl, cudaStream_t st, unsigned long long seed = 0) {
     switch (tpr) {
-        case 1: Ops64<1>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
-        case 2: Ops64<2>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
-        case 8: Ops64<8>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
-        default: Ops64<4>::resid(mode, A, b, x, w, r, tol, max_iter, repl, st); break;
+        case 1: Ops64<1>::resid(mode, A, b, x, w, r, tol, max_iter, repl, seed, st); break;
+        case 2: Ops64<2>::resid(mode, A, b, x, w, r, tol, max_iter, repl, seed, st); break;
+        case 8: Ops64<8>::resid(mode, A, b, x, w, r, tol, max_iter, repl, seed, st); break;
+        default: Ops64<4>::resid(mode, A, b, x, w, r, tol, max_iter, repl, seed, st); break;
     }
 }
 
@@ -854,24 +863,72 @@ double rel_of(const KState& s) {
     return std::sqrt(s.tnorm2);
 }
 
+// Iterations enqueued per host round trip.  A chunk that runs past the end
+// of its pass costs the launches of every iteration after the end (kernels
+// that return at once: ~90 launches, ~0.2 ms, per iteration with the
+// V-cycles); one that stops short costs a round trip (tens of microseconds
+// of idle device).  So the next chunk is the number of iterations the pass
+// still needs at the residual reduction measured so far in it (rate2: factor
+// per iteration on |r|^2), plus one, but at most ~kChunkMs of device time at
+// the measured time per iteration: early BiCGSTAB iterations often reduce
+// the residual slowly and would make the prediction far too long.  Without
+// a measurement: 4, doubling, within the same time cap.
+constexpr double kChunkMs = 4.0;
+
+struct ChunkPlan {
+    int chunk = 4;
+    double rate2 = 0.0;
+    double ms_per_iter = 0.0;
+    int cap() const {
+        if (!(ms_per_iter > 0.0)) return 64;
+        return (int)std::min(64.0, std::max(2.0, std::ceil(kChunkMs / ms_per_iter)));
+    }
+    static int need(double from2, double to2, double rate2) {
+        if (!(rate2 > 0.0 && rate2 < 1.0) || !(from2 > 0.0) || !(to2 > 0.0)) return -1;
+        if (from2 <= to2) return 1;
+        const double n = std::ceil(std::log(to2 / from2) / std::log(rate2));
+        return (int)std::min(n, 63.0) + 1;
+    }
+    // first chunk of a pass starting at |r|^2 = start2 that ends at target2
+    void start(double start2, double target2) {
+        const int n = need(start2, target2, rate2);
+        if (n > 0) chunk = std::min(std::max(n, 1), cap());
+    }
+    void update(const KState& hs, double start2, int ran, double ms) {
+        if (ran > 0 && ms > 0.0) ms_per_iter = ms_per_iter > 0.0 ? 0.5 * (ms_per_iter + ms / ran) : ms / ran;
+        const double target2 = std::max(hs.tol2, hs.repl2 * hs.rmax2);
+        if (hs.iter > 0 && hs.rnorm2 > 0.0 && start2 > 0.0) {
+            const double r2 = std::pow(hs.rnorm2 / start2, 1.0 / hs.iter);
+            if (r2 > 0.0 && r2 < 1.0) rate2 = r2;
+        }
+        const int n = need(hs.rnorm2, target2, rate2);
+        chunk = std::min(n > 0 ? std::max(n, 1) : chunk * 2, cap());
+    }
+};
+
 // Runs chunks of iterations until the state leaves kRunning; returns the
 // flag, or minus a status on a CUDA error.  With profiling on, only the SpMV
 // launches of iterations that ran are accounted (launches after the pass
 // ended return at once and are dropped).
 template <class IterFn>
-int run_chunks(const Work& w, KState* hs, cudaStream_t st, int& chunk, IterFn iter) {
+int run_chunks(const Work& w, KState* hs, cudaStream_t st, ChunkPlan& plan, IterFn iter) {
     std::vector<int> ev;
+    const double start2 = hs->rnorm2;
+    plan.start(start2, std::max(hs->tol2, hs->repl2 * hs->rmax2));
     while (hs->flag == kRunning) {
         const int before = hs->iter;
+        const int chunk = plan.chunk;
+        const auto t0 = std::chrono::steady_clock::now();
         ev.clear();
         for (int c = 0; c < chunk; ++c) iter(ev);
         RBFFD_LAUNCH_CHECK();
         const int rc = read_state(w, hs, st);
         if (rc != RBFFD_OK) return -rc;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // every iteration brackets the same number of launches, in order
         const int per_iter = chunk > 0 ? (int)ev.size() / chunk : 0;
         if (profiling()) prof_commit(ev.data(), (int)ev.size(), per_iter * (hs->iter - before));
-        chunk = std::min(chunk * 2, 64);
+        plan.update(*hs, start2, hs->iter - before, ms);
     }
     return hs->flag;
 }
@@ -907,7 +964,25 @@ struct PassGuard {
         rejected = 0;
         if (cap < 0x7fffffff / 2) cap += std::max(cap / 4, 1);
     }
+    // Last resort once reject() gives up: if the passes used rh = r, retry
+    // with pseudo-random shadow residuals (a pass that blows up in its first
+    // iteration is a near-breakdown, (rh, A M p) ~ 0, of the shadow r).
+    bool switch_shadow(bool& rnd) {
+        if (rnd) return false;
+        rnd = true;
+        rejected = 0;
+        cap = 0x7fffffff;
+        return true;
+    }
 };
+
+// Shadow residual of a pass: r itself (seed 0) by default; a pseudo-random
+// one per pass once rnd is set (RBFFD_SHADOW=1 sets it from the start: better
+// on late passes of small systems, worse on the long first pass of 4M-node
+// systems) or after a pass that broke down with rh = r.
+unsigned long long shadow_seed(bool rnd, int pass) {
+    return rnd ? 0x5EED2107ull + (unsigned long long)pass : 0ull;
+}
 
 int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve_opts& o, const Work& w,
                cudaStream_t st, rbffd_solve_info* info) {
@@ -915,21 +990,31 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     const int tpr = tpr64_for(N, A.nnz);
     KState hs;
     int rc;
-    int total = 0, passes = 0, breakdowns = 0, chunk = 4;
+    int total = 0, passes = 0, breakdowns = 0;
+    ChunkPlan chunk;
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
     PassGuard g;
+    bool rnd = shadow_random();
+    // Multigrid, forward: start from x_b = b_b on the Dirichlet (identity)
+    // rows, so that every residual is zero there.  The right-preconditioned
+    // operator A M = [I 0; (I - L_ii M_ii) L_ib  L_ii M_ii] couples the
+    // Dirichlet part of a vector into the interior through a block of size
+    // ~1/h^2; a residual with Dirichlet entries (nonzero boundary data) made
+    // BiCGSTAB break down in its first step at 1e6 nodes.
+    if (w.mg && !mg_is_transposed(w.mg) && (rc = mg_dirichlet_fix(w.mg, b, x, nullptr, st)) != RBFFD_OK) return rc;
     while (true) {
-        // explicit residual; starts a fresh pass (rh = r, p = v = 0)
+        // explicit residual; starts a fresh pass (rh = r or a pseudo-random
+        // shadow residual, p = v = 0)
         const int budget = std::min(std::max(o.max_iter - total, 0), g.cap);
-        resid64(tpr, kInit, A, b, x, w, w.r, o.tol, budget, o.inner_tol, st);
+        resid64(tpr, kInit, A, b, x, w, w.r, o.tol, budget, o.inner_tol, st, shadow_seed(rnd, passes));
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
         if (passes > 0 && !(hs.sres2 <= g.prev)) {
             // the pass made things worse: undo it and retry with a shorter pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            const bool retry = g.reject();
-            if (trace_on()) fprintf(stderr, "[rbffd fp64] pass undone, %s\n", retry ? "retry shorter" : "stop");
+            const bool retry = g.reject() || g.switch_shadow(rnd);
+            if (trace_on()) fprintf(stderr, "[rbffd fp64] pass undone, %s\n", retry ? "retry" : "stop");
             if (!retry) {
                 resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, 0.0, st);
                 RBFFD_LAUNCH_CHECK();
@@ -968,6 +1053,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
                     passes, hs.iter, hs.flag, std::sqrt(hs.rnorm2 / start2), rel);
         g.last_iters = hs.iter;
         if (hs.flag == kBreakdown) {
+            rnd = true;
             if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
                 break;
@@ -995,10 +1081,12 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     const int tpr32 = tpr32_for(N, A.nnz);
     KState hs;
     int rc;
-    int total = 0, outer = 0, breakdowns = 0, chunk = 4;
+    int total = 0, outer = 0, breakdowns = 0;
+    ChunkPlan chunk;
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
     PassGuard g;
+    bool rnd = shadow_random();
     while (true) {
         resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
         RBFFD_LAUNCH_CHECK();
@@ -1006,8 +1094,8 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         if (outer > 0 && !(hs.sres2 <= g.prev)) {
             // the correction made things worse: undo it, shorter next pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            const bool retry = g.reject();
-            if (trace_on()) fprintf(stderr, "[rbffd mixed] pass undone, %s\n", retry ? "retry shorter" : "stop");
+            const bool retry = g.reject() || g.switch_shadow(rnd);
+            if (trace_on()) fprintf(stderr, "[rbffd mixed] pass undone, %s\n", retry ? "retry" : "stop");
             if (!retry) {
                 resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
                 RBFFD_LAUNCH_CHECK();
@@ -1040,10 +1128,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         // outer tolerance needs
         const double inner = std::min(std::max(o.inner_tol, 0.5 * o.tol / rel), 0.5);
         const int budget = std::min(o.max_iter - total, g.cap);
-        // shadow residual: r itself by default; RBFFD_SHADOW=1 draws a fresh
-        // pseudo-random one per pass (better on late passes of small
-        // systems, worse on the long first pass of 4M-node systems)
-        const unsigned long long seed = shadow_random() ? 0x5EED2107ull + (unsigned long long)outer : 0ull;
+        const unsigned long long seed = shadow_seed(rnd, outer);
         load_df_kernel<<<grid_of(load_df_kernel), kThreads, 0, st>>>(N, w.r64, w.dinv32, w.rd, w.rhd, w.pd, w.vd,
                                                                      w.xd, inner, budget, seed, w.st, w.part);
         note_launches(1);
@@ -1062,6 +1147,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         if (hs.flag == kBreakdown) {
+            rnd = true;
             if (++breakdowns >= 8) {
                 status = RBFFD_ERR_BREAKDOWN;
                 break;
@@ -1083,7 +1169,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
 }
 
 int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x, const rbffd_solve_opts* o,
-               rbffd_solve_info* info, void* ws, size_t ws_bytes, cudaStream_t st) {
+               rbffd_solve_info* info, void* ws, size_t ws_bytes, cudaStream_t st, bool adjoint) {
     if (!csr_ok(A, 0) || !b || !x || !o || !info) return RBFFD_ERR_INVALID_ARG;
     const bool mixed = o->precision == 1;
     if (o->precision != 0 && o->precision != 1) return RBFFD_ERR_INVALID_ARG;
@@ -1097,7 +1183,9 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     const MgHierarchy* mg = nullptr;
     if (o->precond == 1) {
         mg = mg_hierarchy(o->mg);
-        if (!mg || mg_fine_rows(mg) != N || (mixed && !mg_has_fp32(mg))) return RBFFD_ERR_INVALID_ARG;
+        // a hierarchy built for A serves the solve, one built for A^T the adjoint
+        if (!mg || mg_fine_rows(mg) != N || (mixed && !mg_has_fp32(mg)) || mg_is_transposed(mg) != adjoint)
+            return RBFFD_ERR_INVALID_ARG;
     }
     Work w{};
     if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0 || ws_bytes < layout(nullptr, N, mixed, mg != nullptr, nullptr))
@@ -1137,7 +1225,7 @@ extern "C" size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* 
 extern "C" int rbffd_solve(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x,
                            const rbffd_solve_opts* opts, rbffd_solve_info* info, void* ws, size_t ws_bytes,
                            void* stream) {
-    return rbffd::solve_impl(A, A32, b, x, opts, info, ws, ws_bytes, rbffd::as_stream(stream));
+    return rbffd::solve_impl(A, A32, b, x, opts, info, ws, ws_bytes, rbffd::as_stream(stream), false);
 }
 
 extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_t* is_dirichlet,
@@ -1146,9 +1234,8 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
                                    void* stream) {
     using namespace rbffd;
     if (!is_dirichlet && (dLdf || dLdg)) return RBFFD_ERR_INVALID_ARG;
-    if (opts && opts->precond != 0) return RBFFD_ERR_INVALID_ARG;  // the hierarchy is built for A, not A^T
     cudaStream_t st = as_stream(stream);
-    const int rc = solve_impl(AT, AT32, dLdu, lambda, opts, info, ws, ws_bytes, st);
+    const int rc = solve_impl(AT, AT32, dLdu, lambda, opts, info, ws, ws_bytes, st, true);
     if (rc != RBFFD_OK) return rc;
     if (dLdf || dLdg) {
         const int64_t N = AT->n_rows;
@@ -1157,5 +1244,16 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
     }
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_misfit_grad(const double* u, const double* u_target, const uint8_t* is_dirichlet, int64_t N,
+                                 double* dLdu, void* stream) {
+    using namespace rbffd;
+    if (!u || !u_target || !is_dirichlet || !dLdu || N <= 0) return RBFFD_ERR_INVALID_ARG;
+    misfit_grad_kernel<<<(int)std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, as_stream(stream)>>>(
+        N, u, u_target, is_dirichlet, dLdu);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
 }

@@ -21,8 +21,16 @@
 //    the 12 nearest coarse nodes; rows of Dirichlet nodes are zero (the
 //    correction vanishes on the boundary).  Restriction R = (N_c / N_f) P^T
 //    (a deterministic transpose), zero rows at coarse Dirichlet nodes.
-//  * smoothing: nu damped Jacobi sweeps x += omega D^-1 (b - A x) before
-//    and after the coarse correction; the coarsest level (<= 128 nodes) is
+//  * smoothing: nu damped Jacobi sweeps x += W (b - A x), W = Omega D^-1,
+//    before and after the coarse correction.  The damping omega applies to
+//    the interior rows; Dirichlet rows (identity rows of A, identity columns
+//    of A^T) take omega = 1, so a cycle reproduces boundary data exactly.
+//    With omega < 1 there, the Dirichlet values would come back off by
+//    (1 - omega)^(2 nu), and the interior rows next to the boundary, whose
+//    weights scale as 1/h^2, would turn that into a residual ~1/h^2 times
+//    the data: at 1e6 nodes BiCGSTAB broke down in its first step on such
+//    right-hand sides.  W is stored (per level, FP64 and float32) in place of
+//    D^-1.  The coarsest level (<= 128 nodes) is
 //    solved with its dense inverse (Gauss-Jordan with partial pivoting, one
 //    block).
 //
@@ -94,25 +102,25 @@ __device__ __forceinline__ T row_sum(const int64_t* __restrict__ row_ptr, const 
 
 __device__ __forceinline__ bool stopped(const int* flag) { return flag && *(volatile const int*)flag != 0; }
 
-// x = omega D^-1 b (the first sweep from x = 0)
+// x = W b (the first sweep from x = 0); dinv holds W = Omega D^-1
 template <typename T, typename BT>
 __global__ void __launch_bounds__(kT) mg_first_kernel(int64_t N, const BT* __restrict__ b, const T* __restrict__ dinv,
-                                                      T omega, T* __restrict__ x, const int* flag) {
+                                                      T* __restrict__ x, const int* flag) {
     if (stopped(flag)) return;
-    MG_ELEMS(N, i) x[i] = omega * dinv[i] * (T)b[i];
+    MG_ELEMS(N, i) x[i] = dinv[i] * (T)b[i];
 }
 
-// xo = xi + omega D^-1 (b - A xi)
+// xo = xi + W (b - A xi)
 template <typename T, typename BT, typename OT, int TPR>
 __global__ void __launch_bounds__(kT) mg_jacobi_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                                        const T* __restrict__ val, int64_t N, const T* __restrict__ xi,
-                                                       const BT* __restrict__ b, const T* __restrict__ dinv, T omega,
+                                                       const BT* __restrict__ b, const T* __restrict__ dinv,
                                                        OT* __restrict__ xo, const int* flag) {
     if (stopped(flag)) return;
     const int sub = threadIdx.x & (TPR - 1);
     MG_ROWS(TPR, N, i, valid, {
         const T ax = row_sum<T, TPR>(row_ptr, col, val, xi, i, sub, valid);
-        if (valid && sub == 0) xo[i] = (OT)fmaT<T>(omega * dinv[i], (T)b[i] - ax, xi[i]);
+        if (valid && sub == 0) xo[i] = (OT)fmaT<T>(dinv[i], (T)b[i] - ax, xi[i]);
     })
 }
 
@@ -274,8 +282,30 @@ __global__ void __launch_bounds__(kT) mg_gather_kernel(const double2* __restrict
 
 // D^-1 from the diagonal of a CSR matrix (1 where the diagonal is zero or
 // missing); float copies of dinv and, if val32 != NULL, of the values.
+// Dirichlet rows of level 0: y_b += W_b (r_b - (A y)_b), W_b = 1 / a_bb.
+// Forward hierarchy (A's Dirichlet rows are identity rows): y_b = r_b, the
+// starting guess that keeps every later residual zero on Dirichlet rows.
+// Adjoint hierarchy (A^T: identity Dirichlet columns): the back substitution
+// y_b = r_b - sum_i a_ib y_i over interior rows i.  In place: a Dirichlet
+// row reads only interior entries of y and its own.
+__global__ void __launch_bounds__(kT) mg_bfix_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
+                                                     const double* __restrict__ val, int64_t N,
+                                                     const uint8_t* __restrict__ mask, const double* __restrict__ w,
+                                                     const double* __restrict__ r, double* y, const int* flag) {
+    if (stopped(flag)) return;
+    MG_ELEMS(N, i) {
+        if (!mask[i]) continue;
+        double s = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s = fma(val[k], y[col[k]], s);
+        y[i] = fma(w[i], r[i] - s, y[i]);
+    }
+}
+
+// W = Omega D^-1 of the smoother: omega / a_ii on interior rows, 1 / a_ii on
+// Dirichlet rows.
 __global__ void __launch_bounds__(kT) mg_diag_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                                      const double* __restrict__ val, int64_t N, int col_base,
+                                                     const uint8_t* __restrict__ mask, double omega,
                                                      double* __restrict__ dinv, float* __restrict__ dinv32,
                                                      int* __restrict__ bad) {
     int nb = 0;
@@ -285,7 +315,7 @@ __global__ void __launch_bounds__(kT) mg_diag_kernel(const int64_t* __restrict__
             if (col[k] - col_base == (int)i) d = val[k];
         const bool ok = d != 0.0 && isfinite(d);
         nb |= ok ? 0 : 1;
-        const double iv = ok ? 1.0 / d : 1.0;
+        const double iv = ok ? (mask[i] ? 1.0 : omega) / d : 1.0;
         dinv[i] = iv;
         dinv32[i] = __double2float_rn(iv);
     }
@@ -312,18 +342,40 @@ __global__ void __launch_bounds__(kT) mg_pfix_kernel(int64_t N, const uint8_t* _
     }
 }
 
+// CSR row pointer of the ELL prolongation (kMgK entries per row).
+__global__ void __launch_bounds__(kT) mg_ellrow_kernel(int64_t N, int64_t* __restrict__ prow) {
+    MG_ELEMS(N + 1, i) prow[i] = i * kMgK;
+}
+
 // R = scale P^T with zero rows at coarse Dirichlet nodes; float copy.
 __global__ void __launch_bounds__(kT) mg_rscale_kernel(const int64_t* __restrict__ rrow, int64_t Nc,
                                                        const uint8_t* __restrict__ cmask, double scale,
                                                        double* __restrict__ rval, float* __restrict__ rval32) {
     MG_ELEMS(Nc, c) {
-        const double f = cmask[c] ? 0.0 : scale;
+        const double f = (cmask && cmask[c]) ? 0.0 : scale;
         for (int64_t k = rrow[c]; k < rrow[c + 1]; ++k) {
             const double v = rval[k] * f;
             rval[k] = v;
             rval32[k] = __double2float_rn(v);
         }
     }
+}
+
+// Adjoint hierarchy: prolongation R^T = scale P with the columns of coarse
+// Dirichlet nodes zeroed (R zeroes their rows); float copy.
+__global__ void __launch_bounds__(kT) mg_pscale_kernel(int64_t N, const int32_t* __restrict__ pidx,
+                                                       const uint8_t* __restrict__ cmask, double scale,
+                                                       double* __restrict__ pval, float* __restrict__ pval32) {
+    const int64_t total = N * kMgK;
+    MG_ELEMS(total, e) {
+        const double v = cmask[pidx[e]] ? 0.0 : scale * pval[e];
+        pval[e] = v;
+        pval32[e] = __double2float_rn(v);
+    }
+}
+
+__global__ void __launch_bounds__(kT) mg_f32_kernel(const double* __restrict__ v, int64_t n, float* __restrict__ v32) {
+    MG_ELEMS(n, i) v32[i] = __double2float_rn(v[i]);
 }
 
 // A singular stencil at an interior node (Dirichlet rows ignore weights).
@@ -465,23 +517,23 @@ __device__ __forceinline__ float2 from_f<float2>(float v) {
 
 template <typename BT>
 __global__ void __launch_bounds__(kT) mr_first_kernel(int64_t N, int64_t row_off, int R, const BT* __restrict__ b,
-                                                      const float* __restrict__ dinv, float omega,
-                                                      float* __restrict__ x, const int* live) {
+                                                      const float* __restrict__ dinv, float* __restrict__ x,
+                                                      const int* live) {
     if (dead(live)) return;
     const int64_t total = N * R;
     MG_ELEMS(total, e) {
         const int64_t i = e / R;
         const int64_t g = (row_off + i) * R + (e - i * R);
-        x[g] = omega * dinv[i] * to_f(b[g]);
+        x[g] = dinv[i] * to_f(b[g]);
     }
 }
 
-// xo = xi + omega D^-1 (b - A xi), or (RESID) r = b - A xi
+// xo = xi + W (b - A xi), or (RESID) r = b - A xi
 template <typename BT, typename OT, bool RESID>
 __global__ void __launch_bounds__(kT) mr_row_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                                     const float* __restrict__ val, int64_t N, int64_t row_off, int R,
                                                     const float* __restrict__ xi, const BT* __restrict__ b,
-                                                    const float* __restrict__ dinv, float omega, OT* __restrict__ out,
+                                                    const float* __restrict__ dinv, OT* __restrict__ out,
                                                     const int* live) {
     if (dead(live)) return;
     const int lane = threadIdx.x & 31;
@@ -497,7 +549,7 @@ __global__ void __launch_bounds__(kT) mr_row_kernel(const int64_t* __restrict__ 
             if (on1) s1 = fmaf(a, __ldg(xi + c + lane + 32), s1);
         }
         const int64_t g = (row_off + i) * R;
-        const float di = omega * dinv[i];
+        const float di = dinv[i];
         if (on0) {
             const float r = to_f(b[g + lane]) - s0;
             out[g + lane] = from_f<OT>(RESID ? r : fmaf(di, r, xi[g + lane]));
@@ -599,6 +651,9 @@ std::vector<int64_t> level_bounds(int64_t N) {
 }
 
 struct MgScratch {
+    int64_t* a_row;  // adjoint hierarchy: the coarse operator before its transpose
+    int32_t* a_col;
+    double* a_val;
     unsigned long long* cells;
     int* sel;
     int* pos;
@@ -631,6 +686,12 @@ size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
         knn_b = std::max(knn_b, rbffd_stencils_workspace_size(std::max<int64_t>(nb[l], kMgCoarseN), kMgCoarseN));
         asm_b = std::max(asm_b, rbffd_assemble_workspace_size(nb[l]));
         tr_b = std::max(tr_b, rbffd_transpose_workspace_size(nb[l]));
+    }
+    {
+        const int64_t n1b = nb.size() > 1 ? nb[1] : 1;
+        t.a_row = c.take<int64_t>(n1b + 1);
+        t.a_col = c.take<int32_t>((size_t)n1b * kMgCoarseN);
+        t.a_val = c.take<double>((size_t)n1b * kMgCoarseN);
     }
     t.cells = c.take<unsigned long long>((size_t)(2 * N + 16));
     t.sel = c.take<int>(N);
@@ -794,14 +855,14 @@ struct Sel<float> {
 };
 
 template <typename T, typename BT, typename OT>
-void jacobi(const MgLevel& L, const T* xi, const BT* b, T omega, OT* xo, const int* flag, cudaStream_t st) {
+void jacobi(const MgLevel& L, const T* xi, const BT* b, OT* xo, const int* flag, cudaStream_t st) {
     const int g = blocks_for(L.N * L.tpr);
     const T* val = Sel<T>::val(L);
     const T* dinv = Sel<T>::dinv(L);
     switch (L.tpr) {
-        case 4: mg_jacobi_kernel<T, BT, OT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
-        case 2: mg_jacobi_kernel<T, BT, OT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
-        default: mg_jacobi_kernel<T, BT, OT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, omega, xo, flag); break;
+        case 4: mg_jacobi_kernel<T, BT, OT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
+        case 2: mg_jacobi_kernel<T, BT, OT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
+        default: mg_jacobi_kernel<T, BT, OT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
     }
 }
 
@@ -833,7 +894,6 @@ template <typename T>
 T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, double* out, const int* flag,
                cudaStream_t st, int* launches, std::vector<int>* ev) {
     const MgLevel& L = h.lv[l];
-    const T omega = (T)h.omega;
     const bool last_level = (l == h.n_levels - 1);
     const bool top = (l == 0);
     T* cur = Sel<T>::x(L);
@@ -841,9 +901,9 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
     auto launch_first = [&](T* x) {
         const int g = blocks_for(L.N);
         if (b_is_double)
-            mg_first_kernel<T, double><<<g, kT, 0, st>>>(L.N, static_cast<const double*>(bin), Sel<T>::dinv(L), omega, x, flag);
+            mg_first_kernel<T, double><<<g, kT, 0, st>>>(L.N, static_cast<const double*>(bin), Sel<T>::dinv(L), x, flag);
         else
-            mg_first_kernel<T, T><<<g, kT, 0, st>>>(L.N, static_cast<const T*>(bin), Sel<T>::dinv(L), omega, x, flag);
+            mg_first_kernel<T, T><<<g, kT, 0, st>>>(L.N, static_cast<const T*>(bin), Sel<T>::dinv(L), x, flag);
         ++*launches;
     };
     auto sweep = [&](T* xi, T* xo, double* xo64) {
@@ -852,12 +912,12 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
         const int e = (top && ev) ? prof_begin(st) : -1;
         if (b_is_double) {
             const double* b = static_cast<const double*>(bin);
-            if (xo64) jacobi<T, double, double>(L, xi, b, omega, xo64, flag, st);
-            else jacobi<T, double, T>(L, xi, b, omega, xo, flag, st);
+            if (xo64) jacobi<T, double, double>(L, xi, b, xo64, flag, st);
+            else jacobi<T, double, T>(L, xi, b, xo, flag, st);
         } else {
             const T* b = static_cast<const T*>(bin);
-            if (xo64) jacobi<T, T, double>(L, xi, b, omega, xo64, flag, st);
-            else jacobi<T, T, T>(L, xi, b, omega, xo, flag, st);
+            if (xo64) jacobi<T, T, double>(L, xi, b, xo64, flag, st);
+            else jacobi<T, T, T>(L, xi, b, xo, flag, st);
         }
         if (top && ev) {
             const int64_t bytes = L.nnz * (int64_t)(sizeof(T) + 4) + 8 * (L.N + 1) +
@@ -911,7 +971,6 @@ template <typename B0, typename O0>
 float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off, O0* out, float* x0, float* t0,
                    float* r0, float* coarse, int R, const int* live, cudaStream_t st, int* launches) {
     const MgLevel& L = h.lv[l];
-    const float omega = (float)h.omega;
     const bool top = (l == 0);
     // coarse-level buffers: [x | t | r | b] per level, levels 1.. in order
     auto level_base = [&](int lev) {
@@ -948,10 +1007,10 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off
     auto first = [&](float* x) {
         if (top)
             mr_first_kernel<B0><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const B0*>(bin),
-                                                                   L.dinv32, omega, x, live);
+                                                                   L.dinv32, x, live);
         else
             mr_first_kernel<float><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const float*>(bin),
-                                                                      L.dinv32, omega, x, live);
+                                                                      L.dinv32, x, live);
         ++*launches;
     };
     auto sweep = [&](float* xi, float* xo, bool final_top) {
@@ -959,14 +1018,14 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off
             const B0* b = static_cast<const B0*>(bin);
             if (final_top)
                 mr_row_kernel<B0, O0, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                L.dinv32, omega, out, live);
+                                                                L.dinv32, out, live);
             else
                 mr_row_kernel<B0, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                   L.dinv32, omega, xo, live);
+                                                                   L.dinv32, xo, live);
         } else {
             const float* b = static_cast<const float*>(bin);
             mr_row_kernel<float, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                  L.dinv32, omega, xo, live);
+                                                                  L.dinv32, xo, live);
         }
         ++*launches;
     };
@@ -977,10 +1036,10 @@ float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off
     }
     if (top)
         mr_row_kernel<B0, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
-                                                          static_cast<const B0*>(bin), L.dinv32, omega, rr, live);
+                                                          static_cast<const B0*>(bin), L.dinv32, rr, live);
     else
         mr_row_kernel<float, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
-                                                             static_cast<const float*>(bin), L.dinv32, omega, rr, live);
+                                                             static_cast<const float*>(bin), L.dinv32, rr, live);
     const MgLevel& C = h.lv[l + 1];
     float* cb = level_base(l + 1) + (size_t)3 * C.N * R;
     mr_restrict_kernel<<<blocks_for(C.N * 32), kT, 0, st>>>(L.rrow, L.rcol, L.rval32, C.N, R, rr + off * R, cb, live);
@@ -1036,6 +1095,17 @@ int64_t mg_fine_rows(const MgHierarchy* h) { return h ? h->lv[0].N : 0; }
 
 bool mg_has_fp32(const MgHierarchy* h) { return h && h->has32; }
 
+bool mg_is_transposed(const MgHierarchy* h) { return h && h->transposed; }
+
+int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int* flag, cudaStream_t st) {
+    if (!h || !r || !y || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;
+    const MgLevel& L = h->lv[0];
+    mg_bfix_kernel<<<blocks_for(L.N), kT, 0, st>>>(L.row_ptr, L.col, L.val, L.N, L.mask, L.dinv, r, y, flag);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev) {
     if (!h || !b || !x || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;
@@ -1045,6 +1115,9 @@ int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const 
     else cycle_level<double>(*h, 0, b, true, x, flag, st, &launches, ev);
     note_launches(launches);
     RBFFD_LAUNCH_CHECK();
+    // adjoint: the transpose of the boundary-eliminated forward cycle
+    // E_b + B (I - A E_b) is B^T followed by the Dirichlet back substitution
+    if (h->transposed) return mg_dirichlet_fix(h, b, x, flag, st);
     return RBFFD_OK;
 }
 
@@ -1065,6 +1138,53 @@ extern "C" int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes) {
     return h->n_levels;
 }
 
+extern "C" int rbffd_mg_level(const rbffd_mg* mg, int32_t level, rbffd_mg_level_info* out) {
+    using namespace rbffd;
+    if (!mg || !out) return RBFFD_ERR_INVALID_ARG;
+    MgHierarchy h;
+    std::memcpy(&h, mg, sizeof(h));
+    if (h.magic != kMgMagic || level < 0 || level >= h.n_levels) return RBFFD_ERR_INVALID_ARG;
+    const MgLevel& L = h.lv[level];
+    const bool coarsest = level == h.n_levels - 1;
+    std::memset(out, 0, sizeof(*out));
+    out->n_nodes = L.N;
+    out->xy = L.xy;
+    out->is_dirichlet = L.mask;
+    out->A.n_rows = L.N;
+    out->A.nnz = L.nnz;
+    out->A.row_ptr = L.row_ptr;
+    out->A.col = L.col;
+    out->A.val = L.val;
+    out->A.dtype = 0;
+    out->w = L.dinv;
+    out->p_idx = coarsest ? nullptr : L.pidx;
+    out->p_val = coarsest ? nullptr : L.pval;
+    out->p_k = coarsest ? 0 : kMgK;
+    out->minv = coarsest ? L.minv : nullptr;
+    return RBFFD_OK;
+}
+
+extern "C" int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32, rbffd_mg* mg,
+                                   void* ws, size_t ws_bytes, void* stream) {
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    std::memset(mg, 0, sizeof(*mg));
+    const MgHierarchy* F = mg_hierarchy(fwd);
+    if (!F || !AT || !AT->row_ptr || !AT->col || !AT->val || AT->dtype != 0) return RBFFD_ERR_INVALID_ARG;
+    if (AT32 && (!AT32->val || AT32->dtype != 1 || AT32->n_rows != AT->n_rows || AT32->nnz != AT->nnz ||
+                 AT32->row_ptr != AT->row_ptr || AT32->col != AT->col))
+        return RBFFD_ERR_INVALID_ARG;
+    return mg_adjoint_of(*F, AT, AT32 ? static_cast<const float*>(AT32->val) : nullptr, mg, ws, ws_bytes,
+                         as_stream(stream));
+}
+
+extern "C" int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x, void* stream) {
+    using namespace rbffd;
+    const MgHierarchy* h = mg_hierarchy(mg);
+    if (!h || !b || !x || b == x) return RBFFD_ERR_INVALID_ARG;
+    return mg_apply(h, fp32 != 0, b, x, nullptr, as_stream(stream));
+}
+
 extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
                               const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
                               size_t ws_bytes, void* stream) {
@@ -1079,12 +1199,124 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
         return RBFFD_ERR_INVALID_ARG;
     return mg_setup_core(xy, is_dirichlet, N, A->row_ptr, A->col, static_cast<const double*>(A->val),
                          A32 ? static_cast<const float*>(A32->val) : nullptr, A->nnz, 0, nu, omega, mg, ws, ws_bytes,
-                         as_stream(stream));
+                         as_stream(stream), false);
+}
+
+extern "C" int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* AT,
+                                      const rbffd_csr* AT32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
+                                      size_t ws_bytes, void* stream) {
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    std::memset(mg, 0, sizeof(*mg));
+    if (!xy || !is_dirichlet || !AT || !AT->row_ptr || !AT->col || !AT->val || AT->dtype != 0 || N <= 0 ||
+        N > 0x7fffffffLL || AT->n_rows != N || AT->nnz <= 0)
+        return RBFFD_ERR_INVALID_ARG;
+    if (AT32 && (!AT32->val || AT32->dtype != 1 || AT32->n_rows != N || AT32->nnz != AT->nnz ||
+                 AT32->row_ptr != AT->row_ptr || AT32->col != AT->col))
+        return RBFFD_ERR_INVALID_ARG;
+    return mg_setup_core(xy, is_dirichlet, N, AT->row_ptr, AT->col, static_cast<const double*>(AT->val),
+                         AT32 ? static_cast<const float*>(AT32->val) : nullptr, AT->nnz, 0, nu, omega, mg, ws,
+                         ws_bytes, as_stream(stream), true);
+}
+
+// The adjoint hierarchy of a built forward one: the coarse node sets, the
+// smoother weights and the interpolation are the forward ones (copied), the
+// level operators are transposed, the transfers swapped, and the coarsest
+// transposed operator inverted; the same arrays rbffd_mg_setup_adjoint
+// builds from scratch, at the cost of the transposes.
+int rbffd::mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg, void* ws,
+                         size_t ws_bytes, cudaStream_t st) {
+    std::memset(mg, 0, sizeof(*mg));
+    const MgLevel& F0 = F.lv[0];
+    const int64_t N = F0.N;
+    if (F.transposed || F.col_base != 0 || AT->n_rows != N || AT->nnz != F0.nnz) return RBFFD_ERR_INVALID_ARG;
+    if (val32 && !F.has32) return RBFFD_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
+    if (ws_bytes < mg_layout(nullptr, N, nullptr, nullptr)) return RBFFD_ERR_WORKSPACE;
+    MgHierarchy h{};
+    MgScratch s{};
+    mg_layout(ws, N, &h, &s);
+    h.nu = F.nu;
+    h.omega = F.omega;
+    h.has32 = val32 ? 1 : 0;
+    h.col_base = 0;
+    h.transposed = 1;
+    RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
+    MgLevel& L0 = h.lv[0];
+    L0.N = N;
+    L0.row_ptr = AT->row_ptr;
+    L0.col = AT->col;
+    L0.val = static_cast<const double*>(AT->val);
+    L0.val32 = val32;
+    L0.nnz = AT->nnz;
+    L0.tpr = tpr_for(N, AT->nnz);
+    L0.xy = F0.xy;
+    L0.mask = F0.mask;
+    const int n_levels = F.n_levels;
+    for (int l = 0; l < n_levels; ++l) {
+        MgLevel& L = h.lv[l];
+        const MgLevel& FL = F.lv[l];
+        // W: the diagonal and the Dirichlet rows are those of the forward level
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.dinv, FL.dinv, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.dinv32, FL.dinv32, sizeof(float) * L.N, cudaMemcpyDeviceToDevice, st));
+        if (l == n_levels - 1) {
+            int rc = dense_inverse(L, 0, s, st);
+            if (rc != RBFFD_OK) return rc;
+            break;
+        }
+        MgLevel& C = h.lv[l + 1];
+        const MgLevel& FC = F.lv[l + 1];
+        const int64_t nc = FC.N;
+        C.N = nc;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(C.xy), FC.xy, sizeof(double) * 2 * nc,
+                                       cudaMemcpyDeviceToDevice, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(const_cast<uint8_t*>(C.mask), FC.mask, nc, cudaMemcpyDeviceToDevice, st));
+        rbffd_csr Ac{};
+        Ac.n_rows = nc;
+        Ac.nnz = FC.nnz;
+        Ac.row_ptr = FC.row_ptr;
+        Ac.col = FC.col;
+        Ac.val = FC.val;
+        Ac.dtype = 0;
+        int rc = rbffd_transpose(&Ac, const_cast<int64_t*>(C.row_ptr), const_cast<int*>(C.col),
+                                 const_cast<double*>(C.val), s.tr_ws, s.tr_bytes, st);
+        if (rc != RBFFD_OK) return rc;
+        mg_f32_kernel<<<blocks_for(FC.nnz), kT, 0, st>>>(C.val, FC.nnz, const_cast<float*>(C.val32));
+        C.nnz = FC.nnz;
+        C.tpr = tpr_for(nc, FC.nnz);
+        // transfers: R = P^T (raw), prolongation R_fwd^T = (N_c / N_f) P
+        // without the coarse Dirichlet columns
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.pidx, FL.pidx, sizeof(int32_t) * L.N * kMgK, cudaMemcpyDeviceToDevice, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.pval, FL.pval, sizeof(double) * L.N * kMgK, cudaMemcpyDeviceToDevice, st));
+        mg_ellrow_kernel<<<blocks_for(L.N + 1), kT, 0, st>>>(L.N, s.prow);
+        rbffd_csr P{};
+        P.n_rows = L.N;
+        P.nnz = L.N * kMgK;
+        P.row_ptr = s.prow;
+        P.col = L.pidx;
+        P.val = L.pval;
+        P.dtype = 0;
+        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
+        mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
+        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, (double)nc / (double)L.N,
+                                                                 L.pval, L.pval32);
+        note_launches(4);
+        RBFFD_LAUNCH_CHECK();
+        L.rtpr = tpr_for(nc, L.N * kMgK);
+    }
+    int flags[2] = {0, 0};
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags[0]) return RBFFD_ERR_SINGULAR_STENCIL;
+    h.n_levels = n_levels;
+    h.magic = kMgMagic;
+    std::memcpy(mg, &h, sizeof(h));
+    return RBFFD_OK;
 }
 
 int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t N, const int64_t* row_ptr,
                          const int* col, const double* val, const float* val32, int64_t nnz, int col_base, int nu,
-                         double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st) {
+                         double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed) {
     using namespace rbffd;
     std::memset(mg, 0, sizeof(*mg));
     if (nu < 1 || nu > 8 || !(omega > 0.0 && omega < 1.0)) return RBFFD_ERR_INVALID_ARG;
@@ -1101,6 +1333,7 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
     h.omega = omega;
     h.has32 = val32 ? 1 : 0;
     h.col_base = col_base;
+    h.transposed = transposed ? 1 : 0;
     RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
 
     MgLevel& L0 = h.lv[0];
@@ -1113,8 +1346,8 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
     L0.tpr = tpr_for(N, nnz);
     L0.xy = xy;
     L0.mask = is_dirichlet;
-    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, col_base, L0.dinv, L0.dinv32,
-                                                 s.flags + 1);
+    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, col_base, L0.mask, omega, L0.dinv,
+                                                 L0.dinv32, s.flags + 1);
     note_launches(1);
     RBFFD_LAUNCH_CHECK();
 
@@ -1137,18 +1370,38 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
         if ((rc = rbffd_weights(C.xy, s.sidx, nc, kMgCoarseN, kMgCoarseM, s.sw, s.sstat, st)) != RBFFD_OK) return rc;
         mg_count_kernel<<<blocks_for(nc), kT, 0, st>>>(s.sstat, C.mask, nc, s.flags);
         note_launches(1);
-        int64_t* crow = const_cast<int64_t*>(C.row_ptr);
+        // (adjoint hierarchy: assembled into scratch, then transposed into the level)
+        int64_t* crow = transposed ? s.a_row : const_cast<int64_t*>(C.row_ptr);
         if ((rc = rbffd_assemble_pattern(C.mask, nc, kMgCoarseN, crow, s.asm_ws, s.asm_bytes, st)) != RBFFD_OK)
             return rc;
         int64_t cnnz = 0;
         RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnnz, crow + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-        if ((rc = rbffd_assemble(s.sidx, s.sw, C.mask, nc, kMgCoarseN, crow, cnnz, const_cast<int*>(C.col),
-                                 const_cast<double*>(C.val), const_cast<float*>(C.val32), st)) != RBFFD_OK)
-            return rc;
+        if (!transposed) {
+            if ((rc = rbffd_assemble(s.sidx, s.sw, C.mask, nc, kMgCoarseN, crow, cnnz, const_cast<int*>(C.col),
+                                     const_cast<double*>(C.val), const_cast<float*>(C.val32), st)) != RBFFD_OK)
+                return rc;
+        } else {
+            if ((rc = rbffd_assemble(s.sidx, s.sw, C.mask, nc, kMgCoarseN, crow, cnnz, s.a_col, s.a_val, nullptr,
+                                     st)) != RBFFD_OK)
+                return rc;
+            rbffd_csr Ac{};
+            Ac.n_rows = nc;
+            Ac.nnz = cnnz;
+            Ac.row_ptr = s.a_row;
+            Ac.col = s.a_col;
+            Ac.val = s.a_val;
+            Ac.dtype = 0;
+            if ((rc = rbffd_transpose(&Ac, const_cast<int64_t*>(C.row_ptr), const_cast<int*>(C.col),
+                                      const_cast<double*>(C.val), s.tr_ws, s.tr_bytes, st)) != RBFFD_OK)
+                return rc;
+            mg_f32_kernel<<<blocks_for(cnnz), kT, 0, st>>>(C.val, cnnz, const_cast<float*>(C.val32));
+            note_launches(1);
+        }
         C.nnz = cnnz;
         C.tpr = tpr_for(nc, cnnz);
-        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.dinv, C.dinv32, s.flags + 1);
+        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.mask, omega, C.dinv, C.dinv32,
+                                                      s.flags + 1);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         // prolongation: interpolation from the kMgK nearest coarse nodes
@@ -1167,8 +1420,16 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
         P.val = L.pval;
         P.dtype = 0;
         if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
-        mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, C.mask, (double)nc / (double)L.N, L.rval,
-                                                        L.rval32);
+        const double cscale = (double)nc / (double)L.N;
+        if (!transposed) {
+            mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, C.mask, cscale, L.rval, L.rval32);
+        } else {
+            // the transpose of the forward cycle: restrict with P^T, prolong
+            // with R^T = (N_c / N_f) P without the coarse Dirichlet columns
+            mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
+            mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, cscale, L.pval, L.pval32);
+            note_launches(1);
+        }
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         L.rtpr = tpr_for(nc, L.N * kMgK);

@@ -73,6 +73,38 @@ class MgHandle(ctypes.Structure):
 MG_MAX_LEVELS = 24
 
 
+class MgLevelInfo(ctypes.Structure):
+    """rbffd_mg_level_info: device pointers into a built hierarchy."""
+
+    _fields_ = [
+        ("n_nodes", ctypes.c_int64),
+        ("xy", ctypes.c_void_p),
+        ("is_dirichlet", ctypes.c_void_p),
+        ("A", Csr),
+        ("w", ctypes.c_void_p),
+        ("p_idx", ctypes.c_void_p),
+        ("p_val", ctypes.c_void_p),
+        ("p_k", ctypes.c_int32),
+        ("minv", ctypes.c_void_p),
+    ]
+
+
+class _DeviceArray:
+    """A raw device pointer seen as a torch tensor (__cuda_array_interface__);
+    the memory stays owned by whoever allocated it."""
+
+    _TYPESTR = {torch.float64: "<f8", torch.int64: "<i8", torch.int32: "<i4", torch.uint8: "|u1"}
+
+    def __init__(self, ptr: int, shape: tuple, dtype: torch.dtype):
+        self.__cuda_array_interface__ = {"shape": tuple(int(d) for d in shape), "typestr": self._TYPESTR[dtype],
+                                         "data": (int(ptr), False), "version": 2, "strides": None}
+
+
+def _device_copy(ptr: int, shape: tuple, dtype: torch.dtype, device: torch.device) -> torch.Tensor:
+    with torch.cuda.device(device):
+        return torch.as_tensor(_DeviceArray(ptr, shape, dtype), device=device).clone()
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_double),
@@ -154,6 +186,7 @@ SIGNATURES = {
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
     "rbffd_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
+    "rbffd_misfit_grad": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "rbffd_batched_workspace_size": (_SZ, [ctypes.POINTER(BatchDesc), _I32, _I32, ctypes.POINTER(SolveOpts)]),
     "rbffd_solve_batched": (ctypes.c_int, [ctypes.POINTER(BatchDesc), _I32, _VP, _VP, _VP, _VP, _I32, _VP,
                                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
@@ -164,7 +197,15 @@ SIGNATURES = {
     "rbffd_mg_workspace_size": (_SZ, [_I64, _I64]),
     "rbffd_mg_setup": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(Csr), ctypes.POINTER(Csr), _I32, _D,
                                       ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
+    "rbffd_mg_setup_adjoint": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(Csr), ctypes.POINTER(Csr), _I32, _D,
+                                              ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
     "rbffd_mg_levels": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(ctypes.c_int64)]),
+    "rbffd_mg_level": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.c_int32, ctypes.POINTER(MgLevelInfo)]),
+    "rbffd_mg_adjoint_of": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
+                                           ctypes.POINTER(MgHandle), ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p]),
+    "rbffd_mg_apply": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "rbffd_diag_recip": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP]),
     "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
@@ -387,38 +428,91 @@ class Multigrid:
     Holds the host handle and the device workspace it points into."""
 
     def __init__(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2,
-                 omega: float = 0.6, ws: torch.Tensor | None = None):
+                 omega: float = 0.6, ws: torch.Tensor | None = None, adjoint: bool = False):
+        """adjoint=True: A is A^T (the adjoint solve's matrix) and the hierarchy
+        is the transposed one (rbffd_mg_setup_adjoint)."""
         N = xy.shape[0]
         _require(xy, torch.float64, "xy", (N, 2))
         _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
-        lib = load()
         self.handle = MgHandle()
         if ws is None:
             ws = mg_workspace(N, A.nnz, xy.device)
         self.ws = ws
-        self.A = A
-        c64 = A.c64()
-        c32 = A.c32()
-        _check(lib.rbffd_mg_setup(_ptr(xy), _ptr(is_dirichlet), N, ctypes.byref(c64),
-                                  ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
-                                  ctypes.byref(self.handle), _ptr(ws), ws.numel(), _stream(xy.device)),
-               "rbffd_mg_setup")
+        self.adjoint = adjoint
+        self.setup(xy, is_dirichlet, A, nu, omega)
 
     def setup(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2, omega: float = 0.6):
-        """Rebuilds the hierarchy in the same workspace (same node count)."""
+        """(Re)builds the hierarchy in the same workspace (same node count)."""
         lib = load()
         c64 = A.c64()
         c32 = A.c32()
         self.A = A
-        _check(lib.rbffd_mg_setup(_ptr(xy), _ptr(is_dirichlet), xy.shape[0], ctypes.byref(c64),
-                                  ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
-                                  ctypes.byref(self.handle), _ptr(self.ws), self.ws.numel(), _stream(xy.device)),
-               "rbffd_mg_setup")
+        fn = lib.rbffd_mg_setup_adjoint if self.adjoint else lib.rbffd_mg_setup
+        _check(fn(_ptr(xy), _ptr(is_dirichlet), xy.shape[0], ctypes.byref(c64),
+                  ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
+                  ctypes.byref(self.handle), _ptr(self.ws), self.ws.numel(), _stream(xy.device)),
+               "rbffd_mg_setup_adjoint" if self.adjoint else "rbffd_mg_setup")
+
+    @classmethod
+    def adjoint_of(cls, fwd: "Multigrid", AT: "CsrMatrix", ws: torch.Tensor | None = None) -> "Multigrid":
+        """The adjoint hierarchy of the built forward hierarchy fwd, for AT = A^T
+        (rbffd_mg_adjoint_of: fwd's coarse levels reused, operators transposed)."""
+        self = cls.__new__(cls)
+        self.handle = MgHandle()
+        self.ws = ws if ws is not None else mg_workspace(AT.n_rows, AT.nnz, AT.val.device)
+        self.adjoint = True
+        self.rebuild_from(fwd, AT)
+        return self
+
+    def rebuild_from(self, fwd: "Multigrid", AT: "CsrMatrix"):
+        """(Re)builds this adjoint hierarchy from fwd (rbffd_mg_adjoint_of)."""
+        c64, c32 = AT.c64(), AT.c32()
+        self.A = AT
+        _check(load().rbffd_mg_adjoint_of(ctypes.byref(fwd.handle), ctypes.byref(c64),
+                                          ctypes.byref(c32) if c32 is not None else None, ctypes.byref(self.handle),
+                                          _ptr(self.ws), self.ws.numel(), _stream(AT.val.device)),
+               "rbffd_mg_adjoint_of")
 
     def levels(self) -> list:
         arr = (ctypes.c_int64 * MG_MAX_LEVELS)()
         n = load().rbffd_mg_levels(ctypes.byref(self.handle), arr)
         return [int(arr[i]) for i in range(n)]
+
+    def apply(self, b: torch.Tensor, out: torch.Tensor | None = None, fp32: bool = False) -> torch.Tensor:
+        """out = M b, one preconditioner application (rbffd_mg_apply)."""
+        N = self.levels()[0]
+        _require(b, torch.float64, "b", (N,))
+        if out is None:
+            out = torch.empty_like(b)
+        _require(out, torch.float64, "out", (N,))
+        _check(load().rbffd_mg_apply(ctypes.byref(self.handle), 1 if fp32 else 0, _ptr(b), _ptr(out),
+                                     _stream(b.device)), "rbffd_mg_apply")
+        return out
+
+    def level(self, level: int) -> dict:
+        """Copies of one level's arrays (rbffd_mg_level): xy, is_dirichlet, the
+        operator A (CsrMatrix), smoother weights w, prolongation p_idx/p_val
+        into this level (None at the coarsest) and minv (coarsest only)."""
+        info = MgLevelInfo()
+        _check(load().rbffd_mg_level(ctypes.byref(self.handle), int(level), ctypes.byref(info)), "rbffd_mg_level")
+        dev = self.ws.device
+        n, nnz = info.n_nodes, info.A.nnz
+        out = {
+            "n_nodes": n,
+            "xy": _device_copy(info.xy, (n, 2), torch.float64, dev),
+            "is_dirichlet": _device_copy(info.is_dirichlet, (n,), torch.uint8, dev),
+            "A": CsrMatrix(_device_copy(info.A.row_ptr, (n + 1,), torch.int64, dev),
+                           _device_copy(info.A.col, (nnz,), torch.int32, dev),
+                           _device_copy(info.A.val, (nnz,), torch.float64, dev)),
+            "w": _device_copy(info.w, (n,), torch.float64, dev),
+            "p_idx": None, "p_val": None, "minv": None,
+        }
+        if info.p_k:
+            out["p_idx"] = _device_copy(info.p_idx, (n, info.p_k), torch.int32, dev)
+            out["p_val"] = _device_copy(info.p_val, (n, info.p_k), torch.float64, dev)
+        if info.minv:
+            out["minv"] = _device_copy(info.minv, (n, n), torch.float64, dev)
+        return out
 
 
 class ExplicitLoop:
@@ -546,6 +640,20 @@ def rbffd_solve_adjoint(AT: CsrMatrix, is_dirichlet: torch.Tensor, dLdu: torch.T
     d = info.as_dict()
     d["status_code"] = st
     return lam, dLdf, dLdg, d
+
+
+def rbffd_misfit_grad(u: torch.Tensor, u_target: torch.Tensor, is_dirichlet: torch.Tensor,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    """dL/du of L = sum_interior (u - u_target)^2."""
+    N = u.shape[0]
+    _require(u, torch.float64, "u", (N,))
+    _require(u_target, torch.float64, "u_target", (N,))
+    _require(is_dirichlet, torch.uint8, "is_dirichlet", (N,))
+    if out is None:
+        out = torch.empty_like(u)
+    _check(load().rbffd_misfit_grad(_ptr(u), _ptr(u_target), _ptr(is_dirichlet), N, _ptr(out), _stream(u.device)),
+           "rbffd_misfit_grad")
+    return out
 
 
 # --------------------------------------------------------------- profiling --

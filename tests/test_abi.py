@@ -146,6 +146,15 @@ def test_multigrid_argument_errors(cdll):
     assert setup(0x7000, 1000, A, None, 0, 0.5, 0x8000, ws) == INVALID  # nu
     assert setup(0x7000, 1000, A, None, 2, 1.0, 0x8000, ws) == INVALID  # omega
     assert cdll.rbffd_mg_levels(ctypes.byref(h), None) == 0  # nothing built
+    lv = rbffd.MgLevelInfo()
+    assert cdll.rbffd_mg_level(ctypes.byref(h), 0, ctypes.byref(lv)) == INVALID
+    assert cdll.rbffd_mg_level(None, 0, ctypes.byref(lv)) == INVALID
+    assert cdll.rbffd_mg_apply(ctypes.byref(h), 0, 0x4000, 0x5000, None) == INVALID
+    assert cdll.rbffd_mg_apply(None, 0, 0x4000, 0x5000, None) == INVALID
+    h2 = rbffd.MgHandle()
+    assert cdll.rbffd_mg_adjoint_of(ctypes.byref(h), ctypes.byref(A), None, ctypes.byref(h2), 0x8000, ws,
+                                    None) == INVALID  # forward hierarchy never built
+    assert cdll.rbffd_mg_adjoint_of(ctypes.byref(h), ctypes.byref(A), None, None, 0x8000, ws, None) == INVALID
     # a solve asking for multigrid with a handle that was never built
     opts = rbffd.make_opts()
     opts.precond = 1
@@ -156,7 +165,7 @@ def test_multigrid_argument_errors(cdll):
     opts.precond = 2
     assert cdll.rbffd_solve(ctypes.byref(A), None, 0x4000, 0x5000, ctypes.byref(opts), ctypes.byref(info),
                             0x6000, 1 << 30, None) == INVALID
-    # the adjoint solve takes no hierarchy
+    # an adjoint solve with a hierarchy that was never built
     opts.precond = 1
     assert cdll.rbffd_solve_adjoint(ctypes.byref(A), None, 0x7000, 0x4000, 0x5000, None, None,
                                     ctypes.byref(opts), ctypes.byref(info), 0x6000, 1 << 30, None) == INVALID

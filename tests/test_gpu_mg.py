@@ -157,3 +157,209 @@ def test_mg_full_size_sampled_residual(lib):
     assert (np.abs(r) <= bound).all()
     # and the discrete solution approximates sin(pi x) sin(pi y) to the scheme's accuracy
     assert np.abs(u - u_ex).max() <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("h,m,n", [(0.03, 4, 30), (0.04, 6, 56)])
+def test_mg_adjoint_vs_oracle(lib, h, m, n, precision):
+    """The adjoint solve A^T lambda = dL/du with the transposed hierarchy:
+    lambda and the gradients match the oracle's adjoint (direct solve with
+    A^T) to 1e-8, in few iterations."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, idx, w, rp, col, val, b = _system(h, m, n)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    A = rbffd.rbffd_assemble(T(idx), T(w), mask, want_f32=True)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    rng = np.random.default_rng(5)
+    dLdu = rng.standard_normal(d.N) * (d.is_dirichlet == 0)
+    mga = rbffd.Multigrid(xy, mask, AT, adjoint=True)
+    lam, dLdf, dLdg, info = rbffd.rbffd_solve_adjoint(AT, mask, T(dLdu),
+                                                      opts=rbffd.make_opts(tol=1e-10, precision=precision, mg=mga))
+    gf, gg, lam_ref = oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, dLdu)
+    assert info["status"] == 0 and info["iters"] <= 40, info
+    scale = np.abs(lam_ref).max()
+    assert np.abs(lam.cpu().numpy() - lam_ref).max() <= 1e-8 * scale
+    assert np.abs(dLdf.cpu().numpy() - gf).max() <= 1e-8 * scale
+    assert np.abs(dLdg.cpu().numpy() - gg).max() <= 1e-8 * scale
+
+
+def test_mg_forward_and_adjoint_hierarchies_are_not_interchangeable(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    d, idx, w, rp, col, val, b = _system(0.05, 2, 12)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    A = rbffd.rbffd_assemble(T(idx), T(w), mask)
+    AT = rbffd.rbffd_transpose(A)
+    fwd = rbffd.Multigrid(xy, mask, A)
+    adj = rbffd.Multigrid(xy, mask, AT, adjoint=True)
+    _, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(mg=adj), raise_on_error=False)
+    assert info["status_code"] == 1
+    _, _, _, info = rbffd.rbffd_solve_adjoint(AT, mask, T(b), opts=rbffd.make_opts(mg=fwd), raise_on_error=False)
+    assert info["status_code"] == 1
+
+
+def test_misfit_grad_bitexact(lib):
+    from paper_2107_03632_gb300 import rbffd
+
+    rng = np.random.default_rng(9)
+    N = 100003
+    u, ut = rng.standard_normal(N), rng.standard_normal(N)
+    mask = (rng.random(N) < 0.1).astype(np.uint8)
+    g = rbffd.rbffd_misfit_grad(T(u), T(ut), T(mask)).cpu().numpy()
+    assert np.array_equal(g, np.where(mask == 1, 0.0, 2.0 * (u - ut)))
+
+
+def _gpu_system(h, m, n, seed=2107):
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(h, seed)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    idx = rbffd.rbffd_stencils(xy, n)
+    w, _ = rbffd.rbffd_weights(xy, idx, m)
+    A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
+    return d, xy, mask, A
+
+
+def _scipy(A, n):
+    import scipy.sparse as sp
+
+    return sp.csr_matrix((A.val.cpu().numpy(), A.col.cpu().numpy(), A.row_ptr.cpu().numpy()), shape=(n, n))
+
+
+def test_mg_level_views_and_transposed_hierarchy(lib):
+    """Level views: level 0 is the caller's operator; every coarse node is a
+    fine node; the smoother weights are omega / a_ii inside and 1 / a_ii on
+    Dirichlet rows; the coarsest level carries the inverse of its operator.
+    The adjoint hierarchy holds the transposes of the forward operators and
+    R^T = (N_c / N_f) P without the coarse Dirichlet columns as prolongation."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, xy, mask, A = _gpu_system(0.01, 4, 30)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A, omega=0.6)
+    mga = rbffd.Multigrid(xy, mask, AT, omega=0.6, adjoint=True)
+    sizes = mg.levels()
+    assert sizes == mga.levels() and len(sizes) >= 3
+    prev = None
+    for l, n in enumerate(sizes):
+        f, a = mg.level(l), mga.level(l)
+        assert f["n_nodes"] == n
+        Af, Aa = _scipy(f["A"], n), _scipy(a["A"], n)
+        if l == 0:
+            assert (Af != _scipy(A, n)).nnz == 0
+        # the adjoint's operator is the forward one transposed, bit for bit
+        assert (Af.T.tocsr() != Aa).nnz == 0
+        m = f["is_dirichlet"].cpu().numpy().astype(bool)
+        diag = Af.diagonal()
+        want = np.where(m, 1.0, 0.6) / diag
+        assert np.allclose(f["w"].cpu().numpy(), want, rtol=1e-15, atol=0)
+        assert np.all(diag[m] == 1.0)
+        if prev is not None:
+            # coarse nodes are a subset of the finer level's nodes
+            fine = {tuple(p) for p in prev["xy"].cpu().numpy()}
+            assert all(tuple(p) in fine for p in f["xy"].cpu().numpy())
+            # prolongation into the finer level: adjoint = scaled forward,
+            # coarse Dirichlet columns zeroed
+            pv, av = prev["fwd_p_val"], prev["adj_p_val"]
+            pidx = prev["p_idx"]
+            scale = n / prev["n_nodes"]
+            cm = m[pidx]
+            assert np.array_equal(av, np.where(cm, 0.0, pv * scale))
+        if l == len(sizes) - 1:
+            assert f["p_idx"] is None and f["minv"] is not None
+            Ad = Af.toarray()
+            assert np.abs(f["minv"].cpu().numpy() @ Ad - np.eye(n)).max() <= 1e-10
+        else:
+            assert f["minv"] is None
+            assert torch.equal(f["p_idx"], a["p_idx"])
+        prev = {"xy": f["xy"], "n_nodes": n,
+                "p_idx": None if f["p_idx"] is None else f["p_idx"].cpu().numpy(),
+                "fwd_p_val": None if f["p_val"] is None else f["p_val"].cpu().numpy(),
+                "adj_p_val": None if a["p_val"] is None else a["p_val"].cpu().numpy()}
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_mg_adjoint_cycle_is_exact_transpose(lib, fp32):
+    """The adjoint preconditioner is the transpose of the forward one on the
+    residuals a forward solve produces (zero on Dirichlet rows):
+    r . (B s) == (M^T r) . s for every r and every s with s_b = 0, and it maps
+    Dirichlet entries as the back substitution x_b = r_b - sum_i a_ib x_i."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, xy, mask, A = _gpu_system(0.006, 6, 56)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A)
+    mga = rbffd.Multigrid(xy, mask, AT, adjoint=True)
+    rng = np.random.default_rng(5)
+    m = d.is_dirichlet.astype(bool)
+    for _ in range(3):
+        r = rng.standard_normal(d.N)
+        s = np.where(m, 0.0, rng.standard_normal(d.N))
+        Bs = mg.apply(T(s), fp32=fp32).cpu().numpy()
+        Mr = mga.apply(T(r), fp32=fp32).cpu().numpy()
+        lhs, rhs = r @ Bs, Mr @ s
+        tol = 1e-5 if fp32 else 1e-12
+        assert abs(lhs - rhs) <= tol * np.linalg.norm(r) * np.linalg.norm(Bs), (lhs, rhs)
+        assert np.all(Bs[m] == 0.0)  # boundary-free in, boundary-free out
+        # Dirichlet entries of M^T r: the back substitution
+        ATs = _scipy(AT, d.N)
+        resid = r - ATs @ Mr
+        assert np.abs(resid[m]).max() <= 1e-12 * np.abs(r).max() * 100
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mg_boundary_data_and_adjoint_at_1M(lib, precision):
+    """Right-hand sides with boundary data (a Fourier source with the
+    manufactured boundary values) and the adjoint of a misfit at ~1e6 nodes:
+    both converge to 1e-10 within a few dozen iterations."""
+    from fixtures import fourier_sources
+    from paper_2107_03632_gb300 import rbffd
+
+    d, xy, mask, A = _gpu_system(1.7725e-3, 4, 30)
+    _, f, g = manufactured(d.xy)
+    fs = fourier_sources(d.xy, 1, 2108)[0]
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A)
+    mga = rbffd.Multigrid(xy, mask, AT, adjoint=True)
+    o = rbffd.make_opts(tol=1e-10, precision=precision, mg=mg)
+    u, i1 = rbffd.rbffd_solve(A, rbffd.rbffd_rhs(T(f), T(g), mask), opts=o)
+    us, i2 = rbffd.rbffd_solve(A, rbffd.rbffd_rhs(T(fs), T(g), mask), opts=o)
+    for info in (i1, i2):
+        assert info["status"] == 0 and info["iters"] <= 30, info
+    dLdu = rbffd.rbffd_misfit_grad(u, us, mask)
+    lam, dLdf, dLdg, ia = rbffd.rbffd_solve_adjoint(AT, mask, dLdu, None,
+                                                   rbffd.make_opts(tol=1e-10, precision=precision, mg=mga))
+    assert ia["status"] == 0 and ia["iters"] <= 40, ia
+    # check A^T lambda = dL/du in FP64 on the host
+    ATs = _scipy(AT, d.N)
+    lam_h, g_h = lam.cpu().numpy(), dLdu.cpu().numpy()
+    assert np.linalg.norm(g_h - ATs @ lam_h) <= 1e-10 * np.linalg.norm(g_h) * 1.01
+
+
+def test_mg_adjoint_of_forward_equals_adjoint_setup(lib):
+    """rbffd_mg_adjoint_of (coarse levels reused from the forward hierarchy)
+    holds the same values as rbffd_mg_setup_adjoint, bit for bit, and applies
+    the same preconditioner."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, xy, mask, A = _gpu_system(0.008, 4, 30)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A)
+    m1 = rbffd.Multigrid(xy, mask, AT, adjoint=True)
+    m2 = rbffd.Multigrid.adjoint_of(mg, AT)
+    assert m1.levels() == m2.levels()
+    for l in range(len(m1.levels())):
+        a, b = m1.level(l), m2.level(l)
+        for k in ("xy", "is_dirichlet", "w", "p_idx", "p_val", "minv"):
+            assert (a[k] is None) == (b[k] is None), k
+            if a[k] is not None:
+                assert torch.equal(a[k], b[k]), (l, k)
+        for k in ("row_ptr", "col", "val"):
+            assert torch.equal(getattr(a["A"], k), getattr(b["A"], k)), (l, k)
+    r = T(np.random.default_rng(2).standard_normal(d.N))
+    for fp32 in (False, True):
+        assert torch.equal(m1.apply(r, fp32=fp32), m2.apply(r, fp32=fp32))
+    # the forward hierarchy may be rebuilt afterwards: m2 owns its arrays
+    mg.setup(xy, mask, A)
+    assert torch.equal(m1.apply(r), m2.apply(r))
