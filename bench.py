@@ -205,6 +205,63 @@ def weights_flops(n: int, m: int) -> float:
 # FP64 (non-tensor and tensor alike on this chip) peak from unit counts and the
 # maximum clock: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz.
 FP64_PEAK_TFLOPS_UNITS = 152 * 2 * 2 * 2070e6 / 1e12
+# FP32 pipe: 152 SMs x 128 lanes x 2070 MHz, in tera lane-instructions per second.
+FP32_PEAK_TINSTR_UNITS = 152 * 128 * 2070e6 / 1e12
+
+# FP32 instructions of one double-float operation of the weight kernel, as
+# written (df32.cuh and the NsDF policy): c - a b 15, a b 7, a + b 20,
+# a^-1/2 20 (plus one MUFU op), 1/a 10.
+DF_INSTR = {"nfma": 15, "mul": 7, "add": 20, "rsqrt": 20, "rcp": 10}
+
+
+def weights_df_ops(n: int, m: int) -> dict:
+    """Double-float operations per node of the null-space weight solve (the
+    same steps as weights_flops): Gauss-Jordan on P, the r^3 matrix and
+    f = 9|x|, T, u, S, t, Cholesky, the two substitutions and w = w0 + Z z."""
+    s = (m + 1) * (m + 2) // 2
+    q = n - s
+    pairs = n * (n - 1) // 2
+    gj_rows = s * n - s * (s - 1) // 2
+    chol_tr = sum((q - c - 1) * (q - c) // 2 for c in range(q))
+    return {
+        "nfma": (s - 1) * gj_rows + s * q * s + n * s + (q * (q + 1) // 2) * 2 * s + q * s + chol_tr
+                + q * (q - 1) + s * q,
+        "mul": gj_rows + 4 * pairs + 4 * n + q * (q - 1) // 2 + q + 2 * q + n * 2 * m,
+        "add": 3 * pairs + 2 * n + s * q + n + q * (q + 1) // 2 + q + s,
+        "rsqrt": pairs + n + q,
+        "rcp": s,
+    }
+
+
+def weights_df_instr(n: int, m: int) -> float:
+    ops = weights_df_ops(n, m)
+    return float(sum(DF_INSTR[k] * v for k, v in ops.items()))
+
+
+def weights_roofline(kernel_name: str, n: int, m: int, N: int, ms: float, extra: dict) -> dict:
+    """Roofline of the weight solve: FP64 kernels against the FP64 units'
+    peak (counted flops); double-float kernels against the FP32 pipe's peak
+    (FP32 instructions of the df operations), with the FP64-equivalent rate
+    beside it."""
+    fl = weights_flops(n, m)
+    f64_equiv = fl * N / (ms * 1e-3) / 1e12
+    if "df" in kernel_name:
+        ins = weights_df_instr(n, m)
+        ach = ins * N / (ms * 1e-3) / 1e12
+        out = {"kernel": f"weights_ns_kernel, double-float ({kernel_name}), m={m}, n={n}", "bound": "alu",
+               "achieved": ach, "peak": FP32_PEAK_TINSTR_UNITS, "unit": "T FP32 lane-instr/s",
+               "frac": ach / FP32_PEAK_TINSTR_UNITS,
+               "peak_kind": "FP32 lanes x max clock (152 SMs x 128 lanes x 2070 MHz)",
+               "instr_per_node": ins, "df_ops_per_node": weights_df_ops(n, m),
+               "fp64_equivalent_tflops": f64_equiv, "fp64_equivalent_frac_of_fp64_units": f64_equiv / FP64_PEAK_TFLOPS_UNITS}
+    else:
+        out = {"kernel": f"weights_ns_kernel, FP64 ({kernel_name}), m={m}, n={n}", "bound": "alu",
+               "achieved": f64_equiv, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
+               "frac": f64_equiv / FP64_PEAK_TFLOPS_UNITS,
+               "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)"}
+    out.update({"traffic": None, "flops_per_node": fl, "ms_per_launch": ms, "launches": 1})
+    out.update(extra)
+    return out
 
 
 def fp64_peak_tflops(torch, dev):
@@ -804,7 +861,6 @@ def run_gpu_adjoint(args):
         e1.record()
         torch.cuda.synchronize(dev)
         e2e_value, _ = replica_value(dist, ws_, N, args.e2e_steps, e0.elapsed_time(e1), dev)
-    w_tflops = weights_flops(n, m) * N / (stages["weights"] * 1e-3) / 1e12
     cpu = None
     if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
         cv, csecs, cnodes, csample = cpu_adjoint(0, 1)
@@ -821,11 +877,7 @@ def run_gpu_adjoint(args):
                   "forward_rel_residual": info["rel_residual"], "adjoint_rel_residual": info_a["rel_residual"],
                   "grad_f_norm": float(dLdf.norm()), "grad_g_norm": float(dLdg.norm())},
         "stages_ms": stages,
-        "roofline": {"kernel": "weights_ns_kernel (null-space elimination, FP64), m=4, n=30", "bound": "alu",
-                     "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
-                     "frac": w_tflops / FP64_PEAK_TFLOPS_UNITS,
-                     "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)", "traffic": None,
-                     "flops_per_node": weights_flops(n, m), "ms_per_launch": stages["weights"], "launches": 1},
+        "roofline": weights_roofline(wcfg["kernel"], n, m, N, stages["weights"], {}),
         "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "steps": args.e2e_steps} if e2e_value is not None else None),
         "cpu_baseline": cpu,
@@ -1104,12 +1156,8 @@ def run_gpu(args):
                                if spmv_df_source_hash() == SPMV_DF_TRAFFIC["source_sha256_16"] else None)),
                   "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
                   "launches": sp_n, "ms_per_step": sp_ms * sp_n / max(args.steps, 1)}
-    roof_weights = {"kernel": "weights_ns_kernel (null-space elimination, FP64)", "bound": "alu",
-                    "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
-                    "frac": w_tflops / FP64_PEAK_TFLOPS_UNITS,
-                    "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)",
-                    "traffic": None, "flops_per_node": w_flops / N, "ms_per_launch": st_ms[1],
-                    "launches": 1, "cublas_dgemm_tflops": fp64_peak, "lu_equivalent_tflops": lu_equiv}
+    roof_weights = weights_roofline(wcfg["kernel"], n, m, N, st_ms[1],
+                                    {"cublas_dgemm_tflops": fp64_peak, "lu_equivalent_tflops": lu_equiv})
     weights_dominate = st_ms[1] > roof_solve["ms_per_step"]
     iters = [i["iters"] for i in infos]
     line = {

@@ -133,7 +133,14 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* and its threads per stencil -- 0 null-space elimination, one warp per    */
 /* stencil, 1..4 stencils (warps) per block; 1 full Gaussian elimination,  */
 /* likewise; 2 / 3 null-space elimination with two / four warps per        */
-/* stencil, one stencil per block (warps_per_block = 2 / 4).  rbffd_weights_autotune times every candidate   */
+/* stencil, one stencil per block (warps_per_block = 2 / 4); 4 / 5 / 6 the  */
+/* same three null-space forms in double-float arithmetic (pairs of floats, */
+/* ~48 significant bits, on the FP32 pipe; FP64 only for the coordinate    */
+/* scaling and the final division), offered for 1 <= m <= 6, where the     */
+/* scaled systems' conditioning keeps the weights within ~1e-10 of FP64.    */
+/* The default is 4 for 1 <= m <= 6, 0 for m > 6 and 1 for m = 0.           */
+/* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form, =lu    */
+/* the Gaussian elimination.  rbffd_weights_autotune times every candidate   */
 /* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */
 /* the given set (3 launches each after one warm-up, CUDA events), records  */
 /* the fastest for (current device, n, m) in a process-wide table that      */
@@ -142,10 +149,11 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* are overwritten).  Synchronises `stream`.  (Autotuning has no            */
 /* counterpart in the paper.)  rbffd_weights_get_config returns the          */
 /* configuration in force; rbffd_weights_set_config pins one (NULL: back to  */
-/* the default, which follows the shared-memory footprint).                  */
+/* the default above, warps per block from the shared-memory footprint).   */
 typedef struct rbffd_weights_config {
-    int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 / 3 null-space (2 / 4 warps) */
-    int32_t warps_per_block; /* warps per block (kernels 0, 1: one stencil per warp; kernels 2, 3: 2, 4) */
+    int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 / 3 null-space (2 / 4 warps), */
+                             /* 4 / 5 / 6 as 0 / 2 / 3 in double-float arithmetic                         */
+    int32_t warps_per_block; /* kernels 0, 1, 4: stencils (warps) per block; 2, 5: 2; 3, 6: 4            */
     double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
 } rbffd_weights_config;
 int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
@@ -232,13 +240,17 @@ int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t
 /*  * prolongation P: PHS r^3 + degree-2 interpolation from the 12 nearest   */
 /*    coarse nodes (zero rows at Dirichlet nodes); restriction R = (N_c/N_f) */
 /*    P^T with zero rows at coarse Dirichlet nodes;                          */
-/*  * smoothing: nu damped Jacobi sweeps (weight omega) before and after;    */
+/*  * smoothing: nu Jacobi sweeps, weight omega on interior rows and 1 on   */
+/*    Dirichlet rows, before and after;                                     */
 /*    coarsest level: a dense inverse (Gauss-Jordan, partial pivoting).     */
 /* With opts->precond = 1, rbffd_solve runs BiCGSTAB right-preconditioned by */
 /* one V-cycle per application (FP64 V-cycle in precision 0; in precision 1 */
 /* the V-cycle runs in float32 values and vectors inside the FP64 BiCGSTAB, */
-/* which needs A32).  The adjoint solve takes the hierarchy of             */
-/* rbffd_mg_setup_adjoint (below).                                          */
+/* which needs A32), from x_b = b_b on the Dirichlet rows (A's Dirichlet    */
+/* rows must be identity rows, as rbffd_assemble writes them).  The adjoint */
+/* solve takes the hierarchy of rbffd_mg_setup_adjoint / _adjoint_of: it    */
+/* solves the interior block L_ii^T x_i = b_i left-preconditioned by the    */
+/* transposed cycle and sets x_b = b_b - L_ib^T x_i after every pass.       */
 /*   mg       : host object filled here; read by rbffd_solve.  It points     */
 /*              into ws, which must stay allocated and unchanged meanwhile.  */
 /*   A, A32   : the fine-level operator (as passed to rbffd_solve; A32 may   */
@@ -263,8 +275,7 @@ int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, con
 /* transpose of the forward one (coarse levels rediscretised, then          */
 /* transposed), restriction P^T and prolongation R^T = (N_c / N_f) P with   */
 /* the coarse Dirichlet columns zeroed -- the exact transpose of the        */
-/* forward V-cycle, so the adjoint iteration sees the transposed            */
-/* preconditioned operator.  rbffd_solve takes only forward hierarchies,   */
+/* forward V-cycle.  rbffd_solve takes only forward hierarchies,           */
 /* rbffd_solve_adjoint only adjoint ones (else RBFFD_ERR_INVALID_ARG).      */
 int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* AT,
                            const rbffd_csr* AT32, int32_t nu, double omega, rbffd_mg* mg, void* ws,

@@ -86,6 +86,11 @@ bool mg_is_transposed(const MgHierarchy* h);
 // so the adjoint's preconditioned operator is block diagonal.
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev = nullptr);
+// x = Pi B b: the V-cycle alone, Dirichlet entries of the result zeroed
+// (Pi); with the adjoint hierarchy, on boundary-free b, B_ii^T b_i (the left
+// preconditioner of the adjoint's interior system).
+int mg_apply_interior(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
+                      std::vector<int>* ev = nullptr);
 // y_b += W_b (r_b - (A y)_b) on the Dirichlet rows of level 0 (see
 // mg_bfix_kernel); one launch on st.
 int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int* flag, cudaStream_t st);

@@ -127,6 +127,15 @@ __device__ bool reduce_last(double (&v)[NQ], double* part, int slot, unsigned in
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+__device__ __forceinline__ void set_alpha(KState* st, double rv) {
+    if (rv == 0.0 || !finite(rv)) {
+        st->flag = kBreakdown;
+    } else {
+        st->alpha = st->rho_new / rv;
+        st->rho = st->rho_new;
+    }
+}
+
 // omega = (t, s) / (t, t).  (The enlarged omega of Sleijpen & van der Vorst
 // for nearly orthogonal t, s was measured to slow these solves 6x and is
 // not used.)
@@ -335,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) update_p64_kernel(int64_t N, const d
 }
 
 // y = D^-1 A xin; MODE 0: (rh, y) -> alpha.  MODE 1: (y, xin), (y, y) -> omega.
+// MODE 2: the product alone.
 // With right preconditioning xin is M^-1 s and the omega dots take s itself
 // (dotv); dotv NULL: xin.
 template <int TPR, int MODE>
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
             y[i] = yi;
             if (MODE == 0) {
                 acc[0] = fma(rh[i], yi, acc[0]);
-            } else {
+            } else if (MODE == 1) {
                 const double si = dotv ? dotv[i] : xin[i];
                 acc[0] = fma(yi, si, acc[0]);
                 acc[1] = fma(yi, yi, acc[1]);
@@ -363,21 +373,68 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
             }
         }
     })
+    if (MODE == 2) return;
     if (MODE == 0) {
         double a1[1] = {acc[0]}, tot[1];
-        if (reduce_last<1>(a1, part, kSlotV, &st->counter[kSlotV], tot) && threadIdx.x == 0) {
-            const double rv = tot[0];
-            if (rv == 0.0 || !finite(rv)) {
-                st->flag = kBreakdown;
-            } else {
-                st->alpha = st->rho_new / rv;
-                st->rho = st->rho_new;
-            }
-        }
+        if (reduce_last<1>(a1, part, kSlotV, &st->counter[kSlotV], tot) && threadIdx.x == 0) set_alpha(st, tot[0]);
     } else {
         double tot[3];
         if (reduce_last<3>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0)
             set_omega(st, tot[0], tot[1], tot[2]);
+    }
+}
+
+// Left preconditioning (the adjoint with multigrid): the reductions that the
+// SpMV kernels fuse in the right-preconditioned form.  MODE 0: (rh, v) ->
+// alpha.  MODE 1: (t, s), (t, t), (s, s) -> omega.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) dot64_kernel(int64_t N, const double* __restrict__ a,
+                                                         const double* __restrict__ b, KState* st, double* part) {
+    if (st->flag != kRunning) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    RBFFD_ELEM_LOOP(N, i) {
+        const double ai = a[i], bi = b[i];
+        acc[0] = fma(ai, bi, acc[0]);
+        if (MODE == 1) {
+            acc[1] = fma(ai, ai, acc[1]);
+            acc[2] = fma(bi, bi, acc[2]);
+        }
+    }
+    if (MODE == 0) {
+        double a1[1] = {acc[0]}, tot[1];
+        if (reduce_last<1>(a1, part, kSlotV, &st->counter[kSlotV], tot) && threadIdx.x == 0) set_alpha(st, tot[0]);
+    } else {
+        double tot[3];
+        if (reduce_last<3>(acc, part, kSlotT, &st->counter[kSlotT], tot) && threadIdx.x == 0)
+            set_omega(st, tot[0], tot[1], tot[2]);
+    }
+}
+
+// Start of a left-preconditioned pass: r = mr (= M (b - A x), from a pass
+// started by resid64 kInit), rh = r or the pseudo-random shadow of seed;
+// the pass then ends on the relative reduction of |M r| alone (tol2 = 0:
+// the explicit FP64 residual between passes decides convergence).
+__global__ void __launch_bounds__(kThreads) left_init_kernel(int64_t N, const double* __restrict__ mr,
+                                                             double* __restrict__ r, double* __restrict__ rh,
+                                                             unsigned long long seed, KState* st, double* part) {
+    if (st->flag != kRunning) return;
+    double acc[2] = {0.0, 0.0};
+    RBFFD_ELEM_LOOP(N, i) {
+        const double ri = mr[i];
+        const double hi = seed ? (double)shadow_value(seed, i) : ri;
+        r[i] = ri;
+        rh[i] = hi;
+        acc[0] = fma(ri, ri, acc[0]);
+        acc[1] = fma(hi, ri, acc[1]);
+    }
+    double tot[2];
+    if (reduce_last<2>(acc, part, kSlotLoad, &st->counter[kSlotLoad], tot) && threadIdx.x == 0) {
+        st->rnorm2 = tot[0];
+        st->rmax2 = tot[0];
+        st->s0 = tot[0];
+        st->rho_new = tot[1];
+        st->tol2 = 0.0;
+        if (!finite(tot[0]) || !finite(tot[1]) || tot[0] == 0.0 || tot[1] == 0.0) st->flag = kBreakdown;
     }
 }
 
@@ -642,6 +699,7 @@ struct Work {
     double *ph, *sh;
     const MgHierarchy* mg;  // host object, NULL without multigrid
     bool mg32;              // float32 V-cycle
+    bool left;              // left preconditioning on the interior (adjoint with multigrid)
     // mixed engine
     double* r64;
     float *d32, *dinv32, *sigma32;
@@ -765,7 +823,36 @@ struct Ops64 {
                 A.row_ptr, A.col, val, A.n_rows, b, x, w.dinv, r, w.rh, w.p, w.v, tol, max_iter, repl, seed, w.st, w.part);
         note_launches(1);
     }
+    // Left-preconditioned iteration on the interior unknowns (see
+    // solve_fp64): v = Pi B^T (A p), t = Pi B^T (A s), x += alpha p + omega s.
+    static void iteration_left(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st,
+                               std::vector<int>& ev) {
+        const int64_t N = A.n_rows;
+        const double* val = static_cast<const double*>(A.val);
+        const int64_t bytes = spmv_bytes(A, 8);
+        const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const char*>(w.st) + offsetof(KState, flag));
+        update_p64_kernel<<<grid_of(update_p64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.p, w.st);
+        int e = prof_begin(st);
+        spmv64_kernel<TPR, 2><<<grid_of(spmv64_kernel<TPR, 2>), kThreads, 0, st>>>(
+            A.row_ptr, A.col, val, N, w.p, w.dinv, w.ph, nullptr, w.st, w.part, nullptr);
+        prof_end(e, st, kProfSpmv64, bytes);
+        ev.push_back(e);
+        mg_apply_interior(w.mg, w.mg32, w.ph, w.v, flag, st, &ev);
+        dot64_kernel<0><<<grid_of(dot64_kernel<0>), kThreads, 0, st>>>(N, w.rh, w.v, w.st, w.part);
+        update_s64_kernel<<<grid_of(update_s64_kernel), kThreads, 0, st>>>(N, w.r, w.v, w.s, w.st);
+        e = prof_begin(st);
+        spmv64_kernel<TPR, 2><<<grid_of(spmv64_kernel<TPR, 2>), kThreads, 0, st>>>(
+            A.row_ptr, A.col, val, N, w.s, w.dinv, w.sh, nullptr, w.st, w.part, nullptr);
+        prof_end(e, st, kProfSpmv64, bytes);
+        ev.push_back(e);
+        mg_apply_interior(w.mg, w.mg32, w.sh, w.t, flag, st, &ev);
+        dot64_kernel<1><<<grid_of(dot64_kernel<1>), kThreads, 0, st>>>(N, w.t, w.s, w.st, w.part);
+        update_xr64_kernel<<<grid_of(update_xr64_kernel), kThreads, 0, st>>>(N, x, w.p, w.s, w.t, w.r, w.rh, w.d,
+                                                                             w.st, w.part, nullptr);
+        note_launches(7);
+    }
     static void iteration(const rbffd_csr& A, double* x, const Work& w, cudaStream_t st, std::vector<int>& ev) {
+        if (w.left) return iteration_left(A, x, w, st, ev);
         const int64_t N = A.n_rows;
         const double* val = static_cast<const double*>(A.val);
         const int64_t bytes = spmv_bytes(A, 8);
@@ -1002,7 +1089,17 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     // Dirichlet part of a vector into the interior through a block of size
     // ~1/h^2; a residual with Dirichlet entries (nonzero boundary data) made
     // BiCGSTAB break down in its first step at 1e6 nodes.
-    if (w.mg && !mg_is_transposed(w.mg) && (rc = mg_dirichlet_fix(w.mg, b, x, nullptr, st)) != RBFFD_OK) return rc;
+    // Multigrid, adjoint (A here is A^T = [I L_ib^T; 0 L_ii^T]): the
+    // interior unknowns solve L_ii^T x_i = b_i and x_b = b_b - L_ib^T x_i
+    // follows by back substitution (the same Dirichlet-row update, done
+    // here and after every pass).  The interior system runs left
+    // preconditioned, B_ii^T L_ii^T = (L_ii B_ii)^T, the transpose of the
+    // forward's right-preconditioned operator, whose deviation from I is
+    // bounded.  Right preconditioning, L_ii^T B_ii^T = (B_ii L_ii)^T, puts
+    // L^T after the cycle: RBF-FD columns do not sum to zero, so L^T turns
+    // the cycle's smooth error into a rough vector ~1/h^2 larger (growth
+    // ~1e3 in the first BiCGSTAB step at 1e6 nodes, and passes that failed).
+    if (w.mg && (rc = mg_dirichlet_fix(w.mg, b, x, nullptr, st)) != RBFFD_OK) return rc;
     while (true) {
         // explicit residual; starts a fresh pass (rh = r or a pseudo-random
         // shadow residual, p = v = 0)
@@ -1045,8 +1142,20 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         g.prev = hs.sres2;
         RBFFD_CUDA_TRY(cudaMemcpyAsync(w.x_save, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         const double start2 = hs.tnorm2;
+        if (w.left) {
+            // r = Pi B^T (b - A x), rh, scalars of the left-preconditioned pass
+            const int* flag =
+                reinterpret_cast<const int*>(reinterpret_cast<const char*>(w.st) + offsetof(KState, flag));
+            if ((rc = mg_apply_interior(w.mg, w.mg32, w.r, w.ph, flag, st)) != RBFFD_OK) return rc;
+            left_init_kernel<<<grid_of(left_init_kernel), kThreads, 0, st>>>(N, w.ph, w.r, w.rh,
+                                                                             shadow_seed(rnd, passes), w.st, w.part);
+            note_launches(1);
+            RBFFD_LAUNCH_CHECK();
+            if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
+        }
         const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); });
         if (f < 0) return -f;
+        if (w.left && (rc = mg_dirichlet_fix(w.mg, b, x, nullptr, st)) != RBFFD_OK) return rc;
         total += hs.iter;
         if (trace_on())
             fprintf(stderr, "[rbffd fp64] pass %d: %d its, flag %d, recurrence |r|/|r0| %.3e, rel at start %.3e\n",
@@ -1193,6 +1302,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     layout(ws, N, mixed, mg != nullptr, &w);
     w.mg = mg;
     w.mg32 = mg && mixed;
+    w.left = mg && adjoint;
     std::memset(info, 0, sizeof(*info));
 
     KState hs;

@@ -1106,6 +1106,26 @@ int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int
     return RBFFD_OK;
 }
 
+__global__ void __launch_bounds__(kT) mg_zero_dirichlet_kernel(int64_t N, const uint8_t* __restrict__ mask,
+                                                               double* __restrict__ y, const int* flag) {
+    if (stopped(flag)) return;
+    MG_ELEMS(N, i) if (mask[i]) y[i] = 0.0;
+}
+
+int mg_apply_interior(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
+                      std::vector<int>* ev) {
+    if (!h || !b || !x || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;
+    if (fp32 && !h->has32) return RBFFD_ERR_INVALID_ARG;
+    int launches = 0;
+    if (fp32) cycle_level<float>(*h, 0, b, true, x, flag, st, &launches, ev);
+    else cycle_level<double>(*h, 0, b, true, x, flag, st, &launches, ev);
+    const MgLevel& L = h->lv[0];
+    mg_zero_dirichlet_kernel<<<blocks_for(L.N), kT, 0, st>>>(L.N, L.mask, x, flag);
+    note_launches(launches + 1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
+
 int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const int* flag, cudaStream_t st,
              std::vector<int>* ev) {
     if (!h || !b || !x || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;

@@ -25,6 +25,7 @@
 //    P are built (when it is large enough), so a warp needs no extra shared
 //    memory and four m = 6 stencils (M = 84) fit on one SM.
 #include "common.cuh"
+#include "df32.cuh"
 #include "internal.cuh"
 
 #include <algorithm>
@@ -389,27 +390,116 @@ __device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, 
     __syncthreads();
 }
 
-template <int NT>
+// Arithmetic of the null-space kernel.  F64: IEEE double throughout.  DF:
+// double-float values (df32.cuh, ~48 significant bits) on the FP32 pipe,
+// which on this GPU issues 64 lanes per clock per SM against the FP64
+// units' 2: the elimination, the reduced matrix and its Cholesky factor run
+// there; only the shift/scale of the coordinates and the final division by
+// delta^2 stay in FP64.  The rounding unit is ~2^-48 instead of 2^-53; with
+// the scaled PHS system's condition numbers (<= ~1e7 for m <= 6 on the
+// node sets measured) the weights stay within ~1e-10 of the FP64 ones, so
+// the DF form is offered for 1 <= m <= 6 only.
+struct NsF64 {
+    using S = double;
+    using V = double;
+    static __device__ __forceinline__ V ld(const S* p) { return *p; }
+    static __device__ __forceinline__ void st(S* p, V v) { *p = v; }
+    static __device__ __forceinline__ V from_d(double x) { return x; }
+    static __device__ __forceinline__ double to_d(V v) { return v; }
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V cst(double x) { return x; }
+    // c - a b
+    static __device__ __forceinline__ V nfma(V a, V b, V c) { return fma(-a, b, c); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __dadd_rn(a, -b); }
+    static __device__ __forceinline__ V rcp(V a) { return rcp64(a); }
+    static __device__ __forceinline__ V rsqrt(V a) { return rsqrt64(a); }
+    static __device__ __forceinline__ V sqrt(V a) { return __dsqrt_rn(a); }
+    // pivot search key (monotone in |a|) and its value / non-finite test
+    static __device__ __forceinline__ unsigned long long key(V a) { return abs_bits(a); }
+    static __device__ __forceinline__ double key_value(unsigned long long k) {
+        return __longlong_as_double((long long)k);
+    }
+    static __device__ __forceinline__ bool key_nonfinite(unsigned long long k) { return k >= 0x7ff0000000000000ull; }
+    static __device__ __forceinline__ bool is_zero(V a) { return a == 0.0; }
+    static __device__ __forceinline__ bool pos_finite(V a) { return a > 0.0 && isfinite(a); }
+};
+
+struct NsDF {
+    using S = float2;
+    using V = df;
+    static __device__ __forceinline__ V ld(const S* p) { return df_load(p); }
+    static __device__ __forceinline__ void st(S* p, V v) { df_store(p, v); }
+    static __device__ __forceinline__ V from_d(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ double to_d(V v) { return df_to_double(v); }
+    static __device__ __forceinline__ V zero() { return df_make(0.f, 0.f); }
+    static __device__ __forceinline__ V cst(double x) { return df_make((float)x, 0.f); }  // small exact constants
+    // c - a b: the product exactly to ~2^-48 (TwoProd of the leading parts,
+    // cross terms by FMA), then TwoSum with c.
+    static __device__ __forceinline__ V nfma(V a, V b, V c) {
+        const df p = two_prod(a.hi, b.hi);
+        const float pl = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+        const df s = two_sum(c.hi, -p.hi);
+        const float e = __fadd_rn(__fsub_rn(c.lo, pl), s.lo);
+        return fast_two_sum(s.hi, e);
+    }
+    static __device__ __forceinline__ V mul(V a, V b) { return df_mul(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return df_add(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return df_sub(a, b); }
+    // 1/a: float reciprocal r, then one Newton step r + r (1 - a r) with the
+    // residual 1 - a r formed from an exact product
+    static __device__ __forceinline__ V rcp(V a) {
+        const float r = __frcp_rn(a.hi);
+        const df p = two_prod(a.hi, r);
+        const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p.hi), p.lo), __fmul_rn(a.lo, r));
+        return fast_two_sum(r, __fmul_rn(r, e));
+    }
+    // a^-1/2: float rsqrt, one Newton step in float (to ~1 ulp), then one in
+    // double-float, y + (y/2)(1 - a y^2) with a y^2 from an exact square
+    static __device__ __forceinline__ V rsqrt(V a) {
+        const float y0 = rsqrtf(a.hi);
+        const float y = __fmaf_rn(__fmul_rn(0.5f, y0), __fmaf_rn(-__fmul_rn(a.hi, y0), y0, 1.0f), y0);
+        const df y2 = two_prod(y, y);
+        const df ay2 = df_mul(a, y2);
+        const float e = __fsub_rn(__fsub_rn(1.0f, ay2.hi), ay2.lo);
+        return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e));
+    }
+    static __device__ __forceinline__ V sqrt(V a) { return (a.hi > 0.f) ? df_mul(a, rsqrt(a)) : df_make(0.f, 0.f); }
+    static __device__ __forceinline__ unsigned long long key(V a) {
+        return (unsigned long long)(__float_as_uint(a.hi) & 0x7fffffffu);
+    }
+    static __device__ __forceinline__ double key_value(unsigned long long k) {
+        return (double)__uint_as_float((unsigned)k);
+    }
+    static __device__ __forceinline__ bool key_nonfinite(unsigned long long k) { return k >= 0x7f800000ull; }
+    static __device__ __forceinline__ bool is_zero(V a) { return a.hi == 0.f && a.lo == 0.f; }
+    static __device__ __forceinline__ bool pos_finite(V a) { return a.hi > 0.f && isfinite(a.hi); }
+};
+
+template <int NT, class R>
 __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
                                                          int N, int n, int m, int s, int LDF, int LDS,
                                                          int bytes_per_warp, double* __restrict__ w,
                                                          int* __restrict__ node_status) {
+    using S = typename R::S;
+    using V = typename R::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // NT threads per stencil: one warp (several stencils per block) or two
-    // warps (one stencil per block, block-wide synchronisation)
+    // or four warps (one stencil per block, block-wide synchronisation)
     const int lane = threadIdx.x % NT;
     const int wib = threadIdx.x / NT;
     const int wpb = blockDim.x / NT;
     __shared__ unsigned long long red_u64[4];
     __shared__ int red_i[8];
     const int q = n - s;
-    double* Phi = reinterpret_cast<double*>(smem_raw + (size_t)wib * bytes_per_warp);
-    double* P = Phi + (size_t)n * LDF;
-    double* crd = P + (size_t)(n + 1) * LDS;
-    double* fv = crd + 2 * n;
-    double* uv = fv + n;
-    double* wv = uv + n;
-    double* tv = wv + n;
+    S* Phi = reinterpret_cast<S*>(smem_raw + (size_t)wib * bytes_per_warp);
+    S* P = Phi + (size_t)n * LDF;
+    S* crd = P + (size_t)(n + 1) * LDS;
+    S* fv = crd + 2 * n;
+    S* uv = fv + n;
+    S* wv = uv + n;
+    S* tv = wv + n;
     int* perm = reinterpret_cast<int*>(tv + n);
     int* act = perm + n;
     const int total_warps = gridDim.x * wpb;
@@ -418,7 +508,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         const int* sten = idx + (int64_t)node * n;
         const double2 c = xy[node];
 
-        // ---- shift, scale ----------------------------------------------------
+        // ---- shift, scale (FP64) ---------------------------------------------
         unsigned long long dmax = 0;
         int bad = 0;
         for (int j = lane; j < n; j += NT) {
@@ -431,8 +521,6 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
             const unsigned long long b = abs_bits(d2);
             dmax = (b > dmax) ? b : dmax;
-            crd[2 * j] = dx;
-            crd[2 * j + 1] = dy;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -442,30 +530,32 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         dmax = group_max_u64<NT>(dmax, red_u64);
         const double delta = __dsqrt_rn(__longlong_as_double((long long)dmax));
         const double delta2 = __dmul_rn(delta, delta);
-        group_sync<NT>();
 
         // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
         for (int j = lane; j < n; j += NT) {
-            const double xh = __ddiv_rn(crd[2 * j], delta);
-            const double yh = __ddiv_rn(crd[2 * j + 1], delta);
-            crd[2 * j] = xh;
-            crd[2 * j + 1] = yh;
-            double xp[9], yp[9];
-            xp[0] = 1.0;
-            yp[0] = 1.0;
+            const int sj = sten[j];
+            const double2 p = ((unsigned)sj < (unsigned)N) ? xy[sj] : c;
+            const V xh = R::from_d(__ddiv_rn(__dadd_rn(p.x, -c.x), delta));
+            const V yh = R::from_d(__ddiv_rn(__dadd_rn(p.y, -c.y), delta));
+            R::st(crd + 2 * j, xh);
+            R::st(crd + 2 * j + 1, yh);
+            V xp[9], yp[9];
+            xp[0] = R::cst(1.0);
+            yp[0] = R::cst(1.0);
 #pragma unroll
             for (int t = 1; t < 9; ++t) {
-                xp[t] = (t <= m) ? __dmul_rn(xp[t - 1], xh) : 0.0;
-                yp[t] = (t <= m) ? __dmul_rn(yp[t - 1], yh) : 0.0;
+                xp[t] = (t <= m) ? R::mul(xp[t - 1], xh) : R::zero();
+                yp[t] = (t <= m) ? R::mul(yp[t - 1], yh) : R::zero();
             }
             int col = 0;
             for (int d = 0; d <= m; ++d)
-                for (int i = 0; i <= d; ++i, ++col) P[(size_t)j * LDS + col] = (d == 0) ? 1.0 : __dmul_rn(xp[d - i], yp[i]);
+                for (int i = 0; i <= d; ++i, ++col)
+                    R::st(P + (size_t)j * LDS + col, (d == 0) ? R::cst(1.0) : R::mul(xp[d - i], yp[i]));
             act[j] = j;
         }
         for (int col = lane; col < s; col += NT) {
             // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5)
-            P[(size_t)n * LDS + col] = (col == 3 || col == 5) ? 2.0 : 0.0;
+            R::st(P + (size_t)n * LDS + col, (col == 3 || col == 5) ? R::cst(2.0) : R::zero());
         }
         group_sync<NT>();
 
@@ -477,7 +567,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             int bi = 0x7fffffff, bpos = -1;
             for (int t = lane; t < na; t += NT) {
                 const int r = act[t];
-                const unsigned long long b = abs_bits(P[(size_t)r * LDS + k]);
+                const unsigned long long b = R::key(R::ld(P + (size_t)r * LDS + k));
                 if (b > best || (b == best && r < bi)) {
                     best = b;
                     bi = r;
@@ -498,12 +588,12 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             group_argmax<NT>(best, bi, bpos, red_u64, red_i);
             // rank deficient (pivot below 1e-12: P's entries are monomials of
             // points in the unit disk, so |P| <= 1) or non-finite
-            if (__longlong_as_double((long long)best) < 1e-12 || best >= 0x7ff0000000000000ull) {
+            if (R::key_value(best) < 1e-12 || R::key_nonfinite(best)) {
                 singular = 1;
                 break;
             }
             const int pr = bi;
-            const double inv = rcp64(P[(size_t)pr * LDS + k]);
+            const V inv = R::rcp(R::ld(P + (size_t)pr * LDS + k));
             group_sync<NT>();
             if (lane == 0) {
                 perm[k] = pr;
@@ -514,7 +604,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             // scale column k on the active rows and the g row; pivot row -> e_k
             for (int t = lane; t <= na; t += NT) {
                 const int r = (t < na) ? act[t] : n;
-                P[(size_t)r * LDS + k] = __dmul_rn(P[(size_t)r * LDS + k], inv);
+                R::st(P + (size_t)r * LDS + k, R::mul(R::ld(P + (size_t)r * LDS + k), inv));
             }
             group_sync<NT>();
             // column j -= P[pr][j] * column k, on active rows and the g row;
@@ -522,14 +612,14 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             const int cols = s - 1, rows = na + 1, total = rows * cols;
             if (cols > 0) {
                 int t = lane / cols, jj = lane - (lane / cols) * cols;
-                const int st = NT / cols, sj = NT - (NT / cols) * cols;
-                const double* prow = P + (size_t)pr * LDS;
+                const int stp = NT / cols, sj = NT - (NT / cols) * cols;
+                const S* prow = P + (size_t)pr * LDS;
                 for (int e = lane; e < total; e += NT) {
                     const int j = jj + ((jj >= k) ? 1 : 0);
                     const int r = (t < na) ? act[t] : n;
-                    double* rr = P + (size_t)r * LDS;
-                    rr[j] = fma(-prow[j], rr[k], rr[j]);
-                    t += st;
+                    S* rr = P + (size_t)r * LDS;
+                    R::st(rr + j, R::nfma(R::ld(prow + j), R::ld(rr + k), R::ld(rr + j)));
+                    t += stp;
                     jj += sj;
                     if (jj >= cols) {
                         jj -= cols;
@@ -555,20 +645,21 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while ((a + 1) * (2 * n - a - 2) / 2 <= pidx) ++a;
                 const int b = pidx - a * (2 * n - a - 1) / 2 + a + 1;
                 const int ja = perm[a], jb = perm[b];
-                const double dx = __dadd_rn(crd[2 * ja], -crd[2 * jb]);
-                const double dy = __dadd_rn(crd[2 * ja + 1], -crd[2 * jb + 1]);
-                coincident |= (dx == 0.0 && dy == 0.0) ? 1 : 0;
+                const V dx = R::sub(R::ld(crd + 2 * ja), R::ld(crd + 2 * jb));
+                const V dy = R::sub(R::ld(crd + 2 * ja + 1), R::ld(crd + 2 * jb + 1));
+                const bool same = R::is_zero(dx) && R::is_zero(dy);
+                coincident |= same ? 1 : 0;
                 // r^3 = r^2 * (r^2 / r), r^2 / r = r^2 * rsqrt(r^2)
-                const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                const double phi = (r2 > 0.0) ? __dmul_rn(r2, __dmul_rn(r2, rsqrt64(r2))) : 0.0;
-                Phi[(size_t)a * LDF + b] = phi;
-                Phi[(size_t)b * LDF + a] = phi;
+                const V r2 = R::add(R::mul(dx, dx), R::mul(dy, dy));
+                const V phi = same ? R::zero() : R::mul(r2, R::mul(r2, R::rsqrt(r2)));
+                R::st(Phi + (size_t)a * LDF + b, phi);
+                R::st(Phi + (size_t)b * LDF + a, phi);
             }
             for (int a = lane; a < n; a += NT) {
-                Phi[(size_t)a * LDF + a] = 0.0;
+                R::st(Phi + (size_t)a * LDF + a, R::zero());
                 const int ja = perm[a];
-                const double xh = crd[2 * ja], yh = crd[2 * ja + 1];
-                fv[a] = __dmul_rn(9.0, __dsqrt_rn(__dadd_rn(__dmul_rn(xh, xh), __dmul_rn(yh, yh))));
+                const V xh = R::ld(crd + 2 * ja), yh = R::ld(crd + 2 * ja + 1);
+                R::st(fv + a, R::mul(R::cst(9.0), R::sqrt(R::add(R::mul(xh, xh), R::mul(yh, yh)))));
             }
         }
         singular |= group_any<NT>(coincident) ? 1 : 0;
@@ -576,34 +667,34 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
 
         if (!singular) {
             // X[j][k] = P[perm[s + j]][k], w0[k] = P[n][k]
-            const double* w0 = P + (size_t)n * LDS;
+            const S* w0 = P + (size_t)n * LDS;
             // ---- T = Phi12 - Phi11 X^T  (s x q, in place) --------------------
             for (int e = lane; e < s * q; e += NT) {
                 const int a = e / q, j = e - (e / q) * q;
-                const double* xr = P + (size_t)perm[s + j] * LDS;
-                const double* pr = Phi + (size_t)a * LDF;
-                // two independent FMA chains (few warps per SM: latency, not
+                const S* xr = P + (size_t)perm[s + j] * LDS;
+                const S* pr = Phi + (size_t)a * LDF;
+                // two independent chains (few warps per SM: latency, not
                 // issue, limits a single chain)
-                double acc = pr[s + j], acc1 = 0.0;
+                V acc = R::ld(pr + s + j), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = fma(-pr[k], xr[k], acc);
-                    acc1 = fma(-pr[k + 1], xr[k + 1], acc1);
+                    acc = R::nfma(R::ld(pr + k), R::ld(xr + k), acc);
+                    acc1 = R::nfma(R::ld(pr + k + 1), R::ld(xr + k + 1), acc1);
                 }
-                if (k < s) acc = fma(-pr[k], xr[k], acc);
-                Phi[(size_t)a * LDF + s + j] = acc + acc1;
+                if (k < s) acc = R::nfma(R::ld(pr + k), R::ld(xr + k), acc);
+                R::st(Phi + (size_t)a * LDF + s + j, R::add(acc, acc1));
             }
             // ---- u = f - Phi[:, 0..s) w0 ----------------------------------------
             for (int a = lane; a < n; a += NT) {
-                const double* pr = Phi + (size_t)a * LDF;
-                double acc = fv[a], acc1 = 0.0;
+                const S* pr = Phi + (size_t)a * LDF;
+                V acc = R::ld(fv + a), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = fma(-pr[k], w0[k], acc);
-                    acc1 = fma(-pr[k + 1], w0[k + 1], acc1);
+                    acc = R::nfma(R::ld(pr + k), R::ld(w0 + k), acc);
+                    acc1 = R::nfma(R::ld(pr + k + 1), R::ld(w0 + k + 1), acc1);
                 }
-                if (k < s) acc = fma(-pr[k], w0[k], acc);
-                uv[a] = acc + acc1;
+                if (k < s) acc = R::nfma(R::ld(pr + k), R::ld(w0 + k), acc);
+                R::st(uv + a, R::add(acc, acc1));
             }
             group_sync<NT>();
             // ---- S = Phi22 - Phi21 X^T - X T (lower triangle, in place) -----
@@ -613,49 +704,49 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while (j * (j + 1) / 2 > e) --j;
                 while ((j + 1) * (j + 2) / 2 <= e) ++j;
                 const int l = e - j * (j + 1) / 2;
-                const double* xj = P + (size_t)perm[s + j] * LDS;
-                const double* xl = P + (size_t)perm[s + l] * LDS;
-                const double* prj = Phi + (size_t)(s + j) * LDF;
-                double acc = prj[s + l], acc1 = 0.0;
+                const S* xj = P + (size_t)perm[s + j] * LDS;
+                const S* xl = P + (size_t)perm[s + l] * LDS;
+                const S* prj = Phi + (size_t)(s + j) * LDF;
+                V acc = R::ld(prj + s + l), acc1 = R::zero();
                 for (int k = 0; k < s; ++k) {
-                    acc = fma(-prj[k], xl[k], acc);
-                    acc1 = fma(-xj[k], Phi[(size_t)k * LDF + s + l], acc1);
+                    acc = R::nfma(R::ld(prj + k), R::ld(xl + k), acc);
+                    acc1 = R::nfma(R::ld(xj + k), R::ld(Phi + (size_t)k * LDF + s + l), acc1);
                 }
-                Phi[(size_t)(s + j) * LDF + s + l] = acc + acc1;
+                R::st(Phi + (size_t)(s + j) * LDF + s + l, R::add(acc, acc1));
             }
             // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
             for (int j = lane; j < q; j += NT) {
-                const double* xj = P + (size_t)perm[s + j] * LDS;
-                double acc = uv[s + j], acc1 = 0.0;
+                const S* xj = P + (size_t)perm[s + j] * LDS;
+                V acc = R::ld(uv + s + j), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = fma(-xj[k], uv[k], acc);
-                    acc1 = fma(-xj[k + 1], uv[k + 1], acc1);
+                    acc = R::nfma(R::ld(xj + k), R::ld(uv + k), acc);
+                    acc1 = R::nfma(R::ld(xj + k + 1), R::ld(uv + k + 1), acc1);
                 }
-                if (k < s) acc = fma(-xj[k], uv[k], acc);
-                tv[j] = acc + acc1;
+                if (k < s) acc = R::nfma(R::ld(xj + k), R::ld(uv + k), acc);
+                R::st(tv + j, R::add(acc, acc1));
             }
             group_sync<NT>();
             // ---- Cholesky S = L L^T (lower, in place) ----------------------------
             for (int cI = 0; cI < q && !singular; ++cI) {
-                double* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const double dcc = sc[cI];
-                if (!(dcc > 0.0) || !isfinite(dcc)) {
+                S* sc = Phi + (size_t)(s + cI) * LDF + s;
+                const V dcc = R::ld(sc + cI);
+                if (!R::pos_finite(dcc)) {
                     singular = 1;
                     break;
                 }
                 // l = sqrt(d) and 1/l from one reciprocal square root; 1/l is
                 // kept (in fv, free by now) for the substitutions
-                const double inv = rsqrt64(dcc);
-                const double lcc = __dmul_rn(dcc, inv);
+                const V inv = R::rsqrt(dcc);
+                const V lcc = R::mul(dcc, inv);
                 group_sync<NT>();
                 for (int i = cI + 1 + lane; i < q; i += NT) {
-                    double* si = Phi + (size_t)(s + i) * LDF + s;
-                    si[cI] = __dmul_rn(si[cI], inv);
+                    S* si = Phi + (size_t)(s + i) * LDF + s;
+                    R::st(si + cI, R::mul(R::ld(si + cI), inv));
                 }
                 if (lane == 0) {
-                    sc[cI] = lcc;
-                    fv[cI] = inv;
+                    R::st(sc + cI, lcc);
+                    R::st(fv + cI, inv);
                 }
                 group_sync<NT>();
                 // trailing lower triangle: S[i][j] -= L[i][c] L[j][c], c < j <= i
@@ -665,9 +756,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     while (i * (i + 1) / 2 > e) --i;
                     while ((i + 1) * (i + 2) / 2 <= e) ++i;
                     const int j = e - i * (i + 1) / 2;
-                    double* si = Phi + (size_t)(s + cI + 1 + i) * LDF + s;
-                    const double* sj = Phi + (size_t)(s + cI + 1 + j) * LDF + s;
-                    si[cI + 1 + j] = fma(-si[cI], sj[cI], si[cI + 1 + j]);
+                    S* si = Phi + (size_t)(s + cI + 1 + i) * LDF + s;
+                    const S* sj = Phi + (size_t)(s + cI + 1 + j) * LDF + s;
+                    R::st(si + cI + 1 + j, R::nfma(R::ld(si + cI), R::ld(sj + cI), R::ld(si + cI + 1 + j)));
                 }
                 group_sync<NT>();
             }
@@ -675,48 +766,50 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         if (!singular) {
             // ---- forward (L y = t) and back (L^T z = y) substitution -------------
             for (int cI = 0; cI < q; ++cI) {
-                const double yc = __dmul_rn(tv[cI], fv[cI]);
+                const V yc = R::mul(R::ld(tv + cI), R::ld(fv + cI));
                 group_sync<NT>();
                 for (int i = cI + 1 + lane; i < q; i += NT)
-                    tv[i] = fma(-Phi[(size_t)(s + i) * LDF + s + cI], yc, tv[i]);
-                if (lane == 0) tv[cI] = yc;
+                    R::st(tv + i, R::nfma(R::ld(Phi + (size_t)(s + i) * LDF + s + cI), yc, R::ld(tv + i)));
+                if (lane == 0) R::st(tv + cI, yc);
                 group_sync<NT>();
             }
             for (int cI = q - 1; cI >= 0; --cI) {
-                const double* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const double zc = __dmul_rn(tv[cI], fv[cI]);
+                const S* sc = Phi + (size_t)(s + cI) * LDF + s;
+                const V zc = R::mul(R::ld(tv + cI), R::ld(fv + cI));
                 group_sync<NT>();
-                for (int i = lane; i < cI; i += NT) tv[i] = fma(-sc[i], zc, tv[i]);
-                if (lane == 0) tv[cI] = zc;
+                for (int i = lane; i < cI; i += NT) R::st(tv + i, R::nfma(R::ld(sc + i), zc, R::ld(tv + i)));
+                if (lane == 0) R::st(tv + cI, zc);
                 group_sync<NT>();
             }
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
-            const double* w0 = P + (size_t)n * LDS;
+            const S* w0 = P + (size_t)n * LDS;
             for (int k = lane; k < s; k += NT) {
-                double acc = w0[k], acc1 = 0.0;
+                V acc = R::ld(w0 + k), acc1 = R::zero();
                 int j = 0;
                 for (; j + 1 < q; j += 2) {
-                    acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
-                    acc1 = fma(-P[(size_t)perm[s + j + 1] * LDS + k], tv[j + 1], acc1);
+                    acc = R::nfma(R::ld(P + (size_t)perm[s + j] * LDS + k), R::ld(tv + j), acc);
+                    acc1 = R::nfma(R::ld(P + (size_t)perm[s + j + 1] * LDS + k), R::ld(tv + j + 1), acc1);
                 }
-                if (j < q) acc = fma(-P[(size_t)perm[s + j] * LDS + k], tv[j], acc);
-                wv[k] = acc + acc1;
+                if (j < q) acc = R::nfma(R::ld(P + (size_t)perm[s + j] * LDS + k), R::ld(tv + j), acc);
+                R::st(wv + k, R::add(acc, acc1));
             }
-            for (int j = lane; j < q; j += NT) wv[s + j] = tv[j];
+            for (int j = lane; j < q; j += NT) R::st(wv + s + j, R::ld(tv + j));
             group_sync<NT>();
         }
 
-        // ---- scale back to the caller's order --------------------------------
+        // ---- scale back (FP64) to the caller's order -------------------------
+        // (each lane rewrites its own slots of wv as doubles: 8 bytes either way)
         double* wout = w + (int64_t)node * n;
+        double* wd = reinterpret_cast<double*>(wv);
         int nonfinite = 0;
         for (int a = lane; a < n; a += NT) {
-            const double v = singular ? 0.0 : __ddiv_rn(wv[a], delta2);
+            const double v = singular ? 0.0 : __ddiv_rn(R::to_d(R::ld(wv + a)), delta2);
             nonfinite |= isfinite(v) ? 0 : 1;
-            wv[a] = v;
+            wd[a] = v;
         }
         const int fail = (singular || group_any<NT>(nonfinite)) ? 1 : 0;
         group_sync<NT>();
-        for (int a = lane; a < n; a += NT) wout[singular ? a : perm[a]] = fail ? 0.0 : wv[a];
+        for (int a = lane; a < n; a += NT) wout[singular ? a : perm[a]] = fail ? 0.0 : wd[a];
         if (node_status && lane == 0) node_status[node] = fail;
         group_sync<NT>();
     }
@@ -758,7 +851,7 @@ namespace {
 struct WCfg {
     int kernel;  // 0 null-space elimination (one warp per stencil), 1 full Gaussian
                  // elimination, 2 / 3 null-space elimination with two / four warps
-                 // per stencil
+                 // per stencil; 4 / 5 / 6: 0 / 2 / 3 in double-float arithmetic
     int wpb;     // warps per block (kernels 2, 3: 2 or 4, one stencil)
 };
 
@@ -778,23 +871,28 @@ size_t smem_per_stencil(int kernel, int n, int m) {
 }
 
 // Stencils per block of a configuration, and its dynamic shared memory.
-int stencils_per_block(const WCfg& c) { return c.kernel >= 2 ? 1 : c.wpb; }
+int stencils_per_block(const WCfg& c) { return (c.kernel == 2 || c.kernel == 3 || c.kernel >= 5) ? 1 : c.wpb; }
+
+// The double-float null-space kernels: 1 <= m <= 6 (accuracy, see NsDF).
+constexpr int kDfMaxM = 6;
 size_t block_smem(const WCfg& c, int n, int m) { return smem_per_stencil(c.kernel, n, m) * stencils_per_block(c); }
 
 bool cfg_valid(const WCfg& c, int n, int m) {
-    if (c.kernel < 0 || c.kernel > 3) return false;
+    if (c.kernel < 0 || c.kernel > 6) return false;
     if (c.kernel != 1 && m < 1) return false;  // null-space form needs the linear monomials
-    if (c.kernel == 2 && c.wpb != 2) return false;
-    if (c.kernel == 3 && c.wpb != 4) return false;
-    if (c.kernel <= 1 && (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
+    if (c.kernel >= 4 && m > kDfMaxM) return false;
+    if ((c.kernel == 2 || c.kernel == 5) && c.wpb != 2) return false;
+    if ((c.kernel == 3 || c.kernel == 6) && c.wpb != 4) return false;
+    if ((c.kernel <= 1 || c.kernel == 4) && (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
     return block_smem(c, n, m) <= 227 * 1024;
 }
 
 WCfg default_cfg(int n, int m) {
     WCfg c;
     // the null-space form needs r^3 positive definite on the null space of
-    // P^T, which holds once P contains the linear monomials (m >= 1)
-    c.kernel = m < 1 ? 1 : 0;
+    // P^T, which holds once P contains the linear monomials (m >= 1); in
+    // double-float arithmetic up to m = 6
+    c.kernel = m < 1 ? 1 : (m <= kDfMaxM ? 4 : 0);
     size_t smem = 0;
     c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
     return c;
@@ -802,12 +900,13 @@ WCfg default_cfg(int n, int m) {
 
 WCfg chosen_cfg(int n, int m) {
     // RBFFD_WEIGHTS=lu forces the full Gaussian elimination (comparisons)
+    // RBFFD_WEIGHTS=ns64 forces the FP64 null-space elimination
     const char* sel = std::getenv("RBFFD_WEIGHTS");
-    if (sel && std::strcmp(sel, "lu") == 0) {
+    if (sel && (std::strcmp(sel, "lu") == 0 || (std::strcmp(sel, "ns64") == 0 && m >= 1))) {
         WCfg c = default_cfg(n, m);
         size_t smem = 0;
-        c.kernel = 1;
-        c.wpb = warps_per_block_for(smem_per_stencil(1, n, m), &smem);
+        c.kernel = std::strcmp(sel, "lu") == 0 ? 1 : 0;
+        c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
         return c;
     }
     std::lock_guard<std::mutex> lk(g_wcfg_mu);
@@ -816,13 +915,13 @@ WCfg chosen_cfg(int n, int m) {
     return default_cfg(n, m);
 }
 
-template <int NT>
+template <int NT, class R>
 int launch_ns(const WCfg& c, const double2* xy, const int32_t* idx, int64_t N, int n, int m, double* w,
               int32_t* node_status, cudaStream_t st) {
     NsGeom g = ns_geom(n, m);
     const int spb = stencils_per_block(c);
     const size_t smem = block_smem(c, n, m);
-    auto kern = weights_ns_kernel<NT>;
+    auto kern = weights_ns_kernel<NT, R>;
     RBFFD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RBFFD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
@@ -853,11 +952,17 @@ int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t 
         weights_kernel<<<blocks, 32 * wpb, smem, st>>>(p, idx, (int)N, n, m, g.s, g.M, g.LD, g.coords_in_zero_block,
                                                        g.smem_doubles, w, node_status, p, (int)N, 0);
     } else if (c.kernel == 0) {
-        rc = launch_ns<32>(c, p, idx, N, n, m, w, node_status, st);
+        rc = launch_ns<32, NsF64>(c, p, idx, N, n, m, w, node_status, st);
     } else if (c.kernel == 2) {
-        rc = launch_ns<64>(c, p, idx, N, n, m, w, node_status, st);
+        rc = launch_ns<64, NsF64>(c, p, idx, N, n, m, w, node_status, st);
+    } else if (c.kernel == 3) {
+        rc = launch_ns<128, NsF64>(c, p, idx, N, n, m, w, node_status, st);
+    } else if (c.kernel == 4) {
+        rc = launch_ns<32, NsDF>(c, p, idx, N, n, m, w, node_status, st);
+    } else if (c.kernel == 5) {
+        rc = launch_ns<64, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     } else {
-        rc = launch_ns<128>(c, p, idx, N, n, m, w, node_status, st);
+        rc = launch_ns<128, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     }
     if (rc != RBFFD_OK) return rc;
     note_launches(1);
@@ -895,6 +1000,10 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
             if (cfg_valid(WCfg{kernel, wpb}, n, m)) cands.push_back(WCfg{kernel, wpb});
     if (cfg_valid(WCfg{2, 2}, n, m)) cands.push_back(WCfg{2, 2});
     if (cfg_valid(WCfg{3, 4}, n, m)) cands.push_back(WCfg{3, 4});
+    for (int wpb = 1; wpb <= 4; ++wpb)
+        if (cfg_valid(WCfg{4, wpb}, n, m)) cands.push_back(WCfg{4, wpb});
+    if (cfg_valid(WCfg{5, 2}, n, m)) cands.push_back(WCfg{5, 2});
+    if (cfg_valid(WCfg{6, 4}, n, m)) cands.push_back(WCfg{6, 4});
     if (cands.empty()) return RBFFD_ERR_INVALID_ARG;
     cudaEvent_t e0, e1;
     RBFFD_CUDA_TRY(cudaEventCreate(&e0));

@@ -52,6 +52,11 @@ class Csr(ctypes.Structure):
     ]
 
 
+# rbffd_weights_config.kernel ids
+WEIGHTS_KERNELS = ("null-space", "gauss", "null-space-2warp", "null-space-4warp", "null-space-df",
+                   "null-space-df-2warp", "null-space-df-4warp")
+
+
 class WeightsConfig(ctypes.Structure):
     _fields_ = [
         ("kernel", ctypes.c_int32),
@@ -60,7 +65,7 @@ class WeightsConfig(ctypes.Structure):
     ]
 
     def as_dict(self):
-        return {"kernel": ("null-space", "gauss", "null-space-2warp", "null-space-4warp")[self.kernel],
+        return {"kernel": WEIGHTS_KERNELS[self.kernel],
                 "warps_per_block": self.warps_per_block, "ms_per_mnode": self.ms_per_mnode}
 
 
@@ -566,8 +571,7 @@ def set_weights_config(n: int, m: int, kernel: str | None = None, warps_per_bloc
     if kernel is None:
         _check(lib.rbffd_weights_set_config(int(n), int(m), None), "rbffd_weights_set_config")
         return
-    c = WeightsConfig({"null-space": 0, "gauss": 1, "null-space-2warp": 2, "null-space-4warp": 3}[kernel],
-                      int(warps_per_block), 0.0)
+    c = WeightsConfig(WEIGHTS_KERNELS.index(kernel), int(warps_per_block), 0.0)
     _check(lib.rbffd_weights_set_config(int(n), int(m), ctypes.byref(c)), "rbffd_weights_set_config")
 
 

@@ -26,8 +26,9 @@ def test_autotuned_and_pinned_configs_match_oracle(lib, h, m, n, tol):
         assert best["ms_per_mnode"] > 0 and 1 <= best["warps_per_block"] <= 4
         got = rbffd.weights_config(n, m)
         assert (got["kernel"], got["warps_per_block"]) == (best["kernel"], best["warps_per_block"])
-        for kernel in ("null-space", "gauss", "null-space-2warp", "null-space-4warp"):
-            for wpb in {"null-space-2warp": (2,), "null-space-4warp": (4,)}.get(kernel, (1, 2, 4)):
+        for kernel in rbffd.WEIGHTS_KERNELS:
+            for wpb in {"null-space-2warp": (2,), "null-space-4warp": (4,), "null-space-df-2warp": (2,),
+                        "null-space-df-4warp": (4,)}.get(kernel, (1, 2, 4)):
                 try:
                     rbffd.set_weights_config(n, m, kernel, wpb)
                 except rbffd.RbffdError:

@@ -91,12 +91,14 @@ def test_stencils_invalid_args(lib):
 
 
 # ------------------------------------------------------------------- weights --
-@pytest.fixture(params=["nullspace", "lu"])
+@pytest.fixture(params=["nullspace", "nullspace-fp64", "lu"])
 def weights_kernel(request, monkeypatch):
-    """Both weight kernels: the default null-space elimination and the full
-    Gaussian elimination kept for comparison (RBFFD_WEIGHTS=lu)."""
-    if request.param == "lu":
-        monkeypatch.setenv("RBFFD_WEIGHTS", "lu")
+    """Every weight kernel: the default null-space elimination (double-float
+    for 1 <= m <= 6), the FP64 null-space elimination (RBFFD_WEIGHTS=ns64)
+    and the full Gaussian elimination (RBFFD_WEIGHTS=lu)."""
+    env = {"lu": "lu", "nullspace-fp64": "ns64"}.get(request.param)
+    if env:
+        monkeypatch.setenv("RBFFD_WEIGHTS", env)
     else:
         monkeypatch.delenv("RBFFD_WEIGHTS", raising=False)
     return request.param
