@@ -477,11 +477,16 @@ struct NsDF {
     static __device__ __forceinline__ bool pos_finite(V a) { return a.hi > 0.f && isfinite(a.hi); }
 };
 
+// op 0: Laplacian weights at the stencil's first node (N = Nd, cxy = xy).
+// op 1: interpolation weights of the value at the query point cxy[node]
+//       (stencils index the Nd points xy): right-hand side [ |xh_j|^3 ;
+//       p_k(0) ], no rescaling.
 template <int NT, class R>
 __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
                                                          int N, int n, int m, int s, int LDF, int LDS,
                                                          int bytes_per_warp, double* __restrict__ w,
-                                                         int* __restrict__ node_status) {
+                                                         int* __restrict__ node_status,
+                                                         const double2* __restrict__ cxy, int Nd, int op) {
     using S = typename R::S;
     using V = typename R::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -506,14 +511,14 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
 
     for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
         const int* sten = idx + (int64_t)node * n;
-        const double2 c = xy[node];
+        const double2 c = cxy[node];
 
         // ---- shift, scale (FP64) ---------------------------------------------
         unsigned long long dmax = 0;
         int bad = 0;
         for (int j = lane; j < n; j += NT) {
             const int sj = sten[j];
-            const bool ok = (unsigned)sj < (unsigned)N;  // never read outside xy
+            const bool ok = (unsigned)sj < (unsigned)Nd;  // never read outside xy
             bad |= ok ? 0 : 1;
             const double2 p = ok ? xy[sj] : c;
             const double dx = __dadd_rn(p.x, -c.x);
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
         for (int j = lane; j < n; j += NT) {
             const int sj = sten[j];
-            const double2 p = ((unsigned)sj < (unsigned)N) ? xy[sj] : c;
+            const double2 p = ((unsigned)sj < (unsigned)Nd) ? xy[sj] : c;
             const V xh = R::from_d(__ddiv_rn(__dadd_rn(p.x, -c.x), delta));
             const V yh = R::from_d(__ddiv_rn(__dadd_rn(p.y, -c.y), delta));
             R::st(crd + 2 * j, xh);
@@ -554,8 +559,10 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             act[j] = j;
         }
         for (int col = lane; col < s; col += NT) {
-            // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5)
-            R::st(P + (size_t)n * LDS + col, (col == 3 || col == 5) ? R::cst(2.0) : R::zero());
+            // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5);
+            // interpolation: p_k(0), 1 for the constant
+            const bool one = op ? (col == 0) : (col == 3 || col == 5);
+            R::st(P + (size_t)n * LDS + col, one ? R::cst(op ? 1.0 : 2.0) : R::zero());
         }
         group_sync<NT>();
 
@@ -659,7 +666,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 R::st(Phi + (size_t)a * LDF + a, R::zero());
                 const int ja = perm[a];
                 const V xh = R::ld(crd + 2 * ja), yh = R::ld(crd + 2 * ja + 1);
-                R::st(fv + a, R::mul(R::cst(9.0), R::sqrt(R::add(R::mul(xh, xh), R::mul(yh, yh)))));
+                // f = lap |x - x_c|^3 = 9 |xh| at the centre; interpolation: |xh|^3
+                const V rr = R::add(R::mul(xh, xh), R::mul(yh, yh));
+                R::st(fv + a, R::mul(op ? rr : R::cst(9.0), R::sqrt(rr)));
             }
         }
         singular |= group_any<NT>(coincident) ? 1 : 0;
@@ -803,7 +812,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         double* wd = reinterpret_cast<double*>(wv);
         int nonfinite = 0;
         for (int a = lane; a < n; a += NT) {
-            const double v = singular ? 0.0 : __ddiv_rn(R::to_d(R::ld(wv + a)), delta2);
+            const double v = singular ? 0.0 : (op ? R::to_d(R::ld(wv + a)) : __ddiv_rn(R::to_d(R::ld(wv + a)), delta2));
             nonfinite |= isfinite(v) ? 0 : 1;
             wd[a] = v;
         }
@@ -917,7 +926,11 @@ WCfg chosen_cfg(int n, int m) {
 
 template <int NT, class R>
 int launch_ns(const WCfg& c, const double2* xy, const int32_t* idx, int64_t N, int n, int m, double* w,
-              int32_t* node_status, cudaStream_t st) {
+              int32_t* node_status, cudaStream_t st, const double2* cxy = nullptr, int64_t Nd = 0, int op = 0) {
+    if (!cxy) {
+        cxy = xy;
+        Nd = N;
+    }
     NsGeom g = ns_geom(n, m);
     const int spb = stencils_per_block(c);
     const size_t smem = block_smem(c, n, m);
@@ -929,7 +942,8 @@ int launch_ns(const WCfg& c, const double2* xy, const int32_t* idx, int64_t N, i
     if (per_sm < 1) return RBFFD_ERR_INVALID_ARG;
     const int64_t need = (N + spb - 1) / spb;
     const int blocks = (int)std::min<int64_t>(need, (int64_t)per_sm * sm_count());
-    kern<<<blocks, NT * spb, smem, st>>>(xy, idx, (int)N, n, m, g.s, g.LDF, g.LDS, g.bytes, w, node_status);
+    kern<<<blocks, NT * spb, smem, st>>>(xy, idx, (int)N, n, m, g.s, g.LDF, g.LDS, g.bytes, w, node_status, cxy,
+                                         (int)Nd, op);
     return RBFFD_OK;
 }
 
@@ -1087,6 +1101,24 @@ int rbffd::interp_weights(const double* xy, int64_t Nd, const double* qxy, int64
         return RBFFD_ERR_INVALID_ARG;
     const int s = (m + 1) * (m + 2) / 2;
     if (n < s) return RBFFD_ERR_INVALID_ARG;
+    if (m >= 1) {
+        // the null-space elimination of the same saddle system (double-float
+        // for m <= 6), one warp per query point, stencils per block by the
+        // shared-memory footprint
+        WCfg c;
+        size_t smem_b = 0;
+        c.kernel = m <= kDfMaxM ? 4 : 0;
+        c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem_b);
+        if (!cfg_valid(c, n, m)) return RBFFD_ERR_INVALID_ARG;
+        const double2* d2 = reinterpret_cast<const double2*>(xy);
+        const double2* q2 = reinterpret_cast<const double2*>(qxy);
+        const int rc = c.kernel == 4 ? launch_ns<32, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
+                                     : launch_ns<32, NsF64>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1);
+        if (rc != RBFFD_OK) return rc;
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        return RBFFD_OK;
+    }
     WeightsGeom g = weights_geom(n, m);
     size_t smem = 0;
     const int wpb = weights_warps_per_block(g, &smem);

@@ -266,6 +266,21 @@ def test_mg_level_views_and_transposed_hierarchy(lib):
             scale = n / prev["n_nodes"]
             cm = m[pidx]
             assert np.array_equal(av, np.where(cm, 0.0, pv * scale))
+            # the interpolation reproduces quadratics at every interior fine
+            # node (PHS r^3 + degree-2 weights), rows of Dirichlet nodes are 0
+            fxy, cxy = prev["xy"].cpu().numpy(), f["xy"].cpu().numpy()
+            fm = prev["mask"]
+            assert np.all(pv[fm] == 0.0)
+            nb = cxy[pidx]  # fine x 12 x 2
+            for px, py in ((0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)):
+                got = (pv * nb[..., 0] ** px * nb[..., 1] ** py).sum(axis=1)
+                want = fxy[:, 0] ** px * fxy[:, 1] ** py
+                err = np.abs(got - want)[~fm]
+                # (rows of singular interpolation systems fall back to the
+                # nearest coarse node: constants only)
+                assert np.quantile(err, 0.999) <= 1e-10, (l, px, py, np.quantile(err, 0.999))
+                if px == py == 0:
+                    assert err.max() <= 1e-12
         if l == len(sizes) - 1:
             assert f["p_idx"] is None and f["minv"] is not None
             Ad = Af.toarray()
@@ -273,7 +288,7 @@ def test_mg_level_views_and_transposed_hierarchy(lib):
         else:
             assert f["minv"] is None
             assert torch.equal(f["p_idx"], a["p_idx"])
-        prev = {"xy": f["xy"], "n_nodes": n,
+        prev = {"xy": f["xy"], "n_nodes": n, "mask": m,
                 "p_idx": None if f["p_idx"] is None else f["p_idx"].cpu().numpy(),
                 "fwd_p_val": None if f["p_val"] is None else f["p_val"].cpu().numpy(),
                 "adj_p_val": None if a["p_val"] is None else a["p_val"].cpu().numpy()}
