@@ -138,7 +138,8 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* ~48 significant bits, on the FP32 pipe; FP64 only for the coordinate    */
 /* scaling and the final division), offered for 1 <= m <= 6, where the     */
 /* scaled systems' conditioning keeps the weights within ~1e-10 of FP64.    */
-/* The default is 4 for 1 <= m <= 6, 0 for m > 6 and 1 for m = 0.           */
+/* The default is 6 for m = 5, 6, 4 for 1 <= m <= 4, 0 for m > 6 and 1 for */
+/* m = 0.                                                                    */
 /* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form, =lu    */
 /* the Gaussian elimination.  rbffd_weights_autotune times every candidate   */
 /* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */

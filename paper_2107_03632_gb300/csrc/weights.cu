@@ -608,31 +608,18 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             }
             --na;
             group_sync<NT>();
-            // scale column k on the active rows and the g row; pivot row -> e_k
+            // every active row and the g row, one thread per row: scale its
+            // column k by the pivot reciprocal (pivot row -> e_k), then
+            // column j -= P[pr][j] * (scaled) P[r][k]; the pivot row, no
+            // longer active, is only read
+            const S* prow = P + (size_t)pr * LDS;
             for (int t = lane; t <= na; t += NT) {
                 const int r = (t < na) ? act[t] : n;
-                R::st(P + (size_t)r * LDS + k, R::mul(R::ld(P + (size_t)r * LDS + k), inv));
-            }
-            group_sync<NT>();
-            // column j -= P[pr][j] * column k, on active rows and the g row;
-            // flattened (row t, column jj) with incremental indices
-            const int cols = s - 1, rows = na + 1, total = rows * cols;
-            if (cols > 0) {
-                int t = lane / cols, jj = lane - (lane / cols) * cols;
-                const int stp = NT / cols, sj = NT - (NT / cols) * cols;
-                const S* prow = P + (size_t)pr * LDS;
-                for (int e = lane; e < total; e += NT) {
-                    const int j = jj + ((jj >= k) ? 1 : 0);
-                    const int r = (t < na) ? act[t] : n;
-                    S* rr = P + (size_t)r * LDS;
-                    R::st(rr + j, R::nfma(R::ld(prow + j), R::ld(rr + k), R::ld(rr + j)));
-                    t += stp;
-                    jj += sj;
-                    if (jj >= cols) {
-                        jj -= cols;
-                        ++t;
-                    }
-                }
+                S* rr = P + (size_t)r * LDS;
+                const V mk = R::mul(R::ld(rr + k), inv);
+                R::st(rr + k, mk);
+                for (int j = 0; j < k; ++j) R::st(rr + j, R::nfma(R::ld(prow + j), mk, R::ld(rr + j)));
+                for (int j = k + 1; j < s; ++j) R::st(rr + j, R::nfma(R::ld(prow + j), mk, R::ld(rr + j)));
             }
             group_sync<NT>();
         }
@@ -904,6 +891,10 @@ WCfg default_cfg(int n, int m) {
     c.kernel = m < 1 ? 1 : (m <= kDfMaxM ? 4 : 0);
     size_t smem = 0;
     c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
+    // large systems (m >= 5): four warps per stencil, as measured fastest
+    // (m = 6, n = 56, 1M nodes: 179 ms against 183 with two warps, 262 with one)
+    const WCfg big{6, 4};
+    if (m >= 5 && m <= kDfMaxM && cfg_valid(big, n, m)) return big;
     return c;
 }
 

@@ -177,7 +177,8 @@ def test_weights_config_table(cdll):
 
     c = rbffd.WeightsConfig()
     assert cdll.rbffd_weights_get_config(56, 6, ctypes.byref(c)) == 0
-    assert c.kernel == 4 and 1 <= c.warps_per_block <= 4  # double-float null-space by default, 1 <= m <= 6
+    assert (c.kernel, c.warps_per_block) == (6, 4)  # double-float null-space, four warps, by default at m = 6
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 4  # one warp at m = 4
     assert cdll.rbffd_weights_get_config(90, 8, ctypes.byref(c)) == 0 and c.kernel == 0  # FP64 beyond m = 6
     assert cdll.rbffd_weights_get_config(12, 0, ctypes.byref(c)) == 0 and c.kernel == 1  # m = 0: elimination
     pin = rbffd.WeightsConfig(1, 2, 0.0)
