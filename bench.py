@@ -70,6 +70,13 @@ EXPLICIT_SWEEP_n = (12, 15, 20, 30, 45, 60)
 ADJOINT_WORKLOAD = "adjoint_1M_m4_n30"
 ADJOINT_METRIC = ("differentiable solve nodes/s (forward + adjoint gradient dL/df, dL/dg), 1M-node disk, m=4, "
                   "n=30, tol 1e-10")
+# The support-size sweep of the implicit path: n in {12, 15, 20, 30, 45, 60}
+# x m in {2, 4, 6} (n >= s) on the 1M-node disk.
+SWEEP_WORKLOAD = "support_sweep_1M"
+SWEEP_METRIC = ("weights+solve nodes/s over the support sweep n x m on the 1M-node disk (the m = 4, n = 30 point; "
+                "every point in 'sweep')")
+SWEEP_N = (12, 15, 20, 30, 45, 60)
+SWEEP_M = (2, 4, 6)
 BATCH_RHS = 64
 BATCH_SAMPLE_RHS = 8  # oracle sample: right-hand sides of the smallest instance per step
 SEED = 2107
@@ -355,7 +362,9 @@ def run_reference(args):
         return run_reference_explicit(args)
     if args.workload == ADJOINT_WORKLOAD:
         return run_reference_adjoint(args)
-    h, m, n = WORKLOADS[args.workload]
+    # the sweep's reference point is m = 4, n = 30
+    h, m, n = WORKLOADS[args.workload] if args.workload != SWEEP_WORKLOAD else (None, 4, 30)
+    metric = SWEEP_METRIC if args.workload == SWEEP_WORKLOAD else METRIC
     res = cpu_baseline_subprocess(CPU_SAMPLE_H, m, n, steps=args.warmup + args.steps)
     timed = res[args.warmup:]
     nodes = timed[0][0]
@@ -364,7 +373,7 @@ def run_reference(args):
     sample = (f"oracle pipeline (brute-force kNN, per-stencil LU, CSR assembly, SuperLU solve) on the same "
               f"disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m={m}, n={n}) per step")
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric, "value": value, "unit": "nodes/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample_h": CPU_SAMPLE_H, "sample_nodes": nodes, "m": m, "n": n},
@@ -934,6 +943,99 @@ def run_reference_adjoint(args):
     return 0
 
 
+# ---------------------------------------------------------- support sweep ----
+def run_gpu_sweep(args):
+    """Per (n, m): stencils, autotuned weights, assembly, multigrid setup and
+    the mixed multigrid solve (tol 1e-10) on the 1M-node disk; CUDA-event
+    stage times (median of args.steps runs after args.warmup)."""
+    import torch
+
+    from fixtures import disk_nodes, manufactured
+    from paper_2107_03632_gb300 import rbffd
+
+    ws_, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rbffd.load()
+    h = 1.7725e-3
+    d = disk_nodes(h, SEED)
+    N = d.N
+    _, f, g = manufactured(d.xy)
+    xy, mask = torch.from_numpy(d.xy).to(dev), torch.from_numpy(d.is_dirichlet).to(dev)
+    fT, gT = torch.from_numpy(f).to(dev), torch.from_numpy(g).to(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    points = []
+    for m in SWEEP_M:
+        s = (m + 1) * (m + 2) // 2
+        for n in SWEEP_N:
+            if n < s:
+                continue
+            idx = rbffd.rbffd_stencils(xy, n)
+            cfg = rbffd.rbffd_weights_autotune(xy, idx, m)
+            w, st = rbffd.rbffd_weights(xy, idx, m)
+            A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
+            mg = rbffd.Multigrid(xy, mask, A)
+            opts = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mg)
+            wsol = rbffd.solve_workspace(N, opts, dev)
+            b = rbffd.rbffd_rhs(fT, gT, mask)
+            u = torch.zeros(N, dtype=torch.float64, device=dev)
+            times = {k: [] for k in ("stencils", "weights", "assemble", "mg_setup", "solve")}
+            info = None
+            for r in range(args.warmup + args.steps):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                ev[0].record()
+                rbffd.rbffd_stencils(xy, n, idx)
+                ev[1].record()
+                rbffd.rbffd_weights(xy, idx, m, w, st)
+                ev[2].record()
+                rbffd.rbffd_assemble(idx, w, mask, out=A)
+                ev[3].record()
+                mg.setup(xy, mask, A)
+                ev[4].record()
+                u.zero_()
+                _, info = rbffd.rbffd_solve(A, b, u, opts, wsol, raise_on_error=False)
+                ev[5].record()
+                torch.cuda.synchronize(dev)
+                if r >= args.warmup:
+                    for i, k in enumerate(times):
+                        times[k].append(ev[i].elapsed_time(ev[i + 1]))
+            # a point whose solve does not reach 1e-10 (or has singular stencils)
+            # is reported with its status, not dropped
+            status = rbffd.STATUS_NAMES.get(info["status_code"], str(info["status_code"]))
+            if int(st.sum()) != 0:
+                status = f"{int(st.sum())} singular stencils"
+            med = {k: float(np.median(v)) for k, v in times.items()}
+            roof = weights_roofline(cfg["kernel"], n, m, N, med["weights"], {})
+            points.append({"n": n, "m": m, "s": s, "status": status, "stages_ms": med, "iters": info["iters"],
+                           "rel_residual": info["rel_residual"], "weights_config": cfg,
+                           "weights_ns_per_node": 1e6 * med["weights"] / N,
+                           "weights_roofline_frac": roof["frac"], "weights_roofline_unit": roof["unit"],
+                           "fp64_equivalent_tflops": weights_flops(n, m) * N / (med["weights"] * 1e-3) / 1e12,
+                           "nodes_per_s_weights_solve": N / ((med["weights"] + med["assemble"] + med["mg_setup"]
+                                                              + med["solve"]) * 1e-3)})
+            print(json.dumps({"sweep_point": points[-1]}), file=sys.stderr, flush=True)
+            del A, mg, w, st, idx, wsol
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    ref = next(p for p in points if p["n"] == 30 and p["m"] == 4)
+    line = {
+        "metric": SWEEP_METRIC, "value": ref["nodes_per_s_weights_solve"], "unit": "nodes/s", "n_gpus": ws_,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * N / ref["nodes_per_s_weights_solve"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": SWEEP_WORKLOAD, "N": N, "h": h, "n": list(SWEEP_N), "m": list(SWEEP_M),
+                   "timing": "median over steps of CUDA-event stage times", "parallelism": f"replicas x{ws_}",
+                   "l2": "inputs larger than L2 at n >= 30 (CSR >= 0.36 GB)"},
+        "sweep": points, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm -----
 def run_gpu(args):
     import numpy as np
@@ -1206,7 +1308,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="disk_4M_m6_n56",
-                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, EXPLICIT_WORKLOAD, ADJOINT_WORKLOAD])
+                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, EXPLICIT_WORKLOAD, ADJOINT_WORKLOAD, SWEEP_WORKLOAD])
     ap.add_argument("--no-sweep", action="store_true", help="explicit workload: skip the N x n sweep")
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="mixed: residual drop per refinement pass")
     ap.add_argument("--inner-tol64", type=float, default=1e-3, help="FP64: residual drop per restarted pass")
@@ -1231,6 +1333,8 @@ def main():
         return run_gpu_explicit(args)
     if args.workload == ADJOINT_WORKLOAD:
         return run_gpu_adjoint(args)
+    if args.workload == SWEEP_WORKLOAD:
+        return run_gpu_sweep(args)
     return run_gpu(args)
 
 

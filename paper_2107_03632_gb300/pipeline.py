@@ -28,6 +28,8 @@ class PoissonOperator:
         self.A = _r.rbffd_assemble(self.idx, self.w, is_dirichlet, want_f32=want_f32)
         self._AT = None
         self._want_f32 = want_f32
+        self._mg = None
+        self._mga = None
 
     def check_stencils(self):
         bad = int(self.node_status.sum().item())
@@ -40,22 +42,41 @@ class PoissonOperator:
             self._AT = _r.rbffd_transpose(self.A, want_f32=self._want_f32)
         return self._AT
 
+    def multigrid(self) -> _r.Multigrid:
+        """The multigrid hierarchy of A (built on first use)."""
+        if self._mg is None:
+            self._mg = _r.Multigrid(self.xy, self.is_dirichlet, self.A)
+        return self._mg
+
+    def multigrid_adjoint(self) -> _r.Multigrid:
+        """The adjoint hierarchy, derived from the forward one."""
+        if self._mga is None:
+            self._mga = _r.Multigrid.adjoint_of(self.multigrid(), self.AT)
+        return self._mga
+
     def rhs(self, f: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
         return _r.rbffd_rhs(f, g, self.is_dirichlet)
 
-    def solve(self, b: torch.Tensor, x0: torch.Tensor | None = None, **opts):
+    def solve(self, b: torch.Tensor, x0: torch.Tensor | None = None, precond: str | None = None, **opts):
+        """precond "mg": BiCGSTAB preconditioned by the multigrid V-cycle."""
+        if precond == "mg":
+            opts["mg"] = self.multigrid()
         return _r.rbffd_solve(self.A, b, x0, _r.make_opts(**opts))
 
-    def solve_adjoint(self, dLdu: torch.Tensor, **opts):
+    def solve_adjoint(self, dLdu: torch.Tensor, precond: str | None = None, **opts):
+        if precond == "mg":
+            opts["mg"] = self.multigrid_adjoint()
         return _r.rbffd_solve_adjoint(self.AT, self.is_dirichlet, dLdu, None, _r.make_opts(**opts))
 
 
-def poisson_solve(xy, is_dirichlet, f, g, m: int, n: int, precision: str = "fp64", tol: float = 1e-10, **kw):
-    """u solving the RBF-FD Poisson problem; returns (u, info, operator)."""
+def poisson_solve(xy, is_dirichlet, f, g, m: int, n: int, precision: str = "fp64", tol: float = 1e-10,
+                  precond: str | None = None, **kw):
+    """u solving the RBF-FD Poisson problem; returns (u, info, operator).
+    precond "mg": multigrid-preconditioned BiCGSTAB."""
     op = PoissonOperator(xy, is_dirichlet, m, n, want_f32=(precision == "mixed"))
     op.check_stencils()
     b = op.rhs(f, g)
-    u, info = op.solve(b, precision=precision, tol=tol, **kw)
+    u, info = op.solve(b, precision=precision, tol=tol, precond=precond, **kw)
     return u, info, op
 
 
