@@ -323,3 +323,35 @@ def test_weights_collinear_stencil_flagged(lib, weights_kernel):
     _, st_ref = oracle.weights(xy, idx, 2)
     st = st.cpu().numpy()
     assert st_ref.all() and st.all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autograd_with_multigrid_vs_oracle(lib, precision):
+    """PoissonSolve (torch.autograd) with the multigrid forward and adjoint
+    solves: u and the gradients of L = sum_interior (u - u*)^2 with respect
+    to f and g match the oracle's direct and adjoint solves."""
+    import torch
+
+    from fixtures import fourier_sources
+    from paper_2107_03632_gb300 import pipeline
+
+    d = disk_nodes(0.02)
+    u_ex, f, g = manufactured(d.xy)
+    fstar = fourier_sources(d.xy, 1, 2108)[0]
+    ustar, _ = oracle.poisson_solve(d.xy, d.is_dirichlet, fstar, g, 4, 30)
+    op = pipeline.PoissonOperator(T(d.xy), T(d.is_dirichlet), 4, 30, want_f32=(precision == "mixed"))
+    fT = T(f).requires_grad_(True)
+    gT = T(g).requires_grad_(True)
+    opts = {"precond": "mg", "precision": precision, "tol": 1e-11}
+    u = pipeline.PoissonSolve.apply(fT, gT, op, opts)
+    inner = T((d.is_dirichlet == 0).astype(np.float64))
+    L = (((u - T(ustar)) ** 2) * inner).sum()
+    L.backward()
+    uu, (idx, w, rp, col, val, b) = oracle.poisson_solve(d.xy, d.is_dirichlet, f, g, 4, 30)
+    assert np.abs(u.detach().cpu().numpy() - uu).max() / np.abs(uu).max() <= 1e-8
+    dLdu = np.where(d.is_dirichlet == 1, 0.0, 2.0 * (uu - ustar))
+    gf, gg, _ = oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, dLdu)
+    # dL/du = 2 (u - u*) carries u's 1e-8-level solve error into the adjoint
+    assert np.abs(fT.grad.cpu().numpy() - gf).max() / np.abs(gf).max() <= 1e-6
+    assert np.abs(gT.grad.cpu().numpy() - gg).max() / np.abs(gg).max() <= 1e-6
+    assert torch.isfinite(fT.grad).all()
