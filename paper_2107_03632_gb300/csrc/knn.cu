@@ -219,27 +219,27 @@ struct TopList {
     }
 };
 
-// Lower bound of the squared distance from (qx, qy) to cell (cx, cy), minus
-// the margin.  Returns 0 when the query is inside (or near) the cell.
-__device__ __forceinline__ double cell_min_d2(const GridParams& p, double qx, double qy, int cx, int cy) {
-    const double lx = p.x0 + cx * p.cell, hx = lx + p.cell;
-    const double ly = p.y0 + cy * p.cell, hy = ly + p.cell;
-    double dx = fmax(fmax(lx - qx, qx - hx), 0.0);
-    double dy = fmax(fmax(ly - qy, qy - hy), 0.0);
-    dx = fmax(dx - p.margin, 0.0);
-    dy = fmax(dy - p.margin, 0.0);
-    return dx * dx + dy * dy;
-}
-
 // Queries: the indexed points themselves in cell order (qxy = sxy, qorig =
 // sorig: stencils), or separate points in their own order (qorig = NULL:
 // output row q).
+//
+// Search order: first the (2 R0 + 1)^2 block of cells around the query's
+// cell, R0 chosen on the host so that the block holds about n points, row
+// by row from the query's row outwards -- the points of a row of cells are
+// contiguous in the cell-sorted arrays, so a warp reads 32 candidates at a
+// time instead of one cell's few; then rings of cells until the gap to the
+// unvisited cells exceeds the n-th key.  The candidate keys (d^2, index) are
+// FP64 and exact; the pruning bounds for groups of cells are FP32, taken
+// relative to the query and shrunk by a slack, so they only ever keep a cell
+// that an exact bound would have skipped.  (On this chip the FP64 units issue
+// 2 lanes per clock per SM: per-cell FP64 bounds and one-cell candidate
+// batches made the search FP64-bound.)
 template <int SLOTS>
 __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sxy, const int* __restrict__ sorig,
                                                   const int* __restrict__ cell_start,
                                                   const GridParams* __restrict__ gp, int Nq,
                                                   const double2* __restrict__ qxy, const int* __restrict__ qorig,
-                                                  int n, int* __restrict__ idx) {
+                                                  int n, int R0, int* __restrict__ idx) {
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= Nq) return;
@@ -255,53 +255,83 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
     unsigned long long thr_d = ~0ull;  // key of entry n-1 (all-ones: list not full)
     unsigned int thr_j = ~0u;
 
-    for (int r = 0; r <= G; ++r) {
-        for (int yy = cy - r; yy <= cy + r; ++yy) {
-            if (yy < 0 || yy >= G) continue;
-            const bool edge_row = (yy == cy - r) || (yy == cy + r);
-            const int step = (edge_row || r == 0) ? 1 : 2 * r;
-            for (int xx = cx - r; xx <= cx + r; xx += step) {
-                if (xx < 0 || xx >= G) continue;
-                if (thr_d != ~0ull && !(cell_min_d2(p, Q.x, Q.y, xx, yy) <= key_d2(thr_d))) continue;
-                const int c = yy * G + xx;
-                const int beg = cell_start[c], end = cell_start[c + 1];
-                for (int base = beg; base < end; base += 32) {
-                    const int jj = base + lane;
-                    unsigned long long kd = ~0ull;
-                    unsigned int kj = ~0u;
-                    if (jj < end) {
-                        const double2 P = sxy[jj];
-                        const double dx = __dadd_rn(P.x, -Q.x);
-                        const double dy = __dadd_rn(P.y, -Q.y);
-                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                        kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
-                        kj = (unsigned int)sorig[jj];
-                    }
-                    unsigned int m = __ballot_sync(0xffffffffu, key_less(kd, kj, thr_d, thr_j));
-                    while (m) {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1;
-                        const unsigned long long id = __shfl_sync(0xffffffffu, kd, src);
-                        const unsigned int ij = __shfl_sync(0xffffffffu, kj, src);
-                        if (!key_less(id, ij, thr_d, thr_j)) continue;  // threshold moved
-                        top.insert(id, ij, lane);
-                        top.get(n - 1, thr_d, thr_j);
-                    }
-                }
+    // candidates at sorted positions [beg, end)
+    auto scan = [&](int beg, int end) {
+        for (int base = beg; base < end; base += 32) {
+            const int jj = base + lane;
+            unsigned long long kd = ~0ull;
+            unsigned int kj = ~0u;
+            if (jj < end) {
+                const double2 P = sxy[jj];
+                const double dx = __dadd_rn(P.x, -Q.x);
+                const double dy = __dadd_rn(P.y, -Q.y);
+                const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
+                kj = (unsigned int)sorig[jj];
+            }
+            unsigned int m = __ballot_sync(0xffffffffu, key_less(kd, kj, thr_d, thr_j));
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned long long id = __shfl_sync(0xffffffffu, kd, src);
+                const unsigned int ij = __shfl_sync(0xffffffffu, kj, src);
+                if (!key_less(id, ij, thr_d, thr_j)) continue;  // threshold moved
+                top.insert(id, ij, lane);
+                top.get(n - 1, thr_d, thr_j);
             }
         }
-        // Whole grid visited?
-        if (cx - r <= 0 && cy - r <= 0 && cx + r >= G - 1 && cy + r >= G - 1) break;
-        if (thr_d == ~0ull) continue;
-        // Distance from Q to the outside of the visited block (sides at the
-        // grid border have nothing beyond them).
+    };
+    // FP32 lower bound of d^2 from the query to the cells [xl, xh] of row yy,
+    // relative to the query's cell corner (exact in FP64), shrunk by a slack;
+    // true when all of them lie beyond the n-th key
+    const float fx = (float)(Q.x - (p.x0 + cx * p.cell));
+    const float fy = (float)(Q.y - (p.y0 + cy * p.cell));
+    const float cf = (float)p.cell;
+    const float slack = (float)p.margin + 1e-4f * cf;
+    auto beyond = [&](int xl, int xh, int yy) -> bool {
+        if (thr_d == ~0ull) return false;
+        const float lx = (float)(xl - cx) * cf - fx, hx = (float)(xh + 1 - cx) * cf - fx;
+        const float ly = (float)(yy - cy) * cf - fy, hy = ly + cf;
+        const float dx = fmaxf(fmaxf(fmaxf(lx, -hx), 0.f) - slack, 0.f);
+        const float dy = fmaxf(fmaxf(fmaxf(ly, -hy), 0.f) - slack, 0.f);
+        return (dx * dx + dy * dy) * (1.0f - 1e-4f) > (float)key_d2(thr_d);
+    };
+    auto row_range = [&](int xl, int xh, int yy) {
+        if (!beyond(xl, xh, yy)) scan(cell_start[yy * G + xl], cell_start[yy * G + xh + 1]);
+    };
+    // true when the cells within ring r hold the n nearest: whole grid
+    // visited, or the gap from Q to the unvisited cells exceeds the n-th key
+    auto done = [&](int r) -> bool {
+        if (cx - r <= 0 && cy - r <= 0 && cx + r >= G - 1 && cy + r >= G - 1) return true;
+        if (thr_d == ~0ull) return false;
         double gap = INFINITY;
         if (cx - r > 0) gap = fmin(gap, Q.x - (p.x0 + (cx - r) * p.cell));
         if (cx + r < G - 1) gap = fmin(gap, (p.x0 + (cx + r + 1) * p.cell) - Q.x);
         if (cy - r > 0) gap = fmin(gap, Q.y - (p.y0 + (cy - r) * p.cell));
         if (cy + r < G - 1) gap = fmin(gap, (p.y0 + (cy + r + 1) * p.cell) - Q.y);
         gap -= p.margin;
-        if (gap > 0.0 && gap * gap > key_d2(thr_d)) break;
+        return gap > 0.0 && gap * gap > key_d2(thr_d);
+    };
+
+    // the block, rows from the query's outwards
+    const int xlo = max(cx - R0, 0), xhi = min(cx + R0, G - 1);
+    for (int k = 0; k <= 2 * R0; ++k) {
+        const int yy = cy + ((k & 1) ? -((k + 1) >> 1) : (k >> 1));
+        if (yy < 0 || yy >= G) continue;
+        row_range(xlo, xhi, yy);
+    }
+    // then rings: the two edge rows as ranges, the side cells one by one
+    for (int r = R0; !done(r) && r <= G; ) {
+        ++r;
+        for (int yy = cy - r; yy <= cy + r; ++yy) {
+            if (yy < 0 || yy >= G) continue;
+            if (yy == cy - r || yy == cy + r) {
+                row_range(max(cx - r, 0), min(cx + r, G - 1), yy);
+            } else {
+                if (cx - r >= 0) row_range(cx - r, cx - r, yy);
+                if (cx + r < G) row_range(cx + r, cx + r, yy);
+            }
+        }
     }
 
     int* out = idx + (int64_t)qo * n;
@@ -311,6 +341,10 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
         if (e < n) out[e] = (int)top.j[s];
     }
 }
+
+// Block radius of the first search phase: about n points in (2 R0 + 1)^2
+// cells at ~3 points per cell, plus half a cell.
+int block_radius(int n) { return std::max(1, (int)std::ceil(std::sqrt((double)n / (3.0 * 3.14159265358979)) + 0.5)); }
 
 // Cells per axis: about kOcc nodes per cell on a square domain, capped.
 int grid_side(int64_t N, int n) {
@@ -394,12 +428,13 @@ int rbffd::knn_search(const double* xy, int64_t N, const double* qxy, int64_t Nq
     const int blocks = (int)((Nq + warps_per_block - 1) / warps_per_block);
     const double2* q = qxy ? reinterpret_cast<const double2*>(qxy) : L.sxy;
     const int* qo = qxy ? nullptr : L.sorig;
+    const int R0 = block_radius(n);
     if (n <= 32)
-        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
+        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
     else if (n <= 64)
-        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
+        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
     else
-        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, idx);
+        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
     note_launches(5);  // bbox, setup, count, scatter, knn (+3 in the scan)
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;
