@@ -394,8 +394,12 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
                         void* ws, size_t ws_bytes, void* stream);
 
 /* Gradient of the misfit L(u) = sum over interior nodes of (u - u_target)^2 */
-/* (the loss of the differentiable solve): dLdu = 2 (u - u_target) on        */
-/* interior nodes, 0 on Dirichlet nodes.  Device arrays of N; asynchronous. */
+/* (the loss of the differentiable solve; the paper's Sec. VI names         */
+/* gradient-based use of the solver as future work and prints no loss):     */
+/* dLdu = 2 (u - u_target) on interior nodes, 0 on Dirichlet nodes.          */
+/*   u, u_target, dLdu : device, N float64 each; is_dirichlet : N uint8.     */
+/* Asynchronous on `stream`.  Errors: RBFFD_ERR_INVALID_ARG (null pointer,   */
+/* N <= 0), returned before anything is enqueued.                            */
 int rbffd_misfit_grad(const double* u, const double* u_target, const uint8_t* is_dirichlet, int64_t N,
                       double* dLdu, void* stream);
 

@@ -151,6 +151,10 @@ def test_multigrid_argument_errors(cdll):
     assert cdll.rbffd_mg_level(None, 0, ctypes.byref(lv)) == INVALID
     assert cdll.rbffd_mg_apply(ctypes.byref(h), 0, 0x4000, 0x5000, None) == INVALID
     assert cdll.rbffd_mg_apply(None, 0, 0x4000, 0x5000, None) == INVALID
+    # misfit gradient: argument errors before any launch
+    assert cdll.rbffd_misfit_grad(None, 0x4000, 0x5000, 10, 0x6000, None) == INVALID
+    assert cdll.rbffd_misfit_grad(0x3000, 0x4000, 0x5000, 0, 0x6000, None) == INVALID
+    assert cdll.rbffd_misfit_grad(0x3000, 0x4000, None, 10, 0x6000, None) == INVALID
     h2 = rbffd.MgHandle()
     assert cdll.rbffd_mg_adjoint_of(ctypes.byref(h), ctypes.byref(A), None, ctypes.byref(h2), 0x8000, ws,
                                     None) == INVALID  # forward hierarchy never built
