@@ -352,6 +352,66 @@ def cpu_baseline_subprocess(h: float, m: int, n: int, steps: int = 1, batch: boo
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def _oracle_knn_chunk(a):
+    import oracle
+
+    xy, n, q = a
+    return oracle.knn_query(xy, n, q)
+
+
+def _oracle_weights_chunk(a):
+    import oracle
+
+    xy, idx, m, nodes = a
+    return oracle.weights(xy, idx, m, nodes=nodes)
+
+
+def oracle_sample_step_parallel(h: float, m: int, n: int, procs: int):
+    """The oracle pipeline of oracle_sample_step with its loops over nodes (the
+    brute-force kNN and the per-stencil solves) split into contiguous chunks
+    over `procs` worker processes; assembly and the sparse solve sequential.
+    Returns (nodes, seconds, per-stage seconds); the pool is started before
+    the clock."""
+    import multiprocessing as mp
+
+    import oracle
+    from fixtures import disk_nodes, manufactured
+
+    d = disk_nodes(h, SEED)
+    u, f, g = manufactured(d.xy)
+    chunks = np.array_split(np.arange(d.N), procs * 4)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_knn_chunk, [(d.xy[:64], 4, np.arange(4))] * procs)  # start the workers
+        t0 = time.perf_counter()
+        idx = np.concatenate(pool.map(_oracle_knn_chunk, [(d.xy, n, c) for c in chunks]))
+        t1 = time.perf_counter()
+        res = pool.map(_oracle_weights_chunk, [(d.xy, idx, m, c) for c in chunks])
+        t2 = time.perf_counter()
+    w = np.concatenate([r[0] for r in res])
+    if np.concatenate([r[1] for r in res]).any():
+        raise RuntimeError("singular stencil in the CPU sample")
+    rp, col, val = oracle.assemble(idx, w, d.is_dirichlet)
+    oracle.solve_direct(rp, col, val, oracle.rhs(f, g, d.is_dirichlet))
+    t3 = time.perf_counter()
+    return d.N, t3 - t0, {"knn": t1 - t0, "weights": t2 - t1, "assemble_solve": t3 - t2}
+
+
+def cpu_baseline_parallel_subprocess(h: float, m: int, n: int, procs: int):
+    """oracle_sample_step_parallel in a child interpreter without the GPU, BLAS
+    at one thread per worker."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_step_parallel(%r, %d, %d, %d)))" % (ROOT, h, m, n, procs))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800,
+                         cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -1055,7 +1115,6 @@ def run_gpu(args):
 
         dist.init_process_group("nccl", device_id=dev)
     rbffd.load()
-    lib = rbffd.load()
 
     h, m, n = WORKLOADS[args.workload]
     d = disk_nodes(h, SEED)
@@ -1084,9 +1143,19 @@ def run_gpu(args):
     A = rbffd.CsrMatrix(row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
                         torch.empty(nnz, dtype=torch.float64, device=dev),
                         torch.empty(nnz, dtype=torch.float32, device=dev))
-    # one-time tuning of the weight solve's launch configuration for (n, m)
+    # one-time tuning of the weight solve's launch configuration for (n, m):
+    # the double-float candidates (for the labelled df leg), then the FP64
+    # ones, which stay in force for the headline
     rbffd.rbffd_stencils(xy, n, idx, ws_knn)
-    wcfg = rbffd.rbffd_weights_autotune(xy, idx, m)
+    wcfg_df = rbffd.rbffd_weights_autotune(xy, idx, m, "df") if (args.df_steps > 0 and m <= 6) else None
+    if args.no_autotune:  # the library's default configuration (FP64)
+        wcfg = rbffd.weights_config(n, m)
+    else:
+        wcfg = rbffd.rbffd_weights_autotune(xy, idx, m, "fp64")
+
+    def use_weights(cfg):
+        rbffd.set_weights_config(n, m, cfg["kernel"], cfg["warps_per_block"])
+
     use_mg = args.precond == "mg"
     mg = None
     if use_mg:
@@ -1140,6 +1209,9 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
 
     def timed_loop(precision, k, profile=False):
+        """k steps bracketed by events; per-stage events (six records per step,
+        on the launching stream) give the stage times; profile=True also
+        brackets every SpMV and finest V-cycle sweep (a separate loop)."""
         stage = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(k)]
         infos = []
         barrier()
@@ -1161,22 +1233,59 @@ def run_gpu(args):
         st_ms = np.array([[stage[i][j].elapsed_time(stage[i][j + 1]) for j in range(5)] for i in range(k)]).mean(0)
         return ms, wall, st_ms, infos, prof
 
-    # ---- warm-up, then the timed mixed-precision steps ----
+    def stages(st_ms):
+        return {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "mg_setup": st_ms[3],
+                "solve": st_ms[4]}
+
+    def solve_summary(infos):
+        return {"iters": [i["iters"] for i in infos], "passes": [i["outer_sweeps"] for i in infos],
+                "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos],
+                "rel_residual": [i["rel_residual"] for i in infos]}
+
+    # ---- warm-up, then the timed steps: FP64 weights, mixed solve ----------
     for _ in range(args.warmup):
         step("mixed")
     clocks = ClockSampler(local)
     clocks.start()
-    ms, wall, st_ms, infos, prof = timed_loop("mixed", args.steps, profile=True)
-    clk = clocks.stop()
+    ms, wall, st_ms, infos, prof_main = timed_loop("mixed", args.steps)
     value, ms = replica_value(dist, ws, N, args.steps, ms, dev)
     ms_step = ms / args.steps
 
-    # ---- the same steps with the plain FP64 solve ----
+    # ---- the same steps with the FP64 solve (FP64 V-cycle) ------------------
     k64 = args.fp64_steps if args.fp64_steps is not None else args.steps
+    fp64_line = None
     if k64 > 0:
         step("fp64")
-        ms64, wall64, st64, infos64, prof64 = timed_loop("fp64", k64, profile=True)
-        ms64 = max_over_ranks(dist, ms64, dev)
+        ms64, wall64, st64, infos64, _ = timed_loop("fp64", k64)
+        value64, ms64 = replica_value(dist, ws, N, k64, ms64, dev)
+        fp64_line = {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
+                     "precision": "FP64 weights, FP64 BiCGSTAB right-preconditioned by an FP64 V-cycle",
+                     "stages_ms": stages(st64), **solve_summary(infos64)}
+    clk = clocks.stop()
+
+    # ---- labelled extra: the same mixed step with double-float weights ------
+    df_line = None
+    kdf = min(args.df_steps, args.steps)
+    if wcfg_df is not None and kdf > 0:
+        use_weights(wcfg_df)
+        step("mixed")
+        msdf, _, stdf, infosdf, _ = timed_loop("mixed", kdf)
+        use_weights(wcfg)
+        valuedf, msdf = replica_value(dist, ws, N, kdf, msdf, dev)
+        df_line = {"value": valuedf, "ms_per_step": msdf / kdf, "steps": kdf, "weights_precision": "df32",
+                   "weights_config": wcfg_df,
+                   "note": ("weight solves in double-float arithmetic (pairs of floats, ~48 significant bits, "
+                            "FP32 pipe); not the FP64 weights the headline uses"),
+                   "stages_ms": stages(stdf),
+                   "weights_roofline": weights_roofline(wcfg_df["kernel"], n, m, N, stdf[1], {}),
+                   **solve_summary(infosdf)}
+
+    # ---- per-kernel figures of the solve: a separate, profiled loop ---------
+    kp = max(1, min(2, args.steps))
+    _, _, _, _, prof = timed_loop("mixed", kp, profile=True)
+    prof64 = None
+    if k64 > 0:
+        _, _, _, _, prof64 = timed_loop("fp64", kp, profile=True)
 
     # ---- end to end through the API from pinned host buffers ----
     h2d = (h_xy.numel() * 8 + h_mask.numel() + h_f.numel() * 8 + h_g.numel() * 8)
@@ -1203,8 +1312,6 @@ def run_gpu(args):
     # ---- correctness of the timed solves (host check, outside timing) ----
     err_exact = float(np.abs(h_u.numpy() - u_ex).max())
 
-    # ---- roofline of the dominant kernel: the finest-level V-cycle sweep
-    # (multigrid) or the inner SpMV (Jacobi) ----
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
 
@@ -1221,26 +1328,16 @@ def run_gpu(args):
     dom_name = ("mg_jacobi_kernel<float> (finest-level damped Jacobi sweep of the float32 V-cycle)" if use_mg
                 else "spmv_df_kernel (inner BiCGSTAB SpMV, float32 values)")
     outer_ms, outer_bytes, outer_gbs, outer_n = per_launch(prof, "spmv64")
-    fp64_line = None
-    if k64 > 0:
+    if fp64_line is not None:
         sp64_ms, sp64_bytes, sp64_gbs, _ = per_launch(prof64, "mg" if use_mg else "spmv64")
         o64_ms, o64_bytes, o64_gbs, _ = per_launch(prof64, "spmv64")
-        fp64_line = {"value": ws * N * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
-                     "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol64,
-                     "stages_ms": {"stencils": st64[0], "weights": st64[1], "assemble_rhs": st64[2],
-                                   "mg_setup": st64[3], "solve": st64[4]},
-                     "iters": [i["iters"] for i in infos64], "passes": [i["outer_sweeps"] for i in infos64],
-                     "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos64],
-                     "rel_residual": [i["rel_residual"] for i in infos64],
-                     "dominant_kernel": ("mg_jacobi_kernel<double> (finest-level sweep, FP64 V-cycle)" if use_mg
-                                         else "spmv64_kernel"),
-                     "dominant_gbs": sp64_gbs, "dominant_frac_hbm": sp64_gbs / hbm,
-                     "dominant_ms_per_launch": sp64_ms,
-                     "spmv64_gbs": o64_gbs, "spmv64_frac_hbm": o64_gbs / hbm, "spmv64_ms_per_launch": o64_ms}
+        fp64_line.update({
+            "dominant_solve_kernel": ("mg_jacobi_kernel<double> (finest-level sweep, FP64 V-cycle)" if use_mg
+                                      else "spmv64_kernel"),
+            "dominant_gbs": sp64_gbs, "dominant_frac_hbm": sp64_gbs / hbm, "dominant_ms_per_launch": sp64_ms,
+            "spmv64_gbs": o64_gbs, "spmv64_frac_hbm": o64_gbs / hbm, "spmv64_ms_per_launch": o64_ms})
 
     fp64_peak = fp64_peak_tflops(torch, dev) if not args.no_peak_probe else float("nan")
-    w_flops = N * weights_flops(n, m)
-    w_tflops = w_flops / (st_ms[1] * 1e-3) / 1e12
     lu_equiv = N * (2.0 / 3.0 * M ** 3 + 2.0 * M * M) / (st_ms[1] * 1e-3) / 1e12
 
     cpu = None
@@ -1250,6 +1347,14 @@ def run_gpu(args):
         cpu = {"value": nodes / secs, "unit": "nodes/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle pipeline (brute-force kNN, per-stencil LU, CSR assembly, SuperLU) on the same "
                          f"disk recipe at h={CPU_SAMPLE_H} ({nodes} nodes, m={m}, n={n}), one core, {secs:.1f} s"}
+        procs = os.cpu_count() or 1
+        resp = cpu_baseline_parallel_subprocess(CPU_SAMPLE_H, m, n, procs)
+        nodes_p, secs_p, stage_p = resp
+        cpu["all_cores"] = {
+            "value": nodes_p / secs_p, "unit": "nodes/s", "cores": procs, "nproc": procs,
+            "sample": (f"the same oracle pipeline with kNN and weights split over {procs} worker processes "
+                       f"(one thread each), assembly and SuperLU sequential; {secs_p:.1f} s"),
+            "stages_s": stage_p}
 
     roof_solve = {"kernel": dom_name, "bound": "hbm", "achieved": sp_gbs,
                   "peak": hbm, "unit": "GB/s", "frac": sp_gbs / hbm,
@@ -1257,30 +1362,40 @@ def run_gpu(args):
                               (SPMV_DF_TRAFFIC["traffic_over_algorithmic"] * sp_bytes
                                if spmv_df_source_hash() == SPMV_DF_TRAFFIC["source_sha256_16"] else None)),
                   "peak_kind": peak_kind, "bytes_per_launch": sp_bytes, "ms_per_launch": sp_ms,
-                  "launches": sp_n, "ms_per_step": sp_ms * sp_n / max(args.steps, 1)}
+                  "launches": sp_n, "ms_per_step": sp_ms * sp_n / max(kp, 1),
+                  "measured_in": "separate profiled loop (events around every sweep)"}
     roof_weights = weights_roofline(wcfg["kernel"], n, m, N, st_ms[1],
-                                    {"cublas_dgemm_tflops": fp64_peak, "lu_equivalent_tflops": lu_equiv})
+                                    {"cublas_dgemm_tflops": fp64_peak,
+                                     "frac_of_dgemm": (weights_flops(n, m) * N / (st_ms[1] * 1e-3) / 1e12
+                                                       / fp64_peak if fp64_peak == fp64_peak else None),
+                                     "lu_equivalent_tflops": lu_equiv,
+                                     "measured_in": "timed region (events around the weights launch)"})
     weights_dominate = st_ms[1] > roof_solve["ms_per_step"]
-    iters = [i["iters"] for i in infos]
     line = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "nnz": nnz, "h": h, "m": m, "n": n, "seed": SEED,
                    "tol": 1e-10,
-                   "precision": ("mixed (FP64 BiCGSTAB right-preconditioned by a float32 multigrid V-cycle)"
-                                 if use_mg else "mixed (f32 inner BiCGSTAB, f64 refinement)"),
+                   "precision_by_stage": {
+                       "stencils": "f64 distance keys (f32 pruning bounds)",
+                       "weights": "f64 (null-space elimination + L D L^T, FP64 throughout)",
+                       "assembly": "f64 values (+ f32 copy for the preconditioner)",
+                       "krylov": "f64 BiCGSTAB, f64 residual and updates",
+                       "preconditioner": ("float32 multigrid V-cycle (coarse weights in double-float)" if use_mg
+                                          else "f32 inner BiCGSTAB inside f64 refinement")},
+                   "precision": ("mixed: FP64 BiCGSTAB right-preconditioned by a float32 multigrid V-cycle "
+                                 "(float32 preconditioner)" if use_mg else
+                                 "mixed (f32 inner BiCGSTAB, f64 refinement)"),
                    "precond": (f"multigrid V({args.mg_nu},{args.mg_nu}) omega {args.mg_omega}, levels "
                                f"{mg.levels()}" if use_mg else "jacobi"),
                    "inner_tol": args.mg_pass_tol if use_mg else args.inner_tol,
-                   "parallelism": f"replicas x{ws}", "weights_config": wcfg,
+                   "parallelism": f"replicas x{ws}", "weights_config": wcfg, "weights_precision": "f64",
                    "l2": "inputs larger than L2 (CSR ~%.1f GB)" % ((nnz * 16) / 1e9)},
-        "stages_ms": {"stencils": st_ms[0], "weights": st_ms[1], "assemble_rhs": st_ms[2], "mg_setup": st_ms[3],
-                      "solve": st_ms[4]},
-        "solve": {"iters": iters, "refinements": [i["outer_sweeps"] for i in infos],
-                  "status": [rbffd.STATUS_NAMES.get(i["status_code"], i["status_code"]) for i in infos],
-                  "rel_residual": [i["rel_residual"] for i in infos], "max_err_vs_exact": err_exact},
+        "stages_ms": stages(st_ms),
+        "solve": {**solve_summary(infos), "max_err_vs_exact": err_exact},
         "fp64": fp64_line,
+        "df_weights": df_line,
         # the dominant kernel of the step (largest device time) and the solver's own
         "roofline": roof_weights if weights_dominate else roof_solve,
         "solve_roofline": roof_solve if weights_dominate else roof_weights,
@@ -1288,7 +1403,7 @@ def run_gpu(args):
                        "frac": outer_gbs / hbm, "ms_per_launch": outer_ms, "launches": outer_n},
         "e2e": ({"value": e2e_value, "unit": "nodes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "steps": args.e2e_steps} if e2e_value is not None else None),
-        "gpu_launches": prof["launches"],
+        "gpu_launches": prof_main["launches"],
         "clocks": clk,
         "cpu_baseline": cpu,
         "wall_s_timed": wall,
@@ -1318,9 +1433,14 @@ def main():
     ap.add_argument("--mg-omega", type=float, default=0.6, help="Jacobi damping of the V-cycle")
     ap.add_argument("--mg-pass-tol", type=float, default=1e-10,
                     help="multigrid: residual drop per restarted BiCGSTAB pass (1e-10: a single pass)")
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps with the FP64 solve (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps with the FP64 solve (default: --steps; 0: skip)")
+    ap.add_argument("--df-steps", type=int, default=5,
+                    help="timed steps with double-float weights, a labelled extra (at most --steps; 0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default FP64 weight-solve configuration (profiling runs)")
     ap.add_argument("--no-peak-probe", action="store_true", help="skip the cuBLAS DGEMM FP64 peak probe")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -115,11 +115,16 @@ int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx,
 /*      [ Phi  P ] [ w ]   [ lap phi_j(x_i) ]      Phi_jk = |x_j - x_k|^3    */
 /*      [ P^T  0 ] [ l ] = [ lap p_k(x_i)   ]      P_jk   = p_k(x_j)         */
 /* is formed in coordinates shifted to x_i and scaled by delta_i (the        */
-/* largest |x_j - x_i| in the stencil), solved in FP64, and                  */
-/* w[i*n + j] = wh_j / delta_i^2.  Two solvers, one warp per stencil with    */
-/* the system in shared memory: null-space elimination (Gauss-Jordan with   */
-/* row pivoting on P, Cholesky of Z^T Phi Z; the default for m >= 1) and     */
-/* Gaussian elimination with partial pivoting of the whole system (m = 0).   */
+/* largest |x_j - x_i| in the stencil), solved, and                          */
+/* w[i*n + j] = wh_j / delta_i^2.  The system of one stencil lives in shared */
+/* memory and one, two or four warps solve it.  Solvers: null-space         */
+/* elimination (Gauss-Jordan with row pivoting on P, then an L D L^T        */
+/* factorisation of the positive definite Z^T Phi Z; m >= 1) and Gaussian   */
+/* elimination with partial pivoting of the whole system (any m, the only   */
+/* one for m = 0).  Arithmetic: FP64 by default; a double-float form of the */
+/* null-space solver (pairs of floats, ~48 significant bits, on the FP32    */
+/* pipe) is used only when selected through rbffd_weights_set_config or     */
+/* rbffd_weights_autotune with RBFFD_WEIGHTS_DF / _ANY.                      */
 /* Monomials are in graded order 1, x, y, x^2, xy, y^2, ...; s = (m+1)(m+2)/2.*/
 /*   m           : 0 <= m <= 8 and s <= n (the system needs n >= s nodes).   */
 /*   w           : N x n float64, written (rows of singular stencils: 0).    */
@@ -133,24 +138,29 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* and its threads per stencil -- 0 null-space elimination, one warp per    */
 /* stencil, 1..4 stencils (warps) per block; 1 full Gaussian elimination,  */
 /* likewise; 2 / 3 null-space elimination with two / four warps per        */
-/* stencil, one stencil per block (warps_per_block = 2 / 4); 4 / 5 / 6 the  */
-/* same three null-space forms in double-float arithmetic (pairs of floats, */
-/* ~48 significant bits, on the FP32 pipe; FP64 only for the coordinate    */
-/* scaling and the final division), offered for 1 <= m <= 6, where the     */
-/* scaled systems' conditioning keeps the weights within ~1e-10 of FP64.    */
-/* The default is 6 for m = 5, 6, 4 for 1 <= m <= 4, 0 for m > 6 and 1 for */
-/* m = 0.                                                                    */
-/* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form, =lu    */
-/* the Gaussian elimination.  rbffd_weights_autotune times every candidate   */
-/* that fits in shared memory on the first min(N, 128 x SMs) stencils of     */
-/* the given set (3 launches each after one warm-up, CUDA events), records  */
-/* the fastest for (current device, n, m) in a process-wide table that      */
+/* stencil, one stencil per block (warps_per_block = 2 / 4); all in FP64.  */
+/* 4 / 5 / 6: the same three null-space forms in double-float arithmetic   */
+/* (FP64 only for the coordinate shift/scale and the final scaling),       */
+/* offered for 1 <= m <= 6, where the scaled systems' conditioning keeps    */
+/* the weights within ~1e-10 of FP64.                                       */
+/* The default is FP64: 2 (two warps per stencil) for m >= 5 when it fits,  */
+/* 0 for other m >= 1, 1 for m = 0.                                          */
+/* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form with    */
+/* one warp per stencil, =lu the Gaussian elimination.                      */
+/* rbffd_weights_autotune times every candidate of the given precision      */
+/* (RBFFD_WEIGHTS_FP64: kernels 0-3; RBFFD_WEIGHTS_DF: 4-6; _ANY: all) that  */
+/* fits in shared memory on the first min(N, 128 x SMs) stencils of the     */
+/* given set (3 launches each after one warm-up, CUDA events), records the  */
+/* fastest for (current device, n, m) in a process-wide table that          */
 /* rbffd_weights and rbffd_solve_batched then use, and returns it in *best   */
 /* (may be NULL).  w and node_status serve as its scratch (their first rows */
 /* are overwritten).  Synchronises `stream`.  (Autotuning has no            */
 /* counterpart in the paper.)  rbffd_weights_get_config returns the          */
 /* configuration in force; rbffd_weights_set_config pins one (NULL: back to  */
 /* the default above, warps per block from the shared-memory footprint).   */
+#define RBFFD_WEIGHTS_FP64 0
+#define RBFFD_WEIGHTS_DF 1
+#define RBFFD_WEIGHTS_ANY 2
 typedef struct rbffd_weights_config {
     int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 / 3 null-space (2 / 4 warps), */
                              /* 4 / 5 / 6 as 0 / 2 / 3 in double-float arithmetic                         */
@@ -158,7 +168,8 @@ typedef struct rbffd_weights_config {
     double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
 } rbffd_weights_config;
 int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
-                           double* w, int32_t* node_status, rbffd_weights_config* best, void* stream);
+                           double* w, int32_t* node_status, int32_t precision, rbffd_weights_config* best,
+                           void* stream);
 int rbffd_weights_get_config(int32_t n, int32_t m, rbffd_weights_config* cfg);
 int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weights_config* cfg);
 

@@ -88,32 +88,74 @@ __device__ __forceinline__ float shadow_value(unsigned long long seed, long long
     return (float)(z >> 40) * 0x1p-23f - 1.0f;
 }
 
-// FP64 reciprocal and reciprocal square root by Newton-Raphson refinement of
-// a float32 seed (Newton's method on f(y) = 1/y - a and f(y) = 1/y^2 - a:
-// y <- y + y (1 - a y) and y <- y + y (1/2 - (a/2) y^2), each step doubling
-// the correct bits: ~22 -> ~44 -> full double precision, within about one
-// ulp of the correctly rounded result).  Two FMAs per step against the much
-// longer correctly rounded division and square root; the weight solves call
-// them on scalars that every lane of a warp computes.  Outside the float32
-// normal range the seeds are meaningless, so there the IEEE operations run.
+// ---- FP64 scalars with few FP64 instructions ----------------------------
+// On this GPU the FP64 units issue 2 lanes per clock per SM (the FP32 pipe
+// 128), and conversions between float and double and FP64 compares occupy
+// them like a DFMA.  The helpers below move a double's leading bits into a
+// float seed, and a float seed back into a double, with integer
+// instructions only, and finish with FMA-based Newton-type corrections.
+
+// Exponent field of a within [1023 - 100, 1023 + 100], i.e. 2^-100 <= |a| <
+// 2^101: the range where the float seeds below are normal floats.
+__device__ __forceinline__ bool seed_range(double a) {
+    const unsigned e = ((unsigned)__double2hiint(a) >> 20) & 0x7ffu;
+    return e - (1023u - 100u) <= 200u;
+}
+// Sign bit of a clear (a >= +0, or a NaN with the sign clear).
+__device__ __forceinline__ bool sign_clear(double a) { return __double2hiint(a) >= 0; }
+// a truncated to float (sign, exponent rebiased, leading 23 fraction bits);
+// valid where seed_range(a).
+__device__ __forceinline__ float f32_trunc(double a) {
+    const unsigned hi = (unsigned)__double2hiint(a), lo = (unsigned)__double2loint(a);
+    const unsigned mag = __funnelshift_l(lo, (hi & 0x7fffffffu) - (896u << 20), 3);
+    return __uint_as_float(mag | (hi & 0x80000000u));
+}
+// A normal float as a double (exact).
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned hi = (((b & 0x7fffffffu) >> 3) + (896u << 20)) | (b & 0x80000000u);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+// IEEE bit tests without FP64 compares.
+__device__ __forceinline__ bool finite64(double a) {
+    return (((unsigned)__double2hiint(a) >> 20) & 0x7ffu) != 0x7ffu;
+}
+__device__ __forceinline__ bool positive_finite64(double a) {  // 0 < a < inf
+    return (unsigned long long)__double_as_longlong(a) - 1ull < 0x7fefffffffffffffull;
+}
+
+// FP64 reciprocal, reciprocal square root and square root from a float
+// seed y0 (relative error e0 <= ~2^-21: the float function's own error plus
+// the truncation of a to float).
+//  1/a:      e = 1 - a y0, y = y0 (1 + e + e^2)          error ~e0^3 ~ 2^-63
+//  a^-1/2:   e = 1 - a y0^2, y = y0 (1 + e/2 + 3e^2/8)    error ~(5/16) e0^3
+//  sqrt(a):  s = a y0, then twice s += (a - s^2) y0/2     error ~(3/2) e0^3
+// (the truncated Taylor series of (1 - e)^-1 and (1 - e)^-1/2, and Newton's
+// iteration for s^2 = a with the derivative 2 s frozen at 2/y0).  Each ends
+// with one rounding: within about one ulp of the correctly rounded result.
+// Outside seed_range (and for a <= 0 where the root is asked) the IEEE
+// operations run.
 __device__ __forceinline__ double rcp64(double a) {
-    const double m = fabs(a);
-    if (!(m > 1e-30 && m < 1e30)) return __ddiv_rn(1.0, a);
-    double y = (double)__frcp_rn((float)a);
-    double e = fma(-a, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-a, y, 1.0);
-    return fma(y, e, y);
+    if (!seed_range(a)) return __ddiv_rn(1.0, a);
+    const double y = f64_of(__frcp_rn(f32_trunc(a)));
+    const double e = fma(-a, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 __device__ __forceinline__ double rsqrt64(double a) {
-    if (!(a > 1e-30 && a < 1e30)) return __ddiv_rn(1.0, __dsqrt_rn(a));
-    double y = (double)rsqrtf((float)a);
-    const double h = 0.5 * a;
-    double e = fma(-h * y, y, 0.5);
-    y = fma(y, e, y);
-    e = fma(-h * y, y, 0.5);
-    return fma(y, e, y);
+    if (!(seed_range(a) && sign_clear(a))) return __ddiv_rn(1.0, __dsqrt_rn(a));
+    const double y = f64_of(rsqrtf(f32_trunc(a)));
+    const double e = fma(-(a * y), y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+__device__ __forceinline__ double sqrt64(double a) {
+    if (!(seed_range(a) && sign_clear(a))) return __dsqrt_rn(a);
+    const float yf = rsqrtf(f32_trunc(a));
+    const double hy = f64_of(0.5f * yf);
+    double s = a * f64_of(yf);
+    s = fma(fma(-s, s, a), hy, s);
+    return fma(fma(-s, s, a), hy, s);
 }
 
 // Block-wide sum; every thread gets the result.  `sh` needs 32 doubles.

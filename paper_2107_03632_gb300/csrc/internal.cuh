@@ -15,6 +15,11 @@ namespace rbffd {
 int knn_search(const double* xy, int64_t N, const double* qxy, int64_t Nq, int32_t n, int32_t* idx, void* ws,
                size_t ws_bytes, cudaStream_t st);
 
+// Laplacian weights of a multigrid coarse level (double-float null-space
+// solve for 1 <= m <= 6, FP64 otherwise): the preconditioner's operators.
+int coarse_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m, double* w,
+                   int32_t* node_status, cudaStream_t st);
+
 // Interpolation weights at the Nq points qxy from their stencils idx (Nq x n,
 // indices into the Nd points xy): PHS r^3 + monomials of degree <= m, exact
 // for those monomials.  node_status (may be NULL): 1 where singular.

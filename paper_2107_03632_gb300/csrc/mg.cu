@@ -1387,7 +1387,7 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
         C.N = nc;
         // coarse operator: stencils, weights, Dirichlet-row assembly
         if ((rc = rbffd_stencils(C.xy, nc, kMgCoarseN, s.sidx, s.knn_ws, s.knn_bytes, st)) != RBFFD_OK) return rc;
-        if ((rc = rbffd_weights(C.xy, s.sidx, nc, kMgCoarseN, kMgCoarseM, s.sw, s.sstat, st)) != RBFFD_OK) return rc;
+        if ((rc = coarse_weights(C.xy, s.sidx, nc, kMgCoarseN, kMgCoarseM, s.sw, s.sstat, st)) != RBFFD_OK) return rc;
         mg_count_kernel<<<blocks_for(nc), kT, 0, st>>>(s.sstat, C.mask, nc, s.flags);
         note_launches(1);
         // (adjoint hierarchy: assembled into scratch, then transposed into the level)

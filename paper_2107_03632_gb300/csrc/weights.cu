@@ -1,5 +1,6 @@
 // RBF-FD Laplacian weights: one augmented PHS+polynomial system per stencil,
-// solved in FP64 shared memory by one warp (sm_103a).
+// held in shared memory and solved by one, two or four warps (sm_103a), in
+// FP64 (the default) or in double-float arithmetic (opt-in).
 //
 // Sec. II, Eq. 1: (L u)(x_c) ~ sum_j w_j u(x_j) over the stencil of x_c.
 // Sec. V: Phi(r) = r^3 augmented with the monomials of degree <= m, L = lap.
@@ -414,16 +415,21 @@ struct NsF64 {
     static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ V sub(V a, V b) { return __dadd_rn(a, -b); }
     static __device__ __forceinline__ V rcp(V a) { return rcp64(a); }
-    static __device__ __forceinline__ V rsqrt(V a) { return rsqrt64(a); }
-    static __device__ __forceinline__ V sqrt(V a) { return __dsqrt_rn(a); }
-    // pivot search key (monotone in |a|) and its value / non-finite test
+    static __device__ __forceinline__ V sqrt(V a) { return sqrt64(a); }
+    // |x|^3 of the difference (dx, dy): r^2 by one FMA, then r^2 sqrt(r^2)
+    static __device__ __forceinline__ V r3(V dx, V dy) {
+        const double r2 = fma(dx, dx, __dmul_rn(dy, dy));
+        return __dmul_rn(r2, sqrt64(r2));
+    }
+    // pivot search key (monotone in |a|); tests on it and on values by
+    // integer instructions (FP64 compares would occupy the FP64 units)
     static __device__ __forceinline__ unsigned long long key(V a) { return abs_bits(a); }
-    static __device__ __forceinline__ double key_value(unsigned long long k) {
-        return __longlong_as_double((long long)k);
+    static __device__ __forceinline__ bool key_small(unsigned long long k) {
+        return k < 0x3d719799812dea11ull;  // |a| < 1e-12
     }
     static __device__ __forceinline__ bool key_nonfinite(unsigned long long k) { return k >= 0x7ff0000000000000ull; }
-    static __device__ __forceinline__ bool is_zero(V a) { return a == 0.0; }
-    static __device__ __forceinline__ bool pos_finite(V a) { return a > 0.0 && isfinite(a); }
+    static __device__ __forceinline__ bool is_zero(V a) { return (abs_bits(a)) == 0ull; }
+    static __device__ __forceinline__ bool pos_finite(V a) { return positive_finite64(a); }
 };
 
 struct NsDF {
@@ -466,11 +472,16 @@ struct NsDF {
         return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e));
     }
     static __device__ __forceinline__ V sqrt(V a) { return (a.hi > 0.f) ? df_mul(a, rsqrt(a)) : df_make(0.f, 0.f); }
+    // |x|^3 of the difference (dx, dy): r^3 = r^2 (r^2 rsqrt(r^2))
+    static __device__ __forceinline__ V r3(V dx, V dy) {
+        const df r2 = df_add(df_mul(dx, dx), df_mul(dy, dy));
+        return df_mul(r2, df_mul(r2, rsqrt(r2)));
+    }
     static __device__ __forceinline__ unsigned long long key(V a) {
         return (unsigned long long)(__float_as_uint(a.hi) & 0x7fffffffu);
     }
-    static __device__ __forceinline__ double key_value(unsigned long long k) {
-        return (double)__uint_as_float((unsigned)k);
+    static __device__ __forceinline__ bool key_small(unsigned long long k) {
+        return k < 0x2b8cbcccull;  // |a| < 1e-12f
     }
     static __device__ __forceinline__ bool key_nonfinite(unsigned long long k) { return k >= 0x7f800000ull; }
     static __device__ __forceinline__ bool is_zero(V a) { return a.hi == 0.f && a.lo == 0.f; }
@@ -481,6 +492,11 @@ struct NsDF {
 // op 1: interpolation weights of the value at the query point cxy[node]
 //       (stencils index the Nd points xy): right-hand side [ |xh_j|^3 ;
 //       p_k(0) ], no rescaling.
+//
+// Scalars that one step of the elimination needs (a pivot's reciprocal, the
+// next diagonal entry's reciprocal, the scale) are computed by one thread
+// and handed to the others through shared memory: computed by every thread
+// of the group they cost as many FP64 lane-operations as a full row update.
 template <int NT, class R>
 __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restrict__ xy, const int* __restrict__ idx,
                                                          int N, int n, int m, int s, int LDF, int LDS,
@@ -507,13 +523,17 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     S* tv = wv + n;
     int* perm = reinterpret_cast<int*>(tv + n);
     int* act = perm + n;
+    // 8-byte slots either way (S is double or float2): raw FP64 differences
+    // in crd before scaling, the scale factors in wv until the weights
+    double* crdd = reinterpret_cast<double*>(crd);
+    double* scal = reinterpret_cast<double*>(wv);
     const int total_warps = gridDim.x * wpb;
 
     for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
         const int* sten = idx + (int64_t)node * n;
         const double2 c = cxy[node];
 
-        // ---- shift, scale (FP64) ---------------------------------------------
+        // ---- shift (FP64): differences and the largest squared distance ------
         unsigned long long dmax = 0;
         int bad = 0;
         for (int j = lane; j < n; j += NT) {
@@ -523,8 +543,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             const double2 p = ok ? xy[sj] : c;
             const double dx = __dadd_rn(p.x, -c.x);
             const double dy = __dadd_rn(p.y, -c.y);
-            const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            const unsigned long long b = abs_bits(d2);
+            crdd[2 * j] = dx;
+            crdd[2 * j + 1] = dy;
+            const unsigned long long b = abs_bits(fma(dx, dx, __dmul_rn(dy, dy)));
             dmax = (b > dmax) ? b : dmax;
         }
 #pragma unroll
@@ -533,29 +554,33 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             dmax = (t > dmax) ? t : dmax;
         }
         dmax = group_max_u64<NT>(dmax, red_u64);
-        const double delta = __dsqrt_rn(__longlong_as_double((long long)dmax));
-        const double delta2 = __dmul_rn(delta, delta);
+        // scale: 1/delta = (max d^2)^-1/2 and 1/delta^2, by one thread
+        if (lane == 0) {
+            const double id = rsqrt64(__longlong_as_double((long long)dmax));
+            scal[0] = id;
+            scal[1] = __dmul_rn(id, id);
+        }
+        group_sync<NT>();
+        const double inv_delta = scal[0], inv_delta2 = scal[1];
 
         // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
+        // degree d from degree d - 1 of the same row: x^(d-i) y^i = x * x^(d-1-i) y^i
+        // for i < d, and y^d = y * y^(d-1)
         for (int j = lane; j < n; j += NT) {
-            const int sj = sten[j];
-            const double2 p = ((unsigned)sj < (unsigned)Nd) ? xy[sj] : c;
-            const V xh = R::from_d(__ddiv_rn(__dadd_rn(p.x, -c.x), delta));
-            const V yh = R::from_d(__ddiv_rn(__dadd_rn(p.y, -c.y), delta));
+            const V xh = R::from_d(__dmul_rn(crdd[2 * j], inv_delta));
+            const V yh = R::from_d(__dmul_rn(crdd[2 * j + 1], inv_delta));
             R::st(crd + 2 * j, xh);
             R::st(crd + 2 * j + 1, yh);
-            V xp[9], yp[9];
-            xp[0] = R::cst(1.0);
-            yp[0] = R::cst(1.0);
-#pragma unroll
-            for (int t = 1; t < 9; ++t) {
-                xp[t] = (t <= m) ? R::mul(xp[t - 1], xh) : R::zero();
-                yp[t] = (t <= m) ? R::mul(yp[t - 1], yh) : R::zero();
+            S* pr = P + (size_t)j * LDS;
+            R::st(pr, R::cst(1.0));
+            if (m >= 1) {
+                R::st(pr + 1, xh);
+                R::st(pr + 2, yh);
             }
-            int col = 0;
-            for (int d = 0; d <= m; ++d)
-                for (int i = 0; i <= d; ++i, ++col)
-                    R::st(P + (size_t)j * LDS + col, (d == 0) ? R::cst(1.0) : R::mul(xp[d - i], yp[i]));
+            for (int d = 2, prev = 1, cur = 3; d <= m; prev = cur, cur += d + 1, ++d) {
+                for (int i = 0; i < d; ++i) R::st(pr + cur + i, R::mul(xh, R::ld(pr + prev + i)));
+                R::st(pr + cur + d, R::mul(yh, R::ld(pr + prev + d - 1)));
+            }
             act[j] = j;
         }
         for (int col = lane; col < s; col += NT) {
@@ -585,29 +610,32 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+                const int op_ = __shfl_xor_sync(0xffffffffu, bpos, o);
                 if (ob > best || (ob == best && oi < bi)) {
                     best = ob;
                     bi = oi;
-                    bpos = op;
+                    bpos = op_;
                 }
             }
             group_argmax<NT>(best, bi, bpos, red_u64, red_i);
             // rank deficient (pivot below 1e-12: P's entries are monomials of
             // points in the unit disk, so |P| <= 1) or non-finite
-            if (R::key_value(best) < 1e-12 || R::key_nonfinite(best)) {
+            if (R::key_small(best) || R::key_nonfinite(best)) {
                 singular = 1;
                 break;
             }
             const int pr = bi;
-            const V inv = R::rcp(R::ld(P + (size_t)pr * LDS + k));
-            group_sync<NT>();
+            // the pivot's reciprocal, by one thread, in tv[0] (free until the
+            // substitutions); every thread has finished the search above
+            // (shuffles, or the block barriers of group_argmax)
             if (lane == 0) {
+                R::st(tv, R::rcp(R::ld(P + (size_t)pr * LDS + k)));
                 perm[k] = pr;
                 act[bpos] = act[na - 1];  // swap-remove the pivot row
             }
             --na;
             group_sync<NT>();
+            const V inv = R::ld(tv);
             // every active row and the g row, one thread per row: scale its
             // column k by the pivot reciprocal (pivot row -> e_k), then
             // column j -= P[pr][j] * (scaled) P[r][k]; the pivot row, no
@@ -643,9 +671,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 const V dy = R::sub(R::ld(crd + 2 * ja + 1), R::ld(crd + 2 * jb + 1));
                 const bool same = R::is_zero(dx) && R::is_zero(dy);
                 coincident |= same ? 1 : 0;
-                // r^3 = r^2 * (r^2 / r), r^2 / r = r^2 * rsqrt(r^2)
-                const V r2 = R::add(R::mul(dx, dx), R::mul(dy, dy));
-                const V phi = same ? R::zero() : R::mul(r2, R::mul(r2, R::rsqrt(r2)));
+                const V phi = same ? R::zero() : R::r3(dx, dy);
                 R::st(Phi + (size_t)a * LDF + b, phi);
                 R::st(Phi + (size_t)b * LDF + a, phi);
             }
@@ -723,29 +749,33 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 R::st(tv + j, R::add(acc, acc1));
             }
             group_sync<NT>();
-            // ---- Cholesky S = L L^T (lower, in place) ----------------------------
-            for (int cI = 0; cI < q && !singular; ++cI) {
-                S* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const V dcc = R::ld(sc + cI);
-                if (!R::pos_finite(dcc)) {
+            // ---- S = L D L^T: unit lower L in place, 1/D in fv -----------------
+            // (S is positive definite: no pivoting.)  Column c: the unscaled
+            // column goes to uv (free now), L[i][c] = S[i][c] / D[c], then
+            // S[i][j] -= L[i][c] S[j][c] for c < j <= i.  The thread that
+            // updates the next diagonal entry also forms its reciprocal and
+            // the singularity flag (act[0], free after the elimination).
+            if (q > 0) {
+                if (lane == 0) {
+                    const V d0 = R::ld(Phi + (size_t)s * LDF + s);
+                    act[0] = R::pos_finite(d0) ? 0 : 1;
+                    R::st(fv, R::rcp(d0));
+                }
+                group_sync<NT>();
+            }
+            for (int cI = 0; cI < q; ++cI) {
+                if (act[0]) {
                     singular = 1;
                     break;
                 }
-                // l = sqrt(d) and 1/l from one reciprocal square root; 1/l is
-                // kept (in fv, free by now) for the substitutions
-                const V inv = R::rsqrt(dcc);
-                const V lcc = R::mul(dcc, inv);
-                group_sync<NT>();
+                const V invd = R::ld(fv + cI);
                 for (int i = cI + 1 + lane; i < q; i += NT) {
                     S* si = Phi + (size_t)(s + i) * LDF + s;
-                    R::st(si + cI, R::mul(R::ld(si + cI), inv));
-                }
-                if (lane == 0) {
-                    R::st(sc + cI, lcc);
-                    R::st(fv + cI, inv);
+                    const V v = R::ld(si + cI);
+                    R::st(uv + i, v);
+                    R::st(si + cI, R::mul(v, invd));
                 }
                 group_sync<NT>();
-                // trailing lower triangle: S[i][j] -= L[i][c] L[j][c], c < j <= i
                 const int rem = q - cI - 1, ntr = rem * (rem + 1) / 2;
                 for (int e = lane; e < ntr; e += NT) {
                     int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
@@ -753,28 +783,30 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     while ((i + 1) * (i + 2) / 2 <= e) ++i;
                     const int j = e - i * (i + 1) / 2;
                     S* si = Phi + (size_t)(s + cI + 1 + i) * LDF + s;
-                    const S* sj = Phi + (size_t)(s + cI + 1 + j) * LDF + s;
-                    R::st(si + cI + 1 + j, R::nfma(R::ld(si + cI), R::ld(sj + cI), R::ld(si + cI + 1 + j)));
+                    const V nv = R::nfma(R::ld(si + cI), R::ld(uv + cI + 1 + j), R::ld(si + cI + 1 + j));
+                    R::st(si + cI + 1 + j, nv);
+                    if (e == 0) {  // (i, j) = (0, 0): the next diagonal entry, final now
+                        act[0] = R::pos_finite(nv) ? 0 : 1;
+                        R::st(fv + cI + 1, R::rcp(nv));
+                    }
                 }
                 group_sync<NT>();
             }
         }
         if (!singular) {
-            // ---- forward (L y = t) and back (L^T z = y) substitution -------------
+            // ---- L y = t, z = D^-1 y, L^T x = z (unit triangles) -----------------
             for (int cI = 0; cI < q; ++cI) {
-                const V yc = R::mul(R::ld(tv + cI), R::ld(fv + cI));
-                group_sync<NT>();
+                const V yc = R::ld(tv + cI);
                 for (int i = cI + 1 + lane; i < q; i += NT)
                     R::st(tv + i, R::nfma(R::ld(Phi + (size_t)(s + i) * LDF + s + cI), yc, R::ld(tv + i)));
-                if (lane == 0) R::st(tv + cI, yc);
                 group_sync<NT>();
             }
+            for (int i = lane; i < q; i += NT) R::st(tv + i, R::mul(R::ld(tv + i), R::ld(fv + i)));
+            group_sync<NT>();
             for (int cI = q - 1; cI >= 0; --cI) {
                 const S* sc = Phi + (size_t)(s + cI) * LDF + s;
-                const V zc = R::mul(R::ld(tv + cI), R::ld(fv + cI));
-                group_sync<NT>();
+                const V zc = R::ld(tv + cI);
                 for (int i = lane; i < cI; i += NT) R::st(tv + i, R::nfma(R::ld(sc + i), zc, R::ld(tv + i)));
-                if (lane == 0) R::st(tv + cI, zc);
                 group_sync<NT>();
             }
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
@@ -799,8 +831,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         double* wd = reinterpret_cast<double*>(wv);
         int nonfinite = 0;
         for (int a = lane; a < n; a += NT) {
-            const double v = singular ? 0.0 : (op ? R::to_d(R::ld(wv + a)) : __ddiv_rn(R::to_d(R::ld(wv + a)), delta2));
-            nonfinite |= isfinite(v) ? 0 : 1;
+            const double v = singular ? 0.0 : (op ? R::to_d(R::ld(wv + a)) : __dmul_rn(R::to_d(R::ld(wv + a)), inv_delta2));
+            nonfinite |= finite64(v) ? 0 : 1;
             wd[a] = v;
         }
         const int fail = (singular || group_any<NT>(nonfinite)) ? 1 : 0;
@@ -883,18 +915,20 @@ bool cfg_valid(const WCfg& c, int n, int m) {
     return block_smem(c, n, m) <= 227 * 1024;
 }
 
+bool cfg_is_df(const WCfg& c) { return c.kernel >= 4; }
+
 WCfg default_cfg(int n, int m) {
     WCfg c;
-    // the null-space form needs r^3 positive definite on the null space of
-    // P^T, which holds once P contains the linear monomials (m >= 1); in
-    // double-float arithmetic up to m = 6
-    c.kernel = m < 1 ? 1 : (m <= kDfMaxM ? 4 : 0);
+    // FP64 by default: null-space elimination (m >= 1: the form needs r^3
+    // positive definite on the null space of P^T, which holds once P
+    // contains the linear monomials), full elimination for m = 0
+    c.kernel = m < 1 ? 1 : 0;
     size_t smem = 0;
     c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
-    // large systems (m >= 5): four warps per stencil, as measured fastest
-    // (m = 6, n = 56, 1M nodes: 179 ms against 183 with two warps, 262 with one)
-    const WCfg big{6, 4};
-    if (m >= 5 && m <= kDfMaxM && cfg_valid(big, n, m)) return big;
+    // large systems (m >= 5): two warps per stencil, as measured fastest in
+    // FP64 (m = 6, n = 56, 4M nodes: 1,346 ms against 1,595 with one warp)
+    const WCfg big{2, 2};
+    if (m >= 5 && cfg_valid(big, n, m)) return big;
     return c;
 }
 
@@ -993,22 +1027,30 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
 }
 
 extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
-                                      double* w, int32_t* node_status, rbffd_weights_config* best, void* stream) {
+                                      double* w, int32_t* node_status, int32_t precision,
+                                      rbffd_weights_config* best, void* stream) {
     using namespace rbffd;
     if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
+    if (precision != RBFFD_WEIGHTS_FP64 && precision != RBFFD_WEIGHTS_DF && precision != RBFFD_WEIGHTS_ANY)
+        return RBFFD_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     // sample: the first stencils, enough for several waves of resident warps
     const int64_t S = std::min<int64_t>(N, (int64_t)sm_count() * 128);
-    std::vector<WCfg> cands;
+    std::vector<WCfg> all;
     for (int kernel = 0; kernel <= 1; ++kernel)
-        for (int wpb = 1; wpb <= 4; ++wpb)
-            if (cfg_valid(WCfg{kernel, wpb}, n, m)) cands.push_back(WCfg{kernel, wpb});
-    if (cfg_valid(WCfg{2, 2}, n, m)) cands.push_back(WCfg{2, 2});
-    if (cfg_valid(WCfg{3, 4}, n, m)) cands.push_back(WCfg{3, 4});
-    for (int wpb = 1; wpb <= 4; ++wpb)
-        if (cfg_valid(WCfg{4, wpb}, n, m)) cands.push_back(WCfg{4, wpb});
-    if (cfg_valid(WCfg{5, 2}, n, m)) cands.push_back(WCfg{5, 2});
-    if (cfg_valid(WCfg{6, 4}, n, m)) cands.push_back(WCfg{6, 4});
+        for (int wpb = 1; wpb <= 4; ++wpb) all.push_back(WCfg{kernel, wpb});
+    all.push_back(WCfg{2, 2});
+    all.push_back(WCfg{3, 4});
+    for (int wpb = 1; wpb <= 4; ++wpb) all.push_back(WCfg{4, wpb});
+    all.push_back(WCfg{5, 2});
+    all.push_back(WCfg{6, 4});
+    std::vector<WCfg> cands;
+    for (const WCfg& c : all) {
+        if (!cfg_valid(c, n, m)) continue;
+        if (precision == RBFFD_WEIGHTS_FP64 && cfg_is_df(c)) continue;
+        if (precision == RBFFD_WEIGHTS_DF && !cfg_is_df(c)) continue;
+        cands.push_back(c);
+    }
     if (cands.empty()) return RBFFD_ERR_INVALID_ARG;
     cudaEvent_t e0, e1;
     RBFFD_CUDA_TRY(cudaEventCreate(&e0));
@@ -1078,6 +1120,20 @@ extern "C" int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weight
     if (!cfg_valid(WCfg{cfg->kernel, cfg->warps_per_block}, n, m)) return RBFFD_ERR_INVALID_ARG;
     g_wcfg[key] = std::make_pair(WCfg{cfg->kernel, cfg->warps_per_block}, 0.0);
     return RBFFD_OK;
+}
+
+// Laplacian weights of a preconditioner's coarse operator: the double-float
+// null-space form where it is offered (1 <= m <= 6), FP64 otherwise.  Only
+// the multigrid hierarchy uses them; its accuracy does not enter the
+// solution, which the FP64 operator's residual decides.
+int rbffd::coarse_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m, double* w,
+                          int32_t* node_status, cudaStream_t st) {
+    if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
+    WCfg c;
+    size_t smem = 0;
+    c.kernel = m < 1 ? 1 : (m <= kDfMaxM ? 4 : 0);
+    c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
+    return launch_weights(c, xy, idx, N, n, m, w, node_status, st);
 }
 
 // Interpolation weights (used by the multigrid transfer operators): for each

@@ -176,7 +176,7 @@ SIGNATURES = {
     "rbffd_stencils": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _SZ, _VP]),
     "rbffd_stencils_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP]),
     "rbffd_weights": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, _VP]),
-    "rbffd_weights_autotune": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, ctypes.POINTER(WeightsConfig),
+    "rbffd_weights_autotune": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _VP, _I32, ctypes.POINTER(WeightsConfig),
                                               _VP]),
     "rbffd_weights_get_config": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(WeightsConfig)]),
     "rbffd_weights_set_config": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(WeightsConfig)]),
@@ -545,17 +545,22 @@ class ExplicitLoop:
         return u
 
 
-def rbffd_weights_autotune(xy: torch.Tensor, idx: torch.Tensor, m: int) -> dict:
-    """Times the weight-solve configurations on (a sample of) these stencils and
-    keeps the fastest for (n, m); returns it."""
+WEIGHTS_PRECISION = {"fp64": 0, "df": 1, "any": 2}  # RBFFD_WEIGHTS_FP64 / _DF / _ANY
+
+
+def rbffd_weights_autotune(xy: torch.Tensor, idx: torch.Tensor, m: int, precision: str = "fp64") -> dict:
+    """Times the weight-solve configurations of the given arithmetic ("fp64",
+    "df" = double-float, "any") on (a sample of) these stencils and keeps the
+    fastest for (n, m); returns it."""
     N, n = idx.shape
     _require(xy, torch.float64, "xy", (N, 2))
     _require(idx, torch.int32, "idx", (N, n))
     w = torch.empty((N, n), dtype=torch.float64, device=xy.device)
     st = torch.empty(N, dtype=torch.int32, device=xy.device)
     best = WeightsConfig()
-    _check(load().rbffd_weights_autotune(_ptr(xy), _ptr(idx), N, n, int(m), _ptr(w), _ptr(st), ctypes.byref(best),
-                                         _stream(xy.device)), "rbffd_weights_autotune")
+    _check(load().rbffd_weights_autotune(_ptr(xy), _ptr(idx), N, n, int(m), _ptr(w), _ptr(st),
+                                         WEIGHTS_PRECISION[precision], ctypes.byref(best), _stream(xy.device)),
+           "rbffd_weights_autotune")
     return best.as_dict()
 
 

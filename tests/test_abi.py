@@ -181,16 +181,16 @@ def test_weights_config_table(cdll):
 
     c = rbffd.WeightsConfig()
     assert cdll.rbffd_weights_get_config(56, 6, ctypes.byref(c)) == 0
-    assert (c.kernel, c.warps_per_block) == (6, 4)  # double-float null-space, four warps, by default at m = 6
-    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 4  # one warp at m = 4
-    assert cdll.rbffd_weights_get_config(90, 8, ctypes.byref(c)) == 0 and c.kernel == 0  # FP64 beyond m = 6
+    assert (c.kernel, c.warps_per_block) == (2, 2)  # FP64 null-space, two warps, by default at m = 6
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0  # FP64, one warp at m = 4
+    assert cdll.rbffd_weights_get_config(90, 8, ctypes.byref(c)) == 0 and c.kernel == 2  # FP64, two warps, m = 8
     assert cdll.rbffd_weights_get_config(12, 0, ctypes.byref(c)) == 0 and c.kernel == 1  # m = 0: elimination
     pin = rbffd.WeightsConfig(1, 2, 0.0)
     assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(pin)) == 0
     assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0
     assert (c.kernel, c.warps_per_block) == (1, 2)
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
-    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 4
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0
     for good in ((2, 2), (3, 4), (4, 1), (4, 3), (5, 2), (6, 4), (0, 2)):
         assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(rbffd.WeightsConfig(*good, 0.0))) == 0, good
     for bad in (rbffd.WeightsConfig(7, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
@@ -203,4 +203,6 @@ def test_weights_config_table(cdll):
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
     assert cdll.rbffd_weights_set_config(12, 0, ctypes.byref(rbffd.WeightsConfig(0, 1, 0.0))) == 1  # m = 0
     assert cdll.rbffd_weights_set_config(10, 4, ctypes.byref(pin)) == 1  # n < s
-    assert cdll.rbffd_weights_autotune(None, 0x1000, 10, 6, 2, 0x2000, None, None, None) == 1
+    assert cdll.rbffd_weights_autotune(None, 0x1000, 10, 6, 2, 0x2000, None, 0, None, None) == 1
+    # an unknown precision selector is refused before any device access
+    assert cdll.rbffd_weights_autotune(0x1000, 0x1000, 10, 6, 2, 0x2000, None, 7, None, None) == 1

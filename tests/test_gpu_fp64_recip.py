@@ -1,7 +1,8 @@
-"""The weight solves' FP64 reciprocal and reciprocal square root (Newton-
-Raphson on float32 seeds) against IEEE results computed on the host: within
-two ulps over the float32 normal range, and the IEEE operation itself
-outside it."""
+"""The weight solves' FP64 reciprocal and reciprocal square root (float32
+seeds moved in and out of doubles by integer instructions, then one
+FMA-based correction of third order) against IEEE results computed on the
+host: within two ulps (three for the root) for 2^-100 <= |x| < 2^101, and
+the IEEE operation itself outside that range."""
 
 import ctypes
 
