@@ -392,3 +392,94 @@ def test_weights_rank_deficient_stencil_flagged():
     d = disk_nodes(0.08)
     _, st = oracle.weights(d.xy, oracle.knn(d.xy, 56), 6)
     assert not st.any()
+
+
+# ------------------------------------------- full-size oracle machinery -----
+@pytest.mark.parametrize("h,n,jitter", [(0.02, 56, 0.25), (0.02, 12, 0.25), (1.0 / 32, 30, 0.0), (0.05, 56, 0.0)])
+def test_knn_grid_equals_brute_force(h, n, jitter):
+    """The cell-grid search returns the brute force's rows exactly (order and
+    ties included), on jittered disks and on unjittered grids (exact ties)."""
+    d = disk_nodes(h, jitter=jitter)
+    assert np.array_equal(oracle.knn_grid(d.xy, n), oracle.knn(d.xy, n))
+
+
+def test_knn_grid_clustered_and_duplicate_points():
+    """Strongly non-uniform density (clusters, exact duplicates, a lone far
+    point): the ring bound still decides, or the brute force takes over."""
+    rng = np.random.default_rng(7)
+    pts = [rng.normal(c, s, size=(k, 2)) for c, s, k in (((0.0, 0.0), 1e-3, 400), ((0.5, 0.2), 0.05, 300),
+                                                             ((-0.7, 0.6), 0.2, 200))]
+    xy = np.concatenate(pts + [np.array([[5.0, 5.0]]), pts[0][:20]])
+    for n in (8, 30):
+        assert np.array_equal(oracle.knn_grid(xy, n), oracle.knn(xy, n))
+
+
+def test_knn_grid_sampled_at_2e5_nodes():
+    """At N = 2e5 (a 200k-node disk), 400 seeded queries: grid search = brute force."""
+    from fixtures import h_for_nodes
+
+    d = disk_nodes(h_for_nodes(2e5))
+    q = (uniform01(splitmix64(11, 400)) * d.N).astype(np.int64)
+    assert np.array_equal(oracle.knn_grid(d.xy, 56, q), oracle.knn_query(d.xy, 56, q))
+
+
+def test_residual_extended_is_the_exact_residual_rounded():
+    """b - A x with products and sums in extended precision equals the exact
+    rational residual rounded to double, on rows built to cancel badly in
+    plain double arithmetic."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(3)
+    N, k = 40, 6
+    row_ptr = np.arange(0, N * k + 1, k, dtype=np.int64)
+    col = rng.integers(0, N, size=N * k).astype(np.int32)
+    val = rng.normal(size=N * k) * 1e6
+    x = rng.normal(size=N)
+    exact_ax = [sum(Fraction(float(val[a])) * Fraction(float(x[col[a]])) for a in range(row_ptr[i], row_ptr[i + 1]))
+                for i in range(N)]
+    b = np.array([float(v) for v in exact_ax]) + rng.normal(size=N) * 1e-9  # residual ~1e-9 against |Ax| ~1e6
+    r = oracle.residual_extended(row_ptr, col, val, x, b)
+    exact = np.array([float(Fraction(float(b[i])) - exact_ax[i]) for i in range(N)])
+    # long double keeps ~64 bits: the residual to ~2^-64 * sum |a x| ~ 1e-12 absolute here
+    assert np.abs(r - exact).max() <= 1e-11 * np.abs(exact).max() + 4e-13
+    plain = b - to_scipy(row_ptr, col, val, N) @ x
+    assert np.abs(plain - exact).max() > np.abs(r - exact).max()  # double arithmetic loses more
+
+
+def test_gmres_right_matches_dense_solve():
+    """Restarted right-preconditioned GMRES against LAPACK on a small
+    nonsymmetric system, with and without a (diagonal) preconditioner."""
+    rng = np.random.default_rng(5)
+    N = 120
+    A = np.eye(N) * 4 + rng.normal(size=(N, N)) * 0.2
+    b = rng.normal(size=N)
+    ref = np.linalg.solve(A, b)
+    for ps in (lambda v: v, lambda v: v / np.diag(A)):
+        x, its = oracle.gmres_right(lambda v: A @ v, ps, b, 1e-13, restart=25)
+        assert np.abs(x - ref).max() <= 1e-11 * np.abs(ref).max() and its > 0
+
+
+@pytest.mark.parametrize("h,m,n", [(0.02, 6, 56), (0.012, 4, 30)])
+def test_solve_refined_matches_refined_superlu(h, m, n):
+    """The Krylov path of solve_refined (GMRES corrections preconditioned by the
+    degree-2, 12-node operator) and SuperLU of A itself with the same
+    extended-precision refinement reach the same u and lambda to 1e-12; the
+    unrefined direct solve agrees to its own forward error (1e-8)."""
+    d = disk_nodes(h)
+    u_ex, f, g = manufactured(d.xy)
+    A = oracle.assemble(oracle.knn_grid(d.xy, n), oracle.weights(d.xy, oracle.knn_grid(d.xy, n), m)[0],
+                        d.is_dirichlet)
+    idx12 = oracle.knn_grid(d.xy, 12)
+    Mp = oracle.assemble(idx12, oracle.weights(d.xy, idx12, 2)[0], d.is_dirichlet)
+    b = oracle.rhs(f, g, d.is_dirichlet)
+    x_k, info_k = oracle.solve_refined(*A, b, Mp)
+    x_d, info_d = oracle.solve_refined(*A, b, None)
+    assert np.abs(x_k - x_d).max() <= 1e-12 * np.abs(x_d).max()
+    assert info_k["rel_residual"] <= 1e-12 and info_d["rel_residual"] <= 1e-12
+    assert np.abs(x_k - oracle.solve_direct(*A, b)).max() <= 1e-8 * np.abs(x_d).max()
+    rhs_t = np.where(d.is_dirichlet == 0, np.sin(3 * d.xy[:, 0]), 0.0)
+    l_k, _ = oracle.solve_refined(*A, rhs_t, Mp, transpose=True)
+    l_d = oracle.solve_direct(*A, rhs_t, transpose=True)
+    l_r, _ = oracle.solve_refined(*A, rhs_t, None, transpose=True)
+    assert np.abs(l_k - l_r).max() <= 1e-12 * np.abs(l_r).max()
+    assert np.abs(l_k - l_d).max() <= 1e-8 * np.abs(l_r).max()
