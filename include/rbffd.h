@@ -16,10 +16,17 @@
  *
  * Conventions shared by every entry point:
  *  - All array arguments are DEVICE pointers owned by the caller, unless a
- *    comment says "host".  The library allocates no device memory; scratch
- *    space is a caller-provided workspace whose size the matching
- *    *_workspace_size function returns (workspace pointers must be 256-byte
- *    aligned).
+ *    comment says "host".  The library makes no device-memory allocation of
+ *    its own (no cudaMalloc): scratch space is a caller-provided workspace
+ *    whose size the matching *_workspace_size function returns (workspace
+ *    pointers must be 256-byte aligned).  Exceptions, where the CUDA runtime
+ *    allocates on the library's behalf: rbffd_solve_batched creates its
+ *    streams, events and CUDA graphs (captured, instantiated and destroyed
+ *    within the call), and rbffd_explicit_run instantiates a CUDA graph of
+ *    its steps on every call; graph instantiation reserves device memory.
+ *    rbffd_stencils_noalloc uses a static device array (below).
+ *  - Every entry point opens an NVTX range named after it (visible in
+ *    profilers; free when no profiler is attached).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued on that stream; calls return before it completes unless
  *    the comment says the call blocks.
@@ -95,10 +102,12 @@ int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* idx,
 /* RBFFD_STENCILS_NOALLOC_MAX_NODES; larger N returns RBFFD_ERR_INVALID_ARG  */
 /* before anything is enqueued.  The scratch is one fixed device array of   */
 /* RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES inside the library, held by every   */
-/* GPU that loads the library until the process exits.  The first call on  */
-/* a device looks up that array's device address (cudaGetSymbolAddress,     */
-/* with the device current): make that first call before any stream        */
-/* capture.  All calls share the array: calls whose work overlaps on the    */
+/* GPU that loads the library until the process exits.  The first call in  */
+/* each CUDA context (per device, and again after cudaDeviceReset rebuilds  */
+/* the context) looks up that array's device address                        */
+/* (cudaGetSymbolAddress, with the device current) and caches it under the  */
+/* context's unique ID: make that first call before any stream capture.     */
+/* All calls share the array: calls whose work overlaps on the              */
 /* GPU (other streams, other threads) race and give wrong stencils; calls   */
 /* ordered on one stream are safe.  It calls no cudaMalloc, cudaFree or     */
 /* other allocating routine.                                                 */
@@ -146,7 +155,8 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* The default is FP64: 2 (two warps per stencil) for m >= 5 when it fits,  */
 /* 0 for other m >= 1, 1 for m = 0.                                          */
 /* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form with    */
-/* one warp per stencil, =lu the Gaussian elimination.                      */
+/* one warp per stencil, =df its double-float form (1 <= m <= 6), =lu the   */
+/* Gaussian elimination.                                                     */
 /* rbffd_weights_autotune times every candidate of the given precision      */
 /* (RBFFD_WEIGHTS_FP64: kernels 0-3; RBFFD_WEIGHTS_DF: 4-6; _ANY: all) that  */
 /* fits in shared memory on the first min(N, 128 x SMs) stencils of the     */
@@ -208,12 +218,17 @@ typedef struct rbffd_csr {
     int32_t dtype;
 } rbffd_csr;
 
-/* Transpose A (float64 values) into CSR of A^T.  Within a row of A^T the    */
-/* entries are in increasing column order (deterministic).                   */
+/* Transpose A (float64 values) into CSR of A^T (the operator of the       */
+/* adjoint solve, rbffd_solve_adjoint).  Within a row of A^T the entries    */
+/* are in increasing column order (deterministic).                          */
 /*   row_ptr_t : n_rows + 1 int64, col_t : nnz int32, val_t : nnz float64.   */
+/*   val32_t   : nnz float32 (val_t rounded to nearest), or NULL: the       */
+/*               float32 copy the mixed-precision adjoint solve reads.       */
 /*   ws        : rbffd_transpose_workspace_size(n_rows) bytes.               */
+/* Asynchronous on `stream`; argument errors return before anything is      */
+/* enqueued (RBFFD_ERR_INVALID_ARG, RBFFD_ERR_WORKSPACE).                    */
 size_t rbffd_transpose_workspace_size(int64_t n_rows);
-int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t,
+int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t, float* val32_t,
                     void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
@@ -405,8 +420,8 @@ int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, const uint8_
                         void* ws, size_t ws_bytes, void* stream);
 
 /* Gradient of the misfit L(u) = sum over interior nodes of (u - u_target)^2 */
-/* (the loss of the differentiable solve; the paper's Sec. VI names         */
-/* gradient-based use of the solver as future work and prints no loss):     */
+/* (the loss of the differentiable solve; no counterpart in the paper,     */
+/* which has no loss and no gradient):                                      */
 /* dLdu = 2 (u - u_target) on interior nodes, 0 on Dirichlet nodes.          */
 /*   u, u_target, dLdu : device, N float64 each; is_dirichlet : N uint8.     */
 /* Asynchronous on `stream`.  Errors: RBFFD_ERR_INVALID_ARG (null pointer,   */

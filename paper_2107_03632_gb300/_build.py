@@ -21,7 +21,8 @@ LIB_DIR = os.path.join(PKG_DIR, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "librbffd.so")
 OBJ_DIR = os.path.join(PKG_DIR, "_build")
 
-SOURCES = ["api.cu", "knn.cu", "weights.cu", "assemble.cu", "krylov.cu", "batched.cu", "mg.cu", "explicit.cu"]
+SOURCES = ["api.cu", "knn.cu", "weights.cu", "assemble.cu", "krylov.cu", "batched.cu", "mg.cu", "mg_batch.cu",
+           "explicit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]

@@ -117,12 +117,14 @@ void prof_collect() {
 extern "C" {
 
 int rbffd_profile_enable(int on) {
+    RBFFD_NVTX("rbffd_profile_enable");
     rbffd::g_profiling.store(on ? 1 : 0);
     return RBFFD_OK;
 }
 
 int rbffd_profile_read(rbffd_profile* out, int reset) {
     using namespace rbffd;
+    RBFFD_NVTX("rbffd_profile_read");
     if (!out) return RBFFD_ERR_INVALID_ARG;
     {
         std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -193,6 +195,7 @@ __global__ void diag_recip_kernel(const double* __restrict__ x, int64_t n, doubl
 }  // namespace rbffd
 
 extern "C" int rbffd_diag_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {
+    RBFFD_NVTX("rbffd_diag_recip");
     using namespace rbffd;
     if (!x || n <= 0 || (!rcp && !rsqrt)) return RBFFD_ERR_INVALID_ARG;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);

@@ -99,9 +99,10 @@ __global__ void transpose_scatter_kernel(const int64_t* __restrict__ row_ptr, co
     }
 }
 
-// Sort each row of A^T by column index (insertion sort; rows are short).
+// Sort each row of A^T by column index (insertion sort; rows are short);
+// with val32_t, also write the row's float32 copy (rounded to nearest).
 __global__ void row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N, int* __restrict__ col_t,
-                                double* __restrict__ val_t) {
+                                double* __restrict__ val_t, float* __restrict__ val32_t) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = row_ptr_t[r], e = row_ptr_t[r + 1];
         for (int64_t k = a + 1; k < e; ++k) {
@@ -116,6 +117,8 @@ __global__ void row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N
             col_t[q + 1] = c;
             val_t[q + 1] = v;
         }
+        if (val32_t)
+            for (int64_t k = a; k < e; ++k) val32_t[k] = __double2float_rn(val_t[k]);
     }
 }
 
@@ -128,6 +131,7 @@ int grid_for(int64_t work, int per_block) {
 }  // namespace rbffd
 
 extern "C" size_t rbffd_assemble_workspace_size(int64_t N) {
+    RBFFD_NVTX("rbffd_assemble_workspace_size");
     if (N <= 0) return 0;
     rbffd::Carver c(nullptr);
     c.take<int64_t>(rbffd::scan_tiles(N) + 1);
@@ -136,6 +140,7 @@ extern "C" size_t rbffd_assemble_workspace_size(int64_t N) {
 
 extern "C" int rbffd_assemble_pattern(const uint8_t* is_dirichlet, int64_t N, int32_t n, int64_t* row_ptr, void* ws,
                                       size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_assemble_pattern");
     using namespace rbffd;
     if (!is_dirichlet || !row_ptr || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL)
         return RBFFD_ERR_INVALID_ARG;
@@ -150,6 +155,7 @@ extern "C" int rbffd_assemble_pattern(const uint8_t* is_dirichlet, int64_t N, in
 extern "C" int rbffd_assemble(const int32_t* idx, const double* w, const uint8_t* is_dirichlet, int64_t N, int32_t n,
                               const int64_t* row_ptr, int64_t nnz, int32_t* col, double* val, float* val32,
                               void* stream) {
+    RBFFD_NVTX("rbffd_assemble");
     using namespace rbffd;
     if (!idx || !w || !is_dirichlet || !row_ptr || !col || !val || N <= 0 || N > 0x7fffffffLL || n < 1 ||
         n > RBFFD_MAX_STENCIL || nnz < 0)
@@ -163,6 +169,7 @@ extern "C" int rbffd_assemble(const int32_t* idx, const double* w, const uint8_t
 
 extern "C" int rbffd_rhs(const double* f, const double* g, const uint8_t* is_dirichlet, int64_t N, double* b,
                          void* stream) {
+    RBFFD_NVTX("rbffd_rhs");
     using namespace rbffd;
     if (!f || !g || !is_dirichlet || !b || N <= 0) return RBFFD_ERR_INVALID_ARG;
     rhs_kernel<<<grid_for(N, 256), 256, 0, as_stream(stream)>>>(f, g, is_dirichlet, N, b);
@@ -172,6 +179,7 @@ extern "C" int rbffd_rhs(const double* f, const double* g, const uint8_t* is_dir
 }
 
 extern "C" size_t rbffd_transpose_workspace_size(int64_t n_rows) {
+    RBFFD_NVTX("rbffd_transpose_workspace_size");
     if (n_rows <= 0) return 0;
     rbffd::Carver c(nullptr);
     c.take<int>(n_rows);
@@ -179,8 +187,9 @@ extern "C" size_t rbffd_transpose_workspace_size(int64_t n_rows) {
     return c.off;
 }
 
-extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t, void* ws,
-                               size_t ws_bytes, void* stream) {
+extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* col_t, double* val_t,
+                               float* val32_t, void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_transpose");
     using namespace rbffd;
     if (!A || !A->row_ptr || !A->col || !A->val || A->dtype != 0 || !row_ptr_t || !col_t || !val_t ||
         A->n_rows <= 0 || A->n_rows > 0x7fffffffLL || A->nnz < 0)
@@ -198,7 +207,7 @@ extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* 
     RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{counts}, N, row_ptr_t, sums, row_ptr_t + N, st));
     transpose_scatter_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, val, N, A->nnz, row_ptr_t, counts,
                                                                     col_t, val_t);
-    row_sort_kernel<<<grid_for(N, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t);
+    row_sort_kernel<<<grid_for(N, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t, val32_t);
     note_launches(3);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

@@ -115,6 +115,8 @@ struct BWork {
     float *f0, *f1, *f2;
     float* coarse;
     char* mgws;
+    char* mbtab;  // device tables of the batched V-cycle
+    size_t mbtab_bytes;
 };
 
 __device__ __forceinline__ int find_inst(const Inst* inst, int n_inst, int64_t row) {
@@ -1057,12 +1059,16 @@ size_t layout(void* ws, const Plan& pl, BWork* w) {
         t.f2 = c.take<float>(NR);
         t.coarse = c.take<float>(pl.coarse_total);
         t.mgws = c.take<char>(pl.mg_total);
+        t.mbtab_bytes = mg_batch_table_bytes(pl.n_inst, pl.N);
+        t.mbtab = c.take<char>(t.mbtab_bytes);
     }
     if (w) *w = t;
     return c.off;
 }
 
-int grid_units(int n_units) { return std::max(1, std::min(n_units, sm_count() * 8)); }
+// one block per unit: a grid-stride loop over more units than resident
+// blocks runs in uneven waves
+int grid_units(int n_units) { return std::max(1, n_units); }
 
 // RBFFD_TRACE=1: phase times of the batched solve on stderr (host clock
 // after a stream synchronisation; diagnostics only).
@@ -1142,6 +1148,15 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
             return -RBFFD_ERR_WORKSPACE;
     }
     clk.mark("multigrid hierarchies");
+    // the batched V-cycle: one launch per (level, operation) over all instances
+    MgBatch mb{};
+    {
+        std::vector<int64_t> noff(pl.n_inst);
+        for (int i = 0; i < pl.n_inst; ++i) noff[i] = pl.inst[i].node_off;
+        const int rc = mg_batch_build(H.data(), noff.data(), pl.n_inst, R, w.f0, w.f1, w.f2, w.coarse,
+                                      pl.coarse_off.data(), w.mbtab, w.mbtab_bytes, st, &mb);
+        if (rc != RBFFD_OK) return -rc;
+    }
     int vlaunch = 0;
     // double-float views of the outer vectors
     float2* vr = w.mr;
@@ -1154,38 +1169,6 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
     float2* vsh = reinterpret_cast<float2*>(w.msh);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    // the instances' V-cycles are independent: in the graph they run as
-    // kVStreams parallel branches (forked from and joined back to the outer
-    // kernels), so the many small coarse-level kernels overlap
-    constexpr int kVStreams = 32;
-    cudaStream_t vs[kVStreams];
-    cudaEvent_t fork_ev, join_ev[kVStreams];
-    for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&vs[k], cudaStreamNonBlocking));
-    RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
-    for (int k = 0; k < kVStreams; ++k) RBFFD_CUDA_TRY_NEG(cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming));
-    auto vcycles_par = [&](const float2* in, float2* out, cudaStream_t s) -> int {
-        if (cudaEventRecord(fork_ev, s) != cudaSuccess) return RBFFD_ERR_CUDA;
-        for (int k = 0; k < kVStreams; ++k)
-            if (cudaStreamWaitEvent(vs[k], fork_ev, 0) != cudaSuccess) return RBFFD_ERR_CUDA;
-        for (int i = 0; i < pl.n_inst; ++i) {
-            const int rc = mg_apply_multi_df(H[i], pl.inst[i].node_off, R, in, out, w.f0, w.f1, w.f2,
-                                             w.coarse + pl.coarse_off[i], w.inst_running + i, vs[i % kVStreams],
-                                             &vlaunch);
-            if (rc != RBFFD_OK) return rc;
-        }
-        for (int k = 0; k < kVStreams; ++k) {
-            if (cudaEventRecord(join_ev[k], vs[k]) != cudaSuccess) return RBFFD_ERR_CUDA;
-            if (cudaStreamWaitEvent(s, join_ev[k], 0) != cudaSuccess) return RBFFD_ERR_CUDA;
-        }
-        return RBFFD_OK;
-    };
-    auto destroy_par = [&]() {
-        for (int k = 0; k < kVStreams; ++k) {
-            cudaStreamDestroy(vs[k]);
-            cudaEventDestroy(join_ev[k]);
-        }
-        cudaEventDestroy(fork_ev);
-    };
     {
         cudaStream_t cap;
         RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -1193,11 +1176,11 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         int rc = RBFFD_OK;
         if (e == cudaSuccess) {
             md_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vp, w.pr, w.inst_running);
-            rc = vcycles_par(vp, vph, cap);
+            rc = mg_batch_apply_df(mb, R, vp, vph, w.inst_running, cap, &vlaunch);
             md_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
                                                    R, vph, vv, vrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
             md_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vsv, w.pr, w.inst_running);
-            if (rc == RBFFD_OK) rc = vcycles_par(vsv, vsh, cap);
+            if (rc == RBFFD_OK) rc = mg_batch_apply_df(mb, R, vsv, vsh, w.inst_running, cap, &vlaunch);
             md_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
                                                    R, vsh, vt, vsv, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
             md_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, vph, vsh, vsv, vt, vr, vrh,
@@ -1206,7 +1189,6 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         }
         if (e == cudaSuccess && rc == RBFFD_OK) e = cudaGraphInstantiate(&exec, graph, 0);
         cudaStreamDestroy(cap);
-        destroy_par();
         if (e != cudaSuccess || rc != RBFFD_OK) {
             if (graph) cudaGraphDestroy(graph);
             if (e != cudaSuccess) set_cuda_error(e);
@@ -1279,6 +1261,7 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
 
 extern "C" size_t rbffd_batched_workspace_size(const rbffd_batch_desc* desc, int32_t n_inst, int32_t n_rhs,
                                                const rbffd_solve_opts* opts) {
+    RBFFD_NVTX("rbffd_batched_workspace_size");
     rbffd::Plan pl;
     if (opts && opts->precond != 0 && opts->precond != 1) return 0;
     if (!rbffd::make_plan(desc, n_inst, n_rhs, opts && opts->precond == 1, &pl)) return 0;
@@ -1289,6 +1272,7 @@ extern "C" int rbffd_solve_batched(const rbffd_batch_desc* desc, int32_t n_inst,
                                    const uint8_t* is_dirichlet, const double* f, const double* g, int32_t n_rhs,
                                    double* u, const rbffd_solve_opts* o, rbffd_solve_info* info, void* ws,
                                    size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_solve_batched");
     using namespace rbffd;
     Plan pl;
     if (!o || (o->precond != 0 && o->precond != 1)) return RBFFD_ERR_INVALID_ARG;

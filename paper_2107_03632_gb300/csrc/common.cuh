@@ -2,12 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stddef.h>
 
 #include "rbffd.h"
 
 namespace rbffd {
+
+// NVTX range over one C-ABI call (header-only NVTX; a no-op unless a
+// profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define RBFFD_NVTX(name) ::rbffd::NvtxRange rbffd_nvtx_range_(name)
 
 // Records the CUDA error text for rbffd_last_cuda_error().
 void set_cuda_error(cudaError_t e);

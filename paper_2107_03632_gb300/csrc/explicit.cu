@@ -103,12 +103,14 @@ int step_blocks(int64_t Ni) {
 }  // namespace rbffd
 
 extern "C" size_t rbffd_explicit_workspace_size(int64_t N, int32_t n) {
+    RBFFD_NVTX("rbffd_explicit_workspace_size");
     if (N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL) return 0;
     return rbffd::explicit_layout(nullptr, N, n).bytes;
 }
 
 extern "C" int rbffd_explicit_pack(const int32_t* idx, const double* w, const uint8_t* is_dirichlet, int64_t N,
                                    int32_t n, int64_t* n_interior, void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_explicit_pack");
     using namespace rbffd;
     if (!idx || !w || !is_dirichlet || !n_interior || N <= 0 || N > 0x7fffffffLL || n < 1 ||
         n > RBFFD_MAX_STENCIL)
@@ -138,6 +140,7 @@ extern "C" int rbffd_explicit_pack(const int32_t* idx, const double* w, const ui
 
 extern "C" int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t n_interior, double dt,
                                   int64_t steps, void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_explicit_run");
     using namespace rbffd;
     if (!f || !u || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL || n_interior < 0 ||
         n_interior > N || steps < 0 || !(dt == dt))

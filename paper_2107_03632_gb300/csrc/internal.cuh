@@ -112,19 +112,39 @@ int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_
 int mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg, void* ws,
                   size_t ws_bytes, cudaStream_t st);
 
-// Multi-right-hand-side float32 V-cycle on node-major vectors [row][R]
-// (R <= 64): x = M^-1 b for every column.  Level 0 works on rows
-// [row_off, row_off + N) of the caller's arrays b (FP64), x (FP64 output)
-// and the float work vectors x0, t0, r0 (all with the same row numbering,
-// which the level-0 column indices, offset by the hierarchy's col_base,
-// also use); the coarse levels use `coarse` (mg_multi_coarse_floats floats).
-// Every kernel returns at once while *live == 0 (live may be NULL).
+// Coarse-level vectors of the multi-right-hand-side V-cycle (4 float
+// vectors of N_l x R per coarse level l).
 size_t mg_multi_coarse_floats(const MgHierarchy* h, int R);
-int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b, double* x, float* x0, float* t0,
-                   float* r0, float* coarse, const int* live, cudaStream_t st, int* launches);
-// The same with double-float (float2: leading, trailing) right-hand sides
-// and results (the result's trailing part is zero).
-int mg_apply_multi_df(const MgHierarchy* h, int64_t row_off, int R, const float2* b, float2* x, float* x0, float* t0,
-                      float* r0, float* coarse, const int* live, cudaStream_t st, int* launches);
+
+// Batched multi-right-hand-side float32 V-cycle over many instances'
+// hierarchies (mg_batch.cu): one launch per (level, operation) over every
+// instance with that level, from device tables of (instance, level)
+// descriptors and row tiles.  Vectors are node-major [row][R] (R <= 64).
+struct MbLevel;
+struct MbUnit;
+struct MgBatch {
+    const MbLevel* desc;
+    const MbUnit* units;
+    int levels, nu;
+    // per level: units of the instances going deeper (a), of those whose
+    // coarsest level it is (d), and of the next level's rows of the former (c)
+    int a_off[RBFFD_MG_MAX_LEVELS], a_n[RBFFD_MG_MAX_LEVELS];
+    int d_off[RBFFD_MG_MAX_LEVELS], d_n[RBFFD_MG_MAX_LEVELS];
+    int c_off[RBFFD_MG_MAX_LEVELS], c_n[RBFFD_MG_MAX_LEVELS];
+};
+// Device bytes of the tables for n_inst instances of total_nodes nodes.
+size_t mg_batch_table_bytes(int n_inst, int64_t total_nodes);
+// Fills the tables (synchronises st).  H[i]: instance i's hierarchy, built
+// with col_base = node_off[i] on its block of the batched matrix; x0, t0,
+// r0: level-0 work vectors over all rows [N_total][R]; coarse +
+// coarse_off[i]: instance i's coarse-level vectors (mg_multi_coarse_floats).
+int mg_batch_build(const MgHierarchy* const* H, const int64_t* node_off, int n_inst, int R, float* x0, float* t0,
+                   float* r0, float* coarse, const size_t* coarse_off, void* tables, size_t table_bytes,
+                   cudaStream_t st, MgBatch* out);
+// x = M^-1 b for every instance and right-hand side, b and x double-float
+// pairs (the leading float is used; the result's trailing part is zero).
+// Units of instance i return at once while live[i] == 0.
+int mg_batch_apply_df(const MgBatch& B, int R, const float2* b, float2* x, const int* live, cudaStream_t st,
+                      int* launches);
 
 }  // namespace rbffd

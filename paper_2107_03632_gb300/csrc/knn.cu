@@ -22,7 +22,11 @@
 #include "internal.cuh"
 #include "scan.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <map>
 #include <mutex>
 
 namespace rbffd {
@@ -394,12 +398,14 @@ struct CountLoad {
 }  // namespace rbffd
 
 extern "C" size_t rbffd_stencils_workspace_size(int64_t N, int32_t n) {
+    RBFFD_NVTX("rbffd_stencils_workspace_size");
     if (N <= 0 || n <= 0) return 0;
     return rbffd::knn_layout(nullptr, N, n).bytes;
 }
 
 extern "C" int rbffd_stencils(const double* xy, int64_t N, int32_t n, int32_t* idx, void* ws, size_t ws_bytes,
                               void* stream) {
+    RBFFD_NVTX("rbffd_stencils");
     using namespace rbffd;
     if (!xy || !idx || N <= 0 || N > 0x7fffffffLL || n < 1 || n > RBFFD_MAX_STENCIL || (int64_t)n > N)
         return RBFFD_ERR_INVALID_ARG;
@@ -449,36 +455,67 @@ int rbffd::knn_search(const double* xy, int64_t N, const double* qxy, int64_t Nq
 // file-scope device array sized for RBFFD_STENCILS_NOALLOC_MAX_NODES nodes;
 // every GPU that loads this library keeps that array until the process
 // exits.  In host code the array's name is only a host-side stand-in, so
-// its device address is looked up with cudaGetSymbolAddress, once per
-// device, with that device current, on the first call there.
+// its device address is looked up with cudaGetSymbolAddress, with the
+// device current, on the first call in each CUDA context; the address is
+// cached under the context's unique ID (cuCtxGetId, reached through the
+// runtime's driver entry points), so a context rebuilt after
+// cudaDeviceReset gets a fresh lookup instead of a stale address.
 static __device__ __align__(256) unsigned char g_stencils_noalloc_scratch[RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {};
+std::map<unsigned long long, void*> g_noalloc_ptr;  // context ID -> device address of the array
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+
+// Unique ID of the calling thread's current context; makes device `dev`'s
+// primary context current first if the thread has none.
+int current_context_id(int dev, unsigned long long* id) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return RBFFD_ERR_CUDA;
+        g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return RBFFD_ERR_CUDA;
+    if (!ctx) {
+        if (cudaSetDevice(dev) != cudaSuccess || g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return RBFFD_ERR_CUDA;
+    }
+    if (g_ctx_id(ctx, id) != CUDA_SUCCESS) return RBFFD_ERR_CUDA;
+    return RBFFD_OK;
+}
 }  // namespace
 
 extern "C" int rbffd_stencils_noalloc(const double* xy, int64_t N, int32_t n, int32_t* idx, void* stream) {
+    RBFFD_NVTX("rbffd_stencils_noalloc");
     using namespace rbffd;
     if (N > RBFFD_STENCILS_NOALLOC_MAX_NODES || N <= 0) return RBFFD_ERR_INVALID_ARG;
     const size_t need = rbffd_stencils_workspace_size(N, n);
     if (need == 0 || need > (size_t)RBFFD_STENCILS_NOALLOC_SCRATCH_BYTES) return RBFFD_ERR_INVALID_ARG;
     int dev = 0;
     RBFFD_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return RBFFD_ERR_INVALID_ARG;
     void* ptr = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        unsigned long long cid = 0;
+        if (current_context_id(dev, &cid) != RBFFD_OK) return RBFFD_ERR_CUDA;
+        auto it = g_noalloc_ptr.find(cid);
+        if (it == g_noalloc_ptr.end()) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_stencils_noalloc_scratch);
             if (e != cudaSuccess || !p) {
                 set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
                 return RBFFD_ERR_CUDA;
             }
-            g_noalloc_ptr[dev] = p;
+            it = g_noalloc_ptr.emplace(cid, p).first;
         }
-        ptr = g_noalloc_ptr[dev];
+        ptr = it->second;
     }
     // rbffd_stencils clears the cell histogram before use; everything else in
     // the scratch is overwritten, so leftovers of earlier calls do no harm

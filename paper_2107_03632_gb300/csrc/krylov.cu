@@ -1326,6 +1326,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
 }  // namespace rbffd
 
 extern "C" size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* opts) {
+    RBFFD_NVTX("rbffd_solve_workspace_size");
     if (N <= 0) return 0;
     const bool mixed = opts && opts->precision == 1;
     const bool mg = opts && opts->precond == 1;
@@ -1335,6 +1336,7 @@ extern "C" size_t rbffd_solve_workspace_size(int64_t N, const rbffd_solve_opts* 
 extern "C" int rbffd_solve(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double* x,
                            const rbffd_solve_opts* opts, rbffd_solve_info* info, void* ws, size_t ws_bytes,
                            void* stream) {
+    RBFFD_NVTX("rbffd_solve");
     return rbffd::solve_impl(A, A32, b, x, opts, info, ws, ws_bytes, rbffd::as_stream(stream), false);
 }
 
@@ -1342,6 +1344,7 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
                                    const double* dLdu, double* lambda, double* dLdf, double* dLdg,
                                    const rbffd_solve_opts* opts, rbffd_solve_info* info, void* ws, size_t ws_bytes,
                                    void* stream) {
+    RBFFD_NVTX("rbffd_solve_adjoint");
     using namespace rbffd;
     if (!is_dirichlet && (dLdf || dLdg)) return RBFFD_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
@@ -1359,6 +1362,7 @@ extern "C" int rbffd_solve_adjoint(const rbffd_csr* AT, const rbffd_csr* AT32, c
 
 extern "C" int rbffd_misfit_grad(const double* u, const double* u_target, const uint8_t* is_dirichlet, int64_t N,
                                  double* dLdu, void* stream) {
+    RBFFD_NVTX("rbffd_misfit_grad");
     using namespace rbffd;
     if (!u || !u_target || !is_dirichlet || !dLdu || N <= 0) return RBFFD_ERR_INVALID_ARG;
     misfit_grad_kernel<<<(int)std::min<int64_t>((N + 255) / 256, sm_count() * 8), 256, 0, as_stream(stream)>>>(

@@ -486,150 +486,6 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
     }
 }
 
-// ------------------------------------------------------ multi-RHS V-cycle --
-// Node-major vectors [row][R], R <= 64: a warp owns a row, lane k and k + 32
-// own right-hand sides k and k + 32, so each matrix entry is read once for
-// all of them and every gathered row is a contiguous segment.  Level-0 rows
-// are rows row_off + i of the caller's arrays.
-
-__device__ __forceinline__ bool dead(const int* live) { return live && *(volatile const int*)live == 0; }
-
-// Level-0 right-hand sides come as FP64 or as double-float pairs (the
-// leading float suffices for a preconditioner); the level-0 result goes out
-// as FP64 or as a pair with a zero low part.
-__device__ __forceinline__ float to_f(double v) { return (float)v; }
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(float2 v) { return v.x; }
-template <typename OT>
-__device__ __forceinline__ OT from_f(float v);
-template <>
-__device__ __forceinline__ double from_f<double>(float v) {
-    return (double)v;
-}
-template <>
-__device__ __forceinline__ float from_f<float>(float v) {
-    return v;
-}
-template <>
-__device__ __forceinline__ float2 from_f<float2>(float v) {
-    return make_float2(v, 0.f);
-}
-
-template <typename BT>
-__global__ void __launch_bounds__(kT) mr_first_kernel(int64_t N, int64_t row_off, int R, const BT* __restrict__ b,
-                                                      const float* __restrict__ dinv, float* __restrict__ x,
-                                                      const int* live) {
-    if (dead(live)) return;
-    const int64_t total = N * R;
-    MG_ELEMS(total, e) {
-        const int64_t i = e / R;
-        const int64_t g = (row_off + i) * R + (e - i * R);
-        x[g] = dinv[i] * to_f(b[g]);
-    }
-}
-
-// xo = xi + W (b - A xi), or (RESID) r = b - A xi
-template <typename BT, typename OT, bool RESID>
-__global__ void __launch_bounds__(kT) mr_row_kernel(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
-                                                    const float* __restrict__ val, int64_t N, int64_t row_off, int R,
-                                                    const float* __restrict__ xi, const BT* __restrict__ b,
-                                                    const float* __restrict__ dinv, OT* __restrict__ out,
-                                                    const int* live) {
-    if (dead(live)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool on0 = lane < R, on1 = lane + 32 < R;
-    for (int64_t i = w0; i < N; i += nw) {
-        float s0 = 0.f, s1 = 0.f;
-        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
-            const float a = __ldg(val + q);
-            const int64_t c = (int64_t)__ldg(col + q) * R;
-            if (on0) s0 = fmaf(a, __ldg(xi + c + lane), s0);
-            if (on1) s1 = fmaf(a, __ldg(xi + c + lane + 32), s1);
-        }
-        const int64_t g = (row_off + i) * R;
-        const float di = dinv[i];
-        if (on0) {
-            const float r = to_f(b[g + lane]) - s0;
-            out[g + lane] = from_f<OT>(RESID ? r : fmaf(di, r, xi[g + lane]));
-        }
-        if (on1) {
-            const float r = to_f(b[g + lane + 32]) - s1;
-            out[g + lane + 32] = from_f<OT>(RESID ? r : fmaf(di, r, xi[g + lane + 32]));
-        }
-    }
-}
-
-// y = R r (CSR, n rows; r and y with their own row numbering)
-__global__ void __launch_bounds__(kT) mr_restrict_kernel(const int64_t* __restrict__ rrow, const int* __restrict__ rcol,
-                                                         const float* __restrict__ rval, int64_t n, int R,
-                                                         const float* __restrict__ r, float* __restrict__ y,
-                                                         const int* live) {
-    if (dead(live)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool on0 = lane < R, on1 = lane + 32 < R;
-    for (int64_t i = w0; i < n; i += nw) {
-        float s0 = 0.f, s1 = 0.f;
-        for (int64_t q = rrow[i]; q < rrow[i + 1]; ++q) {
-            const float a = __ldg(rval + q);
-            const int64_t c = (int64_t)__ldg(rcol + q) * R;
-            if (on0) s0 = fmaf(a, __ldg(r + c + lane), s0);
-            if (on1) s1 = fmaf(a, __ldg(r + c + lane + 32), s1);
-        }
-        if (on0) y[i * R + lane] = s0;
-        if (on1) y[i * R + lane + 32] = s1;
-    }
-}
-
-// x += P e (ELL, kMgK per row)
-__global__ void __launch_bounds__(kT) mr_prolong_kernel(int64_t N, int R, const int32_t* __restrict__ pidx,
-                                                        const float* __restrict__ pval, const float* __restrict__ e,
-                                                        float* __restrict__ x, const int* live) {
-    if (dead(live)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool on0 = lane < R, on1 = lane + 32 < R;
-    for (int64_t i = w0; i < N; i += nw) {
-        float s0 = on0 ? x[i * R + lane] : 0.f, s1 = on1 ? x[i * R + lane + 32] : 0.f;
-#pragma unroll
-        for (int j = 0; j < kMgK; ++j) {
-            const float a = __ldg(pval + i * kMgK + j);
-            const int64_t c = (int64_t)__ldg(pidx + i * kMgK + j) * R;
-            if (on0) s0 = fmaf(a, __ldg(e + c + lane), s0);
-            if (on1) s1 = fmaf(a, __ldg(e + c + lane + 32), s1);
-        }
-        if (on0) x[i * R + lane] = s0;
-        if (on1) x[i * R + lane + 32] = s1;
-    }
-}
-
-// x = Minv b (dense n x n), rows row_off + i of b and x
-template <typename BT, typename OT>
-__global__ void __launch_bounds__(kT) mr_dense_kernel(int n, int64_t row_off, int R, const float* __restrict__ minv,
-                                                      const BT* __restrict__ b, OT* __restrict__ x, const int* live) {
-    if (dead(live)) return;
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const bool on0 = lane < R, on1 = lane + 32 < R;
-    for (int i = w0; i < n; i += nw) {
-        float s0 = 0.f, s1 = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const float a = minv[(int64_t)i * n + j];
-            const int64_t c = (row_off + j) * R;
-            if (on0) s0 = fmaf(a, to_f(b[c + lane]), s0);
-            if (on1) s1 = fmaf(a, to_f(b[c + lane + 32]), s1);
-        }
-        const int64_t g = (row_off + i) * R;
-        if (on0) x[g + lane] = from_f<OT>(s0);
-        if (on1) x[g + lane + 32] = from_f<OT>(s1);
-    }
-}
-
 // ------------------------------------------------------------------- host --
 int tpr_for(int64_t rows, int64_t nnz) {
     const double L = (double)nnz / (double)std::max<int64_t>(rows, 1);
@@ -963,98 +819,6 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
     return cur;
 }
 
-// Multi-RHS cycle on level l (float32).  Level 0 reads B0 (FP64 or
-// double-float) right-hand sides on global rows and writes O0 output;
-// coarse levels use their own float vectors.  Returns the level's iterate
-// (coarse levels).
-template <typename B0, typename O0>
-float* multi_level(const MgHierarchy& h, int l, const void* bin, int64_t row_off, O0* out, float* x0, float* t0,
-                   float* r0, float* coarse, int R, const int* live, cudaStream_t st, int* launches) {
-    const MgLevel& L = h.lv[l];
-    const bool top = (l == 0);
-    // coarse-level buffers: [x | t | r | b] per level, levels 1.. in order
-    auto level_base = [&](int lev) {
-        size_t off = 0;
-        for (int k = 1; k < lev; ++k) off += (size_t)4 * h.lv[k].N * R;
-        return coarse + off;
-    };
-    float* cur;
-    float* oth;
-    float* rr;
-    if (top) {
-        cur = x0;
-        oth = t0;
-        rr = r0;
-    } else {
-        float* base = level_base(l);
-        const size_t n = (size_t)L.N * R;
-        cur = base;
-        oth = base + n;
-        rr = base + 2 * n;
-    }
-    const int64_t off = top ? row_off : 0;
-    const int gw = blocks_for(L.N * 32);
-    if (l == h.n_levels - 1) {
-        if (top)
-            mr_dense_kernel<B0, O0><<<gw, kT, 0, st>>>((int)L.N, off, R, L.minv32, static_cast<const B0*>(bin), out,
-                                                       live);
-        else
-            mr_dense_kernel<float, float><<<gw, kT, 0, st>>>((int)L.N, 0, R, L.minv32, static_cast<const float*>(bin),
-                                                             cur, live);
-        ++*launches;
-        return cur;
-    }
-    auto first = [&](float* x) {
-        if (top)
-            mr_first_kernel<B0><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const B0*>(bin),
-                                                                   L.dinv32, x, live);
-        else
-            mr_first_kernel<float><<<blocks_for(L.N * R), kT, 0, st>>>(L.N, off, R, static_cast<const float*>(bin),
-                                                                      L.dinv32, x, live);
-        ++*launches;
-    };
-    auto sweep = [&](float* xi, float* xo, bool final_top) {
-        if (top) {
-            const B0* b = static_cast<const B0*>(bin);
-            if (final_top)
-                mr_row_kernel<B0, O0, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                L.dinv32, out, live);
-            else
-                mr_row_kernel<B0, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                   L.dinv32, xo, live);
-        } else {
-            const float* b = static_cast<const float*>(bin);
-            mr_row_kernel<float, float, false><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, xi, b,
-                                                                  L.dinv32, xo, live);
-        }
-        ++*launches;
-    };
-    first(cur);
-    for (int k = 1; k < h.nu; ++k) {
-        sweep(cur, oth, false);
-        std::swap(cur, oth);
-    }
-    if (top)
-        mr_row_kernel<B0, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
-                                                          static_cast<const B0*>(bin), L.dinv32, rr, live);
-    else
-        mr_row_kernel<float, float, true><<<gw, kT, 0, st>>>(L.row_ptr, L.col, L.val32, L.N, off, R, cur,
-                                                             static_cast<const float*>(bin), L.dinv32, rr, live);
-    const MgLevel& C = h.lv[l + 1];
-    float* cb = level_base(l + 1) + (size_t)3 * C.N * R;
-    mr_restrict_kernel<<<blocks_for(C.N * 32), kT, 0, st>>>(L.rrow, L.rcol, L.rval32, C.N, R, rr + off * R, cb, live);
-    *launches += 2;
-    float* e = multi_level<B0, O0>(h, l + 1, cb, 0, nullptr, x0, t0, r0, coarse, R, live, st, launches);
-    mr_prolong_kernel<<<gw, kT, 0, st>>>(L.N, R, L.pidx, L.pval32, e, cur + off * R, live);
-    ++*launches;
-    for (int k = 0; k < h.nu; ++k) {
-        const bool final_top = top && k == h.nu - 1;
-        sweep(cur, oth, final_top);
-        if (!final_top) std::swap(cur, oth);
-    }
-    return cur;
-}
-
 }  // namespace
 
 size_t mg_multi_coarse_floats(const MgHierarchy* h, int R) {
@@ -1062,26 +826,6 @@ size_t mg_multi_coarse_floats(const MgHierarchy* h, int R) {
     size_t t = 0;
     for (int l = 1; l < h->n_levels; ++l) t += (size_t)4 * h->lv[l].N * R;
     return t;
-}
-
-int mg_apply_multi(const MgHierarchy* h, int64_t row_off, int R, const double* b, double* x, float* x0, float* t0,
-                   float* r0, float* coarse, const int* live, cudaStream_t st, int* launches) {
-    if (!h || !b || !x || !x0 || !t0 || !r0 || R < 1 || R > 64 || !h->has32) return RBFFD_ERR_INVALID_ARG;
-    if (h->n_levels > 1 && !coarse) return RBFFD_ERR_INVALID_ARG;
-    int n = 0;
-    multi_level<double, double>(*h, 0, b, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
-    if (launches) *launches += n;
-    return RBFFD_OK;
-}
-
-int mg_apply_multi_df(const MgHierarchy* h, int64_t row_off, int R, const float2* b, float2* x, float* x0, float* t0,
-                      float* r0, float* coarse, const int* live, cudaStream_t st, int* launches) {
-    if (!h || !b || !x || !x0 || !t0 || !r0 || R < 1 || R > 64 || !h->has32) return RBFFD_ERR_INVALID_ARG;
-    if (h->n_levels > 1 && !coarse) return RBFFD_ERR_INVALID_ARG;
-    int n = 0;
-    multi_level<float2, float2>(*h, 0, b, row_off, x, x0, t0, r0, coarse, R, live, st, &n);
-    if (launches) *launches += n;
-    return RBFFD_OK;
 }
 
 const MgHierarchy* mg_hierarchy(const rbffd_mg* h) {
@@ -1145,12 +889,14 @@ int mg_apply(const MgHierarchy* h, bool fp32, const double* b, double* x, const 
 
 // ---------------------------------------------------------------- C ABI -----
 extern "C" size_t rbffd_mg_workspace_size(int64_t N, int64_t nnz) {
+    RBFFD_NVTX("rbffd_mg_workspace_size");
     (void)nnz;  // the fine matrix stays the caller's
     if (N <= 0 || N > 0x7fffffffLL) return 0;
     return rbffd::mg_layout(nullptr, N, nullptr, nullptr);
 }
 
 extern "C" int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes) {
+    RBFFD_NVTX("rbffd_mg_levels");
     const rbffd::MgHierarchy* h = rbffd::mg_hierarchy(mg);
     if (!h) return 0;
     if (n_nodes)
@@ -1159,6 +905,7 @@ extern "C" int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes) {
 }
 
 extern "C" int rbffd_mg_level(const rbffd_mg* mg, int32_t level, rbffd_mg_level_info* out) {
+    RBFFD_NVTX("rbffd_mg_level");
     using namespace rbffd;
     if (!mg || !out) return RBFFD_ERR_INVALID_ARG;
     MgHierarchy h;
@@ -1186,6 +933,7 @@ extern "C" int rbffd_mg_level(const rbffd_mg* mg, int32_t level, rbffd_mg_level_
 
 extern "C" int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32, rbffd_mg* mg,
                                    void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_mg_adjoint_of");
     using namespace rbffd;
     if (!mg) return RBFFD_ERR_INVALID_ARG;
     std::memset(mg, 0, sizeof(*mg));
@@ -1199,6 +947,7 @@ extern "C" int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, con
 }
 
 extern "C" int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x, void* stream) {
+    RBFFD_NVTX("rbffd_mg_apply");
     using namespace rbffd;
     const MgHierarchy* h = mg_hierarchy(mg);
     if (!h || !b || !x || b == x) return RBFFD_ERR_INVALID_ARG;
@@ -1208,6 +957,7 @@ extern "C" int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b,
 extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
                               const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
                               size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_mg_setup");
     using namespace rbffd;
     if (!mg) return RBFFD_ERR_INVALID_ARG;
     std::memset(mg, 0, sizeof(*mg));
@@ -1225,6 +975,7 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
 extern "C" int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* AT,
                                       const rbffd_csr* AT32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
                                       size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_mg_setup_adjoint");
     using namespace rbffd;
     if (!mg) return RBFFD_ERR_INVALID_ARG;
     std::memset(mg, 0, sizeof(*mg));
@@ -1299,7 +1050,7 @@ int rbffd::mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float*
         Ac.val = FC.val;
         Ac.dtype = 0;
         int rc = rbffd_transpose(&Ac, const_cast<int64_t*>(C.row_ptr), const_cast<int*>(C.col),
-                                 const_cast<double*>(C.val), s.tr_ws, s.tr_bytes, st);
+                                 const_cast<double*>(C.val), nullptr, s.tr_ws, s.tr_bytes, st);
         if (rc != RBFFD_OK) return rc;
         mg_f32_kernel<<<blocks_for(FC.nnz), kT, 0, st>>>(C.val, FC.nnz, const_cast<float*>(C.val32));
         C.nnz = FC.nnz;
@@ -1316,7 +1067,7 @@ int rbffd::mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float*
         P.col = L.pidx;
         P.val = L.pval;
         P.dtype = 0;
-        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
+        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, nullptr, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
         mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
         mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, (double)nc / (double)L.N,
                                                                  L.pval, L.pval32);
@@ -1413,7 +1164,7 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
             Ac.val = s.a_val;
             Ac.dtype = 0;
             if ((rc = rbffd_transpose(&Ac, const_cast<int64_t*>(C.row_ptr), const_cast<int*>(C.col),
-                                      const_cast<double*>(C.val), s.tr_ws, s.tr_bytes, st)) != RBFFD_OK)
+                                      const_cast<double*>(C.val), nullptr, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK)
                 return rc;
             mg_f32_kernel<<<blocks_for(cnnz), kT, 0, st>>>(C.val, cnnz, const_cast<float*>(C.val32));
             note_launches(1);
@@ -1439,7 +1190,7 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
         P.col = L.pidx;
         P.val = L.pval;
         P.dtype = 0;
-        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
+        if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, nullptr, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
         const double cscale = (double)nc / (double)L.N;
         if (!transposed) {
             mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, C.mask, cscale, L.rval, L.rval32);

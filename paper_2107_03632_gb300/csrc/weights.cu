@@ -636,18 +636,33 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             --na;
             group_sync<NT>();
             const V inv = R::ld(tv);
-            // every active row and the g row, one thread per row: scale its
-            // column k by the pivot reciprocal (pivot row -> e_k), then
-            // column j -= P[pr][j] * (scaled) P[r][k]; the pivot row, no
-            // longer active, is only read
-            const S* prow = P + (size_t)pr * LDS;
+            // every active row and the g row: column k scaled by the pivot
+            // reciprocal (pivot row -> e_k) ...
             for (int t = lane; t <= na; t += NT) {
-                const int r = (t < na) ? act[t] : n;
-                S* rr = P + (size_t)r * LDS;
-                const V mk = R::mul(R::ld(rr + k), inv);
-                R::st(rr + k, mk);
-                for (int j = 0; j < k; ++j) R::st(rr + j, R::nfma(R::ld(prow + j), mk, R::ld(rr + j)));
-                for (int j = k + 1; j < s; ++j) R::st(rr + j, R::nfma(R::ld(prow + j), mk, R::ld(rr + j)));
+                S* rr = P + (size_t)((t < na) ? act[t] : n) * LDS;
+                R::st(rr + k, R::mul(R::ld(rr + k), inv));
+            }
+            group_sync<NT>();
+            // ... then column j -= P[pr][j] * (scaled) P[r][k] for j != k,
+            // flattened over (row, column) so that every lane of the group
+            // has an element (one thread per row left whole warps idle once
+            // fewer rows than lanes remained); the pivot row is only read
+            const S* prow = P + (size_t)pr * LDS;
+            const int C = s - 1, total = (na + 1) * C;
+            if (C > 0) {
+                int t = lane / C, jj = lane - (lane / C) * C;
+                const int dt = NT / C, dj = NT - (NT / C) * C;
+                for (int e = lane; e < total; e += NT) {
+                    S* rr = P + (size_t)((t < na) ? act[t] : n) * LDS;
+                    const int j = jj < k ? jj : jj + 1;
+                    R::st(rr + j, R::nfma(R::ld(prow + j), R::ld(rr + k), R::ld(rr + j)));
+                    t += dt;
+                    jj += dj;
+                    if (jj >= C) {
+                        jj -= C;
+                        ++t;
+                    }
+                }
             }
             group_sync<NT>();
         }
@@ -934,8 +949,15 @@ WCfg default_cfg(int n, int m) {
 
 WCfg chosen_cfg(int n, int m) {
     // RBFFD_WEIGHTS=lu forces the full Gaussian elimination (comparisons)
-    // RBFFD_WEIGHTS=ns64 forces the FP64 null-space elimination
+    // RBFFD_WEIGHTS=ns64 forces the FP64 null-space elimination, one warp
+    // RBFFD_WEIGHTS=df forces its double-float form, one warp (1 <= m <= 6)
     const char* sel = std::getenv("RBFFD_WEIGHTS");
+    if (sel && std::strcmp(sel, "df") == 0 && m >= 1 && m <= kDfMaxM) {
+        WCfg c{4, 1};
+        size_t smem = 0;
+        c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
+        if (cfg_valid(c, n, m)) return c;
+    }
     if (sel && (std::strcmp(sel, "lu") == 0 || (std::strcmp(sel, "ns64") == 0 && m >= 1))) {
         WCfg c = default_cfg(n, m);
         size_t smem = 0;
@@ -1021,6 +1043,7 @@ bool weights_args_ok(const double* xy, const int32_t* idx, const double* w, int6
 
 extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m, double* w,
                              int32_t* node_status, void* stream) {
+    RBFFD_NVTX("rbffd_weights");
     using namespace rbffd;
     if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
     return launch_weights(chosen_cfg(n, m), xy, idx, N, n, m, w, node_status, as_stream(stream));
@@ -1029,6 +1052,7 @@ extern "C" int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, in
 extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,
                                       double* w, int32_t* node_status, int32_t precision,
                                       rbffd_weights_config* best, void* stream) {
+    RBFFD_NVTX("rbffd_weights_autotune");
     using namespace rbffd;
     if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
     if (precision != RBFFD_WEIGHTS_FP64 && precision != RBFFD_WEIGHTS_DF && precision != RBFFD_WEIGHTS_ANY)
@@ -1091,6 +1115,7 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
 }
 
 extern "C" int rbffd_weights_get_config(int32_t n, int32_t m, rbffd_weights_config* cfg) {
+    RBFFD_NVTX("rbffd_weights_get_config");
     using namespace rbffd;
     if (!cfg || n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8 || n < (m + 1) * (m + 2) / 2)
         return RBFFD_ERR_INVALID_ARG;
@@ -1109,6 +1134,7 @@ extern "C" int rbffd_weights_get_config(int32_t n, int32_t m, rbffd_weights_conf
 }
 
 extern "C" int rbffd_weights_set_config(int32_t n, int32_t m, const rbffd_weights_config* cfg) {
+    RBFFD_NVTX("rbffd_weights_set_config");
     using namespace rbffd;
     if (n < 1 || n > RBFFD_MAX_STENCIL || m < 0 || m > 8 || n < (m + 1) * (m + 2) / 2) return RBFFD_ERR_INVALID_ARG;
     const auto key = std::make_tuple(current_device(), (int)n, (int)m);

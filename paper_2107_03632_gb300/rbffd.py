@@ -185,7 +185,7 @@ SIGNATURES = {
     "rbffd_assemble": (ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _VP, _I64, _VP, _VP, _VP, _VP]),
     "rbffd_rhs": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "rbffd_transpose_workspace_size": (_SZ, [_I64]),
-    "rbffd_transpose": (ctypes.c_int, [ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "rbffd_transpose": (ctypes.c_int, [ctypes.POINTER(Csr), _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "rbffd_solve_workspace_size": (_SZ, [_I64, ctypes.POINTER(SolveOpts)]),
     "rbffd_solve": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), _VP, _VP,
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _VP, _SZ, _VP]),
@@ -401,11 +401,12 @@ def rbffd_transpose(A: CsrMatrix, want_f32: bool = False) -> CsrMatrix:
     row_ptr_t = torch.empty(N + 1, dtype=torch.int64, device=dev)
     col_t = torch.empty(nnz, dtype=torch.int32, device=dev)
     val_t = torch.empty(nnz, dtype=torch.float64, device=dev)
+    val32 = torch.empty(nnz, dtype=torch.float32, device=dev) if want_f32 else None
     ws = _workspace(lib.rbffd_transpose_workspace_size(N), dev)
     c = A.c64()
-    _check(lib.rbffd_transpose(ctypes.byref(c), _ptr(row_ptr_t), _ptr(col_t), _ptr(val_t), _ptr(ws), ws.numel(),
-                               _stream(dev)), "rbffd_transpose")
-    val32 = val_t.to(torch.float32) if want_f32 else None
+    _check(lib.rbffd_transpose(ctypes.byref(c), _ptr(row_ptr_t), _ptr(col_t), _ptr(val_t),
+                               _ptr(val32) if val32 is not None else None, _ptr(ws), ws.numel(), _stream(dev)),
+           "rbffd_transpose")
     return CsrMatrix(row_ptr_t, col_t, val_t, val32)
 
 

@@ -33,21 +33,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
-from fixtures import disk_nodes, fourier_sources, manufactured, splitmix64  # noqa: E402
+from fixtures import disk_nodes, fourier_sources, manufactured, sample_indices  # noqa: E402
 
 WORKLOADS = {"disk_1M_m4_n30": (1.7725e-3, 4, 30), "disk_4M_m6_n56": (8.862e-4, 6, 56)}
 SEED = 2107
 N_SAMPLE = 4096
 _G = {}
-
-
-def sample_indices(N: int, count: int, seed: int) -> np.ndarray:
-    """Up to `count` distinct node indices, the first distinct draws of
-    SplitMix64 (top 53 bits scaled to [0, N)), sorted."""
-    z = splitmix64(seed, 4 * count)
-    draws = ((z >> np.uint64(11)).astype(np.float64) * (N / 9007199254740992.0)).astype(np.int64)
-    _, first = np.unique(draws, return_index=True)
-    return np.sort(draws[np.sort(first)[:count]])
 
 
 def _init(path_xy, path_idx):

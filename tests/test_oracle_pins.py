@@ -483,3 +483,27 @@ def test_solve_refined_matches_refined_superlu(h, m, n):
     l_r, _ = oracle.solve_refined(*A, rhs_t, None, transpose=True)
     assert np.abs(l_k - l_r).max() <= 1e-12 * np.abs(l_r).max()
     assert np.abs(l_k - l_d).max() <= 1e-8 * np.abs(l_r).max()
+
+
+@pytest.mark.parametrize("m,n,bar", [(2, 6, 1e-9), (4, 15, 1e-6)])
+def test_weights_unisolvent_against_exact_rational_solution(m, n, bar):
+    """n = s: P^T w = lap p alone fixes the weights; solved exactly in rational
+    arithmetic from the same shifted coordinates (tests/exact_unisolvent.py).
+    The oracle's LU of the whole (n+s)^2 system stays within `bar` of it
+    (it loses ~cond(P) ulps: 2.8e-8 with x86 LAPACK, 5.4e-7 with aarch64's,
+    at m = 4, n = 15 on this disk)."""
+    from exact_unisolvent import exact_weights
+
+    d = disk_nodes(0.1)
+    idx = oracle.knn(d.xy, n)
+    nodes = np.arange(0, d.N, 3)
+    w, st = oracle.weights(d.xy, idx, m, nodes=nodes)
+    ex = np.array([exact_weights(d.xy, idx[i], i, m) for i in nodes])
+    assert not st.any()
+    assert (np.abs(w - ex).max(axis=1) / np.abs(ex).max(axis=1)).max() <= bar
+    # and the exact weights are Laplacian-exact on the monomials (Pins the helper too.)
+    X = d.xy[idx[nodes[0]]] - d.xy[nodes[0]]
+    for a, b in oracle.monomial_exponents(m):
+        want = 2.0 if (a, b) in ((2, 0), (0, 2)) else 0.0
+        got = float(np.sum(ex[0] * X[:, 0] ** a * X[:, 1] ** b))
+        assert abs(got - want) <= 1e-9 * np.abs(ex[0] * X[:, 0] ** a * X[:, 1] ** b).sum() + 1e-12
