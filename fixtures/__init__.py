@@ -14,6 +14,7 @@ from .disk import (  # noqa: F401
     fourier_params,
     fourier_sources,
     batched_instances,
+    sample_indices,
     DiskNodes,
     CONFIGS,
 )

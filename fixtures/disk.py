@@ -131,6 +131,16 @@ def fourier_sources(xy: np.ndarray, n_rhs: int, seed: int, n_waves: int = 8) -> 
     return out
 
 
+def sample_indices(N: int, count: int, seed: int) -> np.ndarray:
+    """Up to `count` distinct indices in [0, N): the first distinct draws of
+    SplitMix64 (top 53 bits scaled to [0, N)), sorted.  Picks the sampled
+    nodes of the full-size parity checks."""
+    z = splitmix64(seed, 4 * count)
+    draws = ((z >> np.uint64(11)).astype(np.float64) * (N / 9007199254740992.0)).astype(np.int64)
+    _, first = np.unique(draws, return_index=True)
+    return np.sort(draws[np.sort(first)[:count]])
+
+
 def batched_instances(seed: int = 2107, count: int = 256, n_lo: float = 1e4, n_hi: float = 2e5):
     """Per-instance (seed_i, h_i, m_i) for the batched uneven workload.
 

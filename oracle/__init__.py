@@ -23,7 +23,7 @@ tests/test_oracle_*.py.
 """
 
 from .knn import knn, knn_query, knn_grid  # noqa: F401
-from .weights import monomial_exponents, n_monomials, local_system, weights  # noqa: F401
+from .weights import monomial_exponents, n_monomials, local_system, weights, weights_rows  # noqa: F401
 from .assemble import assemble, rhs  # noqa: F401
 from .solve import solve_direct, solve_refined, residual_extended, gmres_right, adjoint_gradient, poisson_solve  # noqa: F401
 from .explicit import explicit_step, l2_estimate_nodes  # noqa: F401

@@ -84,7 +84,11 @@ def local_system(xs: np.ndarray, m: int):
 
 def scaled_stencil(xy: np.ndarray, idx: np.ndarray, nodes: np.ndarray):
     """Shifted/scaled stencil coordinates (B, n, 2) and the scale delta (B,)."""
-    X = xy[idx[nodes].astype(np.int64)] - xy[nodes][:, None, :]
+    return _scaled_rows(xy, idx[nodes], nodes)
+
+
+def _scaled_rows(xy: np.ndarray, sten: np.ndarray, centres: np.ndarray):
+    X = xy[sten.astype(np.int64)] - xy[centres][:, None, :]
     d2 = X[:, :, 0] * X[:, :, 0] + X[:, :, 1] * X[:, :, 1]
     delta = np.sqrt(d2.max(axis=1))
     return X / delta[:, None, None], delta
@@ -96,17 +100,26 @@ def weights(xy: np.ndarray, idx: np.ndarray, m: int, nodes=None, chunk: int = 20
     Row r holds the weights of stencil idx[nodes[r]] in the same order.
     Status 1 marks a stencil whose system is singular (e.g. coincident nodes).
     """
-    xy = np.asarray(xy, dtype=np.float64)
     idx = np.asarray(idx)
     if nodes is None:
         nodes = np.arange(idx.shape[0])
     nodes = np.asarray(nodes, dtype=np.int64)
-    n = idx.shape[1]
-    out = np.zeros((nodes.size, n), dtype=np.float64)
-    status = np.zeros(nodes.size, dtype=np.int32)
-    for s0 in range(0, nodes.size, chunk):
-        sel = nodes[s0 : s0 + chunk]
-        xs, delta = scaled_stencil(xy, idx, sel)
+    return weights_rows(xy, idx[nodes], nodes, m, chunk)
+
+
+def weights_rows(xy: np.ndarray, sten: np.ndarray, centres: np.ndarray, m: int, chunk: int = 2048):
+    """The same for explicit stencil rows: row r of `sten` is the stencil of
+    node centres[r] (its weights approximate the Laplacian at that node)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    sten = np.asarray(sten)
+    centres = np.asarray(centres, dtype=np.int64)
+    n = sten.shape[1]
+    out = np.zeros((centres.size, n), dtype=np.float64)
+    status = np.zeros(centres.size, dtype=np.int32)
+    for s0 in range(0, centres.size, chunk):
+        sel = slice(s0, s0 + chunk)
+        xs, delta = _scaled_rows(xy, sten[sel], centres[sel])
+        B = xs.shape[0]
         A, rhs = local_system(xs, m)
         # coincident nodes: an exactly zero distance off the diagonal
         dxx = xs[:, :, None, 0] - xs[:, None, :, 0]
@@ -120,15 +133,15 @@ def weights(xy: np.ndarray, idx: np.ndarray, m: int, nodes=None, chunk: int = 20
             bad = ~np.isfinite(sol).all(axis=1)
         except np.linalg.LinAlgError:
             sol = np.zeros_like(rhs)
-            bad = np.zeros(sel.size, dtype=bool)
-            for r in range(sel.size):
+            bad = np.zeros(B, dtype=bool)
+            for r in range(B):
                 try:
                     sol[r] = np.linalg.solve(A[r], rhs[r])
                     bad[r] = not np.isfinite(sol[r]).all()
                 except np.linalg.LinAlgError:
                     bad[r] = True
         bad = bad | dup
-        out[s0 : s0 + sel.size] = sol[:, :n] / (delta * delta)[:, None]
-        status[s0 : s0 + sel.size] = bad.astype(np.int32)
-        out[s0 : s0 + sel.size][bad] = 0.0
+        out[sel] = sol[:, :n] / (delta * delta)[:, None]
+        status[sel] = bad.astype(np.int32)
+        out[sel][bad] = 0.0
     return out, status
