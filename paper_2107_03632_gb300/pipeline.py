@@ -83,17 +83,23 @@ def poisson_solve(xy, is_dirichlet, f, g, m: int, n: int, precision: str = "fp64
 class PoissonSolve(torch.autograd.Function):
     """u = A^{-1} b(f, g) with the adjoint gradient in backward."""
 
+    # options that only make sense for the forward solve (its initial guess)
+    _FORWARD_ONLY = ("x0",)
+
     @staticmethod
     def forward(ctx, f, g, op: PoissonOperator, opts: dict | None = None):
         opts = dict(opts or {})
         b = op.rhs(f.detach().contiguous(), g.detach().contiguous())
         u, info = op.solve(b, **opts)
         ctx.op = op
-        ctx.opts = opts
+        ctx.opts = {k: v for k, v in opts.items() if k not in PoissonSolve._FORWARD_ONLY}
         ctx.info = info
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
+        need_f, need_g = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_f or need_g):
+            return None, None, None, None
         lam, dLdf, dLdg, _ = ctx.op.solve_adjoint(grad_u.detach().contiguous(), **ctx.opts)
-        return dLdf, dLdg, None, None
+        return (dLdf if need_f else None), (dLdg if need_g else None), None, None

@@ -94,12 +94,14 @@ def test_full_size_weights_sampled(case):
     assert int(st_ref.sum()) == 0 and int(case["st"].sum().item()) == 0
     assert rbffd.weights_config(n, m)["kernel"].find("-df") < 0
     err64 = _rel_rows(case["w"][T(q)].cpu().numpy(), ref)
+    print(f"{case['name']}: sampled weights, FP64 default: {err64:.3e}")
     assert err64 <= case["wtol"], err64
     try:
         for kernel, wpb in (("null-space-df", 1), ("null-space-df-4warp", 4)):
             rbffd.set_weights_config(n, m, kernel, wpb)
             w, st = rbffd.rbffd_weights(case["xy"], case["idx"], m)
             errdf = _rel_rows(w[T(q)].cpu().numpy(), ref)
+            print(f"{case['name']}: sampled weights, {kernel}: {errdf:.3e}")
             assert errdf <= case["wtol"] and int(st.sum().item()) == 0, (kernel, errdf)
             del w, st
     finally:
@@ -120,6 +122,8 @@ def test_full_size_solution_vs_oracle(case, precision):
     assert info["status"] == 0 and info["rel_residual"] <= 1e-10, info
     u = x.cpu().numpy()
     err = np.abs(u[ref_i] - ref_u).max() / np.abs(ref_u).max()
+    print(f"{case['name']}: solution ({precision}), {info['iters']} iterations, relative residual "
+          f"{info['rel_residual']:.2e}: {err:.3e} against the oracle")
     assert err <= 1e-8, err
     assert np.abs(u - case["u_ex"]).max() <= 1e-5  # the discretisation error of the scheme
     del A, b, mg, x
@@ -152,6 +156,7 @@ def test_full_size_adjoint_gradient(case):
     scale = max(np.abs(gold["dLdf"][1]).max(), np.abs(gold["dLdg"][1]).max())
     ef = np.abs(gf[gold["dLdf"][0]] - gold["dLdf"][1]).max() / scale
     eg = np.abs(gg[gold["dLdg"][0]] - gold["dLdg"][1]).max() / scale
+    print(f"{case['name']}: adjoint ({info_a['iters']} iterations): dL/df {ef:.3e}, dL/dg {eg:.3e} against the oracle")
     assert max(ef, eg) <= 1e-7, (ef, eg)
     assert np.abs(ustar.cpu().numpy()[gold["ustar"][0]] - gold["ustar"][1]).max() <= 1e-8 * np.abs(gold["ustar"][1]).max()
     # central differences of L along 32 seeded directions v = (v_f, v_g), |v|_inf = 1, eps = 1e-6 |theta|_inf.
@@ -176,5 +181,6 @@ def test_full_size_adjoint_gradient(case):
         fd = np.sum(((up - um) * (up + um - 2.0 * us))[interior]) / (2.0 * eps)
         ad = float(np.dot(gf, vf) + np.dot(gg, vg))
         worst = max(worst, abs(fd - ad) / max(abs(fd), abs(ad)))
+    print(f"{case['name']}: central differences, 32 directions: worst relative difference {worst:.3e}")
     assert worst <= 1e-5, worst
     del A, AT, mg, mga

@@ -375,3 +375,25 @@ def test_autograd_with_multigrid_vs_oracle(lib, precision):
     assert np.abs(fT.grad.cpu().numpy() - gf).max() / np.abs(gf).max() <= 1e-6
     assert np.abs(gT.grad.cpu().numpy() - gg).max() / np.abs(gg).max() <= 1e-6
     assert torch.isfinite(fT.grad).all()
+
+
+def test_autograd_forward_only_options_and_needed_gradients(lib):
+    """An initial guess given to the forward solve does not reach the adjoint
+    solve, and only the gradients that torch asks for are formed."""
+    import torch
+
+    from paper_2107_03632_gb300 import pipeline
+
+    d = disk_nodes(0.04)
+    u_ex, f, g = manufactured(d.xy)
+    op = pipeline.PoissonOperator(T(d.xy), T(d.is_dirichlet), 2, 12)
+    fT = T(f).requires_grad_(True)
+    gT = T(g)  # no gradient wanted
+    opts = {"tol": 1e-11, "x0": T(np.zeros(d.N))}
+    u = pipeline.PoissonSolve.apply(fT, gT, op, opts)
+    (u * u).sum().backward()
+    assert fT.grad is not None and torch.isfinite(fT.grad).all()
+    assert gT.grad is None
+    uu, (idx, w, rp, col, val, b) = oracle.poisson_solve(d.xy, d.is_dirichlet, f, g, 2, 12)
+    gf, _, _ = oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, 2.0 * uu)
+    assert np.abs(fT.grad.cpu().numpy() - gf).max() / np.abs(gf).max() <= 1e-7
