@@ -1148,7 +1148,11 @@ def run_gpu(args):
     # ones, which stay in force for the headline
     rbffd.rbffd_stencils(xy, n, idx, ws_knn)
     wcfg_df = rbffd.rbffd_weights_autotune(xy, idx, m, "df") if (args.df_steps > 0 and m <= 6) else None
-    if args.no_autotune:  # the library's default configuration (FP64)
+    if args.weights_config:  # pinned, e.g. "null-space-4warp:4" (profiling runs)
+        kern, wpb = args.weights_config.split(":")
+        rbffd.set_weights_config(n, m, kern, int(wpb))
+        wcfg = rbffd.weights_config(n, m)
+    elif args.no_autotune:  # the library's default configuration (FP64)
         wcfg = rbffd.weights_config(n, m)
     else:
         wcfg = rbffd.rbffd_weights_autotune(xy, idx, m, "fp64")
@@ -1441,6 +1445,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default FP64 weight-solve configuration (profiling runs)")
+    ap.add_argument("--weights-config", default=None,
+                    help="pin the weight-solve configuration KERNEL:WARPS_PER_BLOCK instead of autotuning")
     ap.add_argument("--no-peak-probe", action="store_true", help="skip the cuBLAS DGEMM FP64 peak probe")
     args = ap.parse_args()
     if args.warmup < 3:

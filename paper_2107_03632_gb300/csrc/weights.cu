@@ -307,18 +307,21 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
 // FP64 work is ~n s^2 (elimination) + 2 s^2 q + s q^2 (reduced matrix) +
 // q^3/3 flops instead of (2/3)(n+s)^3, about half at m = 6, n = 56.
 //
-// Shared memory per warp (doubles unless noted), nodes in permuted order
-// [r1, r2] once the pivots are known:
+// Shared memory per stencil (8-byte slots unless noted), nodes in permuted
+// order [r1, r2] once the pivots are known:
 //   Phi  n x LDF     r^3 kernel matrix; T = Phi12 - Phi11 X^T overwrites
-//                    Phi12, S = Z^T Phi Z (lower triangle) overwrites Phi22
-//   P    (n+1) x LDS monomials, row n holds g; after elimination rows r2
-//                    hold X and row n holds w0[r1]
+//                    Phi12, S = Z^T Phi Z (lower triangle) overwrites Phi22.
+//                    Before Phi is built the same region holds
+//   P    (n+1) x LDS monomials, row n holds g; after the elimination rows r2
+//                    hold X and row n holds w0[r1] -- copied out to
+//   X    q x LDX     X compacted (row j = node r2_j), and w0 (s)
 //   crd  2n          scaled coordinates (caller order)
 //   fv, uv, wv  n    rhs 9|xh|, f - Phi w0, permuted weights
 //   tv   n           reduced rhs / solution (q used)
 //   perm, act  n int permutation and the active-row list
+// (~34.6 KB at m = 6, n = 56: six stencils per SM.)
 struct NsGeom {
-    int n, m, s, q, LDF, LDS;
+    int n, m, s, q, LDF, LDS, LDX;
     int doubles, ints, bytes;
 };
 
@@ -330,7 +333,10 @@ NsGeom ns_geom(int n, int m) {
     g.q = n - g.s;
     g.LDF = n | 1;
     g.LDS = g.s | 1;
-    g.doubles = n * g.LDF + (n + 1) * g.LDS + 2 * n + 4 * n;
+    g.LDX = g.s | 1;
+    // P must fit in Phi's region while the elimination runs
+    const int phi = std::max(n * g.LDF, (n + 1) * g.LDS);
+    g.doubles = phi + g.q * g.LDX + g.s + 2 * n + 4 * n;
     g.ints = 2 * n;
     g.bytes = (int)align_up((size_t)g.doubles * 8 + (size_t)g.ints * 4, 16);
     return g;
@@ -514,9 +520,12 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     __shared__ unsigned long long red_u64[4];
     __shared__ int red_i[8];
     const int q = n - s;
+    const int LDX = LDS;
     S* Phi = reinterpret_cast<S*>(smem_raw + (size_t)wib * bytes_per_warp);
-    S* P = Phi + (size_t)n * LDF;
-    S* crd = P + (size_t)(n + 1) * LDS;
+    S* P = Phi;  // the elimination's matrix, inside Phi's region until Phi is built
+    S* X = Phi + max(n * LDF, (n + 1) * LDS);
+    S* w0 = X + (size_t)q * LDX;
+    S* crd = w0 + s;
     S* fv = crd + 2 * n;
     S* uv = fv + n;
     S* wv = uv + n;
@@ -668,6 +677,13 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         }
         if (!singular) {
             for (int t = lane; t < q; t += NT) perm[s + t] = act[t];
+            // X (rows of the non-pivot nodes) and w0 out of P, whose region
+            // Phi takes next: X[j][k] = P[act[j]][k], w0[k] = P[n][k]
+            for (int e = lane; e < (q + 1) * s; e += NT) {
+                const int j = e / s, k = e - (e / s) * s;
+                if (j < q) R::st(X + (size_t)j * LDX + k, R::ld(P + (size_t)act[j] * LDS + k));
+                else R::st(w0 + k, R::ld(P + (size_t)n * LDS + k));
+            }
         }
         group_sync<NT>();
 
@@ -703,12 +719,10 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         group_sync<NT>();
 
         if (!singular) {
-            // X[j][k] = P[perm[s + j]][k], w0[k] = P[n][k]
-            const S* w0 = P + (size_t)n * LDS;
             // ---- T = Phi12 - Phi11 X^T  (s x q, in place) --------------------
             for (int e = lane; e < s * q; e += NT) {
                 const int a = e / q, j = e - (e / q) * q;
-                const S* xr = P + (size_t)perm[s + j] * LDS;
+                const S* xr = X + (size_t)j * LDX;
                 const S* pr = Phi + (size_t)a * LDF;
                 // two independent chains (few warps per SM: latency, not
                 // issue, limits a single chain)
@@ -741,8 +755,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while (j * (j + 1) / 2 > e) --j;
                 while ((j + 1) * (j + 2) / 2 <= e) ++j;
                 const int l = e - j * (j + 1) / 2;
-                const S* xj = P + (size_t)perm[s + j] * LDS;
-                const S* xl = P + (size_t)perm[s + l] * LDS;
+                const S* xj = X + (size_t)j * LDX;
+                const S* xl = X + (size_t)l * LDX;
                 const S* prj = Phi + (size_t)(s + j) * LDF;
                 V acc = R::ld(prj + s + l), acc1 = R::zero();
                 for (int k = 0; k < s; ++k) {
@@ -753,7 +767,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             }
             // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
             for (int j = lane; j < q; j += NT) {
-                const S* xj = P + (size_t)perm[s + j] * LDS;
+                const S* xj = X + (size_t)j * LDX;
                 V acc = R::ld(uv + s + j), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
@@ -825,15 +839,14 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 group_sync<NT>();
             }
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
-            const S* w0 = P + (size_t)n * LDS;
             for (int k = lane; k < s; k += NT) {
                 V acc = R::ld(w0 + k), acc1 = R::zero();
                 int j = 0;
                 for (; j + 1 < q; j += 2) {
-                    acc = R::nfma(R::ld(P + (size_t)perm[s + j] * LDS + k), R::ld(tv + j), acc);
-                    acc1 = R::nfma(R::ld(P + (size_t)perm[s + j + 1] * LDS + k), R::ld(tv + j + 1), acc1);
+                    acc = R::nfma(R::ld(X + (size_t)j * LDX + k), R::ld(tv + j), acc);
+                    acc1 = R::nfma(R::ld(X + (size_t)(j + 1) * LDX + k), R::ld(tv + j + 1), acc1);
                 }
-                if (j < q) acc = R::nfma(R::ld(P + (size_t)perm[s + j] * LDS + k), R::ld(tv + j), acc);
+                if (j < q) acc = R::nfma(R::ld(X + (size_t)j * LDX + k), R::ld(tv + j), acc);
                 R::st(wv + k, R::add(acc, acc1));
             }
             for (int j = lane; j < q; j += NT) R::st(wv + s + j, R::ld(tv + j));
