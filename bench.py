@@ -168,8 +168,8 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM traffic of the inner-solve SpMV from one ncu capture (see
-# profiles/spmv_df_kernel_disk_1M_m4_n30.md): dram read + write per launch
+# DRAM traffic of the inner-solve SpMV from one ncu capture of
+# spmv_df_kernel at 1M nodes (m = 4, n = 30): dram read + write per launch
 # divided by the kernel's algorithmic bytes at that size.  The ratio scales
 # the capture to a full-size launch (traffic grows with the matrix) and is
 # valid only while the kernel's source is the one captured.
@@ -840,7 +840,8 @@ def run_gpu_adjoint(args):
     A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
     AT = rbffd.rbffd_transpose(A, want_f32=True)
     mg = rbffd.Multigrid(xy, mask, A)
-    mga = rbffd.Multigrid.adjoint_of(mg, AT)
+    galerkin = args.adjoint_mg == "galerkin"
+    mga = (rbffd.Multigrid.galerkin_adjoint_of if galerkin else rbffd.Multigrid.adjoint_of)(mg, AT)
     opts = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mg)
     opts_a = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mga)
     ws_s = rbffd.solve_workspace(N, opts, dev)
@@ -939,7 +940,9 @@ def run_gpu_adjoint(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": ADJOINT_WORKLOAD, "N": N, "m": m, "n": n, "tol": 1e-10,
-                   "precond": "multigrid (forward) and transposed multigrid (adjoint), float32 V-cycles",
+                   "precond": ("multigrid (forward) and " +
+                               ("Galerkin multigrid, right-preconditioned" if galerkin else
+                                "transposed multigrid, left-preconditioned") + " (adjoint), float32 V-cycles"),
                    "weights_config": wcfg, "parallelism": f"replicas x{ws_}",
                    "l2": "inputs larger than L2 (CSR + transpose ~%.1f GB)" % (2 * A.nnz * 16 / 1e9)},
         "solve": {"forward_iters": info["iters"], "adjoint_iters": info_a["iters"],
@@ -1441,6 +1444,9 @@ def main():
                     help="timed steps with the FP64 solve (default: --steps; 0: skip)")
     ap.add_argument("--df-steps", type=int, default=5,
                     help="timed steps with double-float weights, a labelled extra (at most --steps; 0: skip)")
+    ap.add_argument("--adjoint-mg", default="galerkin", choices=["galerkin", "transposed"],
+                    help="adjoint workload: the adjoint hierarchy (Galerkin coarse operators, or the transposed "
+                         "forward cycle)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",

@@ -277,7 +277,9 @@ int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t n, int64_t
 /* rows must be identity rows, as rbffd_assemble writes them).  The adjoint */
 /* solve takes the hierarchy of rbffd_mg_setup_adjoint / _adjoint_of: it    */
 /* solves the interior block L_ii^T x_i = b_i left-preconditioned by the    */
-/* transposed cycle and sets x_b = b_b - L_ib^T x_i after every pass.       */
+/* transposed cycle and sets x_b = b_b - L_ib^T x_i after every pass; with  */
+/* a hierarchy of rbffd_mg_galerkin_adjoint it runs right-preconditioned    */
+/* (below).                                                                  */
 /*   mg       : host object filled here; read by rbffd_solve.  It points     */
 /*              into ws, which must stay allocated and unchanged meanwhile.  */
 /*   A, A32   : the fine-level operator (as passed to rbffd_solve; A32 may   */
@@ -320,6 +322,31 @@ int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_
 /* forward hierarchy, sizes differ), RBFFD_ERR_WORKSPACE.                    */
 int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32, rbffd_mg* mg, void* ws,
                         size_t ws_bytes, void* stream);
+/* rbffd_mg_galerkin_adjoint: the adjoint hierarchy of a built forward     */
+/* hierarchy `fwd` with GALERKIN coarse operators: node sets, interpolation */
+/* and transfers as rbffd_mg_adjoint_of (restriction R = P^T, prolongation  */
+/* (N_c / N_f) P without the coarse Dirichlet columns), but each coarse     */
+/* operator is the product R A_l P of the level above (A_0 = AT), its rows  */
+/* at coarse Dirichlet nodes replaced by identity rows, its columns sorted; */
+/* smoother weights from its own diagonal; the coarsest inverted.  The      */
+/* product is computed on the device in a fixed summation order (the same   */
+/* bits on every run).  rbffd_solve_adjoint runs with such a hierarchy       */
+/* RIGHT-preconditioned on the whole system: M = the cycle followed by the  */
+/* Dirichlet back substitution, from x_b = b_b - L_ib^T x_i, so A^T M is    */
+/* block diagonal with an identity Dirichlet block.                         */
+/*   AT, AT32 : as for rbffd_mg_adjoint_of.                                  */
+/*   ws       : rbffd_mg_galerkin_workspace_size(fwd) bytes: the layout of   */
+/*              rbffd_mg_adjoint_of with room for 256 entries per coarse row */
+/*              on average (0 if fwd is not a built forward hierarchy).      */
+/* Synchronises `stream`.  Errors: RBFFD_ERR_INVALID_ARG (as                 */
+/* rbffd_mg_adjoint_of), RBFFD_ERR_WORKSPACE (ws too small; or a coarse row  */
+/* with more than 512 entries, or one with more than 1024 distinct columns  */
+/* in R_c A_l, or more entries on a level than the layout holds),           */
+/* RBFFD_ERR_SINGULAR_STENCIL (a zero diagonal, a singular coarsest         */
+/* matrix).                                                                  */
+size_t rbffd_mg_galerkin_workspace_size(const rbffd_mg* fwd);
+int rbffd_mg_galerkin_adjoint(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32, rbffd_mg* mg,
+                              void* ws, size_t ws_bytes, void* stream);
 /* Levels of a built hierarchy (finest first); n_nodes: RBFFD_MG_MAX_LEVELS  */
 /* entries, may be NULL.  Returns the level count, 0 if mg was not built.    */
 int rbffd_mg_levels(const rbffd_mg* mg, int64_t* n_nodes);
@@ -390,6 +417,15 @@ typedef struct rbffd_solve_opts {
     int32_t jacobi;      /* 1 = left Jacobi scaling (default), 0 = none */
     int32_t precond;     /* 0 = none / Jacobi as above, 1 = multigrid (mg) */
     const rbffd_mg* mg;  /* hierarchy from rbffd_mg_setup when precond = 1 */
+    /* rbffd_solve_batched with multigrid only (others ignore them): */
+    int64_t spin_limit;  /* polls of each bounded device wait of the persistent coarse-level kernel */
+                         /* before the solve stops with RBFFD_ERR_TIMEOUT; 0 = default (2^26) */
+    int32_t wait_test;   /* tests of the timeout path: 1 = the first coarse-level task waits on a */
+                         /* counter that nothing increments (the wait runs out); 0 otherwise */
+    int32_t persistent;  /* 1 = every instance's coarse levels as one persistent launch from a */
+                         /* device task queue; 0 (default) = one launch per level and operation */
+    int32_t device_loop; /* 1 = the whole solve as one CUDA graph launch whose loops run on the */
+                         /* device; 0 (default) = one graph launch per iteration, host-driven */
 } rbffd_solve_opts;
 
 typedef struct rbffd_solve_info {
@@ -450,8 +486,19 @@ int rbffd_misfit_grad(const double* u, const double* u_target, const uint8_t* is
 /* pair runs BiCGSTAB right-preconditioned by the instance's float32        */
 /* V-cycle, applied to all of its right-hand sides at once, with            */
 /* double-float (2 x float32) Krylov vectors and the matrix read as float32 */
-/* (leading, trailing) pairs, the solution kept in FP64; one iteration for  */
-/* all instances is one CUDA graph.  Either way each pair has its own       */
+/* (leading, trailing) pairs, the solution kept in FP64.  The instances'    */
+/* V-cycles run as one launch per (level, operation) over all instances,    */
+/* or (opts->persistent = 1) as launches on level 0 and ONE persistent     */
+/* launch for every instance's levels >= 1 (a device work queue of          */
+/* (instance, level, operation, tile) tasks; each dependency wait is        */
+/* bounded by opts->spin_limit polls, past which the solve stops with       */
+/* RBFFD_ERR_TIMEOUT).  Each iteration (both V-cycles and the BiCGSTAB     */
+/* kernels of every running pair) is one CUDA graph launch, the host       */
+/* reading the count of running pairs in between; with opts->device_loop = */
+/* 1 the whole solve -- rounds of (explicit FP64 residual, BiCGSTAB pass)  */
+/* -- is ONE graph launch whose loops run on the device (conditional WHILE */
+/* nodes, capped by max_outer and the per-pass iteration cap).             */
+/* Either way each pair has its own                                          */
 /* BiCGSTAB scalars and stops on its own relative residual (explicit FP64   */
 /* residual with the FP64 matrix, tol).  Blocks the host like rbffd_solve.  */
 /*   desc    : host array of n_inst descriptors (offsets contiguous, in      */

@@ -97,6 +97,20 @@ void prof_commit(const int* slots, int count, int keep) {
     }
 }
 
+void prof_commit_as(int slot, int count, int64_t bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (slot < 0 || slot >= (int)g_pairs.size()) return;
+    ProfPair& p = g_pairs[slot];
+    if (!p.pending) return;
+    float ms = 0.f;
+    if (count > 0 && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        g_prof_launches[p.kind] += count;
+        g_prof_ms[p.kind] += ms;
+        g_prof_bytes[p.kind] += bytes;
+    }
+    p.pending = false;
+}
+
 void prof_collect() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (ProfPair& p : g_pairs) {

@@ -117,6 +117,7 @@ struct BWork {
     char* mgws;
     char* mbtab;  // device tables of the batched V-cycle
     size_t mbtab_bytes;
+    int* loop;    // counters of the device-side loop (8 ints)
 };
 
 __device__ __forceinline__ int find_inst(const Inst* inst, int n_inst, int64_t row) {
@@ -677,7 +678,8 @@ __global__ void __launch_bounds__(kBT) md_load_kernel(const Unit* __restrict__ u
                                                       float2* __restrict__ rh, float2* __restrict__ p,
                                                       float2* __restrict__ v, Pairs pr, unsigned* inst_cnt,
                                                       int* inst_running, Ctl* ctl, double* part, double inner_tol,
-                                                      int max_iter) {
+                                                      int max_iter, const int* gate) {
+    if (gate && *(volatile const int*)gate == 0) return;  // the device loop decided to stop
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k0 = lane, k1 = lane + 32;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -945,6 +947,48 @@ __global__ void __launch_bounds__(kBT) md_update_xr_kernel(const Unit* __restric
     }
 }
 
+// ------------------------------------------------- the device-side loop ---
+// The multigrid mode's rounds (explicit FP64 residual, then BiCGSTAB passes)
+// run as one graph launch: an outer WHILE node over rounds and an inner
+// WHILE node over iterations, their conditions set by the two kernels below.
+// loop[0]: this round runs, loop[1]: rounds started, loop[2]: iterations
+// started, loop[3]: iterations of this round, loop[4..5]: (instance, rhs)
+// pair-iterations (a 64-bit count).  Each condition is also capped by those
+// counters -- max_outer rounds, and per round the per-pass cap every pair
+// obeys (kPassCap, max_iter) plus one -- so both loops end whatever the
+// solver's flags say.
+__global__ void b_reset_ctl_kernel(Ctl* ctl) {
+    if (threadIdx.x == 0) {
+        ctl->running = 0;
+        ctl->active = 0;
+    }
+}
+
+__global__ void b_decide_outer_kernel(const Ctl* ctl, int* loop, int max_outer, const int* stop,
+                                      cudaGraphConditionalHandle outer) {
+    if (threadIdx.x != 0) return;
+    const bool halt = stop && *(volatile const int*)stop != 0;
+    const int go = (!halt && ctl->active > 0 && loop[1] < max_outer) ? 1 : 0;
+    loop[0] = go;
+    loop[3] = 0;
+    if (go) loop[1] += 1;
+    cudaGraphSetConditional(outer, go);
+}
+
+__global__ void b_decide_inner_kernel(const Ctl* ctl, int* loop, int round_cap, const int* stop,
+                                      cudaGraphConditionalHandle inner) {
+    if (threadIdx.x != 0) return;
+    const bool halt = stop && *(volatile const int*)stop != 0;
+    const int run = ctl->running;
+    const int go = (!halt && loop[0] != 0 && run > 0 && loop[3] < round_cap) ? 1 : 0;
+    if (go) {
+        loop[2] += 1;
+        loop[3] += 1;
+        *reinterpret_cast<unsigned long long*>(loop + 4) += (unsigned long long)run;
+    }
+    cudaGraphSetConditional(inner, go);
+}
+
 // ------------------------------------------------------------------ host ---
 struct Plan {
     int n_inst = 0, R = 0, n_units = 0;
@@ -1061,6 +1105,7 @@ size_t layout(void* ws, const Plan& pl, BWork* w) {
         t.mgws = c.take<char>(pl.mg_total);
         t.mbtab_bytes = mg_batch_table_bytes(pl.n_inst, pl.N);
         t.mbtab = c.take<char>(t.mbtab_bytes);
+        t.loop = c.take<int>(8);
     }
     if (w) *w = t;
     return c.off;
@@ -1154,7 +1199,8 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         std::vector<int64_t> noff(pl.n_inst);
         for (int i = 0; i < pl.n_inst; ++i) noff[i] = pl.inst[i].node_off;
         const int rc = mg_batch_build(H.data(), noff.data(), pl.n_inst, R, w.f0, w.f1, w.f2, w.coarse,
-                                      pl.coarse_off.data(), w.mbtab, w.mbtab_bytes, st, &mb);
+                                      pl.coarse_off.data(), w.mbtab, w.mbtab_bytes, o->persistent,
+                                      (long long)o->spin_limit, o->wait_test, st, &mb);
         if (rc != RBFFD_OK) return -rc;
     }
     int vlaunch = 0;
@@ -1167,25 +1213,102 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
     float2* vt = reinterpret_cast<float2*>(w.mt);
     float2* vph = reinterpret_cast<float2*>(w.mph);
     float2* vsh = reinterpret_cast<float2*>(w.msh);
+    // one BiCGSTAB iteration of every running pair (with its two batched
+    // V-cycles), captured on `cap`
+    auto capture_iteration = [&](cudaStream_t cap) -> int {
+        md_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vp, w.pr, w.inst_running);
+        int rc = mg_batch_apply_df(mb, R, vp, vph, w.inst_running, cap, &vlaunch);
+        md_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo, R,
+                                               vph, vv, vrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+        md_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vsv, w.pr, w.inst_running);
+        if (rc == RBFFD_OK) rc = mg_batch_apply_df(mb, R, vsv, vsh, w.inst_running, cap, &vlaunch);
+        md_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo, R,
+                                               vsh, vt, vsv, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
+        md_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, vph, vsh, vsv, vt, vr, vrh, w.pr,
+                                                 w.inst_running, w.inst_cnt, w.ctl, w.part, o->max_iter);
+        return rc;
+    };
+    const bool device_loop = o->device_loop != 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    const int round_cap = std::min(std::max(o->max_iter, 1), kPassCap) + 1;
+    int* stop = mb.status;  // a bounded wait of the batched V-cycle ran out
     {
         cudaStream_t cap;
         RBFFD_CUDA_TRY_NEG(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int rc = RBFFD_OK;
-        if (e == cudaSuccess) {
-            md_update_p_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vp, w.pr, w.inst_running);
-            rc = mg_batch_apply_df(mb, R, vp, vph, w.inst_running, cap, &vlaunch);
-            md_spmm_kernel<0><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
-                                                   R, vph, vv, vrh, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
-            md_update_s_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, R, vr, vv, vsv, w.pr, w.inst_running);
-            if (rc == RBFFD_OK) rc = mg_batch_apply_df(mb, R, vsv, vsh, w.inst_running, cap, &vlaunch);
-            md_spmm_kernel<1><<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val32, w.val_lo,
-                                                   R, vsh, vt, vsv, w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part);
-            md_update_xr_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, u, vph, vsh, vsv, vt, vr, vrh,
-                                                     w.pr, w.inst_running, w.inst_cnt, w.ctl, w.part, o->max_iter);
-            e = cudaStreamEndCapture(cap, &graph);
+        cudaError_t e = cudaSuccess;
+        if (!device_loop) {
+            // one graph per iteration, launched by the host loop below
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = capture_iteration(cap);
+                e = cudaStreamEndCapture(cap, &graph);
+            }
+        } else {
+            // the whole solve as one graph: WHILE (rounds) { FP64 residual
+            // check, pass start, WHILE (iterations) { one iteration } }
+            e = cudaGraphCreate(&graph, 0);
+            cudaGraphConditionalHandle h_out = 0, h_in = 0;
+            cudaGraph_t body_out = nullptr, body_in = nullptr;
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_out, graph, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) {
+                cudaGraphNodeParams cp{};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h_out;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t n_out;
+                e = cudaGraphAddNode(&n_out, graph, nullptr, nullptr, 0, &cp);
+                if (e == cudaSuccess) body_out = cp.conditional.phGraph_out[0];
+            }
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_in, body_out, 0, 0);
+            // outer body: residual check, decision, pass start, first inner
+            // decision, inner loop
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(cap, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                b_reset_ctl_kernel<<<1, 32, 0, cap>>>(w.ctl);
+                b_check_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.b, u,
+                                                    w.dinv, w.r64, w.pr, w.inst_cnt, w.ctl, w.part, o->tol);
+                b_decide_outer_kernel<<<1, 32, 0, cap>>>(w.ctl, w.loop, o->max_outer, stop, h_out);
+                md_load_kernel<<<gu, kBT, 0, cap>>>(w.units, pl.n_units, w.inst, R, w.r64, vr, vrh, vp, vv, w.pr,
+                                                    w.inst_cnt, w.inst_running, w.ctl, w.part, o->inner_tol,
+                                                    o->max_iter, w.loop);
+                b_decide_inner_kernel<<<1, 32, 0, cap>>>(w.ctl, w.loop, round_cap, stop, h_in);
+                cudaStreamCaptureStatus cs;
+                cudaGraph_t cg = nullptr;
+                const cudaGraphNode_t* deps = nullptr;
+                size_t nd = 0;
+                e = cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &nd);
+                if (e == cudaSuccess) {
+                    cudaGraphNodeParams cp{};
+                    cp.type = cudaGraphNodeTypeConditional;
+                    cp.conditional.handle = h_in;
+                    cp.conditional.type = cudaGraphCondTypeWhile;
+                    cp.conditional.size = 1;
+                    cudaGraphNode_t n_in;
+                    e = cudaGraphAddNode(&n_in, cg, deps, nullptr, nd, &cp);
+                    if (e == cudaSuccess) {
+                        body_in = cp.conditional.phGraph_out[0];
+                        e = cudaStreamUpdateCaptureDependencies(cap, &n_in, nullptr, 1,
+                                                                cudaStreamSetCaptureDependencies);
+                    }
+                }
+                cudaGraph_t got = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(cap, &got);
+                if (e == cudaSuccess) e = e2;
+            }
+            // inner body: one iteration, then the next inner decision
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(cap, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = capture_iteration(cap);
+                b_decide_inner_kernel<<<1, 32, 0, cap>>>(w.ctl, w.loop, round_cap, stop, h_in);
+                cudaGraph_t got = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(cap, &got);
+                if (e == cudaSuccess) e = e2;
+            }
         }
         if (e == cudaSuccess && rc == RBFFD_OK) e = cudaGraphInstantiate(&exec, graph, 0);
         cudaStreamDestroy(cap);
@@ -1195,7 +1318,7 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
             return -(rc != RBFFD_OK ? rc : (int)RBFFD_ERR_CUDA);
         }
     }
-    const int per_iter = 5 + vlaunch;
+    const int per_iter = 5 + vlaunch + (device_loop ? 1 : 0);  // + the inner decision on the device
     // algorithmic bytes of one iteration with every pair running (see the
     // profiling hooks in rbffd.h)
     int64_t nnz = 0;
@@ -1208,41 +1331,70 @@ int solve_mg(const Plan& pl, const BWork& w, const double* xy, const uint8_t* ma
         w.val, w.val32, nnz, w.val_lo);
     note_launches(1);
     clk.mark("iteration graph capture");
-    int rounds = 0, err = RBFFD_OK;
-    Ctl hc;
-    for (;;) {
-        if (cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st) != cudaSuccess) { err = RBFFD_ERR_CUDA; break; }
-        b_check_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.b, u, w.dinv,
-                                           w.r64, w.pr, w.inst_cnt, w.ctl, w.part, o->tol);
-        note_launches(1);
-        if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
+    int err = RBFFD_OK;
+    int rounds = 0;
+    bool timed_out = false;
+    if (device_loop) {
+        int hl[8] = {0};
+        if (cudaMemsetAsync(w.loop, 0, sizeof(int) * 8, st) != cudaSuccess) err = RBFFD_ERR_CUDA;
+        const int ev = prof_begin(st);
+        if (err == RBFFD_OK && cudaGraphLaunch(exec, st) != cudaSuccess) err = RBFFD_ERR_CUDA;
+        prof_end(ev, st, kProfBatchIter, 0);
+        if (err == RBFFD_OK && (cudaMemcpyAsync(hl, w.loop, sizeof(hl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                                cudaStreamSynchronize(st) != cudaSuccess))
             err = RBFFD_ERR_CUDA;
-            break;
-        }
-        if (hc.active == 0 || rounds >= o->max_outer) break;
-        ++rounds;
-        md_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, vr, vrh, vp, vv, w.pr, w.inst_cnt,
-                                           w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter);
-        note_launches(1);
-        for (int guard = 0; guard < 1 << 20; ++guard) {
+        rounds = hl[1];
+        const int iters = hl[2];
+        unsigned long long pair_iters = 0;
+        std::memcpy(&pair_iters, hl + 4, sizeof(pair_iters));
+        // the loop ran on the device: its time counts as `iters` iterations,
+        // bytes in proportion to the pairs that were in a pass
+        prof_commit_as(ev, iters, (int64_t)((double)iter_bytes * (double)pair_iters / (pl.n_inst * (double)R)));
+        note_launches((int)std::min<long long>((long long)iters * per_iter + rounds * 4LL, 1LL << 30));
+        if (err == RBFFD_OK && mg_batch_timed_out(mb, st, &timed_out) != RBFFD_OK) err = RBFFD_ERR_CUDA;
+    } else {
+        Ctl hc;
+        for (;;) {
+            if (cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st) != cudaSuccess) { err = RBFFD_ERR_CUDA; break; }
+            b_check_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, w.row_ptr, w.col, w.val, R, w.b, u,
+                                               w.dinv, w.r64, w.pr, w.inst_cnt, w.ctl, w.part, o->tol);
+            note_launches(1);
             if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) {
                 err = RBFFD_ERR_CUDA;
                 break;
             }
-            if (hc.running <= 0) break;
-            const int ev = prof_begin(st);
-            if (cudaGraphLaunch(exec, st) != cudaSuccess) {
-                err = RBFFD_ERR_CUDA;
-                break;
+            if (hc.active == 0 || rounds >= o->max_outer) break;
+            ++rounds;
+            md_load_kernel<<<gu, kBT, 0, st>>>(w.units, pl.n_units, w.inst, R, w.r64, vr, vrh, vp, vv, w.pr,
+                                               w.inst_cnt, w.inst_running, w.ctl, w.part, o->inner_tol, o->max_iter,
+                                               nullptr);
+            note_launches(1);
+            for (int guard = 0; guard < round_cap; ++guard) {
+                if (cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess) {
+                    err = RBFFD_ERR_CUDA;
+                    break;
+                }
+                if (hc.running <= 0) break;
+                const int ev = prof_begin(st);
+                if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+                    err = RBFFD_ERR_CUDA;
+                    break;
+                }
+                // bytes in proportion to the pairs still in a pass
+                prof_end(ev, st, kProfBatchIter,
+                         (int64_t)((double)iter_bytes * hc.running / (pl.n_inst * (double)R)));
+                note_launches(per_iter);
+                if (mb.persistent) {
+                    if (mg_batch_timed_out(mb, st, &timed_out) != RBFFD_OK) err = RBFFD_ERR_CUDA;
+                    if (err != RBFFD_OK || timed_out) break;
+                }
             }
-            // bytes in proportion to the pairs still in a pass
-            prof_end(ev, st, kProfBatchIter, (int64_t)((double)iter_bytes * hc.running / (pl.n_inst * (double)R)));
-            note_launches(per_iter);
+            if (err != RBFFD_OK || timed_out) break;
         }
-        if (err != RBFFD_OK) break;
     }
+    if (err == RBFFD_OK && timed_out) err = RBFFD_ERR_TIMEOUT;
     clk.mark("solve");
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);

@@ -77,6 +77,9 @@ void prof_collect();
 // After a synchronisation: accounts the first `keep` of `count` bracketed
 // launches and drops the rest (launches that returned without work).
 void prof_commit(const int* slots, int count, int keep);
+// After a synchronisation: accounts the bracketed launch `slot` (a graph
+// that looped on the device) as `count` launches of `bytes` in all.
+void prof_commit_as(int slot, int count, int64_t bytes);
 
 // ---------------------------------------------------------------- device --
 __device__ __forceinline__ double warp_sum(double v) {

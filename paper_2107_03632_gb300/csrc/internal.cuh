@@ -33,6 +33,7 @@ constexpr int kMgInterpM = 2;     // interpolation degree
 constexpr int kMgCoarseN = 12;    // coarse operator: stencil size
 constexpr int kMgCoarseM = 2;     //                  and degree
 constexpr uint32_t kMgMagic = 0x4D475242u;
+constexpr int kMgGalerkinRow = 256;  // Galerkin coarse operators: mean entries per row the layout holds
 
 struct MgLevel {
     int64_t N;
@@ -72,6 +73,7 @@ struct MgHierarchy {
     int has32;
     int col_base;  // level-0 column indices are offset by this (rows local)
     int transposed;  // built for A^T (rbffd_mg_setup_adjoint)
+    int galerkin;    // adjoint hierarchy with Galerkin coarse operators (rbffd_mg_galerkin_adjoint)
     double omega;
     MgLevel lv[RBFFD_MG_MAX_LEVELS];
 };
@@ -79,6 +81,7 @@ const MgHierarchy* mg_hierarchy(const rbffd_mg* h);
 int64_t mg_fine_rows(const MgHierarchy* h);
 bool mg_has_fp32(const MgHierarchy* h);
 bool mg_is_transposed(const MgHierarchy* h);
+bool mg_is_galerkin(const MgHierarchy* h);
 // Enqueues x = M^-1 b, one V-cycle (FP64, or float32 values and vectors when
 // fp32), on st; every kernel returns at once while *flag != 0.  With
 // profiling on and ev given, the finest-level sweeps are bracketed with
@@ -111,6 +114,11 @@ int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_
 // (rbffd_mg_adjoint_of).
 int mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg, void* ws,
                   size_t ws_bytes, cudaStream_t st);
+// The adjoint hierarchy of F with Galerkin coarse operators
+// (rbffd_mg_galerkin_adjoint) and its workspace.
+size_t mg_galerkin_workspace(const MgHierarchy& F);
+int mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg, void* ws,
+                        size_t ws_bytes, cudaStream_t st);
 
 // Coarse-level vectors of the multi-right-hand-side V-cycle (4 float
 // vectors of N_l x R per coarse level l).
@@ -122,15 +130,21 @@ size_t mg_multi_coarse_floats(const MgHierarchy* h, int R);
 // descriptors and row tiles.  Vectors are node-major [row][R] (R <= 64).
 struct MbLevel;
 struct MbUnit;
+struct MbTask;
 struct MgBatch {
     const MbLevel* desc;
     const MbUnit* units;
-    int levels, nu;
+    int levels, nu, persistent;
     // per level: units of the instances going deeper (a), of those whose
     // coarsest level it is (d), and of the next level's rows of the former (c)
     int a_off[RBFFD_MG_MAX_LEVELS], a_n[RBFFD_MG_MAX_LEVELS];
     int d_off[RBFFD_MG_MAX_LEVELS], d_n[RBFFD_MG_MAX_LEVELS];
     int c_off[RBFFD_MG_MAX_LEVELS], c_n[RBFFD_MG_MAX_LEVELS];
+    // the persistent mode's task queue for levels >= 1 and its counters
+    const MbTask* tasks;
+    int ntasks, ncount, coarse_grid;
+    int *head, *done, *status;
+    long long spin_limit;
 };
 // Device bytes of the tables for n_inst instances of total_nodes nodes.
 size_t mg_batch_table_bytes(int n_inst, int64_t total_nodes);
@@ -138,13 +152,19 @@ size_t mg_batch_table_bytes(int n_inst, int64_t total_nodes);
 // with col_base = node_off[i] on its block of the batched matrix; x0, t0,
 // r0: level-0 work vectors over all rows [N_total][R]; coarse +
 // coarse_off[i]: instance i's coarse-level vectors (mg_multi_coarse_floats).
+// persistent: levels >= 1 as one persistent launch from a task queue (else
+// one launch per level and operation); spin_limit: polls of its bounded
+// waits (0: the default); wait_test (tests only): the first coarse task
+// waits on a counter that nothing increments, so the wait runs out.
 int mg_batch_build(const MgHierarchy* const* H, const int64_t* node_off, int n_inst, int R, float* x0, float* t0,
                    float* r0, float* coarse, const size_t* coarse_off, void* tables, size_t table_bytes,
-                   cudaStream_t st, MgBatch* out);
+                   int persistent, long long spin_limit, int wait_test, cudaStream_t st, MgBatch* out);
 // x = M^-1 b for every instance and right-hand side, b and x double-float
 // pairs (the leading float is used; the result's trailing part is zero).
 // Units of instance i return at once while live[i] == 0.
 int mg_batch_apply_df(const MgBatch& B, int R, const float2* b, float2* x, const int* live, cudaStream_t st,
                       int* launches);
+// Whether a bounded wait of the persistent kernel ran out (synchronises st).
+int mg_batch_timed_out(const MgBatch& B, cudaStream_t st, bool* out);
 
 }  // namespace rbffd

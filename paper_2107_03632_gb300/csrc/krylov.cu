@@ -1302,7 +1302,7 @@ int solve_impl(const rbffd_csr* A, const rbffd_csr* A32, const double* b, double
     layout(ws, N, mixed, mg != nullptr, &w);
     w.mg = mg;
     w.mg32 = mg && mixed;
-    w.left = mg && adjoint;
+    w.left = mg && adjoint && !mg_is_galerkin(mg);
     std::memset(info, 0, sizeof(*info));
 
     KState hs;

@@ -487,8 +487,213 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
 }
 
 // ------------------------------------------------------------------- host --
+// ---- Galerkin coarse operators (adjoint hierarchy) -------------------------
+// A_{l+1} = R_l A_l P_l with R_l = P^T (the interpolation's transpose) and
+// P_l = (N_c / N_f) P without the columns of coarse Dirichlet nodes; the rows
+// of coarse Dirichlet nodes become identity rows (their columns are zero in
+// the product, so the coarse system stays block diagonal).  One warp per
+// coarse row c and two shared-memory hash tables (open addressing, linear
+// probing, keys -1 when empty): first D = R_c A_l keyed by fine column, then
+// the row C_c = D P_l keyed by coarse column.  Zero entries of R and P_l
+// (Dirichlet rows of P, the removed columns) are skipped alike in both
+// passes.  The counting pass stores each row's length; the filling pass
+// accumulates every key's terms in a fixed order (the entries of one A row,
+// or one P row, have distinct columns, so the lanes of a batch never share a
+// slot, and batches run in sequence; D is sorted by column before its rows
+// of P are read) and writes the row sorted by column, so the product does not
+// depend on thread timing.
+constexpr int kGalH1 = 1024;  // distinct fine columns of D per row (cap)
+constexpr int kGalH2 = 512;   // distinct coarse columns per row (cap)
+constexpr int kGalWarps = 4;
+constexpr size_t kGalSmem = (size_t)kGalWarps * (kGalH1 + kGalH2) * (sizeof(int) + sizeof(double));
+
+// Slot of `key` in a table of cap = mask + 1 slots (inserted if absent);
+// -1 when the table is full.  *fresh is set when this call inserted it.
+__device__ __forceinline__ int gal_slot(int* keys, unsigned mask, int key, int* fresh) {
+    unsigned h = ((unsigned)key * 2654435761u) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const int k = *(volatile int*)(keys + h);
+        if (k == key) return (int)h;
+        if (k == -1) {
+            const int old = atomicCAS(keys + h, -1, key);
+            if (old == -1) {
+                *fresh = 1;
+                return (int)h;
+            }
+            if (old == key) return (int)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Ascending sort of n <= cap (key, value) pairs held at the front of the
+// arrays, by one warp (bitonic network over the next power of two, padded
+// with INT_MAX keys).
+__device__ __forceinline__ void gal_sort(int* keys, double* vals, int n, int lane) {
+    int m = 32;
+    while (m < n) m <<= 1;
+    for (int i = n + lane; i < m; i += 32) keys[i] = 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < m; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const int a = keys[i], b = keys[p];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[p] = a;
+                        const double t = vals[i];
+                        vals[i] = vals[p];
+                        vals[p] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Moves the occupied slots of a table (cap slots) to its front, in slot
+// order; returns their count.  Every lane gets the count.
+__device__ __forceinline__ int gal_compact(int* keys, double* vals, int cap, int lane, bool with_vals) {
+    int n = 0;
+    for (int base = 0; base < cap; base += 32) {
+        const int i = base + lane;
+        const int k = keys[i];
+        const double v = with_vals ? vals[i] : 0.0;
+        const unsigned occ = __ballot_sync(0xffffffffu, k != -1);
+        __syncwarp();
+        if (k != -1) {
+            const int dst = n + __popc(occ & ((1u << lane) - 1u));
+            keys[dst] = k;
+            if (with_vals) vals[dst] = v;
+        }
+        n += __popc(occ);
+        __syncwarp();
+    }
+    return n;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
+    int64_t Nc, const int64_t* __restrict__ rrow, const int32_t* __restrict__ rcol, const double* __restrict__ rval,
+    const int64_t* __restrict__ arow, const int* __restrict__ acol, const double* __restrict__ aval,
+    const int32_t* __restrict__ pidx, const double* __restrict__ pval, const uint8_t* __restrict__ cmask,
+    int* __restrict__ count, const int64_t* __restrict__ crow, int* __restrict__ ccol, double* __restrict__ cval,
+    float* __restrict__ cval32, int* __restrict__ bad) {
+    extern __shared__ __align__(16) unsigned char gal_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* v1 = reinterpret_cast<double*>(gal_smem) + (size_t)wid * (kGalH1 + kGalH2);
+    double* v2 = v1 + kGalH1;
+    int* k1 = reinterpret_cast<int*>(reinterpret_cast<double*>(gal_smem) + (size_t)kGalWarps * (kGalH1 + kGalH2)) +
+              (size_t)wid * (kGalH1 + kGalH2);
+    int* k2 = k1 + kGalH1;
+    int overflow = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * kGalWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kGalWarps + wid; c < Nc; c += nwarps) {
+        if (cmask[c]) {
+            if (!FILL) {
+                if (lane == 0) count[c] = 1;
+            } else if (lane == 0) {
+                const int64_t o = crow[c];
+                ccol[o] = (int)c;
+                cval[o] = 1.0;
+                cval32[o] = 1.0f;
+            }
+            continue;
+        }
+        for (int i = lane; i < kGalH1; i += 32) {
+            k1[i] = -1;
+            if (FILL) v1[i] = 0.0;
+        }
+        for (int i = lane; i < kGalH2; i += 32) {
+            k2[i] = -1;
+            if (FILL) v2[i] = 0.0;
+        }
+        __syncwarp();
+        bool full = false;
+        // D = R_c A_l: one row of A_l per batch of lanes
+        for (int64_t e = rrow[c]; e < rrow[c + 1]; ++e) {
+            const double rv = rval[e];
+            if (rv == 0.0) continue;
+            const int f = rcol[e];
+            const int64_t a0 = arow[f], a1 = arow[f + 1];
+            for (int64_t b = a0; b < a1; b += 32) {
+                const int64_t k = b + lane;
+                if (k < a1) {
+                    int fresh = 0;
+                    const int sl = gal_slot(k1, kGalH1 - 1, acol[k], &fresh);
+                    if (sl < 0) full = true;
+                    else if (FILL) v1[sl] = fma(rv, aval[k], v1[sl]);
+                }
+                __syncwarp();
+            }
+        }
+        // D's entries at the front, sorted by column (the filling pass)
+        const int n1 = gal_compact(k1, v1, kGalH1, lane, FILL);
+        if (FILL) gal_sort(k1, v1, n1, lane);
+        // C_c = D P_l: two entries of D per batch, lanes 0-11 and 16-27; the
+        // keys go in together, the values in D's order
+        const int half = lane >> 4, j = lane & 15;
+        int n2 = 0;
+        for (int i = 0; i < n1; i += 2) {
+            const int di = i + half;
+            int sl = -1;
+            double term = 0.0;
+            if (di < n1 && j < kMgK) {
+                const int64_t pe = (int64_t)k1[di] * kMgK + j;
+                const double pv = pval[pe];
+                if (pv != 0.0) {
+                    int fresh = 0;
+                    sl = gal_slot(k2, kGalH2 - 1, pidx[pe], &fresh);
+                    n2 += fresh;
+                    if (sl < 0) full = true;
+                    if (FILL) term = v1[di] * pv;
+                }
+            }
+            __syncwarp();
+            if (FILL) {
+                if (half == 0 && sl >= 0) v2[sl] += term;
+                __syncwarp();
+                if (half == 1 && sl >= 0) v2[sl] += term;
+                __syncwarp();
+            }
+        }
+        if (__any_sync(0xffffffffu, full)) {
+            overflow = 1;
+            continue;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        if (!FILL) {
+            if (lane == 0) count[c] = n2;
+            continue;
+        }
+        const int m = gal_compact(k2, v2, kGalH2, lane, true);
+        gal_sort(k2, v2, m, lane);
+        const int64_t o = crow[c];
+        const int len = (int)min((int64_t)m, crow[c + 1] - o);  // (equal, by the counting pass)
+        for (int i = lane; i < len; i += 32) {
+            ccol[o + i] = k2[i];
+            cval[o + i] = v2[i];
+            cval32[o + i] = __double2float_rn(v2[i]);
+        }
+        __syncwarp();
+    }
+    if (overflow && lane == 0) atomicOr(bad, 2);
+}
+
+struct CountLoad64 {
+    const int* c;
+    __device__ int64_t operator()(int64_t i) const { return (int64_t)c[i]; }
+};
+
 int tpr_for(int64_t rows, int64_t nnz) {
     const double L = (double)nnz / (double)std::max<int64_t>(rows, 1);
+    if (L >= 80) return 8;  // (Galerkin coarse operators)
     if (L >= 40) return 4;
     if (L >= 8) return 2;
     return 1;
@@ -528,13 +733,17 @@ struct MgScratch {
     size_t tr_bytes;
     double* aug;
     int64_t* prow;
+    int64_t* sums64;  // tile sums of 64-bit scans
 };
 
 constexpr int kBoxParts = 64;
 
-// Carves the workspace; with ws == NULL only sizes it.
-size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
-    const std::vector<int64_t> nb = level_bounds(N);
+// Carves the workspace; with ws == NULL only sizes it.  Levels: the given
+// sizes (a built hierarchy's), else the upper bounds of level_bounds; the
+// operators of levels >= 1 hold `cap` entries per row.
+size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s, const std::vector<int64_t>* sizes = nullptr,
+                 int cap = kMgCoarseN) {
+    const std::vector<int64_t> nb = sizes ? *sizes : level_bounds(N);
     Carver c(ws);
     MgScratch t{};
     size_t knn_b = 0, asm_b = 0, tr_b = 0;
@@ -568,6 +777,7 @@ size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
     t.tr_ws = c.take<char>(tr_b);
     t.tr_bytes = tr_b;
     t.aug = c.take<double>((size_t)kMgCoarsest * 2 * kMgCoarsest);
+    t.sums64 = c.take<int64_t>(scan_tiles(N) + 1);
     MgHierarchy hh{};
     for (size_t l = 0; l < nb.size(); ++l) {
         const int64_t n = nb[l];
@@ -579,11 +789,11 @@ size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s) {
             L.mask = mk;
             int64_t* rp = c.take<int64_t>(n + 1);
             L.row_ptr = rp;
-            int* cl = c.take<int>((size_t)n * kMgCoarseN);
+            int* cl = c.take<int>((size_t)n * cap);
             L.col = cl;
-            double* v = c.take<double>((size_t)n * kMgCoarseN);
+            double* v = c.take<double>((size_t)n * cap);
             L.val = v;
-            float* v32 = c.take<float>((size_t)n * kMgCoarseN);
+            float* v32 = c.take<float>((size_t)n * cap);
             L.val32 = v32;
         }
         L.dinv = c.take<double>(n);
@@ -716,6 +926,7 @@ void jacobi(const MgLevel& L, const T* xi, const BT* b, OT* xo, const int* flag,
     const T* val = Sel<T>::val(L);
     const T* dinv = Sel<T>::dinv(L);
     switch (L.tpr) {
+        case 8: mg_jacobi_kernel<T, BT, OT, 8><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
         case 4: mg_jacobi_kernel<T, BT, OT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
         case 2: mg_jacobi_kernel<T, BT, OT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
         default: mg_jacobi_kernel<T, BT, OT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, xi, b, dinv, xo, flag); break;
@@ -727,6 +938,7 @@ void resid(const MgLevel& L, const T* x, const BT* b, T* r, const int* flag, cud
     const int g = blocks_for(L.N * L.tpr);
     const T* val = Sel<T>::val(L);
     switch (L.tpr) {
+        case 8: mg_resid_kernel<T, BT, 8><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
         case 4: mg_resid_kernel<T, BT, 4><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
         case 2: mg_resid_kernel<T, BT, 2><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
         default: mg_resid_kernel<T, BT, 1><<<g, kT, 0, st>>>(L.row_ptr, L.col, val, L.N, x, b, r, flag); break;
@@ -738,6 +950,7 @@ void restrict_to(const MgLevel& L, int64_t nc, const T* r, T* bc, const int* fla
     const int g = blocks_for(nc * L.rtpr);
     const T* val = Sel<T>::rval(L);
     switch (L.rtpr) {
+        case 8: mg_restrict_kernel<T, 8><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
         case 4: mg_restrict_kernel<T, 4><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
         case 2: mg_restrict_kernel<T, 2><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
         default: mg_restrict_kernel<T, 1><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
@@ -840,6 +1053,8 @@ int64_t mg_fine_rows(const MgHierarchy* h) { return h ? h->lv[0].N : 0; }
 bool mg_has_fp32(const MgHierarchy* h) { return h && h->has32; }
 
 bool mg_is_transposed(const MgHierarchy* h) { return h && h->transposed; }
+
+bool mg_is_galerkin(const MgHierarchy* h) { return h && h->galerkin; }
 
 int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int* flag, cudaStream_t st) {
     if (!h || !r || !y || h->col_base != 0) return RBFFD_ERR_INVALID_ARG;
@@ -944,6 +1159,29 @@ extern "C" int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, con
         return RBFFD_ERR_INVALID_ARG;
     return mg_adjoint_of(*F, AT, AT32 ? static_cast<const float*>(AT32->val) : nullptr, mg, ws, ws_bytes,
                          as_stream(stream));
+}
+
+extern "C" size_t rbffd_mg_galerkin_workspace_size(const rbffd_mg* fwd) {
+    RBFFD_NVTX("rbffd_mg_galerkin_workspace_size");
+    using namespace rbffd;
+    const MgHierarchy* F = mg_hierarchy(fwd);
+    if (!F || F->transposed) return 0;
+    return mg_galerkin_workspace(*F);
+}
+
+extern "C" int rbffd_mg_galerkin_adjoint(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_csr* AT32,
+                                         rbffd_mg* mg, void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_mg_galerkin_adjoint");
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    std::memset(mg, 0, sizeof(*mg));
+    const MgHierarchy* F = mg_hierarchy(fwd);
+    if (!F || !AT || !AT->row_ptr || !AT->col || !AT->val || AT->dtype != 0) return RBFFD_ERR_INVALID_ARG;
+    if (AT32 && (!AT32->val || AT32->dtype != 1 || AT32->n_rows != AT->n_rows || AT32->nnz != AT->nnz ||
+                 AT32->row_ptr != AT->row_ptr || AT32->col != AT->col))
+        return RBFFD_ERR_INVALID_ARG;
+    return mg_galerkin_adjoint(*F, AT, AT32 ? static_cast<const float*>(AT32->val) : nullptr, mg, ws, ws_bytes,
+                               as_stream(stream));
 }
 
 extern "C" int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x, void* stream) {
@@ -1079,6 +1317,138 @@ int rbffd::mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float*
     RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
     if (flags[0]) return RBFFD_ERR_SINGULAR_STENCIL;
+    h.n_levels = n_levels;
+    h.magic = kMgMagic;
+    std::memcpy(mg, &h, sizeof(h));
+    return RBFFD_OK;
+}
+
+// Level sizes of a built hierarchy (the Galerkin hierarchy's layout).
+static std::vector<int64_t> level_sizes(const rbffd::MgHierarchy& F) {
+    std::vector<int64_t> nb;
+    for (int l = 0; l < F.n_levels; ++l) nb.push_back(F.lv[l].N);
+    return nb;
+}
+
+size_t rbffd::mg_galerkin_workspace(const MgHierarchy& F) {
+    const std::vector<int64_t> nb = level_sizes(F);
+    return mg_layout(nullptr, F.lv[0].N, nullptr, nullptr, &nb, kMgGalerkinRow);
+}
+
+// The adjoint hierarchy of a built forward one with Galerkin coarse
+// operators: node sets, interpolation and transfers as in mg_adjoint_of
+// (restriction P^T, prolongation (N_c / N_f) P without the coarse Dirichlet
+// columns); each coarse operator the product R A P of the level above it
+// (mg_galerkin_kernel), its smoother weights from its own diagonal, the
+// coarsest inverted.
+int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const float* val32, rbffd_mg* mg,
+                               void* ws, size_t ws_bytes, cudaStream_t st) {
+    std::memset(mg, 0, sizeof(*mg));
+    const MgLevel& F0 = F.lv[0];
+    const int64_t N = F0.N;
+    if (F.transposed || F.col_base != 0 || AT->n_rows != N || AT->nnz != F0.nnz) return RBFFD_ERR_INVALID_ARG;
+    if (val32 && !F.has32) return RBFFD_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return RBFFD_ERR_WORKSPACE;
+    const std::vector<int64_t> nb = level_sizes(F);
+    if (ws_bytes < mg_layout(nullptr, N, nullptr, nullptr, &nb, kMgGalerkinRow)) return RBFFD_ERR_WORKSPACE;
+    static bool smem_set = false;
+    if (!smem_set) {
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kGalSmem));
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kGalSmem));
+        smem_set = true;
+    }
+    MgHierarchy h{};
+    MgScratch s{};
+    mg_layout(ws, N, &h, &s, &nb, kMgGalerkinRow);
+    h.nu = F.nu;
+    h.omega = F.omega;
+    h.has32 = val32 ? 1 : 0;
+    h.col_base = 0;
+    h.transposed = 1;
+    h.galerkin = 1;
+    RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
+    MgLevel& L0 = h.lv[0];
+    L0.N = N;
+    L0.row_ptr = AT->row_ptr;
+    L0.col = AT->col;
+    L0.val = static_cast<const double*>(AT->val);
+    L0.val32 = val32;
+    L0.nnz = AT->nnz;
+    L0.tpr = tpr_for(N, AT->nnz);
+    L0.xy = F0.xy;
+    L0.mask = F0.mask;
+    // level 0's smoother: A^T has A's diagonal and Dirichlet rows
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(L0.dinv, F0.dinv, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(L0.dinv32, F0.dinv32, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+    const int n_levels = F.n_levels;
+    const int gal_grid = std::max(1, sm_count() * 3);
+    for (int l = 0; l + 1 < n_levels; ++l) {
+        MgLevel& L = h.lv[l];
+        const MgLevel& FL = F.lv[l];
+        MgLevel& C = h.lv[l + 1];
+        const MgLevel& FC = F.lv[l + 1];
+        const int64_t nc = FC.N;
+        C.N = nc;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(C.xy), FC.xy, sizeof(double) * 2 * nc,
+                                       cudaMemcpyDeviceToDevice, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(const_cast<uint8_t*>(C.mask), FC.mask, nc, cudaMemcpyDeviceToDevice, st));
+        // transfers: R = P^T (raw), prolongation (N_c / N_f) P without the
+        // coarse Dirichlet columns
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.pidx, FL.pidx, sizeof(int32_t) * L.N * kMgK, cudaMemcpyDeviceToDevice, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(L.pval, FL.pval, sizeof(double) * L.N * kMgK, cudaMemcpyDeviceToDevice, st));
+        mg_ellrow_kernel<<<blocks_for(L.N + 1), kT, 0, st>>>(L.N, s.prow);
+        rbffd_csr P{};
+        P.n_rows = L.N;
+        P.nnz = L.N * kMgK;
+        P.row_ptr = s.prow;
+        P.col = L.pidx;
+        P.val = L.pval;
+        P.dtype = 0;
+        int rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, nullptr, s.tr_ws, s.tr_bytes, st);
+        if (rc != RBFFD_OK) return rc;
+        mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
+        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, (double)nc / (double)L.N,
+                                                                 L.pval, L.pval32);
+        note_launches(3);
+        RBFFD_LAUNCH_CHECK();
+        L.rtpr = tpr_for(nc, L.N * kMgK);
+        // C = R A P: row lengths, row pointer, entries
+        int* cnt = s.pos;
+        mg_galerkin_kernel<false><<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
+            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, nullptr, nullptr, nullptr,
+            nullptr, s.flags);
+        note_launches(1);
+        RBFFD_LAUNCH_CHECK();
+        int64_t* crow = const_cast<int64_t*>(C.row_ptr);
+        RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{cnt}, nc, crow, s.sums64, crow + nc, st));
+        int64_t cnnz = 0;
+        int flags[2] = {0, 0};
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnnz, crow + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        // a row wider than the tables, or more entries than the layout holds
+        if ((flags[0] & 2) || cnnz > nc * (int64_t)kMgGalerkinRow) return RBFFD_ERR_WORKSPACE;
+        mg_galerkin_kernel<true><<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
+            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, nullptr, crow,
+            const_cast<int*>(C.col), const_cast<double*>(C.val), const_cast<float*>(C.val32), s.flags);
+        C.nnz = cnnz;
+        C.tpr = tpr_for(nc, cnnz);
+        mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.mask, h.omega, C.dinv,
+                                                      C.dinv32, s.flags + 1);
+        note_launches(2);
+        RBFFD_LAUNCH_CHECK();
+    }
+    {
+        const int rc = dense_inverse(h.lv[n_levels - 1], 0, s, st);
+        if (rc != RBFFD_OK) return rc;
+    }
+    int flags[2] = {0, 0};
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags[0] & 2) return RBFFD_ERR_WORKSPACE;
+    if (flags[0] || flags[1]) return RBFFD_ERR_SINGULAR_STENCIL;
     h.n_levels = n_levels;
     h.magic = kMgMagic;
     std::memcpy(mg, &h, sizeof(h));

@@ -30,6 +30,8 @@ STATUS_NAMES = {
     6: "RBFFD_ERR_TIMEOUT",
     7: "RBFFD_ERR_WORKSPACE",
 }
+for _code, _name in STATUS_NAMES.items():
+    globals()[_name] = _code
 
 
 class RbffdError(RuntimeError):
@@ -120,6 +122,10 @@ class SolveOpts(ctypes.Structure):
         ("jacobi", ctypes.c_int32),
         ("precond", ctypes.c_int32),
         ("mg", ctypes.POINTER(MgHandle)),
+        ("spin_limit", ctypes.c_int64),
+        ("wait_test", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
+        ("device_loop", ctypes.c_int32),
     ]
 
 
@@ -209,6 +215,10 @@ SIGNATURES = {
     "rbffd_mg_adjoint_of": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
                                            ctypes.POINTER(MgHandle), ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
+    "rbffd_mg_galerkin_workspace_size": (_SZ, [ctypes.POINTER(MgHandle)]),
+    "rbffd_mg_galerkin_adjoint": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
+                                                 ctypes.POINTER(MgHandle), ctypes.c_void_p, ctypes.c_size_t,
+                                                 ctypes.c_void_p]),
     "rbffd_mg_apply": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "rbffd_diag_recip": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP]),
@@ -420,7 +430,8 @@ def make_opts(tol=1e-10, max_iter=200000, precision="fp64", inner_tol=None, max_
     prec = {"fp64": 0, "mixed": 1}[precision]
     if inner_tol is None:
         inner_tol = 1e-10 if mg is not None else (1e-5 if prec == 1 else 1e-3)
-    o = SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0, 0, None)
+    o = SolveOpts(float(tol), int(max_iter), prec, float(inner_tol), int(max_outer), 1 if jacobi else 0, 0, None,
+                  0, 0, 0, 0)
     if mg is not None:
         o.precond = 1
         o.mg = ctypes.pointer(mg.handle)
@@ -445,6 +456,7 @@ class Multigrid:
             ws = mg_workspace(N, A.nnz, xy.device)
         self.ws = ws
         self.adjoint = adjoint
+        self.galerkin = False
         self.setup(xy, is_dirichlet, A, nu, omega)
 
     def setup(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, A: "CsrMatrix", nu: int = 2, omega: float = 0.6):
@@ -467,17 +479,37 @@ class Multigrid:
         self.handle = MgHandle()
         self.ws = ws if ws is not None else mg_workspace(AT.n_rows, AT.nnz, AT.val.device)
         self.adjoint = True
+        self.galerkin = False
+        self.rebuild_from(fwd, AT)
+        return self
+
+    @classmethod
+    def galerkin_adjoint_of(cls, fwd: "Multigrid", AT: "CsrMatrix", ws: torch.Tensor | None = None) -> "Multigrid":
+        """The adjoint hierarchy of fwd with Galerkin coarse operators R A P
+        (rbffd_mg_galerkin_adjoint); rbffd_solve_adjoint runs it
+        right-preconditioned."""
+        self = cls.__new__(cls)
+        self.handle = MgHandle()
+        if ws is None:
+            nbytes = load().rbffd_mg_galerkin_workspace_size(ctypes.byref(fwd.handle))
+            if nbytes == 0:
+                raise RbffdError(1, "rbffd_mg_galerkin_workspace_size")
+            ws = _workspace(nbytes, AT.val.device)
+        self.ws = ws
+        self.adjoint = True
+        self.galerkin = True
         self.rebuild_from(fwd, AT)
         return self
 
     def rebuild_from(self, fwd: "Multigrid", AT: "CsrMatrix"):
-        """(Re)builds this adjoint hierarchy from fwd (rbffd_mg_adjoint_of)."""
+        """(Re)builds this adjoint hierarchy from fwd (rbffd_mg_adjoint_of, or
+        rbffd_mg_galerkin_adjoint for a Galerkin hierarchy)."""
         c64, c32 = AT.c64(), AT.c32()
         self.A = AT
-        _check(load().rbffd_mg_adjoint_of(ctypes.byref(fwd.handle), ctypes.byref(c64),
-                                          ctypes.byref(c32) if c32 is not None else None, ctypes.byref(self.handle),
-                                          _ptr(self.ws), self.ws.numel(), _stream(AT.val.device)),
-               "rbffd_mg_adjoint_of")
+        name = "rbffd_mg_galerkin_adjoint" if getattr(self, "galerkin", False) else "rbffd_mg_adjoint_of"
+        _check(getattr(load(), name)(ctypes.byref(fwd.handle), ctypes.byref(c64),
+                                     ctypes.byref(c32) if c32 is not None else None, ctypes.byref(self.handle),
+                                     _ptr(self.ws), self.ws.numel(), _stream(AT.val.device)), name)
 
     def levels(self) -> list:
         arr = (ctypes.c_int64 * MG_MAX_LEVELS)()

@@ -32,9 +32,18 @@ def _batch(specs, n_rhs, seed):
     return sizes, np.concatenate(nodes), np.concatenate(masks), np.concatenate(fs), np.concatenate(gs)
 
 
-@pytest.mark.parametrize("precond", [0, 1])
+# (precond, persistent, device_loop): the Jacobi mixed solver; per-instance
+# multigrid with one launch per (level, operation), host-driven iterations;
+# the same with the persistent coarse-level kernel; with the device-side
+# loop; with both.
+MODES = {"jacobi": (0, 0, 0), "mg": (1, 0, 0), "mg-persistent": (1, 1, 0), "mg-device-loop": (1, 0, 1),
+         "mg-persistent-device-loop": (1, 1, 1)}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("n_rhs", [1, 3, 64])
-def test_batched_vs_oracle(lib, n_rhs, precond):
+def test_batched_vs_oracle(lib, n_rhs, mode):
+    """Every solver mode against the oracle's direct solves, per (instance, rhs)."""
     from paper_2107_03632_gb300 import rbffd
 
     specs = [(0.06, 2, 12), (0.1, 6, 56), (0.07, 4, 30), (0.09, 2, 12), (0.08, 4, 30)]
@@ -43,7 +52,7 @@ def test_batched_vs_oracle(lib, n_rhs, precond):
     sizes, xy, mask, F, G = _batch(specs, n_rhs, 31)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
     opts = rbffd.make_opts(precision="mixed", tol=1e-10)
-    opts.precond = precond  # 1: per-instance multigrid, FP64 BiCGSTAB per pair
+    opts.precond, opts.persistent, opts.device_loop = MODES[mode]  # multigrid: FP64 BiCGSTAB per pair
     u, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G), opts=opts)
     u = u.cpu().numpy()
     assert st == 0 and all(i["status"] == 0 for i in infos)
@@ -103,4 +112,42 @@ def test_batched_multigrid_multilevel_vs_oracle(lib):
             err = np.abs(u[sl, k] - ref).max() / np.abs(ref).max()
             assert err <= 1e-8, (N, m, k, err)
         assert info["rel_residual"] <= 1e-10
+        off += N
+
+
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_batched_bounded_wait_times_out_and_the_context_survives(lib, device_loop):
+    """The persistent coarse-level kernel's waits are bounded: with its test
+    hook the first task waits on a counter that nothing increments, so after
+    spin_limit polls the kernel records a timeout, every block stops, and the
+    solve returns RBFFD_ERR_TIMEOUT (no fault, no hang).  A normal solve on the
+    same context afterwards matches the oracle."""
+    from paper_2107_03632_gb300 import rbffd
+
+    specs = [(0.03, 4, 30), (0.04, 2, 12)]  # multi-level instances (coarse tasks exist)
+    sizes, xy, mask, F, G = _batch(specs, 3, 47)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    opts = rbffd.make_opts(precision="mixed", tol=1e-10)
+    opts.precond = 1
+    opts.persistent = 1
+    opts.device_loop = device_loop
+    opts.spin_limit = 2000
+    opts.wait_test = 1
+    _, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G), opts=opts, raise_on_error=False)
+    assert st == rbffd.RBFFD_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    opts.wait_test = 0
+    opts.spin_limit = 0
+    u, infos, st = rbffd.rbffd_solve_batched(sizes, T(xy), T(mask), T(F), T(G), opts=opts)
+    assert st == 0 and all(i["status"] == 0 for i in infos)
+    u = u.cpu().numpy()
+    off = 0
+    for (N, m, n) in sizes:
+        sl = slice(off, off + N)
+        idx = oracle.knn(xy[sl], n)
+        w, _ = oracle.weights(xy[sl], idx, m)
+        rp, col, val = oracle.assemble(idx, w, mask[sl])
+        for k in range(3):
+            ref = oracle.solve_direct(rp, col, val, oracle.rhs(F[sl, k], G[sl, k], mask[sl]))
+            assert np.abs(u[sl, k] - ref).max() / np.abs(ref).max() <= 1e-8
         off += N

@@ -12,7 +12,7 @@
   own solution of its own system (tests/golden/full_size_*.txt, written by
   tests/golden/make_full_size_reference.py with oracle.solve_refined) at
   4096 sampled nodes, 1e-8 relative max-norm;
-* at 1M nodes, the differentiable solve (BASELINE's C5): the GPU adjoint
+* at 1M nodes, the differentiable solve: the GPU adjoint
   gradient of L = sum over interior nodes of (u - u*)^2 against the oracle's
   adjoint gradient at sampled nodes, and against central differences of L
   along 32 seeded directions of (f, g).
@@ -129,10 +129,12 @@ def test_full_size_solution_vs_oracle(case, precision):
     del A, b, mg, x
 
 
-def test_full_size_adjoint_gradient(case):
-    """C5 at 1M nodes: forward solve, misfit gradient, adjoint solve (the
-    benchmark's configuration) -- against the oracle's adjoint gradient at the
-    stored sampled nodes, and against central differences of L."""
+@pytest.mark.parametrize("hierarchy", ["transposed", "galerkin"])
+def test_full_size_adjoint_gradient(case, hierarchy):
+    """The differentiable solve at 1M nodes: forward solve, misfit gradient,
+    adjoint solve (with either adjoint hierarchy) -- against the oracle's
+    adjoint gradient at the stored sampled nodes, and (once) against central
+    differences of L."""
     from paper_2107_03632_gb300 import rbffd
 
     if case["name"] != "disk_1M_m4_n30":
@@ -142,7 +144,7 @@ def test_full_size_adjoint_gradient(case):
     A = rbffd.rbffd_assemble(case["idx"], case["w"], case["mask"], want_f32=True)
     AT = rbffd.rbffd_transpose(A, want_f32=True)
     mg = rbffd.Multigrid(case["xy"], case["mask"], A)
-    mga = rbffd.Multigrid.adjoint_of(mg, AT)
+    mga = (rbffd.Multigrid.galerkin_adjoint_of if hierarchy == "galerkin" else rbffd.Multigrid.adjoint_of)(mg, AT)
     opts = rbffd.make_opts(tol=1e-10, precision="mixed", mg=mg)
     fstar = fourier_sources(d.xy, 1, SEED + 1)[0]
     u, info = rbffd.rbffd_solve(A, rbffd.rbffd_rhs(T(case["f"]), T(case["g"]), case["mask"]), opts=opts)
@@ -156,9 +158,14 @@ def test_full_size_adjoint_gradient(case):
     scale = max(np.abs(gold["dLdf"][1]).max(), np.abs(gold["dLdg"][1]).max())
     ef = np.abs(gf[gold["dLdf"][0]] - gold["dLdf"][1]).max() / scale
     eg = np.abs(gg[gold["dLdg"][0]] - gold["dLdg"][1]).max() / scale
-    print(f"{case['name']}: adjoint ({info_a['iters']} iterations): dL/df {ef:.3e}, dL/dg {eg:.3e} against the oracle")
+    print(f"{case['name']}: adjoint ({hierarchy} hierarchy, {info_a['iters']} iterations): dL/df {ef:.3e}, "
+          f"dL/dg {eg:.3e} against the oracle")
     assert max(ef, eg) <= 1e-7, (ef, eg)
+    if hierarchy == "galerkin":
+        assert info_a["iters"] <= 20, info_a
     assert np.abs(ustar.cpu().numpy()[gold["ustar"][0]] - gold["ustar"][1]).max() <= 1e-8 * np.abs(gold["ustar"][1]).max()
+    if hierarchy != "galerkin":
+        return  # the central differences below check the gradient once
     # central differences of L along 32 seeded directions v = (v_f, v_g), |v|_inf = 1, eps = 1e-6 |theta|_inf.
     # L is quadratic in theta = (f, g): L(theta +- eps v) uses u(theta +- eps v) = u -+ ... = u +- z with
     # z = A^-1 (b(theta + eps v) - b(theta)) = eps A^-1 b(v_f, v_g), each z a GPU solve of its own right-hand
