@@ -177,6 +177,23 @@ SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorit
                    / 279652728.0}
 
 
+# DRAM traffic of the FP64 weight solve from one ncu capture of
+# weights_ns_kernel<128, NsF64> (four warps per stencil) at 1M nodes, m = 6,
+# n = 56: dram read + write per stencil (idx read, w written; the gathered
+# coordinates come from L2).  Valid only at that (n, m) and while the
+# kernel's sources are the ones captured.
+WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "50556dc05dfb5a0f", "n": 56, "m": 6,
+                       "bytes_per_node": (257.03552e6 + 405.814016e6) / 1001697.0}
+
+
+def weights_source_hash():
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2107_03632_gb300", "csrc")
+    seg = open(os.path.join(d, "weights.cu")).read() + open(os.path.join(d, "common.cuh")).read()
+    return hashlib.sha256(seg.encode()).hexdigest()[:16]
+
+
 def spmv_df_source_hash():
     import hashlib
 
@@ -266,7 +283,12 @@ def weights_roofline(kernel_name: str, n: int, m: int, N: int, ms: float, extra:
                "achieved": f64_equiv, "peak": FP64_PEAK_TFLOPS_UNITS, "unit": "TFLOP/s",
                "frac": f64_equiv / FP64_PEAK_TFLOPS_UNITS,
                "peak_kind": "FP64 units x max clock (152 SMs x 2 FMA/clk x 2070 MHz)"}
-    out.update({"traffic": None, "flops_per_node": fl, "ms_per_launch": ms, "launches": 1})
+    traffic = None
+    t = WEIGHTS_F64_TRAFFIC
+    if "df" not in kernel_name and (n, m) == (t["n"], t["m"]) and weights_source_hash() == t["source_sha256_16"]:
+        traffic = t["bytes_per_node"] * N
+    out.update({"traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write, scaled by N)",
+                "flops_per_node": fl, "ms_per_launch": ms, "launches": 1})
     out.update(extra)
     return out
 

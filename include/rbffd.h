@@ -330,14 +330,16 @@ int rbffd_mg_adjoint_of(const rbffd_mg* fwd, const rbffd_csr* AT, const rbffd_cs
 /* at coarse Dirichlet nodes replaced by identity rows, its columns sorted; */
 /* smoother weights from its own diagonal; the coarsest inverted.  The      */
 /* product is computed on the device in a fixed summation order (the same   */
-/* bits on every run).  rbffd_solve_adjoint runs with such a hierarchy       */
+/* bits on every run: rows are staged, then placed in CSR order).           */
+/* rbffd_solve_adjoint runs with such a hierarchy                            */
 /* RIGHT-preconditioned on the whole system: M = the cycle followed by the  */
 /* Dirichlet back substitution, from x_b = b_b - L_ib^T x_i, so A^T M is    */
 /* block diagonal with an identity Dirichlet block.                         */
 /*   AT, AT32 : as for rbffd_mg_adjoint_of.                                  */
 /*   ws       : rbffd_mg_galerkin_workspace_size(fwd) bytes: the layout of   */
 /*              rbffd_mg_adjoint_of with room for 256 entries per coarse row */
-/*              on average (0 if fwd is not a built forward hierarchy).      */
+/*              on average, plus as much staging room for the largest coarse */
+/*              level (0 if fwd is not a built forward hierarchy).           */
 /* Synchronises `stream`.  Errors: RBFFD_ERR_INVALID_ARG (as                 */
 /* rbffd_mg_adjoint_of), RBFFD_ERR_WORKSPACE (ws too small; or a coarse row  */
 /* with more than 512 entries, or one with more than 1024 distinct columns  */

@@ -495,13 +495,14 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
 // coarse row c and two shared-memory hash tables (open addressing, linear
 // probing, keys -1 when empty): first D = R_c A_l keyed by fine column, then
 // the row C_c = D P_l keyed by coarse column.  Zero entries of R and P_l
-// (Dirichlet rows of P, the removed columns) are skipped alike in both
-// passes.  The counting pass stores each row's length; the filling pass
-// accumulates every key's terms in a fixed order (the entries of one A row,
-// or one P row, have distinct columns, so the lanes of a batch never share a
-// slot, and batches run in sequence; D is sorted by column before its rows
-// of P are read) and writes the row sorted by column, so the product does not
-// depend on thread timing.
+// (Dirichlet rows of P, the removed columns) are skipped.  Every key's terms
+// are summed in a fixed order (the entries of one A row, or one P row, have
+// distinct columns, so the lanes of a batch never share a slot, and batches
+// run in sequence; D is sorted by column before its rows of P are read), and
+// the row is sorted by column and staged at a place taken from an atomic
+// counter; after a scan of the row lengths a second kernel copies each row
+// to its CSR position.  The product therefore does not depend on thread
+// timing.
 constexpr int kGalH1 = 1024;  // distinct fine columns of D per row (cap)
 constexpr int kGalH2 = 512;   // distinct coarse columns per row (cap)
 constexpr int kGalWarps = 4;
@@ -577,13 +578,12 @@ __device__ __forceinline__ int gal_compact(int* keys, double* vals, int cap, int
     return n;
 }
 
-template <bool FILL>
 __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
     int64_t Nc, const int64_t* __restrict__ rrow, const int32_t* __restrict__ rcol, const double* __restrict__ rval,
     const int64_t* __restrict__ arow, const int* __restrict__ acol, const double* __restrict__ aval,
     const int32_t* __restrict__ pidx, const double* __restrict__ pval, const uint8_t* __restrict__ cmask,
-    int* __restrict__ count, const int64_t* __restrict__ crow, int* __restrict__ ccol, double* __restrict__ cval,
-    float* __restrict__ cval32, int* __restrict__ bad) {
+    int* __restrict__ count, int64_t* __restrict__ start, unsigned long long* __restrict__ total, int64_t cap,
+    int* __restrict__ tcol, double* __restrict__ tval, int* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned char gal_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* v1 = reinterpret_cast<double*>(gal_smem) + (size_t)wid * (kGalH1 + kGalH2);
@@ -594,96 +594,112 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
     int overflow = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kGalWarps;
     for (int64_t c = (int64_t)blockIdx.x * kGalWarps + wid; c < Nc; c += nwarps) {
+        int m = 1;
         if (cmask[c]) {
-            if (!FILL) {
-                if (lane == 0) count[c] = 1;
-            } else if (lane == 0) {
-                const int64_t o = crow[c];
-                ccol[o] = (int)c;
-                cval[o] = 1.0;
-                cval32[o] = 1.0f;
+            if (lane == 0) {  // an identity row
+                k2[0] = (int)c;
+                v2[0] = 1.0;
             }
-            continue;
-        }
-        for (int i = lane; i < kGalH1; i += 32) {
-            k1[i] = -1;
-            if (FILL) v1[i] = 0.0;
-        }
-        for (int i = lane; i < kGalH2; i += 32) {
-            k2[i] = -1;
-            if (FILL) v2[i] = 0.0;
-        }
-        __syncwarp();
-        bool full = false;
-        // D = R_c A_l: one row of A_l per batch of lanes
-        for (int64_t e = rrow[c]; e < rrow[c + 1]; ++e) {
-            const double rv = rval[e];
-            if (rv == 0.0) continue;
-            const int f = rcol[e];
-            const int64_t a0 = arow[f], a1 = arow[f + 1];
-            for (int64_t b = a0; b < a1; b += 32) {
-                const int64_t k = b + lane;
-                if (k < a1) {
-                    int fresh = 0;
-                    const int sl = gal_slot(k1, kGalH1 - 1, acol[k], &fresh);
-                    if (sl < 0) full = true;
-                    else if (FILL) v1[sl] = fma(rv, aval[k], v1[sl]);
-                }
-                __syncwarp();
+        } else {
+            for (int i = lane; i < kGalH1; i += 32) {
+                k1[i] = -1;
+                v1[i] = 0.0;
             }
-        }
-        // D's entries at the front, sorted by column (the filling pass)
-        const int n1 = gal_compact(k1, v1, kGalH1, lane, FILL);
-        if (FILL) gal_sort(k1, v1, n1, lane);
-        // C_c = D P_l: two entries of D per batch, lanes 0-11 and 16-27; the
-        // keys go in together, the values in D's order
-        const int half = lane >> 4, j = lane & 15;
-        int n2 = 0;
-        for (int i = 0; i < n1; i += 2) {
-            const int di = i + half;
-            int sl = -1;
-            double term = 0.0;
-            if (di < n1 && j < kMgK) {
-                const int64_t pe = (int64_t)k1[di] * kMgK + j;
-                const double pv = pval[pe];
-                if (pv != 0.0) {
-                    int fresh = 0;
-                    sl = gal_slot(k2, kGalH2 - 1, pidx[pe], &fresh);
-                    n2 += fresh;
-                    if (sl < 0) full = true;
-                    if (FILL) term = v1[di] * pv;
-                }
+            for (int i = lane; i < kGalH2; i += 32) {
+                k2[i] = -1;
+                v2[i] = 0.0;
             }
             __syncwarp();
-            if (FILL) {
+            bool full = false;
+            // D = R_c A_l: one row of A_l per batch of lanes
+            for (int64_t e = rrow[c]; e < rrow[c + 1]; ++e) {
+                const double rv = rval[e];
+                if (rv == 0.0) continue;
+                const int f = rcol[e];
+                const int64_t a0 = arow[f], a1 = arow[f + 1];
+                for (int64_t b = a0; b < a1; b += 32) {
+                    const int64_t k = b + lane;
+                    if (k < a1) {
+                        int fresh = 0;
+                        const int sl = gal_slot(k1, kGalH1 - 1, acol[k], &fresh);
+                        if (sl < 0) full = true;
+                        else v1[sl] = fma(rv, aval[k], v1[sl]);
+                    }
+                    __syncwarp();
+                }
+            }
+            // D's entries at the front, sorted by column
+            const int n1 = gal_compact(k1, v1, kGalH1, lane, true);
+            gal_sort(k1, v1, n1, lane);
+            // C_c = D P_l: two entries of D per batch, lanes 0-11 and 16-27;
+            // the keys go in together, the values in D's order
+            const int half = lane >> 4, j = lane & 15;
+            for (int i = 0; i < n1; i += 2) {
+                const int di = i + half;
+                int sl = -1;
+                double term = 0.0;
+                if (di < n1 && j < kMgK) {
+                    const int64_t pe = (int64_t)k1[di] * kMgK + j;
+                    const double pv = pval[pe];
+                    if (pv != 0.0) {
+                        int fresh = 0;
+                        sl = gal_slot(k2, kGalH2 - 1, pidx[pe], &fresh);
+                        if (sl < 0) full = true;
+                        term = v1[di] * pv;
+                    }
+                }
+                __syncwarp();
                 if (half == 0 && sl >= 0) v2[sl] += term;
                 __syncwarp();
                 if (half == 1 && sl >= 0) v2[sl] += term;
                 __syncwarp();
             }
+            if (__any_sync(0xffffffffu, full)) {
+                overflow = 1;
+                continue;
+            }
+            m = gal_compact(k2, v2, kGalH2, lane, true);
+            gal_sort(k2, v2, m, lane);
         }
-        if (__any_sync(0xffffffffu, full)) {
+        // stage the row (any free place: the copy below puts rows in order)
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(total, (unsigned long long)m);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if ((int64_t)pos + m > cap) {
             overflow = 1;
             continue;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-        if (!FILL) {
-            if (lane == 0) count[c] = n2;
-            continue;
+        for (int i = lane; i < m; i += 32) {
+            tcol[pos + i] = k2[i];
+            tval[pos + i] = v2[i];
         }
-        const int m = gal_compact(k2, v2, kGalH2, lane, true);
-        gal_sort(k2, v2, m, lane);
-        const int64_t o = crow[c];
-        const int len = (int)min((int64_t)m, crow[c + 1] - o);  // (equal, by the counting pass)
-        for (int i = lane; i < len; i += 32) {
-            ccol[o + i] = k2[i];
-            cval[o + i] = v2[i];
-            cval32[o + i] = __double2float_rn(v2[i]);
+        if (lane == 0) {
+            count[c] = m;
+            start[c] = (int64_t)pos;
         }
         __syncwarp();
     }
     if (overflow && lane == 0) atomicOr(bad, 2);
+}
+
+// The staged rows into the level's CSR (row c at crow[c]), with the float copy.
+__global__ void __launch_bounds__(kT) mg_galerkin_place_kernel(int64_t Nc, const int64_t* __restrict__ start,
+                                                               const int64_t* __restrict__ crow,
+                                                               const int* __restrict__ tcol,
+                                                               const double* __restrict__ tval,
+                                                               int* __restrict__ ccol, double* __restrict__ cval,
+                                                               float* __restrict__ cval32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < Nc; c += nw) {
+        const int64_t o = crow[c], len = crow[c + 1] - o, s = start[c];
+        for (int64_t i = lane; i < len; i += 32) {
+            const double v = tval[s + i];
+            ccol[o + i] = tcol[s + i];
+            cval[o + i] = v;
+            cval32[o + i] = __double2float_rn(v);
+        }
+    }
 }
 
 struct CountLoad64 {
@@ -734,6 +750,13 @@ struct MgScratch {
     double* aug;
     int64_t* prow;
     int64_t* sums64;  // tile sums of 64-bit scans
+    // Galerkin products: rows staged before their CSR placement (capacity
+    // gal_cap entries), per-row staging offsets, the staging counter
+    int* gal_col;
+    double* gal_val;
+    int64_t* gal_start;
+    unsigned long long* gal_total;
+    int64_t gal_cap;
 };
 
 constexpr int kBoxParts = 64;
@@ -778,6 +801,13 @@ size_t mg_layout(void* ws, int64_t N, MgHierarchy* h, MgScratch* s, const std::v
     t.tr_bytes = tr_b;
     t.aug = c.take<double>((size_t)kMgCoarsest * 2 * kMgCoarsest);
     t.sums64 = c.take<int64_t>(scan_tiles(N) + 1);
+    if (cap > kMgCoarseN && nb.size() > 1) {
+        t.gal_cap = nb[1] * (int64_t)cap;
+        t.gal_col = c.take<int>((size_t)t.gal_cap);
+        t.gal_val = c.take<double>((size_t)t.gal_cap);
+        t.gal_start = c.take<int64_t>(nb[1]);
+        t.gal_total = c.take<unsigned long long>(1);
+    }
     MgHierarchy hh{};
     for (size_t l = 0; l < nb.size(); ++l) {
         const int64_t n = nb[l];
@@ -1353,9 +1383,7 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
     if (ws_bytes < mg_layout(nullptr, N, nullptr, nullptr, &nb, kMgGalerkinRow)) return RBFFD_ERR_WORKSPACE;
     static bool smem_set = false;
     if (!smem_set) {
-        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kGalSmem));
-        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)kGalSmem));
         smem_set = true;
     }
@@ -1414,11 +1442,12 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
         note_launches(3);
         RBFFD_LAUNCH_CHECK();
         L.rtpr = tpr_for(nc, L.N * kMgK);
-        // C = R A P: row lengths, row pointer, entries
+        // C = R A P: rows staged, row pointer, rows placed
         int* cnt = s.pos;
-        mg_galerkin_kernel<false><<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
-            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, nullptr, nullptr, nullptr,
-            nullptr, s.flags);
+        RBFFD_CUDA_TRY(cudaMemsetAsync(s.gal_total, 0, sizeof(unsigned long long), st));
+        mg_galerkin_kernel<<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
+            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
+            s.gal_total, std::min(s.gal_cap, nc * (int64_t)kMgGalerkinRow), s.gal_col, s.gal_val, s.flags);
         note_launches(1);
         RBFFD_LAUNCH_CHECK();
         int64_t* crow = const_cast<int64_t*>(C.row_ptr);
@@ -1430,9 +1459,10 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
         RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
         // a row wider than the tables, or more entries than the layout holds
         if ((flags[0] & 2) || cnnz > nc * (int64_t)kMgGalerkinRow) return RBFFD_ERR_WORKSPACE;
-        mg_galerkin_kernel<true><<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
-            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, nullptr, crow,
-            const_cast<int*>(C.col), const_cast<double*>(C.val), const_cast<float*>(C.val32), s.flags);
+        mg_galerkin_place_kernel<<<blocks_for(nc * 32), kT, 0, st>>>(nc, s.gal_start, crow, s.gal_col, s.gal_val,
+                                                                     const_cast<int*>(C.col),
+                                                                     const_cast<double*>(C.val),
+                                                                     const_cast<float*>(C.val32));
         C.nnz = cnnz;
         C.tpr = tpr_for(nc, cnnz);
         mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.mask, h.omega, C.dinv,
