@@ -53,7 +53,7 @@ typedef enum rbffd_status {
     RBFFD_ERR_INVALID_ARG = 1,      /* bad size, null pointer, unsupported m/n */
     RBFFD_ERR_CUDA = 2,             /* a CUDA call or launch failed */
     RBFFD_ERR_SINGULAR_STENCIL = 3, /* reported per node in node_status */
-    RBFFD_ERR_NOT_CONVERGED = 4,    /* iteration cap reached */
+    RBFFD_ERR_NOT_CONVERGED = 4,    /* iteration cap reached, or the residual stagnated */
     RBFFD_ERR_BREAKDOWN = 5,        /* BiCGSTAB breakdown persisted after a restart */
     RBFFD_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
     RBFFD_ERR_WORKSPACE = 7         /* workspace too small or misaligned */
@@ -408,7 +408,12 @@ int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x,
 /* start).  The call BLOCKS the host until the solve ends and synchronises   */
 /* `stream`; *info (host) receives the outcome.  A breakdown (rho or omega  */
 /* zero or non-finite) restarts once from the true residual before           */
-/* RBFFD_ERR_BREAKDOWN is returned.                                          */
+/* RBFFD_ERR_BREAKDOWN is returned.  Stagnation ends the solve early with   */
+/* RBFFD_ERR_NOT_CONVERGED: the relative residual (explicit between passes, */
+/* the recurrence estimate inside a pass) must halve at least once per      */
+/* max(2000, k) iterations, k being the iteration count at its last halving */
+/* (operators with spurious modes, e.g. stencils barely larger than the    */
+/* polynomial space, otherwise ran to max_iter).                            */
 /* ------------------------------------------------------------------------ */
 typedef struct rbffd_solve_opts {
     double tol;          /* relative residual target, e.g. 1e-10 */

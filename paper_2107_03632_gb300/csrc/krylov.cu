@@ -993,12 +993,41 @@ struct ChunkPlan {
     }
 };
 
-// Runs chunks of iterations until the state leaves kRunning; returns the
-// flag, or minus a status on a CUDA error.  With profiling on, only the SpMV
-// launches of iterations that ran are accounted (launches after the pass
-// ended return at once and are dropped).
+// Stagnation: the relative residual must halve at least once per
+// max(kStagMin, its age) iterations, its age being the iteration count at
+// which it last halved; a solve that goes longer without halving stops with
+// RBFFD_ERR_NOT_CONVERGED (a converging solve halves its residual steadily,
+// every few iterations with multigrid, every few hundred with Jacobi
+// scaling at millions of nodes; operators with spurious modes, e.g. stencils
+// barely larger than the polynomial space, stall and otherwise ran to
+// max_iter).  Observed at every explicit residual and, inside a pass, from
+// the recurrence residual at each chunk boundary.
+constexpr long long kStagMin = 2000;
+struct StagMonitor {
+    double anchor = -1.0;  // relative residual at the last halving
+    long long at = 0;      // iteration count then
+    bool stalled = false;
+    void observe(double rel, long long it) {
+        if (!(rel >= 0.0) || !std::isfinite(rel)) return;
+        if (anchor < 0.0 || rel <= 0.5 * anchor) {
+            anchor = rel;
+            at = it;
+            return;
+        }
+        if (it - at > std::max(kStagMin, at)) stalled = true;
+    }
+};
+
+// Runs chunks of iterations until the state leaves kRunning (or, with a
+// monitor, until it reports stagnation; the state then stays kRunning and
+// the next pass restarts it); returns the flag, or minus a status on a CUDA
+// error.  rel_start: the relative residual at the pass start, it_base: the
+// iterations before this pass.  With profiling on, only the SpMV launches of
+// iterations that ran are accounted (launches after the pass ended return at
+// once and are dropped).
 template <class IterFn>
-int run_chunks(const Work& w, KState* hs, cudaStream_t st, ChunkPlan& plan, IterFn iter) {
+int run_chunks(const Work& w, KState* hs, cudaStream_t st, ChunkPlan& plan, IterFn iter, StagMonitor* mon = nullptr,
+               double rel_start = 0.0, long long it_base = 0) {
     std::vector<int> ev;
     const double start2 = hs->rnorm2;
     plan.start(start2, std::max(hs->tol2, hs->repl2 * hs->rmax2));
@@ -1016,6 +1045,10 @@ int run_chunks(const Work& w, KState* hs, cudaStream_t st, ChunkPlan& plan, Iter
         const int per_iter = chunk > 0 ? (int)ev.size() / chunk : 0;
         if (profiling()) prof_commit(ev.data(), (int)ev.size(), per_iter * (hs->iter - before));
         plan.update(*hs, start2, hs->iter - before, ms);
+        if (mon && start2 > 0.0 && hs->flag == kRunning) {
+            mon->observe(rel_start * std::sqrt(hs->rnorm2 / start2), it_base + hs->iter);
+            if (mon->stalled) break;
+        }
     }
     return hs->flag;
 }
@@ -1082,6 +1115,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
     PassGuard g;
+    StagMonitor mon;
     bool rnd = shadow_random();
     // Multigrid, forward: start from x_b = b_b on the Dirichlet (identity)
     // rows, so that every residual is zero there.  The right-preconditioned
@@ -1110,7 +1144,7 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
         if (passes > 0 && !(hs.sres2 <= g.prev)) {
             // the pass made things worse: undo it and retry with a shorter pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            const bool retry = g.reject() || g.switch_shadow(rnd);
+            const bool retry = !mon.stalled && (g.reject() || g.switch_shadow(rnd));
             if (trace_on()) fprintf(stderr, "[rbffd fp64] pass undone, %s\n", retry ? "retry" : "stop");
             if (!retry) {
                 resid64(tpr, kCheck, A, b, x, w, w.r, o.tol, 0, 0.0, st);
@@ -1137,6 +1171,11 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
             status = RBFFD_ERR_BREAKDOWN;
             break;
         }
+        mon.observe(rel, total);
+        if (mon.stalled) {
+            if (trace_on()) fprintf(stderr, "[rbffd fp64] stagnation after %d iterations, rel %.3e\n", total, rel);
+            break;
+        }
         if (total >= o.max_iter || passes >= o.max_outer) break;
         ++passes;
         g.prev = hs.sres2;
@@ -1153,7 +1192,8 @@ int solve_fp64(const rbffd_csr& A, const double* b, double* x, const rbffd_solve
             RBFFD_LAUNCH_CHECK();
             if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
         }
-        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); });
+        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter64(tpr, A, x, w, st, ev); },
+                                 &mon, rel, total);
         if (f < 0) return -f;
         if (w.left && (rc = mg_dirichlet_fix(w.mg, b, x, nullptr, st)) != RBFFD_OK) return rc;
         total += hs.iter;
@@ -1195,6 +1235,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
     int status = RBFFD_ERR_NOT_CONVERGED;
     double rel = INFINITY;
     PassGuard g;
+    StagMonitor mon;
     bool rnd = shadow_random();
     while (true) {
         resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
@@ -1203,7 +1244,7 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         if (outer > 0 && !(hs.sres2 <= g.prev)) {
             // the correction made things worse: undo it, shorter next pass
             RBFFD_CUDA_TRY(cudaMemcpyAsync(x, w.x_save, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-            const bool retry = g.reject() || g.switch_shadow(rnd);
+            const bool retry = !mon.stalled && (g.reject() || g.switch_shadow(rnd));
             if (trace_on()) fprintf(stderr, "[rbffd mixed] pass undone, %s\n", retry ? "retry" : "stop");
             if (!retry) {
                 resid64(tpr64, kCheck, A, b, x, w, w.r64, o.tol, 0, 0.0, st);
@@ -1230,6 +1271,11 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
             status = RBFFD_ERR_BREAKDOWN;
             break;
         }
+        mon.observe(rel, total);
+        if (mon.stalled) {
+            if (trace_on()) fprintf(stderr, "[rbffd mixed] stagnation after %d iterations, rel %.3e\n", total, rel);
+            break;
+        }
         if (total >= o.max_iter || outer >= o.max_outer) break;
         ++outer;
         g.prev = hs.sres2;
@@ -1244,7 +1290,8 @@ int solve_mixed(const rbffd_csr& A, const rbffd_csr& A32, const double* b, doubl
         RBFFD_LAUNCH_CHECK();
         if ((rc = read_state(w, &hs, st)) != RBFFD_OK) return rc;
         const double start2 = hs.rmax2;
-        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter_df(tpr32, A32, w, st, ev); });
+        const int f = run_chunks(w, &hs, st, chunk, [&](std::vector<int>& ev) { iter_df(tpr32, A32, w, st, ev); },
+                                 &mon, rel, total);
         if (f < 0) return -f;
         total += hs.iter;
         if (trace_on())

@@ -381,3 +381,23 @@ def test_mg_adjoint_of_forward_equals_adjoint_setup(lib):
     # the forward hierarchy may be rebuilt afterwards: m2 owns its arrays
     mg.setup(xy, mask, A)
     assert torch.equal(m1.apply(r), m2.apply(r))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("use_mg", [True, False])
+def test_solver_stops_on_stagnation(lib, precision, use_mg):
+    """Unisolvent stencils (m = 4, n = s = 15) give an operator with spurious
+    modes on which BiCGSTAB stalls: the solve must give up early
+    (RBFFD_ERR_NOT_CONVERGED after a few thousand iterations, not max_iter),
+    and report the residual it reached."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, xy, mask, A = _gpu_system(0.01, 4, 15)
+    _, f, g = manufactured(d.xy)
+    b = rbffd.rbffd_rhs(T(f), T(g), mask)
+    mg = rbffd.Multigrid(xy, mask, A) if use_mg else None
+    x, info = rbffd.rbffd_solve(A, b, opts=rbffd.make_opts(tol=1e-10, precision=precision, mg=mg, max_iter=200000),
+                                raise_on_error=False)
+    assert info["status_code"] == 4, info
+    assert info["iters"] <= 5000, info
+    assert np.isfinite(info["rel_residual"]) and info["rel_residual"] > 1e-10
