@@ -159,8 +159,9 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* Gaussian elimination.                                                     */
 /* rbffd_weights_autotune times every candidate of the given precision      */
 /* (RBFFD_WEIGHTS_FP64: kernels 0-3; RBFFD_WEIGHTS_DF: 4-6; _ANY: all) that  */
-/* fits in shared memory on the first min(N, 128 x SMs) stencils of the     */
-/* given set (3 launches each after one warm-up, CUDA events), records the  */
+/* fits in shared memory on the first min(N, 512 x SMs) stencils of the     */
+/* given set (the fastest of 3 launches after one warm-up, CUDA events),    */
+/* records the                                                               */
 /* fastest for (current device, n, m) in a process-wide table that          */
 /* rbffd_weights and rbffd_solve_batched then use, and returns it in *best   */
 /* (may be NULL).  w and node_status serve as its scratch (their first rows */

@@ -503,10 +503,14 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
 // counter; after a scan of the row lengths a second kernel copies each row
 // to its CSR position.  The product therefore does not depend on thread
 // timing.
-constexpr int kGalH1 = 1024;  // distinct fine columns of D per row (cap)
-constexpr int kGalH2 = 512;   // distinct coarse columns per row (cap)
+// Two table sizes: (512, 256) slots first, four warps per block, 9 KB of
+// tables per warp (24 warps per SM); a level whose rows overflow them is
+// redone with (1024, 512), 18 KB per warp (12 warps per SM).
 constexpr int kGalWarps = 4;
-constexpr size_t kGalSmem = (size_t)kGalWarps * (kGalH1 + kGalH2) * (sizeof(int) + sizeof(double));
+template <int H1, int H2>
+constexpr size_t gal_smem_bytes() {
+    return (size_t)kGalWarps * (H1 + H2) * (sizeof(int) + sizeof(double));
+}
 
 // Slot of `key` in a table of cap = mask + 1 slots (inserted if absent);
 // -1 when the table is full.  *fresh is set when this call inserted it.
@@ -578,6 +582,7 @@ __device__ __forceinline__ int gal_compact(int* keys, double* vals, int cap, int
     return n;
 }
 
+template <int kGalH1, int kGalH2>
 __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
     int64_t Nc, const int64_t* __restrict__ rrow, const int32_t* __restrict__ rcol, const double* __restrict__ rval,
     const int64_t* __restrict__ arow, const int* __restrict__ acol, const double* __restrict__ aval,
@@ -1383,8 +1388,12 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
     if (ws_bytes < mg_layout(nullptr, N, nullptr, nullptr, &nb, kMgGalerkinRow)) return RBFFD_ERR_WORKSPACE;
     static bool smem_set = false;
     if (!smem_set) {
-        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kGalSmem));
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<512, 256>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)gal_smem_bytes<512, 256>()));
+        RBFFD_CUDA_TRY(cudaFuncSetAttribute(mg_galerkin_kernel<1024, 512>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)gal_smem_bytes<1024, 512>()));
         smem_set = true;
     }
     MgHierarchy h{};
@@ -1411,7 +1420,6 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
     RBFFD_CUDA_TRY(cudaMemcpyAsync(L0.dinv, F0.dinv, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     RBFFD_CUDA_TRY(cudaMemcpyAsync(L0.dinv32, F0.dinv32, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
     const int n_levels = F.n_levels;
-    const int gal_grid = std::max(1, sm_count() * 3);
     for (int l = 0; l + 1 < n_levels; ++l) {
         MgLevel& L = h.lv[l];
         const MgLevel& FL = F.lv[l];
@@ -1442,23 +1450,36 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
         note_launches(3);
         RBFFD_LAUNCH_CHECK();
         L.rtpr = tpr_for(nc, L.N * kMgK);
-        // C = R A P: rows staged, row pointer, rows placed
+        // C = R A P: rows staged (small tables first, the large ones if a row
+        // overflowed them), row pointer, rows placed
         int* cnt = s.pos;
-        RBFFD_CUDA_TRY(cudaMemsetAsync(s.gal_total, 0, sizeof(unsigned long long), st));
-        mg_galerkin_kernel<<<gal_grid, kGalWarps * 32, kGalSmem, st>>>(
-            nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
-            s.gal_total, std::min(s.gal_cap, nc * (int64_t)kMgGalerkinRow), s.gal_col, s.gal_val, s.flags);
-        note_launches(1);
-        RBFFD_LAUNCH_CHECK();
+        int* over = s.flags + 2;
         int64_t* crow = const_cast<int64_t*>(C.row_ptr);
-        RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{cnt}, nc, crow, s.sums64, crow + nc, st));
         int64_t cnnz = 0;
-        int flags[2] = {0, 0};
-        RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnnz, crow + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
-        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-        // a row wider than the tables, or more entries than the layout holds
-        if ((flags[0] & 2) || cnnz > nc * (int64_t)kMgGalerkinRow) return RBFFD_ERR_WORKSPACE;
+        const int64_t stage_cap = std::min(s.gal_cap, nc * (int64_t)kMgGalerkinRow);
+        for (int large = 0; large < 2; ++large) {
+            RBFFD_CUDA_TRY(cudaMemsetAsync(s.gal_total, 0, sizeof(unsigned long long), st));
+            RBFFD_CUDA_TRY(cudaMemsetAsync(over, 0, sizeof(int), st));
+            if (!large)
+                mg_galerkin_kernel<512, 256><<<sm_count() * 6, kGalWarps * 32, gal_smem_bytes<512, 256>(), st>>>(
+                    nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
+                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over);
+            else
+                mg_galerkin_kernel<1024, 512><<<sm_count() * 3, kGalWarps * 32, gal_smem_bytes<1024, 512>(), st>>>(
+                    nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
+                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over);
+            note_launches(1);
+            RBFFD_LAUNCH_CHECK();
+            RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{cnt}, nc, crow, s.sums64, crow + nc, st));
+            int ovf = 0;
+            RBFFD_CUDA_TRY(cudaMemcpyAsync(&cnnz, crow + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            RBFFD_CUDA_TRY(cudaMemcpyAsync(&ovf, over, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+            if (!ovf) break;
+            // a row wider than the large tables, or more entries than the layout holds
+            if (large) return RBFFD_ERR_WORKSPACE;
+        }
+        if (cnnz > nc * (int64_t)kMgGalerkinRow) return RBFFD_ERR_WORKSPACE;
         mg_galerkin_place_kernel<<<blocks_for(nc * 32), kT, 0, st>>>(nc, s.gal_start, crow, s.gal_col, s.gal_val,
                                                                      const_cast<int*>(C.col),
                                                                      const_cast<double*>(C.val),
@@ -1477,7 +1498,6 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
     int flags[2] = {0, 0};
     RBFFD_CUDA_TRY(cudaMemcpyAsync(flags, s.flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-    if (flags[0] & 2) return RBFFD_ERR_WORKSPACE;
     if (flags[0] || flags[1]) return RBFFD_ERR_SINGULAR_STENCIL;
     h.n_levels = n_levels;
     h.magic = kMgMagic;
