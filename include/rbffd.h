@@ -395,7 +395,10 @@ int rbffd_mg_apply(const rbffd_mg* mg, int32_t fp32, const double* b, double* x,
 /* confirmed by an explicitly recomputed residual before returning OK.       */
 /* BiCGSTAB runs in restarted passes: each pass starts from the explicit    */
 /* residual (shadow residual = residual) and ends when its residual has     */
-/* fallen by inner_tol; at most max_outer passes.                            */
+/* fallen by inner_tol, or when its recurrence residual reaches tol (after  */
+/* a pass that ended so while the explicit residual stayed above tol, the   */
+/* next pass aims 4 times lower, down to tol / 1000); at most max_outer     */
+/* passes.                                                                   */
 /*                                                                           */
 /* precision 0 (FP64): matrix, vectors and scalars in float64.               */
 /* precision 1 (mixed): an FP64 refinement loop (r = b - A x with the FP64   */
