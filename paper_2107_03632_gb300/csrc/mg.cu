@@ -616,42 +616,88 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
             }
             __syncwarp();
             bool full = false;
-            // D = R_c A_l: one row of A_l per batch of lanes
-            for (int64_t e = rrow[c]; e < rrow[c + 1]; ++e) {
-                const double rv = rval[e];
-                if (rv == 0.0) continue;
-                const int f = rcol[e];
-                const int64_t a0 = arow[f], a1 = arow[f + 1];
-                for (int64_t b = a0; b < a1; b += 32) {
-                    const int64_t k = b + lane;
-                    if (k < a1) {
-                        int fresh = 0;
-                        const int sl = gal_slot(k1, kGalH1 - 1, acol[k], &fresh);
-                        if (sl < 0) full = true;
-                        else v1[sl] = fma(rv, aval[k], v1[sl]);
+            // D = R_c A_l: one row of A_l per batch of lanes.  The entries of
+            // R's row and the extents of their A rows are loaded 32 at a time,
+            // one per lane (independent loads), then handed out by shuffles,
+            // and each A row's first batch is loaded before the previous
+            // row's keys go into the table.
+            const int64_t r0 = rrow[c], r1 = rrow[c + 1];
+            for (int64_t e0 = r0; e0 < r1; e0 += 32) {
+                double rv_l = 0.0;
+                int64_t a0_l = 0, a1_l = 0;
+                if (e0 + lane < r1) {
+                    rv_l = rval[e0 + lane];
+                    if (rv_l != 0.0) {
+                        const int f = rcol[e0 + lane];
+                        a0_l = arow[f];
+                        a1_l = arow[f + 1];
                     }
-                    __syncwarp();
+                }
+                const int cnt = (int)min((int64_t)32, r1 - e0);
+                // the first batch of the first entry's A row
+                int64_t a0 = __shfl_sync(0xffffffffu, a0_l, 0), a1 = __shfl_sync(0xffffffffu, a1_l, 0);
+                int kc = (a0 + lane < a1) ? acol[a0 + lane] : -1;
+                double kv = (a0 + lane < a1) ? aval[a0 + lane] : 0.0;
+                for (int t = 0; t < cnt; ++t) {
+                    const double rv = __shfl_sync(0xffffffffu, rv_l, t);
+                    const int64_t b0 = a0, b1 = a1;
+                    int cur_c = kc;
+                    double cur_v = kv;
+                    // the next entry's first batch, in flight while this row fills the table
+                    if (t + 1 < cnt) {
+                        a0 = __shfl_sync(0xffffffffu, a0_l, t + 1);
+                        a1 = __shfl_sync(0xffffffffu, a1_l, t + 1);
+                        kc = (a0 + lane < a1) ? acol[a0 + lane] : -1;
+                        kv = (a0 + lane < a1) ? aval[a0 + lane] : 0.0;
+                    }
+                    if (rv == 0.0) continue;  // (warp-uniform: a Dirichlet row of P)
+                    for (int64_t b = b0; b < b1; b += 32) {
+                        const int64_t k = b + lane;
+                        if (b > b0 && k < b1) {  // batches after the first (rows longer than 32)
+                            cur_c = acol[k];
+                            cur_v = aval[k];
+                        }
+                        if (k < b1) {
+                            int fresh = 0;
+                            const int sl = gal_slot(k1, kGalH1 - 1, cur_c, &fresh);
+                            if (sl < 0) full = true;
+                            else v1[sl] = fma(rv, cur_v, v1[sl]);
+                        }
+                        __syncwarp();
+                    }
                 }
             }
             // D's entries at the front, sorted by column
             const int n1 = gal_compact(k1, v1, kGalH1, lane, true);
             gal_sort(k1, v1, n1, lane);
             // C_c = D P_l: two entries of D per batch, lanes 0-11 and 16-27;
-            // the keys go in together, the values in D's order
+            // the keys go in together, the values in D's order; the next
+            // batch's row of P is loaded before this batch's keys go in
             const int half = lane >> 4, j = lane & 15;
+            const bool jl = j < kMgK;
+            int nxt_i = -1;
+            double nxt_v = 0.0;
+            if (half < n1 && jl) {
+                const int64_t pe = (int64_t)k1[half] * kMgK + j;
+                nxt_v = pval[pe];
+                nxt_i = pidx[pe];
+            }
             for (int i = 0; i < n1; i += 2) {
                 const int di = i + half;
+                const int pj = nxt_i;
+                const double pv = nxt_v;
+                if (di + 2 < n1 && jl) {
+                    const int64_t pe = (int64_t)k1[di + 2] * kMgK + j;
+                    nxt_v = pval[pe];
+                    nxt_i = pidx[pe];
+                }
                 int sl = -1;
                 double term = 0.0;
-                if (di < n1 && j < kMgK) {
-                    const int64_t pe = (int64_t)k1[di] * kMgK + j;
-                    const double pv = pval[pe];
-                    if (pv != 0.0) {
-                        int fresh = 0;
-                        sl = gal_slot(k2, kGalH2 - 1, pidx[pe], &fresh);
-                        if (sl < 0) full = true;
-                        term = v1[di] * pv;
-                    }
+                if (di < n1 && jl && pv != 0.0) {
+                    int fresh = 0;
+                    sl = gal_slot(k2, kGalH2 - 1, pj, &fresh);
+                    if (sl < 0) full = true;
+                    term = v1[di] * pv;
                 }
                 __syncwarp();
                 if (half == 0 && sl >= 0) v2[sl] += term;
