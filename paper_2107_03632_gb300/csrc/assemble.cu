@@ -99,26 +99,103 @@ __global__ void transpose_scatter_kernel(const int64_t* __restrict__ row_ptr, co
     }
 }
 
-// Sort each row of A^T by column index (insertion sort; rows are short);
-// with val32_t, also write the row's float32 copy (rounded to nearest).
-__global__ void row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N, int* __restrict__ col_t,
-                                double* __restrict__ val_t, float* __restrict__ val32_t) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+// Sort each row of A^T by column index: one warp per row, a bitonic network
+// over the row's entries held in registers (up to 128 entries, four per
+// lane); a longer row is sorted by one thread (insertion sort).  With
+// val32_t, also write the row's float32 copy (rounded to nearest).  Columns
+// within a row are distinct, so the order is unique.
+__global__ void __launch_bounds__(256) row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N,
+                                                       int* __restrict__ col_t, double* __restrict__ val_t,
+                                                       float* __restrict__ val32_t) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nw) {
         const int64_t a = row_ptr_t[r], e = row_ptr_t[r + 1];
-        for (int64_t k = a + 1; k < e; ++k) {
-            const int c = col_t[k];
-            const double v = val_t[k];
-            int64_t q = k - 1;
-            while (q >= a && col_t[q] > c) {
-                col_t[q + 1] = col_t[q];
-                val_t[q + 1] = val_t[q];
-                --q;
+        const int len = (int)(e - a);
+        if (len > 128) {
+            if (lane == 0) {
+                for (int64_t k = a + 1; k < e; ++k) {
+                    const int c = col_t[k];
+                    const double v = val_t[k];
+                    int64_t q = k - 1;
+                    while (q >= a && col_t[q] > c) {
+                        col_t[q + 1] = col_t[q];
+                        val_t[q + 1] = val_t[q];
+                        --q;
+                    }
+                    col_t[q + 1] = c;
+                    val_t[q + 1] = v;
+                }
             }
-            col_t[q + 1] = c;
-            val_t[q + 1] = v;
+            __syncwarp();
+            if (val32_t)
+                for (int64_t k = a + lane; k < e; k += 32) val32_t[k] = __double2float_rn(val_t[k]);
+            continue;
         }
-        if (val32_t)
-            for (int64_t k = a; k < e; ++k) val32_t[k] = __double2float_rn(val_t[k]);
+        // element i = lane + 32 q in register q; padding keys sort last
+        int key[4];
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            key[q] = i < len ? col_t[a + i] : 0x7fffffff;
+            v[q] = i < len ? val_t[a + i] : 0.0;
+        }
+        const int m = len <= 32 ? 32 : (len <= 64 ? 64 : 128);  // warp-uniform
+        if (len > 1) {
+            for (int k = 2; k <= m; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    if (j >= 32) {
+                        // partner in register q ^ (j / 32) of the same lane
+                        // (registers named at compile time, so they stay registers)
+                        auto cx = [&](int& ka, double& va, int& kb, double& vb, int q) {
+                            const bool up = ((lane + 32 * q) & k) == 0;
+                            if (ka != kb && (ka > kb) == up) {
+                                const int tk = ka;
+                                ka = kb;
+                                kb = tk;
+                                const double tv = va;
+                                va = vb;
+                                vb = tv;
+                            }
+                        };
+                        if (j == 32) {
+                            cx(key[0], v[0], key[1], v[1], 0);
+                            if (m == 128) cx(key[2], v[2], key[3], v[3], 2);
+                        } else {  // j == 64, m == 128
+                            cx(key[0], v[0], key[2], v[2], 0);
+                            cx(key[1], v[1], key[3], v[3], 1);
+                        }
+                    } else {
+                        // partner in lane ^ j, same register
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (32 * q < m) {
+                                const int pk = __shfl_xor_sync(0xffffffffu, key[q], j);
+                                const double pv = __shfl_xor_sync(0xffffffffu, v[q], j);
+                                const bool up = ((lane + 32 * q) & k) == 0;
+                                const bool lower = (lane & j) == 0;
+                                // the lower position keeps the smaller key when ascending
+                                const bool take = (lower == up) ? (pk < key[q]) : (pk > key[q]);
+                                if (take) {
+                                    key[q] = pk;
+                                    v[q] = pv;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i < len) {
+                col_t[a + i] = key[q];
+                val_t[a + i] = v[q];
+                if (val32_t) val32_t[a + i] = __double2float_rn(v[q]);
+            }
+        }
     }
 }
 
@@ -207,7 +284,7 @@ extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* 
     RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{counts}, N, row_ptr_t, sums, row_ptr_t + N, st));
     transpose_scatter_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, val, N, A->nnz, row_ptr_t, counts,
                                                                     col_t, val_t);
-    row_sort_kernel<<<grid_for(N, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t, val32_t);
+    row_sort_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t, val32_t);
     note_launches(3);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

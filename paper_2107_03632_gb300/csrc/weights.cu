@@ -584,6 +584,17 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         }
         group_sync<NT>();
         const double inv_delta = scal[0], inv_delta2 = scal[1];
+        const int bad_any = group_any<NT>(bad);
+
+        // interpolation at a point that is its own first neighbour (a fine
+        // node kept on the coarse level): the weights are e_1, the value there
+        if (op && !bad_any && abs_bits(crdd[0]) == 0ull && abs_bits(crdd[1]) == 0ull) {
+            double* wo = w + (int64_t)node * n;
+            for (int a = lane; a < n; a += NT) wo[a] = a == 0 ? 1.0 : 0.0;
+            if (node_status && lane == 0) node_status[node] = 0;
+            group_sync<NT>();
+            continue;
+        }
 
         // ---- P (rows 0..n-1: monomials at xh_j; row n: g) ------------------
         // degree d from degree d - 1 of the same row: x^(d-i) y^i = x * x^(d-1-i) y^i
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
 
         // ---- Gauss-Jordan with row pivoting on P ------------------------------
         int na = n;  // active (not yet pivot) rows act[0..na)
-        int singular = group_any<NT>(bad) ? 1 : 0;
+        int singular = bad_any ? 1 : 0;
         for (int k = 0; k < s && !singular; ++k) {
             unsigned long long best = 0;
             int bi = 0x7fffffff, bpos = -1;
