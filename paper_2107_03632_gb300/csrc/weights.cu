@@ -352,24 +352,38 @@ NsGeom ns_geom(int n, int m) {
     return g;
 }
 
-// Synchronisation and reductions over the threads of one stencil: a warp
-// (NT = 32) or the whole block (NT = 64, one stencil per block).
+// Synchronisation and reductions over the threads of one stencil: half a
+// warp (NT = 16, two stencils per warp), a warp (NT = 32) or the whole block
+// (NT = 64 or 128, one stencil per block).
+template <int NT>
+__device__ __forceinline__ unsigned group_mask() {
+    if (NT >= 32) return 0xffffffffu;
+    return ((1u << NT) - 1u) << ((threadIdx.x & 31) & ~(NT - 1));
+}
+
+// Shuffle offset the in-warp reductions start from.
+template <int NT>
+constexpr int group_shfl_top() {
+    return NT < 32 ? NT / 2 : 16;
+}
+
 template <int NT>
 __device__ __forceinline__ void group_sync() {
-    if (NT == 32) __syncwarp();
+    if (NT < 32) __syncwarp(group_mask<NT>());
+    else if (NT == 32) __syncwarp();
     else __syncthreads();
 }
 
 template <int NT>
 __device__ __forceinline__ int group_any(int p) {
-    if (NT == 32) return __any_sync(0xffffffffu, p);
+    if (NT <= 32) return __any_sync(group_mask<NT>(), p);
     return __syncthreads_or(p);
 }
 
 // Max over the group of a per-warp maximum (already reduced within each warp).
 template <int NT>
 __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v, unsigned long long* sh) {
-    if (NT == 32) return v;
+    if (NT <= 32) return v;
     constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) sh[w] = v;
@@ -385,7 +399,7 @@ __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v
 template <int NT>
 __device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, int& bpos, unsigned long long* shb,
                                              int* shi) {
-    if (NT == 32) return;
+    if (NT <= 32) return;
     constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
@@ -522,8 +536,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     using S = typename R::S;
     using V = typename R::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // NT threads per stencil: one warp (several stencils per block) or two
-    // or four warps (one stencil per block, block-wide synchronisation)
+    // NT threads per stencil: half a warp or one warp (several stencils per
+    // block) or two or four warps (one stencil per block, block-wide
+    // synchronisation)
     const int lane = threadIdx.x % NT;
     const int wib = threadIdx.x / NT;
     const int wpb = blockDim.x / NT;
@@ -571,8 +586,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             dmax = (b > dmax) ? b : dmax;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long t = __shfl_xor_sync(0xffffffffu, dmax, o);
+        for (int o = group_shfl_top<NT>(); o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(group_mask<NT>(), dmax, o);
             dmax = (t > dmax) ? t : dmax;
         }
         dmax = group_max_u64<NT>(dmax, red_u64);
@@ -640,10 +655,10 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                const int op_ = __shfl_xor_sync(0xffffffffu, bpos, o);
+            for (int o = group_shfl_top<NT>(); o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(group_mask<NT>(), best, o);
+                const int oi = __shfl_xor_sync(group_mask<NT>(), bi, o);
+                const int op_ = __shfl_xor_sync(group_mask<NT>(), bpos, o);
                 if (ob > best || (ob == best && oi < bi)) {
                     best = ob;
                     bi = oi;
@@ -966,7 +981,9 @@ namespace {
 struct WCfg {
     int kernel;  // 0 null-space elimination (one warp per stencil), 1 full Gaussian
                  // elimination, 2 / 3 null-space elimination with two / four warps
-                 // per stencil; 4 / 5 / 6: 0 / 2 / 3 in double-float arithmetic
+                 // per stencil; 4 / 5 / 6: 0 / 2 / 3 in double-float arithmetic;
+                 // 7 / 8: null-space elimination with half a warp per stencil,
+                 // FP64 / double-float
     int wpb;     // warps per block (kernels 2, 3: 2 or 4, one stencil)
 };
 
@@ -986,23 +1003,27 @@ size_t smem_per_stencil(int kernel, int n, int m) {
 }
 
 // Stencils per block of a configuration, and its dynamic shared memory.
-int stencils_per_block(const WCfg& c) { return (c.kernel == 2 || c.kernel == 3 || c.kernel >= 5) ? 1 : c.wpb; }
+int stencils_per_block(const WCfg& c) {
+    if (c.kernel >= 7) return 2 * c.wpb;
+    return (c.kernel == 2 || c.kernel == 3 || c.kernel == 5 || c.kernel == 6) ? 1 : c.wpb;
+}
+
+bool cfg_is_df(const WCfg& c) { return (c.kernel >= 4 && c.kernel <= 6) || c.kernel == 8; }
 
 // The double-float null-space kernels: 1 <= m <= 6 (accuracy, see NsDF).
 constexpr int kDfMaxM = 6;
 size_t block_smem(const WCfg& c, int n, int m) { return smem_per_stencil(c.kernel, n, m) * stencils_per_block(c); }
 
 bool cfg_valid(const WCfg& c, int n, int m) {
-    if (c.kernel < 0 || c.kernel > 6) return false;
+    if (c.kernel < 0 || c.kernel > 8) return false;
     if (c.kernel != 1 && m < 1) return false;  // null-space form needs the linear monomials
-    if (c.kernel >= 4 && m > kDfMaxM) return false;
+    if (cfg_is_df(c) && m > kDfMaxM) return false;
     if ((c.kernel == 2 || c.kernel == 5) && c.wpb != 2) return false;
     if ((c.kernel == 3 || c.kernel == 6) && c.wpb != 4) return false;
-    if ((c.kernel <= 1 || c.kernel == 4) && (c.wpb < 1 || c.wpb > 4)) return false;  // __launch_bounds__(128)
+    if ((c.kernel <= 1 || c.kernel == 4 || c.kernel >= 7) && (c.wpb < 1 || c.wpb > 4))
+        return false;  // __launch_bounds__(128)
     return block_smem(c, n, m) <= 227 * 1024;
 }
-
-bool cfg_is_df(const WCfg& c) { return c.kernel >= 4; }
 
 WCfg default_cfg(int n, int m) {
     WCfg c;
@@ -1016,6 +1037,22 @@ WCfg default_cfg(int n, int m) {
     // FP64 (m = 6, n = 56, 4M nodes: 1,346 ms against 1,595 with one warp)
     const WCfg big{2, 2};
     if (m >= 5 && cfg_valid(big, n, m)) return big;
+    // small systems (m <= 4, n <= 32): half a warp per stencil (1M nodes:
+    // m = 2, n = 12 8.3 ms against 13.0; m = 4, n = 30 45.3 against 50.4)
+    const WCfg half{7, 2};
+    if (m <= 4 && n <= 32 && cfg_valid(half, n, m)) return half;
+    return c;
+}
+
+// The double-float half-warp kernel for the preconditioner's small systems
+// (coarse operators and interpolation, n = 12: 4.9 ms per 1e6 stencils
+// against 7.7 with a warp per stencil), else the warp-per-stencil form.
+WCfg small_df_cfg(int n, int m) {
+    const WCfg half{8, 2};
+    if (n <= 20 && cfg_valid(half, n, m)) return half;
+    WCfg c{4, 1};
+    size_t smem = 0;
+    c.wpb = warps_per_block_for(smem_per_stencil(4, n, m), &smem);
     return c;
 }
 
@@ -1094,8 +1131,12 @@ int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t 
         rc = launch_ns<32, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     } else if (c.kernel == 5) {
         rc = launch_ns<64, NsDF>(c, p, idx, N, n, m, w, node_status, st);
-    } else {
+    } else if (c.kernel == 6) {
         rc = launch_ns<128, NsDF>(c, p, idx, N, n, m, w, node_status, st);
+    } else if (c.kernel == 7) {
+        rc = launch_ns<16, NsF64>(c, p, idx, N, n, m, w, node_status, st);
+    } else {
+        rc = launch_ns<16, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     }
     if (rc != RBFFD_OK) return rc;
     note_launches(1);
@@ -1141,6 +1182,10 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
     for (int wpb = 1; wpb <= 4; ++wpb) all.push_back(WCfg{4, wpb});
     all.push_back(WCfg{5, 2});
     all.push_back(WCfg{6, 4});
+    for (int wpb = 1; wpb <= 4; ++wpb) {
+        all.push_back(WCfg{7, wpb});
+        all.push_back(WCfg{8, wpb});
+    }
     std::vector<WCfg> cands;
     for (const WCfg& c : all) {
         if (!cfg_valid(c, n, m)) continue;
@@ -1234,8 +1279,12 @@ int rbffd::coarse_weights(const double* xy, const int32_t* idx, int64_t N, int32
     if (!weights_args_ok(xy, idx, w, N, n, m)) return RBFFD_ERR_INVALID_ARG;
     WCfg c;
     size_t smem = 0;
-    c.kernel = m < 1 ? 1 : (m <= kDfMaxM ? 4 : 0);
-    c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
+    if (m >= 1 && m <= kDfMaxM) {
+        c = small_df_cfg(n, m);
+    } else {
+        c.kernel = m < 1 ? 1 : 0;
+        c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem);
+    }
     return launch_weights(c, xy, idx, N, n, m, w, node_status, st);
 }
 
@@ -1257,13 +1306,18 @@ int rbffd::interp_weights(const double* xy, int64_t Nd, const double* qxy, int64
         // shared-memory footprint
         WCfg c;
         size_t smem_b = 0;
-        c.kernel = m <= kDfMaxM ? 4 : 0;
-        c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem_b);
+        if (m <= kDfMaxM) {
+            c = small_df_cfg(n, m);
+        } else {
+            c.kernel = 0;
+            c.wpb = warps_per_block_for(smem_per_stencil(c.kernel, n, m), &smem_b);
+        }
         if (!cfg_valid(c, n, m)) return RBFFD_ERR_INVALID_ARG;
         const double2* d2 = reinterpret_cast<const double2*>(xy);
         const double2* q2 = reinterpret_cast<const double2*>(qxy);
-        const int rc = c.kernel == 4 ? launch_ns<32, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
-                                     : launch_ns<32, NsF64>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1);
+        const int rc = c.kernel == 8   ? launch_ns<16, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
+                       : c.kernel == 4 ? launch_ns<32, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
+                                       : launch_ns<32, NsF64>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1);
         if (rc != RBFFD_OK) return rc;
         note_launches(1);
         RBFFD_LAUNCH_CHECK();

@@ -182,7 +182,7 @@ def test_weights_config_table(cdll):
     c = rbffd.WeightsConfig()
     assert cdll.rbffd_weights_get_config(56, 6, ctypes.byref(c)) == 0
     assert (c.kernel, c.warps_per_block) == (2, 2)  # FP64 null-space, two warps, by default at m = 6
-    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0  # FP64, one warp at m = 4
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 7  # FP64, half a warp at m = 4
     assert cdll.rbffd_weights_get_config(90, 8, ctypes.byref(c)) == 0 and c.kernel == 2  # FP64, two warps, m = 8
     assert cdll.rbffd_weights_get_config(12, 0, ctypes.byref(c)) == 0 and c.kernel == 1  # m = 0: elimination
     pin = rbffd.WeightsConfig(1, 2, 0.0)
@@ -190,16 +190,18 @@ def test_weights_config_table(cdll):
     assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0
     assert (c.kernel, c.warps_per_block) == (1, 2)
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
-    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 0
-    for good in ((2, 2), (3, 4), (4, 1), (4, 3), (5, 2), (6, 4), (0, 2)):
+    assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 7
+    for good in ((2, 2), (3, 4), (4, 1), (4, 3), (5, 2), (6, 4), (0, 2), (7, 1), (7, 4), (8, 2)):
         assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(rbffd.WeightsConfig(*good, 0.0))) == 0, good
-    for bad in (rbffd.WeightsConfig(7, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
+    for bad in (rbffd.WeightsConfig(9, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
+                rbffd.WeightsConfig(7, 5, 0.0), rbffd.WeightsConfig(8, 0, 0.0),
                 rbffd.WeightsConfig(5, 4, 0.0), rbffd.WeightsConfig(6, 2, 0.0), rbffd.WeightsConfig(4, 5, 0.0),
                 rbffd.WeightsConfig(0, 5, 0.0),
                 rbffd.WeightsConfig(0, 0, 0.0)):
         assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(bad)) == 1
     # double-float kernels only up to m = 6
     assert cdll.rbffd_weights_set_config(90, 8, ctypes.byref(rbffd.WeightsConfig(4, 1, 0.0))) == 1
+    assert cdll.rbffd_weights_set_config(90, 8, ctypes.byref(rbffd.WeightsConfig(8, 1, 0.0))) == 1
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
     assert cdll.rbffd_weights_set_config(12, 0, ctypes.byref(rbffd.WeightsConfig(0, 1, 0.0))) == 1  # m = 0
     assert cdll.rbffd_weights_set_config(10, 4, ctypes.byref(pin)) == 1  # n < s
