@@ -496,9 +496,10 @@ __global__ void __launch_bounds__(kT) mg_dense_copy_kernel(const double* __restr
 // probing, keys -1 when empty): first D = R_c A_l keyed by fine column, then
 // the row C_c = D P_l keyed by coarse column.  Zero entries of R and P_l
 // (Dirichlet rows of P, the removed columns) are skipped.  Every key's terms
-// are summed in a fixed order (the entries of one A row, or one P row, have
-// distinct columns, so the lanes of a batch never share a slot, and batches
-// run in sequence; D is sorted by column before its rows of P are read), and
+// are summed in a fixed order (a batch is one A row, whose columns are
+// distinct, or two P rows, one per half-warp, whose values go in one half
+// after the other; batches run in sequence; D is sorted by column before its
+// rows of P are read), and
 // the row is sorted by column and staged at a place taken from an atomic
 // counter; after a scan of the row lengths a second kernel copies each row
 // to its CSR position.  The product therefore does not depend on thread
