@@ -792,7 +792,39 @@ __global__ void __launch_bounds__(kBT) md_spmm_kernel(const Unit* __restrict__ u
         for (int64_t row = un.row_lo + wid; row < un.row_hi; row += 8) {
             const int64_t lo = row_ptr[row], hi = row_ptr[row + 1];
             DfAcc s0, s1;
-            for (int64_t q = lo; q < hi; ++q) {
+            int64_t q = lo;
+            // four entries at a time: their indices, then their gathers in
+            // flight together (the same sums, in the same order)
+            for (; q + 4 <= hi; q += 4) {
+                float ah[4], al[4];
+                int64_t c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ah[i] = __ldg(vhi + q + i);
+                    al[i] = __ldg(vlo + q + i);
+                    c[i] = (int64_t)__ldg(col + q + i) * R;
+                }
+                df x0[4], x1[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    x0[i] = on0 ? df_load(xin + c[i] + k0) : df_make(0.f, 0.f);
+                    x1[i] = on1 ? df_load(xin + c[i] + k1) : df_make(0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (on0) {
+                        df pp = two_prod(ah[i], x0[i].hi);
+                        pp.lo = __fmaf_rn(ah[i], x0[i].lo, __fmaf_rn(al[i], x0[i].hi, pp.lo));
+                        s0.add(pp);
+                    }
+                    if (on1) {
+                        df pp = two_prod(ah[i], x1[i].hi);
+                        pp.lo = __fmaf_rn(ah[i], x1[i].lo, __fmaf_rn(al[i], x1[i].hi, pp.lo));
+                        s1.add(pp);
+                    }
+                }
+            }
+            for (; q < hi; ++q) {
                 const float ah = __ldg(vhi + q), al = __ldg(vlo + q);
                 const int64_t c = (int64_t)__ldg(col + q) * R;
                 if (on0) {
