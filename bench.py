@@ -182,8 +182,8 @@ SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorit
 # n = 56: dram read + write per stencil (idx read, w written; the gathered
 # coordinates come from L2).  Valid only at that (n, m) and while the
 # kernel's sources are the ones captured.
-WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "c51a64676b9d78d8", "n": 56, "m": 6,
-                       "bytes_per_node": (258.147584e6 + 406.128128e6) / 1001697.0}
+WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "a3acd9eb6bff4d92", "n": 56, "m": 6,
+                       "bytes_per_node": (258.018304e6 + 406.632448e6) / 1001697.0}
 
 
 def weights_source_hash():

@@ -94,7 +94,8 @@ def test_stencils_invalid_args(lib):
 @pytest.fixture(params=["nullspace", "nullspace-fp64", "nullspace-df", "lu"])
 def weights_kernel(request, monkeypatch):
     """Every weight kernel: the default (FP64 null-space elimination, two warps
-    per stencil at m >= 5), the FP64 null-space elimination with one warp
+    per stencil at m >= 5, half a warp at m <= 4 with n <= 32, else one warp),
+    the FP64 null-space elimination with one warp
     (RBFFD_WEIGHTS=ns64), its double-float form (RBFFD_WEIGHTS=df, for
     1 <= m <= 6) and the full Gaussian elimination (RBFFD_WEIGHTS=lu)."""
     env = {"lu": "lu", "nullspace-fp64": "ns64", "nullspace-df": "df"}.get(request.param)
