@@ -372,9 +372,10 @@ def test_autograd_with_multigrid_vs_oracle(lib, precision):
     assert np.abs(u.detach().cpu().numpy() - uu).max() / np.abs(uu).max() <= 1e-8
     dLdu = np.where(d.is_dirichlet == 1, 0.0, 2.0 * (uu - ustar))
     gf, gg, _ = oracle.adjoint_gradient(rp, col, val, d.is_dirichlet, dLdu)
-    # dL/du = 2 (u - u*) carries u's 1e-8-level solve error into the adjoint
-    assert np.abs(fT.grad.cpu().numpy() - gf).max() / np.abs(gf).max() <= 1e-6
-    assert np.abs(gT.grad.cpu().numpy() - gg).max() / np.abs(gg).max() <= 1e-6
+    # the same 1e-8 bar as the other adjoint tests (measured on a GB300: 4e-12 to 7e-12
+    # for both precisions at tol 1e-11)
+    assert np.abs(fT.grad.cpu().numpy() - gf).max() / np.abs(gf).max() <= 1e-8
+    assert np.abs(gT.grad.cpu().numpy() - gg).max() / np.abs(gg).max() <= 1e-8
     assert torch.isfinite(fT.grad).all()
 
 
