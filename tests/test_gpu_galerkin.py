@@ -184,3 +184,72 @@ def test_galerkin_adjoint_at_1M(lib, precision):
     ATs = _csr(AT, d.N, d.N)
     lam_h, g_h = lam.cpu().numpy(), dLdu.cpu().numpy()
     assert np.linalg.norm(g_h - ATs @ lam_h) <= 1e-10 * np.linalg.norm(g_h) * 1.01
+
+
+def _refined_disk(h, factor, centre=(0.2, 0.1), radius=0.3, seed=2107):
+    """A disk with a patch `factor` times denser: the disk's nodes outside the
+    patch and, inside it, the interior nodes of a disk of spacing h / sqrt(factor)."""
+    from fixtures.disk import DiskNodes
+
+    coarse = disk_nodes(h, seed)
+    fine = disk_nodes(h / np.sqrt(factor), seed + 1)
+    cx, cy = centre
+    out = np.hypot(coarse.xy[:, 0] - cx, coarse.xy[:, 1] - cy) >= radius
+    inn = (np.hypot(fine.xy[:, 0] - cx, fine.xy[:, 1] - cy) < radius) & (fine.is_dirichlet == 0)
+    interior = np.concatenate([coarse.xy[out & (coarse.is_dirichlet == 0)], fine.xy[inn]])
+    boundary = coarse.xy[coarse.is_dirichlet == 1]
+    xy = np.ascontiguousarray(np.concatenate([interior, boundary]))
+    mask = np.zeros(xy.shape[0], dtype=np.uint8)
+    mask[interior.shape[0]:] = 1
+    return DiskNodes(xy, mask, float(h), int(seed), int(interior.shape[0]), int(boundary.shape[0]))
+
+
+def test_galerkin_wide_rows_take_the_large_tables(lib):
+    """A patch twelve times denser than the rest (radius 0.2): on the first
+    level, rows of R A reach more than 512 distinct fine columns (counted here
+    with scipy; ~800), more than the small hash table holds, so the level is
+    redone with the large tables; the coarse operator is still the exact
+    triple product."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d = _refined_disk(0.01, 12.0, radius=0.2)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    idx = rbffd.rbffd_stencils(xy, 30)
+    w, st = rbffd.rbffd_weights(xy, idx, 4)
+    assert int(st.sum()) == 0
+    A = rbffd.rbffd_assemble(idx, w, mask, want_f32=True)
+    AT = rbffd.rbffd_transpose(A, want_f32=True)
+    fwd = rbffd.Multigrid(xy, mask, A)
+    gal = rbffd.Multigrid.galerkin_adjoint_of(fwd, AT)
+    sizes = gal.levels()
+    Nf, Nc = sizes[0], sizes[1]
+    F, G, Gc = fwd.level(0), gal.level(0), gal.level(1)
+    cmask = Gc["is_dirichlet"].cpu().numpy().astype(bool)
+    P = F["p_val"].cpu().numpy()
+    pidx = F["p_idx"].cpu().numpy()
+    p_adj = np.where(cmask[pidx], 0.0, (float(Nc) / float(Nf)) * P)
+    R = _ell(pidx, P, Nc).T.tocsr()
+    Pa = _ell(pidx, p_adj, Nc)
+    R.eliminate_zeros()
+    Pa.eliminate_zeros()
+    Al = _csr(G["A"], Nf, Nf)
+    ones = lambda M: sp.csr_matrix((np.ones_like(M.data), M.indices, M.indptr), shape=M.shape)
+    RA = (ones(R) @ ones(Al)).tocsr()
+    widest = int(np.diff(RA.indptr)[~cmask].max())
+    assert widest > 512, widest  # the small table cannot hold these rows
+    keep = sp.diags((~cmask).astype(np.float64))
+    eye_b = sp.diags(cmask.astype(np.float64))
+    ref = (keep @ (R @ Al @ Pa) + eye_b).tocsr()
+    pat = (keep @ (RA @ ones(Pa)) + eye_b).tocsr()
+    pat.sort_indices()
+    got = _csr(Gc["A"], Nc, Nc)
+    assert np.array_equal(got.indptr, pat.indptr) and np.array_equal(got.indices, pat.indices)
+    scale = abs(ref).max(axis=1).toarray().ravel()
+    assert (abs(got - ref).max(axis=1).toarray().ravel() / scale).max() <= 1e-12
+    # and the adjoint it preconditions converges
+    rng = np.random.default_rng(9)
+    dLdu = T(rng.standard_normal(d.N) * (d.is_dirichlet == 0))
+    lam, _, _, info = rbffd.rbffd_solve_adjoint(AT, mask, dLdu, opts=rbffd.make_opts(tol=1e-10, mg=gal))
+    assert info["status"] == 0, info
+    r = dLdu.cpu().numpy() - _csr(AT, d.N, d.N) @ lam.cpu().numpy()
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(dLdu.cpu().numpy())
