@@ -193,11 +193,15 @@ def test_assemble_and_rhs_bitexact(lib):
     assert np.array_equal(b, oracle.rhs(f, g, d.is_dirichlet))
 
 
-def test_transpose_bitexact(lib):
+@pytest.mark.parametrize("n", [30, 120])
+def test_transpose_bitexact(lib, n):
+    """A^T against scipy's transpose: with n = 30 the rows of A^T take the
+    warp sort's 32- and 64-entry networks, with n = 120 its 128-entry network
+    and its one-thread path for longer rows (305 rows above 128 entries)."""
     from paper_2107_03632_gb300 import rbffd
 
     d = disk_nodes(0.05)
-    idx = oracle.knn(d.xy, 30)
+    idx = oracle.knn(d.xy, n)
     w, _ = oracle.weights(d.xy, idx, 4)
     A = rbffd.rbffd_assemble(T(idx), T(w), T(d.is_dirichlet))
     AT = rbffd.rbffd_transpose(A, want_f32=True)
@@ -205,6 +209,8 @@ def test_transpose_bitexact(lib):
     ref = to_scipy(rp, col, val, d.N).T.tocsr()
     ref.sort_indices()
     assert np.array_equal(AT.row_ptr.cpu().numpy(), ref.indptr)
+    if n == 120:
+        assert np.diff(ref.indptr).max() > 128
     assert np.array_equal(AT.col.cpu().numpy(), ref.indices)
     assert np.array_equal(AT.val.cpu().numpy(), ref.data)
     # the library's float32 copy of A^T: round to nearest of the same values
