@@ -588,6 +588,42 @@ int rbffd_diag_recip(const double* x, int64_t n, double* rcp, double* rsqrt, voi
 int rbffd_profile_enable(int on);
 int rbffd_profile_read(rbffd_profile* out, int reset);
 
+/* Bounds-checked build (no counterpart in the paper; a testing aid).  The   */
+/* library compiled with -DRBFFD_CHECKED (librbffd_checked.so) tests every    */
+/* index its kernels compute -- global gathers and scatters, sub-arrays of   */
+/* larger arrays (stencil rows, CSR rows), and pointers into shared memory   */
+/* -- before the access.  An index out of range does not stop the kernel:    */
+/* the access goes to a private scratch location instead (a read returns     */
+/* its bytes, a write lands there) and the violation is counted in a device  */
+/* record per source unit.  rbffd_checked_read gathers those records into    */
+/* *out: checked = 1 in the checked build (0 and no violations otherwise),   */
+/* violations = their total since the last reset, and file / line / index /  */
+/* bound of the first violation of the first unit that has one (index is    */
+/* the offending index, or the end of the offending sub-array, or the byte   */
+/* offset into shared memory; bound the extent it broke).  Call it after the */
+/* work has completed (synchronise the streams first); reset != 0 clears     */
+/* the records.  Errors: RBFFD_ERR_INVALID_ARG (out NULL), RBFFD_ERR_CUDA.   */
+typedef struct rbffd_checked_report {
+    int32_t checked;     /* 1: this library is the bounds-checked build */
+    int32_t line;        /* first violation: source line */
+    char file[32];       /* first violation: source file (base name) */
+    int64_t violations;  /* violations since the last reset */
+    int64_t index;       /* first violation: the index (or end, or byte offset) */
+    int64_t bound;       /* first violation: the extent it broke */
+} rbffd_checked_report;
+int rbffd_checked_read(rbffd_checked_report* out, int reset);
+/* Self-check of the bounds-checked build: one thread reads entry `index` of */
+/* a 64-entry zero-filled device table tested against `bound` (<= 64), tests */
+/* the sub-array [span_off, span_off + span_len) against `bound`, and stores */
+/* 1 + that entry at byte smem_off (a multiple of 8) of 64 bytes of dynamic  */
+/* shared memory, then reads it back into *out (device, 1 double).  The      */
+/* checked build records (and redirects) each access outside its bound, so  */
+/* out-of-range arguments show up in rbffd_checked_read; the normal build    */
+/* returns RBFFD_ERR_INVALID_ARG for them before launching anything.         */
+/* Asynchronous on `stream`.                                                 */
+int rbffd_checked_probe(int64_t index, int64_t bound, int64_t span_off, int64_t span_len, int64_t smem_off,
+                        double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

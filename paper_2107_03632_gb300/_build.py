@@ -3,6 +3,11 @@
 Each .cu translation unit is compiled in parallel, then linked into one
 shared library with the CUDA runtime linked statically.  A stamp of the
 sources and flags skips the build when nothing changed.
+
+build(checked=True) makes the bounds-checked variant, librbffd_checked.so
+(-DRBFFD_CHECKED: every computed index is tested before its access and a
+violation is recorded instead of performed); the package loads it instead of
+librbffd.so when the environment sets RBFFD_CHECKED=1.
 """
 
 from __future__ import annotations
@@ -19,7 +24,9 @@ CSRC = os.path.join(PKG_DIR, "csrc")
 INCLUDE = os.path.join(REPO_DIR, "include")
 LIB_DIR = os.path.join(PKG_DIR, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "librbffd.so")
+CHECKED_LIB_PATH = os.path.join(LIB_DIR, "librbffd_checked.so")
 OBJ_DIR = os.path.join(PKG_DIR, "_build")
+CHECKED_FLAGS = ["-DRBFFD_CHECKED"]
 
 SOURCES = ["api.cu", "knn.cu", "weights.cu", "assemble.cu", "krylov.cu", "batched.cu", "mg.cu", "mg_batch.cu",
            "explicit.cu"]
@@ -36,9 +43,13 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build librbffd")
 
 
-def _stamp() -> str:
+def lib_path(checked: bool = False) -> str:
+    return CHECKED_LIB_PATH if checked else LIB_PATH
+
+
+def _stamp(extra) -> str:
     h = hashlib.sha256()
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra)).encode())
     for d, names in ((CSRC, sorted(os.listdir(CSRC))), (INCLUDE, sorted(os.listdir(INCLUDE)))):
         for nm in names:
             p = os.path.join(d, nm)
@@ -50,21 +61,25 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile and link the library; returns its path."""
+def build(force: bool = False, verbose: bool = False, extra_flags=None, checked: bool = False) -> str:
+    """Compile and link the library (the bounds-checked variant when
+    `checked`); returns its path."""
+    extra = (CHECKED_FLAGS if checked else []) + list(extra_flags or [])
+    lib = lib_path(checked)
+    obj_dir = os.path.join(OBJ_DIR, "checked") if checked else OBJ_DIR
     os.makedirs(LIB_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    stamp = _stamp()
-    stamp_path = LIB_PATH + ".stamp"
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp_path):
+    os.makedirs(obj_dir, exist_ok=True)
+    stamp = _stamp(extra)
+    stamp_path = lib + ".stamp"
+    if not force and os.path.exists(lib) and os.path.exists(stamp_path):
         with open(stamp_path) as f:
             if f.read().strip() == stamp:
-                return LIB_PATH
+                return lib
     nvcc = _nvcc()
-    flags = ARCH + NVCC_FLAGS + ["-I", INCLUDE, "-I", CSRC] + list(extra_flags or [])
+    flags = ARCH + NVCC_FLAGS + ["-I", INCLUDE, "-I", CSRC] + extra
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -75,15 +90,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib)
     with open(stamp_path, "w") as f:
         f.write(stamp)
-    return LIB_PATH
+    return lib
 
 
 if __name__ == "__main__":

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -126,6 +127,28 @@ void prof_collect() {
     }
 }
 
+// Readers of the bounds-checked build's per-unit violation records (each
+// unit registers one while the library loads; none in the normal build).
+static std::vector<CheckedReader>& checked_readers() {
+    static std::vector<CheckedReader> v;
+    return v;
+}
+static std::mutex& checked_mu() {
+    static std::mutex mu;
+    return mu;
+}
+
+void checked_register(CheckedReader read) {
+    std::lock_guard<std::mutex> lk(checked_mu());
+    checked_readers().push_back(read);
+}
+
+// Source files whose lines the records may name.
+static const char* const kCheckedFiles[] = {"api.cu",     "knn.cu",      "weights.cu",  "assemble.cu",
+                                             "krylov.cu",  "batched.cu",  "mg.cu",       "mg_batch.cu",
+                                             "explicit.cu", "common.cuh", "scan.cuh",    "internal.cuh",
+                                             "df32.cuh",   "checked.cuh"};
+
 }  // namespace rbffd
 
 extern "C" {
@@ -172,6 +195,36 @@ int rbffd_profile_read(rbffd_profile* out, int reset) {
 }
 
 
+int rbffd_checked_read(rbffd_checked_report* out, int reset) {
+    using namespace rbffd;
+    RBFFD_NVTX("rbffd_checked_read");
+    if (!out) return RBFFD_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+#ifdef RBFFD_CHECKED
+    out->checked = 1;
+#endif
+    std::lock_guard<std::mutex> lk(checked_mu());
+    for (CheckedReader read : checked_readers()) {
+        CheckedRecord r{};
+        const int e = read(&r, reset);
+        if (e != (int)cudaSuccess) {
+            set_cuda_error((cudaError_t)e);
+            return RBFFD_ERR_CUDA;
+        }
+        if (r.count && !out->violations) {
+            out->line = (int32_t)r.line;
+            out->index = r.index;
+            out->bound = r.bound;
+            const char* name = "?";
+            for (const char* f : kCheckedFiles)
+                if ((long long)chk_name_hash(f) == r.file_hash) name = f;
+            snprintf(out->file, sizeof(out->file), "%s", name);
+        }
+        out->violations += (int64_t)r.count;
+    }
+    return RBFFD_OK;
+}
+
 const char* rbffd_status_string(int s) {
     switch (s) {
         case RBFFD_OK: return "RBFFD_OK";
@@ -207,6 +260,50 @@ __global__ void diag_recip_kernel(const double* __restrict__ x, int64_t n, doubl
 }
 }  // namespace
 }  // namespace rbffd
+
+// ---------------------------------------------------------------------------
+// Self-check of the bounds-checked build: one thread reads entry `index` of
+// a 64-entry table with RB_AT against `bound`, tests the sub-array [span_off,
+// span_off + span_len) against `bound` with RB_SPAN, and stores the value at
+// byte `smem_off` of 64 bytes of dynamic shared memory through RB_SH.  In
+// the checked build an index outside its bound is recorded and redirected
+// (never performed); the normal build takes only in-range arguments, tested
+// on the host before anything is launched.
+namespace rbffd {
+namespace {
+constexpr int kProbeTable = 64;
+constexpr int kProbeSmem = 64;
+__device__ double g_probe_table[kProbeTable];
+
+__global__ void checked_probe_kernel(int64_t index, int64_t bound, int64_t span_off, int64_t span_len,
+                                     int64_t smem_off, double* out) {
+    extern __shared__ __align__(16) unsigned char probe_smem[];
+    const double v = RB_AT(g_probe_table, index, bound) + 1.0;
+    RB_SPAN(span_off, span_len, bound);
+    double* slot = reinterpret_cast<double*>(probe_smem + smem_off);
+    *RB_SH(slot) = v;
+    __syncwarp();
+    out[0] = *RB_SH(slot);
+}
+}  // namespace
+}  // namespace rbffd
+
+extern "C" int rbffd_checked_probe(int64_t index, int64_t bound, int64_t span_off, int64_t span_len,
+                                   int64_t smem_off, double* out, void* stream) {
+    RBFFD_NVTX("rbffd_checked_probe");
+    using namespace rbffd;
+    if (!out || bound < 0 || bound > kProbeTable || smem_off % 8 != 0) return RBFFD_ERR_INVALID_ARG;
+#ifndef RBFFD_CHECKED
+    // the normal build performs only in-range accesses
+    if (index < 0 || index >= bound || span_off < 0 || span_len < 0 || span_off > bound - span_len ||
+        smem_off < 0 || smem_off > kProbeSmem - 8)
+        return RBFFD_ERR_INVALID_ARG;
+#endif
+    checked_probe_kernel<<<1, 1, kProbeSmem, as_stream(stream)>>>(index, bound, span_off, span_len, smem_off, out);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    return RBFFD_OK;
+}
 
 extern "C" int rbffd_diag_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {
     RBFFD_NVTX("rbffd_diag_recip");

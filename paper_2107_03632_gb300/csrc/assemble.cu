@@ -93,8 +93,8 @@ __global__ void transpose_scatter_kernel(const int64_t* __restrict__ row_ptr, co
             const int c = col[k];
             if ((unsigned)c >= (unsigned)N) continue;
             const int64_t pos = row_ptr_t[c + 1] - atomicSub(&counts[c], 1);
-            col_t[pos] = (int)r;
-            val_t[pos] = val[k];
+            RB_AT(col_t, pos, nnz) = (int)r;
+            RB_AT(val_t, pos, nnz) = val[k];
         }
     }
 }
@@ -105,13 +105,15 @@ __global__ void transpose_scatter_kernel(const int64_t* __restrict__ row_ptr, co
 // val32_t, also write the row's float32 copy (rounded to nearest).  Columns
 // within a row are distinct, so the order is unique.
 __global__ void __launch_bounds__(256) row_sort_kernel(const int64_t* __restrict__ row_ptr_t, int64_t N,
-                                                       int* __restrict__ col_t, double* __restrict__ val_t,
-                                                       float* __restrict__ val32_t) {
+                                                       int64_t nnz, int* __restrict__ col_t,
+                                                       double* __restrict__ val_t, float* __restrict__ val32_t) {
+    (void)nnz;  // bound of the checked build's tests (the transpose has at most nnz entries)
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nw) {
         const int64_t a = row_ptr_t[r], e = row_ptr_t[r + 1];
         const int len = (int)(e - a);
+        RB_SPAN(a, len, nnz);
         if (len > 128) {
             if (lane == 0) {
                 for (int64_t k = a + 1; k < e; ++k) {
@@ -284,7 +286,7 @@ extern "C" int rbffd_transpose(const rbffd_csr* A, int64_t* row_ptr_t, int32_t* 
     RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{counts}, N, row_ptr_t, sums, row_ptr_t + N, st));
     transpose_scatter_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(A->row_ptr, A->col, val, N, A->nnz, row_ptr_t, counts,
                                                                     col_t, val_t);
-    row_sort_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(row_ptr_t, N, col_t, val_t, val32_t);
+    row_sort_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(row_ptr_t, N, A->nnz, col_t, val_t, val32_t);
     note_launches(3);
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

@@ -273,6 +273,12 @@ __global__ void __launch_bounds__(kBT) b_check_kernel(const Unit* __restrict__ u
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
+        // the instance's block of x (the bound of the checked build's tests)
+        const double* xb = x + in.node_off * R;
+        const int64_t xn = in.n_nodes * R;
+        (void)xb;
+        (void)xn;
         // skip instances whose pairs are all finished
         bool any = false;
         for (int k = 0; k < R; ++k) {
@@ -287,8 +293,8 @@ __global__ void __launch_bounds__(kBT) b_check_kernel(const Unit* __restrict__ u
             for (int64_t q = lo; q < hi; ++q) {
                 const double a = __ldg(val + q);
                 const int64_t c = (int64_t)__ldg(col + q) * R;
-                if (k0 < R) s0 = fma(a, x[c + k0], s0);
-                if (k1 < R) s1 = fma(a, x[c + k1], s1);
+                if (k0 < R) s0 = fma(a, RB_PT(x + c + k0, xb, xn), s0);
+                if (k1 < R) s1 = fma(a, RB_PT(x + c + k1, xb, xn), s1);
             }
             const double di = dinv[row];
             if (k0 < R) {
@@ -340,6 +346,7 @@ __global__ void __launch_bounds__(kBT) b_load_kernel(const Unit* __restrict__ un
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
         bool any = false;
         for (int k = 0; k < R; ++k) any |= pr.flag[un.inst * R + k] == kPassEnd;
         if (!any) continue;
@@ -465,6 +472,12 @@ __global__ void __launch_bounds__(kBT) b_spmm_kernel(const Unit* __restrict__ un
         const Unit un = units[u];
         if (!inst_live(inst_running, un.inst)) continue;
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
+        // the instance's block of xin (the bound of the checked build's tests)
+        const float2* xb = xin + in.node_off * R;
+        const int64_t xn = in.n_nodes * R;
+        (void)xb;
+        (void)xn;
         const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kRun;
         const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kRun;
         DfAcc c0a, c0b, c1a, c1b;
@@ -477,13 +490,13 @@ __global__ void __launch_bounds__(kBT) b_spmm_kernel(const Unit* __restrict__ un
                 const float w = __ldg(val + q);
                 const int64_t c = (int64_t)__ldg(col + q) * R;
                 if (on0) {
-                    const df xj = df_load(xin + c + k0);
+                    const df xj = df_load(&RB_PT(xin + c + k0, xb, xn));
                     df pp = two_prod(w, __fsub_rn(xj.hi, x0.hi));
                     pp.lo = __fmaf_rn(w, __fsub_rn(xj.lo, x0.lo), pp.lo);
                     s0.add(pp);
                 }
                 if (on1) {
-                    const df xj = df_load(xin + c + k1);
+                    const df xj = df_load(&RB_PT(xin + c + k1, xb, xn));
                     df pp = two_prod(w, __fsub_rn(xj.hi, x1.hi));
                     pp.lo = __fmaf_rn(w, __fsub_rn(xj.lo, x1.lo), pp.lo);
                     s1.add(pp);
@@ -577,6 +590,7 @@ __global__ void __launch_bounds__(kBT) b_update_xr_kernel(const Unit* __restrict
         const Unit un = units[u];
         if (!inst_live(inst_running, un.inst)) continue;
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
         double a[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -685,6 +699,7 @@ __global__ void __launch_bounds__(kBT) md_load_kernel(const Unit* __restrict__ u
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
         bool any = false;
         for (int k = 0; k < R; ++k) any |= pr.flag[un.inst * R + k] == kPassEnd;
         if (!any) continue;
@@ -786,6 +801,12 @@ __global__ void __launch_bounds__(kBT) md_spmm_kernel(const Unit* __restrict__ u
         const Unit un = units[u];
         if (!inst_live(inst_running, un.inst)) continue;
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
+        // the instance's block of xin (the bound of the checked build's tests)
+        const float2* xb = xin + in.node_off * R;
+        const int64_t xn = in.n_nodes * R;
+        (void)xb;
+        (void)xn;
         const bool on0 = k0 < R && pr.flag[un.inst * R + k0] == kRun;
         const bool on1 = k1 < R && pr.flag[un.inst * R + k1] == kRun;
         DfAcc c0a, c0b, c1a, c1b;
@@ -807,8 +828,8 @@ __global__ void __launch_bounds__(kBT) md_spmm_kernel(const Unit* __restrict__ u
                 df x0[4], x1[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    x0[i] = on0 ? df_load(xin + c[i] + k0) : df_make(0.f, 0.f);
-                    x1[i] = on1 ? df_load(xin + c[i] + k1) : df_make(0.f, 0.f);
+                    x0[i] = on0 ? df_load(&RB_PT(xin + c[i] + k0, xb, xn)) : df_make(0.f, 0.f);
+                    x1[i] = on1 ? df_load(&RB_PT(xin + c[i] + k1, xb, xn)) : df_make(0.f, 0.f);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -828,13 +849,13 @@ __global__ void __launch_bounds__(kBT) md_spmm_kernel(const Unit* __restrict__ u
                 const float ah = __ldg(vhi + q), al = __ldg(vlo + q);
                 const int64_t c = (int64_t)__ldg(col + q) * R;
                 if (on0) {
-                    const df xj = df_load(xin + c + k0);
+                    const df xj = df_load(&RB_PT(xin + c + k0, xb, xn));
                     df pp = two_prod(ah, xj.hi);
                     pp.lo = __fmaf_rn(ah, xj.lo, __fmaf_rn(al, xj.hi, pp.lo));
                     s0.add(pp);
                 }
                 if (on1) {
-                    const df xj = df_load(xin + c + k1);
+                    const df xj = df_load(&RB_PT(xin + c + k1, xb, xn));
                     df pp = two_prod(ah, xj.hi);
                     pp.lo = __fmaf_rn(ah, xj.lo, __fmaf_rn(al, xj.hi, pp.lo));
                     s1.add(pp);
@@ -930,6 +951,7 @@ __global__ void __launch_bounds__(kBT) md_update_xr_kernel(const Unit* __restric
         const Unit un = units[u];
         if (!inst_live(inst_running, un.inst)) continue;
         const Inst in = inst[un.inst];
+        RB_SPAN(un.row_lo - in.node_off, un.row_hi - un.row_lo, in.n_nodes);
         double a[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

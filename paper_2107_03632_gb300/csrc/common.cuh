@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include "checked.cuh"
 #include "rbffd.h"
 
 namespace rbffd {

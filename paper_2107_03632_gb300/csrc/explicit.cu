@@ -66,15 +66,15 @@ __global__ void __launch_bounds__(kT) explicit_pack_kernel(const int32_t* __rest
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         if (mask[i]) continue;
         const int64_t r = pos[i];
-        rows[r] = (int32_t)i;
+        RB_AT(rows, r, Ni) = (int32_t)i;
         for (int j = 0; j < n; ++j) {
             int32_t c = idx[i * n + j];
             if ((uint32_t)c >= (uint32_t)N) {  // never let the loop read outside u
                 nb = 1;
                 c = (int32_t)i;
             }
-            idxT[(int64_t)j * Ni + r] = c;
-            wT[(int64_t)j * Ni + r] = w[i * n + j];
+            RB_AT(idxT, (int64_t)j * Ni + r, (int64_t)n * Ni) = c;
+            RB_AT(wT, (int64_t)j * Ni + r, (int64_t)n * Ni) = w[i * n + j];
         }
     }
     if (nb) atomicOr(bad, 1);
@@ -85,12 +85,15 @@ __global__ void __launch_bounds__(kT) explicit_step_kernel(const int32_t* __rest
                                                            const int32_t* __restrict__ idxT,
                                                            const double* __restrict__ wT, int64_t Ni, int n,
                                                            const double* __restrict__ f, double dt,
-                                                           const double* __restrict__ u1, double* __restrict__ u2) {
+                                                           const double* __restrict__ u1, double* __restrict__ u2,
+                                                           int64_t N) {
+    (void)N;  // nodes: bound of the checked build's tests
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < Ni; r += (int64_t)gridDim.x * blockDim.x) {
         double lap = 0.0;
-        for (int j = 0; j < n; ++j) lap = fma(__ldg(wT + (int64_t)j * Ni + r), __ldg(u1 + __ldg(idxT + (int64_t)j * Ni + r)), lap);
+        for (int j = 0; j < n; ++j)
+            lap = fma(__ldg(wT + (int64_t)j * Ni + r), __ldg(&RB_AT(u1, __ldg(idxT + (int64_t)j * Ni + r), N)), lap);
         const int i = __ldg(rows + r);
-        u2[i] = fma(dt, __ldg(f + i) + lap, u1[i]);
+        RB_AT(u2, i, N) = fma(dt, __ldg(&RB_AT(f, i, N)) + lap, RB_AT(u1, i, N));
     }
 }
 
@@ -166,7 +169,7 @@ extern "C" int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t
         if (e == cudaSuccess) {
             for (int k = 0; k < kGraphSteps; ++k) {
                 explicit_step_kernel<<<g, kT, 0, cap>>>(L.rows, L.idx, L.w, Ni, n, f, dt, (k & 1) ? b : a,
-                                                        (k & 1) ? a : b);
+                                                        (k & 1) ? a : b, N);
             }
             e = cudaStreamEndCapture(cap, &graph);
         }
@@ -189,7 +192,7 @@ extern "C" int rbffd_explicit_run(const double* f, double* u, int64_t N, int32_t
         done = reps * kGraphSteps;  // even: the current level is back in a
     }
     for (int64_t k = done; k < steps; ++k) {
-        explicit_step_kernel<<<g, kT, 0, st>>>(L.rows, L.idx, L.w, Ni, n, f, dt, a, b);
+        explicit_step_kernel<<<g, kT, 0, st>>>(L.rows, L.idx, L.w, Ni, n, f, dt, a, b, N);
         std::swap(a, b);
         note_launches(1);
     }

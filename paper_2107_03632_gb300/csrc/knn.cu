@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_partial_kernel(const double2
     }
     __shared__ Box sh[kBoxThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = Box{mnx, mny, mxx, mxy};
+    if (lane == 0) RB_AT(sh, wid, kBoxThreads / 32) = Box{mnx, mny, mxx, mxy};
     __syncthreads();
     if (threadIdx.x == 0) {
         Box r = sh[0];
@@ -122,7 +122,7 @@ __global__ void cell_count_kernel(const double2* __restrict__ xy, int64_t N, con
         const int cy = cell_coord(q.y, p.y0, p.inv_cell, p.G);
         const int key = cy * p.G + cx;
         keys[i] = key;
-        atomicAdd(&counts[key], 1);
+        atomicAdd(&RB_AT(counts, key, p.G * p.G), 1);
     }
 }
 
@@ -130,13 +130,14 @@ __global__ void cell_count_kernel(const double2* __restrict__ xy, int64_t N, con
 // [start[key], start[key+1]) exactly once.  Order inside a cell is arbitrary;
 // stencils do not depend on it because the ranking key is a total order.
 __global__ void cell_scatter_kernel(const double2* __restrict__ xy, int64_t N, const int* __restrict__ keys,
-                                    const int* __restrict__ cell_start, int* __restrict__ counts,
+                                    const int* __restrict__ cell_start, int* __restrict__ counts, int64_t cells,
                                     double2* __restrict__ sxy, int* __restrict__ sorig) {
+    (void)cells;  // bound of the checked build's tests
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int key = keys[i];
-        const int pos = cell_start[key + 1] - atomicSub(&counts[key], 1);
-        sxy[pos] = xy[i];
-        sorig[pos] = (int)i;
+        const int pos = RB_AT(cell_start, key + 1, cells + 1) - atomicSub(&RB_AT(counts, key, cells), 1);
+        RB_AT(sxy, pos, N) = xy[i];
+        RB_AT(sorig, pos, N) = (int)i;
     }
 }
 
@@ -240,7 +241,7 @@ struct TopList {
 // batches made the search FP64-bound.)
 template <int SLOTS>
 __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sxy, const int* __restrict__ sorig,
-                                                  const int* __restrict__ cell_start,
+                                                  const int* __restrict__ cell_start, int Np,
                                                   const GridParams* __restrict__ gp, int Nq,
                                                   const double2* __restrict__ qxy, const int* __restrict__ qorig,
                                                   int n, int R0, int* __restrict__ idx) {
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
     const double2 Q = qxy[q];
     const int qo = qorig ? qorig[q] : q;
     const int G = p.G;
+    (void)Np;  // bound of the checked build's tests
     const int cx = cell_coord(Q.x, p.x0, p.inv_cell, G);
     const int cy = cell_coord(Q.y, p.y0, p.inv_cell, G);
 
@@ -266,12 +268,12 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
             unsigned long long kd = ~0ull;
             unsigned int kj = ~0u;
             if (jj < end) {
-                const double2 P = sxy[jj];
+                const double2 P = RB_AT(sxy, jj, Np);
                 const double dx = __dadd_rn(P.x, -Q.x);
                 const double dy = __dadd_rn(P.y, -Q.y);
                 const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
                 kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
-                kj = (unsigned int)sorig[jj];
+                kj = (unsigned int)RB_AT(sorig, jj, Np);
             }
             unsigned int m = __ballot_sync(0xffffffffu, key_less(kd, kj, thr_d, thr_j));
             while (m) {
@@ -301,7 +303,8 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
         return (dx * dx + dy * dy) * (1.0f - 1e-4f) > (float)key_d2(thr_d);
     };
     auto row_range = [&](int xl, int xh, int yy) {
-        if (!beyond(xl, xh, yy)) scan(cell_start[yy * G + xl], cell_start[yy * G + xh + 1]);
+        if (!beyond(xl, xh, yy))
+            scan(RB_AT(cell_start, yy * G + xl, G * G + 1), RB_AT(cell_start, yy * G + xh + 1, G * G + 1));
     };
     // true when the cells within ring r hold the n nearest: whole grid
     // visited, or the gap from Q to the unvisited cells exceeds the n-th key
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
         }
     }
 
+    RB_SPAN((int64_t)qo * n, n, (int64_t)Nq * n);
     int* out = idx + (int64_t)qo * n;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
@@ -429,18 +433,18 @@ int rbffd::knn_search(const double* xy, int64_t N, const double* qxy, int64_t Nq
     RBFFD_CUDA_TRY(cudaMemsetAsync(L.counts, 0, sizeof(int) * cells, st));
     cell_count_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.gp, L.keys, L.counts);
     RBFFD_CUDA_TRY(exclusive_scan<int>(CountLoad{L.counts}, cells, L.cell_start, L.sums, L.cell_start + cells, st));
-    cell_scatter_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.keys, L.cell_start, L.counts, L.sxy, L.sorig);
+    cell_scatter_kernel<<<grid_pts, 256, 0, st>>>(p, N, L.keys, L.cell_start, L.counts, cells, L.sxy, L.sorig);
     const int warps_per_block = 8;
     const int blocks = (int)((Nq + warps_per_block - 1) / warps_per_block);
     const double2* q = qxy ? reinterpret_cast<const double2*>(qxy) : L.sxy;
     const int* qo = qxy ? nullptr : L.sorig;
     const int R0 = block_radius(n);
     if (n <= 32)
-        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
+        knn_kernel<1><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, (int)N, L.gp, (int)Nq, q, qo, n, R0, idx);
     else if (n <= 64)
-        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
+        knn_kernel<2><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, (int)N, L.gp, (int)Nq, q, qo, n, R0, idx);
     else
-        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, L.gp, (int)Nq, q, qo, n, R0, idx);
+        knn_kernel<4><<<blocks, 256, 0, st>>>(L.sxy, L.sorig, L.cell_start, (int)N, L.gp, (int)Nq, q, qo, n, R0, idx);
     note_launches(5);  // bbox, setup, count, scatter, knn (+3 in the scan)
     RBFFD_LAUNCH_CHECK();
     return RBFFD_OK;

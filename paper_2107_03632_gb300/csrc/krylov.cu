@@ -106,7 +106,7 @@ __device__ bool reduce_last(double (&v)[NQ], double* part, int slot, unsigned in
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const double bs = block_sum<kThreads>(v[q], sh);
-        if (threadIdx.x == 0) part_at(part, slot, q)[blockIdx.x] = bs;
+        if (threadIdx.x == 0) RB_AT(part_at(part, slot, q), blockIdx.x, kMaxBlocks) = bs;
     }
     __threadfence();
     __syncthreads();
@@ -170,7 +170,8 @@ __device__ __forceinline__ void set_omega(KState* st, double ts, double tt, doub
 template <int TPR>
 __device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                             const double* __restrict__ val, const double* __restrict__ x,
-                                            int64_t row, int sub, bool valid) {
+                                            int64_t nx, int64_t row, int sub, bool valid) {
+    (void)nx;  // length of x: bound of the checked build's tests
     int64_t a = 0, e = 0;
     if (valid) {
         a = __ldg(row_ptr + row);
@@ -178,7 +179,7 @@ __device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr,
     }
     double sum = 0.0;
 #pragma unroll 4
-    for (int64_t k = a + sub; k < e; k += TPR) sum = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), sum);
+    for (int64_t k = a + sub; k < e; k += TPR) sum = fma(__ldg(val + k), __ldg(&RB_AT(x, __ldg(col + k), nx)), sum);
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
     return sum;
@@ -199,7 +200,8 @@ __device__ __forceinline__ void two_sum64(double a, double b, double& s, double&
 template <int TPR>
 __device__ __forceinline__ double row_residual64(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                                  const double* __restrict__ val, const double* __restrict__ x,
-                                                 int64_t row, int sub, bool valid, double bi) {
+                                                 int64_t nx, int64_t row, int sub, bool valid, double bi) {
+    (void)nx;  // length of x: bound of the checked build's tests
     int64_t a = 0, e = 0;
     if (valid) {
         a = __ldg(row_ptr + row);
@@ -208,7 +210,7 @@ __device__ __forceinline__ double row_residual64(const int64_t* __restrict__ row
     double sh = 0.0, sl = 0.0;
 #pragma unroll 2
     for (int64_t k = a + sub; k < e; k += TPR) {
-        const double av = __ldg(val + k), xv = __ldg(x + __ldg(col + k));
+        const double av = __ldg(val + k), xv = __ldg(&RB_AT(x, __ldg(col + k), nx));
         const double p = __dmul_rn(av, xv);
         const double pe = fma(av, xv, -p);
         double t, te;
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) resid64_kernel(const int64_t* __rest
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
         const double bi = valid ? b[i] : 0.0;
-        const double rt = row_residual64<TPR>(row_ptr, col, val, x, i, sub, valid, bi);
+        const double rt = row_residual64<TPR>(row_ptr, col, val, x, N, i, sub, valid, bi);
         if (valid && sub == 0) {
             acc[0] = fma(rt, rt, acc[0]);
             acc[1] = fma(bi, bi, acc[1]);
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) spmv64_kernel(const int64_t* __restr
     const int sub = threadIdx.x & (TPR - 1);
     double acc[3] = {0.0, 0.0, 0.0};
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
-        const double ax = row_dot64<TPR>(row_ptr, col, val, xin, i, sub, valid);
+        const double ax = row_dot64<TPR>(row_ptr, col, val, xin, N, i, sub, valid);
         if (valid && sub == 0) {
             const double yi = ax * dinv[i];
             y[i] = yi;
@@ -497,7 +499,8 @@ __global__ void __launch_bounds__(kThreads) update_xr64_kernel(int64_t N, double
 template <int TPR>
 __device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
                                            const float* __restrict__ val, const float2* __restrict__ x,
-                                           int64_t row, int sub, bool valid, df xi) {
+                                           int64_t nx, int64_t row, int sub, bool valid, df xi) {
+    (void)nx;  // length of x: bound of the checked build's tests
     int64_t a = 0, e = 0;
     if (valid) {
         a = __ldg(row_ptr + row);
@@ -507,7 +510,7 @@ __device__ __forceinline__ df row_apply_df(const int64_t* __restrict__ row_ptr, 
 #pragma unroll 4
     for (int64_t k = a + sub; k < e; k += TPR) {
         const float w = __ldg(val + k);
-        const df xj = df_ldg(x + __ldg(col + k));
+        const df xj = df_ldg(&RB_AT(x, __ldg(col + k), nx));
         // d_j - d_i as an unnormalised pair: the rounding of the leading
         // difference is at most eps_32 of that difference (exact when the
         // two values are within a factor 2), so no cancellation is lost
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) spmv_df_kernel(const int64_t* __rest
     DfAcc a0, a1, a2;
     RBFFD_ROW_LOOP(TPR, N, i, valid, {
         const df xi = valid ? df_ldg(xin + i) : df_make(0.f, 0.f);
-        df ax = row_apply_df<TPR>(row_ptr, col, val, xin, i, sub, valid, xi);
+        df ax = row_apply_df<TPR>(row_ptr, col, val, xin, N, i, sub, valid, xi);
         if (valid && sub == 0) {
             ax = df_add(ax, df_mul_f(xi, sigma[i]));
             const df yi = df_mul_f(ax, dinv[i]);

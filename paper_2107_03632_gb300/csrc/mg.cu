@@ -85,8 +85,9 @@ __device__ __forceinline__ float fmaT<float>(float a, float b, float c) {
 
 template <typename T, int TPR>
 __device__ __forceinline__ T row_sum(const int64_t* __restrict__ row_ptr, const int* __restrict__ col,
-                                     const T* __restrict__ val, const T* __restrict__ x, int64_t row, int sub,
-                                     bool valid) {
+                                     const T* __restrict__ val, const T* __restrict__ x, int64_t nx, int64_t row,
+                                     int sub, bool valid) {
+    (void)nx;  // length of x: bound of the checked build's tests
     int64_t a = 0, e = 0;
     if (valid) {
         a = __ldg(row_ptr + row);
@@ -94,7 +95,7 @@ __device__ __forceinline__ T row_sum(const int64_t* __restrict__ row_ptr, const 
     }
     T sum = T(0);
 #pragma unroll 4
-    for (int64_t k = a + sub; k < e; k += TPR) sum = fmaT<T>(__ldg(val + k), __ldg(x + __ldg(col + k)), sum);
+    for (int64_t k = a + sub; k < e; k += TPR) sum = fmaT<T>(__ldg(val + k), __ldg(&RB_AT(x, __ldg(col + k), nx)), sum);
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
     return sum;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kT) mg_jacobi_kernel(const int64_t* __restrict
     if (stopped(flag)) return;
     const int sub = threadIdx.x & (TPR - 1);
     MG_ROWS(TPR, N, i, valid, {
-        const T ax = row_sum<T, TPR>(row_ptr, col, val, xi, i, sub, valid);
+        const T ax = row_sum<T, TPR>(row_ptr, col, val, xi, N, i, sub, valid);
         if (valid && sub == 0) xo[i] = (OT)fmaT<T>(dinv[i], (T)b[i] - ax, xi[i]);
     })
 }
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kT) mg_resid_kernel(const int64_t* __restrict_
     if (stopped(flag)) return;
     const int sub = threadIdx.x & (TPR - 1);
     MG_ROWS(TPR, N, i, valid, {
-        const T ax = row_sum<T, TPR>(row_ptr, col, val, x, i, sub, valid);
+        const T ax = row_sum<T, TPR>(row_ptr, col, val, x, N, i, sub, valid);
         if (valid && sub == 0) r[i] = (T)b[i] - ax;
     })
 }
@@ -141,12 +142,12 @@ __global__ void __launch_bounds__(kT) mg_resid_kernel(const int64_t* __restrict_
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kT) mg_restrict_kernel(const int64_t* __restrict__ row_ptr,
                                                          const int* __restrict__ col, const T* __restrict__ val,
-                                                         int64_t n, const T* __restrict__ r, T* __restrict__ y,
-                                                         const int* flag) {
+                                                         int64_t n, const T* __restrict__ r, int64_t nr,
+                                                         T* __restrict__ y, const int* flag) {
     if (stopped(flag)) return;
     const int sub = threadIdx.x & (TPR - 1);
     MG_ROWS(TPR, n, i, valid, {
-        const T v = row_sum<T, TPR>(row_ptr, col, val, r, i, sub, valid);
+        const T v = row_sum<T, TPR>(row_ptr, col, val, r, nr, i, sub, valid);
         if (valid && sub == 0) y[i] = v;
     })
 }
@@ -155,14 +156,15 @@ __global__ void __launch_bounds__(kT) mg_restrict_kernel(const int64_t* __restri
 template <typename T>
 __global__ void __launch_bounds__(kT) mg_prolong_kernel(int64_t N, const int32_t* __restrict__ pidx,
                                                         const T* __restrict__ pval, const T* __restrict__ e,
-                                                        T* __restrict__ x, const int* flag) {
+                                                        int64_t ne, T* __restrict__ x, const int* flag) {
+    (void)ne;  // length of e: bound of the checked build's tests
     if (stopped(flag)) return;
     MG_ELEMS(N, i) {
         const int32_t* ip = pidx + i * kMgK;
         const T* vp = pval + i * kMgK;
         T acc = x[i];
 #pragma unroll
-        for (int j = 0; j < kMgK; ++j) acc = fmaT<T>(__ldg(vp + j), __ldg(e + __ldg(ip + j)), acc);
+        for (int j = 0; j < kMgK; ++j) acc = fmaT<T>(__ldg(vp + j), __ldg(&RB_AT(e, __ldg(ip + j), ne)), acc);
         x[i] = acc;
     }
 }
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kT) mg_bbox_kernel(const double2* __restrict__
     }
     __shared__ MgBox sh[kT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = MgBox{mnx, mny, mxx, mxy};
+    if (lane == 0) RB_AT(sh, wid, kT / 32) = MgBox{mnx, mny, mxx, mxy};
     __syncthreads();
     if (threadIdx.x == 0) {
         MgBox r = sh[0];
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(kT) mg_mark_kernel(const double2* __restrict__
         if (!(d2 >= 0.f) || d2 > 1e30f) d2 = 1e30f;
         const unsigned long long key = ((unsigned long long)(mask[i] ? 0u : 1u) << 63) |
                                        ((unsigned long long)__float_as_uint(d2) << 31) | (unsigned long long)i;
-        atomicMin(best + c, key);
+        atomicMin(&RB_AT(best, c, (int64_t)g.gx * g.gy), key);
     }
 }
 
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(kT) mg_select_kernel(const double2* __restrict
     MG_ELEMS(N, i) {
         const double2 p = xy[i];
         const int64_t c = cell_of(g, p.x, p.y);
-        sel[i] = ((best[c] & 0x7fffffffull) == (unsigned long long)i) ? 1 : 0;
+        sel[i] = ((RB_AT(best, c, (int64_t)g.gx * g.gy) & 0x7fffffffull) == (unsigned long long)i) ? 1 : 0;
     }
 }
 
@@ -269,13 +271,14 @@ struct SelLoad {
 
 __global__ void __launch_bounds__(kT) mg_gather_kernel(const double2* __restrict__ xy, const uint8_t* __restrict__ mask,
                                                        int64_t N, const int* __restrict__ sel,
-                                                       const int* __restrict__ pos, double2* __restrict__ cxy,
-                                                       uint8_t* __restrict__ cmask) {
+                                                       const int* __restrict__ pos, int64_t Nc,
+                                                       double2* __restrict__ cxy, uint8_t* __restrict__ cmask) {
+    (void)Nc;  // coarse points: bound of the checked build's tests
     MG_ELEMS(N, i) {
         if (sel[i]) {
             const int k = pos[i];
-            cxy[k] = xy[i];
-            cmask[k] = mask[i] ? 1 : 0;
+            RB_AT(cxy, k, Nc) = xy[i];
+            RB_AT(cmask, k, Nc) = mask[i] ? 1 : 0;
         }
     }
 }
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kT) mg_bfix_kernel(const int64_t* __restrict__
     MG_ELEMS(N, i) {
         if (!mask[i]) continue;
         double s = 0.0;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s = fma(val[k], y[col[k]], s);
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s = fma(val[k], RB_AT(y, col[k], N), s);
         y[i] = fma(w[i], r[i] - s, y[i]);
     }
 }
@@ -364,11 +367,12 @@ __global__ void __launch_bounds__(kT) mg_rscale_kernel(const int64_t* __restrict
 // Adjoint hierarchy: prolongation R^T = scale P with the columns of coarse
 // Dirichlet nodes zeroed (R zeroes their rows); float copy.
 __global__ void __launch_bounds__(kT) mg_pscale_kernel(int64_t N, const int32_t* __restrict__ pidx,
-                                                       const uint8_t* __restrict__ cmask, double scale,
+                                                       const uint8_t* __restrict__ cmask, int64_t Nc, double scale,
                                                        double* __restrict__ pval, float* __restrict__ pval32) {
     const int64_t total = N * kMgK;
     MG_ELEMS(total, e) {
-        const double v = cmask[pidx[e]] ? 0.0 : scale * pval[e];
+        (void)Nc;  // coarse points: bound of the checked build's tests
+        const double v = RB_AT(cmask, pidx[e], Nc) ? 0.0 : scale * pval[e];
         pval[e] = v;
         pval32[e] = __double2float_rn(v);
     }
@@ -464,12 +468,12 @@ __global__ void __launch_bounds__(kGJ) mg_gj_kernel(double* __restrict__ aug, in
         }
         __syncthreads();
         for (int j = tid; j < n2; j += kGJ) aug[(int64_t)k * n2 + j] *= piv;
-        for (int i = tid; i < n; i += kGJ) f[i] = (i == k) ? 0.0 : aug[(int64_t)i * n2 + k];
+        for (int i = tid; i < n; i += kGJ) RB_AT(f, i, kMgCoarsest) = (i == k) ? 0.0 : aug[(int64_t)i * n2 + k];
         __syncthreads();
         const int64_t total = (int64_t)n * n2;
         for (int64_t e = tid; e < total; e += kGJ) {
             const int i = (int)(e / n2), j = (int)(e - (int64_t)i * n2);
-            if (i != k) aug[e] = fma(-f[i], aug[(int64_t)k * n2 + j], aug[e]);
+            if (i != k) aug[e] = fma(-RB_AT(f, i, kMgCoarsest), aug[(int64_t)k * n2 + j], aug[e]);
         }
         __syncthreads();
     }
@@ -536,24 +540,25 @@ __device__ __forceinline__ int gal_slot(int* keys, unsigned mask, int key, int* 
 // Ascending sort of n <= cap (key, value) pairs held at the front of the
 // arrays, by one warp (bitonic network over the next power of two, padded
 // with INT_MAX keys).
-__device__ __forceinline__ void gal_sort(int* keys, double* vals, int n, int lane) {
+__device__ __forceinline__ void gal_sort(int* keys, double* vals, int n, int cap, int lane) {
+    (void)cap;  // table size: bound of the checked build's tests
     int m = 32;
     while (m < n) m <<= 1;
-    for (int i = n + lane; i < m; i += 32) keys[i] = 0x7fffffff;
+    for (int i = n + lane; i < m; i += 32) RB_AT(keys, i, cap) = 0x7fffffff;
     __syncwarp();
     for (int k = 2; k <= m; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = lane; i < m; i += 32) {
                 const int p = i ^ j;
                 if (p > i) {
-                    const int a = keys[i], b = keys[p];
+                    const int a = RB_AT(keys, i, cap), b = RB_AT(keys, p, cap);
                     const bool up = (i & k) == 0;
                     if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[p] = a;
-                        const double t = vals[i];
-                        vals[i] = vals[p];
-                        vals[p] = t;
+                        RB_AT(keys, i, cap) = b;
+                        RB_AT(keys, p, cap) = a;
+                        const double t = RB_AT(vals, i, cap);
+                        RB_AT(vals, i, cap) = RB_AT(vals, p, cap);
+                        RB_AT(vals, p, cap) = t;
                     }
                 }
             }
@@ -574,8 +579,8 @@ __device__ __forceinline__ int gal_compact(int* keys, double* vals, int cap, int
         __syncwarp();
         if (k != -1) {
             const int dst = n + __popc(occ & ((1u << lane) - 1u));
-            keys[dst] = k;
-            if (with_vals) vals[dst] = v;
+            RB_AT(keys, dst, cap) = k;
+            if (with_vals) RB_AT(vals, dst, cap) = v;
         }
         n += __popc(occ);
         __syncwarp();
@@ -589,7 +594,9 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
     const int64_t* __restrict__ arow, const int* __restrict__ acol, const double* __restrict__ aval,
     const int32_t* __restrict__ pidx, const double* __restrict__ pval, const uint8_t* __restrict__ cmask,
     int* __restrict__ count, int64_t* __restrict__ start, unsigned long long* __restrict__ total, int64_t cap,
-    int* __restrict__ tcol, double* __restrict__ tval, int* __restrict__ bad) {
+    int* __restrict__ tcol, double* __restrict__ tval, int* __restrict__ bad, int64_t Nf, int64_t annz) {
+    (void)Nf;  // fine points and A's entries: bounds of the checked build's tests
+    (void)annz;
     extern __shared__ __align__(16) unsigned char gal_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* v1 = reinterpret_cast<double*>(gal_smem) + (size_t)wid * (kGalH1 + kGalH2);
@@ -597,6 +604,8 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
     int* k1 = reinterpret_cast<int*>(reinterpret_cast<double*>(gal_smem) + (size_t)kGalWarps * (kGalH1 + kGalH2)) +
               (size_t)wid * (kGalH1 + kGalH2);
     int* k2 = k1 + kGalH1;
+    (void)RB_SH(v2 + kGalH2 - 1);  // the warp's tables lie in the launch's shared memory
+    (void)RB_SH(k2 + kGalH2 - 1);
     int overflow = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kGalWarps;
     for (int64_t c = (int64_t)blockIdx.x * kGalWarps + wid; c < Nc; c += nwarps) {
@@ -630,15 +639,15 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
                     rv_l = rval[e0 + lane];
                     if (rv_l != 0.0) {
                         const int f = rcol[e0 + lane];
-                        a0_l = arow[f];
-                        a1_l = arow[f + 1];
+                        a0_l = RB_AT(arow, f, Nf + 1);
+                        a1_l = RB_AT(arow, f + 1, Nf + 1);
                     }
                 }
                 const int cnt = (int)min((int64_t)32, r1 - e0);
                 // the first batch of the first entry's A row
                 int64_t a0 = __shfl_sync(0xffffffffu, a0_l, 0), a1 = __shfl_sync(0xffffffffu, a1_l, 0);
-                int kc = (a0 + lane < a1) ? acol[a0 + lane] : -1;
-                double kv = (a0 + lane < a1) ? aval[a0 + lane] : 0.0;
+                int kc = (a0 + lane < a1) ? RB_AT(acol, a0 + lane, annz) : -1;
+                double kv = (a0 + lane < a1) ? RB_AT(aval, a0 + lane, annz) : 0.0;
                 for (int t = 0; t < cnt; ++t) {
                     const double rv = __shfl_sync(0xffffffffu, rv_l, t);
                     const int64_t b0 = a0, b1 = a1;
@@ -648,21 +657,21 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
                     if (t + 1 < cnt) {
                         a0 = __shfl_sync(0xffffffffu, a0_l, t + 1);
                         a1 = __shfl_sync(0xffffffffu, a1_l, t + 1);
-                        kc = (a0 + lane < a1) ? acol[a0 + lane] : -1;
-                        kv = (a0 + lane < a1) ? aval[a0 + lane] : 0.0;
+                        kc = (a0 + lane < a1) ? RB_AT(acol, a0 + lane, annz) : -1;
+                        kv = (a0 + lane < a1) ? RB_AT(aval, a0 + lane, annz) : 0.0;
                     }
                     if (rv == 0.0) continue;  // (warp-uniform: a Dirichlet row of P)
                     for (int64_t b = b0; b < b1; b += 32) {
                         const int64_t k = b + lane;
                         if (b > b0 && k < b1) {  // batches after the first (rows longer than 32)
-                            cur_c = acol[k];
-                            cur_v = aval[k];
+                            cur_c = RB_AT(acol, k, annz);
+                            cur_v = RB_AT(aval, k, annz);
                         }
                         if (k < b1) {
                             int fresh = 0;
                             const int sl = gal_slot(k1, kGalH1 - 1, cur_c, &fresh);
                             if (sl < 0) full = true;
-                            else v1[sl] = fma(rv, cur_v, v1[sl]);
+                            else RB_AT(v1, sl, kGalH1) = fma(rv, cur_v, RB_AT(v1, sl, kGalH1));
                         }
                         __syncwarp();
                     }
@@ -670,7 +679,7 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
             }
             // D's entries at the front, sorted by column
             const int n1 = gal_compact(k1, v1, kGalH1, lane, true);
-            gal_sort(k1, v1, n1, lane);
+            gal_sort(k1, v1, n1, kGalH1, lane);
             // C_c = D P_l: two entries of D per batch, lanes 0-11 and 16-27;
             // the keys go in together, the values in D's order; the next
             // batch's row of P is loaded before this batch's keys go in
@@ -679,18 +688,18 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
             int nxt_i = -1;
             double nxt_v = 0.0;
             if (half < n1 && jl) {
-                const int64_t pe = (int64_t)k1[half] * kMgK + j;
-                nxt_v = pval[pe];
-                nxt_i = pidx[pe];
+                const int64_t pe = (int64_t)RB_AT(k1, half, kGalH1) * kMgK + j;
+                nxt_v = RB_AT(pval, pe, Nf * kMgK);
+                nxt_i = RB_AT(pidx, pe, Nf * kMgK);
             }
             for (int i = 0; i < n1; i += 2) {
                 const int di = i + half;
                 const int pj = nxt_i;
                 const double pv = nxt_v;
                 if (di + 2 < n1 && jl) {
-                    const int64_t pe = (int64_t)k1[di + 2] * kMgK + j;
-                    nxt_v = pval[pe];
-                    nxt_i = pidx[pe];
+                    const int64_t pe = (int64_t)RB_AT(k1, di + 2, kGalH1) * kMgK + j;
+                    nxt_v = RB_AT(pval, pe, Nf * kMgK);
+                    nxt_i = RB_AT(pidx, pe, Nf * kMgK);
                 }
                 int sl = -1;
                 double term = 0.0;
@@ -698,12 +707,12 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
                     int fresh = 0;
                     sl = gal_slot(k2, kGalH2 - 1, pj, &fresh);
                     if (sl < 0) full = true;
-                    term = v1[di] * pv;
+                    term = RB_AT(v1, di, kGalH1) * pv;
                 }
                 __syncwarp();
-                if (half == 0 && sl >= 0) v2[sl] += term;
+                if (half == 0 && sl >= 0) RB_AT(v2, sl, kGalH2) += term;
                 __syncwarp();
-                if (half == 1 && sl >= 0) v2[sl] += term;
+                if (half == 1 && sl >= 0) RB_AT(v2, sl, kGalH2) += term;
                 __syncwarp();
             }
             if (__any_sync(0xffffffffu, full)) {
@@ -711,7 +720,7 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
                 continue;
             }
             m = gal_compact(k2, v2, kGalH2, lane, true);
-            gal_sort(k2, v2, m, lane);
+            gal_sort(k2, v2, m, kGalH2, lane);
         }
         // stage the row (any free place: the copy below puts rows in order)
         unsigned long long pos = 0;
@@ -722,8 +731,8 @@ __global__ void __launch_bounds__(kGalWarps * 32) mg_galerkin_kernel(
             continue;
         }
         for (int i = lane; i < m; i += 32) {
-            tcol[pos + i] = k2[i];
-            tval[pos + i] = v2[i];
+            RB_AT(tcol, pos + i, cap) = RB_AT(k2, i, kGalH2);
+            RB_AT(tval, pos + i, cap) = RB_AT(v2, i, kGalH2);
         }
         if (lane == 0) {
             count[c] = m;
@@ -740,16 +749,21 @@ __global__ void __launch_bounds__(kT) mg_galerkin_place_kernel(int64_t Nc, const
                                                                const int* __restrict__ tcol,
                                                                const double* __restrict__ tval,
                                                                int* __restrict__ ccol, double* __restrict__ cval,
-                                                               float* __restrict__ cval32) {
+                                                               float* __restrict__ cval32, int64_t tcap,
+                                                               int64_t cnnz) {
+    (void)tcap;  // staged and placed entries: bounds of the checked build's tests
+    (void)cnnz;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < Nc; c += nw) {
         const int64_t o = crow[c], len = crow[c + 1] - o, s = start[c];
+        RB_SPAN(s, len, tcap);
+        RB_SPAN(o, len, cnnz);
         for (int64_t i = lane; i < len; i += 32) {
-            const double v = tval[s + i];
-            ccol[o + i] = tcol[s + i];
-            cval[o + i] = v;
-            cval32[o + i] = __double2float_rn(v);
+            const double v = RB_AT(tval, s + i, tcap);
+            RB_AT(ccol, o + i, cnnz) = RB_AT(tcol, s + i, tcap);
+            RB_AT(cval, o + i, cnnz) = v;
+            RB_AT(cval32, o + i, cnnz) = __double2float_rn(v);
         }
     }
 }
@@ -952,7 +966,7 @@ int coarsen(const MgLevel& L, MgLevel& C, const MgScratch& s, cudaStream_t st, i
         RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
         if ((int64_t)cnt > N / 2) continue;
         if (cnt <= kMgK) return RBFFD_ERR_INVALID_ARG;  // degenerate node set
-        mg_gather_kernel<<<blocks_for(N), kT, 0, st>>>(xy, L.mask, N, s.sel, s.pos,
+        mg_gather_kernel<<<blocks_for(N), kT, 0, st>>>(xy, L.mask, N, s.sel, s.pos, (int64_t)cnt,
                                                        reinterpret_cast<double2*>(const_cast<double*>(C.xy)),
                                                        const_cast<uint8_t*>(C.mask));
         note_launches(1);
@@ -1032,10 +1046,10 @@ void restrict_to(const MgLevel& L, int64_t nc, const T* r, T* bc, const int* fla
     const int g = blocks_for(nc * L.rtpr);
     const T* val = Sel<T>::rval(L);
     switch (L.rtpr) {
-        case 8: mg_restrict_kernel<T, 8><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
-        case 4: mg_restrict_kernel<T, 4><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
-        case 2: mg_restrict_kernel<T, 2><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
-        default: mg_restrict_kernel<T, 1><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, bc, flag); break;
+        case 8: mg_restrict_kernel<T, 8><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, L.N, bc, flag); break;
+        case 4: mg_restrict_kernel<T, 4><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, L.N, bc, flag); break;
+        case 2: mg_restrict_kernel<T, 2><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, L.N, bc, flag); break;
+        default: mg_restrict_kernel<T, 1><<<g, kT, 0, st>>>(L.rrow, L.rcol, val, nc, r, L.N, bc, flag); break;
     }
 }
 
@@ -1103,7 +1117,7 @@ T* cycle_level(const MgHierarchy& h, int l, const void* bin, bool b_is_double, d
     restrict_to<T>(L, C.N, Sel<T>::r(L), Sel<T>::b(C), flag, st);
     *launches += 2;
     T* e = cycle_level<T>(h, l + 1, Sel<T>::b(C), false, nullptr, flag, st, launches, ev);
-    mg_prolong_kernel<T><<<blocks_for(L.N), kT, 0, st>>>(L.N, L.pidx, Sel<T>::pval(L), e, cur, flag);
+    mg_prolong_kernel<T><<<blocks_for(L.N), kT, 0, st>>>(L.N, L.pidx, Sel<T>::pval(L), e, C.N, cur, flag);
     ++*launches;
     // post-smoothing; the last sweep of level 0 writes the FP64 output
     for (int k = 0; k < h.nu; ++k) {
@@ -1389,7 +1403,7 @@ int rbffd::mg_adjoint_of(const MgHierarchy& F, const rbffd_csr* AT, const float*
         P.dtype = 0;
         if ((rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, nullptr, s.tr_ws, s.tr_bytes, st)) != RBFFD_OK) return rc;
         mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
-        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, (double)nc / (double)L.N,
+        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, nc, (double)nc / (double)L.N,
                                                                  L.pval, L.pval32);
         note_launches(4);
         RBFFD_LAUNCH_CHECK();
@@ -1492,7 +1506,7 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
         int rc = rbffd_transpose(&P, L.rrow, L.rcol, L.rval, nullptr, s.tr_ws, s.tr_bytes, st);
         if (rc != RBFFD_OK) return rc;
         mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
-        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, (double)nc / (double)L.N,
+        mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, nc, (double)nc / (double)L.N,
                                                                  L.pval, L.pval32);
         note_launches(3);
         RBFFD_LAUNCH_CHECK();
@@ -1510,11 +1524,11 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
             if (!large)
                 mg_galerkin_kernel<512, 256><<<sm_count() * 6, kGalWarps * 32, gal_smem_bytes<512, 256>(), st>>>(
                     nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
-                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over);
+                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over, L.N, L.nnz);
             else
                 mg_galerkin_kernel<1024, 512><<<sm_count() * 3, kGalWarps * 32, gal_smem_bytes<1024, 512>(), st>>>(
                     nc, L.rrow, L.rcol, L.rval, L.row_ptr, L.col, L.val, L.pidx, L.pval, C.mask, cnt, s.gal_start,
-                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over);
+                    s.gal_total, stage_cap, s.gal_col, s.gal_val, over, L.N, L.nnz);
             note_launches(1);
             RBFFD_LAUNCH_CHECK();
             RBFFD_CUDA_TRY(exclusive_scan<int64_t>(CountLoad64{cnt}, nc, crow, s.sums64, crow + nc, st));
@@ -1530,7 +1544,7 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
         mg_galerkin_place_kernel<<<blocks_for(nc * 32), kT, 0, st>>>(nc, s.gal_start, crow, s.gal_col, s.gal_val,
                                                                      const_cast<int*>(C.col),
                                                                      const_cast<double*>(C.val),
-                                                                     const_cast<float*>(C.val32));
+                                                                     const_cast<float*>(C.val32), stage_cap, cnnz);
         C.nnz = cnnz;
         C.tpr = tpr_for(nc, cnnz);
         mg_diag_kernel<<<blocks_for(nc), kT, 0, st>>>(C.row_ptr, C.col, C.val, nc, 0, C.mask, h.omega, C.dinv,
@@ -1665,7 +1679,7 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
             // the transpose of the forward cycle: restrict with P^T, prolong
             // with R^T = (N_c / N_f) P without the coarse Dirichlet columns
             mg_rscale_kernel<<<blocks_for(nc), kT, 0, st>>>(L.rrow, nc, nullptr, 1.0, L.rval, L.rval32);
-            mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, cscale, L.pval, L.pval32);
+            mg_pscale_kernel<<<blocks_for(L.N * kMgK), kT, 0, st>>>(L.N, L.pidx, C.mask, nc, cscale, L.pval, L.pval32);
             note_launches(1);
         }
         note_launches(1);

@@ -123,7 +123,11 @@ __device__ __forceinline__ T ldv(const T* p) {
 template <bool NC>
 __device__ __forceinline__ void row_dot(const int* __restrict__ col, const float* __restrict__ val,
                                         const float* __restrict__ x, int64_t a, int64_t e, int R, int lane,
-                                        bool on0, bool on1, float& s0, float& s1) {
+                                        bool on0, bool on1, float& s0, float& s1, const float* xlo, int64_t nx) {
+    // (xlo, nx: the gathered entries lie in xlo[0 .. nx), the bound of the
+    // checked build's tests)
+    (void)xlo;
+    (void)nx;
     float t0 = 0.f, t1 = 0.f, u0 = 0.f, u1 = 0.f;
     int64_t q = a;
     for (; q + 8 <= e; q += 8) {
@@ -137,8 +141,8 @@ __device__ __forceinline__ void row_dot(const int* __restrict__ col, const float
         float x0[8], x1[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            x0[i] = on0 ? ldv<NC>(x + c[i] + lane) : 0.f;
-            x1[i] = on1 ? ldv<NC>(x + c[i] + lane + 32) : 0.f;
+            x0[i] = on0 ? ldv<NC>(&RB_PT(x + c[i] + lane, xlo, nx)) : 0.f;
+            x1[i] = on1 ? ldv<NC>(&RB_PT(x + c[i] + lane + 32, xlo, nx)) : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
@@ -153,16 +157,18 @@ __device__ __forceinline__ void row_dot(const int* __restrict__ col, const float
         const int64_t c2 = (int64_t)__ldg(col + q + 2) * R, c3 = (int64_t)__ldg(col + q + 3) * R;
         const float v0 = __ldg(val + q), v1 = __ldg(val + q + 1), v2 = __ldg(val + q + 2), v3 = __ldg(val + q + 3);
         if (on0) {
-            const float x0 = ldv<NC>(x + c0 + lane), x1 = ldv<NC>(x + c1 + lane);
-            const float x2 = ldv<NC>(x + c2 + lane), x3 = ldv<NC>(x + c3 + lane);
+            const float x0 = ldv<NC>(&RB_PT(x + c0 + lane, xlo, nx)), x1 = ldv<NC>(&RB_PT(x + c1 + lane, xlo, nx));
+            const float x2 = ldv<NC>(&RB_PT(x + c2 + lane, xlo, nx)), x3 = ldv<NC>(&RB_PT(x + c3 + lane, xlo, nx));
             t0 = fmaf(v0, x0, t0);
             u0 = fmaf(v1, x1, u0);
             t0 = fmaf(v2, x2, t0);
             u0 = fmaf(v3, x3, u0);
         }
         if (on1) {
-            const float x0 = ldv<NC>(x + c0 + lane + 32), x1 = ldv<NC>(x + c1 + lane + 32);
-            const float x2 = ldv<NC>(x + c2 + lane + 32), x3 = ldv<NC>(x + c3 + lane + 32);
+            const float x0 = ldv<NC>(&RB_PT(x + c0 + lane + 32, xlo, nx));
+            const float x1 = ldv<NC>(&RB_PT(x + c1 + lane + 32, xlo, nx));
+            const float x2 = ldv<NC>(&RB_PT(x + c2 + lane + 32, xlo, nx));
+            const float x3 = ldv<NC>(&RB_PT(x + c3 + lane + 32, xlo, nx));
             t1 = fmaf(v0, x0, t1);
             u1 = fmaf(v1, x1, u1);
             t1 = fmaf(v2, x2, t1);
@@ -172,8 +178,8 @@ __device__ __forceinline__ void row_dot(const int* __restrict__ col, const float
     for (; q < e; ++q) {
         const float v = __ldg(val + q);
         const int64_t c = (int64_t)__ldg(col + q) * R;
-        if (on0) t0 = fmaf(v, ldv<NC>(x + c + lane), t0);
-        if (on1) t1 = fmaf(v, ldv<NC>(x + c + lane + 32), t1);
+        if (on0) t0 = fmaf(v, ldv<NC>(&RB_PT(x + c + lane, xlo, nx)), t0);
+        if (on1) t1 = fmaf(v, ldv<NC>(&RB_PT(x + c + lane + 32, xlo, nx)), t1);
     }
     s0 = t0 + u0;
     s1 = t1 + u1;
@@ -188,6 +194,7 @@ __device__ __forceinline__ void tile_first(const MbUnit& U, const MbLevel* Dp, i
     const float* __restrict__ b = Dp->b;
     float* __restrict__ x = Dp->x;
     const int64_t roff = Dp->row_off;
+    RB_SPAN(U.lo, U.hi - U.lo, Dp->N);
     MB_ROW_LOOP(i) {
         const int64_t g = (roff + i) * R;
         const float di = __ldg(dinv + i);
@@ -212,10 +219,11 @@ __device__ __forceinline__ void tile_sweep(const MbUnit& U, const MbLevel* Dp, i
     float* __restrict__ xo = MODE == 1 ? Dp->r : (dir ? Dp->x : Dp->t);
     const float* __restrict__ b = Dp->b;
     const int64_t roff = Dp->row_off;
+    RB_SPAN(U.lo, U.hi - U.lo, Dp->N);
     MB_ROW_LOOP(i) {
         const int64_t a = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1);
         float s0, s1;
-        row_dot<NC>(col, val, xi, a, e, R, lane, on0, on1, s0, s1);
+        row_dot<NC>(col, val, xi, a, e, R, lane, on0, on1, s0, s1, xi + roff * R, Dp->N * R);
         const int64_t g = (roff + i) * R;
         const float di = __ldg(dinv + i);
         if (on0) {
@@ -243,10 +251,11 @@ __device__ __forceinline__ void tile_restrict(const MbUnit& U, const MbLevel* Dp
     const float* __restrict__ rval = Dp->rval;
     const float* __restrict__ r = Dp->r + Dp->row_off * R;
     float* __restrict__ y = Dp->b_next;
+    RB_SPAN(U.lo, U.hi - U.lo, Dp->N_next);
     MB_ROW_LOOP(i) {
         const int64_t a = __ldg(rrow + i), e = __ldg(rrow + i + 1);
         float s0, s1;
-        row_dot<NC>(rcol, rval, r, a, e, R, lane, on0, on1, s0, s1);
+        row_dot<NC>(rcol, rval, r, a, e, R, lane, on0, on1, s0, s1, r, Dp->N * R);
         if (on0) y[i * R + lane] = s0;
         if (on1) y[i * R + lane + 32] = s1;
     }
@@ -261,6 +270,7 @@ __device__ __forceinline__ void tile_prolong(const MbUnit& U, const MbLevel* Dp,
     const float* __restrict__ pval = Dp->pval;
     const float* __restrict__ en = Dp->e_next;
     float* __restrict__ xb = (dir ? Dp->t : Dp->x) + Dp->row_off * R;
+    RB_SPAN(U.lo, U.hi - U.lo, Dp->N);
     MB_ROW_LOOP(i) {
         float* x = xb + i * R;
         float s0 = on0 ? x[lane] : 0.f, s1 = on1 ? x[lane + 32] : 0.f;
@@ -268,8 +278,8 @@ __device__ __forceinline__ void tile_prolong(const MbUnit& U, const MbLevel* Dp,
         for (int j = 0; j < kMgK; ++j) {
             const float a = __ldg(pval + i * kMgK + j);
             const int64_t c = (int64_t)__ldg(pidx + i * kMgK + j) * R;
-            if (on0) s0 = fmaf(a, ldv<NC>(en + c + lane), s0);
-            if (on1) s1 = fmaf(a, ldv<NC>(en + c + lane + 32), s1);
+            if (on0) s0 = fmaf(a, ldv<NC>(&RB_PT(en + c + lane, en, Dp->N_next * R)), s0);
+            if (on1) s1 = fmaf(a, ldv<NC>(&RB_PT(en + c + lane + 32, en, Dp->N_next * R)), s1);
         }
         if (on0) x[lane] = s0;
         if (on1) x[lane + 32] = s1;
@@ -287,6 +297,7 @@ __device__ __forceinline__ void tile_dense(const MbUnit& U, const MbLevel* Dp, i
     const float* __restrict__ b = Dp->b;
     float* __restrict__ x = Dp->x;
     const int64_t n = Dp->N, roff = Dp->row_off;
+    RB_SPAN(U.lo, U.hi - U.lo, n);
     MB_ROW_LOOP(i) {
         float s0 = 0.f, s1 = 0.f;
         for (int64_t j = 0; j < n; ++j) {
@@ -369,15 +380,16 @@ __global__ void __launch_bounds__(kMbT) mb_dense_kernel(const MbUnit* __restrict
 // status[0]: stop (set on a timeout); status[1]: a wait ran out.
 __global__ void __launch_bounds__(kMbT) mb_coarse_kernel(const MbTask* __restrict__ tasks, int ntasks,
                                                          const MbLevel* __restrict__ descs, int R, int* head,
-                                                         int* done, int* status, long long spin_limit,
+                                                         int* done, int ncount, int* status, long long spin_limit,
                                                          const int* live) {
+    (void)ncount;  // counters: bound of the checked build's tests
     __shared__ int s_task, s_go;
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(head, 1);
             int go = t < ntasks && *(volatile int*)status == 0;
             if (go && tasks[t].wait >= 0) {
-                const int* c = done + tasks[t].wait;
+                const int* c = &RB_AT(done, tasks[t].wait, ncount);
                 const int need = tasks[t].need;
                 long long polls = 0;
                 while (*(volatile const int*)c < need) {
@@ -420,7 +432,7 @@ __global__ void __launch_bounds__(kMbT) mb_coarse_kernel(const MbTask* __restric
         __syncthreads();  // every thread's writes of the tile ...
         if (threadIdx.x == 0) {
             __threadfence();  // ... before the tile counts as done
-            atomicAdd(done + T.post, 1);
+            atomicAdd(&RB_AT(done, T.post, ncount), 1);
         }
     }
 }
@@ -677,8 +689,8 @@ int mg_batch_apply_df(const MgBatch& B, int R, const float2* b, float2* x, const
     // levels >= 1 of every instance: one persistent launch
     if (pers && B.a_n[0]) {
         RBFFD_CUDA_TRY(cudaMemsetAsync(B.head, 0, sizeof(int) * (2 + (size_t)B.ncount), st));
-        mb_coarse_kernel<<<B.coarse_grid, kMbT, 0, st>>>(B.tasks, B.ntasks, D, R, B.head, B.done, B.status,
-                                                          B.spin_limit, live);
+        mb_coarse_kernel<<<B.coarse_grid, kMbT, 0, st>>>(B.tasks, B.ntasks, D, R, B.head, B.done, B.ncount,
+                                                          B.status, B.spin_limit, live);
         ++n;
     }
     // ascend

@@ -20,7 +20,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* sh, T& total) {
         T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) sh[wid] = x;
+    if (lane == 31) RB_AT(sh, wid, kScanThreads / 32) = x;
     __syncthreads();
     if (wid == 0) {
         T w = (lane < kScanThreads / 32) ? sh[lane] : T(0);
@@ -32,7 +32,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* sh, T& total) {
         if (lane < kScanThreads / 32) sh[lane] = w;
     }
     __syncthreads();
-    T warp_prefix = (wid > 0) ? sh[wid - 1] : T(0);
+    T warp_prefix = (wid > 0) ? RB_AT(sh, wid - 1, kScanThreads / 32) : T(0);
     total = sh[kScanThreads / 32 - 1];
     __syncthreads();
     return warp_prefix + x - v;

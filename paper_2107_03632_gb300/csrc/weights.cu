@@ -83,6 +83,10 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
     // coordinate scratch of 2n doubles past the matrix, when the zero block
     // is too small to hold it
     double* cx = A + (size_t)M * LD;
+    // entry i of the warp's region (tested against it in the checked build,
+    // whose first test is that the region lies in the launch's shared memory)
+    (void)RB_SH(A + (size_t)smem_doubles - 1);
+    auto a = [&](size_t i) -> double& { return RB_AT(A, i, smem_doubles); };
     const int total_warps = gridDim.x * wpb;
 
     for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
@@ -93,8 +97,8 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         // Coordinates go to a linear scratch of 2n doubles.  In the zero
         // block, entry t is stored at row n + t / s, column n + t % s.
         auto cs = [&](int t) -> double& {
-            if (coords_zb) return A[(size_t)(n + t / s) * LD + n + t % s];
-            return cx[t];
+            if (coords_zb) return a((size_t)(n + t / s) * LD + n + t % s);
+            return RB_AT(cx, t, 2 * n);
         };
         unsigned long long dmax = 0;
         int bad_index = 0;
@@ -142,14 +146,14 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                 const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
                 coincident |= (dx == 0.0 && dy == 0.0) ? 1 : 0;
                 const double phi = __dmul_rn(__dmul_rn(r, r), r);
-                A[(size_t)j * LD + k] = phi;
-                A[(size_t)k * LD + j] = phi;
+                a((size_t)j * LD + k) = phi;
+                a((size_t)k * LD + j) = phi;
             }
             for (int j = lane; j < n; j += 32) {
-                A[(size_t)j * LD + j] = 0.0;
+                a((size_t)j * LD + j) = 0.0;
                 const double xh = cs(2 * j), yh = cs(2 * j + 1);
                 const double rj = __dsqrt_rn(__dadd_rn(__dmul_rn(xh, xh), __dmul_rn(yh, yh)));
-                A[(size_t)j * LD + M] = op ? __dmul_rn(__dmul_rn(rj, rj), rj) : __dmul_rn(9.0, rj);
+                a((size_t)j * LD + M) = op ? __dmul_rn(__dmul_rn(rj, rj), rj) : __dmul_rn(9.0, rj);
                 // monomials x^a y^b, graded order; powers by repeated products
                 double xp[9], yp[9];
                 xp[0] = 1.0;
@@ -163,8 +167,8 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                 for (int d = 0; d <= m; ++d) {
                     for (int i = 0; i <= d; ++i) {
                         const double v = (d == 0) ? 1.0 : __dmul_rn(xp[d - i], yp[i]);
-                        A[(size_t)j * LD + n + col] = v;  // P
-                        A[(size_t)(n + col) * LD + j] = v;  // P^T
+                        a((size_t)j * LD + n + col) = v;  // P
+                        a((size_t)(n + col) * LD + j) = v;  // P^T
                         ++col;
                     }
                 }
@@ -172,13 +176,13 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         }
         __syncwarp();
         // zero block and polynomial RHS (coordinates no longer needed)
-        for (int t = lane; t < s * s; t += 32) A[(size_t)(n + t / s) * LD + n + t % s] = 0.0;
+        for (int t = lane; t < s * s; t += 32) a((size_t)(n + t / s) * LD + n + t % s) = 0.0;
         {
             int col = 0;
             for (int d = 0; d <= m; ++d)
                 for (int i = 0; i <= d; ++i, ++col)
                     if (lane == 0)
-                        A[(size_t)(n + col) * LD + M] =
+                        a((size_t)(n + col) * LD + M) =
                             op ? (d == 0 ? 1.0 : 0.0) : ((d == 2 && (i == 0 || i == 2)) ? 2.0 : 0.0);
         }
         __syncwarp();
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
             unsigned long long best = 0;
             int bi = k;
             for (int i = k + lane; i < M; i += 32) {
-                const unsigned long long b = abs_bits(A[(size_t)i * LD + k]);
+                const unsigned long long b = abs_bits(a((size_t)i * LD + k));
                 if (b > best) {  // ascending i per lane: keeps the first maximum
                     best = b;
                     bi = i;
@@ -211,18 +215,18 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
             }
             if (bi != k) {
                 for (int j = k + lane; j <= M; j += 32) {
-                    const double t = A[(size_t)k * LD + j];
-                    A[(size_t)k * LD + j] = A[(size_t)bi * LD + j];
-                    A[(size_t)bi * LD + j] = t;
+                    const double t = a((size_t)k * LD + j);
+                    a((size_t)k * LD + j) = a((size_t)bi * LD + j);
+                    a((size_t)bi * LD + j) = t;
                 }
             }
             __syncwarp();
             // the pivot's reciprocal replaces the pivot (only the back
             // substitution reads it again, and multiplies by it)
-            const double inv = rcp64(A[(size_t)k * LD + k]);
-            for (int i = k + 1 + lane; i < M; i += 32) A[(size_t)i * LD + k] = __dmul_rn(A[(size_t)i * LD + k], inv);
+            const double inv = rcp64(a((size_t)k * LD + k));
+            for (int i = k + 1 + lane; i < M; i += 32) a((size_t)i * LD + k) = __dmul_rn(a((size_t)i * LD + k), inv);
             __syncwarp();
-            if (lane == 0) A[(size_t)k * LD + k] = inv;
+            if (lane == 0) a((size_t)k * LD + k) = inv;
             // trailing update, flattened over rows i in (k, M), cols j in (k, M]
             const int R = M - k - 1, C = M - k;
             if (R > 0) {
@@ -246,17 +250,23 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                     double* r1 = A + (size_t)(k + 1 + i1) * LD + k;
                     double* r2 = A + (size_t)(k + 1 + i2) * LD + k;
                     double* r3 = A + (size_t)(k + 1 + i3) * LD + k;
-                    const double l0 = r0[0], l1 = r1[0], l2 = r2[0], l3 = r3[0];
-                    const double u0 = prow[j0], u1 = prow[j1], u2 = prow[j2], u3 = prow[j3];
-                    const double a0 = r0[1 + j0], a1 = r1[1 + j1], a2 = r2[1 + j2], a3 = r3[1 + j3];
-                    r0[1 + j0] = fma(-l0, u0, a0);
-                    r1[1 + j1] = fma(-l1, u1, a1);
-                    r2[1 + j2] = fma(-l2, u2, a2);
-                    r3[1 + j3] = fma(-l3, u3, a3);
+                    const int L = smem_doubles;
+                    const double l0 = RB_PT(r0, A, L), l1 = RB_PT(r1, A, L), l2 = RB_PT(r2, A, L),
+                                 l3 = RB_PT(r3, A, L);
+                    const double u0 = RB_PT(prow + j0, A, L), u1 = RB_PT(prow + j1, A, L),
+                                 u2 = RB_PT(prow + j2, A, L), u3 = RB_PT(prow + j3, A, L);
+                    const double a0 = RB_PT(r0 + 1 + j0, A, L), a1 = RB_PT(r1 + 1 + j1, A, L),
+                                 a2 = RB_PT(r2 + 1 + j2, A, L), a3 = RB_PT(r3 + 1 + j3, A, L);
+                    RB_PT(r0 + 1 + j0, A, L) = fma(-l0, u0, a0);
+                    RB_PT(r1 + 1 + j1, A, L) = fma(-l1, u1, a1);
+                    RB_PT(r2 + 1 + j2, A, L) = fma(-l2, u2, a2);
+                    RB_PT(r3 + 1 + j3, A, L) = fma(-l3, u3, a3);
                 }
                 for (; e < total; e += 32) {
                     double* r0 = A + (size_t)(k + 1 + ii) * LD + k;
-                    r0[1 + jj] = fma(-r0[0], prow[jj], r0[1 + jj]);
+                    RB_PT(r0 + 1 + jj, A, smem_doubles) = fma(-RB_PT(r0, A, smem_doubles),
+                                                              RB_PT(prow + jj, A, smem_doubles),
+                                                              RB_PT(r0 + 1 + jj, A, smem_doubles));
                     ii += si;
                     jj += sj;
                     if (jj >= C) { jj -= C; ++ii; }
@@ -268,10 +278,11 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         // ---- back substitution on U x = b' (b' in column M) -----------------
         if (!singular) {
             for (int j = M - 1; j >= 0; --j) {
-                const double xj = __dmul_rn(A[(size_t)j * LD + M], A[(size_t)j * LD + j]);
+                const double xj = __dmul_rn(a((size_t)j * LD + M), a((size_t)j * LD + j));
                 __syncwarp();
-                for (int i = lane; i < j; i += 32) A[(size_t)i * LD + M] = fma(-A[(size_t)i * LD + j], xj, A[(size_t)i * LD + M]);
-                if (lane == 0) A[(size_t)j * LD + M] = xj;
+                for (int i = lane; i < j; i += 32)
+                    a((size_t)i * LD + M) = fma(-a((size_t)i * LD + j), xj, a((size_t)i * LD + M));
+                if (lane == 0) a((size_t)j * LD + M) = xj;
                 __syncwarp();
             }
         }
@@ -280,12 +291,12 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
         int bad = singular;
         double* wout = w + (int64_t)node * n;
         for (int j = lane; j < n; j += 32) {
-            const double v = singular ? 0.0 : (op ? A[(size_t)j * LD + M] : __ddiv_rn(A[(size_t)j * LD + M], delta2));
+            const double v = singular ? 0.0 : (op ? a((size_t)j * LD + M) : __ddiv_rn(a((size_t)j * LD + M), delta2));
             if (!isfinite(v)) bad = 1;
-            A[(size_t)j * LD + M] = v;
+            a((size_t)j * LD + M) = v;
         }
         bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
-        for (int j = lane; j < n; j += 32) wout[j] = bad ? 0.0 : A[(size_t)j * LD + M];
+        for (int j = lane; j < n; j += 32) wout[j] = bad ? 0.0 : a((size_t)j * LD + M);
         if (node_status && lane == 0) node_status[node] = bad;
         __syncwarp();
     }
@@ -357,8 +368,8 @@ NsGeom ns_geom(int n, int m) {
 // (NT = 64 or 128, one stencil per block).
 template <int NT>
 __device__ __forceinline__ unsigned group_mask() {
-    if (NT >= 32) return 0xffffffffu;
-    return ((1u << NT) - 1u) << ((threadIdx.x & 31) & ~(NT - 1));
+    if constexpr (NT >= 32) return 0xffffffffu;
+    else return ((1u << NT) - 1u) << ((threadIdx.x & 31) & ~(NT - 1));
 }
 
 // Shuffle offset the in-warp reductions start from.
@@ -386,7 +397,7 @@ __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v
     if (NT <= 32) return v;
     constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    if ((threadIdx.x & 31) == 0) RB_AT(sh, w, W) = v;
     __syncthreads();
     unsigned long long r = sh[0];
 #pragma unroll
@@ -403,9 +414,9 @@ __device__ __forceinline__ void group_argmax(unsigned long long& best, int& bi, 
     constexpr int W = NT / 32;
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        shb[w] = best;
-        shi[2 * w] = bi;
-        shi[2 * w + 1] = bpos;
+        RB_AT(shb, w, W) = best;
+        RB_AT(shi, 2 * w, 2 * W) = bi;
+        RB_AT(shi, 2 * w + 1, 2 * W) = bpos;
     }
     __syncthreads();
     best = shb[0];
@@ -565,6 +576,13 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     double* crdd = reinterpret_cast<double*>(crd);
     double* scal = reinterpret_cast<double*>(wv);
     const int total_warps = gridDim.x * wpb;
+    // loads and stores of the group's region (tested against it in the
+    // checked build, whose first test is that the region lies in the launch's
+    // shared memory)
+    const int region = bytes_per_warp / (int)sizeof(S);
+    (void)RB_SH(smem_raw + (size_t)(wib + 1) * bytes_per_warp - 1);
+    auto ldc = [&](const S* p) -> V { return R::ld(&RB_PT(p, Phi, region)); };
+    auto stc = [&](S* p, V v) { R::st(&RB_PT(p, Phi, region), v); };
 
     for (int node = blockIdx.x * wpb + wib; node < N; node += total_warps) {
         const int* sten = idx + (int64_t)node * n;
@@ -580,8 +598,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             const double2 p = ok ? xy[sj] : c;
             const double dx = __dadd_rn(p.x, -c.x);
             const double dy = __dadd_rn(p.y, -c.y);
-            crdd[2 * j] = dx;
-            crdd[2 * j + 1] = dy;
+            RB_AT(crdd, 2 * j, 2 * n) = dx;
+            RB_AT(crdd, 2 * j + 1, 2 * n) = dy;
             const unsigned long long b = abs_bits(fma(dx, dx, __dmul_rn(dy, dy)));
             dmax = (b > dmax) ? b : dmax;
         }
@@ -603,7 +621,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
 
         // interpolation at a point that is its own first neighbour (a fine
         // node kept on the coarse level): the weights are e_1, the value there
-        if (op && !bad_any && abs_bits(crdd[0]) == 0ull && abs_bits(crdd[1]) == 0ull) {
+        if (op && !bad_any && abs_bits(RB_AT(crdd, 0, 2 * n)) == 0ull && abs_bits(RB_AT(crdd, 1, 2 * n)) == 0ull) {
             double* wo = w + (int64_t)node * n;
             for (int a = lane; a < n; a += NT) wo[a] = a == 0 ? 1.0 : 0.0;
             if (node_status && lane == 0) node_status[node] = 0;
@@ -615,27 +633,27 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         // degree d from degree d - 1 of the same row: x^(d-i) y^i = x * x^(d-1-i) y^i
         // for i < d, and y^d = y * y^(d-1)
         for (int j = lane; j < n; j += NT) {
-            const V xh = R::from_d(__dmul_rn(crdd[2 * j], inv_delta));
-            const V yh = R::from_d(__dmul_rn(crdd[2 * j + 1], inv_delta));
-            R::st(crd + 2 * j, xh);
-            R::st(crd + 2 * j + 1, yh);
+            const V xh = R::from_d(__dmul_rn(RB_AT(crdd, 2 * j, 2 * n), inv_delta));
+            const V yh = R::from_d(__dmul_rn(RB_AT(crdd, 2 * j + 1, 2 * n), inv_delta));
+            stc(crd + 2 * j, xh);
+            stc(crd + 2 * j + 1, yh);
             S* pr = P + (size_t)j * LDS;
-            R::st(pr, R::cst(1.0));
+            stc(pr, R::cst(1.0));
             if (m >= 1) {
-                R::st(pr + 1, xh);
-                R::st(pr + 2, yh);
+                stc(pr + 1, xh);
+                stc(pr + 2, yh);
             }
             for (int d = 2, prev = 1, cur = 3; d <= m; prev = cur, cur += d + 1, ++d) {
-                for (int i = 0; i < d; ++i) R::st(pr + cur + i, R::mul(xh, R::ld(pr + prev + i)));
-                R::st(pr + cur + d, R::mul(yh, R::ld(pr + prev + d - 1)));
+                for (int i = 0; i < d; ++i) stc(pr + cur + i, R::mul(xh, ldc(pr + prev + i)));
+                stc(pr + cur + d, R::mul(yh, ldc(pr + prev + d - 1)));
             }
-            act[j] = j;
+            RB_AT(act, j, n) = j;
         }
         for (int col = lane; col < s; col += NT) {
             // g_k = lap p_k(0): 2 for x^2 (index 3) and y^2 (index 5);
             // interpolation: p_k(0), 1 for the constant
             const bool one = op ? (col == 0) : (col == 3 || col == 5);
-            R::st(P + (size_t)n * LDS + col, one ? R::cst(op ? 1.0 : 2.0) : R::zero());
+            stc(P + (size_t)n * LDS + col, one ? R::cst(op ? 1.0 : 2.0) : R::zero());
         }
         group_sync<NT>();
 
@@ -646,8 +664,8 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             unsigned long long best = 0;
             int bi = 0x7fffffff, bpos = -1;
             for (int t = lane; t < na; t += NT) {
-                const int r = act[t];
-                const unsigned long long b = R::key(R::ld(P + (size_t)r * LDS + k));
+                const int r = RB_AT(act, t, n);
+                const unsigned long long b = R::key(ldc(P + (size_t)r * LDS + k));
                 if (b > best || (b == best && r < bi)) {
                     best = b;
                     bi = r;
@@ -677,18 +695,18 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             // substitutions); every thread has finished the search above
             // (shuffles, or the block barriers of group_argmax)
             if (lane == 0) {
-                R::st(tv, R::rcp(R::ld(P + (size_t)pr * LDS + k)));
-                perm[k] = pr;
-                act[bpos] = act[na - 1];  // swap-remove the pivot row
+                stc(tv, R::rcp(ldc(P + (size_t)pr * LDS + k)));
+                RB_AT(perm, k, n) = pr;
+                RB_AT(act, bpos, n) = RB_AT(act, na - 1, n);  // swap-remove the pivot row
             }
             --na;
             group_sync<NT>();
-            const V inv = R::ld(tv);
+            const V inv = ldc(tv);
             // every active row and the g row: column k scaled by the pivot
             // reciprocal (pivot row -> e_k) ...
             for (int t = lane; t <= na; t += NT) {
-                S* rr = P + (size_t)((t < na) ? act[t] : n) * LDS;
-                R::st(rr + k, R::mul(R::ld(rr + k), inv));
+                S* rr = P + (size_t)((t < na) ? RB_AT(act, t, n) : n) * LDS;
+                stc(rr + k, R::mul(ldc(rr + k), inv));
             }
             group_sync<NT>();
             // ... then column j -= P[pr][j] * (scaled) P[r][k] for j != k,
@@ -701,9 +719,9 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 int t = lane / C, jj = lane - (lane / C) * C;
                 const int dt = NT / C, dj = NT - (NT / C) * C;
                 for (int e = lane; e < total; e += NT) {
-                    S* rr = P + (size_t)((t < na) ? act[t] : n) * LDS;
+                    S* rr = P + (size_t)((t < na) ? RB_AT(act, t, n) : n) * LDS;
                     const int j = jj < k ? jj : jj + 1;
-                    R::st(rr + j, R::nfma(R::ld(prow + j), R::ld(rr + k), R::ld(rr + j)));
+                    stc(rr + j, R::nfma(ldc(prow + j), ldc(rr + k), ldc(rr + j)));
                     t += dt;
                     jj += dj;
                     if (jj >= C) {
@@ -715,13 +733,13 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             group_sync<NT>();
         }
         if (!singular) {
-            for (int t = lane; t < q; t += NT) perm[s + t] = act[t];
+            for (int t = lane; t < q; t += NT) RB_AT(perm, s + t, n) = RB_AT(act, t, n);
             // X (rows of the non-pivot nodes) and w0 out of P, whose region
             // Phi takes next: X[j][k] = P[act[j]][k], w0[k] = P[n][k]
             for (int e = lane; e < (q + 1) * s; e += NT) {
                 const int j = e / s, k = e - (e / s) * s;
-                if (j < q) R::st(X + (size_t)j * LDX + k, R::ld(P + (size_t)act[j] * LDS + k));
-                else R::st(w0 + k, R::ld(P + (size_t)n * LDS + k));
+                if (j < q) stc(X + (size_t)j * LDX + k, ldc(P + (size_t)RB_AT(act, j, n) * LDS + k));
+                else stc(w0 + k, ldc(P + (size_t)n * LDS + k));
             }
         }
         group_sync<NT>();
@@ -736,30 +754,30 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while (a > 0 && a * (2 * n - a - 1) / 2 > pidx) --a;
                 while ((a + 1) * (2 * n - a - 2) / 2 <= pidx) ++a;
                 const int b = pidx - a * (2 * n - a - 1) / 2 + a + 1;  // a < b
-                const int ja = perm[a], jb = perm[b];
-                const V dx = R::sub(R::ld(crd + 2 * ja), R::ld(crd + 2 * jb));
-                const V dy = R::sub(R::ld(crd + 2 * ja + 1), R::ld(crd + 2 * jb + 1));
+                const int ja = RB_AT(perm, a, n), jb = RB_AT(perm, b, n);
+                const V dx = R::sub(ldc(crd + 2 * ja), ldc(crd + 2 * jb));
+                const V dy = R::sub(ldc(crd + 2 * ja + 1), ldc(crd + 2 * jb + 1));
                 const bool same = R::is_zero(dx) && R::is_zero(dy);
                 coincident |= same ? 1 : 0;
                 const V phi = same ? R::zero() : R::r3(dx, dy);
                 if (b < s) {
-                    R::st(A11 + (size_t)a * LDS + b, phi);
-                    R::st(A11 + (size_t)b * LDS + a, phi);
+                    stc(A11 + (size_t)a * LDS + b, phi);
+                    stc(A11 + (size_t)b * LDS + a, phi);
                 } else if (a < s) {
-                    R::st(A12 + (size_t)a * LDQ + (b - s), phi);
+                    stc(A12 + (size_t)a * LDQ + (b - s), phi);
                 } else {
                     const int i = b - s;
-                    R::st(A22 + (size_t)(i * (i + 1) / 2 + (a - s)), phi);
+                    stc(A22 + (size_t)(i * (i + 1) / 2 + (a - s)), phi);
                 }
             }
             for (int a = lane; a < n; a += NT) {
-                if (a < s) R::st(A11 + (size_t)a * LDS + a, R::zero());
-                else R::st(A22 + (size_t)((a - s) * (a - s + 1) / 2 + (a - s)), R::zero());
-                const int ja = perm[a];
-                const V xh = R::ld(crd + 2 * ja), yh = R::ld(crd + 2 * ja + 1);
+                if (a < s) stc(A11 + (size_t)a * LDS + a, R::zero());
+                else stc(A22 + (size_t)((a - s) * (a - s + 1) / 2 + (a - s)), R::zero());
+                const int ja = RB_AT(perm, a, n);
+                const V xh = ldc(crd + 2 * ja), yh = ldc(crd + 2 * ja + 1);
                 // f = lap |x - x_c|^3 = 9 |xh| at the centre; interpolation: |xh|^3
                 const V rr = R::add(R::mul(xh, xh), R::mul(yh, yh));
-                R::st(fv + a, R::mul(op ? rr : R::cst(9.0), R::sqrt(rr)));
+                stc(fv + a, R::mul(op ? rr : R::cst(9.0), R::sqrt(rr)));
             }
         }
         singular |= group_any<NT>(coincident) ? 1 : 0;
@@ -775,35 +793,35 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while ((j + 1) * (j + 2) / 2 <= e) ++j;
                 const int l = e - j * (j + 1) / 2;
                 const S* xl = X + (size_t)l * LDX;
-                V acc = R::ld(A22 + e), acc1 = R::zero();
+                V acc = ldc(A22 + e), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = R::nfma(R::ld(A12 + (size_t)k * LDQ + j), R::ld(xl + k), acc);
-                    acc1 = R::nfma(R::ld(A12 + (size_t)(k + 1) * LDQ + j), R::ld(xl + k + 1), acc1);
+                    acc = R::nfma(ldc(A12 + (size_t)k * LDQ + j), ldc(xl + k), acc);
+                    acc1 = R::nfma(ldc(A12 + (size_t)(k + 1) * LDQ + j), ldc(xl + k + 1), acc1);
                 }
-                if (k < s) acc = R::nfma(R::ld(A12 + (size_t)k * LDQ + j), R::ld(xl + k), acc);
-                R::st(A22 + e, R::add(acc, acc1));
+                if (k < s) acc = R::nfma(ldc(A12 + (size_t)k * LDQ + j), ldc(xl + k), acc);
+                stc(A22 + e, R::add(acc, acc1));
             }
             // ---- u = f - Phi[:, 0..s) w0 (rows r1 from A11, rows r2 from A12^T) ----
             for (int a = lane; a < n; a += NT) {
-                V acc = R::ld(fv + a), acc1 = R::zero();
+                V acc = ldc(fv + a), acc1 = R::zero();
                 int k = 0;
                 if (a < s) {
                     const S* pr = A11 + (size_t)a * LDS;
                     for (; k + 1 < s; k += 2) {
-                        acc = R::nfma(R::ld(pr + k), R::ld(w0 + k), acc);
-                        acc1 = R::nfma(R::ld(pr + k + 1), R::ld(w0 + k + 1), acc1);
+                        acc = R::nfma(ldc(pr + k), ldc(w0 + k), acc);
+                        acc1 = R::nfma(ldc(pr + k + 1), ldc(w0 + k + 1), acc1);
                     }
-                    if (k < s) acc = R::nfma(R::ld(pr + k), R::ld(w0 + k), acc);
+                    if (k < s) acc = R::nfma(ldc(pr + k), ldc(w0 + k), acc);
                 } else {
                     const S* pc = A12 + (a - s);
                     for (; k + 1 < s; k += 2) {
-                        acc = R::nfma(R::ld(pc + (size_t)k * LDQ), R::ld(w0 + k), acc);
-                        acc1 = R::nfma(R::ld(pc + (size_t)(k + 1) * LDQ), R::ld(w0 + k + 1), acc1);
+                        acc = R::nfma(ldc(pc + (size_t)k * LDQ), ldc(w0 + k), acc);
+                        acc1 = R::nfma(ldc(pc + (size_t)(k + 1) * LDQ), ldc(w0 + k + 1), acc1);
                     }
-                    if (k < s) acc = R::nfma(R::ld(pc + (size_t)k * LDQ), R::ld(w0 + k), acc);
+                    if (k < s) acc = R::nfma(ldc(pc + (size_t)k * LDQ), ldc(w0 + k), acc);
                 }
-                R::st(uv + a, R::add(acc, acc1));
+                stc(uv + a, R::add(acc, acc1));
             }
             group_sync<NT>();
             // ---- T = Phi12 - Phi11 X^T (s x q, in place in A12) --------------
@@ -812,26 +830,26 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 const S* xr = X + (size_t)j * LDX;
                 const S* pr = A11 + (size_t)a * LDS;
                 // two independent chains (latency, not issue, limits a single one)
-                V acc = R::ld(A12 + (size_t)a * LDQ + j), acc1 = R::zero();
+                V acc = ldc(A12 + (size_t)a * LDQ + j), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = R::nfma(R::ld(pr + k), R::ld(xr + k), acc);
-                    acc1 = R::nfma(R::ld(pr + k + 1), R::ld(xr + k + 1), acc1);
+                    acc = R::nfma(ldc(pr + k), ldc(xr + k), acc);
+                    acc1 = R::nfma(ldc(pr + k + 1), ldc(xr + k + 1), acc1);
                 }
-                if (k < s) acc = R::nfma(R::ld(pr + k), R::ld(xr + k), acc);
-                R::st(A12 + (size_t)a * LDQ + j, R::add(acc, acc1));
+                if (k < s) acc = R::nfma(ldc(pr + k), ldc(xr + k), acc);
+                stc(A12 + (size_t)a * LDQ + j, R::add(acc, acc1));
             }
             // ---- t = Z^T u = u[r2] - X u[r1] -------------------------------------
             for (int j = lane; j < q; j += NT) {
                 const S* xj = X + (size_t)j * LDX;
-                V acc = R::ld(uv + s + j), acc1 = R::zero();
+                V acc = ldc(uv + s + j), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = R::nfma(R::ld(xj + k), R::ld(uv + k), acc);
-                    acc1 = R::nfma(R::ld(xj + k + 1), R::ld(uv + k + 1), acc1);
+                    acc = R::nfma(ldc(xj + k), ldc(uv + k), acc);
+                    acc1 = R::nfma(ldc(xj + k + 1), ldc(uv + k + 1), acc1);
                 }
-                if (k < s) acc = R::nfma(R::ld(xj + k), R::ld(uv + k), acc);
-                R::st(tv + j, R::add(acc, acc1));
+                if (k < s) acc = R::nfma(ldc(xj + k), ldc(uv + k), acc);
+                stc(tv + j, R::add(acc, acc1));
             }
             group_sync<NT>();
             // ---- S = S' - X T (lower triangle, in place) ---------------------
@@ -841,14 +859,14 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                 while ((j + 1) * (j + 2) / 2 <= e) ++j;
                 const int l = e - j * (j + 1) / 2;
                 const S* xj = X + (size_t)j * LDX;
-                V acc = R::ld(A22 + e), acc1 = R::zero();
+                V acc = ldc(A22 + e), acc1 = R::zero();
                 int k = 0;
                 for (; k + 1 < s; k += 2) {
-                    acc = R::nfma(R::ld(xj + k), R::ld(A12 + (size_t)k * LDQ + l), acc);
-                    acc1 = R::nfma(R::ld(xj + k + 1), R::ld(A12 + (size_t)(k + 1) * LDQ + l), acc1);
+                    acc = R::nfma(ldc(xj + k), ldc(A12 + (size_t)k * LDQ + l), acc);
+                    acc1 = R::nfma(ldc(xj + k + 1), ldc(A12 + (size_t)(k + 1) * LDQ + l), acc1);
                 }
-                if (k < s) acc = R::nfma(R::ld(xj + k), R::ld(A12 + (size_t)k * LDQ + l), acc);
-                R::st(A22 + e, R::add(acc, acc1));
+                if (k < s) acc = R::nfma(ldc(xj + k), ldc(A12 + (size_t)k * LDQ + l), acc);
+                stc(A22 + e, R::add(acc, acc1));
             }
             group_sync<NT>();
             // ---- S = L D L^T: unit lower L in place, 1/D in fv -----------------
@@ -856,26 +874,26 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             // column goes to uv (free now), L[i][c] = S[i][c] / D[c], then
             // S[i][j] -= L[i][c] S[j][c] for c < j <= i.  The thread that
             // updates the next diagonal entry also forms its reciprocal and
-            // the singularity flag (act[0], free after the elimination).
+            // the singularity flag (RB_AT(act, 0, n), free after the elimination).
             if (q > 0) {
                 if (lane == 0) {
-                    const V d0 = R::ld(A22);
-                    act[0] = R::pos_finite(d0) ? 0 : 1;
-                    R::st(fv, R::rcp(d0));
+                    const V d0 = ldc(A22);
+                    RB_AT(act, 0, n) = R::pos_finite(d0) ? 0 : 1;
+                    stc(fv, R::rcp(d0));
                 }
                 group_sync<NT>();
             }
             for (int cI = 0; cI < q; ++cI) {
-                if (act[0]) {
+                if (RB_AT(act, 0, n)) {
                     singular = 1;
                     break;
                 }
-                const V invd = R::ld(fv + cI);
+                const V invd = ldc(fv + cI);
                 for (int i = cI + 1 + lane; i < q; i += NT) {
                     S* si = A22 + (size_t)(i * (i + 1) / 2);
-                    const V v = R::ld(si + cI);
-                    R::st(uv + i, v);
-                    R::st(si + cI, R::mul(v, invd));
+                    const V v = ldc(si + cI);
+                    stc(uv + i, v);
+                    stc(si + cI, R::mul(v, invd));
                 }
                 group_sync<NT>();
                 const int rem = q - cI - 1, ntr = rem * (rem + 1) / 2;
@@ -886,11 +904,11 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
                     const int j = e - i * (i + 1) / 2;
                     const int ri = cI + 1 + i;
                     S* si = A22 + (size_t)(ri * (ri + 1) / 2);
-                    const V nv = R::nfma(R::ld(si + cI), R::ld(uv + cI + 1 + j), R::ld(si + cI + 1 + j));
-                    R::st(si + cI + 1 + j, nv);
+                    const V nv = R::nfma(ldc(si + cI), ldc(uv + cI + 1 + j), ldc(si + cI + 1 + j));
+                    stc(si + cI + 1 + j, nv);
                     if (e == 0) {  // (i, j) = (0, 0): the next diagonal entry, final now
-                        act[0] = R::pos_finite(nv) ? 0 : 1;
-                        R::st(fv + cI + 1, R::rcp(nv));
+                        RB_AT(act, 0, n) = R::pos_finite(nv) ? 0 : 1;
+                        stc(fv + cI + 1, R::rcp(nv));
                     }
                 }
                 group_sync<NT>();
@@ -899,31 +917,31 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         if (!singular) {
             // ---- L y = t, z = D^-1 y, L^T x = z (unit triangles) -----------------
             for (int cI = 0; cI < q; ++cI) {
-                const V yc = R::ld(tv + cI);
+                const V yc = ldc(tv + cI);
                 for (int i = cI + 1 + lane; i < q; i += NT)
-                    R::st(tv + i, R::nfma(R::ld(A22 + (size_t)(i * (i + 1) / 2 + cI)), yc, R::ld(tv + i)));
+                    stc(tv + i, R::nfma(ldc(A22 + (size_t)(i * (i + 1) / 2 + cI)), yc, ldc(tv + i)));
                 group_sync<NT>();
             }
-            for (int i = lane; i < q; i += NT) R::st(tv + i, R::mul(R::ld(tv + i), R::ld(fv + i)));
+            for (int i = lane; i < q; i += NT) stc(tv + i, R::mul(ldc(tv + i), ldc(fv + i)));
             group_sync<NT>();
             for (int cI = q - 1; cI >= 0; --cI) {
                 const S* sc = A22 + (size_t)(cI * (cI + 1) / 2);
-                const V zc = R::ld(tv + cI);
-                for (int i = lane; i < cI; i += NT) R::st(tv + i, R::nfma(R::ld(sc + i), zc, R::ld(tv + i)));
+                const V zc = ldc(tv + cI);
+                for (int i = lane; i < cI; i += NT) stc(tv + i, R::nfma(ldc(sc + i), zc, ldc(tv + i)));
                 group_sync<NT>();
             }
             // ---- w = w0 + Z z: w[r2_j] = z_j, w[r1_k] = w0_k - sum_j X[j][k] z_j ----
             for (int k = lane; k < s; k += NT) {
-                V acc = R::ld(w0 + k), acc1 = R::zero();
+                V acc = ldc(w0 + k), acc1 = R::zero();
                 int j = 0;
                 for (; j + 1 < q; j += 2) {
-                    acc = R::nfma(R::ld(X + (size_t)j * LDX + k), R::ld(tv + j), acc);
-                    acc1 = R::nfma(R::ld(X + (size_t)(j + 1) * LDX + k), R::ld(tv + j + 1), acc1);
+                    acc = R::nfma(ldc(X + (size_t)j * LDX + k), ldc(tv + j), acc);
+                    acc1 = R::nfma(ldc(X + (size_t)(j + 1) * LDX + k), ldc(tv + j + 1), acc1);
                 }
-                if (j < q) acc = R::nfma(R::ld(X + (size_t)j * LDX + k), R::ld(tv + j), acc);
-                R::st(wv + k, R::add(acc, acc1));
+                if (j < q) acc = R::nfma(ldc(X + (size_t)j * LDX + k), ldc(tv + j), acc);
+                stc(wv + k, R::add(acc, acc1));
             }
-            for (int j = lane; j < q; j += NT) R::st(wv + s + j, R::ld(tv + j));
+            for (int j = lane; j < q; j += NT) stc(wv + s + j, ldc(tv + j));
             group_sync<NT>();
         }
 
@@ -933,13 +951,13 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
         double* wd = reinterpret_cast<double*>(wv);
         int nonfinite = 0;
         for (int a = lane; a < n; a += NT) {
-            const double v = singular ? 0.0 : (op ? R::to_d(R::ld(wv + a)) : __dmul_rn(R::to_d(R::ld(wv + a)), inv_delta2));
+            const double v = singular ? 0.0 : (op ? R::to_d(ldc(wv + a)) : __dmul_rn(R::to_d(ldc(wv + a)), inv_delta2));
             nonfinite |= finite64(v) ? 0 : 1;
             wd[a] = v;
         }
         const int fail = (singular || group_any<NT>(nonfinite)) ? 1 : 0;
         group_sync<NT>();
-        for (int a = lane; a < n; a += NT) wout[singular ? a : perm[a]] = fail ? 0.0 : wd[a];
+        for (int a = lane; a < n; a += NT) RB_AT(wout, singular ? a : RB_AT(perm, a, n), n) = fail ? 0.0 : wd[a];
         if (node_status && lane == 0) node_status[node] = fail;
         group_sync<NT>();
     }

@@ -163,6 +163,17 @@ class Profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class CheckedReport(ctypes.Structure):
+    _fields_ = [
+        ("checked", ctypes.c_int32),
+        ("line", ctypes.c_int32),
+        ("file", ctypes.c_char * 32),
+        ("violations", ctypes.c_int64),
+        ("index", ctypes.c_int64),
+        ("bound", ctypes.c_int64),
+    ]
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [
         ("node_offset", ctypes.c_int64),
@@ -224,23 +235,32 @@ SIGNATURES = {
     "rbffd_diag_recip": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP]),
     "rbffd_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rbffd_profile_read": (ctypes.c_int, [ctypes.POINTER(Profile), ctypes.c_int]),
+    "rbffd_checked_read": (ctypes.c_int, [ctypes.POINTER(CheckedReport), ctypes.c_int]),
+    "rbffd_checked_probe": (ctypes.c_int, [_I64, _I64, _I64, _I64, _I64, _VP, _VP]),
 }
 
 
+def checked_build_selected() -> bool:
+    """RBFFD_CHECKED=1 in the environment selects the bounds-checked library."""
+    return os.environ.get("RBFFD_CHECKED", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB_PATH
+    return _build.lib_path(checked_build_selected())
 
 
 def load(build_if_missing: bool = True):
-    """Load librbffd.so (building it when missing); raises if it cannot be loaded."""
+    """Load librbffd.so, or librbffd_checked.so under RBFFD_CHECKED=1
+    (building it when missing); raises if it cannot be loaded."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB_PATH
+    checked = checked_build_selected()
+    path = _build.lib_path(checked)
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError(f"librbffd not built at {path}")
-        _build.build()
+        _build.build(checked=checked)
     lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
@@ -707,6 +727,25 @@ def rbffd_profile_read(reset: bool = False) -> dict:
     p = Profile()
     _check(load().rbffd_profile_read(ctypes.byref(p), 1 if reset else 0), "rbffd_profile_read")
     return p.as_dict()
+
+
+def rbffd_checked_probe(index: int, bound: int, span_off: int = 0, span_len: int = 0, smem_off: int = 0,
+                        device="cuda") -> torch.Tensor:
+    """One self-check access of the bounds-checked build (see the header);
+    returns the value read back (a 1-element device tensor)."""
+    out = torch.zeros(1, dtype=torch.float64, device=device)
+    _check(load().rbffd_checked_probe(int(index), int(bound), int(span_off), int(span_len), int(smem_off),
+                                      _ptr(out), _stream(out.device)), "rbffd_checked_probe")
+    return out
+
+
+def rbffd_checked_read(reset: bool = False) -> dict:
+    """Violation records of the bounds-checked build (checked = 0 and no
+    violations in the normal build); synchronise the device first."""
+    r = CheckedReport()
+    _check(load().rbffd_checked_read(ctypes.byref(r), 1 if reset else 0), "rbffd_checked_read")
+    return {"checked": int(r.checked), "violations": int(r.violations), "file": r.file.decode(),
+            "line": int(r.line), "index": int(r.index), "bound": int(r.bound)}
 
 
 # ----------------------------------------------------------------- batched --

@@ -208,3 +208,38 @@ def test_weights_config_table(cdll):
     assert cdll.rbffd_weights_autotune(None, 0x1000, 10, 6, 2, 0x2000, None, 0, None, None) == 1
     # an unknown precision selector is refused before any device access
     assert cdll.rbffd_weights_autotune(0x1000, 0x1000, 10, 6, 2, 0x2000, None, 7, None, None) == 1
+
+
+# ------------------------------------------------------ bounds-checked build --
+def test_normal_build_reports_no_checker(cdll):
+    """The normal build has no violation records and reads back zeros."""
+    from paper_2107_03632_gb300 import rbffd
+
+    r = rbffd.rbffd_checked_read(reset=True)
+    assert r == {"checked": 0, "violations": 0, "file": "", "line": 0, "index": 0, "bound": 0}
+
+
+@pytest.mark.parametrize("args", [(8, 8, 0, 0, 0), (-1, 8, 0, 0, 0), (0, 8, 5, 4, 0), (0, 8, -1, 1, 0),
+                                  (0, 8, 0, 0, 64), (0, 8, 0, 0, -8), (0, 8, 0, 0, 4), (0, 65, 0, 0, 0)])
+def test_normal_build_refuses_out_of_range_probes(cdll, args):
+    """The normal build's self-check entry takes in-range arguments only and
+    refuses the rest on the host, before anything touches CUDA."""
+    out = ctypes.c_void_p(0x1000)
+    assert cdll.rbffd_checked_probe(*args, out, None) == 1  # RBFFD_ERR_INVALID_ARG
+
+
+def test_checked_build_compiles_and_exports_every_symbol():
+    """librbffd_checked.so (every computed index tested before its access)
+    builds for sm_103a and exports the header's symbols; without a GPU its
+    probe still refuses a bound above the table on the host."""
+    from paper_2107_03632_gb300 import _build
+
+    path = _build.build(checked=True)
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    for nm in names:
+        assert hasattr(lib, nm), f"{nm} not exported by the checked build"
+    f = lib.rbffd_checked_probe
+    f.argtypes = [ctypes.c_int64] * 5 + [ctypes.c_void_p] * 2
+    f.restype = ctypes.c_int
+    assert f(0, 65, 0, 0, 0, ctypes.c_void_p(0x1000), None) == 1
