@@ -282,6 +282,44 @@ def test_solve_deterministic(lib):
         assert torch.equal(x1, x2) and i1["iters"] == i2["iters"]
 
 
+# launch configurations of each arithmetic of the null-space weight solve:
+# (kernel, warps per block)
+_NS_CONFIGS = {"fp64": [("null-space", 1), ("null-space", 4), ("null-space-2warp", 2), ("null-space-4warp", 4),
+                        ("null-space-half", 1), ("null-space-half", 4)],
+               "df": [("null-space-df", 1), ("null-space-df", 3), ("null-space-df-2warp", 2),
+                      ("null-space-df-4warp", 4), ("null-space-df-half", 2)]}
+
+
+@pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.04, 4, 30), (0.05, 6, 56)])
+def test_stencils_and_weights_identical_across_runs_and_launch_shapes(lib, h, m, n):
+    """Stencils: identical bits run to run.  Weights: identical bits across
+    every launch configuration of one arithmetic (one, two or four warps or
+    half a warp per stencil, 1 to 4 warps per block): a stencil's arithmetic
+    is the same whatever the group size (each entry is accumulated by one
+    thread in a fixed order; the group reductions are max and argmax)."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d = disk_nodes(h)
+    xy = T(d.xy)
+    idx = rbffd.rbffd_stencils(xy, n)
+    assert torch.equal(idx, rbffd.rbffd_stencils(xy, n))
+    try:
+        for prec, cfgs in _NS_CONFIGS.items():
+            got = []
+            for kernel, wpb in cfgs:
+                if "half" in kernel and (m > 4 or n > 32):
+                    continue
+                rbffd.set_weights_config(n, m, kernel, wpb)
+                w, st = rbffd.rbffd_weights(xy, idx, m)
+                assert int(st.sum()) == 0
+                got.append((kernel, wpb, w))
+            assert len(got) >= 4
+            for kernel, wpb, w in got[1:]:
+                assert torch.equal(w, got[0][2]), (prec, kernel, wpb)
+    finally:
+        rbffd.set_weights_config(n, m, None)
+
+
 def test_profile_counts_launches_and_spmv_time(lib):
     from paper_2107_03632_gb300 import rbffd
 
