@@ -306,6 +306,24 @@ size_t rbffd_mg_workspace_size(int64_t N, int64_t nnz);
 int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* A,
                    const rbffd_csr* A32, int32_t nu, double omega, rbffd_mg* mg, void* ws, size_t ws_bytes,
                    void* stream);
+/* The same hierarchy as rbffd_mg_setup, built in two calls.  Everything   */
+/* but the fine level's operator depends only on the nodes and the mask --  */
+/* the coarse node sets, their operators and smoother weights, the          */
+/* interpolation and restriction, the coarsest level's dense inverse -- so  */
+/* rbffd_mg_setup_geometry builds it, and synchronises `stream`, while the  */
+/* fine operator may still be computed on another stream (the weight solve, */
+/* assembly).  rbffd_mg_setup_operator then attaches A (and A32, as in      */
+/* rbffd_mg_setup) to level 0: its smoother weights, asynchronous on        */
+/* `stream`; when the node set is a single level (N <= 128) also its dense  */
+/* inverse, which synchronises `stream`.  Between the calls the hierarchy   */
+/* serves nothing (rbffd_solve refuses it).  Forward hierarchies only.      */
+/* ws: rbffd_mg_workspace_size(N, nnz) bytes (the size depends on N only). */
+/* Errors: as rbffd_mg_setup; rbffd_mg_setup_operator returns               */
+/* RBFFD_ERR_INVALID_ARG unless mg holds a geometry of N = A->n_rows nodes.  */
+/* (The split has no counterpart in the paper.)                             */
+int rbffd_mg_setup_geometry(const double* xy, const uint8_t* is_dirichlet, int64_t N, int32_t nu, double omega,
+                            rbffd_mg* mg, void* ws, size_t ws_bytes, void* stream);
+int rbffd_mg_setup_operator(rbffd_mg* mg, const rbffd_csr* A, const rbffd_csr* A32, void* stream);
 /* rbffd_mg_setup_adjoint: the same hierarchy for the adjoint operator AT  */
 /* = A^T (as passed to rbffd_solve_adjoint): every level's operator is the  */
 /* transpose of the forward one (coarse levels rediscretised, then          */

@@ -33,6 +33,7 @@ constexpr int kMgInterpM = 2;     // interpolation degree
 constexpr int kMgCoarseN = 12;    // coarse operator: stencil size
 constexpr int kMgCoarseM = 2;     //                  and degree
 constexpr uint32_t kMgMagic = 0x4D475242u;
+constexpr uint32_t kMgGeometryMagic = 0x4D474753u;  // geometry built, fine operator not attached yet
 constexpr int kMgGalerkinRow = 256;  // Galerkin coarse operators: mean entries per row the layout holds
 
 struct MgLevel {
@@ -75,6 +76,8 @@ struct MgHierarchy {
     int transposed;  // built for A^T (rbffd_mg_setup_adjoint)
     int galerkin;    // adjoint hierarchy with Galerkin coarse operators (rbffd_mg_galerkin_adjoint)
     double omega;
+    void* ws;         // the workspace the hierarchy lives in
+    size_t ws_bytes;
     MgLevel lv[RBFFD_MG_MAX_LEVELS];
 };
 const MgHierarchy* mg_hierarchy(const rbffd_mg* h);
@@ -109,6 +112,17 @@ int mg_dirichlet_fix(const MgHierarchy* h, const double* r, double* y, const int
 int mg_setup_core(const double* xy, const uint8_t* mask, int64_t N, const int64_t* row_ptr, const int* col,
                   const double* val, const float* val32, int64_t nnz, int col_base, int nu, double omega,
                   rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed = false);
+
+// The two phases of mg_setup_core.  Geometry: everything that depends on
+// the nodes and the mask only -- the coarse node sets, their operators and
+// smoother weights, interpolation and restriction, the coarsest level's
+// dense inverse -- and level 0's geometry; synchronises st.  Operator: the
+// fine operator attached to level 0 (its smoother weights; its dense
+// inverse when it is the only level, which synchronises st).
+int mg_setup_geometry(const double* xy, const uint8_t* mask, int64_t N, int col_base, int nu, double omega,
+                      rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed = false);
+int mg_setup_operator(rbffd_mg* mg, const int64_t* row_ptr, const int* col, const double* val, const float* val32,
+                      int64_t nnz, cudaStream_t st);
 
 // The adjoint hierarchy of the forward hierarchy F for AT = A^T
 // (rbffd_mg_adjoint_of).

@@ -1306,6 +1306,32 @@ extern "C" int rbffd_mg_setup(const double* xy, const uint8_t* is_dirichlet, int
                          as_stream(stream), false);
 }
 
+extern "C" int rbffd_mg_setup_geometry(const double* xy, const uint8_t* is_dirichlet, int64_t N, int32_t nu,
+                                       double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, void* stream) {
+    RBFFD_NVTX("rbffd_mg_setup_geometry");
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    std::memset(mg, 0, sizeof(*mg));
+    if (!xy || !is_dirichlet || N <= 0 || N > 0x7fffffffLL) return RBFFD_ERR_INVALID_ARG;
+    return mg_setup_geometry(xy, is_dirichlet, N, 0, nu, omega, mg, ws, ws_bytes, as_stream(stream), false);
+}
+
+extern "C" int rbffd_mg_setup_operator(rbffd_mg* mg, const rbffd_csr* A, const rbffd_csr* A32, void* stream) {
+    RBFFD_NVTX("rbffd_mg_setup_operator");
+    using namespace rbffd;
+    if (!mg) return RBFFD_ERR_INVALID_ARG;
+    const MgHierarchy* g = reinterpret_cast<const MgHierarchy*>(mg);
+    if (g->magic != kMgGeometryMagic || g->transposed) return RBFFD_ERR_INVALID_ARG;
+    const int64_t N = g->lv[0].N;
+    if (!A || !A->row_ptr || !A->col || !A->val || A->dtype != 0 || A->n_rows != N || A->nnz <= 0)
+        return RBFFD_ERR_INVALID_ARG;
+    if (A32 && (!A32->val || A32->dtype != 1 || A32->n_rows != N || A32->nnz != A->nnz || A32->row_ptr != A->row_ptr ||
+                A32->col != A->col))
+        return RBFFD_ERR_INVALID_ARG;
+    return mg_setup_operator(mg, A->row_ptr, A->col, static_cast<const double*>(A->val),
+                             A32 ? static_cast<const float*>(A32->val) : nullptr, A->nnz, as_stream(stream));
+}
+
 extern "C" int rbffd_mg_setup_adjoint(const double* xy, const uint8_t* is_dirichlet, int64_t N, const rbffd_csr* AT,
                                       const rbffd_csr* AT32, int32_t nu, double omega, rbffd_mg* mg, void* ws,
                                       size_t ws_bytes, void* stream) {
@@ -1566,9 +1592,9 @@ int rbffd::mg_galerkin_adjoint(const MgHierarchy& F, const rbffd_csr* AT, const 
     return RBFFD_OK;
 }
 
-int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t N, const int64_t* row_ptr,
-                         const int* col, const double* val, const float* val32, int64_t nnz, int col_base, int nu,
-                         double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed) {
+int rbffd::mg_setup_geometry(const double* xy, const uint8_t* is_dirichlet, int64_t N, int col_base, int nu,
+                             double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st,
+                             bool transposed) {
     using namespace rbffd;
     std::memset(mg, 0, sizeof(*mg));
     if (nu < 1 || nu > 8 || !(omega > 0.0 && omega < 1.0)) return RBFFD_ERR_INVALID_ARG;
@@ -1583,25 +1609,16 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
     h.magic = 0;
     h.nu = nu;
     h.omega = omega;
-    h.has32 = val32 ? 1 : 0;
     h.col_base = col_base;
     h.transposed = transposed ? 1 : 0;
+    h.ws = ws;
+    h.ws_bytes = ws_bytes;
     RBFFD_CUDA_TRY(cudaMemsetAsync(s.flags, 0, sizeof(int) * 64, st));
 
     MgLevel& L0 = h.lv[0];
     L0.N = N;
-    L0.row_ptr = row_ptr;
-    L0.col = col;
-    L0.val = val;
-    L0.val32 = val32;
-    L0.nnz = nnz;
-    L0.tpr = tpr_for(N, nnz);
     L0.xy = xy;
     L0.mask = is_dirichlet;
-    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, col_base, L0.mask, omega, L0.dinv,
-                                                 L0.dinv32, s.flags + 1);
-    note_launches(1);
-    RBFFD_LAUNCH_CHECK();
 
     int levels = 1;
     int rc = RBFFD_OK;
@@ -1609,7 +1626,8 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
         MgLevel& L = h.lv[l];
         if (L.N <= kMgCoarsest || l + 1 >= RBFFD_MG_MAX_LEVELS) {
             if (L.N > kMgCoarsest) return RBFFD_ERR_INVALID_ARG;
-            if ((rc = dense_inverse(L, l == 0 ? col_base : 0, s, st)) != RBFFD_OK) return rc;
+            // (a single level is the fine operator itself: inverted by the operator phase)
+            if (l > 0 && (rc = dense_inverse(L, 0, s, st)) != RBFFD_OK) return rc;
             levels = l + 1;
             break;
         }
@@ -1691,7 +1709,50 @@ int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t 
     RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
     if (flags[0]) return RBFFD_ERR_SINGULAR_STENCIL;
     h.n_levels = levels;
+    h.magic = kMgGeometryMagic;
+    std::memcpy(mg, &h, sizeof(h));
+    return RBFFD_OK;
+}
+
+int rbffd::mg_setup_operator(rbffd_mg* mg, const int64_t* row_ptr, const int* col, const double* val,
+                             const float* val32, int64_t nnz, cudaStream_t st) {
+    using namespace rbffd;
+    MgHierarchy h;
+    std::memcpy(&h, mg, sizeof(h));
+    if (h.magic != kMgGeometryMagic || h.n_levels < 1) return RBFFD_ERR_INVALID_ARG;
+    MgScratch s{};
+    mg_layout(h.ws, h.lv[0].N, nullptr, &s);  // the scratch of the geometry phase's layout
+    MgLevel& L0 = h.lv[0];
+    const int64_t N = L0.N;
+    L0.row_ptr = row_ptr;
+    L0.col = col;
+    L0.val = val;
+    L0.val32 = val32;
+    L0.nnz = nnz;
+    L0.tpr = tpr_for(N, nnz);
+    h.has32 = val32 ? 1 : 0;
+    mg_diag_kernel<<<blocks_for(N), kT, 0, st>>>(L0.row_ptr, L0.col, L0.val, N, h.col_base, L0.mask, h.omega, L0.dinv,
+                                                 L0.dinv32, s.flags + 1);
+    note_launches(1);
+    RBFFD_LAUNCH_CHECK();
+    if (h.n_levels == 1) {  // the fine operator is the coarsest level
+        int rc = dense_inverse(L0, h.col_base, s, st);
+        if (rc != RBFFD_OK) return rc;
+        int flag = 0;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(&flag, s.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        if (flag) return RBFFD_ERR_SINGULAR_STENCIL;
+    }
     h.magic = kMgMagic;
     std::memcpy(mg, &h, sizeof(h));
     return RBFFD_OK;
+}
+
+int rbffd::mg_setup_core(const double* xy, const uint8_t* is_dirichlet, int64_t N, const int64_t* row_ptr,
+                         const int* col, const double* val, const float* val32, int64_t nnz, int col_base, int nu,
+                         double omega, rbffd_mg* mg, void* ws, size_t ws_bytes, cudaStream_t st, bool transposed) {
+    int rc = mg_setup_geometry(xy, is_dirichlet, N, col_base, nu, omega, mg, ws, ws_bytes, st, transposed);
+    if (rc == RBFFD_OK) rc = mg_setup_operator(mg, row_ptr, col, val, val32, nnz, st);
+    if (rc != RBFFD_OK) std::memset(mg, 0, sizeof(*mg));
+    return rc;
 }

@@ -221,6 +221,9 @@ SIGNATURES = {
                                       ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
     "rbffd_mg_setup_adjoint": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(Csr), ctypes.POINTER(Csr), _I32, _D,
                                               ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
+    "rbffd_mg_setup_geometry": (ctypes.c_int, [_VP, _VP, _I64, _I32, _D, ctypes.POINTER(MgHandle), _VP, _SZ, _VP]),
+    "rbffd_mg_setup_operator": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
+                                               _VP]),
     "rbffd_mg_levels": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(ctypes.c_int64)]),
     "rbffd_mg_level": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.c_int32, ctypes.POINTER(MgLevelInfo)]),
     "rbffd_mg_adjoint_of": (ctypes.c_int, [ctypes.POINTER(MgHandle), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
@@ -490,6 +493,28 @@ class Multigrid:
                   ctypes.byref(c32) if c32 is not None else None, int(nu), float(omega),
                   ctypes.byref(self.handle), _ptr(self.ws), self.ws.numel(), _stream(xy.device)),
                "rbffd_mg_setup_adjoint" if self.adjoint else "rbffd_mg_setup")
+
+    def setup_geometry(self, xy: torch.Tensor, is_dirichlet: torch.Tensor, nu: int = 2, omega: float = 0.6,
+                       stream: torch.cuda.Stream | None = None):
+        """First phase of a rebuild (rbffd_mg_setup_geometry): everything that
+        depends on the nodes and the mask only, on `stream` (default: the
+        current one), which it synchronises.  A forward hierarchy only."""
+        if self.adjoint:
+            raise RbffdError(1, "rbffd_mg_setup_geometry", "forward hierarchies only")
+        st = (stream or torch.cuda.current_stream(xy.device)).cuda_stream
+        _check(load().rbffd_mg_setup_geometry(_ptr(xy), _ptr(is_dirichlet), xy.shape[0], int(nu), float(omega),
+                                              ctypes.byref(self.handle), _ptr(self.ws), self.ws.numel(), st),
+               "rbffd_mg_setup_geometry")
+
+    def setup_operator(self, A: "CsrMatrix"):
+        """Second phase (rbffd_mg_setup_operator): the fine operator A attached
+        to level 0, on the current stream."""
+        c64 = A.c64()
+        c32 = A.c32()
+        self.A = A
+        _check(load().rbffd_mg_setup_operator(ctypes.byref(self.handle), ctypes.byref(c64),
+                                              ctypes.byref(c32) if c32 is not None else None,
+                                              _stream(A.val.device)), "rbffd_mg_setup_operator")
 
     @classmethod
     def adjoint_of(cls, fwd: "Multigrid", AT: "CsrMatrix", ws: torch.Tensor | None = None) -> "Multigrid":

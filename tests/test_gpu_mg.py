@@ -401,3 +401,66 @@ def test_solver_stops_on_stagnation(lib, precision, use_mg):
     assert info["status_code"] == 4, info
     assert info["iters"] <= 5000, info
     assert np.isfinite(info["rel_residual"]) and info["rel_residual"] > 1e-10
+
+
+@pytest.mark.parametrize("h,m,n", [(0.02, 4, 30), (0.1, 2, 12)])
+def test_two_phase_setup_equals_one_call(lib, h, m, n):
+    """rbffd_mg_setup_geometry on a second stream while the fine weights are
+    computed, then rbffd_mg_setup_operator: the same hierarchy as
+    rbffd_mg_setup (identical levels, V-cycle outputs and solutions, bit for
+    bit).  h = 0.1: a node set that is a single (dense) level."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, idx, w, rp, col, val, b = _system(h, m, n)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    idx_t = T(idx)
+    w1, _ = rbffd.rbffd_weights(xy, idx_t, m)
+    A = rbffd.rbffd_assemble(idx_t, w1, mask, want_f32=True)
+    one = rbffd.Multigrid(xy, mask, A)
+    # the second hierarchy: the same weights again on the current stream (the
+    # same bits), the geometry on a side stream meanwhile
+    side = torch.cuda.Stream(DEV)
+    two = rbffd.Multigrid(xy, mask, A, ws=torch.empty_like(one.ws))
+    w2, _ = rbffd.rbffd_weights(xy, idx_t, m)  # in flight while the geometry is built
+    two.setup_geometry(xy, mask, stream=side)
+    A2 = rbffd.rbffd_assemble(idx_t, w2, mask, want_f32=True)
+    two.setup_operator(A2)
+    assert torch.equal(A2.val, A.val)
+    assert two.levels() == one.levels()
+    for l in range(len(one.levels())):
+        a, c = one.level(l), two.level(l)
+        for k in ("xy", "is_dirichlet", "w", "p_idx", "p_val", "minv"):
+            if a.get(k) is not None:
+                assert torch.equal(a[k], c[k]), (l, k)
+        if l > 0:
+            assert torch.equal(a["A"].val, c["A"].val) and torch.equal(a["A"].col, c["A"].col)
+    bb = T(b)
+    for fp32 in (False, True):
+        assert torch.equal(one.apply(bb, fp32=fp32), two.apply(bb, fp32=fp32))
+    for prec in ("fp64", "mixed"):
+        x1, i1 = rbffd.rbffd_solve(A, bb, opts=rbffd.make_opts(precision=prec, mg=one))
+        x2, i2 = rbffd.rbffd_solve(A2, bb, opts=rbffd.make_opts(precision=prec, mg=two))
+        assert torch.equal(x1, x2) and i1["iters"] == i2["iters"], prec
+
+
+def test_two_phase_setup_refuses_misuse(lib):
+    """A hierarchy between the two phases serves no solve; the operator phase
+    takes only a geometry of the same node count."""
+    from paper_2107_03632_gb300 import rbffd
+
+    d, idx, w, rp, col, val, b = _system(0.04, 2, 12)
+    xy, mask = T(d.xy), T(d.is_dirichlet)
+    A = rbffd.rbffd_assemble(T(idx), T(w), mask, want_f32=True)
+    mg = rbffd.Multigrid(xy, mask, A)
+    mg.setup_geometry(xy, mask)
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(mg=mg), raise_on_error=False)
+    assert info["status_code"] == 1  # RBFFD_ERR_INVALID_ARG
+    d2, idx2, w2, *_ = _system(0.05, 2, 12)
+    A_other = rbffd.rbffd_assemble(T(idx2), T(w2), T(d2.is_dirichlet), want_f32=True)
+    with pytest.raises(rbffd.RbffdError):
+        mg.setup_operator(A_other)
+    mg.setup_operator(A)
+    with pytest.raises(rbffd.RbffdError):
+        mg.setup_operator(A)  # already attached
+    x, info = rbffd.rbffd_solve(A, T(b), opts=rbffd.make_opts(mg=mg))
+    assert info["status"] == 0
