@@ -182,7 +182,7 @@ SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorit
 # n = 56: dram read + write per stencil (idx read, w written; the gathered
 # coordinates come from L2).  Valid only at that (n, m) and while the
 # kernel's sources are the ones captured.
-WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "38d22c7f714a4d48", "n": 56, "m": 6,
+WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "334768f3fd96fc1b", "n": 56, "m": 6,
                        "bytes_per_node": (259.903744e6 + 406.790144e6) / 1001697.0}
 
 

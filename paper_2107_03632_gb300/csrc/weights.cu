@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
             // column goes to uv (free now), L[i][c] = S[i][c] / D[c], then
             // S[i][j] -= L[i][c] S[j][c] for c < j <= i.  The thread that
             // updates the next diagonal entry also forms its reciprocal and
-            // the singularity flag (RB_AT(act, 0, n), free after the elimination).
+            // the singularity flag (act[0], free after the elimination).
             if (q > 0) {
                 if (lane == 0) {
                     const V d0 = ldc(A22);
