@@ -208,6 +208,47 @@ struct TopList {
         }
     }
 
+    // Merge a batch of 32 keys (one per lane, sorted ascending over the
+    // lanes): afterwards the list holds the SLOTS*32 smallest of the list
+    // and the batch, sorted.  Classic bitonic merge: the last slot against
+    // the reversed batch keeps the smaller key of each pair, which leaves the
+    // list a bitonic sequence of the smallest keys; compare-exchange stages of
+    // halving distance then sort it (between slots in registers, within a
+    // slot by shuffles).
+    __device__ __forceinline__ void merge(unsigned long long bd, unsigned int bj, int lane) {
+        const unsigned long long rd = __shfl_sync(0xffffffffu, bd, 31 - lane);
+        const unsigned int rj = __shfl_sync(0xffffffffu, bj, 31 - lane);
+        if (key_less(rd, rj, d[SLOTS - 1], j[SLOTS - 1])) {
+            d[SLOTS - 1] = rd;
+            j[SLOTS - 1] = rj;
+        }
+#pragma unroll
+        for (int h = SLOTS / 2; h > 0; h >>= 1)  // distance 32 h: slot s against slot s + h
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s)
+                if ((s & h) == 0 && key_less(d[s + h], j[s + h], d[s], j[s])) {
+                    const unsigned long long td = d[s];
+                    const unsigned int tj = j[s];
+                    d[s] = d[s + h];
+                    j[s] = j[s + h];
+                    d[s + h] = td;
+                    j[s + h] = tj;
+                }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const bool lower = (lane & o) == 0;
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) {
+                const unsigned long long pd = __shfl_xor_sync(0xffffffffu, d[s], o);
+                const unsigned int pj = __shfl_xor_sync(0xffffffffu, j[s], o);
+                if (lower ? key_less(pd, pj, d[s], j[s]) : key_less(d[s], j[s], pd, pj)) {
+                    d[s] = pd;
+                    j[s] = pj;
+                }
+            }
+        }
+    }
+
     // Entry e broadcast to the warp.
     __device__ __forceinline__ void get(int e, unsigned long long& od, unsigned int& oj) const {
         const int s = e >> 5, l = e & 31;
@@ -223,6 +264,28 @@ struct TopList {
         oj = __shfl_sync(0xffffffffu, w, l);
     }
 };
+
+// Ascending bitonic sort of 32 keys, one per lane.
+__device__ __forceinline__ void warp_sort32(unsigned long long& d, unsigned int& j, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int o = k >> 1; o > 0; o >>= 1) {
+            const unsigned long long pd = __shfl_xor_sync(0xffffffffu, d, o);
+            const unsigned int pj = __shfl_xor_sync(0xffffffffu, j, o);
+            const bool up = (lane & k) == 0 || k == 32;  // this run ascending
+            const bool lower = (lane & o) == 0;
+            if (lower == up ? key_less(pd, pj, d, j) : key_less(d, j, pd, pj)) {
+                d = pd;
+                j = pj;
+            }
+        }
+    }
+}
+
+// Batches with more accepted candidates than this are sorted and merged into
+// the list at once; fewer are inserted one by one.
+constexpr int kMergeBatch = 4;
 
 // Queries: the indexed points themselves in cell order (qxy = sxy, qorig =
 // sorig: stencils), or separate points in their own order (qorig = NULL:
@@ -275,7 +338,16 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
                 kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
                 kj = (unsigned int)RB_AT(sorig, jj, Np);
             }
-            unsigned int m = __ballot_sync(0xffffffffu, key_less(kd, kj, thr_d, thr_j));
+            const bool acc = key_less(kd, kj, thr_d, thr_j);
+            unsigned int m = __ballot_sync(0xffffffffu, acc);
+            if (__popc(m) > kMergeBatch) {  // many at once (the first batches of a query)
+                unsigned long long md = acc ? kd : ~0ull;
+                unsigned int mj = acc ? kj : ~0u;
+                warp_sort32(md, mj, lane);
+                top.merge(md, mj, lane);
+                top.get(n - 1, thr_d, thr_j);
+                continue;
+            }
             while (m) {
                 const int src = __ffs(m) - 1;
                 m &= m - 1;
