@@ -284,8 +284,10 @@ __device__ __forceinline__ void warp_sort32(unsigned long long& d, unsigned int&
 }
 
 // Batches with more accepted candidates than this are sorted and merged into
-// the list at once; fewer are inserted one by one.
-constexpr int kMergeBatch = 4;
+// the list at once; fewer are inserted one by one (4M nodes, n = 56: 24.9 /
+// 24.4 / 24.0 / 23.6 / 23.1 ms of stencils with 1 / 2 / 4 / 8 / 16 here,
+// 34.3 ms inserting every candidate).
+constexpr int kMergeBatch = 16;
 
 // Queries: the indexed points themselves in cell order (qxy = sxy, qorig =
 // sorig: stencils), or separate points in their own order (qorig = NULL:
