@@ -1193,11 +1193,11 @@ def run_gpu(args):
         rbffd.rbffd_weights(xy, idx, m, w, st)
         rbffd.rbffd_assemble(idx, w, mask, out=A)
         mg = rbffd.Multigrid(xy, mask, A, nu=args.mg_nu, omega=args.mg_omega)
-        opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.mg_pass_tol, mg=mg),
-                "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.mg_pass_tol, mg=mg)}
+        opts = {"mixed": rbffd.make_opts(tol=args.tol, precision="mixed", inner_tol=args.mg_pass_tol, mg=mg),
+                "fp64": rbffd.make_opts(tol=args.tol, precision="fp64", inner_tol=args.mg_pass_tol, mg=mg)}
     else:
-        opts = {"mixed": rbffd.make_opts(tol=1e-10, precision="mixed", inner_tol=args.inner_tol),
-                "fp64": rbffd.make_opts(tol=1e-10, precision="fp64", inner_tol=args.inner_tol64)}
+        opts = {"mixed": rbffd.make_opts(tol=args.tol, precision="mixed", inner_tol=args.inner_tol),
+                "fp64": rbffd.make_opts(tol=args.tol, precision="fp64", inner_tol=args.inner_tol64)}
     ws_solve = rbffd.solve_workspace(N, opts["mixed"], dev)
     if use_mg:
         ws_solve64 = ws_solve
@@ -1437,7 +1437,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "nnz": nnz, "h": h, "m": m, "n": n, "seed": SEED,
-                   "tol": 1e-10,
+                   "tol": args.tol,
                    "precision_by_stage": {
                        "stencils": "f64 distance keys (f32 pruning bounds)",
                        "weights": "f64 (null-space elimination + L D L^T, FP64 throughout)",
@@ -1514,7 +1514,29 @@ def main():
     ap.add_argument("--weights-config", default=None,
                     help="pin the weight-solve configuration KERNEL:WARPS_PER_BLOCK instead of autotuning")
     ap.add_argument("--no-peak-probe", action="store_true", help="skip the cuBLAS DGEMM FP64 peak probe")
+    ap.add_argument("--config", default=None,
+                    help="a JSON workload {\"h\": spacing or \"N\": nodes, \"m\", \"n\", optional \"seed\", "
+                         "\"tol\", \"name\"} for the single-system step, instead of --workload")
+    ap.add_argument("--seed", type=int, default=None, help="seed of the node sets and sources (default 2107)")
+    ap.add_argument("--tol", type=float, default=1e-10,
+                    help="relative residual of the single-system solves (default 1e-10, the metric's)")
     args = ap.parse_args()
+    global SEED
+    if args.config:
+        with open(args.config) as fh:
+            c = json.load(fh)
+        from fixtures import h_for_nodes
+
+        h = float(c["h"]) if "h" in c else h_for_nodes(float(c["N"]))
+        name = "config:" + str(c.get("name", os.path.splitext(os.path.basename(args.config))[0]))
+        WORKLOADS[name] = (h, int(c["m"]), int(c["n"]))
+        args.workload = name
+        if "seed" in c and args.seed is None:
+            args.seed = int(c["seed"])
+        if "tol" in c:
+            args.tol = float(c["tol"])
+    if args.seed is not None:
+        SEED = args.seed
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
