@@ -202,9 +202,10 @@ def assembly_and_solves():
         bar(f"explicit m={m} n={n}", err, 1e-12)
 
 
-def batched():
+def batched(n_rhs):
+    """n_rhs odd: one right-hand side per lane and half-warp; even: two
+    adjacent ones per lane (8- and 16-byte accesses)."""
     specs = [(0.1, 2, 12), (0.12, 6, 56), (0.08, 4, 30)]
-    n_rhs = 3
     nodes, masks, fs, gs, sizes = [], [], [], [], []
     for k, (h, m, n) in enumerate(specs):
         d = disk_nodes(h, seed=40 + k)
@@ -241,10 +242,10 @@ def batched():
             for k in range(n_rhs):
                 err = max(err, rel(u[off:off + N, k], ref[k]))
             off += N
-        stage(f"batched {mode}", err=err, status=int(st))
-        bar(f"batched {mode}", err, 1e-8)
+        stage(f"batched {mode} rhs={n_rhs}", err=err, status=int(st))
+        bar(f"batched {mode} rhs={n_rhs}", err, 1e-8)
         if st != 0:
-            REPORT["failures"].append(f"batched {mode}: status {st}")
+            REPORT["failures"].append(f"batched {mode} rhs={n_rhs}: status {st}")
 
 
 def main():
@@ -255,11 +256,12 @@ def main():
     if first["checked"] != 1:
         REPORT["failures"].append("the loaded library is not the checked build")
     del lib
-    for part in (probes, stencils_and_weights, assembly_and_solves, batched):
+    parts = (probes, stencils_and_weights, assembly_and_solves, lambda: batched(3), lambda: batched(4))
+    for part in parts:
         try:
             part()
         except Exception as e:  # report, do not hide
-            REPORT["failures"].append(f"{part.__name__}: {type(e).__name__}: {e}")
+            REPORT["failures"].append(f"{getattr(part, '__name__', 'part')}: {type(e).__name__}: {e}")
     print(json.dumps(REPORT))
     return 0
 

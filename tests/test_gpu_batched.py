@@ -41,7 +41,7 @@ MODES = {"jacobi": (0, 0, 0), "mg": (1, 0, 0), "mg-persistent": (1, 1, 0), "mg-d
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-@pytest.mark.parametrize("n_rhs", [1, 3, 64])
+@pytest.mark.parametrize("n_rhs", [1, 2, 3, 64])
 def test_batched_vs_oracle(lib, n_rhs, mode):
     """Every solver mode against the oracle's direct solves, per (instance, rhs)."""
     from paper_2107_03632_gb300 import rbffd

@@ -40,6 +40,6 @@ def test_checked_pipeline_has_no_violations(lib):
     assert not report["failures"], report["failures"]
     # every part ran (a part that raised is listed in failures above)
     for must in ("probe index", "stencils noalloc", "weights autotune", "adjoint galerkin m=6 n=56",
-                 "explicit m=2 n=12", "batched mg-persistent", "batched mg-device-loop"):
+                 "explicit m=2 n=12", "batched mg-persistent rhs=3", "batched mg-device-loop rhs=4"):
         assert must in stages, must
     assert sum(1 for k in stages if k.startswith("weights ")) >= 25
