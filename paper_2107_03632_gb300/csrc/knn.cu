@@ -326,40 +326,41 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
     unsigned long long thr_d = ~0ull;  // key of entry n-1 (all-ones: list not full)
     unsigned int thr_j = ~0u;
 
+    // one batch: lane's candidate at sorted position jj (none: jj < 0)
+    auto eval = [&](int jj) {
+        unsigned long long kd = ~0ull;
+        unsigned int kj = ~0u;
+        if (jj >= 0) {
+            const double2 P = RB_AT(sxy, jj, Np);
+            const double dx = __dadd_rn(P.x, -Q.x);
+            const double dy = __dadd_rn(P.y, -Q.y);
+            const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
+            kj = (unsigned int)RB_AT(sorig, jj, Np);
+        }
+        const bool acc = key_less(kd, kj, thr_d, thr_j);
+        unsigned int m = __ballot_sync(0xffffffffu, acc);
+        if (__popc(m) > kMergeBatch) {  // many at once (the first batches of a query)
+            unsigned long long md = acc ? kd : ~0ull;
+            unsigned int mj = acc ? kj : ~0u;
+            warp_sort32(md, mj, lane);
+            top.merge(md, mj, lane);
+            top.get(n - 1, thr_d, thr_j);
+            return;
+        }
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const unsigned long long id = __shfl_sync(0xffffffffu, kd, src);
+            const unsigned int ij = __shfl_sync(0xffffffffu, kj, src);
+            if (!key_less(id, ij, thr_d, thr_j)) continue;  // threshold moved
+            top.insert(id, ij, lane);
+            top.get(n - 1, thr_d, thr_j);
+        }
+    };
     // candidates at sorted positions [beg, end)
     auto scan = [&](int beg, int end) {
-        for (int base = beg; base < end; base += 32) {
-            const int jj = base + lane;
-            unsigned long long kd = ~0ull;
-            unsigned int kj = ~0u;
-            if (jj < end) {
-                const double2 P = RB_AT(sxy, jj, Np);
-                const double dx = __dadd_rn(P.x, -Q.x);
-                const double dy = __dadd_rn(P.y, -Q.y);
-                const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                kd = (unsigned long long)__double_as_longlong(d2) & 0x7fffffffffffffffull;
-                kj = (unsigned int)RB_AT(sorig, jj, Np);
-            }
-            const bool acc = key_less(kd, kj, thr_d, thr_j);
-            unsigned int m = __ballot_sync(0xffffffffu, acc);
-            if (__popc(m) > kMergeBatch) {  // many at once (the first batches of a query)
-                unsigned long long md = acc ? kd : ~0ull;
-                unsigned int mj = acc ? kj : ~0u;
-                warp_sort32(md, mj, lane);
-                top.merge(md, mj, lane);
-                top.get(n - 1, thr_d, thr_j);
-                continue;
-            }
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const unsigned long long id = __shfl_sync(0xffffffffu, kd, src);
-                const unsigned int ij = __shfl_sync(0xffffffffu, kj, src);
-                if (!key_less(id, ij, thr_d, thr_j)) continue;  // threshold moved
-                top.insert(id, ij, lane);
-                top.get(n - 1, thr_d, thr_j);
-            }
-        }
+        for (int base = beg; base < end; base += 32) eval(base + lane < end ? base + lane : -1);
     };
     // FP32 lower bound of d^2 from the query to the cells [xl, xh] of row yy,
     // relative to the query's cell corner (exact in FP64), shrunk by a slack;
@@ -394,12 +395,36 @@ __global__ void __launch_bounds__(256) knn_kernel(const double2* __restrict__ sx
         return gap > 0.0 && gap * gap > key_d2(thr_d);
     };
 
-    // the block, rows from the query's outwards
-    const int xlo = max(cx - R0, 0), xhi = min(cx + R0, G - 1);
-    for (int k = 0; k <= 2 * R0; ++k) {
-        const int yy = cy + ((k & 1) ? -((k + 1) >> 1) : (k >> 1));
-        if (yy < 0 || yy >= G) continue;
-        row_range(xlo, xhi, yy);
+    // the block, rows from the query's outwards, their candidates packed into
+    // batches of 32 across row boundaries (a row is tested against the n-th
+    // key when the batch that would start it is filled)
+    {
+        const int xlo = max(cx - R0, 0), xhi = min(cx + R0, G - 1);
+        int k = 0, sb = 0, sl = 0;  // next row; the current row's unread range [sb, sb + sl)
+        for (;;) {
+            int mine = -1, fill = 0;
+            while (fill < 32) {
+                if (sl == 0) {
+                    bool got = false;
+                    while (k <= 2 * R0 && !got) {
+                        const int yy = cy + ((k & 1) ? -((k + 1) >> 1) : (k >> 1));
+                        ++k;
+                        if (yy < 0 || yy >= G || beyond(xlo, xhi, yy)) continue;
+                        sb = RB_AT(cell_start, yy * G + xlo, G * G + 1);
+                        sl = RB_AT(cell_start, yy * G + xhi + 1, G * G + 1) - sb;
+                        got = sl > 0;
+                    }
+                    if (!got) break;
+                }
+                const int t = min(32 - fill, sl);
+                if (lane >= fill && lane < fill + t) mine = sb + lane - fill;
+                sb += t;
+                sl -= t;
+                fill += t;
+            }
+            if (fill == 0) break;
+            eval(mine);
+        }
     }
     // then rings: the two edge rows as ranges, the side cells one by one
     for (int r = R0; !done(r) && r <= G; ) {
