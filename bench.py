@@ -173,7 +173,7 @@ class ClockSampler:
 # divided by the kernel's algorithmic bytes at that size.  The ratio scales
 # the capture to a full-size launch (traffic grows with the matrix) and is
 # valid only while the kernel's source is the one captured.
-SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorithmic": (271.693312e6 + 8.42624e6)
+SPMV_DF_TRAFFIC = {"source_sha256_16": "ea63d4b54b1529b9", "traffic_over_algorithmic": (271.693312e6 + 8.42624e6)
                    / 279652728.0}
 
 
@@ -182,7 +182,7 @@ SPMV_DF_TRAFFIC = {"source_sha256_16": "70199ca29a9baa96", "traffic_over_algorit
 # n = 56: dram read + write per stencil (idx read, w written; the gathered
 # coordinates come from L2).  Valid only at that (n, m) and while the
 # kernel's sources are the ones captured.
-WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "334768f3fd96fc1b", "n": 56, "m": 6,
+WEIGHTS_F64_TRAFFIC = {"source_sha256_16": "5a541d3a57e1eb7e", "n": 56, "m": 6,
                        "bytes_per_node": (259.903744e6 + 406.790144e6) / 1001697.0}
 
 

@@ -153,15 +153,19 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 /* offered for 1 <= m <= 6, where the scaled systems' conditioning keeps    */
 /* the weights within ~1e-10 of FP64.  7 / 8: the null-space form with     */
 /* half a warp (16 threads) per stencil, two stencils per warp, FP64 /      */
-/* double-float (warps_per_block 1..4: 2..8 stencils per block).            */
+/* double-float (warps_per_block 1..4: 2..8 stencils per block); 9 / 10:    */
+/* a quarter of a warp (8 threads), four stencils per warp (4..16 per      */
+/* block).                                                                  */
 /* The default is FP64: 2 (two warps per stencil) for m >= 5 when it fits,  */
-/* 7 (half a warp, warps_per_block 2) for m <= 4 with n <= 32, 0 for other  */
+/* 9 (a quarter warp, warps_per_block 2) for m <= 2 with n <= 16, 7 (half a */
+/* warp, warps_per_block 2) for other m <= 4 with n <= 32, 0 for other     */
 /* m >= 1, 1 for m = 0.                                                      */
 /* RBFFD_WEIGHTS=ns64 (environment) forces the FP64 null-space form with    */
 /* one warp per stencil, =df its double-float form (1 <= m <= 6), =lu the   */
 /* Gaussian elimination.                                                     */
 /* rbffd_weights_autotune times every candidate of the given precision      */
-/* (RBFFD_WEIGHTS_FP64: kernels 0-3, 7; RBFFD_WEIGHTS_DF: 4-6, 8; _ANY: all) */
+/* (RBFFD_WEIGHTS_FP64: kernels 0-3, 7, 9; RBFFD_WEIGHTS_DF: 4-6, 8, 10;    */
+/* _ANY: all)                                                               */
 /* that                                                                     */
 /* fits in shared memory on the first min(N, 512 x SMs) stencils of the     */
 /* given set (the fastest of 3 launches after one warm-up, CUDA events),    */
@@ -179,9 +183,10 @@ int rbffd_weights(const double* xy, const int32_t* idx, int64_t N, int32_t n, in
 typedef struct rbffd_weights_config {
     int32_t kernel;          /* 0 null-space (1 warp/stencil), 1 Gaussian, 2 / 3 null-space (2 / 4 warps), */
                              /* 4 / 5 / 6 as 0 / 2 / 3 in double-float arithmetic; 7 / 8 null-space     */
-                             /* with half a warp per stencil, FP64 / double-float                        */
+                             /* with half a warp per stencil, FP64 / double-float; 9 / 10 the same     */
+                             /* with a quarter of a warp                                                 */
     int32_t warps_per_block; /* kernels 0, 1, 4: stencils (warps) per block; 2, 5: 2; 3, 6: 4;          */
-                             /* 7, 8: warps per block (two stencils per warp)                            */
+                             /* 7, 8: warps per block (two stencils per warp); 9, 10: four per warp     */
     double ms_per_mnode;     /* autotune: measured ms per 1e6 stencils (0 otherwise) */
 } rbffd_weights_config;
 int rbffd_weights_autotune(const double* xy, const int32_t* idx, int64_t N, int32_t n, int32_t m,

@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(128) weights_kernel(const double2* __restrict_
                     double* r2 = A + (size_t)(k + 1 + i2) * LD + k;
                     double* r3 = A + (size_t)(k + 1 + i3) * LD + k;
                     const int L = smem_doubles;
+                    (void)L;  // the bound of the checked build's tests
                     const double l0 = RB_PT(r0, A, L), l1 = RB_PT(r1, A, L), l2 = RB_PT(r2, A, L),
                                  l3 = RB_PT(r3, A, L);
                     const double u0 = RB_PT(prow + j0, A, L), u1 = RB_PT(prow + j1, A, L),
@@ -580,6 +581,7 @@ __global__ void __launch_bounds__(128) weights_ns_kernel(const double2* __restri
     // checked build, whose first test is that the region lies in the launch's
     // shared memory)
     const int region = bytes_per_warp / (int)sizeof(S);
+    (void)region;  // the bound of the checked build's tests
     (void)RB_SH(smem_raw + (size_t)(wib + 1) * bytes_per_warp - 1);
     auto ldc = [&](const S* p) -> V { return R::ld(&RB_PT(p, Phi, region)); };
     auto stc = [&](S* p, V v) { R::st(&RB_PT(p, Phi, region), v); };
@@ -1001,7 +1003,7 @@ struct WCfg {
                  // elimination, 2 / 3 null-space elimination with two / four warps
                  // per stencil; 4 / 5 / 6: 0 / 2 / 3 in double-float arithmetic;
                  // 7 / 8: null-space elimination with half a warp per stencil,
-                 // FP64 / double-float
+                 // FP64 / double-float; 9 / 10: the same with a quarter warp
     int wpb;     // warps per block (kernels 2, 3: 2 or 4, one stencil)
 };
 
@@ -1022,18 +1024,19 @@ size_t smem_per_stencil(int kernel, int n, int m) {
 
 // Stencils per block of a configuration, and its dynamic shared memory.
 int stencils_per_block(const WCfg& c) {
+    if (c.kernel >= 9) return 4 * c.wpb;
     if (c.kernel >= 7) return 2 * c.wpb;
     return (c.kernel == 2 || c.kernel == 3 || c.kernel == 5 || c.kernel == 6) ? 1 : c.wpb;
 }
 
-bool cfg_is_df(const WCfg& c) { return (c.kernel >= 4 && c.kernel <= 6) || c.kernel == 8; }
+bool cfg_is_df(const WCfg& c) { return (c.kernel >= 4 && c.kernel <= 6) || c.kernel == 8 || c.kernel == 10; }
 
 // The double-float null-space kernels: 1 <= m <= 6 (accuracy, see NsDF).
 constexpr int kDfMaxM = 6;
 size_t block_smem(const WCfg& c, int n, int m) { return smem_per_stencil(c.kernel, n, m) * stencils_per_block(c); }
 
 bool cfg_valid(const WCfg& c, int n, int m) {
-    if (c.kernel < 0 || c.kernel > 8) return false;
+    if (c.kernel < 0 || c.kernel > 10) return false;
     if (c.kernel != 1 && m < 1) return false;  // null-space form needs the linear monomials
     if (cfg_is_df(c) && m > kDfMaxM) return false;
     if ((c.kernel == 2 || c.kernel == 5) && c.wpb != 2) return false;
@@ -1055,6 +1058,11 @@ WCfg default_cfg(int n, int m) {
     // FP64 (m = 6, n = 56, 4M nodes: 1,346 ms against 1,595 with one warp)
     const WCfg big{2, 2};
     if (m >= 5 && cfg_valid(big, n, m)) return big;
+    // the smallest systems (m <= 2, n <= 16): a quarter of a warp per stencil
+    // (2M nodes, m = 2, n = 12: 6.3 ms per 1e6 stencils against 8.2 with
+    // half a warp and 13.0 with a warp)
+    const WCfg quarter{9, 2};
+    if (m <= 2 && n <= 16 && cfg_valid(quarter, n, m)) return quarter;
     // small systems (m <= 4, n <= 32): half a warp per stencil (1M nodes:
     // m = 2, n = 12 8.3 ms against 13.0; m = 4, n = 30 45.3 against 50.4)
     const WCfg half{7, 2};
@@ -1062,10 +1070,13 @@ WCfg default_cfg(int n, int m) {
     return c;
 }
 
-// The double-float half-warp kernel for the preconditioner's small systems
-// (coarse operators and interpolation, n = 12: 4.9 ms per 1e6 stencils
-// against 7.7 with a warp per stencil), else the warp-per-stencil form.
+// The double-float kernels for the preconditioner's small systems (coarse
+// operators and interpolation, n = 12, m = 2: 3.6 ms per 1e6 stencils with a
+// quarter of a warp per stencil against 4.9 with half a warp and 7.7 with a
+// warp), else the warp-per-stencil form.
 WCfg small_df_cfg(int n, int m) {
+    const WCfg quarter{10, 2};
+    if (n <= 16 && m <= 2 && cfg_valid(quarter, n, m)) return quarter;
     const WCfg half{8, 2};
     if (n <= 20 && cfg_valid(half, n, m)) return half;
     WCfg c{4, 1};
@@ -1153,8 +1164,12 @@ int launch_weights(const WCfg& c, const double* xy, const int32_t* idx, int64_t 
         rc = launch_ns<128, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     } else if (c.kernel == 7) {
         rc = launch_ns<16, NsF64>(c, p, idx, N, n, m, w, node_status, st);
-    } else {
+    } else if (c.kernel == 8) {
         rc = launch_ns<16, NsDF>(c, p, idx, N, n, m, w, node_status, st);
+    } else if (c.kernel == 9) {
+        rc = launch_ns<8, NsF64>(c, p, idx, N, n, m, w, node_status, st);
+    } else {
+        rc = launch_ns<8, NsDF>(c, p, idx, N, n, m, w, node_status, st);
     }
     if (rc != RBFFD_OK) return rc;
     note_launches(1);
@@ -1203,6 +1218,8 @@ extern "C" int rbffd_weights_autotune(const double* xy, const int32_t* idx, int6
     for (int wpb = 1; wpb <= 4; ++wpb) {
         all.push_back(WCfg{7, wpb});
         all.push_back(WCfg{8, wpb});
+        all.push_back(WCfg{9, wpb});
+        all.push_back(WCfg{10, wpb});
     }
     std::vector<WCfg> cands;
     for (const WCfg& c : all) {
@@ -1333,7 +1350,8 @@ int rbffd::interp_weights(const double* xy, int64_t Nd, const double* qxy, int64
         if (!cfg_valid(c, n, m)) return RBFFD_ERR_INVALID_ARG;
         const double2* d2 = reinterpret_cast<const double2*>(xy);
         const double2* q2 = reinterpret_cast<const double2*>(qxy);
-        const int rc = c.kernel == 8   ? launch_ns<16, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
+        const int rc = c.kernel == 10  ? launch_ns<8, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
+                       : c.kernel == 8 ? launch_ns<16, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
                        : c.kernel == 4 ? launch_ns<32, NsDF>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1)
                                        : launch_ns<32, NsF64>(c, d2, idx, Nq, n, m, w, node_status, st, q2, Nd, 1);
         if (rc != RBFFD_OK) return rc;

@@ -56,7 +56,8 @@ class Csr(ctypes.Structure):
 
 # rbffd_weights_config.kernel ids
 WEIGHTS_KERNELS = ("null-space", "gauss", "null-space-2warp", "null-space-4warp", "null-space-df",
-                   "null-space-df-2warp", "null-space-df-4warp", "null-space-half", "null-space-df-half")
+                   "null-space-df-2warp", "null-space-df-4warp", "null-space-half", "null-space-df-half",
+                   "null-space-quarter", "null-space-df-quarter")
 
 
 class WeightsConfig(ctypes.Structure):

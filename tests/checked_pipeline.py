@@ -110,11 +110,12 @@ def stencils_and_weights():
             df = "df" in kernel
             if (m == 0 and kernel != "gauss") or (df and not 1 <= m <= 6):
                 continue
-            if "half" in kernel and (m > 4 or n > 32):
+            if ("half" in kernel or "quarter" in kernel) and (m > 4 or n > 32):
                 continue
             # warps per block: 1 for the one-warp kernels, 2 / 4 for the
-            # two- and four-warp ones, 2 (four stencils) for the half-warp ones
-            wpb = 4 if "4warp" in kernel else (2 if ("2warp" in kernel or "half" in kernel) else 1)
+            # two- and four-warp ones, 2 for the half- and quarter-warp ones
+            wpb = 4 if "4warp" in kernel else (2 if ("2warp" in kernel or "half" in kernel or "quarter" in kernel)
+                                               else 1)
             try:
                 rbffd.set_weights_config(n, m, kernel, wpb)
             except rbffd.RbffdError as e:  # does not fit in shared memory at this (n, m)

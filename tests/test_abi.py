@@ -191,9 +191,11 @@ def test_weights_config_table(cdll):
     assert (c.kernel, c.warps_per_block) == (1, 2)
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
     assert cdll.rbffd_weights_get_config(30, 4, ctypes.byref(c)) == 0 and c.kernel == 7
-    for good in ((2, 2), (3, 4), (4, 1), (4, 3), (5, 2), (6, 4), (0, 2), (7, 1), (7, 4), (8, 2)):
+    assert cdll.rbffd_weights_get_config(12, 2, ctypes.byref(c)) == 0 and c.kernel == 9  # FP64, a quarter warp
+    for good in ((2, 2), (3, 4), (4, 1), (4, 3), (5, 2), (6, 4), (0, 2), (7, 1), (7, 4), (8, 2), (9, 1), (10, 4)):
         assert cdll.rbffd_weights_set_config(30, 4, ctypes.byref(rbffd.WeightsConfig(*good, 0.0))) == 0, good
-    for bad in (rbffd.WeightsConfig(9, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
+    for bad in (rbffd.WeightsConfig(11, 1, 0.0), rbffd.WeightsConfig(3, 2, 0.0), rbffd.WeightsConfig(2, 1, 0.0),
+                rbffd.WeightsConfig(9, 5, 0.0), rbffd.WeightsConfig(10, 0, 0.0),
                 rbffd.WeightsConfig(7, 5, 0.0), rbffd.WeightsConfig(8, 0, 0.0),
                 rbffd.WeightsConfig(5, 4, 0.0), rbffd.WeightsConfig(6, 2, 0.0), rbffd.WeightsConfig(4, 5, 0.0),
                 rbffd.WeightsConfig(0, 5, 0.0),
@@ -202,6 +204,7 @@ def test_weights_config_table(cdll):
     # double-float kernels only up to m = 6
     assert cdll.rbffd_weights_set_config(90, 8, ctypes.byref(rbffd.WeightsConfig(4, 1, 0.0))) == 1
     assert cdll.rbffd_weights_set_config(90, 8, ctypes.byref(rbffd.WeightsConfig(8, 1, 0.0))) == 1
+    assert cdll.rbffd_weights_set_config(90, 8, ctypes.byref(rbffd.WeightsConfig(10, 1, 0.0))) == 1
     assert cdll.rbffd_weights_set_config(30, 4, None) == 0
     assert cdll.rbffd_weights_set_config(12, 0, ctypes.byref(rbffd.WeightsConfig(0, 1, 0.0))) == 1  # m = 0
     assert cdll.rbffd_weights_set_config(10, 4, ctypes.byref(pin)) == 1  # n < s

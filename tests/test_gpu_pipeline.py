@@ -285,16 +285,16 @@ def test_solve_deterministic(lib):
 # launch configurations of each arithmetic of the null-space weight solve:
 # (kernel, warps per block)
 _NS_CONFIGS = {"fp64": [("null-space", 1), ("null-space", 4), ("null-space-2warp", 2), ("null-space-4warp", 4),
-                        ("null-space-half", 1), ("null-space-half", 4)],
+                        ("null-space-half", 1), ("null-space-half", 4), ("null-space-quarter", 2)],
                "df": [("null-space-df", 1), ("null-space-df", 3), ("null-space-df-2warp", 2),
-                      ("null-space-df-4warp", 4), ("null-space-df-half", 2)]}
+                      ("null-space-df-4warp", 4), ("null-space-df-half", 2), ("null-space-df-quarter", 4)]}
 
 
 @pytest.mark.parametrize("h,m,n", [(0.04, 2, 12), (0.04, 4, 30), (0.05, 6, 56)])
 def test_stencils_and_weights_identical_across_runs_and_launch_shapes(lib, h, m, n):
     """Stencils: identical bits run to run.  Weights: identical bits across
-    every launch configuration of one arithmetic (one, two or four warps or
-    half a warp per stencil, 1 to 4 warps per block): a stencil's arithmetic
+    every launch configuration of one arithmetic (one, two or four warps,
+    half or a quarter of a warp per stencil, 1 to 4 warps per block): a stencil's arithmetic
     is the same whatever the group size (each entry is accumulated by one
     thread in a fixed order; the group reductions are max and argmax)."""
     from paper_2107_03632_gb300 import rbffd
@@ -307,7 +307,7 @@ def test_stencils_and_weights_identical_across_runs_and_launch_shapes(lib, h, m,
         for prec, cfgs in _NS_CONFIGS.items():
             got = []
             for kernel, wpb in cfgs:
-                if "half" in kernel and (m > 4 or n > 32):
+                if ("half" in kernel or "quarter" in kernel) and (m > 4 or n > 32):
                     continue
                 rbffd.set_weights_config(n, m, kernel, wpb)
                 w, st = rbffd.rbffd_weights(xy, idx, m)
